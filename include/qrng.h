@@ -1,0 +1,209 @@
+/*
+ * qrng.h -- C ABI of the GB300 QRNG post-processing library (libqrng_gb300.so).
+ *
+ * The library implements the data-parallel hot path of quantum-random-number post-processing:
+ *   1. a min-entropy estimate of an ADC sample stream with the statistical-distance correction
+ *      of Sec. II (histogram -> H_min -> Gaussian model -> d_U -> Delta H_m -> H_modify);
+ *   2. Toeplitz-hashing randomness extraction k = T r (mod 2) over independent n-bit blocks of a
+ *      raw bit stream (Sec. III.B standard matrix, Sec. III.D modified matrix (A, I_m),
+ *      Sec. III.E block splitting).
+ * Every step runs in CUDA kernels on one GPU; there is no CPU fallback.
+ *
+ * Conventions used by every entry point
+ * -------------------------------------
+ * Bits are packed LSB-first: bit t of a packed buffer is bit (t mod 8) of byte (t / 8).
+ * 0-based indices: raw block r[0..n), seed a[0..L), output k[0..m).
+ *   standard (Sec. III.B, T[i][j] = a_{n+i-j} 1-based):
+ *       k_i = XOR_{j<n}    a[n-1+i-j]   AND r[j],                 L = n+m-1 seed bits
+ *   modified (Sec. III.D, A[i][j] = a_{n-m+i-j} 1-based, then I_m):
+ *       k_i = XOR_{j<n-m}  a[n-m-1+i-j] AND r[j]  XOR r[n-m+i],    L = n-1 seed bits
+ * Block b of a stream occupies raw bits [b n, (b+1) n) and output bits [b m, (b+1) m).
+ *
+ * Pointers: every buffer argument is caller-owned. "device" pointers are CUDA device (or
+ * managed) memory of the context's device; "host" pointers are host memory (pinned memory
+ * gives the fastest copies). The context owns only its workspace, caches and statistics.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ * Extraction calls are asynchronous: they return after enqueueing the work on `stream`.
+ * Calls that return host results (qrng_minentropy, qrng_postprocess_host) synchronise `stream`.
+ *
+ * Errors: every int-returning function returns a qrng_status; on failure the context keeps a
+ * message (qrng_last_error). No function aborts or raises; a kernel never traps.
+ *
+ * Threads: a context may be used by one host thread at a time.
+ */
+#ifndef QRNG_H
+#define QRNG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#if defined(__GNUC__)
+#define QRNG_API __attribute__((visibility("default")))
+#else
+#define QRNG_API
+#endif
+
+typedef enum {
+  QRNG_OK = 0,
+  QRNG_EINVAL = 1,      /* an argument is out of range, misaligned or NULL                  */
+  QRNG_ENOMEM = 2,      /* device or pinned-host allocation failed                          */
+  QRNG_ECUDA = 3,       /* a CUDA runtime call or a kernel launch failed                    */
+  QRNG_ETIMEOUT = 4,    /* a bounded device-side wait gave up; the kernel returned cleanly  */
+  QRNG_EPRECISION = 5,  /* a floating-point rounding guard tripped and could not be repaired */
+  QRNG_ENOTSUP = 6      /* the requested algorithm does not support these arguments         */
+} qrng_status;
+
+typedef struct qrng_ctx qrng_ctx;
+typedef void* qrng_stream_t; /* cudaStream_t */
+
+/* Create a context bound to CUDA device `device` (makes it current on the calling thread).
+ * *out receives the context, or NULL on failure. */
+QRNG_API int qrng_create(qrng_ctx** out, int device);
+
+/* Destroy a context: waits for its outstanding work and frees its workspace. NULL is ignored. */
+QRNG_API void qrng_destroy(qrng_ctx* ctx);
+
+/* Message describing the last failing call on `ctx` ("" if none). Valid until the next call. */
+QRNG_API const char* qrng_last_error(const qrng_ctx* ctx);
+
+/* Static name of a status code. */
+QRNG_API const char* qrng_status_string(int status);
+
+/* ----------------------------------------------------------------------------------------------
+ * Min-entropy estimate (Sec. II)
+ * --------------------------------------------------------------------------------------------*/
+
+typedef struct {
+  double h_modify;   /* corrected min-entropy max(0, h_model - delta_hm), bits per sample (Sec. II.C) */
+  double h_emp;      /* -log2(max_count / count): min-entropy of the measured distribution P'      */
+  double h_model;    /* -log2 max_v P_v of the ideal model P: the Gaussian with the measured mean and
+                        population variance (Sec. II.B), rounded to codes, tails clipped into the
+                        end codes 0 and 2^bits - 1; a point mass when the variance is 0             */
+  double d_u;        /* statistical distance 1/2 sum_v |P'_v - P_v| over every code (Sec. II.C)    */
+  double d_u_peak;   /* the same sum restricted to U = {argmax P'} (reported only)                */
+  double delta_fs;   /* finite-size amplification 1/2 sqrt(2 (2^bits ln 2 + ln(1/eps)) / count)   */
+  double delta_hm;   /* Delta H_m = log2((d_u + delta_fs) / 2^(-bits-1) + 1) (Sec. II.C)          */
+  double mean;       /* sample mean                                                              */
+  double var;        /* population variance                                                      */
+  uint64_t count;    /* number of samples                                                        */
+  uint64_t max_count;/* largest histogram bin                                                    */
+  uint32_t argmax;   /* lowest code holding max_count                                            */
+  uint32_t bits;     /* ADC resolution used                                                      */
+} qrng_hmin_report;
+
+/*
+ * qrng_minentropy -- Sec. II.A (H_min = -log2 max P), Sec. II.B (Gaussian model fixed by the
+ * measured variance), Sec. II.C (statistical distance, correction term Delta H_m, H_modify).
+ *
+ *   samples  device; `count` ADC codes, uint8 when bits <= 8, little-endian uint16 otherwise;
+ *            any alignment.
+ *   count    >= 1 samples.
+ *   bits     ADC resolution, 1..16. A sample >= 2^bits makes the call fail with QRNG_EINVAL.
+ *   eps      confidence parameter of the finite-size term, 0 < eps < 1.
+ *   rep      host; receives the report.
+ * Synchronises `stream`. Uses context workspace for the histogram.
+ */
+QRNG_API int qrng_minentropy(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps,
+                    qrng_hmin_report* rep, qrng_stream_t stream);
+
+/*
+ * Output length of the extractor, Sec. III.B (leftover hash lemma):
+ *   m = floor(n * h_per_sample / bits - 2 log2(1 / eps_lhl)), or 0 if that is not positive.
+ * eps_lhl = 1 drops the security term (m = floor(n h / bits)). Pure host arithmetic.
+ */
+QRNG_API uint64_t qrng_output_length(uint64_t n, double h_per_sample, int bits, double eps_lhl);
+
+/* ----------------------------------------------------------------------------------------------
+ * Toeplitz extraction (Sec. III.B-E)
+ * --------------------------------------------------------------------------------------------*/
+
+enum { QRNG_FORM_STANDARD = 0, QRNG_FORM_MODIFIED = 1 };
+
+enum {
+  QRNG_ALGO_AUTO = 0,     /* pick the fastest supported algorithm (autotuned, cached per shape)   */
+  QRNG_ALGO_DIRECT = 1,   /* bit-packed AND/XOR + parity, each block on its own (Sec. III.B, O(mn)) */
+  QRNG_ALGO_GEMM_TC = 2,  /* all blocks as one GF(2) matrix product T X on tcgen05 tensor cores   */
+  QRNG_ALGO_FFT64 = 3,    /* circulant embedding + FP64 FFT convolution per block (Sec. III.B-D) */
+  QRNG_ALGO_FFT32_SEG = 4 /* FP32 FFT over short segments with a proven rounding bound, parities
+                             of the segments XOR-combined                                          */
+};
+
+/* Seed length in bits: n+m-1 (standard) or n-1 (modified); 0 for an invalid shape. */
+QRNG_API uint64_t qrng_seed_bits(uint64_t n, uint64_t m, int form);
+
+/*
+ * qrng_toeplitz_extract -- hash num_blocks independent n-bit blocks with one shared seed.
+ *
+ *   raw         device; num_blocks * n bits, block b at bit b*n (packed LSB-first).
+ *   n, m        block length and output length per block; standard: 1 <= m <= n,
+ *               modified: 1 <= m < n; n <= 2^26.
+ *   seed        device; qrng_seed_bits(n, m, form) bits, shared by every block.
+ *   form        QRNG_FORM_STANDARD or QRNG_FORM_MODIFIED.
+ *   algo        QRNG_ALGO_*; an algorithm that cannot run these arguments returns QRNG_ENOTSUP.
+ *   num_blocks  >= 1.
+ *   out         device; ceil(num_blocks*m / 8) bytes; block b's output at bit b*m; the pad bits
+ *               of the last byte are written as 0. Must not overlap raw or seed.
+ * Asynchronous on `stream`. Any pointer alignment is accepted; 16-byte aligned raw and out with
+ * n and m multiples of 128 take the copy-free path.
+ */
+QRNG_API int qrng_toeplitz_extract(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed,
+                          int form, int algo, uint64_t num_blocks, uint8_t* out, qrng_stream_t stream);
+
+/* ----------------------------------------------------------------------------------------------
+ * Whole pipeline on host buffers
+ * --------------------------------------------------------------------------------------------*/
+
+/*
+ * qrng_postprocess_host -- the post-processing of Sec. II + III on host memory: copy the ADC
+ * samples to the device, estimate H_modify (as qrng_minentropy), size the output
+ * m = qrng_output_length(n, H_modify, bits, eps_lhl), treat the sample bytes as the raw bit
+ * stream (sample s occupies raw bits [8s, 8s+8) for bits <= 8, [16s, 16s+16) otherwise), hash
+ * its floor(total_bits / n) whole n-bit blocks, and copy the packed output back.
+ *
+ *   samples_host   host; count samples as for qrng_minentropy.
+ *   seed_host      host; at least seed_capacity_bits bits; must cover qrng_seed_bits(n, m, form).
+ *   out_host       host; out_capacity_bytes bytes; must hold ceil(num_blocks*m/8) bytes.
+ *   m_out, num_blocks_out, rep   host; receive m, the number of blocks and the entropy report
+ *                  (any of them may be NULL).
+ * Returns QRNG_EINVAL when m comes out 0 or a capacity is too small (m_out / num_blocks_out
+ * are still written). Synchronises `stream`.
+ */
+QRNG_API int qrng_postprocess_host(qrng_ctx* ctx, const void* samples_host, uint64_t count, int bits, double eps,
+                          double eps_lhl, uint64_t n, const uint8_t* seed_host, uint64_t seed_capacity_bits,
+                          int form, int algo, uint8_t* out_host, uint64_t out_capacity_bytes, uint64_t* m_out,
+                          uint64_t* num_blocks_out, qrng_hmin_report* rep, qrng_stream_t stream);
+
+/* ----------------------------------------------------------------------------------------------
+ * Statistics
+ * --------------------------------------------------------------------------------------------*/
+
+typedef struct {
+  int last_algo;                 /* algorithm the last extraction ran (QRNG_ALGO_*)            */
+  uint32_t last_kernels;         /* kernels the last extraction call launched                   */
+  uint64_t kernels_launched;     /* kernels launched by this context since creation / reset    */
+  double worst_fft_round_err;    /* max |s - round(s)| seen by the FFT paths since the reset    */
+  uint64_t timed_launches;       /* main extraction kernels timed since the reset (see below)   */
+  double timed_ms;               /* their summed device time, from CUDA events on their stream  */
+} qrng_stats;
+
+/* Statistics since creation or the last reset. When timing is on, this call waits for the
+ * timed launches to finish (it synchronises their events). */
+QRNG_API int qrng_get_stats(qrng_ctx* ctx, qrng_stats* out);
+QRNG_API int qrng_reset_stats(qrng_ctx* ctx);
+
+/* Timing of the main extraction kernel of each qrng_toeplitz_extract call (on = 1, off = 0):
+ * a CUDA event pair is recorded around that one launch on the caller's stream and summed into
+ * timed_ms / timed_launches. At most 4096 launches are kept between two qrng_get_stats calls;
+ * later ones are not timed. */
+QRNG_API int qrng_set_timing(qrng_ctx* ctx, int on);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QRNG_H */

@@ -1,0 +1,367 @@
+// C ABI of the library (declared in include/qrng.h): argument checks, workspace, dispatch of the
+// min-entropy and extraction kernels, and the host-buffer pipeline.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <cstdio>
+#include <new>
+#include <string>
+
+#include "qrng_internal.h"
+
+using namespace qrng;
+
+namespace {
+
+int fail(qrng_ctx* ctx, int status, const std::string& msg) {
+  if (ctx) ctx->err = msg;
+  return status;
+}
+
+int cuda_fail(qrng_ctx* ctx, cudaError_t e, const char* where) {
+  std::string msg = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  return fail(ctx, e == cudaErrorMemoryAllocation ? QRNG_ENOMEM : QRNG_ECUDA, msg);
+}
+
+#define QRNG_CUDA(ctx, call, where)                 \
+  do {                                              \
+    cudaError_t e_ = (call);                        \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, where); \
+  } while (0)
+
+constexpr size_t kMaxTimed = 4096;
+
+// Brackets one launch with a CUDA event pair on its stream when timing is on.
+struct LaunchTimer {
+  qrng_ctx* ctx;
+  cudaStream_t s;
+  size_t slot = (size_t)-1;
+  LaunchTimer(qrng_ctx* c, cudaStream_t st) : ctx(c), s(st) {
+    if (!ctx->timing || ctx->ev_used >= kMaxTimed) return;
+    if (ctx->ev_used == ctx->ev_start.size()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return;
+      if (cudaEventCreate(&b) != cudaSuccess) {
+        cudaEventDestroy(a);
+        return;
+      }
+      ctx->ev_start.push_back(a);
+      ctx->ev_end.push_back(b);
+    }
+    slot = ctx->ev_used;
+    if (cudaEventRecord(ctx->ev_start[slot], s) != cudaSuccess) slot = (size_t)-1;
+  }
+  void done() {
+    if (slot == (size_t)-1) return;
+    if (cudaEventRecord(ctx->ev_end[slot], s) == cudaSuccess) ctx->ev_used = slot + 1;
+    slot = (size_t)-1;
+  }
+};
+
+bool shape_ok(uint64_t n, uint64_t m, int form) {
+  if (n == 0 || m == 0 || n > kMaxBlockBits) return false;
+  if (form == QRNG_FORM_STANDARD) return m <= n;
+  if (form == QRNG_FORM_MODIFIED) return m < n;
+  return false;
+}
+
+// Direct bit-packed extraction of word-aligned or arbitrary layouts.
+int extract_direct(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
+                   uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels) {
+  const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
+  const uint64_t L_t = n_t + m - 1;
+
+  const uint64_t rev_words = kSeedFrontWords + ceil_div(L_t, 32) + kSeedBackWords;
+  QRNG_CUDA(ctx, ctx->seed_rev.ensure(rev_words * 4), "seed workspace");
+  QRNG_CUDA(ctx, launch_seed_reverse(seed, L_t, ctx->seed_rev.as<uint32_t>(), rev_words, s, kernels), "seed reverse");
+
+  DirectArgs a{};
+  const bool raw_direct = (n % 32 == 0) && ((reinterpret_cast<uintptr_t>(raw) & 3) == 0);
+  if (raw_direct) {
+    a.raw = reinterpret_cast<const uint32_t*>(raw);
+    a.raw_stride = n / 32;
+  } else {
+    const uint64_t stride = ceil_div(n, 32);
+    QRNG_CUDA(ctx, ctx->raw_stage.ensure(num_blocks * stride * 4), "raw staging workspace");
+    QRNG_CUDA(ctx, launch_repack_blocks(raw, 0, n, num_blocks, ctx->raw_stage.as<uint32_t>(), stride, s, kernels),
+              "raw repack");
+    a.raw = ctx->raw_stage.as<uint32_t>();
+    a.raw_stride = stride;
+  }
+  const uint64_t mw = ceil_div(m, 32);
+  const bool out_direct = (m % 32 == 0) && ((reinterpret_cast<uintptr_t>(out) & 3) == 0);
+  uint32_t* out_w;
+  if (out_direct) {
+    out_w = reinterpret_cast<uint32_t*>(out);
+  } else {
+    QRNG_CUDA(ctx, ctx->out_stage.ensure(num_blocks * mw * 4), "output staging workspace");
+    out_w = ctx->out_stage.as<uint32_t>();
+  }
+
+  a.nw_t = (uint32_t)ceil_div(n_t, 32);
+  a.tail_mask = (n_t % 32) ? ((1u << (n_t % 32)) - 1u) : 0xffffffffu;
+  a.m = (uint32_t)m;
+  a.mw = (uint32_t)mw;
+  a.seed_rev = ctx->seed_rev.as<uint32_t>();
+  a.modified = (form == QRNG_FORM_MODIFIED);
+  a.id_off = (uint32_t)(n - m);
+  a.out = out_w;
+  a.out_stride = mw;
+  a.num_blocks = num_blocks;
+  const uint64_t per_warp = (uint64_t)direct_outputs_per_warp();
+  const uint64_t R = per_warp / 32;
+  a.tiles = (uint32_t)ceil_div(m, per_warp);
+  const uint64_t base_warps = num_blocks * a.tiles;
+  const uint64_t target_warps = (uint64_t)ctx->num_sms * 32;
+  uint64_t splits = 1;
+  if (base_warps < target_warps) {
+    splits = ceil_div(target_warps, base_warps);
+    const uint64_t max_splits = ceil_div(a.nw_t, R);
+    if (splits > max_splits) splits = max_splits;
+  }
+  uint64_t wps = ceil_div(ceil_div(a.nw_t, splits), R) * R;
+  splits = ceil_div(a.nw_t, wps);
+  a.splits = (uint32_t)splits;
+  a.words_per_split = (uint32_t)wps;
+  if (splits > 1) QRNG_CUDA(ctx, cudaMemsetAsync(out_w, 0, num_blocks * mw * 4, s), "output clear");
+  LaunchTimer timer(ctx, s);
+  QRNG_CUDA(ctx, launch_direct(a, s, kernels), "direct extraction kernel");
+  timer.done();
+  if (!out_direct)
+    QRNG_CUDA(ctx, launch_pack_blocks(out_w, mw, m, num_blocks, out, s, kernels), "output pack");
+  return QRNG_OK;
+}
+
+int minentropy_dev(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps, qrng_hmin_report* rep,
+                   cudaStream_t s) {
+  const uint64_t K = 1ull << bits;
+  uint32_t kernels = 0;
+  QRNG_CUDA(ctx, ctx->hist.ensure((K + 1) * sizeof(unsigned long long)), "histogram workspace");
+  QRNG_CUDA(ctx, ctx->result.ensure(sizeof(DevHminResult)), "result workspace");
+  QRNG_CUDA(ctx, launch_histogram(samples, count, bits, ctx->hist.as<unsigned long long>(), ctx->num_sms, s, &kernels),
+            "histogram kernel");
+  QRNG_CUDA(ctx, launch_hmin_finalize(ctx->hist.as<unsigned long long>(), bits, eps, ctx->result.as<DevHminResult>(),
+                                      s, &kernels),
+            "min-entropy finaliser kernel");
+  QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->result_host, ctx->result.p, sizeof(DevHminResult), cudaMemcpyDeviceToHost, s),
+            "report copy");
+  QRNG_CUDA(ctx, cudaStreamSynchronize(s), "min-entropy synchronise");
+  ctx->stats.kernels_launched += kernels;
+  const DevHminResult& r = *ctx->result_host;
+  if (r.out_of_range)
+    return fail(ctx, QRNG_EINVAL, "qrng_minentropy: " + std::to_string(r.out_of_range) + " samples are >= 2^bits");
+  if (r.status != QRNG_OK) return fail(ctx, r.status, "qrng_minentropy: finaliser reported an error");
+  *rep = r.rep;
+  return QRNG_OK;
+}
+
+int check_minentropy_args(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps,
+                          const qrng_hmin_report* rep) {
+  if (!samples || !rep) return fail(ctx, QRNG_EINVAL, "qrng_minentropy: NULL pointer");
+  if (count == 0) return fail(ctx, QRNG_EINVAL, "qrng_minentropy: count must be >= 1");
+  if (bits < 1 || bits > 16) return fail(ctx, QRNG_EINVAL, "qrng_minentropy: bits must be in [1, 16]");
+  if (!(eps > 0.0 && eps < 1.0)) return fail(ctx, QRNG_EINVAL, "qrng_minentropy: eps must be in (0, 1)");
+  return QRNG_OK;
+}
+
+int check_extract_args(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
+                       int algo, uint64_t num_blocks, const uint8_t* out) {
+  if (!raw || !seed || !out) return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: NULL pointer");
+  if (form != QRNG_FORM_STANDARD && form != QRNG_FORM_MODIFIED)
+    return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: unknown form");
+  if (!shape_ok(n, m, form))
+    return fail(ctx, QRNG_EINVAL,
+                "qrng_toeplitz_extract: need 1 <= m <= n (standard) or 1 <= m < n (modified), n <= 2^26");
+  if (num_blocks == 0) return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: num_blocks must be >= 1");
+  if (num_blocks > (1ull << 62) / n) return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: stream too long");
+  if (algo < QRNG_ALGO_AUTO || algo > QRNG_ALGO_FFT32_SEG)
+    return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: unknown algorithm");
+  return QRNG_OK;
+}
+
+int extract_dispatch(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
+                     int algo, uint64_t num_blocks, uint8_t* out, cudaStream_t s) {
+  uint32_t kernels = 0;
+  int st;
+  int used = algo == QRNG_ALGO_AUTO ? QRNG_ALGO_DIRECT : algo;
+  switch (used) {
+    case QRNG_ALGO_DIRECT:
+      st = extract_direct(ctx, raw, n, m, seed, form, num_blocks, out, s, &kernels);
+      break;
+    default:
+      return fail(ctx, QRNG_ENOTSUP, "qrng_toeplitz_extract: algorithm not available for these arguments");
+  }
+  ctx->stats.kernels_launched += kernels;
+  if (st == QRNG_OK) {
+    ctx->stats.last_algo = used;
+    ctx->stats.last_kernels = kernels;
+  }
+  return st;
+}
+
+}  // namespace
+
+extern "C" {
+
+int qrng_create(qrng_ctx** out, int device) {
+  if (!out) return QRNG_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return QRNG_EINVAL;
+  if (cudaSetDevice(device) != cudaSuccess) return QRNG_ECUDA;
+  qrng_ctx* ctx = new (std::nothrow) qrng_ctx();
+  if (!ctx) return QRNG_ENOMEM;
+  ctx->device = device;
+  if (cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+    delete ctx;
+    return QRNG_ECUDA;
+  }
+  if (cudaMallocHost(reinterpret_cast<void**>(&ctx->result_host), sizeof(DevHminResult)) != cudaSuccess) {
+    delete ctx;
+    return QRNG_ENOMEM;
+  }
+  *out = ctx;
+  return QRNG_OK;
+}
+
+void qrng_destroy(qrng_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  cudaDeviceSynchronize();
+  ctx->hist.release();
+  ctx->result.release();
+  ctx->seed_rev.release();
+  ctx->raw_stage.release();
+  ctx->out_stage.release();
+  ctx->samples_dev.release();
+  ctx->out_dev.release();
+  ctx->seed_dev.release();
+  if (ctx->result_host) cudaFreeHost(ctx->result_host);
+  for (cudaEvent_t e : ctx->ev_start) cudaEventDestroy(e);
+  for (cudaEvent_t e : ctx->ev_end) cudaEventDestroy(e);
+  delete ctx;
+}
+
+const char* qrng_last_error(const qrng_ctx* ctx) { return ctx ? ctx->err.c_str() : "no context"; }
+
+const char* qrng_status_string(int status) {
+  switch (status) {
+    case QRNG_OK: return "QRNG_OK";
+    case QRNG_EINVAL: return "QRNG_EINVAL";
+    case QRNG_ENOMEM: return "QRNG_ENOMEM";
+    case QRNG_ECUDA: return "QRNG_ECUDA";
+    case QRNG_ETIMEOUT: return "QRNG_ETIMEOUT";
+    case QRNG_EPRECISION: return "QRNG_EPRECISION";
+    case QRNG_ENOTSUP: return "QRNG_ENOTSUP";
+    default: return "unknown status";
+  }
+}
+
+int qrng_minentropy(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps, qrng_hmin_report* rep,
+                    qrng_stream_t stream) {
+  if (!ctx) return QRNG_EINVAL;
+  int st = check_minentropy_args(ctx, samples, count, bits, eps, rep);
+  if (st) return st;
+  QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+  return minentropy_dev(ctx, samples, count, bits, eps, rep, static_cast<cudaStream_t>(stream));
+}
+
+uint64_t qrng_output_length(uint64_t n, double h_per_sample, int bits, double eps_lhl) {
+  if (bits < 1 || !(h_per_sample >= 0.0) || !(eps_lhl > 0.0 && eps_lhl <= 1.0)) return 0;
+  const double m = (double)n * h_per_sample / (double)bits - 2.0 * log2(1.0 / eps_lhl);
+  if (!(m > 0.0)) return 0;
+  return (uint64_t)floor(m);
+}
+
+uint64_t qrng_seed_bits(uint64_t n, uint64_t m, int form) {
+  if (!shape_ok(n, m, form)) return 0;
+  return form == QRNG_FORM_STANDARD ? n + m - 1 : n - 1;
+}
+
+int qrng_toeplitz_extract(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
+                          int algo, uint64_t num_blocks, uint8_t* out, qrng_stream_t stream) {
+  if (!ctx) return QRNG_EINVAL;
+  int st = check_extract_args(ctx, raw, n, m, seed, form, algo, num_blocks, out);
+  if (st) return st;
+  QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+  return extract_dispatch(ctx, raw, n, m, seed, form, algo, num_blocks, out, static_cast<cudaStream_t>(stream));
+}
+
+int qrng_postprocess_host(qrng_ctx* ctx, const void* samples_host, uint64_t count, int bits, double eps,
+                          double eps_lhl, uint64_t n, const uint8_t* seed_host, uint64_t seed_capacity_bits,
+                          int form, int algo, uint8_t* out_host, uint64_t out_capacity_bytes, uint64_t* m_out,
+                          uint64_t* num_blocks_out, qrng_hmin_report* rep, qrng_stream_t stream) {
+  if (!ctx) return QRNG_EINVAL;
+  if (!samples_host || !seed_host || !out_host) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: NULL pointer");
+  if (form != QRNG_FORM_STANDARD && form != QRNG_FORM_MODIFIED)
+    return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: unknown form");
+  if (n < 2 || n > kMaxBlockBits) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: n must be in [2, 2^26]");
+  qrng_hmin_report local{};
+  int st = check_minentropy_args(ctx, samples_host, count, bits, eps, &local);
+  if (st) return st;
+  if (!(eps_lhl > 0.0 && eps_lhl <= 1.0)) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: eps_lhl in (0, 1]");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+
+  const uint64_t bytes = count * (bits <= 8 ? 1 : 2);
+  QRNG_CUDA(ctx, ctx->samples_dev.ensure(bytes), "sample workspace");
+  QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->samples_dev.p, samples_host, bytes, cudaMemcpyHostToDevice, s), "sample upload");
+  st = minentropy_dev(ctx, ctx->samples_dev.p, count, bits, eps, &local, s);
+  if (st) return st;
+  if (rep) *rep = local;
+
+  uint64_t m = qrng_output_length(n, local.h_modify, bits, eps_lhl);
+  if (form == QRNG_FORM_MODIFIED && m >= n) m = n - 1;
+  if (m > n) m = n;
+  const uint64_t num_blocks = bytes * 8 / n;
+  if (m_out) *m_out = m;
+  if (num_blocks_out) *num_blocks_out = num_blocks;
+  if (m == 0) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: the corrected min-entropy gives m = 0");
+  if (num_blocks == 0) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: fewer than n raw bits");
+  const uint64_t L = qrng_seed_bits(n, m, form);
+  if (seed_capacity_bits < L) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: seed shorter than the hash needs");
+  const uint64_t out_bytes = ceil_div(num_blocks * m, 8);
+  if (out_capacity_bytes < out_bytes) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: output buffer too small");
+
+  QRNG_CUDA(ctx, ctx->seed_dev.ensure(ceil_div(L, 8)), "seed workspace");
+  QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->seed_dev.p, seed_host, ceil_div(L, 8), cudaMemcpyHostToDevice, s), "seed upload");
+  QRNG_CUDA(ctx, ctx->out_dev.ensure(out_bytes), "output workspace");
+  st = extract_dispatch(ctx, ctx->samples_dev.as<uint8_t>(), n, m, ctx->seed_dev.as<uint8_t>(), form, algo,
+                        num_blocks, ctx->out_dev.as<uint8_t>(), s);
+  if (st) return st;
+  QRNG_CUDA(ctx, cudaMemcpyAsync(out_host, ctx->out_dev.p, out_bytes, cudaMemcpyDeviceToHost, s), "output download");
+  QRNG_CUDA(ctx, cudaStreamSynchronize(s), "pipeline synchronise");
+  return QRNG_OK;
+}
+
+int qrng_get_stats(qrng_ctx* ctx, qrng_stats* out) {
+  if (!ctx || !out) return QRNG_EINVAL;
+  for (size_t i = 0; i < ctx->ev_used; ++i) {
+    float ms = 0.f;
+    QRNG_CUDA(ctx, cudaEventSynchronize(ctx->ev_end[i]), "timing event wait");
+    QRNG_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_start[i], ctx->ev_end[i]), "timing event read");
+    ctx->stats.timed_ms += ms;
+    ctx->stats.timed_launches += 1;
+  }
+  ctx->ev_used = 0;
+  *out = ctx->stats;
+  return QRNG_OK;
+}
+
+int qrng_reset_stats(qrng_ctx* ctx) {
+  if (!ctx) return QRNG_EINVAL;
+  for (size_t i = 0; i < ctx->ev_used; ++i) cudaEventSynchronize(ctx->ev_end[i]);
+  ctx->ev_used = 0;
+  ctx->stats = qrng_stats{};
+  return QRNG_OK;
+}
+
+int qrng_set_timing(qrng_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return QRNG_EINVAL;
+  ctx->timing = (on == 1);
+  return QRNG_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,240 @@
+// Min-entropy estimate of an ADC sample stream (Sec. II of the paper):
+//   1. exact histogram of the codes (warp-privatised shared-memory counters, one pass over HBM);
+//   2. a one-CTA FP64 finaliser: H_min of the measured distribution (Sec. II.A), the Gaussian
+//      model fixed by the measured mean and variance (Sec. II.B), the statistical distance d_U,
+//      the finite-size term, Delta H_m and H_modify (Sec. II.C).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "qrng_internal.h"
+
+namespace qrng {
+namespace {
+
+constexpr int kHistThreads = 256;
+constexpr int kHistWarps = kHistThreads / 32;
+
+// bits <= 8: each warp owns 256 counters; codes >= 2^bits land in counters the merge step
+// adds to the out-of-range total.
+__global__ void __launch_bounds__(kHistThreads) hist_u8_kernel(const uint8_t* __restrict__ samples, uint64_t count,
+                                                                int bits, unsigned long long* __restrict__ hist) {
+  __shared__ uint32_t sh[kHistWarps][256];
+  for (int i = threadIdx.x; i < kHistWarps * 256; i += blockDim.x) (&sh[0][0])[i] = 0;
+  __syncthreads();
+  uint32_t* my = sh[threadIdx.x >> 5];
+
+  // Bytes before the first 16-byte boundary, then 16-byte vectors, then the tail.
+  const uint64_t head = (16 - (reinterpret_cast<uintptr_t>(samples) & 15)) & 15;
+  const uint64_t nhead = head < count ? head : count;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  if (tid < nhead) atomicAdd(&my[samples[tid]], 1u);
+  const uint64_t nvec = (count - nhead) / 16;
+  const uint4* vec = reinterpret_cast<const uint4*>(samples + nhead);
+  for (uint64_t v = tid; v < nvec; v += nthreads) {
+    uint4 x = __ldcs(vec + v);
+    uint32_t w[4] = {x.x, x.y, x.z, x.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+#pragma unroll
+      for (int s = 0; s < 32; s += 8) atomicAdd(&my[(w[k] >> s) & 0xffu], 1u);
+    }
+  }
+  const uint64_t tail0 = nhead + nvec * 16;
+  if (tail0 + tid < count) atomicAdd(&my[samples[tail0 + tid]], 1u);
+  __syncthreads();
+
+  const uint32_t K = 1u << bits;
+  for (int b = threadIdx.x; b < 256; b += blockDim.x) {
+    uint32_t s = 0;
+#pragma unroll
+    for (int w = 0; w < kHistWarps; ++w) s += sh[w][b];
+    if (s) atomicAdd(&hist[b < (int)K ? b : (int)K], (unsigned long long)s);
+  }
+}
+
+// 9 <= bits <= 13: one shared histogram per CTA (<= 8192 counters + one out-of-range counter).
+__global__ void __launch_bounds__(kHistThreads) hist_u16_smem_kernel(const uint16_t* __restrict__ samples,
+                                                                      uint64_t count, int bits,
+                                                                      unsigned long long* __restrict__ hist) {
+  extern __shared__ uint32_t shc[];
+  const uint32_t K = 1u << bits;
+  for (uint32_t i = threadIdx.x; i <= K; i += blockDim.x) shc[i] = 0;
+  __syncthreads();
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t s = tid; s < count; s += nthreads) {
+    uint32_t v = __ldcs(samples + s);
+    atomicAdd(&shc[v < K ? v : K], 1u);
+  }
+  __syncthreads();
+  for (uint32_t b = threadIdx.x; b <= K; b += blockDim.x)
+    if (shc[b]) atomicAdd(&hist[b], (unsigned long long)shc[b]);
+}
+
+// 14 <= bits <= 16: counters straight in global memory.
+__global__ void __launch_bounds__(kHistThreads) hist_u16_global_kernel(const uint16_t* __restrict__ samples,
+                                                                        uint64_t count, int bits,
+                                                                        unsigned long long* __restrict__ hist) {
+  const uint32_t K = 1u << bits;
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t s = tid; s < count; s += nthreads) {
+    uint32_t v = __ldcs(samples + s);
+    atomicAdd(&hist[v < K ? v : K], 1ull);
+  }
+}
+
+// ------------------------------------------------------------------------------------------------
+// Finaliser: one CTA.
+// ------------------------------------------------------------------------------------------------
+
+constexpr int kFinThreads = 512;
+
+__device__ __forceinline__ double std_normal_cdf(double z) { return 0.5 * erfc(-z * M_SQRT1_2); }
+
+// Model probability of code v under N(mu, sigma^2), rounded to codes, tails clipped to the end codes.
+__device__ __forceinline__ double model_cell(uint32_t v, uint32_t K, double mu, double sigma) {
+  double lo = (v == 0) ? 0.0 : std_normal_cdf(((double)v - 0.5 - mu) / sigma);
+  double hi = (v == K - 1) ? 1.0 : std_normal_cdf(((double)v + 0.5 - mu) / sigma);
+  return hi - lo;
+}
+
+__global__ void __launch_bounds__(kFinThreads) hmin_finalize_kernel(const unsigned long long* __restrict__ hist,
+                                                                     int bits, double eps,
+                                                                     DevHminResult* __restrict__ out) {
+  typedef unsigned __int128 u128;
+  __shared__ unsigned long long s_n[kFinThreads];
+  __shared__ unsigned long long s_max[kFinThreads];
+  __shared__ uint32_t s_arg[kFinThreads];
+  __shared__ u128 s_s1[kFinThreads];
+  __shared__ u128 s_s2[kFinThreads];
+  __shared__ double s_pmax[kFinThreads];
+  __shared__ double s_dsum[kFinThreads];
+  __shared__ double s_mu, s_sigma;
+  __shared__ int s_point;
+
+  const uint32_t K = 1u << bits;
+  const int t = threadIdx.x;
+
+  // Pass 1: count, exact first and second moments, largest bin (lowest code on ties).
+  unsigned long long n = 0, mx = 0;
+  uint32_t arg = 0xffffffffu;
+  u128 s1 = 0, s2 = 0;
+  for (uint32_t v = t; v < K; v += kFinThreads) {
+    unsigned long long h = hist[v];
+    n += h;
+    s1 += (u128)v * h;
+    s2 += (u128)((unsigned long long)v * v) * h;
+    if (arg == 0xffffffffu || h > mx) {  // codes visited in increasing order: ties keep the lowest
+      mx = h;
+      arg = v;
+    }
+  }
+  s_n[t] = n; s_max[t] = mx; s_arg[t] = arg; s_s1[t] = s1; s_s2[t] = s2;
+  __syncthreads();
+  for (int w = kFinThreads / 2; w > 0; w >>= 1) {
+    if (t < w) {
+      s_n[t] += s_n[t + w];
+      s_s1[t] += s_s1[t + w];
+      s_s2[t] += s_s2[t + w];
+      unsigned long long m2 = s_max[t + w];
+      uint32_t a2 = s_arg[t + w];
+      if (a2 != 0xffffffffu && (s_arg[t] == 0xffffffffu || m2 > s_max[t] || (m2 == s_max[t] && a2 < s_arg[t]))) {
+        s_max[t] = m2;
+        s_arg[t] = a2;
+      }
+    }
+    __syncthreads();
+  }
+  const unsigned long long N = s_n[0];
+  if (N == 0) {
+    if (t == 0) out->status = QRNG_EINVAL;
+    return;
+  }
+  if (t == 0) {
+    const u128 S1 = s_s1[0], S2 = s_s2[0];
+    const u128 num = (u128)N * S2 - S1 * S1;  // N^2 * population variance, exact
+    const double mu = (double)S1 / (double)N;
+    const double var = (double)num / ((double)N * (double)N);
+    s_mu = mu;
+    s_sigma = sqrt(var);
+    s_point = (num == 0);
+    qrng_hmin_report& r = out->rep;
+    r.count = N;
+    r.max_count = s_max[0];
+    r.argmax = s_arg[0];
+    r.bits = (uint32_t)bits;
+    r.mean = mu;
+    r.var = var;
+    r.h_emp = -log2((double)s_max[0] / (double)N);
+    out->out_of_range = hist[K];
+  }
+  __syncthreads();
+
+  // Pass 2: model cells, their maximum, and the distance to the measured distribution.
+  const double mu = s_mu, sigma = s_sigma;
+  const int point = s_point;
+  const uint32_t amax = s_arg[0];
+  double pmax = 0.0, dsum = 0.0;
+  for (uint32_t v = t; v < K; v += kFinThreads) {
+    double P = point ? (v == amax ? 1.0 : 0.0) : model_cell(v, K, mu, sigma);
+    pmax = fmax(pmax, P);
+    dsum += fabs((double)hist[v] / (double)N - P);
+  }
+  s_pmax[t] = pmax;
+  s_dsum[t] = dsum;
+  __syncthreads();
+  for (int w = kFinThreads / 2; w > 0; w >>= 1) {
+    if (t < w) {
+      s_pmax[t] = fmax(s_pmax[t], s_pmax[t + w]);
+      s_dsum[t] += s_dsum[t + w];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    qrng_hmin_report& r = out->rep;
+    r.h_model = -log2(s_pmax[0]);
+    r.d_u = 0.5 * s_dsum[0];
+    double Pa = point ? 1.0 : model_cell(amax, K, mu, sigma);
+    r.d_u_peak = 0.5 * fabs((double)s_max[0] / (double)N - Pa);
+    r.delta_fs = 0.5 * sqrt(2.0 * ((double)K * M_LN2 + log(1.0 / eps)) / (double)N);
+    r.delta_hm = log2((r.d_u + r.delta_fs) * ldexp(1.0, bits + 1) + 1.0);
+    double h = r.h_model - r.delta_hm;
+    r.h_modify = h > 0.0 ? h : 0.0;
+    out->status = out->out_of_range ? QRNG_EINVAL : QRNG_OK;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_histogram(const void* samples, uint64_t count, int bits, unsigned long long* hist, int num_sms,
+                             cudaStream_t s, uint32_t* kernels) {
+  const uint32_t K = 1u << bits;
+  cudaError_t e = cudaMemsetAsync(hist, 0, (K + 1) * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  const uint64_t per_cta = bits <= 8 ? 16ull * kHistThreads * 8 : (uint64_t)kHistThreads * 16;
+  uint64_t want = ceil_div(count, per_cta);
+  uint64_t cap = (uint64_t)num_sms * (bits <= 8 ? 6 : 4);
+  int grid = (int)(want < cap ? (want ? want : 1) : cap);
+  if (bits <= 8) {
+    hist_u8_kernel<<<grid, kHistThreads, 0, s>>>(static_cast<const uint8_t*>(samples), count, bits, hist);
+  } else if (bits <= 13) {
+    hist_u16_smem_kernel<<<grid, kHistThreads, (K + 1) * sizeof(uint32_t), s>>>(
+        static_cast<const uint16_t*>(samples), count, bits, hist);
+  } else {
+    hist_u16_global_kernel<<<grid, kHistThreads, 0, s>>>(static_cast<const uint16_t*>(samples), count, bits, hist);
+  }
+  ++*kernels;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_hmin_finalize(const unsigned long long* hist, int bits, double eps, DevHminResult* out,
+                                 cudaStream_t s, uint32_t* kernels) {
+  hmin_finalize_kernel<<<1, kFinThreads, 0, s>>>(hist, bits, eps, out);
+  ++*kernels;
+  return cudaGetLastError();
+}
+
+}  // namespace qrng

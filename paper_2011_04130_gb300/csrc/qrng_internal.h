@@ -1,0 +1,117 @@
+// Internal declarations shared by the library's translation units (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/qrng.h"
+
+namespace qrng {
+
+// Front padding (in 32-bit words) of the bit-reversed seed buffer, so that every window the
+// extraction kernels read sits at a non-negative word index.
+constexpr int kSeedFrontWords = 64;
+// Back padding beyond the last seed word.
+constexpr int kSeedBackWords = 72;
+
+constexpr uint64_t kMaxBlockBits = 1ull << 26;
+
+inline uint64_t ceil_div(uint64_t a, uint64_t b) { return (a + b - 1) / b; }
+
+// Grow-only device buffer owned by a context.
+struct DevBuf {
+  void* p = nullptr;
+  size_t cap = 0;
+  cudaError_t ensure(size_t bytes) {
+    if (bytes <= cap) return cudaSuccess;
+    if (p) {
+      cudaError_t e = cudaFree(p);
+      p = nullptr;
+      cap = 0;
+      if (e != cudaSuccess) return e;
+    }
+    size_t want = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&p, want);
+    if (e != cudaSuccess) {
+      p = nullptr;
+      return e;
+    }
+    cap = want;
+    return cudaSuccess;
+  }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+  }
+  template <class T>
+  T* as() const { return static_cast<T*>(p); }
+};
+
+// Device-side min-entropy result: the public report plus the count of out-of-range samples.
+struct DevHminResult {
+  qrng_hmin_report rep;
+  unsigned long long out_of_range;
+  int status;
+};
+
+// ---- histogram + finaliser (k_hist.cu) ----
+// hist: (2^bits + 1) uint64 counters, the last one counts samples >= 2^bits. Zeroed by the launcher.
+cudaError_t launch_histogram(const void* samples, uint64_t count, int bits, unsigned long long* hist, int num_sms,
+                             cudaStream_t s, uint32_t* kernels);
+cudaError_t launch_hmin_finalize(const unsigned long long* hist, int bits, double eps, DevHminResult* out,
+                                 cudaStream_t s, uint32_t* kernels);
+
+// ---- bit layout helpers (k_bits.cu) ----
+// Bit-reversed, padded copy of seed bits [0, L): word kSeedFrontWords+w, bit t holds a[L-1-(32w+t)]
+// (zero outside [0, L)). rev_words = kSeedFrontWords + ceil(L/32) + kSeedBackWords.
+cudaError_t launch_seed_reverse(const uint8_t* seed, uint64_t L, uint32_t* rev, uint64_t rev_words, cudaStream_t s,
+                                uint32_t* kernels);
+// Copy num_blocks blocks of n bits (block b at bit raw_bit_off + b*n of src) into word-aligned
+// blocks of `stride_w` words each, bits beyond n zero.
+cudaError_t launch_repack_blocks(const uint8_t* src, uint64_t raw_bit_off, uint64_t n, uint64_t num_blocks,
+                                 uint32_t* dst, uint64_t stride_w, cudaStream_t s, uint32_t* kernels);
+// Pack per-block word-aligned outputs (stride_w words per block, m valid bits each) into a
+// bit-contiguous stream at bit out_bit_off of dst (bits outside the range untouched except
+// the pad bits of the final byte when out_bit_off == 0, which are zeroed).
+cudaError_t launch_pack_blocks(const uint32_t* src, uint64_t stride_w, uint64_t m, uint64_t num_blocks, uint8_t* dst,
+                               cudaStream_t s, uint32_t* kernels);
+
+// ---- direct bit-packed extraction (k_direct.cu) ----
+struct DirectArgs {
+  const uint32_t* raw;   // word-aligned blocks
+  uint64_t raw_stride;   // words per block
+  uint32_t nw_t;         // words of the Toeplitz part: ceil(n_t/32), n_t = n (standard) or n-m (modified)
+  uint32_t tail_mask;    // valid bits of word nw_t-1
+  uint32_t m;
+  uint32_t mw;           // ceil(m/32)
+  const uint32_t* seed_rev;  // from launch_seed_reverse with L = n_t + m - 1
+  int modified;
+  uint32_t id_off;       // n - m (modified only)
+  uint32_t* out;         // word-aligned outputs
+  uint64_t out_stride;   // words per block
+  uint64_t num_blocks;
+  uint32_t tiles;        // output tiles per block
+  uint32_t splits;       // split of the raw words across warps (XOR-combined)
+  uint32_t words_per_split;
+};
+int direct_outputs_per_warp();
+cudaError_t launch_direct(const DirectArgs& a, cudaStream_t s, uint32_t* kernels);
+
+}  // namespace qrng
+
+struct qrng_ctx {
+  int device = 0;
+  int num_sms = 0;
+  std::string err;
+  qrng::DevBuf hist, result, seed_rev, raw_stage, out_stage, samples_dev, out_dev, seed_dev;
+  qrng::DevHminResult* result_host = nullptr;  // pinned
+  qrng_stats stats{};
+  // optional CUDA-event timing of the main extraction kernel
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_start, ev_end;
+  size_t ev_used = 0;
+};

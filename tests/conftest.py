@@ -19,3 +19,28 @@ def oracle_mod():
 
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def qlib():
+    """The CUDA library, built in-tree if it is missing or stale (nvcc cross-compiles without a GPU)."""
+    from paper_2011_04130_gb300 import _build
+
+    _build.build()
+    import paper_2011_04130_gb300 as q
+
+    q.load_library()
+    return q
+
+
+@pytest.fixture(scope="session")
+def gpu(qlib):
+    """A library context on cuda:0 (GPU tests only)."""
+    import torch
+
+    assert torch.cuda.is_available(), "GPU tests need a CUDA device"
+    torch.cuda.set_device(0)
+    ctx = qlib.Context(0)
+    yield ctx
+    torch.cuda.synchronize()
+    ctx.close()

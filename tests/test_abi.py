@@ -1,0 +1,86 @@
+"""The C ABI without a GPU: the library loads, exports every function include/qrng.h declares,
+and its pure host functions agree with the oracle. No compute call is made here."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = []
+    for fn in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if fn.endswith(".h"):
+            txt = open(os.path.join(ROOT, "include", fn)).read()
+            names += re.findall(r"QRNG_API\s+[\w\s\*]*?\b(qrng_\w+)\s*\(", txt)
+    return names
+
+
+def test_header_declares_entry_points():
+    names = _declared()
+    assert "qrng_minentropy" in names and "qrng_toeplitz_extract" in names
+    assert len(names) == len(set(names))
+
+
+def test_library_exports_every_declared_symbol(qlib):
+    import ctypes
+
+    import paper_2011_04130_gb300 as q
+
+    lib = q.load_library()
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert isinstance(getattr(lib, name), ctypes._CFuncPtr)
+    assert set(_declared()) == set(q.EXPORTED)
+
+
+def test_no_internal_symbols_exported(qlib):
+    import subprocess
+
+    import paper_2011_04130_gb300 as q
+
+    out = subprocess.run(["nm", "-D", "--defined-only", q.LIB_PATH], capture_output=True, text=True).stdout
+    syms = [l.split()[-1] for l in out.splitlines() if " T " in l]
+    assert sorted(syms) == sorted(_declared())
+
+
+@pytest.mark.parametrize("n,h,bits,eps", [(1024, 8.0, 8, 2.0 ** -10), (4096, 4.0, 8, 1.0), (1000, 3.3, 5, 0.5),
+                                          (100, 0.1, 8, 1e-6), (65536, 4.4567, 8, 1.0), (1 << 20, 11.9, 16, 1e-9)])
+def test_output_length_matches_oracle(qlib, oracle_mod, n, h, bits, eps):
+    import paper_2011_04130_gb300 as q
+
+    assert q.qrng_output_length(n, h, bits, eps) == oracle_mod.output_length(n, h, bits, eps)
+
+
+@pytest.mark.parametrize("n,m,form", [(10, 4, 0), (10, 10, 0), (10, 4, 1), (10, 10, 1), (5, 0, 0), (1 << 27, 3, 0)])
+def test_seed_bits(qlib, oracle_mod, n, m, form):
+    import paper_2011_04130_gb300 as q
+
+    valid = m >= 1 and ((form == 0 and m <= n) or (form == 1 and m < n)) and n <= (1 << 26)
+    want = oracle_mod.seed_bits(n, m, form) if valid else 0
+    assert q.qrng_seed_bits(n, m, form) == want
+
+
+def test_create_rejects_bad_device(qlib):
+    import paper_2011_04130_gb300 as q
+
+    with pytest.raises(q.QrngError):
+        q.Context(10_000)
+
+
+def test_status_strings(qlib):
+    import paper_2011_04130_gb300 as q
+
+    assert q.qrng_status_string(q.QRNG_OK) == "QRNG_OK"
+    assert q.qrng_status_string(q.QRNG_ENOTSUP) == "QRNG_ENOTSUP"
+
+
+def test_product_package_does_not_import_oracle():
+    """The product path never reaches the oracle: no reference to it in the package sources."""
+    pkg = os.path.join(ROOT, "paper_2011_04130_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        for fn in files:
+            if fn.endswith((".py", ".cu", ".h", ".cpp")):
+                txt = open(os.path.join(dirpath, fn)).read()
+                assert "import oracle" not in txt and "qrng_oracle" not in txt and "liboracle" not in txt, fn

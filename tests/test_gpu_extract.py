@@ -1,0 +1,178 @@
+"""GPU parity of qrng_toeplitz_extract against the oracle (Sec. III.B standard, Sec. III.D modified,
+Sec. III.E blocks). Bar: bit-exact.
+
+Small and medium shapes are compared in full. The full-size workloads are compared on every
+block with the oracle's Freivalds check (64 random parity tests per block, escape probability
+2^-64) and on sampled output bits computed one by one by the oracle.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import extract, spot_check
+
+pytestmark = pytest.mark.gpu
+
+STD, MOD = 0, 1
+ALGOS = {"direct": 1}
+
+
+def _seed_len(n, m, form):
+    return n + m - 1 if form == STD else n - 1
+
+
+def _case(n, m, form, B, s):
+    raw = W.random_bits(n * B, 1000 + s)
+    seed = W.random_bits(_seed_len(n, m, form), 2000 + s)
+    return raw, seed
+
+
+SMALL = [
+    (1, 1, STD, 1), (2, 1, MOD, 3), (2, 2, STD, 5), (31, 7, STD, 5), (32, 32, STD, 4), (33, 17, MOD, 7),
+    (64, 1, STD, 9), (100, 99, MOD, 2), (1000, 333, STD, 5), (1000, 333, MOD, 5), (4096, 2048, STD, 1),
+    (4096, 3072, MOD, 16), (4101, 1000, STD, 3), (3000, 2900, STD, 2), (2048, 1024, MOD, 40),
+    (511, 257, STD, 33), (1 << 12, (1 << 12) - 1, MOD, 2), (777, 777, STD, 3),
+]
+
+
+@pytest.mark.parametrize("algo", list(ALGOS))
+@pytest.mark.parametrize("n,m,form,B", SMALL)
+def test_small_shapes_bit_exact(qlib, gpu, oracle_mod, algo, n, m, form, B):
+    raw, seed = _case(n, m, form, B, n * 31 + m + B)
+    want = oracle_mod.toeplitz_blocks(raw, n, m, seed, form, B)
+    got = extract(qlib, gpu, raw, n, m, seed, form, ALGOS[algo], B)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("algo", list(ALGOS))
+@pytest.mark.parametrize("raw_off,seed_off,out_off", [(1, 0, 0), (0, 3, 0), (0, 0, 1), (5, 7, 2), (4, 4, 4)])
+@pytest.mark.parametrize("n,m,form,B", [(4096, 2048, STD, 3), (1000, 333, MOD, 4), (256, 96, MOD, 8)])
+def test_unaligned_pointers(qlib, gpu, oracle_mod, algo, raw_off, seed_off, out_off, n, m, form, B):
+    raw, seed = _case(n, m, form, B, 7 + raw_off + 3 * out_off)
+    want = oracle_mod.toeplitz_blocks(raw, n, m, seed, form, B)
+    got = extract(qlib, gpu, raw, n, m, seed, form, ALGOS[algo], B, raw_off, seed_off, out_off)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("algo", list(ALGOS))
+def test_single_long_block_full(qlib, gpu, oracle_mod, algo):
+    n, m = 1 << 16, 36_000
+    raw, seed = _case(n, m, STD, 1, 99)
+    want = oracle_mod.toeplitz(raw, n, m, seed, STD)
+    assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, STD, ALGOS[algo], 1), want)
+
+
+@pytest.mark.parametrize("algo", list(ALGOS))
+def test_identity_block_with_zero_seed(qlib, gpu, algo):
+    n, m, B = 4096, 3000, 6
+    raw = W.random_bits(n * B, 55)
+    seed = np.zeros((n - 1 + 7) // 8, dtype=np.uint8)
+    got = np.unpackbits(extract(qlib, gpu, raw, n, m, seed, MOD, ALGOS[algo], B), bitorder="little")
+    bits = np.unpackbits(raw, bitorder="little")
+    for b in range(B):
+        assert np.array_equal(got[b * m:(b + 1) * m], bits[b * n + n - m:(b + 1) * n])
+
+
+@pytest.mark.parametrize("algo", list(ALGOS))
+def test_all_ones(qlib, gpu, oracle_mod, algo):
+    """Every raw and seed bit set: each output is the parity of the row's seed-bit count."""
+    n, m, B = 2048, 1500, 4
+    raw = np.full(n * B // 8, 0xFF, dtype=np.uint8)
+    seed = W.pack_bits(np.ones(n + m - 1, dtype=np.uint8))
+    want = oracle_mod.toeplitz_blocks(raw, n, m, seed, STD, B)
+    assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, STD, ALGOS[algo], B), want)
+
+
+def test_laser_stream_full_size(qlib, gpu, oracle_mod):
+    """2^26 ADC samples as a 2^29-bit raw stream, n = 2^16, m = floor(n H_modify / 8), one shared seed."""
+    import torch
+
+    c = W.CFG2
+    samples = W.adc_samples(c["samples"], c["sample_seed"])
+    dev = torch.from_numpy(samples).to("cuda")
+    rep = qlib.qrng_minentropy(gpu, dev, bits=8, eps=c["eps"])
+    n = c["n"]
+    m = qlib.qrng_output_length(n, rep["h_modify"], 8, 1.0)
+    assert m == oracle_mod.output_length(n, oracle_mod.minentropy(samples, 8, c["eps"])["h_modify"], 8, 1.0)
+    B = samples.size * 8 // n
+    seed = W.random_bits(n + m - 1, c["seed_seed"])
+    got = extract(qlib, gpu, samples, n, m, seed, STD, qlib.QRNG_ALGO_AUTO, B)
+    mism = oracle_mod.freivalds(samples, n, m, seed, STD, B, got)
+    assert not mism.any(), f"{np.count_nonzero(mism)} blocks fail the Freivalds check"
+    spot_check(oracle_mod, samples, n, m, seed, STD, got, blocks=[0, 1, B // 2, B - 1], per_block=128)
+
+
+@pytest.mark.parametrize("log2n", [10, 12, 14, 16, 18, 20, 22, 24])
+def test_block_length_sweep_point(qlib, gpu, oracle_mod, log2n):
+    """Fixed 2^30-bit stream, modified form, m = 0.75 n. Every block is Freivalds-checked where the
+    oracle's O(nm) preparation is affordable; otherwise sampled bits of several blocks are checked."""
+    c = W.CFG3
+    n = 1 << log2n
+    m = int(n * c["ratio"])
+    B = c["stream_bits"] // n
+    raw = W.random_bits(c["stream_bits"], c["raw_seed"])
+    seed = W.random_bits(n - 1, c["seed_seed"] + log2n)
+    got = extract(qlib, gpu, raw, n, m, seed, MOD, qlib.QRNG_ALGO_AUTO, B)
+    if n * m <= (1 << 31):
+        mism = oracle_mod.freivalds(raw, n, m, seed, MOD, B, got)
+        assert not mism.any()
+    blocks = sorted({0, 1, B // 3, B - 1})
+    spot_check(oracle_mod, raw, n, m, seed, MOD, got, blocks=blocks, per_block=64 if n > (1 << 20) else 256)
+
+
+def test_tensor_core_shape(qlib, gpu, oracle_mod):
+    """One standard seed, m = 6144, n = 8192, 4096 blocks."""
+    c = W.CFG4
+    n, m, B = c["n"], c["m"], c["blocks"]
+    raw = W.random_bits(n * B, c["raw_seed"])
+    seed = W.random_bits(n + m - 1, c["seed_seed"])
+    got = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_AUTO, B)
+    assert not oracle_mod.freivalds(raw, n, m, seed, STD, B, got).any()
+    spot_check(oracle_mod, raw, n, m, seed, STD, got, blocks=[0, 5, B - 1])
+
+
+def test_maximum_block_length(qlib, gpu, oracle_mod):
+    """n = 2^26 (the largest block), short output, every output bit checked."""
+    n, m = 1 << 26, 96
+    raw, seed = _case(n, m, STD, 1, 4242)
+    got = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_DIRECT, 1)
+    want = oracle_mod.toeplitz_bits(raw, n, m, seed, STD, np.arange(m, dtype=np.uint64))
+    assert np.array_equal(np.unpackbits(got, bitorder="little")[:m], want)
+
+
+def test_bad_arguments(qlib, gpu):
+    import torch
+
+    t = torch.zeros(1 << 12, dtype=torch.uint8, device="cuda")
+    bad = [
+        (64, 65, STD, 1, 1),   # m > n
+        (64, 64, MOD, 1, 1),   # modified needs m < n
+        (64, 0, STD, 1, 1),
+        (0, 0, STD, 1, 1),
+        (64, 8, 7, 1, 1),      # unknown form
+        (64, 8, STD, 9, 1),    # unknown algorithm
+        (64, 8, STD, 1, 0),    # no blocks
+        ((1 << 26) + 1, 8, STD, 1, 1),
+    ]
+    for n, m, form, algo, B in bad:
+        with pytest.raises(qlib.QrngError) as e:
+            qlib.qrng_toeplitz_extract(gpu, t, n, m, t, form, algo, B, t)
+        assert e.value.status == qlib.QRNG_EINVAL, (n, m, form, algo, B)
+    with pytest.raises(qlib.QrngError):
+        qlib.qrng_toeplitz_extract(gpu, 0, 64, 8, t, STD, 1, 1, t)
+
+
+def test_postprocess_host_pipeline(qlib, gpu, oracle_mod):
+    """Host buffers in, host buffer out: entropy, sizing and extraction in one call."""
+    c = W.CFG1
+    samples = W.adc_samples(c["samples"] * 4, 77)
+    n = 4096
+    seed = W.random_bits(2 * n - 1, 78)
+    out = np.zeros(samples.size, dtype=np.uint8)
+    m, B, rep = qlib.qrng_postprocess_host(gpu, samples, samples.size, 8, 1e-6, 1.0, n, seed, 2 * n - 1, STD,
+                                           qlib.QRNG_ALGO_AUTO, out, out.size)
+    ref = oracle_mod.minentropy(samples, 8, 1e-6)
+    assert abs(rep["h_modify"] - ref["h_modify"]) < 1e-12
+    assert m == oracle_mod.output_length(n, ref["h_modify"], 8, 1.0) and B == samples.size * 8 // n
+    want = oracle_mod.toeplitz_blocks(samples, n, m, seed, STD, B)
+    assert np.array_equal(out[:want.size], want)

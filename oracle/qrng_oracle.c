@@ -203,8 +203,16 @@ int oracle_histogram(const void* samples, uint64_t count, int bits, uint64_t* hi
   return ORACLE_OK;
 }
 
-/* Standard normal CDF. */
-static double Phi(double z) { return 0.5 * erfc(-z / sqrt(2.0)); }
+/* Mass of the standard normal law on (y, z], y < z, either end possibly infinite; this is
+ * Phi(z) - Phi(y), written so that no two nearly equal numbers are subtracted: both ends above
+ * the mean -> difference of upper-tail masses, both below -> difference of lower-tail masses,
+ * ends on either side of the mean -> sum of two central masses. */
+static double std_normal_mass(double y, double z) {
+  const double r = sqrt(0.5);
+  if (y >= 0.0) return 0.5 * (erfc(y * r) - erfc(z * r));
+  if (z <= 0.0) return 0.5 * (erfc(-z * r) - erfc(-y * r));
+  return 0.5 * (erf(z * r) - erf(y * r));
+}
 
 /* Min-entropy report from an exact histogram (the steps of Sec. II in the paper's order). */
 int oracle_minentropy_from_hist(const uint64_t* hist, int bits, double eps, oracle_hmin_report* rep) {
@@ -244,9 +252,10 @@ int oracle_minentropy_from_hist(const uint64_t* hist, int bits, double eps, orac
   } else {
     double sigma = sqrt(var);
     for (uint64_t v = 0; v < K; ++v) {
-      double lo = (v == 0) ? 0.0 : Phi(((double)v - 0.5 - mu) / sigma);
-      double hi = (v == K - 1) ? 1.0 : Phi(((double)v + 0.5 - mu) / sigma);
-      P[v] = hi - lo;
+      /* code v collects the real line between v - 1/2 and v + 1/2; the end codes take the tails */
+      double lo = (v == 0) ? -INFINITY : ((double)v - 0.5 - mu) / sigma;
+      double hi = (v == K - 1) ? INFINITY : ((double)v + 0.5 - mu) / sigma;
+      P[v] = std_normal_mass(lo, hi);
     }
   }
   double pmax = 0.0;

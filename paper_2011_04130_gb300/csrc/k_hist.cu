@@ -5,6 +5,7 @@
 //      the finite-size term, Delta H_m and H_modify (Sec. II.C).
 #include <cuda_runtime.h>
 #include <math.h>
+#include <math_constants.h>
 #include <stdint.h>
 
 #include "qrng_internal.h"
@@ -92,13 +93,22 @@ __global__ void __launch_bounds__(kHistThreads) hist_u16_global_kernel(const uin
 
 constexpr int kFinThreads = 512;
 
-__device__ __forceinline__ double std_normal_cdf(double z) { return 0.5 * erfc(-z * M_SQRT1_2); }
+// Phi(z) - Phi(y) for y < z (either may be infinite) without cancellation: tails as differences
+// of tail masses on their own side of the mean, a cell across the mean as a sum of central masses.
+// (Subtracting two CDF values near 1/2 would lose ~1e-16 absolute, i.e. ~1e-12 relative for the
+// 6e-5 cells of a 16-bit ADC.)
+__device__ __forceinline__ double std_normal_mass(double y, double z) {
+  if (y >= 0.0) return 0.5 * (erfc(y * M_SQRT1_2) - erfc(z * M_SQRT1_2));
+  if (z <= 0.0) return 0.5 * (erfc(-z * M_SQRT1_2) - erfc(-y * M_SQRT1_2));
+  return 0.5 * (erf(z * M_SQRT1_2) - erf(y * M_SQRT1_2));
+}
 
-// Model probability of code v under N(mu, sigma^2), rounded to codes, tails clipped to the end codes.
+// Model probability of code v under N(mu, sigma^2): the real line between v - 1/2 and v + 1/2,
+// the end codes also taking the tails (the ADC rounds and clips).
 __device__ __forceinline__ double model_cell(uint32_t v, uint32_t K, double mu, double sigma) {
-  double lo = (v == 0) ? 0.0 : std_normal_cdf(((double)v - 0.5 - mu) / sigma);
-  double hi = (v == K - 1) ? 1.0 : std_normal_cdf(((double)v + 0.5 - mu) / sigma);
-  return hi - lo;
+  const double lo = (v == 0) ? -CUDART_INF : ((double)v - 0.5 - mu) / sigma;
+  const double hi = (v == K - 1) ? CUDART_INF : ((double)v + 0.5 - mu) / sigma;
+  return std_normal_mass(lo, hi);
 }
 
 __global__ void __launch_bounds__(kFinThreads) hmin_finalize_kernel(const unsigned long long* __restrict__ hist,

@@ -24,8 +24,9 @@ MUTANTS = {
     "modified_seed_mirrored": ("a[n - m - 1 + i - j] & r[j]", "a[i + j] & r[j]"),
     "msb_first_bit_order": ("return (buf[t >> 3] >> (t & 7)) & 1;", "return (buf[t >> 3] >> (7 - (t & 7))) & 1;"),
     # entropy
-    "half_cell_shift": ("Phi(((double)v - 0.5 - mu) / sigma)", "Phi(((double)v - mu) / sigma)"),
-    "lower_tail_dropped": ("double lo = (v == 0) ? 0.0 :", "double lo = (v == 0) ? Phi((-0.5 - mu) / sigma) :"),
+    "half_cell_shift": ("((double)v - 0.5 - mu) / sigma;", "((double)v - mu) / sigma;"),
+    "lower_tail_dropped": ("double lo = (v == 0) ? -INFINITY :", "double lo = (v == 0) ? (-0.5 - mu) / sigma :"),
+    "central_cell_sign": ("return 0.5 * (erf(z * r) - erf(y * r));", "return 0.5 * (erf(z * r) + erf(y * r));"),
     "sample_variance": ("double var = (double)num / ((double)N * (double)N);",
                         "double var = (double)num / ((double)N * (double)(N - 1));"),
     "distance_missing_half": ("rep->d_u = 0.5 * d;", "rep->d_u = d;"),

@@ -46,6 +46,8 @@ def parse():
     p.add_argument("--algo", default="auto")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--blocks", type=int, default=0,
+                   help="hash only the first BLOCKS blocks (a smaller case for profiler captures)")
     return p.parse_args()
 
 
@@ -130,6 +132,8 @@ def run_ours(args, world, rank, local):
     seed_h = W.random_bits(2 * n - 1, c["seed_seed"])  # long enough for any m <= n
     seed = torch.from_numpy(seed_h).to(dev)
     num_blocks = samples_h.size * 8 // n
+    if args.blocks:
+        num_blocks = min(num_blocks, args.blocks)
     out = torch.empty((num_blocks * n + 7) // 8, dtype=torch.uint8, device=dev)
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 

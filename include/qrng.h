@@ -196,6 +196,11 @@ typedef struct {
 QRNG_API int qrng_get_stats(qrng_ctx* ctx, qrng_stats* out);
 QRNG_API int qrng_reset_stats(qrng_ctx* ctx);
 
+/* Waits for `stream` and reports device-side failures of the work enqueued so far: returns
+ * QRNG_ETIMEOUT (and clears the condition) when a kernel's bounded wait gave up, in which case
+ * the output of that call is incomplete. Kernels never trap or hang on such a failure. */
+QRNG_API int qrng_synchronize(qrng_ctx* ctx, qrng_stream_t stream);
+
 /* Timing of the main extraction kernel of each qrng_toeplitz_extract call (on = 1, off = 0):
  * a CUDA event pair is recorded around that one launch on the caller's stream and summed into
  * timed_ms / timed_launches. At most 4096 launches are kept between two qrng_get_stats calls;

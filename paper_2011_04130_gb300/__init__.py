@@ -22,7 +22,7 @@ ALGO_NAMES = {QRNG_ALGO_AUTO: "auto", QRNG_ALGO_DIRECT: "direct", QRNG_ALGO_GEMM
 
 EXPORTED = ["qrng_create", "qrng_destroy", "qrng_last_error", "qrng_status_string", "qrng_minentropy",
             "qrng_output_length", "qrng_seed_bits", "qrng_toeplitz_extract", "qrng_postprocess_host",
-            "qrng_get_stats", "qrng_reset_stats", "qrng_set_timing"]
+            "qrng_get_stats", "qrng_reset_stats", "qrng_set_timing", "qrng_synchronize"]
 
 
 class QrngError(RuntimeError):
@@ -96,6 +96,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qrng_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.qrng_reset_stats.argtypes = [vp]
     lib.qrng_set_timing.argtypes = [vp, i32]
+    lib.qrng_synchronize.argtypes = [vp, vp]
     _lib = lib
     return lib
 
@@ -235,3 +236,8 @@ def qrng_reset_stats(ctx: Context):
 
 def qrng_set_timing(ctx: Context, on: bool):
     ctx.check(load_library().qrng_set_timing(ctx.handle, 1 if on else 0), "qrng_set_timing")
+
+
+def qrng_synchronize(ctx: Context, stream=None):
+    """Wait for the stream; raises QrngError(QRNG_ETIMEOUT) if a kernel's bounded wait gave up."""
+    ctx.check(load_library().qrng_synchronize(ctx.handle, _stream(stream)), "qrng_synchronize")

@@ -67,9 +67,9 @@ bool shape_ok(uint64_t n, uint64_t m, int form) {
   return false;
 }
 
-// Direct bit-packed extraction of word-aligned or arbitrary layouts.
-int extract_direct(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
-                   uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels) {
+// Bit-packed extraction (direct kernel or tensor-core GEMM) of word-aligned or arbitrary layouts.
+int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed,
+                    int form, uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels) {
   const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
   const uint64_t L_t = n_t + m - 1;
 
@@ -110,6 +110,15 @@ int extract_direct(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, co
   a.out = out_w;
   a.out_stride = mw;
   a.num_blocks = num_blocks;
+  if (algo == QRNG_ALGO_GEMM_TC) {
+    QRNG_CUDA(ctx, ctx->dev_err.ensure(sizeof(int)), "error word");
+    LaunchTimer timer(ctx, s);
+    QRNG_CUDA(ctx, launch_gemm_tc(a, ctx->dev_err.as<int>(), ctx->num_sms, s, kernels), "tensor-core extraction kernel");
+    timer.done();
+    if (!out_direct)
+      QRNG_CUDA(ctx, launch_pack_blocks(out_w, mw, m, num_blocks, out, s, kernels), "output pack");
+    return QRNG_OK;
+  }
   const uint64_t per_warp = (uint64_t)direct_outputs_per_warp();
   const uint64_t R = per_warp / 32;
   a.tiles = (uint32_t)ceil_div(m, per_warp);
@@ -185,10 +194,16 @@ int extract_dispatch(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, 
                      int algo, uint64_t num_blocks, uint8_t* out, cudaStream_t s) {
   uint32_t kernels = 0;
   int st;
+  const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
   int used = algo == QRNG_ALGO_AUTO ? QRNG_ALGO_DIRECT : algo;
   switch (used) {
     case QRNG_ALGO_DIRECT:
-      st = extract_direct(ctx, raw, n, m, seed, form, num_blocks, out, s, &kernels);
+      st = extract_bitwise(ctx, used, raw, n, m, seed, form, num_blocks, out, s, &kernels);
+      break;
+    case QRNG_ALGO_GEMM_TC:
+      if (n_t > kGemmMaxColumns)
+        return fail(ctx, QRNG_ENOTSUP, "qrng_toeplitz_extract: the tensor-core path needs n (n-m modified) <= 2^22");
+      st = extract_bitwise(ctx, used, raw, n, m, seed, form, num_blocks, out, s, &kernels);
       break;
     default:
       return fail(ctx, QRNG_ENOTSUP, "qrng_toeplitz_extract: algorithm not available for these arguments");
@@ -222,6 +237,12 @@ int qrng_create(qrng_ctx** out, int device) {
     delete ctx;
     return QRNG_ENOMEM;
   }
+  if (ctx->dev_err.ensure(sizeof(int)) != cudaSuccess || cudaMemset(ctx->dev_err.p, 0, sizeof(int)) != cudaSuccess) {
+    cudaFreeHost(ctx->result_host);
+    ctx->dev_err.release();
+    delete ctx;
+    return QRNG_ENOMEM;
+  }
   *out = ctx;
   return QRNG_OK;
 }
@@ -238,6 +259,7 @@ void qrng_destroy(qrng_ctx* ctx) {
   ctx->samples_dev.release();
   ctx->out_dev.release();
   ctx->seed_dev.release();
+  ctx->dev_err.release();
   if (ctx->result_host) cudaFreeHost(ctx->result_host);
   for (cudaEvent_t e : ctx->ev_start) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->ev_end) cudaEventDestroy(e);
@@ -332,8 +354,7 @@ int qrng_postprocess_host(qrng_ctx* ctx, const void* samples_host, uint64_t coun
                         num_blocks, ctx->out_dev.as<uint8_t>(), s);
   if (st) return st;
   QRNG_CUDA(ctx, cudaMemcpyAsync(out_host, ctx->out_dev.p, out_bytes, cudaMemcpyDeviceToHost, s), "output download");
-  QRNG_CUDA(ctx, cudaStreamSynchronize(s), "pipeline synchronise");
-  return QRNG_OK;
+  return qrng_synchronize(ctx, stream);
 }
 
 int qrng_get_stats(qrng_ctx* ctx, qrng_stats* out) {
@@ -355,6 +376,21 @@ int qrng_reset_stats(qrng_ctx* ctx) {
   for (size_t i = 0; i < ctx->ev_used; ++i) cudaEventSynchronize(ctx->ev_end[i]);
   ctx->ev_used = 0;
   ctx->stats = qrng_stats{};
+  return QRNG_OK;
+}
+
+int qrng_synchronize(qrng_ctx* ctx, qrng_stream_t stream) {
+  if (!ctx) return QRNG_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+  QRNG_CUDA(ctx, cudaStreamSynchronize(s), "stream synchronise");
+  int code = 0;
+  QRNG_CUDA(ctx, cudaMemcpy(&code, ctx->dev_err.p, sizeof(int), cudaMemcpyDeviceToHost), "error word read");
+  if (code != 0) {
+    QRNG_CUDA(ctx, cudaMemset(ctx->dev_err.p, 0, sizeof(int)), "error word clear");
+    return fail(ctx, QRNG_ETIMEOUT,
+                "a bounded device wait gave up (site " + std::to_string(code) + "); the affected output is incomplete");
+  }
   return QRNG_OK;
 }
 

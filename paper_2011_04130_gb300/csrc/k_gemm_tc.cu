@@ -1,0 +1,383 @@
+// Block-batched Toeplitz hashing on the tcgen05 tensor cores.
+//
+// All blocks of a stream share one seed (Sec. III.E), so hashing them is one matrix product
+//     D[i][b] = sum_j T[i][j] X[b][j],   k_i(block b) = D[i][b] mod 2,
+// with T the m x n Toeplitz matrix (Sec. III.B; the first n-m columns of (A, I_m) for the modified
+// form of Sec. III.D, whose identity part is XORed in the epilogue) and X the raw blocks, one per
+// row. GB300's tcgen05 has no integer (i8) kind, so 0/1 entries are fed as E4M3 values 2^-6
+// (byte 0x08) and the product is accumulated in FP32 in tensor memory: each sum is an integer
+// count c <= n <= 2^26 scaled by 2^-12, exact in FP32 for c < 2^24, and its parity is read from
+// the scaled float in the epilogue.
+//
+// CTA tile: 128 outputs (UMMA M) x 256 blocks (UMMA N), K step 128 (one 128-byte swizzle row).
+//   warps 0-5  producers: build the K-step's operand tiles in shared memory straight from the
+//              packed bits -- T rows from the bit-reversed seed (one funnel-shifted window per
+//              row), X rows from the raw words -- in the canonical K-major SWIZZLE_128B layout;
+//   warp 6     allocates tensor memory and issues tcgen05.mma (one elected lane);
+//   warps 7-10 epilogue: tcgen05.ld the FP32 accumulator, parity, __ballot_sync into output
+//              words (32 outputs of one block per word), identity XOR for the modified form.
+// Stages are handed over with mbarriers; every wait is bounded (about one second of clock),
+// after which the kernel records an error code, stops issuing work, waits for its own MMAs and
+// frees its tensor memory.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qrng_internal.h"
+
+namespace qrng {
+namespace {
+
+constexpr int BM = 128;
+constexpr int BN = 256;
+constexpr int BK = 128;                // fp8 elements (= bytes) per K step
+constexpr int STAGES = 4;
+constexpr int A_BYTES = BM * BK;        // 16 KB
+constexpr int B_BYTES = BN * BK;        // 32 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int PRODUCER_WARPS = 6;
+constexpr int PRODUCERS = PRODUCER_WARPS * 32;
+constexpr int MMA_WARP = PRODUCER_WARPS;
+constexpr int EPI_WARP0 = MMA_WARP + 1;
+constexpr int THREADS = (EPI_WARP0 + 4) * 32;  // 352
+constexpr int TMEM_COLS = 256;
+constexpr uint32_t kOneE4M3 = 0x08u;   // 2^-6
+constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait on phase `parity`; on timeout records `code` and raises the CTA abort flag.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
+                                          int code) {
+  if (mbar_test(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (true) {
+    if (*abort_flag) return false;
+    if (mbar_test(bar, parity)) return true;
+    if (clock64() - t0 > kWaitCycles) {
+      *abort_flag = 1;
+      atomicCAS(err, 0, code);
+      return false;
+    }
+  }
+}
+
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+
+// K-major, SWIZZLE_128B shared-memory matrix descriptor (rows of 128 bytes, 8-row atoms 1024 B apart).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: next 8-row atom
+  d |= (uint64_t)1 << 46;             // descriptor version
+  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor: kind::f8f6f4, D = F32, A = B = E4M3, both K-major, M = 128, N = 256.
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+// Spreads 4 bits to 4 bytes: bit j -> byte j with value kOneE4M3 (the shifted copies x << 7k never
+// overlap for a 4-bit x, so the multiply has no carries).
+__device__ __forceinline__ uint32_t nib_to_e4m3(uint32_t nib) { return (nib * 0x01020408u) & 0x08080808u; }
+static_assert(0x08080808u == kOneE4M3 * 0x01010101u, "spread mask must select the E4M3 encoding of one");
+
+// Writes 32 bits (K elements 32w..32w+31 of one row) as two 16-byte chunks of the swizzled row.
+__device__ __forceinline__ void store_word_e4m3(uint32_t row_addr, uint32_t row, uint32_t w, uint32_t x) {
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const uint32_t y = x >> (16 * h);
+    const uint32_t c = 2 * w + h;
+    const uint32_t addr = row_addr + (((c ^ (row & 7u)) & 7u) << 4);
+    asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(nib_to_e4m3(y & 0xFu)),
+                 "r"(nib_to_e4m3((y >> 4) & 0xFu)), "r"(nib_to_e4m3((y >> 8) & 0xFu)),
+                 "r"(nib_to_e4m3((y >> 12) & 0xFu))
+                 : "memory");
+  }
+}
+
+struct GemmArgs {
+  const uint32_t* raw;
+  uint64_t raw_stride;
+  uint32_t nw_t;
+  uint32_t tail_mask;
+  uint32_t m;
+  uint32_t mw;
+  const uint32_t* seed_rev;
+  int modified;
+  uint32_t id_off;
+  uint32_t* out;
+  uint64_t out_stride;
+  uint64_t num_blocks;
+  uint32_t mtiles;
+  uint32_t ntiles;
+  uint32_t ksteps;
+  int* err;
+};
+
+__global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const GemmArgs a) {
+  extern __shared__ uint8_t dyn_smem[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t accum_full_bar;
+  __shared__ __align__(8) uint64_t accum_empty_bar;
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  const uint32_t warp = threadIdx.x >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t smem_base = (smem_u32(dyn_smem) + 1023u) & ~1023u;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], PRODUCERS);
+      mbar_init(&empty_bar[s], 1);
+    }
+    mbar_init(&accum_full_bar, 1);
+    mbar_init(&accum_empty_bar, 4 * 32);
+    mbar_init(&drain_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_slot;
+
+  const uint64_t ntile_total = (uint64_t)a.mtiles * a.ntiles;
+
+  if (warp < PRODUCER_WARPS) {
+    // ------------------------------------------------------------------ producers
+    const uint32_t p = threadIdx.x;
+    uint32_t stage = 0, phase = 0;
+    for (uint64_t tile = blockIdx.x; tile < ntile_total && !abort_flag; tile += gridDim.x) {
+      const uint32_t mt = (uint32_t)(tile % a.mtiles);
+      const uint32_t nt = (uint32_t)(tile / a.mtiles);
+      for (uint32_t ks = 0; ks < a.ksteps; ++ks) {
+        if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, a.err, 1)) break;
+        const uint32_t sA = smem_base + stage * STAGE_BYTES;
+        const uint32_t sB = sA + A_BYTES;
+        for (uint32_t r = p; r < BM + BN; r += PRODUCERS) {
+          if (r < BM) {
+            // T row i: reversed-seed bits m-1-i+128ks .. +127 (front padding keeps the index >= 0)
+            const int64_t i = (int64_t)mt * BM + r;
+            const int64_t u0 = (int64_t)a.m - 1 - i + (int64_t)ks * BK + 32 * (int64_t)kSeedFrontWords;
+            const uint32_t sh = (uint32_t)(u0 & 31);
+            const uint32_t* src = a.seed_rev + (u0 >> 5);
+            uint32_t wv[5];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) wv[k] = __ldg(src + k);
+            const uint32_t row_addr = sA + r * BK;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) store_word_e4m3(row_addr, r, w, __funnelshift_r(wv[w], wv[w + 1], sh));
+          } else {
+            const uint32_t rb = r - BM;
+            const uint64_t b = (uint64_t)nt * BN + rb;
+            uint32_t wv[4] = {0u, 0u, 0u, 0u};
+            if (b < a.num_blocks) {
+              const uint32_t* src = a.raw + b * a.raw_stride;
+              const uint32_t w0 = ks * 4;
+              if (w0 + 4 <= a.nw_t && (w0 + 4 < a.nw_t || a.tail_mask == 0xffffffffu) &&
+                  ((reinterpret_cast<uintptr_t>(src + w0) & 15) == 0)) {
+                const uint4 v = __ldg(reinterpret_cast<const uint4*>(src + w0));
+                wv[0] = v.x; wv[1] = v.y; wv[2] = v.z; wv[3] = v.w;
+              } else {
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                  const uint32_t wi = w0 + w;
+                  uint32_t x = wi < a.nw_t ? __ldg(src + wi) : 0u;
+                  if (wi == a.nw_t - 1) x &= a.tail_mask;
+                  wv[w] = x;
+                }
+              }
+            }
+            const uint32_t row_addr = sB + rb * BK;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) store_word_e4m3(row_addr, rb, w, wv[w]);
+          }
+        }
+        fence_proxy_async_smem();
+        mbar_arrive(&full_bar[stage]);
+        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+      }
+    }
+  } else if (warp == MMA_WARP) {
+    // ------------------------------------------------------------------ MMA issuer
+    uint32_t stage = 0, phase = 0, acc_phase = 0;
+    bool issued = false;
+    for (uint64_t tile = blockIdx.x; tile < ntile_total && !abort_flag; tile += gridDim.x) {
+      // the epilogue must have drained the previous tile's accumulator
+      if (tile != blockIdx.x && !mbar_wait(&accum_empty_bar, acc_phase ^ 1u, &abort_flag, a.err, 2)) break;
+      for (uint32_t ks = 0; ks < a.ksteps; ++ks) {
+        if (!mbar_wait(&full_bar[stage], phase, &abort_flag, a.err, 3)) break;
+        tc_fence_after();
+        if (lane == 0) {
+          const uint32_t sA = smem_base + stage * STAGE_BYTES;
+          const uint32_t sB = sA + A_BYTES;
+#pragma unroll
+          for (int k = 0; k < BK / 32; ++k) {
+            mma_f8(tmem_base, smem_desc_sw128(sA + 32 * k), smem_desc_sw128(sB + 32 * k), (ks | k) != 0);
+          }
+          mma_commit(&empty_bar[stage]);  // frees the stage once these MMAs have read it
+          issued = true;
+        }
+        __syncwarp();
+        if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+      }
+      if (abort_flag) break;
+      if (lane == 0) mma_commit(&accum_full_bar);
+      __syncwarp();
+      acc_phase ^= 1u;
+    }
+    // wait for every MMA this CTA issued before the tensor memory is released
+    if (lane == 0 && issued) {
+      mma_commit(&drain_bar);
+      const long long t0 = clock64();
+      while (!mbar_test(&drain_bar, 0)) {
+        if (clock64() - t0 > kWaitCycles) {
+          atomicCAS(a.err, 0, 4);
+          break;
+        }
+      }
+    }
+    __syncwarp();
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    const uint32_t q = warp & 3u;  // TMEM lane quarter this warp may access
+    uint32_t acc_phase = 0;
+    for (uint64_t tile = blockIdx.x; tile < ntile_total && !abort_flag; tile += gridDim.x) {
+      const uint32_t mt = (uint32_t)(tile % a.mtiles);
+      const uint32_t nt = (uint32_t)(tile / a.mtiles);
+      if (!mbar_wait(&accum_full_bar, acc_phase, &abort_flag, a.err, 5)) break;
+      tc_fence_after();
+      const uint32_t ow = mt * (BM / 32) + q;  // output word (32 outputs) of every block in this tile
+      const uint32_t rem = (ow < a.mw) ? a.m - 32 * ow : 0u;
+      const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+      for (uint32_t g = 0; g < BN / 32; ++g) {
+        uint32_t v[32];
+        const uint32_t taddr = tmem_base + ((32u * q) << 16) + 32u * g;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+              "=r"(v[30]), "=r"(v[31])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        uint32_t mine = 0;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          // count = value * 2^12 is an integer < 2^24: adding 1.5 * 2^23 leaves it in the low mantissa bits
+          const float cnt = __fmaf_rn(__uint_as_float(v[c]), 4096.0f, 12582912.0f);
+          const uint32_t wrd = __ballot_sync(0xffffffffu, __float_as_uint(cnt) & 1u);
+          if (lane == (uint32_t)c) mine = wrd;
+        }
+        const uint64_t b = (uint64_t)nt * BN + 32u * g + lane;
+        if (ow < a.mw && b < a.num_blocks) {
+          mine &= omask;
+          if (a.modified) {
+            const uint64_t bit = (uint64_t)a.id_off + 32ull * ow;
+            const uint32_t* rr = a.raw + b * a.raw_stride;
+            const uint64_t rq = bit >> 5;
+            const uint32_t rs = (uint32_t)(bit & 31);
+            const uint32_t rlo = __ldg(rr + rq);
+            const uint32_t rhi = (rs && rq + 1 < a.raw_stride) ? __ldg(rr + rq + 1) : 0u;
+            mine ^= __funnelshift_r(rlo, rhi, rs) & omask;
+          }
+          a.out[b * a.out_stride + ow] = mine;
+        }
+      }
+      tc_fence_before();
+      mbar_arrive(&accum_empty_bar);
+      acc_phase ^= 1u;
+    }
+  }
+
+  tc_fence_before();
+  __syncthreads();
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+}  // namespace
+
+size_t gemm_tc_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + 1024; }
+
+cudaError_t launch_gemm_tc(const DirectArgs& d, int* err, int num_sms, cudaStream_t s, uint32_t* kernels) {
+  GemmArgs a{};
+  a.raw = d.raw;
+  a.raw_stride = d.raw_stride;
+  a.nw_t = d.nw_t;
+  a.tail_mask = d.tail_mask;
+  a.m = d.m;
+  a.mw = d.mw;
+  a.seed_rev = d.seed_rev;
+  a.modified = d.modified;
+  a.id_off = d.id_off;
+  a.out = d.out;
+  a.out_stride = d.out_stride;
+  a.num_blocks = d.num_blocks;
+  a.mtiles = (uint32_t)ceil_div(d.m, BM);
+  a.ntiles = (uint32_t)ceil_div(d.num_blocks, BN);
+  a.ksteps = (uint32_t)ceil_div((uint64_t)d.nw_t * 32, BK);
+  a.err = err;
+  const size_t smem = gemm_tc_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const uint64_t tiles = (uint64_t)a.mtiles * a.ntiles;
+  const int grid = (int)(tiles < (uint64_t)num_sms ? tiles : (uint64_t)num_sms);
+  gemm_tc_kernel<<<grid, THREADS, smem, s>>>(a);
+  ++*kernels;
+  return cudaGetLastError();
+}
+
+}  // namespace qrng

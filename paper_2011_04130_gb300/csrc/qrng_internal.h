@@ -101,6 +101,12 @@ struct DirectArgs {
 int direct_outputs_per_warp();
 cudaError_t launch_direct(const DirectArgs& a, cudaStream_t s, uint32_t* kernels);
 
+// ---- tensor-core block-batched extraction (k_gemm_tc.cu) ----
+// Same layout arguments as the direct kernel (splits unused). Exact for n_t <= kGemmMaxColumns.
+constexpr uint64_t kGemmMaxColumns = 1ull << 22;
+size_t gemm_tc_smem_bytes();
+cudaError_t launch_gemm_tc(const DirectArgs& a, int* err, int num_sms, cudaStream_t s, uint32_t* kernels);
+
 }  // namespace qrng
 
 struct qrng_ctx {
@@ -108,6 +114,7 @@ struct qrng_ctx {
   int num_sms = 0;
   std::string err;
   qrng::DevBuf hist, result, seed_rev, raw_stage, out_stage, samples_dev, out_dev, seed_dev;
+  qrng::DevBuf dev_err;  // int error word written by kernels with bounded waits (0 = no error)
   qrng::DevHminResult* result_host = nullptr;  // pinned
   qrng_stats stats{};
   // optional CUDA-event timing of the main extraction kernel

@@ -26,6 +26,7 @@ def extract(q, ctx, raw: np.ndarray, n: int, m: int, seed: np.ndarray, form: int
     out = torch.full((nbytes + out_off + 64,), sentinel, dtype=torch.uint8, device="cuda")
     out_p = out.data_ptr() + out_off
     q.qrng_toeplitz_extract(ctx, raw_p, n, m, seed_p, form, algo, num_blocks, out_p)
+    q.qrng_synchronize(ctx)  # raises if a kernel's bounded wait gave up
     torch.cuda.synchronize()
     host = out.cpu().numpy()
     assert np.all(host[:out_off] == sentinel), "wrote before the output buffer"

@@ -14,7 +14,7 @@ from gpu_util import extract, spot_check
 pytestmark = pytest.mark.gpu
 
 STD, MOD = 0, 1
-ALGOS = {"direct": 1}
+ALGOS = {"direct": 1, "gemm_tc": 2}
 
 
 def _seed_len(n, m, form):
@@ -81,6 +81,43 @@ def test_all_ones(qlib, gpu, oracle_mod, algo):
     seed = W.pack_bits(np.ones(n + m - 1, dtype=np.uint8))
     want = oracle_mod.toeplitz_blocks(raw, n, m, seed, STD, B)
     assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, STD, ALGOS[algo], B), want)
+
+
+@pytest.mark.parametrize("n,m,B", [(1 << 16, 4096, 300), (1 << 22, 1024, 8)])
+def test_gemm_all_ones_largest_sums(qlib, gpu, oracle_mod, n, m, B):
+    """All-ones raw and seed make every tensor-core sum equal to n, the largest count the FP32
+    accumulator has to hold exactly; each output is the parity of n."""
+    raw = np.full(n * B // 8, 0xFF, dtype=np.uint8)
+    seed = W.pack_bits(np.ones(n + m - 1, dtype=np.uint8))
+    got = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_GEMM_TC, B)
+    want = np.zeros(m * B, dtype=np.uint8) + (n & 1)
+    assert np.array_equal(np.unpackbits(got, bitorder="little")[:m * B], want)
+    # and a random seed with all-ones raw bits: each output is the parity of a seed window
+    seed = W.random_bits(n + m - 1, 5)
+    got = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_GEMM_TC, B)
+    spot_check(oracle_mod, raw, n, m, seed, STD, got, blocks=[0, B - 1], per_block=64)
+
+
+@pytest.mark.parametrize("algo", list(ALGOS))
+def test_algorithms_agree_on_laser_stream(qlib, gpu, algo):
+    """Every algorithm gives byte-identical output on the full-size stream."""
+    c = W.CFG2
+    samples = W.adc_samples(c["samples"], c["sample_seed"])
+    n, m = c["n"], 36473
+    B = samples.size * 8 // n
+    seed = W.random_bits(n + m - 1, c["seed_seed"])
+    ref = extract(qlib, gpu, samples, n, m, seed, STD, qlib.QRNG_ALGO_DIRECT, B)
+    got = extract(qlib, gpu, samples, n, m, seed, STD, ALGOS[algo], B)
+    assert np.array_equal(got, ref)
+
+
+def test_gemm_rejects_too_long_blocks(qlib, gpu):
+    import torch
+
+    t = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(qlib.QrngError) as e:
+        qlib.qrng_toeplitz_extract(gpu, t, (1 << 22) + 32, 8, t, STD, qlib.QRNG_ALGO_GEMM_TC, 1, t)
+    assert e.value.status == qlib.QRNG_ENOTSUP
 
 
 def test_laser_stream_full_size(qlib, gpu, oracle_mod):

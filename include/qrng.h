@@ -112,6 +112,29 @@ QRNG_API int qrng_minentropy(qrng_ctx* ctx, const void* samples, uint64_t count,
                     qrng_hmin_report* rep, qrng_stream_t stream);
 
 /*
+ * qrng_minentropy_noalloc -- the same estimate and report as qrng_minentropy, for callers that
+ * cannot allocate device memory. The paper has no counterpart; this is a deployment variant.
+ *
+ * Who it is for: acquisition loops that must not allocate once streaming has started (a device
+ * allocation can block and synchronise the whole GPU, stalling the ADC data path), and programs
+ * whose device memory belongs to another allocator or that keep no context object between calls.
+ * It takes no context and allocates nothing: no cudaMalloc/cudaFree or other allocating call.
+ * Its scratch is a fixed area compiled into the library (a histogram of up to 2^16 codes plus
+ * the device-side report, about 513 KB), held on every GPU that loads the library until exit.
+ *
+ *   samples, count, eps, rep, stream   as for qrng_minentropy; samples on the current device.
+ *   bits   1..16; a larger value (more codes than the fixed histogram holds) is QRNG_EINVAL.
+ * Runs on the calling thread's current CUDA device and synchronises `stream`. Returns only a
+ * status (there is no context to hold a message): QRNG_EINVAL for bad arguments or a sample
+ * >= 2^bits, QRNG_ECUDA when a CUDA call fails.
+ * Every call on a device shares the one scratch area (cleared at the start of each call): calls
+ * whose GPU work overlaps, e.g. on two streams at once, race and return wrong reports. The first
+ * call on a device looks up the scratch's device address; make it before any stream capture.
+ */
+QRNG_API int qrng_minentropy_noalloc(const void* samples, uint64_t count, int bits, double eps,
+                                     qrng_hmin_report* rep, qrng_stream_t stream);
+
+/*
  * Output length of the extractor, Sec. III.B (leftover hash lemma):
  *   m = floor(n * h_per_sample / bits - 2 log2(1 / eps_lhl)), or 0 if that is not positive.
  * eps_lhl = 1 drops the security term (m = floor(n h / bits)). Pure host arithmetic.

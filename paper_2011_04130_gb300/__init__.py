@@ -22,7 +22,8 @@ ALGO_NAMES = {QRNG_ALGO_AUTO: "auto", QRNG_ALGO_DIRECT: "direct", QRNG_ALGO_GEMM
 
 EXPORTED = ["qrng_create", "qrng_destroy", "qrng_last_error", "qrng_status_string", "qrng_minentropy",
             "qrng_output_length", "qrng_seed_bits", "qrng_toeplitz_extract", "qrng_postprocess_host",
-            "qrng_get_stats", "qrng_reset_stats", "qrng_set_timing", "qrng_synchronize"]
+            "qrng_get_stats", "qrng_reset_stats", "qrng_set_timing", "qrng_synchronize",
+            "qrng_minentropy_noalloc"]
 
 
 class QrngError(RuntimeError):
@@ -97,6 +98,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qrng_reset_stats.argtypes = [vp]
     lib.qrng_set_timing.argtypes = [vp, i32]
     lib.qrng_synchronize.argtypes = [vp, vp]
+    lib.qrng_minentropy_noalloc.argtypes = [vp, u64, i32, dbl, ctypes.POINTER(HminReport), vp]
     _lib = lib
     return lib
 
@@ -241,3 +243,16 @@ def qrng_set_timing(ctx: Context, on: bool):
 def qrng_synchronize(ctx: Context, stream=None):
     """Wait for the stream; raises QrngError(QRNG_ETIMEOUT) if a kernel's bounded wait gave up."""
     ctx.check(load_library().qrng_synchronize(ctx.handle, _stream(stream)), "qrng_synchronize")
+
+
+def qrng_minentropy_noalloc(samples, count: int | None = None, bits: int = 8, eps: float = 1e-6,
+                            stream=None) -> dict:
+    """qrng_minentropy without a context and without any device allocation (fixed scratch
+    compiled into the library; see include/qrng.h). Runs on the current CUDA device."""
+    if count is None:
+        count = samples.numel()
+    rep = HminReport()
+    st = load_library().qrng_minentropy_noalloc(_ptr(samples), count, bits, eps, ctypes.byref(rep), _stream(stream))
+    if st != QRNG_OK:
+        raise QrngError(st, "qrng_minentropy_noalloc")
+    return rep.as_dict()

@@ -78,12 +78,15 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
   QRNG_CUDA(ctx, launch_seed_reverse(seed, L_t, ctx->seed_rev.as<uint32_t>(), rev_words, s, kernels), "seed reverse");
 
   DirectArgs a{};
-  const bool raw_direct = (n % 32 == 0) && ((reinterpret_cast<uintptr_t>(raw) & 3) == 0);
+  // The tensor-core kernel loads raw tiles with TMA: 16-byte aligned rows, a multiple of 4 words apart.
+  const bool gemm = (algo == QRNG_ALGO_GEMM_TC);
+  const bool raw_direct = gemm ? (n % 128 == 0) && ((reinterpret_cast<uintptr_t>(raw) & 15) == 0)
+                               : (n % 32 == 0) && ((reinterpret_cast<uintptr_t>(raw) & 3) == 0);
   if (raw_direct) {
     a.raw = reinterpret_cast<const uint32_t*>(raw);
     a.raw_stride = n / 32;
   } else {
-    const uint64_t stride = ceil_div(n, 32);
+    const uint64_t stride = gemm ? ceil_div(n, 128) * 4 : ceil_div(n, 32);
     QRNG_CUDA(ctx, ctx->raw_stage.ensure(num_blocks * stride * 4), "raw staging workspace");
     QRNG_CUDA(ctx, launch_repack_blocks(raw, 0, n, num_blocks, ctx->raw_stage.as<uint32_t>(), stride, s, kernels),
               "raw repack");
@@ -195,7 +198,13 @@ int extract_dispatch(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, 
   uint32_t kernels = 0;
   int st;
   const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
-  int used = algo == QRNG_ALGO_AUTO ? QRNG_ALGO_DIRECT : algo;
+  int used = algo;
+  if (used == QRNG_ALGO_AUTO) {
+    // Many blocks sharing the seed form a dense product worth the tensor cores; few or tiny blocks
+    // do not fill a 256 x 256 tile and stay on the bit-packed integer kernel.
+    const bool dense = num_blocks >= 128 && m >= 128 && n_t >= 512 && n_t <= kGemmMaxColumns;
+    used = dense ? QRNG_ALGO_GEMM_TC : QRNG_ALGO_DIRECT;
+  }
   switch (used) {
     case QRNG_ALGO_DIRECT:
       st = extract_bitwise(ctx, used, raw, n, m, seed, form, num_blocks, out, s, &kernels);

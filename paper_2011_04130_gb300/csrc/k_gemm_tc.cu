@@ -6,19 +6,23 @@
 // form of Sec. III.D, whose identity part is XORed in the epilogue) and X the raw blocks, one per
 // row. GB300's tcgen05 has no integer (i8) kind, so 0/1 entries are fed as E4M3 values 2^-6
 // (byte 0x08) and the product is accumulated in FP32 in tensor memory: each sum is an integer
-// count c <= n <= 2^26 scaled by 2^-12, exact in FP32 for c < 2^24, and its parity is read from
-// the scaled float in the epilogue.
+// count c <= n_t scaled by 2^-12, exact in FP32, and its parity is read from the scaled float in
+// the epilogue (valid for c < 2^22, the launcher's limit on n_t).
 //
-// CTA tile: 128 outputs (UMMA M) x 256 blocks (UMMA N), K step 128 (one 128-byte swizzle row).
-//   warps 0-5  producers: build the K-step's operand tiles in shared memory straight from the
-//              packed bits -- T rows from the bit-reversed seed (one funnel-shifted window per
-//              row), X rows from the raw words -- in the canonical K-major SWIZZLE_128B layout;
-//   warp 6     allocates tensor memory and issues tcgen05.mma (one elected lane);
-//   warps 7-10 epilogue: tcgen05.ld the FP32 accumulator, parity, __ballot_sync into output
-//              words (32 outputs of one block per word), identity XOR for the modified form.
-// Stages are handed over with mbarriers; every wait is bounded (about one second of clock),
-// after which the kernel records an error code, stops issuing work, waits for its own MMAs and
-// frees its tensor memory.
+// CTA tile: 256 outputs (two UMMA M=128 halves sharing one B tile, two FP32 accumulators of 256
+// columns = all 512 TMEM columns) x 256 blocks (UMMA N), K step 128 (one 128-byte swizzle row).
+//   warps 0-7   producers: each K step, thread t builds T row t (from a funnel-shifted window of
+//               the bit-reversed seed) and X row t (from 16 packed raw bytes that TMA already put
+//               in shared memory) as E4M3 bytes in the canonical K-major SWIZZLE_128B layout;
+//   warp 8      TMA: cp.async.bulk.tensor loads of the packed raw tile (256 blocks x 16 bytes),
+//               running up to PK_STAGES K steps ahead;
+//   warp 9      allocates tensor memory and issues tcgen05.mma (one elected lane);
+//   warps 10-13 epilogue: tcgen05.ld of both accumulators, parity, __ballot_sync into output
+//               words (32 outputs of one block per word), identity XOR for the modified form.
+// Stages are handed over with mbarriers. Every wait is bounded (about one second of clock): on
+// timeout the kernel records an error code, stops issuing work, waits for its own MMAs and TMA
+// loads, frees its tensor memory and returns.
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -27,21 +31,26 @@
 namespace qrng {
 namespace {
 
-constexpr int BM = 128;
-constexpr int BN = 256;
-constexpr int BK = 128;                // fp8 elements (= bytes) per K step
-constexpr int STAGES = 4;
-constexpr int A_BYTES = BM * BK;        // 16 KB
+constexpr int UM = 128;                 // UMMA M
+constexpr int BM = 2 * UM;              // outputs per CTA tile
+constexpr int BN = 256;                 // blocks per CTA tile (UMMA N)
+constexpr int BK = 128;                 // K elements (= E4M3 bytes) per step
+constexpr int STAGES = 3;
+constexpr int A_BYTES = BM * BK;        // 32 KB
 constexpr int B_BYTES = BN * BK;        // 32 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int PRODUCER_WARPS = 6;
+constexpr int PK_STAGES = 6;            // packed raw tiles in flight
+constexpr int PK_BYTES = BN * 16;       // 256 rows x 4 words
+constexpr int PRODUCER_WARPS = 8;
 constexpr int PRODUCERS = PRODUCER_WARPS * 32;
-constexpr int MMA_WARP = PRODUCER_WARPS;
+constexpr int TMA_WARP = PRODUCER_WARPS;
+constexpr int MMA_WARP = TMA_WARP + 1;
 constexpr int EPI_WARP0 = MMA_WARP + 1;
-constexpr int THREADS = (EPI_WARP0 + 4) * 32;  // 352
-constexpr int TMEM_COLS = 256;
-constexpr uint32_t kOneE4M3 = 0x08u;   // 2^-6
+constexpr int THREADS = (EPI_WARP0 + 4) * 32;  // 448
+constexpr int TMEM_COLS = 512;
+constexpr uint32_t kOneE4M3 = 0x08u;    // 2^-6
 constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
+static_assert(PRODUCERS == BM && PRODUCERS == BN, "one T row and one X row per producer thread");
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -53,6 +62,11 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
 
 __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
 }
 
 __device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
@@ -81,6 +95,17 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
   }
 }
 
+// Bounded wait that ignores the abort flag (used to drain the CTA's own asynchronous work).
+__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, int* err, int code) {
+  const long long t0 = clock64();
+  while (!mbar_test(bar, parity)) {
+    if (clock64() - t0 > kWaitCycles) {
+      atomicCAS(err, 0, code);
+      return;
+    }
+  }
+}
+
 __device__ __forceinline__ void fence_proxy_async_smem() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
@@ -100,7 +125,7 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
 }
 
 // Instruction descriptor: kind::f8f6f4, D = F32, A = B = E4M3, both K-major, M = 128, N = 256.
-constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(UM >> 4) << 24);
 
 __device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
   asm volatile(
@@ -113,6 +138,14 @@ __device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 
 // Spreads 4 bits to 4 bytes: bit j -> byte j with value kOneE4M3 (the shifted copies x << 7k never
@@ -153,10 +186,13 @@ struct GemmArgs {
   int* err;
 };
 
-__global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const GemmArgs a) {
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_tc_kernel(const GemmArgs a, const __grid_constant__ CUtensorMap raw_map) {
   extern __shared__ uint8_t dyn_smem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];
   __shared__ __align__(8) uint64_t empty_bar[STAGES];
+  __shared__ __align__(8) uint64_t pk_full_bar[PK_STAGES];
+  __shared__ __align__(8) uint64_t pk_empty_bar[PK_STAGES];
   __shared__ __align__(8) uint64_t accum_full_bar;
   __shared__ __align__(8) uint64_t accum_empty_bar;
   __shared__ __align__(8) uint64_t drain_bar;
@@ -166,11 +202,16 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const GemmArgs a) {
   const uint32_t warp = threadIdx.x >> 5;
   const uint32_t lane = threadIdx.x & 31;
   const uint32_t smem_base = (smem_u32(dyn_smem) + 1023u) & ~1023u;
+  const uint32_t pk_base = smem_base + STAGES * STAGE_BYTES;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full_bar[s], PRODUCERS);
       mbar_init(&empty_bar[s], 1);
+    }
+    for (int s = 0; s < PK_STAGES; ++s) {
+      mbar_init(&pk_full_bar[s], 1);
+      mbar_init(&pk_empty_bar[s], PRODUCERS);
     }
     mbar_init(&accum_full_bar, 1);
     mbar_init(&accum_empty_bar, 4 * 32);
@@ -193,75 +234,89 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const GemmArgs a) {
 
   if (warp < PRODUCER_WARPS) {
     // ------------------------------------------------------------------ producers
-    const uint32_t p = threadIdx.x;
-    uint32_t stage = 0, phase = 0;
+    const uint32_t t = threadIdx.x;  // T row t and X row t of every K step
+    uint32_t stage = 0, phase = 0, pstage = 0, pphase = 0;
     for (uint64_t tile = blockIdx.x; tile < ntile_total && !abort_flag; tile += gridDim.x) {
       const uint32_t mt = (uint32_t)(tile % a.mtiles);
-      const uint32_t nt = (uint32_t)(tile / a.mtiles);
+      // T row i: reversed-seed bits m-1-i+128ks .. +127 (front padding keeps the index >= 0)
+      const int64_t i = (int64_t)mt * BM + t;
+      const int64_t ubase = (int64_t)a.m - 1 - i + 32 * (int64_t)kSeedFrontWords;
+      const uint32_t sh = (uint32_t)(ubase & 31);
+      const uint32_t* seed_row = a.seed_rev + (ubase >> 5);
       for (uint32_t ks = 0; ks < a.ksteps; ++ks) {
-        if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, a.err, 1)) break;
+        // packed raw words of X row t for this K step (delivered by TMA)
+        if (!mbar_wait(&pk_full_bar[pstage], pphase, &abort_flag, a.err, 1)) break;
+        uint32_t xw[4];
+        asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                     : "=r"(xw[0]), "=r"(xw[1]), "=r"(xw[2]), "=r"(xw[3])
+                     : "r"(pk_base + pstage * PK_BYTES + t * 16)
+                     : "memory");
+        mbar_arrive(&pk_empty_bar[pstage]);
+        if (++pstage == PK_STAGES) { pstage = 0; pphase ^= 1u; }
+        if (4 * ks + 4 > a.nw_t - 1) {  // words past the Toeplitz part (zero-filled) and its partial last word
+#pragma unroll
+          for (int w = 0; w < 4; ++w)
+            if (4 * ks + w == a.nw_t - 1) xw[w] &= a.tail_mask;
+        }
+        uint32_t sw[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) sw[k] = __ldg(seed_row + 4 * ks + k);
+
+        if (!mbar_wait(&empty_bar[stage], phase ^ 1u, &abort_flag, a.err, 2)) break;
         const uint32_t sA = smem_base + stage * STAGE_BYTES;
         const uint32_t sB = sA + A_BYTES;
-        for (uint32_t r = p; r < BM + BN; r += PRODUCERS) {
-          if (r < BM) {
-            // T row i: reversed-seed bits m-1-i+128ks .. +127 (front padding keeps the index >= 0)
-            const int64_t i = (int64_t)mt * BM + r;
-            const int64_t u0 = (int64_t)a.m - 1 - i + (int64_t)ks * BK + 32 * (int64_t)kSeedFrontWords;
-            const uint32_t sh = (uint32_t)(u0 & 31);
-            const uint32_t* src = a.seed_rev + (u0 >> 5);
-            uint32_t wv[5];
+        const uint32_t rowA = sA + t * BK;
+        const uint32_t rowB = sB + t * BK;
 #pragma unroll
-            for (int k = 0; k < 5; ++k) wv[k] = __ldg(src + k);
-            const uint32_t row_addr = sA + r * BK;
-#pragma unroll
-            for (int w = 0; w < 4; ++w) store_word_e4m3(row_addr, r, w, __funnelshift_r(wv[w], wv[w + 1], sh));
-          } else {
-            const uint32_t rb = r - BM;
-            const uint64_t b = (uint64_t)nt * BN + rb;
-            uint32_t wv[4] = {0u, 0u, 0u, 0u};
-            if (b < a.num_blocks) {
-              const uint32_t* src = a.raw + b * a.raw_stride;
-              const uint32_t w0 = ks * 4;
-              if (w0 + 4 <= a.nw_t && (w0 + 4 < a.nw_t || a.tail_mask == 0xffffffffu) &&
-                  ((reinterpret_cast<uintptr_t>(src + w0) & 15) == 0)) {
-                const uint4 v = __ldg(reinterpret_cast<const uint4*>(src + w0));
-                wv[0] = v.x; wv[1] = v.y; wv[2] = v.z; wv[3] = v.w;
-              } else {
-#pragma unroll
-                for (int w = 0; w < 4; ++w) {
-                  const uint32_t wi = w0 + w;
-                  uint32_t x = wi < a.nw_t ? __ldg(src + wi) : 0u;
-                  if (wi == a.nw_t - 1) x &= a.tail_mask;
-                  wv[w] = x;
-                }
-              }
-            }
-            const uint32_t row_addr = sB + rb * BK;
-#pragma unroll
-            for (int w = 0; w < 4; ++w) store_word_e4m3(row_addr, rb, w, wv[w]);
-          }
+        for (int w = 0; w < 4; ++w) {
+          store_word_e4m3(rowA, t, w, __funnelshift_r(sw[w], sw[w + 1], sh));
+          store_word_e4m3(rowB, t, w, xw[w]);
         }
         fence_proxy_async_smem();
         mbar_arrive(&full_bar[stage]);
         if (++stage == STAGES) { stage = 0; phase ^= 1u; }
       }
     }
+  } else if (warp == TMA_WARP) {
+    // ------------------------------------------------------------------ TMA loads of packed raw tiles
+    uint32_t pstage = 0, pphase = 0, issued = 0;
+    if (lane == 0) {
+      for (uint64_t tile = blockIdx.x; tile < ntile_total && !abort_flag; tile += gridDim.x) {
+        const uint32_t nt = (uint32_t)(tile / a.mtiles);
+        for (uint32_t ks = 0; ks < a.ksteps; ++ks) {
+          if (!mbar_wait(&pk_empty_bar[pstage], pphase ^ 1u, &abort_flag, a.err, 3)) break;
+          mbar_arrive_expect_tx(&pk_full_bar[pstage], PK_BYTES);
+          tma_load_2d(pk_base + pstage * PK_BYTES, &raw_map, (int)(4 * ks), (int)(nt * BN), &pk_full_bar[pstage]);
+          ++issued;
+          if (++pstage == PK_STAGES) { pstage = 0; pphase ^= 1u; }
+        }
+      }
+      // the loads still in flight must land before the CTA exits: wait for the last PK_STAGES slots
+      for (uint32_t k = 0; k < PK_STAGES && k < issued; ++k) {
+        if (pstage == 0) { pstage = PK_STAGES; pphase ^= 1u; }
+        --pstage;
+        mbar_drain(&pk_full_bar[pstage], pphase, a.err, 4);
+      }
+    }
+    __syncwarp();
   } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------------ MMA issuer
     uint32_t stage = 0, phase = 0, acc_phase = 0;
     bool issued = false;
     for (uint64_t tile = blockIdx.x; tile < ntile_total && !abort_flag; tile += gridDim.x) {
-      // the epilogue must have drained the previous tile's accumulator
-      if (tile != blockIdx.x && !mbar_wait(&accum_empty_bar, acc_phase ^ 1u, &abort_flag, a.err, 2)) break;
+      // the epilogue must have drained the previous tile's accumulators
+      if (tile != blockIdx.x && !mbar_wait(&accum_empty_bar, acc_phase ^ 1u, &abort_flag, a.err, 5)) break;
       for (uint32_t ks = 0; ks < a.ksteps; ++ks) {
-        if (!mbar_wait(&full_bar[stage], phase, &abort_flag, a.err, 3)) break;
+        if (!mbar_wait(&full_bar[stage], phase, &abort_flag, a.err, 6)) break;
         tc_fence_after();
         if (lane == 0) {
           const uint32_t sA = smem_base + stage * STAGE_BYTES;
           const uint32_t sB = sA + A_BYTES;
 #pragma unroll
           for (int k = 0; k < BK / 32; ++k) {
-            mma_f8(tmem_base, smem_desc_sw128(sA + 32 * k), smem_desc_sw128(sB + 32 * k), (ks | k) != 0);
+            const uint64_t bdesc = smem_desc_sw128(sB + 32 * k);
+            mma_f8(tmem_base, smem_desc_sw128(sA + 32 * k), bdesc, (ks | k) != 0);
+            mma_f8(tmem_base + BN, smem_desc_sw128(sA + UM * BK + 32 * k), bdesc, (ks | k) != 0);
           }
           mma_commit(&empty_bar[stage]);  // frees the stage once these MMAs have read it
           issued = true;
@@ -274,16 +329,10 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const GemmArgs a) {
       __syncwarp();
       acc_phase ^= 1u;
     }
-    // wait for every MMA this CTA issued before the tensor memory is released
+    // every MMA this CTA issued must finish before the tensor memory is released
     if (lane == 0 && issued) {
       mma_commit(&drain_bar);
-      const long long t0 = clock64();
-      while (!mbar_test(&drain_bar, 0)) {
-        if (clock64() - t0 > kWaitCycles) {
-          atomicCAS(a.err, 0, 4);
-          break;
-        }
-      }
+      mbar_drain(&drain_bar, 0, a.err, 7);
     }
     __syncwarp();
   } else {
@@ -293,45 +342,47 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const GemmArgs a) {
     for (uint64_t tile = blockIdx.x; tile < ntile_total && !abort_flag; tile += gridDim.x) {
       const uint32_t mt = (uint32_t)(tile % a.mtiles);
       const uint32_t nt = (uint32_t)(tile / a.mtiles);
-      if (!mbar_wait(&accum_full_bar, acc_phase, &abort_flag, a.err, 5)) break;
+      if (!mbar_wait(&accum_full_bar, acc_phase, &abort_flag, a.err, 8)) break;
       tc_fence_after();
-      const uint32_t ow = mt * (BM / 32) + q;  // output word (32 outputs) of every block in this tile
-      const uint32_t rem = (ow < a.mw) ? a.m - 32 * ow : 0u;
-      const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
-      for (uint32_t g = 0; g < BN / 32; ++g) {
-        uint32_t v[32];
-        const uint32_t taddr = tmem_base + ((32u * q) << 16) + 32u * g;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-              "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
-              "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
-              "=r"(v[30]), "=r"(v[31])
-            : "r"(taddr));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        uint32_t mine = 0;
+      for (uint32_t half = 0; half < 2; ++half) {
+        const uint32_t ow = mt * (BM / 32) + half * (UM / 32) + q;  // output word of every block in the tile
+        const uint32_t rem = (ow < a.mw) ? a.m - 32 * ow : 0u;
+        const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+        for (uint32_t g = 0; g < BN / 32; ++g) {
+          uint32_t v[32];
+          const uint32_t taddr = tmem_base + ((32u * q) << 16) + half * BN + 32u * g;
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+              : "r"(taddr));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          uint32_t mine = 0;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          // count = value * 2^12 is an integer < 2^24: adding 1.5 * 2^23 leaves it in the low mantissa bits
-          const float cnt = __fmaf_rn(__uint_as_float(v[c]), 4096.0f, 12582912.0f);
-          const uint32_t wrd = __ballot_sync(0xffffffffu, __float_as_uint(cnt) & 1u);
-          if (lane == (uint32_t)c) mine = wrd;
-        }
-        const uint64_t b = (uint64_t)nt * BN + 32u * g + lane;
-        if (ow < a.mw && b < a.num_blocks) {
-          mine &= omask;
-          if (a.modified) {
-            const uint64_t bit = (uint64_t)a.id_off + 32ull * ow;
-            const uint32_t* rr = a.raw + b * a.raw_stride;
-            const uint64_t rq = bit >> 5;
-            const uint32_t rs = (uint32_t)(bit & 31);
-            const uint32_t rlo = __ldg(rr + rq);
-            const uint32_t rhi = (rs && rq + 1 < a.raw_stride) ? __ldg(rr + rq + 1) : 0u;
-            mine ^= __funnelshift_r(rlo, rhi, rs) & omask;
+          for (int c = 0; c < 32; ++c) {
+            // count = value * 2^12 is an integer < 2^22: adding 1.5 * 2^23 leaves it in the low mantissa bits
+            const float cnt = __fmaf_rn(__uint_as_float(v[c]), 4096.0f, 12582912.0f);
+            const uint32_t wrd = __ballot_sync(0xffffffffu, __float_as_uint(cnt) & 1u);
+            if (lane == (uint32_t)c) mine = wrd;
           }
-          a.out[b * a.out_stride + ow] = mine;
+          const uint64_t b = (uint64_t)nt * BN + 32u * g + lane;
+          if (ow < a.mw && b < a.num_blocks) {
+            mine &= omask;
+            if (a.modified) {
+              const uint64_t bit = (uint64_t)a.id_off + 32ull * ow;
+              const uint32_t* rr = a.raw + b * a.raw_stride;
+              const uint64_t rq = bit >> 5;
+              const uint32_t rs = (uint32_t)(bit & 31);
+              const uint32_t rlo = __ldg(rr + rq);
+              const uint32_t rhi = (rs && rq + 1 < a.raw_stride) ? __ldg(rr + rq + 1) : 0u;
+              mine ^= __funnelshift_r(rlo, rhi, rs) & omask;
+            }
+            a.out[b * a.out_stride + ow] = mine;
+          }
         }
       }
       tc_fence_before();
@@ -350,9 +401,14 @@ __global__ void __launch_bounds__(THREADS, 1) gemm_tc_kernel(const GemmArgs a) {
 
 }  // namespace
 
-size_t gemm_tc_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + 1024; }
+size_t gemm_tc_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + (size_t)PK_STAGES * PK_BYTES + 1024; }
+
+bool gemm_tc_layout_ok(const DirectArgs& d) {
+  return (reinterpret_cast<uintptr_t>(d.raw) & 15) == 0 && (d.raw_stride % 4) == 0;
+}
 
 cudaError_t launch_gemm_tc(const DirectArgs& d, int* err, int num_sms, cudaStream_t s, uint32_t* kernels) {
+  if (!gemm_tc_layout_ok(d)) return cudaErrorInvalidValue;
   GemmArgs a{};
   a.raw = d.raw;
   a.raw_stride = d.raw_stride;
@@ -370,12 +426,25 @@ cudaError_t launch_gemm_tc(const DirectArgs& d, int* err, int num_sms, cudaStrea
   a.ntiles = (uint32_t)ceil_div(d.num_blocks, BN);
   a.ksteps = (uint32_t)ceil_div((uint64_t)d.nw_t * 32, BK);
   a.err = err;
+
+  // Tensor map over the raw words: dim 0 = the Toeplitz part's words of a block (reads beyond it
+  // are zero-filled), dim 1 = blocks (rows past the last block are zero-filled); box 4 x 256.
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {(cuuint64_t)d.nw_t, (cuuint64_t)d.num_blocks};
+  const cuuint64_t gstride[1] = {(cuuint64_t)d.raw_stride * 4};
+  const cuuint32_t box[2] = {4, (cuuint32_t)BN};
+  const cuuint32_t estride[2] = {1, 1};
+  CUresult r = cuTensorMapEncodeTiled(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(d.raw), gdim,
+                                      gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+
   const size_t smem = gemm_tc_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(gemm_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const uint64_t tiles = (uint64_t)a.mtiles * a.ntiles;
   const int grid = (int)(tiles < (uint64_t)num_sms ? tiles : (uint64_t)num_sms);
-  gemm_tc_kernel<<<grid, THREADS, smem, s>>>(a);
+  gemm_tc_kernel<<<grid, THREADS, smem, s>>>(a, map);
   ++*kernels;
   return cudaGetLastError();
 }

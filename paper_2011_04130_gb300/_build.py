@@ -65,7 +65,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
             list(ex.map(run, jobs))
     if force or jobs or _stale(LIB, objs):
         tmp = LIB + ".tmp.%d" % os.getpid()
-        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs, "-lcuda"])
+        run([nvcc, *ARCH, "-shared", "-o", tmp, *objs])
         os.replace(tmp, LIB)
     return LIB
 

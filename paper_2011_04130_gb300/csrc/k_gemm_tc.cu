@@ -401,6 +401,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 }  // namespace
 
+typedef CUresult (*PFN_encodeTiled)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                    const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                    CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
 size_t gemm_tc_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + (size_t)PK_STAGES * PK_BYTES + 1024; }
 
 bool gemm_tc_layout_ok(const DirectArgs& d) {
@@ -429,14 +433,24 @@ cudaError_t launch_gemm_tc(const DirectArgs& d, int* err, int num_sms, cudaStrea
 
   // Tensor map over the raw words: dim 0 = the Toeplitz part's words of a block (reads beyond it
   // are zero-filled), dim 1 = blocks (rows past the last block are zero-filled); box 4 x 256.
+  // The driver's encoder is looked up at run time, so the library has no link-time libcuda dependency.
+  static PFN_encodeTiled encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_encodeTiled>(fn);
+  }
   CUtensorMap map;
   const cuuint64_t gdim[2] = {(cuuint64_t)d.nw_t, (cuuint64_t)d.num_blocks};
   const cuuint64_t gstride[1] = {(cuuint64_t)d.raw_stride * 4};
   const cuuint32_t box[2] = {4, (cuuint32_t)BN};
   const cuuint32_t estride[2] = {1, 1};
-  CUresult r = cuTensorMapEncodeTiled(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(d.raw), gdim,
-                                      gstride, box, estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(d.raw), gdim, gstride, box,
+                      estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
 
   const size_t smem = gemm_tc_smem_bytes();

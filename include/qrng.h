@@ -221,7 +221,9 @@ QRNG_API int qrng_reset_stats(qrng_ctx* ctx);
 
 /* Waits for `stream` and reports device-side failures of the work enqueued so far: returns
  * QRNG_ETIMEOUT (and clears the condition) when a kernel's bounded wait gave up, in which case
- * the output of that call is incomplete. Kernels never trap or hang on such a failure. */
+ * the output of that call is incomplete, and QRNG_EPRECISION when an FFT path saw a convolution
+ * sum 0.25 or more away from an integer since the last qrng_reset_stats (its rounding, hence its
+ * parity, is then not trustworthy). Kernels never trap or hang on such a failure. */
 QRNG_API int qrng_synchronize(qrng_ctx* ctx, qrng_stream_t stream);
 
 /* Timing of the main extraction kernel of each qrng_toeplitz_extract call (on = 1, off = 0):

@@ -32,6 +32,8 @@ int cuda_fail(qrng_ctx* ctx, cudaError_t e, const char* where) {
   } while (0)
 
 constexpr size_t kMaxTimed = 4096;
+// Largest distance of an FFT convolution sum from its integer that still counts as exact.
+constexpr double kFftRoundGuard = 0.25;
 
 // Brackets one launch with a CUDA event pair on its stream when timing is on.
 struct LaunchTimer {
@@ -72,10 +74,14 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
                     int form, uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels) {
   const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
   const uint64_t L_t = n_t + m - 1;
+  const bool fft = (algo == QRNG_ALGO_FFT64 || algo == QRNG_ALGO_FFT32_SEG);
 
-  const uint64_t rev_words = kSeedFrontWords + ceil_div(L_t, 32) + kSeedBackWords;
-  QRNG_CUDA(ctx, ctx->seed_rev.ensure(rev_words * 4), "seed workspace");
-  QRNG_CUDA(ctx, launch_seed_reverse(seed, L_t, ctx->seed_rev.as<uint32_t>(), rev_words, s, kernels), "seed reverse");
+  if (!fft) {  // the bit-packed kernels read Toeplitz rows as windows of the reversed seed
+    const uint64_t rev_words = kSeedFrontWords + ceil_div(L_t, 32) + kSeedBackWords;
+    QRNG_CUDA(ctx, ctx->seed_rev.ensure(rev_words * 4), "seed workspace");
+    QRNG_CUDA(ctx, launch_seed_reverse(seed, L_t, ctx->seed_rev.as<uint32_t>(), rev_words, s, kernels),
+              "seed reverse");
+  }
 
   DirectArgs a{};
   // The tensor-core kernel loads raw tiles with TMA: 16-byte aligned rows, a multiple of 4 words apart.
@@ -103,6 +109,7 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
     out_w = ctx->out_stage.as<uint32_t>();
   }
 
+  a.n_t = n_t;
   a.nw_t = (uint32_t)ceil_div(n_t, 32);
   a.tail_mask = (n_t % 32) ? ((1u << (n_t % 32)) - 1u) : 0xffffffffu;
   a.m = (uint32_t)m;
@@ -113,6 +120,17 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
   a.out = out_w;
   a.out_stride = mw;
   a.num_blocks = num_blocks;
+  if (fft) {
+    ctx->fft.worst = ctx->fft_worst.as<unsigned long long>();
+    LaunchTimer timer(ctx, s);
+    const cudaError_t e = algo == QRNG_ALGO_FFT64 ? launch_fft64(a, seed, L_t, ctx->fft, s, kernels)
+                                                  : launch_fft32_seg(a, seed, L_t, ctx->fft, s, kernels);
+    timer.done();
+    QRNG_CUDA(ctx, e, algo == QRNG_ALGO_FFT64 ? "FP64 FFT extraction" : "FP32 segmented FFT extraction");
+    if (!out_direct)
+      QRNG_CUDA(ctx, launch_pack_blocks(out_w, mw, m, num_blocks, out, s, kernels), "output pack");
+    return QRNG_OK;
+  }
   if (algo == QRNG_ALGO_GEMM_TC) {
     QRNG_CUDA(ctx, ctx->dev_err.ensure(sizeof(int)), "error word");
     LaunchTimer timer(ctx, s);
@@ -209,6 +227,10 @@ int extract_dispatch(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, 
     case QRNG_ALGO_DIRECT:
       st = extract_bitwise(ctx, used, raw, n, m, seed, form, num_blocks, out, s, &kernels);
       break;
+    case QRNG_ALGO_FFT64:
+    case QRNG_ALGO_FFT32_SEG:
+      st = extract_bitwise(ctx, used, raw, n, m, seed, form, num_blocks, out, s, &kernels);
+      break;
     case QRNG_ALGO_GEMM_TC:
       if (n_t > kGemmMaxColumns)
         return fail(ctx, QRNG_ENOTSUP, "qrng_toeplitz_extract: the tensor-core path needs n (n-m modified) <= 2^22");
@@ -246,9 +268,12 @@ int qrng_create(qrng_ctx** out, int device) {
     delete ctx;
     return QRNG_ENOMEM;
   }
-  if (ctx->dev_err.ensure(sizeof(int)) != cudaSuccess || cudaMemset(ctx->dev_err.p, 0, sizeof(int)) != cudaSuccess) {
+  if (ctx->dev_err.ensure(sizeof(int)) != cudaSuccess || cudaMemset(ctx->dev_err.p, 0, sizeof(int)) != cudaSuccess ||
+      ctx->fft_worst.ensure(sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(ctx->fft_worst.p, 0, sizeof(unsigned long long)) != cudaSuccess) {
     cudaFreeHost(ctx->result_host);
     ctx->dev_err.release();
+    ctx->fft_worst.release();
     delete ctx;
     return QRNG_ENOMEM;
   }
@@ -269,6 +294,8 @@ void qrng_destroy(qrng_ctx* ctx) {
   ctx->out_dev.release();
   ctx->seed_dev.release();
   ctx->dev_err.release();
+  ctx->fft_worst.release();
+  ctx->fft.release();
   if (ctx->result_host) cudaFreeHost(ctx->result_host);
   for (cudaEvent_t e : ctx->ev_start) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->ev_end) cudaEventDestroy(e);
@@ -376,6 +403,11 @@ int qrng_get_stats(qrng_ctx* ctx, qrng_stats* out) {
     ctx->stats.timed_launches += 1;
   }
   ctx->ev_used = 0;
+  unsigned long long worst = 0;
+  QRNG_CUDA(ctx, cudaMemcpy(&worst, ctx->fft_worst.p, sizeof(worst), cudaMemcpyDeviceToHost), "FFT error read");
+  double w;
+  memcpy(&w, &worst, sizeof(w));
+  ctx->stats.worst_fft_round_err = w;
   *out = ctx->stats;
   return QRNG_OK;
 }
@@ -385,6 +417,7 @@ int qrng_reset_stats(qrng_ctx* ctx) {
   for (size_t i = 0; i < ctx->ev_used; ++i) cudaEventSynchronize(ctx->ev_end[i]);
   ctx->ev_used = 0;
   ctx->stats = qrng_stats{};
+  QRNG_CUDA(ctx, cudaMemset(ctx->fft_worst.p, 0, sizeof(unsigned long long)), "FFT error reset");
   return QRNG_OK;
 }
 
@@ -400,6 +433,13 @@ int qrng_synchronize(qrng_ctx* ctx, qrng_stream_t stream) {
     return fail(ctx, QRNG_ETIMEOUT,
                 "a bounded device wait gave up (site " + std::to_string(code) + "); the affected output is incomplete");
   }
+  unsigned long long worst = 0;
+  QRNG_CUDA(ctx, cudaMemcpy(&worst, ctx->fft_worst.p, sizeof(worst), cudaMemcpyDeviceToHost), "FFT error read");
+  double w;
+  memcpy(&w, &worst, sizeof(w));
+  if (w >= kFftRoundGuard)
+    return fail(ctx, QRNG_EPRECISION,
+                "an FFT convolution sum was " + std::to_string(w) + " away from an integer; its parity is unreliable");
   return QRNG_OK;
 }
 

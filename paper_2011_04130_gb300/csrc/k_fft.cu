@@ -1,0 +1,435 @@
+// FFT routes to the Toeplitz hash (Sec. III.B Thm. 1-2 and Sec. III.D of the paper).
+//
+// The Toeplitz part of the hash is a slice of a linear convolution: with c = a * r,
+//     k_i = c[n_t - 1 + i] mod 2,  n_t = n (standard) or n - m (modified, whose identity part
+// I_m is XORed afterwards). Embedding a and r in a cyclic convolution of length P >= n_t + m - 1
+// (the circulant of Sec. III.B) leaves every needed entry free of wrap-around, and the
+// convolution theorem turns it into F^-1(F a . F r).
+//
+// FFT64 (the paper's route): one P-point FP64 transform per PAIR of blocks -- two real blocks are
+// the real and imaginary parts of one complex vector, and because the seed spectrum is the
+// transform of a real sequence, F^-1(F a . F(r1 + i r2)) = a*r1 + i a*r2 separates them with no
+// extra work. Radix-2 Stockham passes run over global memory (one launch per pass over a chunk of
+// pairs), with a cached FP64 twiddle table. The worst |s - round(s)| of every entry used is kept
+// as evidence of exactness (FP64 with P <= 2^27 keeps it far below 1/2).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "qrng_internal.h"
+
+namespace qrng {
+namespace {
+
+struct cd {
+  double x, y;
+};
+
+__device__ __forceinline__ cd cmul(cd a, cd b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+
+// tw[k] = exp(-2 pi i k / P), k < P/2.
+__global__ void twiddle_kernel(cd* __restrict__ tw, uint64_t P) {
+  uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= P / 2) return;
+  double s, c;
+  sincospi(-2.0 * (double)k / (double)P, &s, &c);
+  tw[k] = {c, s};
+}
+
+// One radix-2 Stockham pass over `batch` transforms of length P (half-length L of the butterflies
+// produced by this pass): y[g 2L + k] = x[j] + w x[j + P/2], y[g 2L + k + L] = x[j] - w x[j + P/2],
+// j = g L + k, w = exp(-+ 2 pi i k / (2L)) = tw[k P / (2L)] (conjugated for the inverse).
+__global__ void stockham_pass_kernel(const cd* __restrict__ x, cd* __restrict__ y, const cd* __restrict__ tw,
+                                     uint64_t P, uint32_t logL, uint32_t logP, int inverse, uint64_t total) {
+  uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const uint64_t half = P >> 1;
+  const uint64_t b = idx >> (logP - 1);
+  const uint64_t j = idx & (half - 1);
+  const uint64_t L = 1ull << logL;
+  const uint64_t k = j & (L - 1);
+  const uint64_t g = j >> logL;
+  cd w = tw[k << (logP - 1 - logL)];
+  if (inverse) w.y = -w.y;
+  const cd* xb = x + b * P;
+  cd* yb = y + b * P;
+  const cd a = xb[j];
+  const cd t = cmul(w, xb[j + half]);
+  yb[(g << (logL + 1)) + k] = {a.x + t.x, a.y + t.y};
+  yb[(g << (logL + 1)) + k + L] = {a.x - t.x, a.y - t.y};
+}
+
+// Zero-padded seed (first L_t bits) as the real part of one complex vector.
+__global__ void seed_to_complex_kernel(const uint8_t* __restrict__ seed, uint64_t L, cd* __restrict__ z, uint64_t P) {
+  uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P) return;
+  double v = 0.0;
+  if (t < L) v = (double)((seed[t >> 3] >> (t & 7)) & 1u);
+  z[t] = {v, 0.0};
+}
+
+// z_p[t] = r_{2p}[t] + i r_{2p+1}[t] for t < n_t, zero beyond (pairs p0 .. p0+npairs-1).
+__global__ void pack_pairs_kernel(const uint32_t* __restrict__ raw, uint64_t stride, uint64_t n_t,
+                                  uint64_t num_blocks, uint64_t p0, uint64_t npairs, cd* __restrict__ z, uint64_t P) {
+  uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= npairs * P) return;
+  const uint64_t p = idx / P, t = idx - p * P;
+  const uint64_t b0 = 2 * (p0 + p), b1 = b0 + 1;
+  double re = 0.0, im = 0.0;
+  if (t < n_t) {
+    re = (double)((raw[b0 * stride + (t >> 5)] >> (t & 31)) & 1u);
+    if (b1 < num_blocks) im = (double)((raw[b1 * stride + (t >> 5)] >> (t & 31)) & 1u);
+  }
+  z[idx] = {re, im};
+}
+
+// Z_p[k] *= A[k] / P  (the 1/P of the inverse transform folded in).
+__global__ void spectrum_mul_kernel(cd* __restrict__ z, const cd* __restrict__ A, uint64_t P, uint64_t total) {
+  uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const cd a = A[idx & (P - 1)];
+  const double s = 1.0 / (double)P;
+  cd v = cmul(z[idx], a);
+  z[idx] = {v.x * s, v.y * s};
+}
+
+// Output word w (32 outputs) of both blocks of pair p: parities of round(c[n_t - 1 + i]), the
+// identity bits for the modified form, and the worst rounding distance.
+__global__ void extract_pairs_kernel(const cd* __restrict__ z, uint64_t P, uint64_t n_t, uint64_t m, uint64_t mw,
+                                     const uint32_t* __restrict__ raw, uint64_t stride, int modified, uint64_t id_off,
+                                     uint64_t num_blocks, uint64_t p0, uint64_t npairs, uint32_t* __restrict__ out,
+                                     uint64_t out_stride, unsigned long long* __restrict__ worst) {
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;  // one warp per (pair, word)
+  const uint32_t lane = threadIdx.x & 31;
+  if (gw >= npairs * mw) return;
+  const uint64_t p = gw / mw, w = gw - p * mw;
+  const uint64_t i = 32 * w + lane;
+  double err = 0.0;
+  uint32_t bit0 = 0, bit1 = 0;
+  if (i < m) {
+    const cd v = z[p * P + n_t - 1 + i];
+    const double r0 = rint(v.x), r1 = rint(v.y);
+    err = fmax(fabs(v.x - r0), fabs(v.y - r1));
+    bit0 = (uint32_t)((long long)r0 & 1);
+    bit1 = (uint32_t)((long long)r1 & 1);
+  }
+  uint32_t w0 = __ballot_sync(0xffffffffu, bit0);
+  uint32_t w1 = __ballot_sync(0xffffffffu, bit1);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
+  if (lane == 0) {
+    atomicMax(worst, (unsigned long long)__double_as_longlong(err));
+    const uint64_t rem = m - 32 * w;
+    const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+    const uint64_t bb[2] = {2 * (p0 + p), 2 * (p0 + p) + 1};
+    const uint32_t ww[2] = {w0, w1};
+    for (int h = 0; h < 2; ++h) {
+      if (bb[h] >= num_blocks) continue;
+      uint32_t word = ww[h] & omask;
+      if (modified) {
+        const uint32_t* rr = raw + bb[h] * stride;
+        const uint64_t bit = id_off + 32 * w;
+        const uint64_t rq = bit >> 5;
+        const uint32_t rs = (uint32_t)(bit & 31);
+        const uint32_t lo = rr[rq];
+        const uint32_t hi = (rs && rq + 1 < stride) ? rr[rq + 1] : 0u;
+        word ^= __funnelshift_r(lo, hi, rs) & omask;
+      }
+      out[bb[h] * out_stride + w] = word;
+    }
+  }
+}
+
+inline unsigned grid_for(uint64_t total, int threads) { return (unsigned)ceil_div(total, (uint64_t)threads); }
+
+cudaError_t run_fft(cd* a, cd* b, const cd* tw, uint64_t P, uint32_t logP, uint64_t batch, int inverse,
+                    cudaStream_t s, uint32_t* kernels, cd** result) {
+  const uint64_t total = batch * (P >> 1);
+  cd* x = a;
+  cd* y = b;
+  for (uint32_t logL = 0; logL < logP; ++logL) {
+    stockham_pass_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total);
+    ++*kernels;
+    cd* t = x;
+    x = y;
+    y = t;
+  }
+  *result = x;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+uint64_t fft64_length(uint64_t n_t, uint64_t m) {
+  uint64_t need = n_t + m - 1, P = 2;
+  while (P < need) P <<= 1;
+  return P;
+}
+
+cudaError_t launch_fft64(const DirectArgs& d, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
+                         uint32_t* kernels) {
+  const uint64_t n_t = d.n_t;
+  const uint64_t P = fft64_length(n_t, d.m);
+  uint32_t logP = 0;
+  while ((1ull << logP) < P) ++logP;
+  cudaError_t e;
+  if (ws.tw_P != P) {
+    if ((e = ws.tw.ensure((P / 2) * sizeof(cd))) != cudaSuccess) return e;
+    twiddle_kernel<<<grid_for(P / 2, 256), 256, 0, s>>>(ws.tw.as<cd>(), P);
+    ++*kernels;
+    ws.tw_P = P;
+  }
+  const uint64_t npairs_total = ceil_div(d.num_blocks, 2);
+  // chunk of pairs so that the two ping-pong buffers stay within the workspace budget
+  uint64_t chunk = kFftWorkspaceBytes / (2 * P * sizeof(cd));
+  if (chunk < 1) chunk = 1;
+  if (chunk > npairs_total) chunk = npairs_total;
+  if ((e = ws.buf0.ensure(chunk * P * sizeof(cd))) != cudaSuccess) return e;
+  if ((e = ws.buf1.ensure(chunk * P * sizeof(cd))) != cudaSuccess) return e;
+  if ((e = ws.spec.ensure(P * sizeof(cd))) != cudaSuccess) return e;
+
+  // seed spectrum A = F a
+  cd* out_ptr = nullptr;
+  seed_to_complex_kernel<<<grid_for(P, 256), 256, 0, s>>>(seed, L_t, ws.buf0.as<cd>(), P);
+  ++*kernels;
+  if ((e = run_fft(ws.buf0.as<cd>(), ws.buf1.as<cd>(), ws.tw.as<cd>(), P, logP, 1, 0, s, kernels, &out_ptr)) !=
+      cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(ws.spec.p, out_ptr, P * sizeof(cd), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+
+  for (uint64_t p0 = 0; p0 < npairs_total; p0 += chunk) {
+    const uint64_t np = (npairs_total - p0) < chunk ? (npairs_total - p0) : chunk;
+    pack_pairs_kernel<<<grid_for(np * P, 256), 256, 0, s>>>(d.raw, d.raw_stride, n_t, d.num_blocks, p0, np,
+                                                            ws.buf0.as<cd>(), P);
+    ++*kernels;
+    if ((e = run_fft(ws.buf0.as<cd>(), ws.buf1.as<cd>(), ws.tw.as<cd>(), P, logP, np, 0, s, kernels, &out_ptr)) !=
+        cudaSuccess)
+      return e;
+    spectrum_mul_kernel<<<grid_for(np * P, 256), 256, 0, s>>>(out_ptr, ws.spec.as<cd>(), P, np * P);
+    ++*kernels;
+    cd* other = (out_ptr == ws.buf0.as<cd>()) ? ws.buf1.as<cd>() : ws.buf0.as<cd>();
+    cd* res = nullptr;
+    if ((e = run_fft(out_ptr, other, ws.tw.as<cd>(), P, logP, np, 1, s, kernels, &res)) != cudaSuccess) return e;
+    extract_pairs_kernel<<<grid_for(np * d.mw * 32, 256), 256, 0, s>>>(
+        res, P, n_t, d.m, d.mw, d.raw, d.raw_stride, d.modified, d.id_off, d.num_blocks, p0, np, d.out, d.out_stride,
+        ws.worst);
+    ++*kernels;
+  }
+  return cudaGetLastError();
+}
+
+
+// ------------------------------------------------------------------------------------------------
+// FFT32_SEG: FP32 transforms on short segments, parities XOR-combined.
+//
+// Raw segment s = r[sS, (s+1)S) and output tile q = outputs [qS, (q+1)S) meet through an S x S
+// Toeplitz block whose 2S-1 seed bits depend only on d = q - s: the window
+//     w_d[u] = a[n_t - 1 + dS - S + 1 + u],  u < 2S - 1  (zero outside the seed),
+// and partial_{q,s}[i'] = (w_d (*) r_s)[i' + S - 1] for the 2S-point cyclic convolution (*).
+// Each partial sum is an integer <= S, small enough that the FP32 transform's rounding error
+// stays below 1/2 (S = 4096, N = 2S = 8192); its parity is exact, and the parities of all
+// segments XOR together into k (addition mod 2 is linear).
+// One CTA owns (block, tile q). Per pair of segments it transforms r_s + i r_{s+1} once (forward
+// DIF, bit-reversed order, in shared memory), separates the two spectra by conjugate symmetry,
+// multiplies them by the window spectra (precomputed once per call, also bit-reversed), sums the
+// two products and runs one inverse DIT transform back to natural order -- no bit-reversal pass.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+constexpr int kSegS = 4096;
+constexpr int kSegN = 2 * kSegS;
+constexpr int kSegLogN = 13;
+constexpr int kSegThreads = 512;
+
+__global__ void twiddle32_kernel(float2* __restrict__ tw) {
+  int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= kSegN / 2) return;
+  double s, c;
+  sincospi(-2.0 * (double)j / (double)kSegN, &s, &c);
+  tw[j] = make_float2((float)c, (float)s);
+}
+
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+
+// In-place forward DIF over kSegN points: natural order in, bit-reversed order out.
+__device__ void dif_forward(float2* x, const float2* tw) {
+  for (int h = kSegN / 2, sh = kSegLogN - 1; h >= 1; h >>= 1, --sh) {
+    for (int t = threadIdx.x; t < kSegN / 2; t += blockDim.x) {
+      const int j = t & (h - 1);
+      const int i = ((t >> sh) << (sh + 1)) + j;
+      const float2 u = x[i], v = x[i + h];
+      x[i] = make_float2(u.x + v.x, u.y + v.y);
+      x[i + h] = cmulf(make_float2(u.x - v.x, u.y - v.y), tw[j << (kSegLogN - 1 - sh)]);
+    }
+    __syncthreads();
+  }
+}
+
+// In-place inverse DIT over kSegN points: bit-reversed order in, natural order out (unscaled).
+__device__ void dit_inverse(float2* x, const float2* tw) {
+  for (int h = 1, sh = 0; h < kSegN; h <<= 1, ++sh) {
+    for (int t = threadIdx.x; t < kSegN / 2; t += blockDim.x) {
+      const int j = t & (h - 1);
+      const int i = ((t >> sh) << (sh + 1)) + j;
+      float2 w = tw[j << (kSegLogN - 1 - sh)];
+      w.y = -w.y;
+      const float2 v = cmulf(x[i + h], w);
+      const float2 u = x[i];
+      x[i] = make_float2(u.x + v.x, u.y + v.y);
+      x[i + h] = make_float2(u.x - v.x, u.y - v.y);
+    }
+    __syncthreads();
+  }
+}
+
+// One CTA per window d = dmin + blockIdx.x: its bit-reversed spectrum.
+__global__ void __launch_bounds__(kSegThreads) window_spectra_kernel(const uint8_t* __restrict__ seed, uint64_t L,
+                                                                      int64_t D, int64_t dmin,
+                                                                      const float2* __restrict__ tw_g,
+                                                                      float2* __restrict__ spec) {
+  extern __shared__ float2 sm[];
+  float2* x = sm;
+  float2* tw = sm + kSegN;
+  for (int j = threadIdx.x; j < kSegN / 2; j += blockDim.x) tw[j] = tw_g[j];
+  const int64_t d = dmin + blockIdx.x;
+  const int64_t base = D + d * kSegS - kSegS + 1;
+  for (int u = threadIdx.x; u < kSegN; u += blockDim.x) {
+    const int64_t xi = base + u;
+    float v = 0.f;
+    if (u < kSegN - 1 && xi >= 0 && xi < (int64_t)L) v = (float)((seed[xi >> 3] >> (xi & 7)) & 1u);
+    x[u] = make_float2(v, 0.f);
+  }
+  __syncthreads();
+  dif_forward(x, tw);
+  float2* out = spec + (uint64_t)blockIdx.x * kSegN;
+  for (int p = threadIdx.x; p < kSegN; p += blockDim.x) out[p] = x[p];
+}
+
+__device__ __forceinline__ float raw_bit(const uint32_t* row, uint64_t t, uint64_t n_t) {
+  return t < n_t ? (float)((row[t >> 5] >> (t & 31)) & 1u) : 0.f;
+}
+
+__global__ void __launch_bounds__(kSegThreads) seg_conv_kernel(const DirectArgs a, uint64_t NQ, uint64_t NS,
+                                                                int64_t dmin, const float2* __restrict__ spec,
+                                                                const float2* __restrict__ tw_g,
+                                                                unsigned long long* __restrict__ worst) {
+  extern __shared__ float2 sm[];
+  float2* buf = sm;
+  float2* acc = sm + kSegN;
+  float2* tw = sm + 2 * kSegN;
+  uint32_t* bits = reinterpret_cast<uint32_t*>(sm + 2 * kSegN + kSegN / 2);
+  __shared__ float s_err[kSegThreads / 32];
+
+  const uint64_t blk = blockIdx.x / NQ;
+  const uint64_t q = blockIdx.x - blk * NQ;
+  const uint32_t* row = a.raw + blk * a.raw_stride;
+  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int j = threadIdx.x; j < kSegN / 2; j += blockDim.x) tw[j] = tw_g[j];
+  for (int w = threadIdx.x; w < kSegS / 32; w += blockDim.x) bits[w] = 0u;
+  float err = 0.f;
+
+  for (uint64_t s = 0; s < NS; s += 2) {
+    const bool two = (s + 1 < NS);
+    for (int t = threadIdx.x; t < kSegN; t += blockDim.x) {
+      float re = 0.f, im = 0.f;
+      if (t < kSegS) {
+        re = raw_bit(row, s * kSegS + t, a.n_t);
+        if (two) im = raw_bit(row, (s + 1) * kSegS + t, a.n_t);
+      }
+      buf[t] = make_float2(re, im);
+    }
+    __syncthreads();
+    dif_forward(buf, tw);
+    const float2* W0 = spec + (uint64_t)((int64_t)q - (int64_t)s - dmin) * kSegN;
+    const float2* W1 = two ? spec + (uint64_t)((int64_t)q - (int64_t)s - 1 - dmin) * kSegN : W0;
+    for (int p = threadIdx.x; p < kSegN; p += blockDim.x) {
+      // frequency f sits at bit-reversed position p; -f at the bit-reversed position of N - f
+      const uint32_t f = __brev((uint32_t)p) >> (32 - kSegLogN);
+      const uint32_t pm = __brev((kSegN - f) & (kSegN - 1)) >> (32 - kSegLogN);
+      const float2 zf = buf[p], zm = buf[pm];
+      // R_s = (Z_f + conj Z_-f) / 2,  R_{s+1} = (Z_f - conj Z_-f) / (2i)
+      const float2 r0 = make_float2(0.5f * (zf.x + zm.x), 0.5f * (zf.y - zm.y));
+      float2 o = cmulf(W0[p], r0);
+      if (two) {
+        const float2 r1 = make_float2(0.5f * (zf.y + zm.y), -0.5f * (zf.x - zm.x));
+        const float2 o1 = cmulf(W1[p], r1);
+        o.x += o1.x;
+        o.y += o1.y;
+      }
+      acc[p] = o;
+    }
+    __syncthreads();
+    dit_inverse(acc, tw);
+    // partial sums for the tile's outputs i' = t - (S - 1): round, parity, XOR into the tile bits
+    for (int t = threadIdx.x; t < kSegS; t += blockDim.x) {
+      const float v = acc[kSegS - 1 + t].x * (1.0f / kSegN);
+      const float r = rintf(v);
+      err = fmaxf(err, fabsf(v - r));
+      const uint32_t wrd = __ballot_sync(0xffffffffu, ((int)r) & 1);
+      if (lane == 0) bits[t >> 5] ^= wrd;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) err = fmaxf(err, __shfl_xor_sync(0xffffffffu, err, o));
+  if (lane == 0) s_err[wid] = err;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float e = 0.f;
+    for (int w = 0; w < kSegThreads / 32; ++w) e = fmaxf(e, s_err[w]);
+    atomicMax(worst, (unsigned long long)__double_as_longlong((double)e));
+  }
+  for (int w = threadIdx.x; w < kSegS / 32; w += blockDim.x) {
+    const uint64_t ow = q * (kSegS / 32) + w;
+    if (ow >= a.mw) continue;
+    const uint32_t rem = a.m - 32 * (uint32_t)ow;
+    const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+    uint32_t word = bits[w] & omask;
+    if (a.modified) {
+      const uint64_t bit = (uint64_t)a.id_off + 32ull * ow;
+      const uint64_t rq = bit >> 5;
+      const uint32_t rs = (uint32_t)(bit & 31);
+      const uint32_t lo = row[rq];
+      const uint32_t hi = (rs && rq + 1 < a.raw_stride) ? row[rq + 1] : 0u;
+      word ^= __funnelshift_r(lo, hi, rs) & omask;
+    }
+    a.out[blk * a.out_stride + ow] = word;
+  }
+}
+
+}  // namespace
+
+uint64_t fft32_segment() { return kSegS; }
+
+cudaError_t launch_fft32_seg(const DirectArgs& d, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
+                             uint32_t* kernels) {
+  const uint64_t NS = ceil_div(d.n_t, kSegS), NQ = ceil_div(d.m, kSegS);
+  const int64_t dmin = -(int64_t)(NS - 1);
+  const uint64_t nwin = NQ + NS - 1;
+  cudaError_t e;
+  if ((e = ws.tw32.ensure((kSegN / 2) * sizeof(float2))) != cudaSuccess) return e;
+  if ((e = ws.spec.ensure(nwin * kSegN * sizeof(float2))) != cudaSuccess) return e;
+  twiddle32_kernel<<<kSegN / 2 / 256, 256, 0, s>>>(ws.tw32.as<float2>());
+  ++*kernels;
+  const size_t smem_win = (kSegN + kSegN / 2) * sizeof(float2);
+  if ((e = cudaFuncSetAttribute(window_spectra_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_win)) !=
+      cudaSuccess)
+    return e;
+  window_spectra_kernel<<<(unsigned)nwin, kSegThreads, smem_win, s>>>(seed, L_t, (int64_t)d.n_t - 1, dmin,
+                                                                      ws.tw32.as<float2>(), ws.spec.as<float2>());
+  ++*kernels;
+  const size_t smem = (2 * kSegN + kSegN / 2) * sizeof(float2) + (kSegS / 32) * sizeof(uint32_t);
+  if ((e = cudaFuncSetAttribute(seg_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return e;
+  const uint64_t ctas = d.num_blocks * NQ;
+  if (ctas > 0x7fffffffull) return cudaErrorInvalidConfiguration;
+  seg_conv_kernel<<<(unsigned)ctas, kSegThreads, smem, s>>>(d, NQ, NS, dmin, ws.spec.as<float2>(),
+                                                            ws.tw32.as<float2>(), ws.worst);
+  ++*kernels;
+  return cudaGetLastError();
+}
+
+}  // namespace qrng

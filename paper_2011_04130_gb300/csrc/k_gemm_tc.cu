@@ -438,7 +438,7 @@ cudaError_t launch_gemm_tc(const DirectArgs& d, int* err, int num_sms, cudaStrea
   if (!encode) {
     void* fn = nullptr;
     cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPoint("cuTensorMapEncodeTiled", &fn, cudaEnableDefault, &q) != cudaSuccess ||
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
         q != cudaDriverEntryPointSuccess || !fn)
       return cudaErrorNotSupported;
     encode = reinterpret_cast<PFN_encodeTiled>(fn);

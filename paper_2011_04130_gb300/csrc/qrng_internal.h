@@ -82,6 +82,7 @@ cudaError_t launch_pack_blocks(const uint32_t* src, uint64_t stride_w, uint64_t 
 
 // ---- direct bit-packed extraction (k_direct.cu) ----
 struct DirectArgs {
+  uint64_t n_t;          // Toeplitz columns: n (standard) or n-m (modified)
   const uint32_t* raw;   // word-aligned blocks
   uint64_t raw_stride;   // words per block
   uint32_t nw_t;         // words of the Toeplitz part: ceil(n_t/32), n_t = n (standard) or n-m (modified)
@@ -101,6 +102,28 @@ struct DirectArgs {
 int direct_outputs_per_warp();
 cudaError_t launch_direct(const DirectArgs& a, cudaStream_t s, uint32_t* kernels);
 
+// ---- FFT routes (k_fft.cu) ----
+constexpr uint64_t kFftWorkspaceBytes = 1ull << 31;  // budget for the FP64 ping-pong buffers
+struct FftWorkspace {
+  DevBuf buf0, buf1, spec, tw, tw32;
+  uint64_t tw_P = 0;                    // length the FP64 twiddle table holds
+  unsigned long long* worst = nullptr;  // device: bits of the largest |s - round(s)| (a double)
+  void release() {
+    buf0.release();
+    buf1.release();
+    spec.release();
+    tw.release();
+    tw32.release();
+    tw_P = 0;
+  }
+};
+uint64_t fft64_length(uint64_t n_t, uint64_t m);
+uint64_t fft32_segment();
+cudaError_t launch_fft64(const DirectArgs& a, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
+                         uint32_t* kernels);
+cudaError_t launch_fft32_seg(const DirectArgs& a, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
+                             uint32_t* kernels);
+
 // ---- tensor-core block-batched extraction (k_gemm_tc.cu) ----
 // Same layout arguments as the direct kernel (splits unused). Exact for n_t <= kGemmMaxColumns.
 constexpr uint64_t kGemmMaxColumns = 1ull << 22;
@@ -115,6 +138,8 @@ struct qrng_ctx {
   std::string err;
   qrng::DevBuf hist, result, seed_rev, raw_stage, out_stage, samples_dev, out_dev, seed_dev;
   qrng::DevBuf dev_err;  // int error word written by kernels with bounded waits (0 = no error)
+  qrng::DevBuf fft_worst;  // double bits of the worst FFT rounding distance since the last reset
+  qrng::FftWorkspace fft;
   qrng::DevHminResult* result_host = nullptr;  // pinned
   qrng_stats stats{};
   // optional CUDA-event timing of the main extraction kernel

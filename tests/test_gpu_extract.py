@@ -14,7 +14,7 @@ from gpu_util import extract, spot_check
 pytestmark = pytest.mark.gpu
 
 STD, MOD = 0, 1
-ALGOS = {"direct": 1, "gemm_tc": 2}
+ALGOS = {"direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4}
 
 
 def _seed_len(n, m, form):
@@ -109,6 +109,34 @@ def test_algorithms_agree_on_laser_stream(qlib, gpu, algo):
     ref = extract(qlib, gpu, samples, n, m, seed, STD, qlib.QRNG_ALGO_DIRECT, B)
     got = extract(qlib, gpu, samples, n, m, seed, STD, ALGOS[algo], B)
     assert np.array_equal(got, ref)
+
+
+@pytest.mark.parametrize("algo,bound", [("fft64", 1e-6), ("fft32_seg", 0.25)])
+def test_fft_rounding_evidence(qlib, gpu, oracle_mod, algo, bound):
+    """The FFT paths report the largest distance of a used convolution sum from its integer; it
+    stays inside the exactness margin (the guard trips at 0.25)."""
+    n, m, B = 1 << 14, 12000, 16
+    raw, seed = _case(n, m, STD, B, 4711)
+    qlib.qrng_reset_stats(gpu)
+    got = extract(qlib, gpu, raw, n, m, seed, STD, ALGOS[algo], B)
+    st = qlib.qrng_get_stats(gpu)
+    assert 0.0 < st["worst_fft_round_err"] < bound, st
+    assert not oracle_mod.freivalds(raw, n, m, seed, STD, B, got).any()
+
+
+@pytest.mark.parametrize("log2n", [12, 16, 20])
+def test_fft64_block_length_sweep_point(qlib, gpu, oracle_mod, log2n):
+    """The paper's FFT route on the fixed 2^30-bit stream, modified form, m = 0.75 n."""
+    c = W.CFG3
+    n = 1 << log2n
+    m = int(n * c["ratio"])
+    B = c["stream_bits"] // n
+    raw = W.random_bits(c["stream_bits"], c["raw_seed"])
+    seed = W.random_bits(n - 1, c["seed_seed"] + log2n)
+    got = extract(qlib, gpu, raw, n, m, seed, MOD, qlib.QRNG_ALGO_FFT64, B)
+    ref = extract(qlib, gpu, raw, n, m, seed, MOD, qlib.QRNG_ALGO_DIRECT, B)
+    assert np.array_equal(got, ref)
+    spot_check(oracle_mod, raw, n, m, seed, MOD, got, blocks=[0, B - 1], per_block=128)
 
 
 def test_gemm_rejects_too_long_blocks(qlib, gpu):

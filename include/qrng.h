@@ -148,7 +148,9 @@ QRNG_API uint64_t qrng_output_length(uint64_t n, double h_per_sample, int bits, 
 enum { QRNG_FORM_STANDARD = 0, QRNG_FORM_MODIFIED = 1 };
 
 enum {
-  QRNG_ALGO_AUTO = 0,     /* pick the fastest supported algorithm (autotuned, cached per shape)   */
+  QRNG_ALGO_AUTO = 0,     /* the fastest algorithm for the shape: on the first call of a shape the
+                             candidates a cost model keeps are each run once and timed (that call
+                             synchronises the stream), and the winner is cached on the context     */
   QRNG_ALGO_DIRECT = 1,   /* bit-packed AND/XOR + parity, each block on its own (Sec. III.B, O(mn)) */
   QRNG_ALGO_GEMM_TC = 2,  /* all blocks as one GF(2) matrix product T X on tcgen05 tensor cores   */
   QRNG_ALGO_FFT64 = 3,    /* circulant embedding + FP64 FFT convolution per block (Sec. III.B-D) */
@@ -176,6 +178,36 @@ QRNG_API uint64_t qrng_seed_bits(uint64_t n, uint64_t m, int form);
  */
 QRNG_API int qrng_toeplitz_extract(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed,
                           int form, int algo, uint64_t num_blocks, uint8_t* out, qrng_stream_t stream);
+
+/* ----------------------------------------------------------------------------------------------
+ * Uneven batches (Sec. III.E block processing, many independent requests)
+ * --------------------------------------------------------------------------------------------*/
+
+typedef struct {
+  const uint8_t* raw;     /* device; the request's n raw bits start at bit raw_bit_off          */
+  uint64_t raw_bit_off;
+  uint64_t n, m;          /* one block: standard 1 <= m <= n, modified 1 <= m < n, n <= 2^26    */
+  const uint8_t* seed;    /* device; qrng_seed_bits(n, m, form) bits from bit 0 (its own seed)  */
+  int form;               /* QRNG_FORM_STANDARD or QRNG_FORM_MODIFIED                          */
+  uint8_t* out;           /* device; the m output bits are written at bit out_bit_off; every
+                             other bit of the buffer is left as it was (requests may share bytes) */
+  uint64_t out_bit_off;
+} qrng_request;
+
+/*
+ * qrng_extract_batch -- hash `count` independent requests, each one block with its own seed and
+ * shape (Sec. III.B / III.D per request; Sec. III.E independence), in ONE persistent kernel launch:
+ * work items (request, output tile, raw-word range) are numbered largest request first and taken
+ * from an atomic counter by resident warps. The layout, hashing and output-merge kernels are
+ * captured once into a CUDA graph cached on the context (keyed by the request table and its
+ * buffers); a repeated identical call replays the graph.
+ *   reqs   host; `count` >= 1 requests (device pointers inside; outputs must not overlap raw or
+ *          seed data, and two requests' output bit ranges must not overlap).
+ *   algo   QRNG_ALGO_AUTO or QRNG_ALGO_DIRECT; anything else is QRNG_ENOTSUP.
+ * Asynchronous on `stream`. Batch calls on one context must not overlap on the GPU.
+ */
+QRNG_API int qrng_extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int algo,
+                                qrng_stream_t stream);
 
 /* ----------------------------------------------------------------------------------------------
  * Whole pipeline on host buffers
@@ -225,6 +257,10 @@ QRNG_API int qrng_reset_stats(qrng_ctx* ctx);
  * sum 0.25 or more away from an integer since the last qrng_reset_stats (its rounding, hence its
  * parity, is then not trustworthy). Kernels never trap or hang on such a failure. */
 QRNG_API int qrng_synchronize(qrng_ctx* ctx, qrng_stream_t stream);
+
+/* Autotuning of QRNG_ALGO_AUTO (on = 1, the default; off = 0 uses the cost model alone and never
+ * synchronises). Changing it forgets the shapes tuned so far. */
+QRNG_API int qrng_set_autotune(qrng_ctx* ctx, int on);
 
 /* Timing of the main extraction kernel of each qrng_toeplitz_extract call (on = 1, off = 0):
  * a CUDA event pair is recorded around that one launch on the caller's stream and summed into

@@ -23,7 +23,7 @@ ALGO_NAMES = {QRNG_ALGO_AUTO: "auto", QRNG_ALGO_DIRECT: "direct", QRNG_ALGO_GEMM
 EXPORTED = ["qrng_create", "qrng_destroy", "qrng_last_error", "qrng_status_string", "qrng_minentropy",
             "qrng_output_length", "qrng_seed_bits", "qrng_toeplitz_extract", "qrng_postprocess_host",
             "qrng_get_stats", "qrng_reset_stats", "qrng_set_timing", "qrng_synchronize",
-            "qrng_minentropy_noalloc"]
+            "qrng_minentropy_noalloc", "qrng_extract_batch", "qrng_set_autotune"]
 
 
 class QrngError(RuntimeError):
@@ -51,6 +51,20 @@ class HminReport(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+class Request(ctypes.Structure):
+    """qrng_request: one block with its own seed and shape (device pointers)."""
+    _fields_ = [
+        ("raw", ctypes.c_void_p),
+        ("raw_bit_off", ctypes.c_uint64),
+        ("n", ctypes.c_uint64),
+        ("m", ctypes.c_uint64),
+        ("seed", ctypes.c_void_p),
+        ("form", ctypes.c_int),
+        ("out", ctypes.c_void_p),
+        ("out_bit_off", ctypes.c_uint64),
+    ]
 
 
 class Stats(ctypes.Structure):
@@ -98,6 +112,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qrng_reset_stats.argtypes = [vp]
     lib.qrng_set_timing.argtypes = [vp, i32]
     lib.qrng_synchronize.argtypes = [vp, vp]
+    lib.qrng_set_autotune.argtypes = [vp, i32]
+    lib.qrng_extract_batch.argtypes = [vp, ctypes.POINTER(Request), u64, i32, vp]
     lib.qrng_minentropy_noalloc.argtypes = [vp, u64, i32, dbl, ctypes.POINTER(HminReport), vp]
     _lib = lib
     return lib
@@ -256,3 +272,21 @@ def qrng_minentropy_noalloc(samples, count: int | None = None, bits: int = 8, ep
     if st != QRNG_OK:
         raise QrngError(st, "qrng_minentropy_noalloc")
     return rep.as_dict()
+
+
+def qrng_extract_batch(ctx: Context, requests, algo: int = QRNG_ALGO_AUTO, stream=None):
+    """Hash a list of requests, each a dict or tuple (raw, raw_bit_off, n, m, seed, form, out, out_bit_off)
+    with device addresses (tensors or ints), in one persistent launch."""
+    arr = (Request * len(requests))()
+    for i, r in enumerate(requests):
+        if isinstance(r, dict):
+            r = (r["raw"], r.get("raw_bit_off", 0), r["n"], r["m"], r["seed"], r.get("form", 0), r["out"],
+                 r.get("out_bit_off", 0))
+        raw, roff, n, m, seed, form, out, ooff = r
+        arr[i] = Request(_ptr(raw), roff, n, m, _ptr(seed), form, _ptr(out), ooff)
+    st = load_library().qrng_extract_batch(ctx.handle, arr, len(requests), algo, _stream(stream))
+    ctx.check(st, "qrng_extract_batch")
+
+
+def qrng_set_autotune(ctx: Context, on: bool):
+    ctx.check(load_library().qrng_set_autotune(ctx.handle, 1 if on else 0), "qrng_set_autotune")

@@ -6,7 +6,9 @@
 #include <string.h>
 
 #include <cstdio>
+#include <algorithm>
 #include <new>
+#include <vector>
 #include <string>
 
 #include "qrng_internal.h"
@@ -211,6 +213,103 @@ int check_extract_args(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m
   return QRNG_OK;
 }
 
+// Rough time model (seconds) of each algorithm, used to prune the autotuner's candidates and as
+// the choice when autotuning is off. Rates are the ones measured on GB300 for these kernels.
+double model_seconds(int algo, uint64_t n_t, uint64_t m, uint64_t B) {
+  const double bm = (double)m * (double)n_t * (double)B;
+  switch (algo) {
+    case QRNG_ALGO_DIRECT:
+      return bm / 5.6e14 + 5e-6;
+    case QRNG_ALGO_GEMM_TC: {
+      const double mp = (double)ceil_div(m, 256) * 256, bp = (double)ceil_div(B, 256) * 256;
+      return mp * (double)n_t * bp / 1.75e15 + 1e-5;
+    }
+    case QRNG_ALGO_FFT64: {
+      const double P = (double)fft64_length(n_t, m), lg = log2(P), pairs = (double)ceil_div(B, 2);
+      return pairs * (10.0 * P * lg / 6e11 + 64.0 * P * lg / 6e12) + 2.0 * lg * 4e-6;
+    }
+    case QRNG_ALGO_FFT32_SEG: {
+      const double S = (double)fft32_segment(), N = 2 * S;
+      const double pairs = (double)B * (double)ceil_div(m, (uint64_t)S) * ceil((double)ceil_div(n_t, (uint64_t)S) / 2);
+      return pairs * 10.0 * N * log2(N) / 1.5e13 + 2e-5;
+    }
+  }
+  return 1e30;
+}
+
+bool algo_applicable(int algo, uint64_t n_t, uint64_t m, uint64_t B) {
+  switch (algo) {
+    case QRNG_ALGO_DIRECT:
+      return true;
+    case QRNG_ALGO_GEMM_TC:
+      return n_t <= kGemmMaxColumns;
+    case QRNG_ALGO_FFT64:
+      return fft64_length(n_t, m) <= (1ull << 27);
+    case QRNG_ALGO_FFT32_SEG:
+      return true;
+  }
+  return false;
+}
+
+int extract_one(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
+                uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels) {
+  return extract_bitwise(ctx, algo, raw, n, m, seed, form, num_blocks, out, s, kernels);
+}
+
+// QRNG_ALGO_AUTO: the candidates within 4x of the best modelled time are each run once on the
+// call's own data (they give identical bits), timed with CUDA events, and the fastest is kept for
+// this shape; later calls of the shape use it directly.
+int choose_auto(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
+                uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels, int* chosen, bool* done) {
+  const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
+  const int algos[4] = {QRNG_ALGO_DIRECT, QRNG_ALGO_GEMM_TC, QRNG_ALGO_FFT64, QRNG_ALGO_FFT32_SEG};
+  double best_model = 1e30;
+  int best_algo = QRNG_ALGO_DIRECT;
+  for (int a : algos)
+    if (algo_applicable(a, n_t, m, num_blocks)) {
+      const double t = model_seconds(a, n_t, m, num_blocks);
+      if (t < best_model) { best_model = t; best_algo = a; }
+    }
+  *done = false;
+  if (!ctx->autotune) {
+    *chosen = best_algo;
+    return QRNG_OK;
+  }
+  uint32_t lb = 0;
+  while ((1ull << lb) < num_blocks) ++lb;
+  const qrng_ctx::TuneKey key{n, m, lb, form};
+  for (const auto& e : ctx->tuned)
+    if (e.first == key) {
+      *chosen = e.second;
+      return QRNG_OK;
+    }
+  int best = -1;
+  float best_ms = 0.f;
+  for (int a : algos) {
+    if (!algo_applicable(a, n_t, m, num_blocks) || model_seconds(a, n_t, m, num_blocks) > 4.0 * best_model) continue;
+    cudaEvent_t e0, e1;
+    QRNG_CUDA(ctx, cudaEventCreate(&e0), "autotune event");
+    QRNG_CUDA(ctx, cudaEventCreate(&e1), "autotune event");
+    QRNG_CUDA(ctx, cudaEventRecord(e0, s), "autotune event");
+    const int st = extract_one(ctx, a, raw, n, m, seed, form, num_blocks, out, s, kernels);
+    QRNG_CUDA(ctx, cudaEventRecord(e1, s), "autotune event");
+    QRNG_CUDA(ctx, cudaEventSynchronize(e1), "autotune wait");
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, e0, e1);
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (st == QRNG_OK && (best < 0 || ms < best_ms)) {
+      best = a;
+      best_ms = ms;
+    }
+  }
+  if (best < 0) best = QRNG_ALGO_DIRECT;
+  ctx->tuned.push_back({key, best});
+  *chosen = best;
+  *done = true;  // the output already holds the result (every candidate writes the same bits)
+  return QRNG_OK;
+}
+
 int extract_dispatch(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
                      int algo, uint64_t num_blocks, uint8_t* out, cudaStream_t s) {
   uint32_t kernels = 0;
@@ -218,10 +317,15 @@ int extract_dispatch(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, 
   const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
   int used = algo;
   if (used == QRNG_ALGO_AUTO) {
-    // Many blocks sharing the seed form a dense product worth the tensor cores; few or tiny blocks
-    // do not fill a 256 x 256 tile and stay on the bit-packed integer kernel.
-    const bool dense = num_blocks >= 128 && m >= 128 && n_t >= 512 && n_t <= kGemmMaxColumns;
-    used = dense ? QRNG_ALGO_GEMM_TC : QRNG_ALGO_DIRECT;
+    bool done = false;
+    st = choose_auto(ctx, raw, n, m, seed, form, num_blocks, out, s, &kernels, &used, &done);
+    if (st != QRNG_OK) return st;
+    if (done) {
+      ctx->stats.kernels_launched += kernels;
+      ctx->stats.last_algo = used;
+      ctx->stats.last_kernels = kernels;
+      return QRNG_OK;
+    }
   }
   switch (used) {
     case QRNG_ALGO_DIRECT:
@@ -245,6 +349,151 @@ int extract_dispatch(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, 
     ctx->stats.last_kernels = kernels;
   }
   return st;
+}
+
+uint64_t fnv1a(const void* data, size_t bytes, uint64_t h = 1469598103934665603ull) {
+  const uint8_t* p = static_cast<const uint8_t*>(data);
+  for (size_t i = 0; i < bytes; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+void drop_graph(qrng_ctx::BatchGraph& g) {
+  if (g.exec) cudaGraphExecDestroy(g.exec);
+  if (g.graph) cudaGraphDestroy(g.graph);
+  if (g.meta_host) cudaFreeHost(g.meta_host);
+  g = qrng_ctx::BatchGraph{};
+}
+
+void drop_all_graphs(qrng_ctx* ctx) {
+  for (auto& g : ctx->graphs) drop_graph(g);
+  ctx->graphs.clear();
+}
+
+// Grows a batch buffer; any move invalidates the graphs that captured the old address.
+cudaError_t ensure_batch(qrng_ctx* ctx, DevBuf& b, size_t bytes) {
+  if (bytes <= b.cap) return cudaSuccess;
+  cudaError_t e = cudaStreamSynchronize(ctx->capture_stream);
+  if (e != cudaSuccess) return e;
+  drop_all_graphs(ctx);
+  ++ctx->batch_generation;
+  return b.ensure(bytes);
+}
+
+constexpr size_t kMaxGraphs = 4;
+
+int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, cudaStream_t s) {
+  // Request table in device layout, largest work first.
+  std::vector<BatchReq> t(count);
+  std::vector<uint64_t> order(count);
+  for (uint64_t i = 0; i < count; ++i) {
+    const qrng_request& r = reqs[i];
+    BatchReq& q = t[i];
+    q = BatchReq{};
+    q.raw = r.raw;
+    q.raw_bit_off = r.raw_bit_off;
+    q.n = r.n;
+    q.m = r.m;
+    q.seed = r.seed;
+    q.form = r.form;
+    q.out = r.out;
+    q.out_bit_off = r.out_bit_off;
+    q.n_t = r.form == QRNG_FORM_MODIFIED ? r.n - r.m : r.n;
+    q.L_t = q.n_t + r.m - 1;
+    q.nw_t = (uint32_t)ceil_div(q.n_t, 32);
+    q.tail_mask = (q.n_t % 32) ? ((1u << (q.n_t % 32)) - 1u) : 0xffffffffu;
+    q.mw = (uint32_t)ceil_div(r.m, 32);
+    q.tiles = (uint32_t)ceil_div(r.m, (uint64_t)direct_outputs_per_warp());
+    q.splits = (uint32_t)ceil_div(q.nw_t, kBatchWordsPerSplit);
+    q.id_off = (uint32_t)(r.n - r.m);
+    q.raw_words = ceil_div(r.n, 32);
+    q.rev_words = kSeedFrontWords + ceil_div(q.L_t, 32) + kSeedBackWords;
+    const uint64_t first = (reinterpret_cast<uintptr_t>(r.out) * 8 + r.out_bit_off);
+    q.dst_word0 = first / 32;
+    q.dst_words = (first + r.m - 1) / 32 - q.dst_word0 + 1;
+    order[i] = i;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](uint64_t x, uint64_t y) {
+    return t[x].m * t[x].n_t > t[y].m * t[y].n_t;
+  });
+  std::vector<BatchReq> sorted(count);
+  uint64_t raw_total = 0, rev_total = 0, out_total = 0, items = 0, dst_total = 0;
+  for (uint64_t k = 0; k < count; ++k) {
+    BatchReq q = t[order[k]];
+    q.raw_stage_off = raw_total;
+    raw_total += q.raw_words;
+    q.rev_off = rev_total;
+    rev_total += q.rev_words;
+    q.out_stage_off = out_total;
+    out_total += q.mw;
+    q.item_begin = items;
+    items += (uint64_t)q.tiles * q.splits;
+    q.dst_begin = dst_total;
+    dst_total += q.dst_words;
+    sorted[k] = q;
+  }
+
+  const uint64_t key = fnv1a(sorted.data(), sorted.size() * sizeof(BatchReq), fnv1a(&count, sizeof(count)));
+  uint32_t kernels = 0;
+  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_meta, count * sizeof(BatchReq)), "batch table workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_raw, raw_total * 4), "batch raw workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_rev, rev_total * 4), "batch seed workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_out, out_total * 4), "batch output workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_counter, sizeof(unsigned long long)), "batch counter");
+
+  qrng_ctx::BatchGraph* hit = nullptr;
+  for (auto& g : ctx->graphs)
+    if (g.key == key && g.generation == ctx->batch_generation) hit = &g;
+  if (!hit) {
+    if (ctx->graphs.size() >= kMaxGraphs) {  // evict the least recently used graph
+      size_t victim = 0;
+      for (size_t i = 1; i < ctx->graphs.size(); ++i)
+        if (ctx->graphs[i].stamp < ctx->graphs[victim].stamp) victim = i;
+      QRNG_CUDA(ctx, cudaStreamSynchronize(s), "graph eviction");
+      drop_graph(ctx->graphs[victim]);
+      ctx->graphs.erase(ctx->graphs.begin() + victim);
+    }
+    qrng_ctx::BatchGraph g;
+    g.key = key;
+    g.generation = ctx->batch_generation;
+    QRNG_CUDA(ctx, cudaMallocHost(&g.meta_host, count * sizeof(BatchReq)), "pinned request table");
+    memcpy(g.meta_host, sorted.data(), count * sizeof(BatchReq));
+    cudaStream_t cs = ctx->capture_stream;
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->batch_meta.p, g.meta_host, count * sizeof(BatchReq),
+                                              cudaMemcpyHostToDevice, cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->batch_counter.p, 0, sizeof(unsigned long long), cs);
+    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->batch_out.p, 0, out_total * 4, cs);
+    if (e == cudaSuccess)
+      e = launch_batch_layout(ctx->batch_meta.as<BatchReq>(), (uint32_t)count, raw_total, rev_total,
+                              ctx->batch_raw.as<uint32_t>(), ctx->batch_rev.as<uint32_t>(), cs, &kernels);
+    if (e == cudaSuccess)
+      e = launch_batch_direct(ctx->batch_meta.as<BatchReq>(), (uint32_t)count, items, ctx->batch_raw.as<uint32_t>(),
+                              ctx->batch_rev.as<uint32_t>(), ctx->batch_out.as<uint32_t>(),
+                              ctx->batch_counter.as<unsigned long long>(), ctx->num_sms, cs, &kernels);
+    if (e == cudaSuccess)
+      e = launch_batch_pack(ctx->batch_meta.as<BatchReq>(), (uint32_t)count, dst_total, ctx->batch_out.as<uint32_t>(),
+                            cs, &kernels);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
+    if (e == cudaSuccess) e = e2;
+    g.graph = graph;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&g.exec, g.graph, 0);
+    if (e != cudaSuccess) {
+      drop_graph(g);
+      return cuda_fail(ctx, e, "batch graph capture");
+    }
+    ctx->graphs.push_back(g);
+    hit = &ctx->graphs.back();
+  }
+  hit->stamp = ++ctx->graph_clock;
+  QRNG_CUDA(ctx, cudaGraphLaunch(hit->exec, s), "batch graph launch");
+  ctx->stats.kernels_launched += 4;
+  ctx->stats.last_kernels = 4;
+  ctx->stats.last_algo = QRNG_ALGO_DIRECT;
+  return QRNG_OK;
 }
 
 }  // namespace
@@ -277,6 +526,13 @@ int qrng_create(qrng_ctx** out, int device) {
     delete ctx;
     return QRNG_ENOMEM;
   }
+  if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaFreeHost(ctx->result_host);
+    ctx->dev_err.release();
+    ctx->fft_worst.release();
+    delete ctx;
+    return QRNG_ECUDA;
+  }
   *out = ctx;
   return QRNG_OK;
 }
@@ -296,6 +552,13 @@ void qrng_destroy(qrng_ctx* ctx) {
   ctx->dev_err.release();
   ctx->fft_worst.release();
   ctx->fft.release();
+  drop_all_graphs(ctx);
+  ctx->batch_meta.release();
+  ctx->batch_raw.release();
+  ctx->batch_rev.release();
+  ctx->batch_out.release();
+  ctx->batch_counter.release();
+  if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   if (ctx->result_host) cudaFreeHost(ctx->result_host);
   for (cudaEvent_t e : ctx->ev_start) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->ev_end) cudaEventDestroy(e);
@@ -345,6 +608,22 @@ int qrng_toeplitz_extract(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_
   if (st) return st;
   QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
   return extract_dispatch(ctx, raw, n, m, seed, form, algo, num_blocks, out, static_cast<cudaStream_t>(stream));
+}
+
+int qrng_extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int algo, qrng_stream_t stream) {
+  if (!ctx) return QRNG_EINVAL;
+  if (!reqs || count == 0 || count > (1ull << 31)) return fail(ctx, QRNG_EINVAL, "qrng_extract_batch: bad request table");
+  if (algo != QRNG_ALGO_AUTO && algo != QRNG_ALGO_DIRECT)
+    return fail(ctx, QRNG_ENOTSUP, "qrng_extract_batch: batches run the direct kernel (AUTO or DIRECT)");
+  for (uint64_t i = 0; i < count; ++i) {
+    const qrng_request& r = reqs[i];
+    if (!r.raw || !r.seed || !r.out)
+      return fail(ctx, QRNG_EINVAL, "qrng_extract_batch: request " + std::to_string(i) + " has a NULL pointer");
+    if ((r.form != QRNG_FORM_STANDARD && r.form != QRNG_FORM_MODIFIED) || !shape_ok(r.n, r.m, r.form))
+      return fail(ctx, QRNG_EINVAL, "qrng_extract_batch: request " + std::to_string(i) + " has a bad shape or form");
+  }
+  QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+  return extract_batch(ctx, reqs, count, static_cast<cudaStream_t>(stream));
 }
 
 int qrng_postprocess_host(qrng_ctx* ctx, const void* samples_host, uint64_t count, int bits, double eps,
@@ -440,6 +719,13 @@ int qrng_synchronize(qrng_ctx* ctx, qrng_stream_t stream) {
   if (w >= kFftRoundGuard)
     return fail(ctx, QRNG_EPRECISION,
                 "an FFT convolution sum was " + std::to_string(w) + " away from an integer; its parity is unreliable");
+  return QRNG_OK;
+}
+
+int qrng_set_autotune(qrng_ctx* ctx, int on) {
+  if (!ctx || (on != 0 && on != 1)) return QRNG_EINVAL;
+  ctx->autotune = (on == 1);
+  ctx->tuned.clear();
   return QRNG_OK;
 }
 

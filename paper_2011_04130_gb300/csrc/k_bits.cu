@@ -99,7 +99,111 @@ __global__ void pack_blocks_kernel(const uint32_t* __restrict__ src, uint64_t st
   }
 }
 
+// Index of the request whose range [first(r), first(r+1)) holds idx (ranges are non-decreasing).
+template <class F>
+__device__ __forceinline__ uint32_t find_req(uint32_t nreq, uint64_t idx, F first) {
+  uint32_t lo = 0, hi = nreq - 1;
+  while (lo < hi) {
+    const uint32_t mid = (lo + hi + 1) >> 1;
+    if (first(mid) <= idx) lo = mid;
+    else hi = mid - 1;
+  }
+  return lo;
+}
+
+// Raw staging word idx of the batch (each request one word-aligned block, bits beyond n zero).
+__global__ void batch_repack_kernel(const BatchReq* __restrict__ reqs, uint32_t nreq, uint64_t total,
+                                    uint32_t* __restrict__ dst) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const uint32_t r = find_req(nreq, idx, [&](uint32_t k) { return reqs[k].raw_stage_off; });
+  const BatchReq& q = reqs[r];
+  const uint64_t w = idx - q.raw_stage_off;
+  uint32_t v = 0;
+  if (32 * w < q.n) {
+    v = read_bits32(q.raw, q.raw_bit_off + q.n, q.raw_bit_off + 32 * w);
+    const uint64_t left = q.n - 32 * w;
+    if (left < 32) v &= (1u << left) - 1u;
+  }
+  dst[idx] = v;
+}
+
+// Reversed, padded seed word idx of the batch (the layout of seed_reverse_kernel, per request).
+__global__ void batch_seed_reverse_kernel(const BatchReq* __restrict__ reqs, uint32_t nreq, uint64_t total,
+                                          uint32_t* __restrict__ rev) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const uint32_t r = find_req(nreq, idx, [&](uint32_t k) { return reqs[k].rev_off; });
+  const BatchReq& q = reqs[r];
+  const int64_t w = (int64_t)(idx - q.rev_off) - kSeedFrontWords;
+  uint32_t out = 0;
+  if (w >= 0) {
+    const int64_t top = (int64_t)q.L_t - 1 - 32 * w;
+    if (top >= 0) {
+      const int64_t lo = top - 31;
+      const uint32_t x = lo >= 0 ? read_bits32(q.seed, q.L_t, (uint64_t)lo)
+                                 : read_bits32(q.seed, q.L_t, 0) << (uint32_t)(-lo);
+      out = __brev(x);
+    }
+  }
+  rev[idx] = out;
+}
+
+// Destination word idx of the batch: bits of one request's output moved to its bit offset in the
+// caller's buffer. Words shared with other bits of the buffer are merged with atomics.
+__global__ void batch_pack_kernel(const BatchReq* __restrict__ reqs, uint32_t nreq, uint64_t total,
+                                  const uint32_t* __restrict__ src) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const uint32_t r = find_req(nreq, idx, [&](uint32_t k) { return reqs[k].dst_begin; });
+  const BatchReq& q = reqs[r];
+  const uint64_t W = q.dst_word0 + (idx - q.dst_begin);      // absolute 32-bit word index
+  const uint64_t start = reinterpret_cast<uintptr_t>(q.out) * 8 + q.out_bit_off;  // absolute first output bit
+  const uint64_t g0 = (32 * W > start) ? 32 * W : start;
+  const uint64_t g1 = (32 * W + 32 < start + q.m) ? 32 * W + 32 : start + q.m;
+  const uint32_t* row = src + q.out_stage_off;
+  uint32_t val = 0, mask = 0;
+  for (uint64_t g = g0; g < g1;) {
+    const uint64_t i = g - start;  // output index within the request
+    const uint64_t qw = i >> 5;
+    const uint32_t sh = (uint32_t)(i & 31);
+    const uint32_t take = (uint32_t)min((uint64_t)(32 - sh), g1 - g);
+    const uint32_t lo = row[qw];
+    const uint32_t hi = (sh && qw + 1 < q.mw) ? row[qw + 1] : 0u;
+    uint32_t bits = __funnelshift_r(lo, hi, sh);
+    const uint32_t tm = take >= 32 ? 0xffffffffu : ((1u << take) - 1u);
+    const uint32_t pos = (uint32_t)(g - 32 * W);
+    val |= (bits & tm) << pos;
+    mask |= tm << pos;
+    g += take;
+  }
+  uint32_t* dst = reinterpret_cast<uint32_t*>(W * 4);
+  if (mask == 0xffffffffu) {
+    *dst = val;
+  } else {
+    atomicAnd(dst, ~mask);
+    atomicOr(dst, val);
+  }
+}
+
 }  // namespace
+
+cudaError_t launch_batch_layout(const BatchReq* reqs, uint32_t nreq, uint64_t raw_words_total, uint64_t rev_words_total,
+                                uint32_t* raw_stage, uint32_t* rev, cudaStream_t s, uint32_t* kernels) {
+  const int T = 256;
+  batch_repack_kernel<<<(unsigned)ceil_div(raw_words_total, T), T, 0, s>>>(reqs, nreq, raw_words_total, raw_stage);
+  batch_seed_reverse_kernel<<<(unsigned)ceil_div(rev_words_total, T), T, 0, s>>>(reqs, nreq, rev_words_total, rev);
+  *kernels += 2;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batch_pack(const BatchReq* reqs, uint32_t nreq, uint64_t dst_words_total, const uint32_t* out_stage,
+                              cudaStream_t s, uint32_t* kernels) {
+  const int T = 256;
+  batch_pack_kernel<<<(unsigned)ceil_div(dst_words_total, T), T, 0, s>>>(reqs, nreq, dst_words_total, out_stage);
+  ++*kernels;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_seed_reverse(const uint8_t* seed, uint64_t L, uint32_t* rev, uint64_t rev_words, cudaStream_t s,
                                 uint32_t* kernels) {

@@ -25,27 +25,15 @@ namespace {
 constexpr int kR = 16;           // output words per warp (= outputs per lane)
 constexpr int kWarpsPerCta = 4;
 
+// Parities of the 32R outputs i0 .. i0+32R-1 (i0 = 32 R tile) over raw words [w_begin, w_end) of
+// one block; lane k < R returns output word (R tile + k), unmasked. Warp-uniform arguments.
 template <int R>
-__global__ void __launch_bounds__(32 * kWarpsPerCta) direct_kernel(const DirectArgs a) {
-  const uint32_t lane = threadIdx.x & 31;
-  const uint64_t gwarp = (uint64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
-  const uint64_t total = a.num_blocks * a.tiles * a.splits;
-  if (gwarp >= total) return;  // warp-uniform
-  const uint32_t split = (uint32_t)(gwarp % a.splits);
-  const uint64_t t2 = gwarp / a.splits;
-  const uint32_t tile = (uint32_t)(t2 % a.tiles);
-  const uint64_t blk = t2 / a.tiles;
-
-  const uint32_t w_begin = split * a.words_per_split;
-  uint32_t w_end = w_begin + a.words_per_split;
-  if (w_end > a.nw_t) w_end = a.nw_t;
-
-  const uint32_t* __restrict__ raw = a.raw + blk * a.raw_stride;
-  const uint32_t* __restrict__ seed = a.seed_rev;
-
+__device__ __forceinline__ uint32_t direct_tile(const uint32_t* __restrict__ raw, uint32_t nw_t, uint32_t tail_mask,
+                                                const uint32_t* __restrict__ seed, uint32_t m, uint32_t tile,
+                                                uint32_t w_begin, uint32_t w_end, uint32_t lane) {
   // Padded reversed-seed bit of window (lane, t):  P(t) = c + 32 t, c = m-1-i0-lane + 32*front.
   const int64_t i0 = (int64_t)tile * 32 * R;
-  const int64_t c = (int64_t)a.m - 1 - i0 - (int64_t)lane + 32 * (int64_t)kSeedFrontWords;
+  const int64_t c = (int64_t)m - 1 - i0 - (int64_t)lane + 32 * (int64_t)kSeedFrontWords;
   const uint32_t sh = (uint32_t)(c & 31);
   // word index of window t is (c >> 5) + t
   const int64_t qbase = c >> 5;
@@ -67,7 +55,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) direct_kernel(const DirectA
   win[0] = 0;
   q += R;  // now: word of window w_begin; lo holds seed[q]
 
-  const uint32_t nfull = (a.tail_mask == 0xffffffffu) ? a.nw_t : a.nw_t - 1;  // words needing no mask
+  const uint32_t nfull = (tail_mask == 0xffffffffu) ? nw_t : nw_t - 1;  // words needing no mask
   for (uint32_t base = w_begin; base < w_end; base += R) {
     uint32_t r[R];
     if (base + R <= w_end && base + R <= nfull) {
@@ -78,7 +66,7 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) direct_kernel(const DirectA
       for (int u = 0; u < R; ++u) {
         uint32_t w = base + u;
         uint32_t x = (w < w_end) ? __ldg(raw + w) : 0u;
-        if (w == a.nw_t - 1) x &= a.tail_mask;
+        if (w == nw_t - 1) x &= tail_mask;
         r[u] = x;
       }
     }
@@ -96,28 +84,56 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) direct_kernel(const DirectA
     q += R;
   }
 
-  // Epilogue: parities -> output words (lane k keeps word k of this tile).
+  // parities -> output words (lane k keeps word k of this tile)
   uint32_t myword = 0;
 #pragma unroll
   for (int k = 0; k < R; ++k) {
     uint32_t wrd = __ballot_sync(0xffffffffu, __popc(acc[k]) & 1u);
     if (lane == (uint32_t)k) myword = wrd;
   }
+  return myword;
+}
+
+// Masks output word ow (32 outputs) to m and, for the modified form, XORs in raw bits
+// [id_off + 32 ow, +32) of the block (the identity block I_m).
+__device__ __forceinline__ uint32_t finish_word(uint32_t word, uint32_t ow, uint32_t m, int modified,
+                                                uint32_t id_off, const uint32_t* __restrict__ raw,
+                                                uint64_t raw_words) {
+  const uint32_t rem = m - 32 * ow;
+  const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+  word &= omask;
+  if (modified) {
+    const uint64_t bit = (uint64_t)id_off + 32ull * ow;
+    const uint64_t rq = bit >> 5;
+    const uint32_t rs = (uint32_t)(bit & 31);
+    const uint32_t rlo = __ldg(raw + rq);
+    const uint32_t rhi = (rs && rq + 1 < raw_words) ? __ldg(raw + rq + 1) : 0u;
+    word ^= __funnelshift_r(rlo, rhi, rs) & omask;
+  }
+  return word;
+}
+
+template <int R>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) direct_kernel(const DirectArgs a) {
+  const uint32_t lane = threadIdx.x & 31;
+  const uint64_t gwarp = (uint64_t)blockIdx.x * kWarpsPerCta + (threadIdx.x >> 5);
+  const uint64_t total = a.num_blocks * a.tiles * a.splits;
+  if (gwarp >= total) return;  // warp-uniform
+  const uint32_t split = (uint32_t)(gwarp % a.splits);
+  const uint64_t t2 = gwarp / a.splits;
+  const uint32_t tile = (uint32_t)(t2 % a.tiles);
+  const uint64_t blk = t2 / a.tiles;
+
+  const uint32_t w_begin = split * a.words_per_split;
+  uint32_t w_end = w_begin + a.words_per_split;
+  if (w_end > a.nw_t) w_end = a.nw_t;
+
+  const uint32_t* __restrict__ raw = a.raw + blk * a.raw_stride;
+  uint32_t myword = direct_tile<R>(raw, a.nw_t, a.tail_mask, a.seed_rev, a.m, tile, w_begin, w_end, lane);
   if (lane < (uint32_t)R) {
     const uint32_t ow = tile * R + lane;
     if (ow < a.mw) {
-      const uint32_t rem = a.m - 32 * ow;
-      const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
-      myword &= omask;
-      if (a.modified && split == 0) {
-        // identity block: raw bits [n-m + 32 ow, +32)
-        const uint64_t bit = (uint64_t)a.id_off + 32ull * ow;
-        const uint64_t rq = bit >> 5;
-        const uint32_t rs = (uint32_t)(bit & 31);
-        const uint32_t rlo = __ldg(raw + rq);
-        const uint32_t rhi = (rs && rq + 1 < a.raw_stride) ? __ldg(raw + rq + 1) : 0u;
-        myword ^= __funnelshift_r(rlo, rhi, rs) & omask;
-      }
+      myword = finish_word(myword, ow, a.m, a.modified && split == 0, a.id_off, raw, a.raw_stride);
       uint32_t* dst = a.out + blk * a.out_stride + ow;
       if (a.splits > 1) atomicXor(dst, myword);
       else *dst = myword;
@@ -125,9 +141,65 @@ __global__ void __launch_bounds__(32 * kWarpsPerCta) direct_kernel(const DirectA
   }
 }
 
+// Uneven requests, each with its own seed (one block per request), from one persistent launch:
+// every warp repeatedly takes the next work item (request, output tile, raw-word split) from a
+// global counter; items are numbered with the largest requests first so the tail stays short.
+// Partial parities of the splits of one tile are XOR-combined in the zeroed output staging.
+template <int R>
+__global__ void __launch_bounds__(32 * kWarpsPerCta) batch_direct_kernel(const BatchReq* __restrict__ reqs,
+                                                                          uint32_t nreq, uint64_t total_items,
+                                                                          const uint32_t* __restrict__ raw_stage,
+                                                                          const uint32_t* __restrict__ rev,
+                                                                          uint32_t* __restrict__ out_stage,
+                                                                          unsigned long long* __restrict__ counter) {
+  const uint32_t lane = threadIdx.x & 31;
+  while (true) {
+    unsigned long long item = 0;
+    if (lane == 0) item = atomicAdd(counter, 1ull);
+    item = __shfl_sync(0xffffffffu, item, 0);
+    if (item >= total_items) return;
+    // request r: the last one whose first item is <= item
+    uint32_t lo = 0, hi = nreq - 1;
+    while (lo < hi) {
+      const uint32_t mid = (lo + hi + 1) >> 1;
+      if (reqs[mid].item_begin <= item) lo = mid;
+      else hi = mid - 1;
+    }
+    const BatchReq& q = reqs[lo];
+    const uint64_t local = item - q.item_begin;
+    const uint32_t split = (uint32_t)(local % q.splits);
+    const uint32_t tile = (uint32_t)(local / q.splits);
+    const uint32_t w_begin = split * kBatchWordsPerSplit;
+    const uint32_t w_end = min(w_begin + kBatchWordsPerSplit, q.nw_t);
+    const uint32_t* raw = raw_stage + q.raw_stage_off;
+    uint32_t myword = direct_tile<R>(raw, q.nw_t, q.tail_mask, rev + q.rev_off, q.m, tile, w_begin, w_end, lane);
+    if (lane < (uint32_t)R) {
+      const uint32_t ow = tile * R + lane;
+      if (ow < q.mw) {
+        myword = finish_word(myword, ow, q.m, q.form == QRNG_FORM_MODIFIED && split == 0, q.id_off, raw,
+                             q.raw_words);
+        uint32_t* dst = out_stage + q.out_stage_off + ow;
+        if (q.splits > 1) atomicXor(dst, myword);
+        else *dst = myword;
+      }
+    }
+  }
+}
+
 }  // namespace
 
 int direct_outputs_per_warp() { return 32 * kR; }
+
+cudaError_t launch_batch_direct(const BatchReq* reqs, uint32_t nreq, uint64_t total_items, const uint32_t* raw_stage,
+                                const uint32_t* rev, uint32_t* out_stage, unsigned long long* counter, int num_sms,
+                                cudaStream_t s, uint32_t* kernels) {
+  const uint64_t want = ceil_div(total_items, kWarpsPerCta);
+  const uint64_t cap = (uint64_t)num_sms * 8;  // persistent: a few resident CTAs per SM
+  batch_direct_kernel<kR><<<(unsigned)(want < cap ? want : cap), 32 * kWarpsPerCta, 0, s>>>(
+      reqs, nreq, total_items, raw_stage, rev, out_stage, counter);
+  ++*kernels;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_direct(const DirectArgs& a, cudaStream_t s, uint32_t* kernels) {
   const uint64_t warps = a.num_blocks * a.tiles * a.splits;

@@ -102,6 +102,38 @@ struct DirectArgs {
 int direct_outputs_per_warp();
 cudaError_t launch_direct(const DirectArgs& a, cudaStream_t s, uint32_t* kernels);
 
+// ---- uneven batched requests (k_direct.cu persistent kernel, k_bits.cu layout kernels) ----
+constexpr uint32_t kBatchWordsPerSplit = 2048;  // raw words per work item (a multiple of the tile depth)
+struct BatchReq {
+  // caller's request
+  const uint8_t* raw;
+  uint64_t raw_bit_off;
+  uint64_t n, m;
+  const uint8_t* seed;
+  int form;
+  uint8_t* out;
+  uint64_t out_bit_off;
+  // derived layout
+  uint64_t n_t, L_t;
+  uint32_t nw_t, tail_mask, mw, tiles, splits, id_off;
+  uint64_t raw_words;      // words of the request's staged raw block
+  uint64_t raw_stage_off;  // first word in the raw staging buffer
+  uint64_t rev_off;        // first word of its reversed, padded seed
+  uint64_t rev_words;
+  uint64_t out_stage_off;  // first word in the output staging buffer
+  uint64_t item_begin;     // first work item of the persistent kernel
+  uint64_t dst_word0;      // absolute index of the first 32-bit destination word ((addr*8 + off) / 32)
+  uint64_t dst_begin;      // first destination word in the pack kernel's numbering
+  uint64_t dst_words;
+};
+cudaError_t launch_batch_direct(const BatchReq* reqs, uint32_t nreq, uint64_t total_items, const uint32_t* raw_stage,
+                                const uint32_t* rev, uint32_t* out_stage, unsigned long long* counter, int num_sms,
+                                cudaStream_t s, uint32_t* kernels);
+cudaError_t launch_batch_layout(const BatchReq* reqs, uint32_t nreq, uint64_t raw_words_total, uint64_t rev_words_total,
+                                uint32_t* raw_stage, uint32_t* rev, cudaStream_t s, uint32_t* kernels);
+cudaError_t launch_batch_pack(const BatchReq* reqs, uint32_t nreq, uint64_t dst_words_total, const uint32_t* out_stage,
+                              cudaStream_t s, uint32_t* kernels);
+
 // ---- FFT routes (k_fft.cu) ----
 constexpr uint64_t kFftWorkspaceBytes = 1ull << 31;  // budget for the FP64 ping-pong buffers
 struct FftWorkspace {
@@ -140,6 +172,29 @@ struct qrng_ctx {
   qrng::DevBuf dev_err;  // int error word written by kernels with bounded waits (0 = no error)
   qrng::DevBuf fft_worst;  // double bits of the worst FFT rounding distance since the last reset
   qrng::FftWorkspace fft;
+  // uneven-batch workspace and its captured graphs (see api.cu)
+  qrng::DevBuf batch_meta, batch_raw, batch_rev, batch_out, batch_counter;
+  uint64_t batch_generation = 0;  // bumped whenever a batch buffer moves (invalidates cached graphs)
+  cudaStream_t capture_stream = nullptr;
+  struct BatchGraph {
+    uint64_t key = 0, generation = 0, stamp = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    void* meta_host = nullptr;  // pinned copy of the request table the graph uploads
+  };
+  std::vector<BatchGraph> graphs;
+  uint64_t graph_clock = 0;
+  // autotuner: fastest measured algorithm per shape (n, m, log2 of the block count, form)
+  struct TuneKey {
+    uint64_t n, m;
+    uint32_t log2_blocks;
+    int form;
+    bool operator==(const TuneKey& o) const {
+      return n == o.n && m == o.m && log2_blocks == o.log2_blocks && form == o.form;
+    }
+  };
+  bool autotune = true;
+  std::vector<std::pair<TuneKey, int>> tuned;
   qrng::DevHminResult* result_host = nullptr;  // pinned
   qrng_stats stats{};
   // optional CUDA-event timing of the main extraction kernel

@@ -1,0 +1,139 @@
+"""GPU parity of qrng_extract_batch (uneven requests, one persistent launch in a cached CUDA graph)
+against the oracle. Bar: bit-exact, and every bit outside the requests' output ranges untouched.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import to_dev
+
+pytestmark = pytest.mark.gpu
+
+STD, MOD = 0, 1
+
+
+def _make_batch(count, seed, log2n_lo, log2n_hi, mixed_forms=True):
+    """Requests over one shared raw buffer and one output buffer, packed at odd bit offsets."""
+    n, m, p = W.uneven_requests(count, seed, log2n_lo, log2n_hi)
+    g = W.rng(seed + 1)
+    forms = g.integers(0, 2, count) if mixed_forms else np.zeros(count, dtype=np.int64)
+    m = np.where((forms == MOD) & (m >= n), n - 1, m)
+    raw_offs, seeds, out_offs = [], [], []
+    pos = int(g.integers(0, 8))
+    for i in range(count):
+        raw_offs.append(pos)
+        pos += int(n[i]) + int(g.integers(0, 40))
+    raw_bits = pos + 64
+    # Bernoulli(p_i) raw bits per request, written into one stream
+    stream = np.zeros(raw_bits, dtype=np.uint8)
+    for i in range(count):
+        stream[raw_offs[i]:raw_offs[i] + n[i]] = W.unpack_bits(W.random_bits(int(n[i]), 100 + i, float(p[i])), int(n[i]))
+    raw = W.pack_bits(stream)
+    opos = int(g.integers(0, 8))
+    for i in range(count):
+        L = int(n[i] + m[i] - 1) if forms[i] == STD else int(n[i] - 1)
+        seeds.append(W.random_bits(L, 5000 + i))
+        out_offs.append(opos)
+        opos += int(m[i]) + (int(g.integers(0, 3)) if i % 3 == 0 else 0)  # mostly back to back
+    return n, m, forms, raw, raw_offs, seeds, out_offs, opos
+
+
+def _run(qlib, ctx, batch, sentinel=0x5A):
+    import torch
+
+    n, m, forms, raw, raw_offs, seeds, out_offs, out_bits = batch
+    raw_t, raw_p = to_dev(raw)
+    seed_t = [to_dev(s) for s in seeds]
+    nbytes = (out_bits + 7) // 8 + 8
+    out = torch.full((nbytes,), sentinel, dtype=torch.uint8, device="cuda")
+    reqs = [(raw_p, raw_offs[i], int(n[i]), int(m[i]), seed_t[i][1], int(forms[i]), out.data_ptr(), out_offs[i])
+            for i in range(len(n))]
+    qlib.qrng_extract_batch(ctx, reqs)
+    qlib.qrng_synchronize(ctx)
+    return out.cpu().numpy(), (raw_t, seed_t, out, reqs)
+
+
+def _check(oracle_mod, batch, host, sentinel=0x5A, full_upto=1 << 14):
+    n, m, forms, raw, raw_offs, seeds, out_offs, out_bits = batch
+    got = np.unpackbits(host, bitorder="little")
+    covered = np.zeros(got.size, dtype=bool)
+    for i in range(len(n)):
+        o = out_offs[i]
+        covered[o:o + m[i]] = True
+        k = got[o:o + m[i]]
+        if n[i] <= full_upto:
+            want = W.unpack_bits(oracle_mod.toeplitz(raw, int(n[i]), int(m[i]), seeds[i], int(forms[i]),
+                                                     raw_off=raw_offs[i]), int(m[i]))
+            assert np.array_equal(k, want), f"request {i} (n={n[i]}, m={m[i]}, form={forms[i]})"
+        else:
+            idx = np.unique(np.concatenate([np.arange(32), np.arange(m[i] - 32, m[i]),
+                                            W.rng(i).integers(0, m[i], 96)])).astype(np.uint64)
+            want = oracle_mod.toeplitz_bits(raw, int(n[i]), int(m[i]), seeds[i], int(forms[i]), idx,
+                                            raw_off=raw_offs[i])
+            assert np.array_equal(k[idx.astype(np.int64)], want), f"request {i} (n={n[i]}, m={m[i]})"
+    sent = np.unpackbits(np.full(host.size, sentinel, dtype=np.uint8), bitorder="little")
+    assert np.array_equal(got[~covered], sent[~covered]), "bits outside the requests changed"
+
+
+def test_uneven_small_requests_bit_exact(qlib, gpu, oracle_mod):
+    batch = _make_batch(80, 11, 5, 13)
+    host, _ = _run(qlib, gpu, batch)
+    _check(oracle_mod, batch, host)
+
+
+def test_uneven_requests_log_uniform(qlib, gpu, oracle_mod):
+    """The uneven-request shape (n log-uniform, m/n uniform in [0.5, 0.9], p uniform in
+    [0.45, 0.55]) on a reduced n range the oracle checks quickly."""
+    batch = _make_batch(300, 9, 12, 17)
+    host, _ = _run(qlib, gpu, batch)
+    _check(oracle_mod, batch, host)
+
+
+def test_graph_replay_sees_new_data(qlib, gpu, oracle_mod):
+    """An identical request table replays the cached graph; the kernels read the buffers anew."""
+    import torch
+
+    batch = _make_batch(40, 21, 6, 12)
+    host1, keep = _run(qlib, gpu, batch)
+    _check(oracle_mod, batch, host1)
+    raw_t, seed_t, out, reqs = keep
+    new_raw = W.random_bits(len(batch[3]) * 8, 777)
+    raw_t[:new_raw.size] = torch.from_numpy(new_raw).to("cuda")
+    out.fill_(0x5A)
+    qlib.qrng_extract_batch(gpu, reqs)
+    qlib.qrng_synchronize(gpu)
+    batch2 = batch[:3] + (new_raw,) + batch[4:]
+    _check(oracle_mod, batch2, out.cpu().numpy())
+
+
+def test_batch_matches_single_block_calls(qlib, gpu):
+    """One request per block of a shared-seed stream equals the stream call."""
+    import torch
+
+    n, m, B = 4096, 3000, 24
+    raw = W.random_bits(n * B, 3)
+    seed = W.random_bits(n + m - 1, 4)
+    raw_t, raw_p = to_dev(raw)
+    seed_t, seed_p = to_dev(seed)
+    ref = torch.zeros((m * B + 7) // 8, dtype=torch.uint8, device="cuda")
+    qlib.qrng_toeplitz_extract(gpu, raw_p, n, m, seed_p, STD, qlib.QRNG_ALGO_DIRECT, B, ref)
+    out = torch.zeros_like(ref)
+    qlib.qrng_extract_batch(gpu, [(raw_p, b * n, n, m, seed_p, STD, out.data_ptr(), b * m) for b in range(B)])
+    qlib.qrng_synchronize(gpu)
+    assert torch.equal(out, ref)
+
+
+def test_batch_bad_arguments(qlib, gpu):
+    import torch
+
+    t = torch.zeros(64, dtype=torch.uint8, device="cuda")
+    ok = (t, 0, 64, 32, t, STD, t, 0)
+    with pytest.raises(qlib.QrngError) as e:
+        qlib.qrng_extract_batch(gpu, [ok], algo=qlib.QRNG_ALGO_FFT64)
+    assert e.value.status == qlib.QRNG_ENOTSUP
+    with pytest.raises(qlib.QrngError) as e:
+        qlib.qrng_extract_batch(gpu, [ok, (t, 0, 64, 64, t, MOD, t, 0)])
+    assert e.value.status == qlib.QRNG_EINVAL
+    with pytest.raises(qlib.QrngError) as e:
+        qlib.qrng_extract_batch(gpu, [(0, 0, 64, 32, t, STD, t, 0)])
+    assert e.value.status == qlib.QRNG_EINVAL

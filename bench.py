@@ -40,7 +40,7 @@ ALU_PEAK_TBITMAC = LOP3_PER_CLK_SM * 32 * SMS * SM_MAX_MHZ * 1e6 / 1e12
 def parse():
     p = argparse.ArgumentParser()
     p.add_argument("--gpus", type=int, default=1)
-    p.add_argument("--steps", type=int, default=10)
+    p.add_argument("--steps", type=int, default=30)
     p.add_argument("--warmup", type=int, default=3)
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--algo", default="auto")
@@ -48,6 +48,13 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--blocks", type=int, default=0,
                    help="hash only the first BLOCKS blocks (a smaller case for profiler captures)")
+    p.add_argument("--workload", default="laser", choices=["laser", "single", "sweep", "tc", "uneven"],
+                   help="laser: the headline stream (default); single: one 4096-bit block; sweep: block-length "
+                        "sweep on a 2^30-bit stream; tc: m=6144, n=8192, 4096 blocks; uneven: 10,000 requests")
+    p.add_argument("--sweep-algos", default="direct,gemm_tc,fft64",
+                   help="algorithms timed at each block length of the sweep")
+    p.add_argument("--uneven-max-log2n", type=float, default=22.0,
+                   help="upper end of the log-uniform n range of the uneven requests")
     return p.parse_args()
 
 
@@ -58,8 +65,32 @@ def dist_env():
     return world, rank, local
 
 
+def rank_stream_seed(base: int, rank: int) -> int:
+    """Weak scaling: every rank hashes its own stream of the same size (blocks are independent,
+    Sec. III.E), so ranks only differ in the seed of their synthetic input."""
+    return base + 1000 * rank
+
+
+def reduce_max(value: float, world: int, device) -> float:
+    """Largest value over the ranks (the timing rule: the job takes as long as its slowest rank)."""
+    if world <= 1:
+        return value
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(world: int, bits_per_rank: int, steps: int, t_ms: float) -> float:
+    """Whole-job Gbit/s: output bits of all ranks over the slowest rank's time."""
+    return world * bits_per_rank * steps / (t_ms / 1e3) / 1e9
+
+
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while the timed region runs."""
+    """nvidia-smi clocks and throttle reasons, sampled every 50 ms from before the warm-up until
+    after the timed region; `summary` keeps the samples whose host time falls in the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -68,31 +99,50 @@ class ClockSampler:
     def __init__(self, gpu_index: int):
         self.gpu = gpu_index
         self.proc = None
+        self.samples = []  # (host time, line)
+        self.window = None
 
-    def __enter__(self):
+    def start(self):
+        import threading
+
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits",
-                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+                 "-lms", "50"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True, bufsize=1)
         except OSError:
             self.proc = None
+            return self
+
+        def reader():
+            for line in self.proc.stdout:
+                if line.strip():
+                    self.samples.append((time.time(), line))
+
+        self.thread = threading.Thread(target=reader, daemon=True)
+        self.thread.start()
+        time.sleep(0.3)  # let the first samples arrive before the timed region
         return self
 
-    def __exit__(self, *exc):
-        self.lines = []
+    def mark(self, t0, t1):
+        self.window = (t0, t1)
+
+    def stop(self):
         if self.proc is not None:
+            time.sleep(0.1)
             self.proc.terminate()
             try:
-                out, _ = self.proc.communicate(timeout=5)
+                self.proc.wait(timeout=5)
             except subprocess.TimeoutExpired:
                 self.proc.kill()
-                out, _ = self.proc.communicate()
-            self.lines = [l for l in out.splitlines() if l.strip()]
+            self.thread.join(timeout=5)
 
     def summary(self):
         sm, smax, reasons = [], None, set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in getattr(self, "lines", []):
+        t0, t1 = self.window if self.window else (float("-inf"), float("inf"))
+        for ts, line in self.samples:
+            if not (t0 <= ts <= t1 + 0.06):  # a sample is printed shortly after it is taken
+                continue
             f = [x.strip() for x in line.split(",")]
             if len(f) < 9:
                 continue
@@ -105,7 +155,7 @@ class ClockSampler:
                 if val.lower() == "active":
                     reasons.add(name)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
-                "samples": len(sm)}
+                "samples_in_timed_region": len(sm)}
 
 
 def run_ours(args, world, rank, local):
@@ -127,7 +177,7 @@ def run_ours(args, world, rank, local):
     c = W.CFG2
     n, eps, bits = c["n"], c["eps"], 8
     # weak scaling: every rank owns its own stream of the same size (independent blocks)
-    samples_h = W.adc_samples(c["samples"], c["sample_seed"] + 1000 * rank)
+    samples_h = W.adc_samples(c["samples"], rank_stream_seed(c["sample_seed"], rank))
     samples = torch.from_numpy(samples_h).to(dev)
     seed_h = W.random_bits(2 * n - 1, c["seed_seed"])  # long enough for any m <= n
     seed = torch.from_numpy(seed_h).to(dev)
@@ -150,28 +200,27 @@ def run_ours(args, world, rank, local):
     q.qrng_set_timing(ctx, True)
 
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    clocks = ClockSampler(local).start()
     if world > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
-    with ClockSampler(local) as clocks:
-        for i in range(args.steps):
-            flush.fill_(i & 0xFF)  # evict the 64 MiB input from the 129 MB L2 between steps
-            ev[i][0].record(stream)
-            m = step()
-            ev[i][1].record(stream)
-        torch.cuda.synchronize()
+    t_wall0 = time.time()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)  # evict the 64 MiB input from the 129 MB L2 between steps
+        ev[i][0].record(stream)
+        m = step()
+        ev[i][1].record(stream)
+    torch.cuda.synchronize()
+    clocks.mark(t_wall0, time.time())
+    clocks.stop()
     if world > 1:
         torch.distributed.barrier()
     stats = q.qrng_get_stats(ctx)
     q.qrng_set_timing(ctx, False)
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_total = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([t_total], dtype=torch.float64, device=dev)
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        t_total = float(t.item())
+    t_total = reduce_max(sum(step_ms), world, dev)
     out_bits = num_blocks * m
-    value = world * out_bits * args.steps / (t_total / 1e3) / 1e9
+    value = job_throughput(world, out_bits, args.steps, t_total)
     kernel_ms = stats["timed_ms"] / max(1, stats["timed_launches"])
     used_algo = q.ALGO_NAMES.get(stats["last_algo"], str(stats["last_algo"]))
 
@@ -212,12 +261,8 @@ def run_ours(args, world, rank, local):
             b.synchronize()
             if i >= args.warmup:
                 e_ms.append(a.elapsed_time(b))
-        et = sum(e_ms)
-        if world > 1:
-            t = torch.tensor([et], dtype=torch.float64, device=dev)
-            torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-            et = float(t.item())
-        e2e = {"value": world * nb2 * m2 * len(e_ms) / (et / 1e3) / 1e9, "unit": UNIT,
+        et = reduce_max(sum(e_ms), world, dev)
+        e2e = {"value": job_throughput(world, nb2 * m2, len(e_ms), et), "unit": UNIT,
                "h2d_bytes_per_step": int(samples_h.nbytes + (q.qrng_seed_bits(n, m2, 0) + 7) // 8),
                "d2h_bytes_per_step": int((nb2 * m2 + 7) // 8 + 112), "ms_per_step": et / len(e_ms)}
 
@@ -346,11 +391,167 @@ def run_reference(args, world, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+ALGOS = {"auto": 0, "direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4}
+
+
+def _time_extract(q, ctx, raw, n, m, seed, form, algo, blocks, out, reps, warmup=1):
+    """Mean CUDA-event time (ms) of the main extraction kernel and of the whole call."""
+    import torch
+
+    stream = torch.cuda.current_stream()
+    for _ in range(warmup):
+        q.qrng_toeplitz_extract(ctx, raw, n, m, seed, form, algo, blocks, out, stream=stream)
+    torch.cuda.synchronize()
+    q.qrng_reset_stats(ctx)
+    q.qrng_set_timing(ctx, True)
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        q.qrng_toeplitz_extract(ctx, raw, n, m, seed, form, algo, blocks, out, stream=stream)
+    b.record(stream)
+    b.synchronize()
+    q.qrng_synchronize(ctx)
+    st = q.qrng_get_stats(ctx)
+    q.qrng_set_timing(ctx, False)
+    return st["timed_ms"] / max(1, st["timed_launches"]), a.elapsed_time(b) / reps, st
+
+
+def run_sweep(args):
+    """Block-length sweep (the paper's Fig. 6 question on GB300): a fixed 2^30-bit Bernoulli(0.5)
+    stream, n = 2^10 .. 2^24, m = 0.75 n, modified form, one (n-1)-bit seed per n."""
+    import torch
+
+    import paper_2011_04130_gb300 as q
+
+    torch.cuda.set_device(0)
+    ctx = q.Context(0)
+    c = W.CFG3
+    raw = torch.from_numpy(W.random_bits(c["stream_bits"], c["raw_seed"])).cuda()
+    out = torch.empty(c["stream_bits"] // 8, dtype=torch.uint8, device="cuda")
+    rows = []
+    for n in c["n_list"]:
+        m = int(n * c["ratio"])
+        B = c["stream_bits"] // n
+        seed = torch.from_numpy(W.random_bits(n - 1, c["seed_seed"] + n.bit_length() - 1)).cuda()
+        row = {"n": n, "m": m, "blocks": B}
+        for name in args.sweep_algos.split(","):
+            try:
+                kms, cms, st = _time_extract(q, ctx, raw, n, m, seed, 1, ALGOS[name], B, out, reps=2)
+                row[name] = {"kernel_ms": kms, "call_ms": cms, "gbps": B * m / (cms / 1e3) / 1e9}
+                if name.startswith("fft"):
+                    row[name]["worst_round_err"] = st["worst_fft_round_err"]
+            except q.QrngError as e:
+                row[name] = {"unsupported": str(e)}
+        rows.append(row)
+        print(json.dumps(row), file=sys.stderr)
+    ctx.close()
+    return {"workload": "block-length sweep: 2^30-bit Bernoulli(0.5) stream, n = 2^10..2^24, m = 0.75n, "
+                        "modified form", "unit": UNIT, "data": "synthetic", "rows": rows}
+
+
+def run_tc(args):
+    """One standard seed, m = 6144, n = 8192, 4096 blocks: tensor-core product vs the direct kernel."""
+    import torch
+
+    import paper_2011_04130_gb300 as q
+
+    torch.cuda.set_device(0)
+    ctx = q.Context(0)
+    c = W.CFG4
+    n, m, B = c["n"], c["m"], c["blocks"]
+    raw = torch.from_numpy(W.random_bits(n * B, c["raw_seed"])).cuda()
+    seed = torch.from_numpy(W.random_bits(n + m - 1, c["seed_seed"])).cuda()
+    out = torch.empty(m * B // 8, dtype=torch.uint8, device="cuda")
+    res = {"workload": "m=6144, n=8192, 4096 blocks, one standard seed", "unit": UNIT, "data": "synthetic"}
+    pk = measured_peaks()
+    for name in ("gemm_tc", "direct"):
+        kms, cms, _ = _time_extract(q, ctx, raw, n, m, seed, 0, ALGOS[name], B, out, reps=args.steps)
+        res[name] = {"kernel_ms": kms, "gbps": B * m / (kms / 1e3) / 1e9}
+        if name == "gemm_tc":
+            tf = 2.0 * m * n * B / (kms / 1e3) / 1e12
+            res[name].update({"tflops": tf, "frac_of_fp8": tf / (2 * pk["bf16_tflops"]), "peak_source": pk["source"]})
+    ctx.close()
+    return res
+
+
+def run_single(args):
+    """One 4096-bit block, m = 2048, plus the min-entropy of 65,536 samples: latency."""
+    import torch
+
+    import paper_2011_04130_gb300 as q
+
+    torch.cuda.set_device(0)
+    ctx = q.Context(0)
+    c = W.CFG1
+    samples = torch.from_numpy(W.adc_samples(c["samples"], c["sample_seed"])).cuda()
+    n, m = c["n"], c["m"]
+    raw = torch.from_numpy(W.random_bits(n, c["raw_seed"])).cuda()
+    seed = torch.from_numpy(W.random_bits(n + m - 1, c["seed_seed"])).cuda()
+    out = torch.empty(m // 8, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        q.qrng_minentropy(ctx, samples, bits=8, eps=c["eps"])
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        q.qrng_minentropy(ctx, samples, bits=8, eps=c["eps"])
+    ent_us = (time.perf_counter() - t0) / args.steps * 1e6
+    kms, cms, _ = _time_extract(q, ctx, raw, n, m, seed, 0, ALGOS["direct"], 1, out, reps=args.steps)
+    ctx.close()
+    return {"workload": "65,536 samples + one block n=4096, m=2048", "minentropy_us_host": ent_us,
+            "extract_kernel_us": kms * 1e3, "extract_call_us": cms * 1e3, "gbps": m / (cms / 1e3) / 1e9}
+
+
+def run_uneven(args):
+    """10,000 uneven requests (n log-uniform, m/n uniform in [0.5, 0.9], per-request seeds, raw
+    Bernoulli(p), p uniform in [0.45, 0.55]) in one persistent launch under a CUDA graph."""
+    import torch
+
+    import paper_2011_04130_gb300 as q
+
+    torch.cuda.set_device(0)
+    ctx = q.Context(0)
+    c = W.CFG5
+    n, m, p = W.uneven_requests(c["requests"], c["seed"], c["log2n_lo"], args.uneven_max_log2n, c["rho_lo"],
+                                c["rho_hi"], c["p_lo"], c["p_hi"])
+    raw_off = np.concatenate([[0], np.cumsum(((n + 31) // 32) * 32)[:-1]])
+    total_raw = int(raw_off[-1] + n[-1] + 64)
+    seed_off = np.concatenate([[0], np.cumsum(((n + m + 7) // 8) * 8)[:-1]])  # byte-aligned seeds
+    out_off = np.concatenate([[0], np.cumsum(m)[:-1]])
+    g = W.rng(c["seed"] + 7)
+    raw = torch.empty((total_raw + 7) // 8, dtype=torch.uint8, device="cuda")
+    # raw bits per request are Bernoulli(p_r): fill in chunks of requests to bound host memory
+    for i in range(len(n)):
+        bits = W.random_bits(int(n[i]), 10_000 + i, float(p[i]))
+        raw[raw_off[i] // 8:raw_off[i] // 8 + bits.size] = torch.from_numpy(bits).cuda()
+    seeds = torch.from_numpy(g.integers(0, 256, int(seed_off[-1] + (n[-1] + m[-1] + 7) // 8), dtype=np.uint8)).cuda()
+    out = torch.empty(int((out_off[-1] + m[-1] + 7) // 8 + 8), dtype=torch.uint8, device="cuda")
+    reqs = [(raw.data_ptr(), int(raw_off[i]), int(n[i]), int(m[i]), seeds.data_ptr() + int(seed_off[i]) // 8, 0,
+             out.data_ptr(), int(out_off[i])) for i in range(len(n))]
+    q.qrng_extract_batch(ctx, reqs)  # capture + first run
+    q.qrng_synchronize(ctx)
+    stream = torch.cuda.current_stream()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(max(1, args.steps)):
+        q.qrng_extract_batch(ctx, reqs)  # graph replay
+    b.record(stream)
+    b.synchronize()
+    q.qrng_synchronize(ctx)
+    ms = a.elapsed_time(b) / max(1, args.steps)
+    bitmacs = float(np.sum(m.astype(np.float64) * n))
+    ctx.close()
+    return {"workload": f"{len(n)} uneven requests, n log-uniform in [2^12, 2^{args.uneven_max_log2n:g}], "
+                        "m/n uniform in [0.5, 0.9], per-request seeds", "ms": ms,
+            "output_gbit": float(np.sum(m)) / 1e9, "gbps": float(np.sum(m)) / (ms / 1e3) / 1e9,
+            "tbitmac_per_s": bitmacs / (ms / 1e3) / 1e12, "frac_of_lop3_peak": bitmacs / (ms / 1e3) / 1e12 / ALU_PEAK_TBITMAC}
+
+
 def main():
     args = parse()
     world, rank, local = dist_env()
     if args.impl == "reference":
         res = run_reference(args, world, rank)
+    elif args.workload != "laser":
+        res = {"sweep": run_sweep, "tc": run_tc, "single": run_single, "uneven": run_uneven}[args.workload](args)
     else:
         res = run_ours(args, world, rank, local)
     if rank == 0 and res is not None:

@@ -258,6 +258,15 @@ QRNG_API int qrng_reset_stats(qrng_ctx* ctx);
  * parity, is then not trustworthy). Kernels never trap or hang on such a failure. */
 QRNG_API int qrng_synchronize(qrng_ctx* ctx, qrng_stream_t stream);
 
+/* Failure injection for testing the device-side failure path (no GPU fault involved): arms a
+ * fault for the next tensor-core extraction on this context only.
+ *   QRNG_FAULT_GEMM_NO_TMA  the kernel's loader publishes no raw tile; every wait that depends on
+ *                           it gives up after its bound (about a second), the kernel frees its
+ *                           tensor memory and returns, and qrng_synchronize reports QRNG_ETIMEOUT.
+ * The context stays usable afterwards. */
+enum { QRNG_FAULT_NONE = 0, QRNG_FAULT_GEMM_NO_TMA = 1 };
+QRNG_API int qrng_inject_fault(qrng_ctx* ctx, int fault);
+
 /* Autotuning of QRNG_ALGO_AUTO (on = 1, the default; off = 0 uses the cost model alone and never
  * synchronises). Changing it forgets the shapes tuned so far. */
 QRNG_API int qrng_set_autotune(qrng_ctx* ctx, int on);

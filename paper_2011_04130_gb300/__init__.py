@@ -23,7 +23,8 @@ ALGO_NAMES = {QRNG_ALGO_AUTO: "auto", QRNG_ALGO_DIRECT: "direct", QRNG_ALGO_GEMM
 EXPORTED = ["qrng_create", "qrng_destroy", "qrng_last_error", "qrng_status_string", "qrng_minentropy",
             "qrng_output_length", "qrng_seed_bits", "qrng_toeplitz_extract", "qrng_postprocess_host",
             "qrng_get_stats", "qrng_reset_stats", "qrng_set_timing", "qrng_synchronize",
-            "qrng_minentropy_noalloc", "qrng_extract_batch", "qrng_set_autotune"]
+            "qrng_minentropy_noalloc", "qrng_extract_batch", "qrng_set_autotune", "qrng_inject_fault"]
+QRNG_FAULT_NONE, QRNG_FAULT_GEMM_NO_TMA = 0, 1
 
 
 class QrngError(RuntimeError):
@@ -113,6 +114,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qrng_set_timing.argtypes = [vp, i32]
     lib.qrng_synchronize.argtypes = [vp, vp]
     lib.qrng_set_autotune.argtypes = [vp, i32]
+    lib.qrng_inject_fault.argtypes = [vp, i32]
     lib.qrng_extract_batch.argtypes = [vp, ctypes.POINTER(Request), u64, i32, vp]
     lib.qrng_minentropy_noalloc.argtypes = [vp, u64, i32, dbl, ctypes.POINTER(HminReport), vp]
     _lib = lib
@@ -290,3 +292,7 @@ def qrng_extract_batch(ctx: Context, requests, algo: int = QRNG_ALGO_AUTO, strea
 
 def qrng_set_autotune(ctx: Context, on: bool):
     ctx.check(load_library().qrng_set_autotune(ctx.handle, 1 if on else 0), "qrng_set_autotune")
+
+
+def qrng_inject_fault(ctx: Context, fault: int):
+    ctx.check(load_library().qrng_inject_fault(ctx.handle, fault), "qrng_inject_fault")

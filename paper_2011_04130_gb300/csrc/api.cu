@@ -136,7 +136,10 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
   if (algo == QRNG_ALGO_GEMM_TC) {
     QRNG_CUDA(ctx, ctx->dev_err.ensure(sizeof(int)), "error word");
     LaunchTimer timer(ctx, s);
-    QRNG_CUDA(ctx, launch_gemm_tc(a, ctx->dev_err.as<int>(), ctx->num_sms, s, kernels), "tensor-core extraction kernel");
+    const int fault = ctx->fault;
+    ctx->fault = 0;  // one-shot
+    QRNG_CUDA(ctx, launch_gemm_tc(a, ctx->dev_err.as<int>(), fault, ctx->num_sms, s, kernels),
+              "tensor-core extraction kernel");
     timer.done();
     if (!out_direct)
       QRNG_CUDA(ctx, launch_pack_blocks(out_w, mw, m, num_blocks, out, s, kernels), "output pack");
@@ -719,6 +722,12 @@ int qrng_synchronize(qrng_ctx* ctx, qrng_stream_t stream) {
   if (w >= kFftRoundGuard)
     return fail(ctx, QRNG_EPRECISION,
                 "an FFT convolution sum was " + std::to_string(w) + " away from an integer; its parity is unreliable");
+  return QRNG_OK;
+}
+
+int qrng_inject_fault(qrng_ctx* ctx, int fault) {
+  if (!ctx || (fault != QRNG_FAULT_NONE && fault != QRNG_FAULT_GEMM_NO_TMA)) return QRNG_EINVAL;
+  ctx->fault = fault;
   return QRNG_OK;
 }
 

@@ -184,6 +184,7 @@ struct GemmArgs {
   uint32_t ntiles;
   uint32_t ksteps;
   int* err;
+  int fault_no_tma;  // test hook: the loader publishes no raw tile, so every consumer's bounded wait runs out
 };
 
 __global__ void __launch_bounds__(THREADS, 1)
@@ -285,9 +286,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t nt = (uint32_t)(tile / a.mtiles);
         for (uint32_t ks = 0; ks < a.ksteps; ++ks) {
           if (!mbar_wait(&pk_empty_bar[pstage], pphase ^ 1u, &abort_flag, a.err, 3)) break;
-          mbar_arrive_expect_tx(&pk_full_bar[pstage], PK_BYTES);
-          tma_load_2d(pk_base + pstage * PK_BYTES, &raw_map, (int)(4 * ks), (int)(nt * BN), &pk_full_bar[pstage]);
-          ++issued;
+          if (!a.fault_no_tma) {
+            mbar_arrive_expect_tx(&pk_full_bar[pstage], PK_BYTES);
+            tma_load_2d(pk_base + pstage * PK_BYTES, &raw_map, (int)(4 * ks), (int)(nt * BN), &pk_full_bar[pstage]);
+            ++issued;
+          }
           if (++pstage == PK_STAGES) { pstage = 0; pphase ^= 1u; }
         }
       }
@@ -411,7 +414,7 @@ bool gemm_tc_layout_ok(const DirectArgs& d) {
   return (reinterpret_cast<uintptr_t>(d.raw) & 15) == 0 && (d.raw_stride % 4) == 0;
 }
 
-cudaError_t launch_gemm_tc(const DirectArgs& d, int* err, int num_sms, cudaStream_t s, uint32_t* kernels) {
+cudaError_t launch_gemm_tc(const DirectArgs& d, int* err, int fault, int num_sms, cudaStream_t s, uint32_t* kernels) {
   if (!gemm_tc_layout_ok(d)) return cudaErrorInvalidValue;
   GemmArgs a{};
   a.raw = d.raw;
@@ -430,6 +433,7 @@ cudaError_t launch_gemm_tc(const DirectArgs& d, int* err, int num_sms, cudaStrea
   a.ntiles = (uint32_t)ceil_div(d.num_blocks, BN);
   a.ksteps = (uint32_t)ceil_div((uint64_t)d.nw_t * 32, BK);
   a.err = err;
+  a.fault_no_tma = (fault == QRNG_FAULT_GEMM_NO_TMA);
 
   // Tensor map over the raw words: dim 0 = the Toeplitz part's words of a block (reads beyond it
   // are zero-filled), dim 1 = blocks (rows past the last block are zero-filled); box 4 x 256.

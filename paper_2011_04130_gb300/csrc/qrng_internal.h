@@ -160,7 +160,7 @@ cudaError_t launch_fft32_seg(const DirectArgs& a, const uint8_t* seed, uint64_t 
 // Same layout arguments as the direct kernel (splits unused). Exact for n_t <= kGemmMaxColumns.
 constexpr uint64_t kGemmMaxColumns = 1ull << 22;
 size_t gemm_tc_smem_bytes();
-cudaError_t launch_gemm_tc(const DirectArgs& a, int* err, int num_sms, cudaStream_t s, uint32_t* kernels);
+cudaError_t launch_gemm_tc(const DirectArgs& a, int* err, int fault, int num_sms, cudaStream_t s, uint32_t* kernels);
 
 }  // namespace qrng
 
@@ -194,6 +194,7 @@ struct qrng_ctx {
     }
   };
   bool autotune = true;
+  int fault = 0;  // QRNG_FAULT_* armed for the next tensor-core extraction only
   std::vector<std::pair<TuneKey, int>> tuned;
   qrng::DevHminResult* result_host = nullptr;  // pinned
   qrng_stats stats{};

@@ -139,6 +139,26 @@ def test_fft64_block_length_sweep_point(qlib, gpu, oracle_mod, log2n):
     spot_check(oracle_mod, raw, n, m, seed, MOD, got, blocks=[0, B - 1], per_block=128)
 
 
+def test_auto_tunes_once_per_shape(qlib, gpu, oracle_mod):
+    """AUTO runs the candidates once for a new shape, keeps the fastest, and reuses it."""
+    n, m, B = 8192, 6144, 512
+    raw, seed = _case(n, m, STD, B, 77)
+    want = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_DIRECT, B)
+    qlib.qrng_set_autotune(gpu, True)
+    qlib.qrng_reset_stats(gpu)
+    got1 = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_AUTO, B)
+    first = qlib.qrng_get_stats(gpu)
+    got2 = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_AUTO, B)
+    second = qlib.qrng_get_stats(gpu)
+    assert np.array_equal(got1, want) and np.array_equal(got2, want)
+    assert second["last_algo"] == first["last_algo"] != qlib.QRNG_ALGO_AUTO
+    assert second["last_kernels"] <= first["last_kernels"]  # no candidates re-run
+    qlib.qrng_set_autotune(gpu, False)
+    got3 = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_AUTO, B)
+    assert np.array_equal(got3, want)
+    qlib.qrng_set_autotune(gpu, True)
+
+
 def test_gemm_rejects_too_long_blocks(qlib, gpu):
     import torch
 

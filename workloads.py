@@ -35,17 +35,21 @@ def adc_samples(count: int, seed: int, mu: float = 128.0, sigma: float = 16.0, b
 
 
 def random_bits(nbits: int, seed: int, p: float = 0.5) -> np.ndarray:
-    """nbits Bernoulli(p) bits packed LSB-first into ceil(nbits/8) bytes; pad bits are zero."""
+    """nbits Bernoulli(p) bits packed LSB-first into ceil(nbits/8) bytes; pad bits are zero
+    (p is resolved to a multiple of 2^-16)."""
     g = rng(seed)
     nbytes = (nbits + 7) // 8
     if p == 0.5:
         out = g.integers(0, 256, size=nbytes, dtype=np.uint8)
     else:
+        # P(bit = 1) = round(p * 2^16) / 2^16
+        thr = int(round(p * 65536))
         out = np.empty(nbytes, dtype=np.uint8)
         chunk = 1 << 26
         for s in range(0, nbits, chunk):
             e = min(nbits, s + chunk)
-            out[s // 8:(e + 7) // 8] = np.packbits(g.random(e - s) < p, bitorder="little")
+            out[s // 8:(e + 7) // 8] = np.packbits(g.integers(0, 65536, e - s, dtype=np.uint16) < thr,
+                                                   bitorder="little")
     if nbits % 8:
         out[-1] &= (1 << (nbits % 8)) - 1
     return out

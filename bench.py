@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--workload", default="laser", choices=["laser", "single", "sweep", "tc", "uneven"],
                    help="laser: the headline stream (default); single: one 4096-bit block; sweep: block-length "
                         "sweep on a 2^30-bit stream; tc: m=6144, n=8192, 4096 blocks; uneven: 10,000 requests")
-    p.add_argument("--sweep-algos", default="direct,gemm_tc,fft64",
+    p.add_argument("--sweep-algos", default="direct,gemm_tc,ntt,fft64",
                    help="algorithms timed at each block length of the sweep")
     p.add_argument("--uneven-max-log2n", type=float, default=22.0,
                    help="upper end of the log-uniform n range of the uneven requests")
@@ -171,8 +171,7 @@ def run_ours(args, world, rank, local):
         dist.init_process_group("nccl", device_id=dev)
     stream = torch.cuda.current_stream()
     ctx = q.Context(local)
-    algo = {"auto": q.QRNG_ALGO_AUTO, "direct": q.QRNG_ALGO_DIRECT, "gemm_tc": q.QRNG_ALGO_GEMM_TC,
-            "fft64": q.QRNG_ALGO_FFT64, "fft32_seg": q.QRNG_ALGO_FFT32_SEG}[args.algo]
+    algo = ALGOS[args.algo]
 
     c = W.CFG2
     n, eps, bits = c["n"], c["eps"], 8
@@ -391,7 +390,7 @@ def run_reference(args, world, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-ALGOS = {"auto": 0, "direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4}
+ALGOS = {"auto": 0, "direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4, "ntt": 5}
 
 
 def _time_extract(q, ctx, raw, n, m, seed, form, algo, blocks, out, reps, warmup=1):

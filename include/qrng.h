@@ -154,8 +154,11 @@ enum {
   QRNG_ALGO_DIRECT = 1,   /* bit-packed AND/XOR + parity, each block on its own (Sec. III.B, O(mn)) */
   QRNG_ALGO_GEMM_TC = 2,  /* all blocks as one GF(2) matrix product T X on tcgen05 tensor cores   */
   QRNG_ALGO_FFT64 = 3,    /* circulant embedding + FP64 FFT convolution per block (Sec. III.B-D) */
-  QRNG_ALGO_FFT32_SEG = 4 /* FP32 FFT over short segments with a proven rounding bound, parities
+  QRNG_ALGO_FFT32_SEG = 4,/* FP32 FFT over short segments with a proven rounding bound, parities
                              of the segments XOR-combined                                          */
+  QRNG_ALGO_NTT = 5       /* the circulant convolution of Sec. III.B with a number-theoretic
+                             transform mod 2013265921 (exact integers, integer pipes); lengths up
+                             to 2^27                                                                */
 };
 
 /* Seed length in bits: n+m-1 (standard) or n-1 (modified); 0 for an invalid shape. */

@@ -76,7 +76,7 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
                     int form, uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels) {
   const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
   const uint64_t L_t = n_t + m - 1;
-  const bool fft = (algo == QRNG_ALGO_FFT64 || algo == QRNG_ALGO_FFT32_SEG);
+  const bool fft = (algo == QRNG_ALGO_FFT64 || algo == QRNG_ALGO_FFT32_SEG || algo == QRNG_ALGO_NTT);
 
   if (!fft) {  // the bit-packed kernels read Toeplitz rows as windows of the reversed seed
     const uint64_t rev_words = kSeedFrontWords + ceil_div(L_t, 32) + kSeedBackWords;
@@ -126,9 +126,12 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
     ctx->fft.worst = ctx->fft_worst.as<unsigned long long>();
     LaunchTimer timer(ctx, s);
     const cudaError_t e = algo == QRNG_ALGO_FFT64 ? launch_fft64(a, seed, L_t, ctx->fft, s, kernels)
+                          : algo == QRNG_ALGO_NTT ? launch_ntt(a, seed, L_t, ctx->fft, s, kernels)
                                                   : launch_fft32_seg(a, seed, L_t, ctx->fft, s, kernels);
     timer.done();
-    QRNG_CUDA(ctx, e, algo == QRNG_ALGO_FFT64 ? "FP64 FFT extraction" : "FP32 segmented FFT extraction");
+    QRNG_CUDA(ctx, e, algo == QRNG_ALGO_FFT64 ? "FP64 FFT extraction"
+                      : algo == QRNG_ALGO_NTT ? "number-theoretic transform extraction"
+                                              : "FP32 segmented FFT extraction");
     if (!out_direct)
       QRNG_CUDA(ctx, launch_pack_blocks(out_w, mw, m, num_blocks, out, s, kernels), "output pack");
     return QRNG_OK;
@@ -211,7 +214,7 @@ int check_extract_args(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m
                 "qrng_toeplitz_extract: need 1 <= m <= n (standard) or 1 <= m < n (modified), n <= 2^26");
   if (num_blocks == 0) return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: num_blocks must be >= 1");
   if (num_blocks > (1ull << 62) / n) return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: stream too long");
-  if (algo < QRNG_ALGO_AUTO || algo > QRNG_ALGO_FFT32_SEG)
+  if (algo < QRNG_ALGO_AUTO || algo > QRNG_ALGO_NTT)
     return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: unknown algorithm");
   return QRNG_OK;
 }
@@ -231,6 +234,10 @@ double model_seconds(int algo, uint64_t n_t, uint64_t m, uint64_t B) {
       const double P = (double)fft64_length(n_t, m), lg = log2(P), pairs = (double)ceil_div(B, 2);
       return pairs * (10.0 * P * lg / 6e11 + 64.0 * P * lg / 6e12) + 2.0 * lg * 4e-6;
     }
+    case QRNG_ALGO_NTT: {
+      const double P = (double)fft64_length(n_t, m), lg = log2(P);
+      return (double)B * (16.0 * P * lg / 6e12 + 12.0 * P * lg / 1.5e13) + 2.0 * lg * 4e-6;
+    }
     case QRNG_ALGO_FFT32_SEG: {
       const double S = (double)fft32_segment(), N = 2 * S;
       const double pairs = (double)B * (double)ceil_div(m, (uint64_t)S) * ceil((double)ceil_div(n_t, (uint64_t)S) / 2);
@@ -247,6 +254,7 @@ bool algo_applicable(int algo, uint64_t n_t, uint64_t m, uint64_t B) {
     case QRNG_ALGO_GEMM_TC:
       return n_t <= kGemmMaxColumns;
     case QRNG_ALGO_FFT64:
+    case QRNG_ALGO_NTT:
       return fft64_length(n_t, m) <= (1ull << 27);
     case QRNG_ALGO_FFT32_SEG:
       return true;
@@ -265,7 +273,7 @@ int extract_one(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uint64_
 int choose_auto(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
                 uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels, int* chosen, bool* done) {
   const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
-  const int algos[4] = {QRNG_ALGO_DIRECT, QRNG_ALGO_GEMM_TC, QRNG_ALGO_FFT64, QRNG_ALGO_FFT32_SEG};
+  const int algos[5] = {QRNG_ALGO_DIRECT, QRNG_ALGO_GEMM_TC, QRNG_ALGO_NTT, QRNG_ALGO_FFT64, QRNG_ALGO_FFT32_SEG};
   double best_model = 1e30;
   int best_algo = QRNG_ALGO_DIRECT;
   for (int a : algos)
@@ -336,6 +344,11 @@ int extract_dispatch(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, 
       break;
     case QRNG_ALGO_FFT64:
     case QRNG_ALGO_FFT32_SEG:
+      st = extract_bitwise(ctx, used, raw, n, m, seed, form, num_blocks, out, s, &kernels);
+      break;
+    case QRNG_ALGO_NTT:
+      if (fft64_length(n_t, m) > (1ull << 27))
+        return fail(ctx, QRNG_ENOTSUP, "qrng_toeplitz_extract: the transform length exceeds 2^27");
       st = extract_bitwise(ctx, used, raw, n, m, seed, form, num_blocks, out, s, &kernels);
       break;
     case QRNG_ALGO_GEMM_TC:

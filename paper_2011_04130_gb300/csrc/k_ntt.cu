@@ -1,0 +1,238 @@
+// Exact convolution route to the Toeplitz hash with a number-theoretic transform.
+//
+// Same embedding as the paper's FFT route (Sec. III.B Thm. 1-2, Sec. III.D): the Toeplitz part of
+// k is the slice c[n_t - 1 + i] of the linear convolution c = a * r, taken from a cyclic
+// convolution of length P >= n_t + m - 1 and computed as F^-1(F a . F r). Here F is the discrete
+// Fourier transform over the prime field Z_p, p = 15 * 2^27 + 1 (2013265921), whose multiplicative
+// group has elements of every order 2^k, k <= 27. Every entry of c is an integer <= n_t < p, so the
+// field result IS the integer: there is no rounding to guard, and the transform runs on the integer
+// pipes (FP64 is the slowest unit of the GB300).
+//
+// Arithmetic: elements in [0, p); twiddles in Montgomery form (w 2^32 mod p) so that one Montgomery
+// product w (*) x = w x mod p returns ordinary residues. Radix-2 Stockham passes over global
+// memory, one launch per pass over a chunk of blocks (the same schedule as the FP64 route, with
+// 4-byte elements instead of 16).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qrng_internal.h"
+
+namespace qrng {
+namespace {
+
+constexpr uint32_t kP = 2013265921u;        // 15 * 2^27 + 1
+constexpr uint32_t kPinvNeg = 2013265919u;  // -p^-1 mod 2^32
+constexpr uint32_t kGen = 31u;              // a generator of Z_p^*
+
+__host__ __device__ __forceinline__ uint32_t add_mod(uint32_t a, uint32_t b) {
+  const uint32_t s = a + b;  // < 2p < 2^32
+  return s >= kP ? s - kP : s;
+}
+
+__host__ __device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b) { return a >= b ? a - b : a + kP - b; }
+
+// Montgomery product a b 2^-32 mod p, for a, b < p.
+__host__ __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b) {
+  const uint64_t t = (uint64_t)a * b;
+  const uint32_t q = (uint32_t)t * kPinvNeg;
+  const uint64_t u = (t + (uint64_t)q * kP) >> 32;  // < 2p
+  return u >= kP ? (uint32_t)(u - kP) : (uint32_t)u;
+}
+
+uint32_t pow_mod(uint64_t b, uint64_t e) {
+  uint64_t r = 1;
+  b %= kP;
+  while (e) {
+    if (e & 1) r = r * b % kP;
+    b = b * b % kP;
+    e >>= 1;
+  }
+  return (uint32_t)r;
+}
+
+uint32_t to_mont(uint32_t x) { return (uint32_t)(((uint64_t)x << 32) % kP); }
+
+// tw[q] = omega^q in Montgomery form, q < P/2, omega a primitive P-th root of unity.
+__global__ void ntt_twiddle_kernel(uint32_t* __restrict__ tw, uint64_t half, uint32_t omega_m, uint32_t one_m,
+                                   uint32_t step_m) {
+  // thread j fills tw[j*S .. (j+1)*S) by repeated multiplication from omega^(jS)
+  const uint64_t S = 256;
+  const uint64_t j = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (j * S >= half) return;
+  // omega^(jS): square-and-multiply in Montgomery form
+  uint32_t base = step_m, acc = one_m;
+  uint64_t e = j;
+  while (e) {
+    if (e & 1) acc = mont_mul(acc, base);
+    base = mont_mul(base, base);
+    e >>= 1;
+  }
+  for (uint64_t q = j * S; q < (j + 1) * S && q < half; ++q) {
+    tw[q] = acc;
+    acc = mont_mul(acc, omega_m);
+  }
+}
+
+// One radix-2 Stockham pass (see the FP64 route): y[g 2L + k] = x[j] + w x[j+P/2],
+// y[g 2L + k + L] = x[j] - w x[j+P/2], w = omega^(+-k P/(2L)); the inverse uses
+// omega^-q = -omega^(P/2 - q).
+__global__ void ntt_pass_kernel(const uint32_t* __restrict__ x, uint32_t* __restrict__ y,
+                                const uint32_t* __restrict__ tw, uint64_t P, uint32_t logL, uint32_t logP, int inverse,
+                                uint64_t total) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const uint64_t half = P >> 1;
+  const uint64_t b = idx >> (logP - 1);
+  const uint64_t j = idx & (half - 1);
+  const uint64_t L = 1ull << logL;
+  const uint64_t k = j & (L - 1);
+  const uint64_t g = j >> logL;
+  const uint64_t q = k << (logP - 1 - logL);
+  uint32_t w;
+  if (!inverse || q == 0) w = tw[q];
+  else w = kP - tw[half - q];
+  const uint32_t* xb = x + b * P;
+  uint32_t* yb = y + b * P;
+  const uint32_t a = xb[j];
+  const uint32_t t = mont_mul(w, xb[j + half]);
+  yb[(g << (logL + 1)) + k] = add_mod(a, t);
+  yb[(g << (logL + 1)) + k + L] = sub_mod(a, t);
+}
+
+__global__ void ntt_seed_kernel(const uint8_t* __restrict__ seed, uint64_t L, uint32_t* __restrict__ z, uint64_t P) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P) return;
+  z[t] = t < L ? (uint32_t)((seed[t >> 3] >> (t & 7)) & 1u) : 0u;
+}
+
+// Seed spectrum A -> A P^-1 2^32 mod p, so that one Montgomery product with a block's spectrum
+// yields (A . R) / P, the spectrum of the convolution with the inverse transform's 1/P folded in.
+__global__ void ntt_scale_kernel(uint32_t* __restrict__ z, uint64_t P, uint32_t factor_m) {
+  const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= P) return;
+  z[t] = mont_mul(z[t], factor_m);
+}
+
+__global__ void ntt_pack_kernel(const uint32_t* __restrict__ raw, uint64_t stride, uint64_t n_t, uint64_t num_blocks,
+                                uint64_t b0, uint64_t nb, uint32_t* __restrict__ z, uint64_t P) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nb * P) return;
+  const uint64_t bl = idx / P, t = idx - bl * P;
+  const uint64_t b = b0 + bl;
+  z[idx] = (t < n_t && b < num_blocks) ? ((raw[b * stride + (t >> 5)] >> (t & 31)) & 1u) : 0u;
+}
+
+__global__ void ntt_mul_kernel(uint32_t* __restrict__ z, const uint32_t* __restrict__ A, uint64_t P, uint64_t total) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  z[idx] = mont_mul(z[idx], A[idx & (P - 1)]);
+}
+
+// Output word w of block b0+bl: parities of c[n_t - 1 + i] (exact integers), identity bits.
+__global__ void ntt_extract_kernel(const uint32_t* __restrict__ z, uint64_t P, uint64_t n_t, uint64_t m, uint64_t mw,
+                                   const uint32_t* __restrict__ raw, uint64_t stride, int modified, uint64_t id_off,
+                                   uint64_t num_blocks, uint64_t b0, uint64_t nb, uint32_t* __restrict__ out,
+                                   uint64_t out_stride) {
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  if (gw >= nb * mw) return;
+  const uint64_t bl = gw / mw, w = gw - bl * mw;
+  const uint64_t b = b0 + bl;
+  const uint64_t i = 32 * w + lane;
+  const uint32_t bit = (i < m) ? (z[bl * P + n_t - 1 + i] & 1u) : 0u;
+  uint32_t word = __ballot_sync(0xffffffffu, bit);
+  if (lane == 0 && b < num_blocks) {
+    const uint64_t rem = m - 32 * w;
+    const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+    word &= omask;
+    if (modified) {
+      const uint32_t* rr = raw + b * stride;
+      const uint64_t pos = id_off + 32 * w;
+      const uint64_t rq = pos >> 5;
+      const uint32_t rs = (uint32_t)(pos & 31);
+      const uint32_t lo = rr[rq];
+      const uint32_t hi = (rs && rq + 1 < stride) ? rr[rq + 1] : 0u;
+      word ^= __funnelshift_r(lo, hi, rs) & omask;
+    }
+    out[b * out_stride + w] = word;
+  }
+}
+
+inline unsigned grid_for(uint64_t total, int threads) { return (unsigned)ceil_div(total, (uint64_t)threads); }
+
+cudaError_t run_ntt(uint32_t* a, uint32_t* b, const uint32_t* tw, uint64_t P, uint32_t logP, uint64_t batch,
+                    int inverse, cudaStream_t s, uint32_t* kernels, uint32_t** result) {
+  const uint64_t total = batch * (P >> 1);
+  uint32_t* x = a;
+  uint32_t* y = b;
+  for (uint32_t logL = 0; logL < logP; ++logL) {
+    ntt_pass_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total);
+    ++*kernels;
+    uint32_t* t = x;
+    x = y;
+    y = t;
+  }
+  *result = x;
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+cudaError_t launch_ntt(const DirectArgs& d, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
+                       uint32_t* kernels) {
+  const uint64_t n_t = d.n_t;
+  const uint64_t P = fft64_length(n_t, d.m);
+  if (P > (1ull << 27)) return cudaErrorInvalidValue;
+  uint32_t logP = 0;
+  while ((1ull << logP) < P) ++logP;
+  cudaError_t e;
+  if (ws.ntt_P != P) {
+    if ((e = ws.ntt_tw.ensure((P / 2) * sizeof(uint32_t))) != cudaSuccess) return e;
+    const uint32_t omega = pow_mod(kGen, (kP - 1) / P);  // primitive P-th root of unity
+    const uint32_t omega_m = to_mont(omega);
+    const uint32_t step_m = to_mont(pow_mod(omega, 256));
+    ntt_twiddle_kernel<<<grid_for(ceil_div(P / 2, 256), 128), 128, 0, s>>>(ws.ntt_tw.as<uint32_t>(), P / 2, omega_m,
+                                                                          to_mont(1), step_m);
+    ++*kernels;
+    ws.ntt_P = P;
+  }
+  uint64_t chunk = kFftWorkspaceBytes / (2 * P * sizeof(uint32_t));
+  if (chunk < 1) chunk = 1;
+  if (chunk > d.num_blocks) chunk = d.num_blocks;
+  if ((e = ws.buf0.ensure(chunk * P * sizeof(uint32_t))) != cudaSuccess) return e;
+  if ((e = ws.buf1.ensure(chunk * P * sizeof(uint32_t))) != cudaSuccess) return e;
+  if ((e = ws.spec.ensure(P * sizeof(uint32_t))) != cudaSuccess) return e;
+  uint32_t* b0p = ws.buf0.as<uint32_t>();
+  uint32_t* b1p = ws.buf1.as<uint32_t>();
+
+  // seed spectrum, scaled by P^-1 and kept in Montgomery form
+  uint32_t* res = nullptr;
+  ntt_seed_kernel<<<grid_for(P, 256), 256, 0, s>>>(seed, L_t, b0p, P);
+  ++*kernels;
+  if ((e = run_ntt(b0p, b1p, ws.ntt_tw.as<uint32_t>(), P, logP, 1, 0, s, kernels, &res)) != cudaSuccess) return e;
+  const uint32_t pinv = pow_mod(P % kP, kP - 2);
+  const uint32_t factor_m = to_mont(to_mont(pinv));  // P^-1 2^64 mod p: one product leaves P^-1 2^32
+  ntt_scale_kernel<<<grid_for(P, 256), 256, 0, s>>>(res, P, factor_m);
+  ++*kernels;
+  if ((e = cudaMemcpyAsync(ws.spec.p, res, P * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
+
+  for (uint64_t bb = 0; bb < d.num_blocks; bb += chunk) {
+    const uint64_t nb = (d.num_blocks - bb) < chunk ? (d.num_blocks - bb) : chunk;
+    ntt_pack_kernel<<<grid_for(nb * P, 256), 256, 0, s>>>(d.raw, d.raw_stride, n_t, d.num_blocks, bb, nb, b0p, P);
+    ++*kernels;
+    if ((e = run_ntt(b0p, b1p, ws.ntt_tw.as<uint32_t>(), P, logP, nb, 0, s, kernels, &res)) != cudaSuccess) return e;
+    ntt_mul_kernel<<<grid_for(nb * P, 256), 256, 0, s>>>(res, ws.spec.as<uint32_t>(), P, nb * P);
+    ++*kernels;
+    uint32_t* other = (res == b0p) ? b1p : b0p;
+    uint32_t* fin = nullptr;
+    if ((e = run_ntt(res, other, ws.ntt_tw.as<uint32_t>(), P, logP, nb, 1, s, kernels, &fin)) != cudaSuccess)
+      return e;
+    ntt_extract_kernel<<<grid_for(nb * d.mw * 32, 256), 256, 0, s>>>(fin, P, n_t, d.m, d.mw, d.raw, d.raw_stride,
+                                                                     d.modified, d.id_off, d.num_blocks, bb, nb,
+                                                                     d.out, d.out_stride);
+    ++*kernels;
+  }
+  return cudaGetLastError();
+}
+
+}  // namespace qrng

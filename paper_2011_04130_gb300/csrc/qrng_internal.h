@@ -137,8 +137,9 @@ cudaError_t launch_batch_pack(const BatchReq* reqs, uint32_t nreq, uint64_t dst_
 // ---- FFT routes (k_fft.cu) ----
 constexpr uint64_t kFftWorkspaceBytes = 1ull << 31;  // budget for the FP64 ping-pong buffers
 struct FftWorkspace {
-  DevBuf buf0, buf1, spec, tw, tw32;
+  DevBuf buf0, buf1, spec, tw, tw32, ntt_tw;
   uint64_t tw_P = 0;                    // length the FP64 twiddle table holds
+  uint64_t ntt_P = 0;                   // length the number-theoretic twiddle table holds
   unsigned long long* worst = nullptr;  // device: bits of the largest |s - round(s)| (a double)
   void release() {
     buf0.release();
@@ -146,13 +147,17 @@ struct FftWorkspace {
     spec.release();
     tw.release();
     tw32.release();
+    ntt_tw.release();
     tw_P = 0;
+    ntt_P = 0;
   }
 };
 uint64_t fft64_length(uint64_t n_t, uint64_t m);
 uint64_t fft32_segment();
 cudaError_t launch_fft64(const DirectArgs& a, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
                          uint32_t* kernels);
+cudaError_t launch_ntt(const DirectArgs& a, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
+                       uint32_t* kernels);
 cudaError_t launch_fft32_seg(const DirectArgs& a, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
                              uint32_t* kernels);
 

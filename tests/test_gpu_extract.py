@@ -14,7 +14,7 @@ from gpu_util import extract, spot_check
 pytestmark = pytest.mark.gpu
 
 STD, MOD = 0, 1
-ALGOS = {"direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4}
+ALGOS = {"direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4, "ntt": 5}
 
 
 def _seed_len(n, m, form):
@@ -122,6 +122,21 @@ def test_fft_rounding_evidence(qlib, gpu, oracle_mod, algo, bound):
     st = qlib.qrng_get_stats(gpu)
     assert 0.0 < st["worst_fft_round_err"] < bound, st
     assert not oracle_mod.freivalds(raw, n, m, seed, STD, B, got).any()
+
+
+@pytest.mark.parametrize("log2n", [12, 18, 24])
+def test_ntt_block_length_sweep_point(qlib, gpu, oracle_mod, log2n):
+    """The exact number-theoretic route on the fixed 2^30-bit stream, modified form, m = 0.75 n."""
+    c = W.CFG3
+    n = 1 << log2n
+    m = int(n * c["ratio"])
+    B = c["stream_bits"] // n
+    raw = W.random_bits(c["stream_bits"], c["raw_seed"])
+    seed = W.random_bits(n - 1, c["seed_seed"] + log2n)
+    got = extract(qlib, gpu, raw, n, m, seed, MOD, qlib.QRNG_ALGO_NTT, B)
+    ref = extract(qlib, gpu, raw, n, m, seed, MOD, qlib.QRNG_ALGO_FFT64, B)
+    assert np.array_equal(got, ref)
+    spot_check(oracle_mod, raw, n, m, seed, MOD, got, blocks=[0, B - 1], per_block=128)
 
 
 @pytest.mark.parametrize("log2n", [12, 16, 20])
@@ -236,6 +251,7 @@ def test_bad_arguments(qlib, gpu):
         (0, 0, STD, 1, 1),
         (64, 8, 7, 1, 1),      # unknown form
         (64, 8, STD, 9, 1),    # unknown algorithm
+        (64, 8, STD, 6, 1),    # unknown algorithm
         (64, 8, STD, 1, 0),    # no blocks
         ((1 << 26) + 1, 8, STD, 1, 1),
     ]

@@ -523,23 +523,33 @@ def run_uneven(args):
         raw[raw_off[i] // 8:raw_off[i] // 8 + bits.size] = torch.from_numpy(bits).cuda()
     seeds = torch.from_numpy(g.integers(0, 256, int(seed_off[-1] + (n[-1] + m[-1] + 7) // 8), dtype=np.uint8)).cuda()
     out = torch.empty(int((out_off[-1] + m[-1] + 7) // 8 + 8), dtype=torch.uint8, device="cuda")
-    reqs = [(raw.data_ptr(), int(raw_off[i]), int(n[i]), int(m[i]), seeds.data_ptr() + int(seed_off[i]) // 8, 0,
-             out.data_ptr(), int(out_off[i])) for i in range(len(n))]
-    q.qrng_extract_batch(ctx, reqs)  # capture + first run
-    q.qrng_synchronize(ctx)
+    table = (q.Request * len(n))()
+    for i in range(len(n)):
+        table[i] = q.Request(raw.data_ptr(), int(raw_off[i]), int(n[i]), int(m[i]),
+                             seeds.data_ptr() + int(seed_off[i]) // 8, 0, out.data_ptr(), int(out_off[i]))
+    lib = q.load_library()
     stream = torch.cuda.current_stream()
+    sp = stream.cuda_stream
+
+    def call():
+        ctx.check(lib.qrng_extract_batch(ctx.handle, table, len(n), q.QRNG_ALGO_AUTO, sp), "qrng_extract_batch")
+
+    call()  # capture + first run
+    q.qrng_synchronize(ctx)
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    t0 = time.perf_counter()
     a.record(stream)
     for _ in range(max(1, args.steps)):
-        q.qrng_extract_batch(ctx, reqs)  # graph replay
+        call()  # graph replay (the request table is hashed on the host each call)
     b.record(stream)
     b.synchronize()
+    host_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
     q.qrng_synchronize(ctx)
     ms = a.elapsed_time(b) / max(1, args.steps)
     bitmacs = float(np.sum(m.astype(np.float64) * n))
     ctx.close()
     return {"workload": f"{len(n)} uneven requests, n log-uniform in [2^12, 2^{args.uneven_max_log2n:g}], "
-                        "m/n uniform in [0.5, 0.9], per-request seeds", "ms": ms,
+                        "m/n uniform in [0.5, 0.9], per-request seeds", "ms": ms, "host_wall_ms": host_ms,
             "output_gbit": float(np.sum(m)) / 1e9, "gbps": float(np.sum(m)) / (ms / 1e3) / 1e9,
             "tbitmac_per_s": bitmacs / (ms / 1e3) / 1e12, "frac_of_lop3_peak": bitmacs / (ms / 1e3) / 1e12 / ALU_PEAK_TBITMAC}
 

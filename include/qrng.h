@@ -199,14 +199,18 @@ typedef struct {
 
 /*
  * qrng_extract_batch -- hash `count` independent requests, each one block with its own seed and
- * shape (Sec. III.B / III.D per request; Sec. III.E independence), in ONE persistent kernel launch:
- * work items (request, output tile, raw-word range) are numbered largest request first and taken
- * from an atomic counter by resident warps. The layout, hashing and output-merge kernels are
- * captured once into a CUDA graph cached on the context (keyed by the request table and its
- * buffers); a repeated identical call replays the graph.
+ * shape (Sec. III.B / III.D per request; Sec. III.E independence).
+ * Requests on the direct route run in ONE persistent kernel launch: work items (request, output
+ * tile, raw-word range) are numbered largest request first and taken from an atomic counter by
+ * resident warps. The layout, hashing and output-merge kernels are captured once into a CUDA graph
+ * cached on the context (keyed by the request table and its buffers); a repeated identical call
+ * replays the graph. Requests on the transform route (exact number-theoretic transform of the
+ * circulant convolution, three transforms each) run before the graph, batched by length.
  *   reqs   host; `count` >= 1 requests (device pointers inside; outputs must not overlap raw or
  *          seed data, and two requests' output bit ranges must not overlap).
- *   algo   QRNG_ALGO_AUTO or QRNG_ALGO_DIRECT; anything else is QRNG_ENOTSUP.
+ *   algo   QRNG_ALGO_AUTO (each request on the route its cost model prefers: the transform for
+ *          long blocks), QRNG_ALGO_DIRECT (all direct) or QRNG_ALGO_NTT (all on the transform
+ *          route where its length fits 2^27); anything else is QRNG_ENOTSUP.
  * Asynchronous on `stream`. Batch calls on one context must not overlap on the GPU.
  */
 QRNG_API int qrng_extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int algo,

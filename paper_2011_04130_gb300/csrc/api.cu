@@ -400,10 +400,22 @@ cudaError_t ensure_batch(qrng_ctx* ctx, DevBuf& b, size_t bytes) {
 
 constexpr size_t kMaxGraphs = 4;
 
-int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, cudaStream_t s) {
-  // Request table in device layout, largest work first.
+// Batch routing: a request goes to the transform route when its modelled time there is below the
+// direct kernel's (the number-theoretic transform costs about 3 P log2 P x 2 ps per request, three
+// transforms of the P-point padded seed and raw bits; the direct kernel m n_t / 5.6e14 s).
+bool batch_prefers_ntt(uint64_t n_t, uint64_t m) {
+  const uint64_t P = fft64_length(n_t, m);
+  if (P > (1ull << 27)) return false;
+  const double lg = log2((double)P);
+  return 3.0 * (double)P * lg * 2e-12 < (double)m * (double)n_t / 5.6e14;
+}
+
+int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int algo, cudaStream_t s) {
+  // Request table in device layout: direct requests first (largest work first), then the requests
+  // routed to the transform, grouped by transform length.
   std::vector<BatchReq> t(count);
   std::vector<uint64_t> order(count);
+  std::vector<uint64_t> tlen(count, 0);  // transform length, 0 = direct
   for (uint64_t i = 0; i < count; ++i) {
     const qrng_request& r = reqs[i];
     BatchReq& q = t[i];
@@ -429,15 +441,30 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, cudaS
     const uint64_t first = (reinterpret_cast<uintptr_t>(r.out) * 8 + r.out_bit_off);
     q.dst_word0 = first / 32;
     q.dst_words = (first + r.m - 1) / 32 - q.dst_word0 + 1;
+    const bool ntt = (algo == QRNG_ALGO_NTT && fft64_length(q.n_t, r.m) <= (1ull << 27)) ||
+                     (algo == QRNG_ALGO_AUTO && batch_prefers_ntt(q.n_t, r.m));
+    if (ntt) {  // no direct work, no staging of raw bits or reversed seed
+      tlen[i] = fft64_length(q.n_t, r.m);
+      q.tiles = 0;
+      q.raw_words = 0;
+      q.rev_words = 0;
+    }
     order[i] = i;
   }
   std::stable_sort(order.begin(), order.end(), [&](uint64_t x, uint64_t y) {
-    return t[x].m * t[x].n_t > t[y].m * t[y].n_t;
+    if ((tlen[x] != 0) != (tlen[y] != 0)) return tlen[x] == 0;        // direct requests first
+    if (tlen[x] != tlen[y]) return tlen[x] > tlen[y];                  // transforms grouped by length
+    return t[x].m * t[x].n_t > t[y].m * t[y].n_t;                      // largest work first
   });
   std::vector<BatchReq> sorted(count);
-  uint64_t raw_total = 0, rev_total = 0, out_total = 0, items = 0, dst_total = 0;
+  uint64_t raw_total = 0, rev_total = 0, out_total = 0, items = 0, dst_total = 0, direct_out = 0;
+  uint64_t first_ntt = count;
   for (uint64_t k = 0; k < count; ++k) {
     BatchReq q = t[order[k]];
+    if (tlen[order[k]] != 0 && first_ntt == count) {
+      first_ntt = k;
+      direct_out = out_total;  // the direct requests' staging is [0, direct_out)
+    }
     q.raw_stage_off = raw_total;
     raw_total += q.raw_words;
     q.rev_off = rev_total;
@@ -450,12 +477,13 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, cudaS
     dst_total += q.dst_words;
     sorted[k] = q;
   }
+  if (first_ntt == count) direct_out = out_total;
 
   const uint64_t key = fnv1a(sorted.data(), sorted.size() * sizeof(BatchReq), fnv1a(&count, sizeof(count)));
   uint32_t kernels = 0;
   QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_meta, count * sizeof(BatchReq)), "batch table workspace");
-  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_raw, raw_total * 4), "batch raw workspace");
-  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_rev, rev_total * 4), "batch seed workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_raw, (raw_total ? raw_total : 1) * 4), "batch raw workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_rev, (rev_total ? rev_total : 1) * 4), "batch seed workspace");
   QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_out, out_total * 4), "batch output workspace");
   QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_counter, sizeof(unsigned long long)), "batch counter");
 
@@ -481,11 +509,11 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, cudaS
     if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->batch_meta.p, g.meta_host, count * sizeof(BatchReq),
                                               cudaMemcpyHostToDevice, cs);
     if (e == cudaSuccess) e = cudaMemsetAsync(ctx->batch_counter.p, 0, sizeof(unsigned long long), cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->batch_out.p, 0, out_total * 4, cs);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && direct_out) e = cudaMemsetAsync(ctx->batch_out.p, 0, direct_out * 4, cs);
+    if (e == cudaSuccess && raw_total)
       e = launch_batch_layout(ctx->batch_meta.as<BatchReq>(), (uint32_t)count, raw_total, rev_total,
                               ctx->batch_raw.as<uint32_t>(), ctx->batch_rev.as<uint32_t>(), cs, &kernels);
-    if (e == cudaSuccess)
+    if (e == cudaSuccess && items)
       e = launch_batch_direct(ctx->batch_meta.as<BatchReq>(), (uint32_t)count, items, ctx->batch_raw.as<uint32_t>(),
                               ctx->batch_rev.as<uint32_t>(), ctx->batch_out.as<uint32_t>(),
                               ctx->batch_counter.as<unsigned long long>(), ctx->num_sms, cs, &kernels);
@@ -505,10 +533,33 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, cudaS
     hit = &ctx->graphs.back();
   }
   hit->stamp = ++ctx->graph_clock;
+  uint32_t graph_kernels = (raw_total ? 2 : 0) + (items ? 1 : 0) + 1;
+  // Requests routed to the transform run first (eagerly, grouped by length) into their own staging
+  // region; the graph then runs the direct requests and merges every output into place.
+  if (first_ntt < count) {
+    QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->batch_meta.p, hit->meta_host, count * sizeof(BatchReq),
+                                   cudaMemcpyHostToDevice, s), "batch table upload");
+    uint32_t nk = 0;
+    for (uint64_t k = first_ntt; k < count;) {
+      const uint64_t P = tlen[order[k]];
+      uint64_t cap = kFftWorkspaceBytes / (2 * 2 * P * sizeof(uint32_t));
+      if (cap < 1) cap = 1;
+      uint64_t e = k, max_mw = 0;
+      while (e < count && tlen[order[e]] == P && e - k < cap) {
+        if (sorted[e].mw > max_mw) max_mw = sorted[e].mw;
+        ++e;
+      }
+      QRNG_CUDA(ctx, launch_ntt_batch(ctx->batch_meta.as<BatchReq>() + k, e - k, P, max_mw, ctx->fft,
+                                      ctx->batch_out.as<uint32_t>(), s, &nk),
+                "batched transform extraction");
+      k = e;
+    }
+    graph_kernels += nk;
+  }
   QRNG_CUDA(ctx, cudaGraphLaunch(hit->exec, s), "batch graph launch");
-  ctx->stats.kernels_launched += 4;
-  ctx->stats.last_kernels = 4;
-  ctx->stats.last_algo = QRNG_ALGO_DIRECT;
+  ctx->stats.kernels_launched += graph_kernels;
+  ctx->stats.last_kernels = graph_kernels;
+  ctx->stats.last_algo = first_ntt < count ? (first_ntt == 0 ? QRNG_ALGO_NTT : QRNG_ALGO_AUTO) : QRNG_ALGO_DIRECT;
   return QRNG_OK;
 }
 
@@ -629,8 +680,8 @@ int qrng_toeplitz_extract(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_
 int qrng_extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int algo, qrng_stream_t stream) {
   if (!ctx) return QRNG_EINVAL;
   if (!reqs || count == 0 || count > (1ull << 31)) return fail(ctx, QRNG_EINVAL, "qrng_extract_batch: bad request table");
-  if (algo != QRNG_ALGO_AUTO && algo != QRNG_ALGO_DIRECT)
-    return fail(ctx, QRNG_ENOTSUP, "qrng_extract_batch: batches run the direct kernel (AUTO or DIRECT)");
+  if (algo != QRNG_ALGO_AUTO && algo != QRNG_ALGO_DIRECT && algo != QRNG_ALGO_NTT)
+    return fail(ctx, QRNG_ENOTSUP, "qrng_extract_batch: batches run AUTO, DIRECT or NTT");
   for (uint64_t i = 0; i < count; ++i) {
     const qrng_request& r = reqs[i];
     if (!r.raw || !r.seed || !r.out)
@@ -639,7 +690,7 @@ int qrng_extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, 
       return fail(ctx, QRNG_EINVAL, "qrng_extract_batch: request " + std::to_string(i) + " has a bad shape or form");
   }
   QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
-  return extract_batch(ctx, reqs, count, static_cast<cudaStream_t>(stream));
+  return extract_batch(ctx, reqs, count, algo, static_cast<cudaStream_t>(stream));
 }
 
 int qrng_postprocess_host(qrng_ctx* ctx, const void* samples_host, uint64_t count, int bits, double eps,

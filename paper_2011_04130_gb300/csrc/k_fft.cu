@@ -59,6 +59,47 @@ __global__ void stockham_pass_kernel(const cd* __restrict__ x, cd* __restrict__ 
   yb[(g << (logL + 1)) + k + L] = {a.x - t.x, a.y - t.y};
 }
 
+// exp(-2 pi i t / P) for 0 <= t < P, from the half table (the second half is the negated first).
+__device__ __forceinline__ cd fft_root(const cd* __restrict__ tw, uint64_t half, uint64_t t) {
+  if (t < half) return tw[t];
+  const cd w = tw[t - half];
+  return {-w.x, -w.y};
+}
+
+// One radix-4 Stockham pass: with a_q = x[j + q P/4] and b_q = w^(q k P/(4L)) a_q,
+// y[g 4L + k + r L] = sum_q b_q (-+i)^(qr)  (w and -i conjugated for the inverse).
+__global__ void stockham_pass4_kernel(const cd* __restrict__ x, cd* __restrict__ y, const cd* __restrict__ tw,
+                                      uint64_t P, uint32_t logL, uint32_t logP, int inverse, uint64_t total) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const uint64_t quarter = P >> 2, half = P >> 1;
+  const uint64_t b = idx >> (logP - 2);
+  const uint64_t j = idx & (quarter - 1);
+  const uint64_t L = 1ull << logL;
+  const uint64_t k = j & (L - 1);
+  const uint64_t g = j >> logL;
+  const uint64_t stride = k << (logP - 2 - logL);
+  const cd* xb = x + b * P;
+  cd bq[4];
+  bq[0] = xb[j];
+#pragma unroll
+  for (int q = 1; q < 4; ++q) {
+    cd w = fft_root(tw, half, (uint64_t)q * stride);
+    if (inverse) w.y = -w.y;
+    bq[q] = cmul(w, xb[j + q * quarter]);
+  }
+  const cd s02 = {bq[0].x + bq[2].x, bq[0].y + bq[2].y}, d02 = {bq[0].x - bq[2].x, bq[0].y - bq[2].y};
+  const cd s13 = {bq[1].x + bq[3].x, bq[1].y + bq[3].y};
+  const cd t13 = {bq[1].x - bq[3].x, bq[1].y - bq[3].y};
+  // (-i) t forward, (+i) t inverse
+  const cd d13 = inverse ? cd{-t13.y, t13.x} : cd{t13.y, -t13.x};
+  cd* yb = y + b * P + (g << (logL + 2)) + k;
+  yb[0] = {s02.x + s13.x, s02.y + s13.y};
+  yb[L] = {d02.x + d13.x, d02.y + d13.y};
+  yb[2 * L] = {s02.x - s13.x, s02.y - s13.y};
+  yb[3 * L] = {d02.x - d13.x, d02.y - d13.y};
+}
+
 // Zero-padded seed (first L_t bits) as the real part of one complex vector.
 __global__ void seed_to_complex_kernel(const uint8_t* __restrict__ seed, uint64_t L, cd* __restrict__ z, uint64_t P) {
   uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -144,11 +185,18 @@ inline unsigned grid_for(uint64_t total, int threads) { return (unsigned)ceil_di
 
 cudaError_t run_fft(cd* a, cd* b, const cd* tw, uint64_t P, uint32_t logP, uint64_t batch, int inverse,
                     cudaStream_t s, uint32_t* kernels, cd** result) {
-  const uint64_t total = batch * (P >> 1);
   cd* x = a;
   cd* y = b;
-  for (uint32_t logL = 0; logL < logP; ++logL) {
-    stockham_pass_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total);
+  for (uint32_t logL = 0; logL < logP;) {
+    if (logP - logL >= 2) {  // radix 4 while two factors of 2 remain, then one radix-2 pass
+      const uint64_t total = batch * (P >> 2);
+      stockham_pass4_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total);
+      logL += 2;
+    } else {
+      const uint64_t total = batch * (P >> 1);
+      stockham_pass_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total);
+      logL += 1;
+    }
     ++*kernels;
     cd* t = x;
     x = y;

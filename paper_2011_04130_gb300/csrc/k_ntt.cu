@@ -99,6 +99,44 @@ __global__ void ntt_pass_kernel(const uint32_t* __restrict__ x, uint32_t* __rest
   yb[(g << (logL + 1)) + k + L] = sub_mod(a, t);
 }
 
+// omega^t in Montgomery form for 0 <= t < P, from the half table (omega^(P/2) = -1).
+__device__ __forceinline__ uint32_t ntt_root(const uint32_t* __restrict__ tw, uint64_t half, uint64_t t) {
+  return t < half ? tw[t] : kP - tw[t - half];
+}
+
+// One radix-4 Stockham pass: with a_q = x[j + q P/4] and b_q = omega^(+-q k P/(4L)) a_q,
+// y[g 4L + k + r L] = sum_q b_q i^(qr), i = omega^(+-P/4) a primitive 4th root of unity.
+__global__ void ntt_pass4_kernel(const uint32_t* __restrict__ x, uint32_t* __restrict__ y,
+                                 const uint32_t* __restrict__ tw, uint64_t P, uint32_t logL, uint32_t logP,
+                                 int inverse, uint64_t total) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total) return;
+  const uint64_t quarter = P >> 2, half = P >> 1;
+  const uint64_t b = idx >> (logP - 2);
+  const uint64_t j = idx & (quarter - 1);
+  const uint64_t L = 1ull << logL;
+  const uint64_t k = j & (L - 1);
+  const uint64_t g = j >> logL;
+  const uint64_t stride = k << (logP - 2 - logL);  // k P / (4L)
+  const uint32_t* xb = x + b * P;
+  uint32_t bq[4];
+  bq[0] = xb[j];
+#pragma unroll
+  for (int q = 1; q < 4; ++q) {
+    const uint64_t t = (uint64_t)q * stride;
+    const uint32_t w = inverse ? (t == 0 ? tw[0] : ntt_root(tw, half, P - t)) : ntt_root(tw, half, t);
+    bq[q] = mont_mul(w, xb[j + q * quarter]);
+  }
+  const uint32_t im = inverse ? kP - tw[quarter] : tw[quarter];  // omega^(+-P/4)
+  const uint32_t s02 = add_mod(bq[0], bq[2]), d02 = sub_mod(bq[0], bq[2]);
+  const uint32_t s13 = add_mod(bq[1], bq[3]), d13 = mont_mul(im, sub_mod(bq[1], bq[3]));
+  uint32_t* yb = y + b * P + (g << (logL + 2)) + k;
+  yb[0] = add_mod(s02, s13);
+  yb[L] = add_mod(d02, d13);
+  yb[2 * L] = sub_mod(s02, s13);
+  yb[3 * L] = sub_mod(d02, d13);
+}
+
 __global__ void ntt_seed_kernel(const uint8_t* __restrict__ seed, uint64_t L, uint32_t* __restrict__ z, uint64_t P) {
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= P) return;
@@ -162,11 +200,18 @@ inline unsigned grid_for(uint64_t total, int threads) { return (unsigned)ceil_di
 
 cudaError_t run_ntt(uint32_t* a, uint32_t* b, const uint32_t* tw, uint64_t P, uint32_t logP, uint64_t batch,
                     int inverse, cudaStream_t s, uint32_t* kernels, uint32_t** result) {
-  const uint64_t total = batch * (P >> 1);
   uint32_t* x = a;
   uint32_t* y = b;
-  for (uint32_t logL = 0; logL < logP; ++logL) {
-    ntt_pass_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total);
+  for (uint32_t logL = 0; logL < logP;) {
+    if (logP - logL >= 2) {  // radix 4 while two factors of 2 remain, then one radix-2 pass
+      const uint64_t total = batch * (P >> 2);
+      ntt_pass4_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total);
+      logL += 2;
+    } else {
+      const uint64_t total = batch * (P >> 1);
+      ntt_pass_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total);
+      logL += 1;
+    }
     ++*kernels;
     uint32_t* t = x;
     x = y;
@@ -176,7 +221,90 @@ cudaError_t run_ntt(uint32_t* a, uint32_t* b, const uint32_t* tw, uint64_t P, ui
   return cudaGetLastError();
 }
 
+// ---- uneven batches: requests with their own seeds, grouped by transform length P ----
+
+__device__ __forceinline__ uint32_t bit_at(const uint8_t* __restrict__ p, uint64_t bit) {
+  return (p[bit >> 3] >> (bit & 7)) & 1u;
+}
+
+// Entry 2r of the chunk holds request r's seed bits [0, L_t), entry 2r+1 its raw bits [0, n_t),
+// both zero-padded to P.
+__global__ void ntt_batch_inputs_kernel(const BatchReq* __restrict__ reqs, uint64_t nr, uint32_t* __restrict__ z,
+                                        uint64_t P) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= 2 * nr * P) return;
+  const uint64_t e = idx / P, t = idx - e * P;
+  const BatchReq& q = reqs[e >> 1];
+  uint32_t v = 0;
+  if (e & 1) {
+    if (t < q.n_t) v = bit_at(q.raw, q.raw_bit_off + t);
+  } else {
+    if (t < q.L_t) v = bit_at(q.seed, t);
+  }
+  z[idx] = v;
+}
+
+// c_r = (S_2r (*) S_2r+1) (*) factor = A R / P  (Montgomery products; factor = P^-1 2^64 mod p).
+__global__ void ntt_batch_mul_kernel(const uint32_t* __restrict__ z, uint32_t* __restrict__ c, uint64_t P, uint64_t nr,
+                                     uint32_t factor_m) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nr * P) return;
+  const uint64_t r = idx / P, t = idx - r * P;
+  c[idx] = mont_mul(mont_mul(z[(2 * r) * P + t], z[(2 * r + 1) * P + t]), factor_m);
+}
+
+// Output word w of chunk request r (one warp per word): parities of c[n_t - 1 + i], identity bits.
+__global__ void ntt_batch_extract_kernel(const BatchReq* __restrict__ reqs, uint64_t nr, uint64_t max_mw,
+                                         const uint32_t* __restrict__ c, uint64_t P, uint32_t* __restrict__ out_stage) {
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  if (gw >= nr * max_mw) return;
+  const uint64_t r = gw / max_mw, w = gw - r * max_mw;
+  const BatchReq& q = reqs[r];
+  if (w >= q.mw) return;  // warp-uniform
+  const uint64_t i = 32 * w + lane;
+  const uint32_t bit = (i < q.m) ? (c[r * P + q.n_t - 1 + i] & 1u) : 0u;
+  uint32_t word = __ballot_sync(0xffffffffu, bit);
+  const uint32_t ident = (q.form == QRNG_FORM_MODIFIED && i < q.m) ? bit_at(q.raw, q.raw_bit_off + q.id_off + i) : 0u;
+  word ^= __ballot_sync(0xffffffffu, ident);
+  if (lane == 0) out_stage[q.out_stage_off + w] = word;
+}
+
 }  // namespace
+
+cudaError_t launch_ntt_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P,
+                             uint64_t max_mw, FftWorkspace& ws, uint32_t* out_stage, cudaStream_t s,
+                             uint32_t* kernels) {
+  uint32_t logP = 0;
+  while ((1ull << logP) < P) ++logP;
+  cudaError_t e;
+  if (ws.ntt_P != P) {
+    if ((e = ws.ntt_tw.ensure((P / 2) * sizeof(uint32_t))) != cudaSuccess) return e;
+    const uint32_t omega = pow_mod(kGen, (kP - 1) / P);
+    ntt_twiddle_kernel<<<grid_for(ceil_div(P / 2, 256), 128), 128, 0, s>>>(
+        ws.ntt_tw.as<uint32_t>(), P / 2, to_mont(omega), to_mont(1), to_mont(pow_mod(omega, 256)));
+    ++*kernels;
+    ws.ntt_P = P;
+  }
+  if ((e = ws.buf0.ensure(2 * nr * P * sizeof(uint32_t))) != cudaSuccess) return e;
+  if ((e = ws.buf1.ensure(2 * nr * P * sizeof(uint32_t))) != cudaSuccess) return e;
+  uint32_t* b0p = ws.buf0.as<uint32_t>();
+  uint32_t* b1p = ws.buf1.as<uint32_t>();
+  ntt_batch_inputs_kernel<<<grid_for(2 * nr * P, 256), 256, 0, s>>>(reqs_dev, nr, b0p, P);
+  ++*kernels;
+  uint32_t* spec = nullptr;
+  if ((e = run_ntt(b0p, b1p, ws.ntt_tw.as<uint32_t>(), P, logP, 2 * nr, 0, s, kernels, &spec)) != cudaSuccess)
+    return e;
+  uint32_t* other = (spec == b0p) ? b1p : b0p;
+  const uint32_t factor_m = to_mont(to_mont(pow_mod(P % kP, kP - 2)));
+  ntt_batch_mul_kernel<<<grid_for(nr * P, 256), 256, 0, s>>>(spec, other, P, nr, factor_m);
+  ++*kernels;
+  uint32_t* res = nullptr;
+  if ((e = run_ntt(other, spec, ws.ntt_tw.as<uint32_t>(), P, logP, nr, 1, s, kernels, &res)) != cudaSuccess) return e;
+  ntt_batch_extract_kernel<<<grid_for(nr * max_mw * 32, 256), 256, 0, s>>>(reqs_dev, nr, max_mw, res, P, out_stage);
+  ++*kernels;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_ntt(const DirectArgs& d, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
                        uint32_t* kernels) {

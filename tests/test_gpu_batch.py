@@ -38,7 +38,7 @@ def _make_batch(count, seed, log2n_lo, log2n_hi, mixed_forms=True):
     return n, m, forms, raw, raw_offs, seeds, out_offs, opos
 
 
-def _run(qlib, ctx, batch, sentinel=0x5A):
+def _run(qlib, ctx, batch, sentinel=0x5A, algo=0):
     import torch
 
     n, m, forms, raw, raw_offs, seeds, out_offs, out_bits = batch
@@ -48,7 +48,7 @@ def _run(qlib, ctx, batch, sentinel=0x5A):
     out = torch.full((nbytes,), sentinel, dtype=torch.uint8, device="cuda")
     reqs = [(raw_p, raw_offs[i], int(n[i]), int(m[i]), seed_t[i][1], int(forms[i]), out.data_ptr(), out_offs[i])
             for i in range(len(n))]
-    qlib.qrng_extract_batch(ctx, reqs)
+    qlib.qrng_extract_batch(ctx, reqs, algo=algo)
     qlib.qrng_synchronize(ctx)
     return out.cpu().numpy(), (raw_t, seed_t, out, reqs)
 
@@ -87,6 +87,24 @@ def test_uneven_requests_log_uniform(qlib, gpu, oracle_mod):
     batch = _make_batch(300, 9, 12, 17)
     host, _ = _run(qlib, gpu, batch)
     _check(oracle_mod, batch, host)
+
+
+def test_all_requests_on_the_transform_route(qlib, gpu, oracle_mod):
+    """QRNG_ALGO_NTT sends every request through the batched number-theoretic transform."""
+    batch = _make_batch(60, 13, 5, 14)
+    host, _ = _run(qlib, gpu, batch, algo=qlib.QRNG_ALGO_NTT)
+    _check(oracle_mod, batch, host)
+    assert qlib.qrng_get_stats(gpu)["last_algo"] == qlib.QRNG_ALGO_NTT
+
+
+def test_mixed_routes_long_requests(qlib, gpu, oracle_mod):
+    """AUTO on requests up to 2^20 bits: short ones on the persistent kernel, long ones on the
+    transform route, all merged into one output buffer."""
+    batch = _make_batch(120, 17, 10, 20)
+    host, _ = _run(qlib, gpu, batch)
+    _check(oracle_mod, batch, host)
+    direct = _run(qlib, gpu, batch, algo=qlib.QRNG_ALGO_DIRECT)[0]
+    assert np.array_equal(host, direct)
 
 
 def test_graph_replay_sees_new_data(qlib, gpu, oracle_mod):
@@ -130,6 +148,9 @@ def test_batch_bad_arguments(qlib, gpu):
     ok = (t, 0, 64, 32, t, STD, t, 0)
     with pytest.raises(qlib.QrngError) as e:
         qlib.qrng_extract_batch(gpu, [ok], algo=qlib.QRNG_ALGO_FFT64)
+    assert e.value.status == qlib.QRNG_ENOTSUP
+    with pytest.raises(qlib.QrngError) as e:
+        qlib.qrng_extract_batch(gpu, [ok], algo=qlib.QRNG_ALGO_GEMM_TC)
     assert e.value.status == qlib.QRNG_ENOTSUP
     with pytest.raises(qlib.QrngError) as e:
         qlib.qrng_extract_batch(gpu, [ok, (t, 0, 64, 64, t, MOD, t, 0)])

@@ -532,7 +532,7 @@ def run_uneven(args):
     sp = stream.cuda_stream
 
     def call():
-        ctx.check(lib.qrng_extract_batch(ctx.handle, table, len(n), q.QRNG_ALGO_AUTO, sp), "qrng_extract_batch")
+        ctx.check(lib.qrng_extract_batch(ctx.handle, table, len(n), ALGOS[args.algo], sp), "qrng_extract_batch")
 
     call()  # capture + first run
     q.qrng_synchronize(ctx)
@@ -547,11 +547,17 @@ def run_uneven(args):
     q.qrng_synchronize(ctx)
     ms = a.elapsed_time(b) / max(1, args.steps)
     bitmacs = float(np.sum(m.astype(np.float64) * n))
+    st = q.qrng_get_stats(ctx)
     ctx.close()
-    return {"workload": f"{len(n)} uneven requests, n log-uniform in [2^12, 2^{args.uneven_max_log2n:g}], "
-                        "m/n uniform in [0.5, 0.9], per-request seeds", "ms": ms, "host_wall_ms": host_ms,
-            "output_gbit": float(np.sum(m)) / 1e9, "gbps": float(np.sum(m)) / (ms / 1e3) / 1e9,
-            "tbitmac_per_s": bitmacs / (ms / 1e3) / 1e12, "frac_of_lop3_peak": bitmacs / (ms / 1e3) / 1e12 / ALU_PEAK_TBITMAC}
+    res = {"workload": f"{len(n)} uneven requests, n log-uniform in [2^12, 2^{args.uneven_max_log2n:g}], "
+                       "m/n uniform in [0.5, 0.9], per-request seeds", "algo": args.algo, "ms": ms,
+           "host_wall_ms": host_ms, "output_gbit": float(np.sum(m)) / 1e9,
+           "gbps": float(np.sum(m)) / (ms / 1e3) / 1e9, "kernels_per_call": st["last_kernels"],
+           "route": q.ALGO_NAMES.get(st["last_algo"], "mixed") if st["last_algo"] else "mixed (direct + ntt)",
+           "direct_equivalent_tbitmac_per_s": bitmacs / (ms / 1e3) / 1e12}
+    if st["last_algo"] == q.QRNG_ALGO_DIRECT:
+        res["frac_of_lop3_peak"] = res["direct_equivalent_tbitmac_per_s"] / ALU_PEAK_TBITMAC
+    return res
 
 
 def main():

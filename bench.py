@@ -48,7 +48,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--blocks", type=int, default=0,
                    help="hash only the first BLOCKS blocks (a smaller case for profiler captures)")
-    p.add_argument("--workload", default="laser", choices=["laser", "single", "sweep", "tc", "uneven"],
+    p.add_argument("--workload", default="laser", choices=["laser", "single", "sweep", "tc", "uneven", "forms"],
                    help="laser: the headline stream (default); single: one 4096-bit block; sweep: block-length "
                         "sweep on a 2^30-bit stream; tc: m=6144, n=8192, 4096 blocks; uneven: 10,000 requests")
     p.add_argument("--sweep-algos", default="direct,gemm_tc,ntt,fft64",
@@ -448,6 +448,37 @@ def run_sweep(args):
                         "modified form", "unit": UNIT, "data": "synthetic", "rows": rows}
 
 
+def run_forms(args):
+    """Standard (n+m-1-bit seed) vs modified ((A, I_m), n-1-bit seed) Toeplitz hashing at equal n and
+    m on the same 2^30-bit stream, for every algorithm: the comparison the paper leaves as future work."""
+    import torch
+
+    import paper_2011_04130_gb300 as q
+
+    torch.cuda.set_device(0)
+    ctx = q.Context(0)
+    c = W.CFG3
+    raw = torch.from_numpy(W.random_bits(c["stream_bits"], c["raw_seed"])).cuda()
+    out = torch.empty(c["stream_bits"] // 8, dtype=torch.uint8, device="cuda")
+    rows = []
+    for n in (1 << 12, 1 << 16, 1 << 20):
+        for ratio in (0.5, 0.75):
+            m = int(n * ratio)
+            B = c["stream_bits"] // n
+            row = {"n": n, "m": m, "blocks": B}
+            for form, fname in ((0, "standard"), (1, "modified")):
+                L = n + m - 1 if form == 0 else n - 1
+                seed = torch.from_numpy(W.random_bits(L, 99)).cuda()
+                row[fname] = {"seed_bits": L}
+                for name in ("direct", "gemm_tc", "ntt"):
+                    kms, cms, _ = _time_extract(q, ctx, raw, n, m, seed, form, ALGOS[name], B, out, reps=2)
+                    row[fname][name] = {"call_ms": cms, "gbps": B * m / (cms / 1e3) / 1e9}
+            rows.append(row)
+            print(json.dumps(row), file=sys.stderr)
+    ctx.close()
+    return {"workload": "standard vs modified Toeplitz on a 2^30-bit stream", "unit": UNIT, "rows": rows}
+
+
 def run_tc(args):
     """One standard seed, m = 6144, n = 8192, 4096 blocks: tensor-core product vs the direct kernel."""
     import torch
@@ -566,7 +597,8 @@ def main():
     if args.impl == "reference":
         res = run_reference(args, world, rank)
     elif args.workload != "laser":
-        res = {"sweep": run_sweep, "tc": run_tc, "single": run_single, "uneven": run_uneven}[args.workload](args)
+        res = {"sweep": run_sweep, "tc": run_tc, "single": run_single, "uneven": run_uneven,
+               "forms": run_forms}[args.workload](args)
     else:
         res = run_ours(args, world, rank, local)
     if rank == 0 and res is not None:

@@ -208,9 +208,13 @@ typedef struct {
  * circulant convolution, three transforms each) run before the graph, batched by length.
  *   reqs   host; `count` >= 1 requests (device pointers inside; outputs must not overlap raw or
  *          seed data, and two requests' output bit ranges must not overlap).
- *   algo   QRNG_ALGO_AUTO (each request on the route its cost model prefers: the transform for
- *          long blocks), QRNG_ALGO_DIRECT (all direct) or QRNG_ALGO_NTT (all on the transform
- *          route where its length fits 2^27); anything else is QRNG_ENOTSUP.
+ *   algo   QRNG_ALGO_AUTO (each request on the route its cost model prefers: the exact
+ *          number-theoretic transform for long blocks), QRNG_ALGO_DIRECT (all direct),
+ *          QRNG_ALGO_NTT or QRNG_ALGO_FFT64 (every request whose transform length fits 2^27 on that
+ *          transform: the FP64 one packs seed and raw bits into one complex vector per request and
+ *          two requests into one inverse); anything else (the shared-seed tensor-core product, the
+ *          FP32 segmented route whose per-request seed windows would cost O(mn/S)) is
+ *          QRNG_ENOTSUP.
  * Asynchronous on `stream`. Batch calls on one context must not overlap on the GPU.
  */
 QRNG_API int qrng_extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int algo,

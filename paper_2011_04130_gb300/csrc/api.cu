@@ -441,7 +441,7 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int a
     const uint64_t first = (reinterpret_cast<uintptr_t>(r.out) * 8 + r.out_bit_off);
     q.dst_word0 = first / 32;
     q.dst_words = (first + r.m - 1) / 32 - q.dst_word0 + 1;
-    const bool ntt = (algo == QRNG_ALGO_NTT && fft64_length(q.n_t, r.m) <= (1ull << 27)) ||
+    const bool ntt = ((algo == QRNG_ALGO_NTT || algo == QRNG_ALGO_FFT64) && fft64_length(q.n_t, r.m) <= (1ull << 27)) ||
                      (algo == QRNG_ALGO_AUTO && batch_prefers_ntt(q.n_t, r.m));
     if (ntt) {  // no direct work, no staging of raw bits or reversed seed
       tlen[i] = fft64_length(q.n_t, r.m);
@@ -542,15 +542,21 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int a
     uint32_t nk = 0;
     for (uint64_t k = first_ntt; k < count;) {
       const uint64_t P = tlen[order[k]];
-      uint64_t cap = kFftWorkspaceBytes / (2 * 2 * P * sizeof(uint32_t));
+      const bool fp64 = (algo == QRNG_ALGO_FFT64);
+      const uint64_t per_req = fp64 ? 2 * P * 16 : 2 * 2 * P * sizeof(uint32_t);  // both ping-pong buffers
+      uint64_t cap = kFftWorkspaceBytes / per_req;
       if (cap < 1) cap = 1;
       uint64_t e = k, max_mw = 0;
       while (e < count && tlen[order[e]] == P && e - k < cap) {
         if (sorted[e].mw > max_mw) max_mw = sorted[e].mw;
         ++e;
       }
-      QRNG_CUDA(ctx, launch_ntt_batch(ctx->batch_meta.as<BatchReq>() + k, e - k, P, max_mw, ctx->fft,
-                                      ctx->batch_out.as<uint32_t>(), s, &nk),
+      ctx->fft.worst = ctx->fft_worst.as<unsigned long long>();
+      QRNG_CUDA(ctx,
+                fp64 ? launch_fft64_batch(ctx->batch_meta.as<BatchReq>() + k, e - k, P, max_mw, ctx->fft,
+                                          ctx->batch_out.as<uint32_t>(), s, &nk)
+                     : launch_ntt_batch(ctx->batch_meta.as<BatchReq>() + k, e - k, P, max_mw, ctx->fft,
+                                        ctx->batch_out.as<uint32_t>(), s, &nk),
                 "batched transform extraction");
       k = e;
     }
@@ -559,7 +565,8 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int a
   QRNG_CUDA(ctx, cudaGraphLaunch(hit->exec, s), "batch graph launch");
   ctx->stats.kernels_launched += graph_kernels;
   ctx->stats.last_kernels = graph_kernels;
-  ctx->stats.last_algo = first_ntt < count ? (first_ntt == 0 ? QRNG_ALGO_NTT : QRNG_ALGO_AUTO) : QRNG_ALGO_DIRECT;
+  const int transform = (algo == QRNG_ALGO_FFT64) ? QRNG_ALGO_FFT64 : QRNG_ALGO_NTT;
+  ctx->stats.last_algo = first_ntt < count ? (first_ntt == 0 ? transform : QRNG_ALGO_AUTO) : QRNG_ALGO_DIRECT;
   return QRNG_OK;
 }
 
@@ -680,8 +687,8 @@ int qrng_toeplitz_extract(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_
 int qrng_extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int algo, qrng_stream_t stream) {
   if (!ctx) return QRNG_EINVAL;
   if (!reqs || count == 0 || count > (1ull << 31)) return fail(ctx, QRNG_EINVAL, "qrng_extract_batch: bad request table");
-  if (algo != QRNG_ALGO_AUTO && algo != QRNG_ALGO_DIRECT && algo != QRNG_ALGO_NTT)
-    return fail(ctx, QRNG_ENOTSUP, "qrng_extract_batch: batches run AUTO, DIRECT or NTT");
+  if (algo != QRNG_ALGO_AUTO && algo != QRNG_ALGO_DIRECT && algo != QRNG_ALGO_NTT && algo != QRNG_ALGO_FFT64)
+    return fail(ctx, QRNG_ENOTSUP, "qrng_extract_batch: batches run AUTO, DIRECT, NTT or FFT64");
   for (uint64_t i = 0; i < count; ++i) {
     const qrng_request& r = reqs[i];
     if (!r.raw || !r.seed || !r.out)

@@ -268,6 +268,113 @@ cudaError_t launch_fft64(const DirectArgs& d, const uint8_t* seed, uint64_t L_t,
 
 
 // ------------------------------------------------------------------------------------------------
+// FP64 route for uneven batches (each request its own seed, all of one transform length P):
+// z_r = a_r + i r_r carries request r's seed and raw bits in one complex vector; from Z = F z the
+// two spectra are A = (Z_k + conj Z_-k)/2 and R = (Z_k - conj Z_-k)/(2i); C_r = A R / P is the
+// spectrum of the real convolution, so two requests share one inverse: F^-1(C_r + i C_r') =
+// c_r + i c_r'. One forward and half an inverse transform per request.
+// ------------------------------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ double bit_at_f(const uint8_t* __restrict__ p, uint64_t bit) {
+  return (double)((p[bit >> 3] >> (bit & 7)) & 1u);
+}
+
+__global__ void fft_batch_inputs_kernel(const BatchReq* __restrict__ reqs, uint64_t nr, cd* __restrict__ z, uint64_t P) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= nr * P) return;
+  const uint64_t r = idx / P, t = idx - r * P;
+  const BatchReq& q = reqs[r];
+  z[idx] = {t < q.L_t ? bit_at_f(q.seed, t) : 0.0, t < q.n_t ? bit_at_f(q.raw, q.raw_bit_off + t) : 0.0};
+}
+
+// W_pair[k] = C_{2 pair}[k] + i C_{2 pair + 1}[k],  C_r = A_r R_r / P.
+__global__ void fft_batch_mul_kernel(const cd* __restrict__ Z, cd* __restrict__ W, uint64_t P, uint64_t nr) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t npairs = (nr + 1) / 2;
+  if (idx >= npairs * P) return;
+  const uint64_t pr = idx / P, k = idx - pr * P;
+  const uint64_t km = (P - k) & (P - 1);
+  const double s = 1.0 / (double)P;
+  cd c[2] = {{0.0, 0.0}, {0.0, 0.0}};
+  for (int h = 0; h < 2; ++h) {
+    const uint64_t r = 2 * pr + h;
+    if (r >= nr) break;
+    const cd zk = Z[r * P + k], zm = Z[r * P + km];
+    const cd a = {0.5 * (zk.x + zm.x), 0.5 * (zk.y - zm.y)};   // (Z_k + conj Z_-k) / 2
+    const cd rr = {0.5 * (zk.y + zm.y), -0.5 * (zk.x - zm.x)};  // (Z_k - conj Z_-k) / (2i)
+    const cd v = cmul(a, rr);
+    c[h] = {v.x * s, v.y * s};
+  }
+  W[idx] = {c[0].x - c[1].y, c[0].y + c[1].x};  // c0 + i c1
+}
+
+// Output word w of request r (one warp per word): parity of round(c_r[n_t - 1 + i]), identity bits.
+__global__ void fft_batch_extract_kernel(const BatchReq* __restrict__ reqs, uint64_t nr, uint64_t max_mw,
+                                         const cd* __restrict__ Wt, uint64_t P, uint32_t* __restrict__ out_stage,
+                                         unsigned long long* __restrict__ worst) {
+  const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  if (gw >= nr * max_mw) return;
+  const uint64_t r = gw / max_mw, w = gw - r * max_mw;
+  const BatchReq& q = reqs[r];
+  if (w >= q.mw) return;  // warp-uniform
+  const uint64_t i = 32 * w + lane;
+  double err = 0.0;
+  uint32_t bit = 0;
+  if (i < q.m) {
+    const cd v = Wt[(r / 2) * P + q.n_t - 1 + i];
+    const double x = (r & 1) ? v.y : v.x;
+    const double rx = rint(x);
+    err = fabs(x - rx);
+    bit = (uint32_t)((long long)rx & 1);
+  }
+  uint32_t word = __ballot_sync(0xffffffffu, bit);
+  const uint32_t ident = (q.form == QRNG_FORM_MODIFIED && i < q.m)
+                             ? (uint32_t)bit_at_f(q.raw, q.raw_bit_off + q.id_off + i) : 0u;
+  word ^= __ballot_sync(0xffffffffu, ident);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) err = fmax(err, __shfl_xor_sync(0xffffffffu, err, o));
+  if (lane == 0) {
+    atomicMax(worst, (unsigned long long)__double_as_longlong(err));
+    out_stage[q.out_stage_off + w] = word;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_fft64_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P, uint64_t max_mw, FftWorkspace& ws,
+                               uint32_t* out_stage, cudaStream_t s, uint32_t* kernels) {
+  uint32_t logP = 0;
+  while ((1ull << logP) < P) ++logP;
+  cudaError_t e;
+  if (ws.tw_P != P) {
+    if ((e = ws.tw.ensure((P / 2) * sizeof(cd))) != cudaSuccess) return e;
+    twiddle_kernel<<<grid_for(P / 2, 256), 256, 0, s>>>(ws.tw.as<cd>(), P);
+    ++*kernels;
+    ws.tw_P = P;
+  }
+  if ((e = ws.buf0.ensure(nr * P * sizeof(cd))) != cudaSuccess) return e;
+  if ((e = ws.buf1.ensure(nr * P * sizeof(cd))) != cudaSuccess) return e;
+  cd* b0p = ws.buf0.as<cd>();
+  cd* b1p = ws.buf1.as<cd>();
+  fft_batch_inputs_kernel<<<grid_for(nr * P, 256), 256, 0, s>>>(reqs_dev, nr, b0p, P);
+  ++*kernels;
+  cd* Z = nullptr;
+  if ((e = run_fft(b0p, b1p, ws.tw.as<cd>(), P, logP, nr, 0, s, kernels, &Z)) != cudaSuccess) return e;
+  cd* Wb = (Z == b0p) ? b1p : b0p;
+  const uint64_t npairs = (nr + 1) / 2;
+  fft_batch_mul_kernel<<<grid_for(npairs * P, 256), 256, 0, s>>>(Z, Wb, P, nr);
+  ++*kernels;
+  cd* res = nullptr;
+  if ((e = run_fft(Wb, Z, ws.tw.as<cd>(), P, logP, npairs, 1, s, kernels, &res)) != cudaSuccess) return e;
+  fft_batch_extract_kernel<<<grid_for(nr * max_mw * 32, 256), 256, 0, s>>>(reqs_dev, nr, max_mw, res, P, out_stage,
+                                                                          ws.worst);
+  ++*kernels;
+  return cudaGetLastError();
+}
+
+// ------------------------------------------------------------------------------------------------
 // FFT32_SEG: FP32 transforms on short segments, parities XOR-combined.
 //
 // Raw segment s = r[sS, (s+1)S) and output tile q = outputs [qS, (q+1)S) meet through an S x S

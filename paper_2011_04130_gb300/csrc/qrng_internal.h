@@ -164,6 +164,8 @@ struct BatchReq;
 cudaError_t launch_ntt_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P,
                              uint64_t max_mw, FftWorkspace& ws, uint32_t* out_stage, cudaStream_t s,
                              uint32_t* kernels);
+cudaError_t launch_fft64_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P, uint64_t max_mw, FftWorkspace& ws,
+                               uint32_t* out_stage, cudaStream_t s, uint32_t* kernels);
 cudaError_t launch_fft32_seg(const DirectArgs& a, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
                              uint32_t* kernels);
 

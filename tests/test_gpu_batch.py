@@ -97,6 +97,17 @@ def test_all_requests_on_the_transform_route(qlib, gpu, oracle_mod):
     assert qlib.qrng_get_stats(gpu)["last_algo"] == qlib.QRNG_ALGO_NTT
 
 
+def test_all_requests_on_the_fp64_route(qlib, gpu, oracle_mod):
+    """QRNG_ALGO_FFT64: seed and raw bits of a request in one complex vector, two requests per
+    inverse transform; exact after rounding, with the rounding distance reported."""
+    batch = _make_batch(61, 15, 5, 15)  # odd count: the last pair has one request
+    qlib.qrng_reset_stats(gpu)
+    host, _ = _run(qlib, gpu, batch, algo=qlib.QRNG_ALGO_FFT64)
+    _check(oracle_mod, batch, host)
+    st = qlib.qrng_get_stats(gpu)
+    assert st["last_algo"] == qlib.QRNG_ALGO_FFT64 and st["worst_fft_round_err"] < 1e-6
+
+
 def test_mixed_routes_long_requests(qlib, gpu, oracle_mod):
     """AUTO on requests up to 2^20 bits: short ones on the persistent kernel, long ones on the
     transform route, all merged into one output buffer."""
@@ -147,7 +158,7 @@ def test_batch_bad_arguments(qlib, gpu):
     t = torch.zeros(64, dtype=torch.uint8, device="cuda")
     ok = (t, 0, 64, 32, t, STD, t, 0)
     with pytest.raises(qlib.QrngError) as e:
-        qlib.qrng_extract_batch(gpu, [ok], algo=qlib.QRNG_ALGO_FFT64)
+        qlib.qrng_extract_batch(gpu, [ok], algo=qlib.QRNG_ALGO_FFT32_SEG)
     assert e.value.status == qlib.QRNG_ENOTSUP
     with pytest.raises(qlib.QrngError) as e:
         qlib.qrng_extract_batch(gpu, [ok], algo=qlib.QRNG_ALGO_GEMM_TC)

@@ -78,6 +78,13 @@ def _load():
                                                         ctypes.POINTER(HminReport)]
             lib.oracle_minentropy.argtypes = [ctypes.c_void_p, u64, ctypes.c_int, ctypes.c_double,
                                               ctypes.POINTER(HminReport)]
+            lib.oracle_minentropy_quantum_from_hist.argtypes = [u64p, u64p, ctypes.c_int, ctypes.c_double,
+                                                                ctypes.POINTER(HminReport),
+                                                                ctypes.POINTER(ctypes.c_double)]
+            lib.oracle_splitmix64.argtypes = [u64, u64]
+            lib.oracle_splitmix64.restype = u64
+            lib.oracle_histogram_sampled.argtypes = [ctypes.c_void_p, u64, ctypes.c_int, ctypes.c_double, u64, u64p,
+                                                     u64p]
             lib.oracle_output_length.argtypes = [u64, ctypes.c_double, ctypes.c_int, ctypes.c_double]
             lib.oracle_output_length.restype = u64
             lib.oracle_seed_bits.argtypes = [u64, u64, ctypes.c_int]
@@ -165,3 +172,37 @@ def minentropy(samples: np.ndarray, bits: int, eps: float) -> dict:
 
 def output_length(n: int, h_per_sample: float, bits: int, eps_lhl: float) -> int:
     return int(_load().oracle_output_length(n, h_per_sample, bits, eps_lhl))
+
+
+def minentropy_quantum(samples_on: np.ndarray, samples_off: np.ndarray, bits: int, eps: float):
+    """Classical-noise subtraction (Sec. II.B): (report of the quantum model, H^{q+c} - H'^c)."""
+    h_on, bad_on = histogram(samples_on, bits)
+    h_off, bad_off = histogram(samples_off, bits)
+    if bad_on or bad_off:
+        raise ValueError("sample >= 2^bits")
+    rep = HminReport()
+    hs = ctypes.c_double()
+    _check(_load().oracle_minentropy_quantum_from_hist(_u64(h_on), _u64(h_off), bits, eps, ctypes.byref(rep),
+                                                       ctypes.byref(hs)), "minentropy_quantum")
+    return rep.as_dict(), hs.value
+
+
+def splitmix64(x0: int, s: int) -> int:
+    return int(_load().oracle_splitmix64(x0 & (2**64 - 1), s))
+
+
+def histogram_sampled(samples: np.ndarray, bits: int, fraction: float, sel_seed: int):
+    samples = np.ascontiguousarray(samples)
+    hist = np.zeros(1 << bits, dtype=np.uint64)
+    bad = np.zeros(1, dtype=np.uint64)
+    _check(_load().oracle_histogram_sampled(samples.ctypes.data, samples.size, bits, fraction, sel_seed, _u64(hist),
+                                            _u64(bad)), "histogram_sampled")
+    return hist, int(bad[0])
+
+
+def minentropy_sampled(samples: np.ndarray, bits: int, eps: float, fraction: float, sel_seed: int) -> dict:
+    """Sec. II.C: the corrected entropy from a random subsample of the stream."""
+    hist, bad = histogram_sampled(samples, bits, fraction, sel_seed)
+    if bad:
+        raise ValueError("sample >= 2^bits")
+    return minentropy_from_hist(hist, bits, eps)

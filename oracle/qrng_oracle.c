@@ -214,6 +214,17 @@ static double std_normal_mass(double y, double z) {
   return 0.5 * (erf(z * r) - erf(y * r));
 }
 
+/* Model cells of a Gaussian of mean mu and variance var (> 0) discretised like the ADC: code v
+ * collects the real line between v - 1/2 and v + 1/2, and the end codes also take the tails. */
+static void gaussian_cells(double mu, double var, uint64_t K, double* P) {
+  double sigma = sqrt(var);
+  for (uint64_t v = 0; v < K; ++v) {
+    double lo = (v == 0) ? -INFINITY : ((double)v - 0.5 - mu) / sigma;
+    double hi = (v == K - 1) ? INFINITY : ((double)v + 0.5 - mu) / sigma;
+    P[v] = std_normal_mass(lo, hi);
+  }
+}
+
 /* Min-entropy report from an exact histogram (the steps of Sec. II in the paper's order). */
 int oracle_minentropy_from_hist(const uint64_t* hist, int bits, double eps, oracle_hmin_report* rep) {
   if (bits < 1 || bits > 16 || !(eps > 0.0 && eps < 1.0)) return ORACLE_EINVAL;
@@ -250,13 +261,7 @@ int oracle_minentropy_from_hist(const uint64_t* hist, int bits, double eps, orac
   if (num == 0) {
     for (uint64_t v = 0; v < K; ++v) P[v] = (v == argmax) ? 1.0 : 0.0;
   } else {
-    double sigma = sqrt(var);
-    for (uint64_t v = 0; v < K; ++v) {
-      /* code v collects the real line between v - 1/2 and v + 1/2; the end codes take the tails */
-      double lo = (v == 0) ? -INFINITY : ((double)v - 0.5 - mu) / sigma;
-      double hi = (v == K - 1) ? INFINITY : ((double)v + 0.5 - mu) / sigma;
-      P[v] = std_normal_mass(lo, hi);
-    }
+    gaussian_cells(mu, var, K, P);
   }
   double pmax = 0.0;
   for (uint64_t v = 0; v < K; ++v)
@@ -275,6 +280,69 @@ int oracle_minentropy_from_hist(const uint64_t* hist, int bits, double eps, orac
   rep->delta_hm = log2((rep->d_u + rep->delta_fs) / ldexp(1.0, -bits - 1) + 1.0);
   double h = rep->h_model - rep->delta_hm;
   rep->h_modify = h > 0.0 ? h : 0.0;
+  return ORACLE_OK;
+}
+
+/*
+ * Classical-noise subtraction (Sec. II.B): the laser-off stream holds the classical noise alone,
+ * the quantum noise variance is sigma_q^2 = sigma_{q+c}^2 - sigma_c^2, and the ideal model of the
+ * quantum part is the Gaussian of that variance around the laser-on mean, discretised like the ADC.
+ * The report is the laser-on stream's (counts, moments, empirical entropy, distance to its own
+ * Gaussian model, finite-size term, correction) except h_model = -log2 max of the quantum model,
+ * h_modify = max(0, h_model - delta_hm) and var = sigma_q^2. *h_subtracted receives the paper's
+ * H^{q+c} - H'^c: the model min-entropy of the laser-on stream minus that of the laser-off stream.
+ */
+int oracle_minentropy_quantum_from_hist(const uint64_t* hist_on, const uint64_t* hist_off, int bits, double eps,
+                                        oracle_hmin_report* rep, double* h_subtracted) {
+  oracle_hmin_report off;
+  int st = oracle_minentropy_from_hist(hist_off, bits, eps, &off);
+  if (st) return st;
+  st = oracle_minentropy_from_hist(hist_on, bits, eps, rep);
+  if (st) return st;
+  double var_q = rep->var - off.var;
+  if (!(var_q > 0.0)) return ORACLE_EINVAL;
+  uint64_t K = 1ull << bits;
+  double* P = (double*)malloc(K * sizeof(double));
+  if (!P) return ORACLE_ENOMEM;
+  gaussian_cells(rep->mean, var_q, K, P);
+  double pmax = 0.0;
+  for (uint64_t v = 0; v < K; ++v)
+    if (P[v] > pmax) pmax = P[v];
+  free(P);
+  *h_subtracted = rep->h_model - off.h_model;
+  rep->h_model = -log2(pmax);
+  rep->var = var_q;
+  double h = rep->h_model - rep->delta_hm;
+  rep->h_modify = h > 0.0 ? h : 0.0;
+  return ORACLE_OK;
+}
+
+/* splitmix64 (Steele, Lea and Flood, 2014): output number s (s >= 1) of the generator started at x0. */
+uint64_t oracle_splitmix64(uint64_t x0, uint64_t s) {
+  uint64_t z = x0 + s * 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+/*
+ * Random subsample (Sec. II.C: the corrected entropy may be estimated from randomly selected
+ * samples): sample i (0-based) is kept when output i+1 of splitmix64 started at sel_seed, shifted
+ * right by 11 bits, is below floor(fraction * 2^53); fraction 1 keeps every sample.
+ */
+int oracle_histogram_sampled(const void* samples, uint64_t count, int bits, double fraction, uint64_t sel_seed,
+                             uint64_t* hist, uint64_t* out_of_range) {
+  if (bits < 1 || bits > 16 || !(fraction > 0.0 && fraction <= 1.0)) return ORACLE_EINVAL;
+  uint64_t K = 1ull << bits;
+  uint64_t thr = (uint64_t)floor(fraction * 9007199254740992.0);
+  memset(hist, 0, K * sizeof(uint64_t));
+  *out_of_range = 0;
+  for (uint64_t s = 0; s < count; ++s) {
+    if ((oracle_splitmix64(sel_seed, s + 1) >> 11) >= thr) continue;
+    uint64_t v = bits <= 8 ? ((const uint8_t*)samples)[s] : ((const uint16_t*)samples)[s];
+    if (v >= K) (*out_of_range)++;
+    else hist[v]++;
+  }
   return ORACLE_OK;
 }
 

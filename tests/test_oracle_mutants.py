@@ -12,6 +12,7 @@ import numpy as np
 import pytest
 
 import test_oracle_entropy as E
+import test_oracle_entropy_ext as X
 import test_oracle_toeplitz as T
 
 ORACLE_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "oracle")
@@ -33,6 +34,10 @@ MUTANTS = {
     "correction_wrong_power": ("ldexp(1.0, -bits - 1)", "ldexp(1.0, -bits)"),
     "finite_size_term_dropped": ("rep->delta_hm = log2((rep->d_u + rep->delta_fs)",
                                  "rep->delta_hm = log2((rep->d_u)"),
+    # entropy-side extensions
+    "quantum_variance_added": ("double var_q = rep->var - off.var;", "double var_q = rep->var + off.var;"),
+    "subsample_wrong_bits": (">> 11) >= thr) continue;", ">> 10) >= thr) continue;"),
+    "splitmix_wrong_shift": ("z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;", "z = (z ^ (z >> 28)) * 0x94D049BB133111EBull;"),
 }
 
 PINS = [
@@ -45,6 +50,9 @@ PINS = [
     (E.test_one_bit_source_closed_form, dict(h0=123456, h1=654321)),
     (E.test_reflection_invariance, dict(seed=2)),
     (E.test_flat_histogram_has_bits_of_entropy, dict(bits=8)),
+    (X.test_splitmix64_published_outputs, dict()),
+    (X.test_quantum_model_closed_form, dict()),
+    (X.test_subsample_is_binomial_and_matches_selection, dict(fraction=0.5, seed=1)),
 ]
 
 

@@ -112,6 +112,34 @@ QRNG_API int qrng_minentropy(qrng_ctx* ctx, const void* samples, uint64_t count,
                     qrng_hmin_report* rep, qrng_stream_t stream);
 
 /*
+ * qrng_minentropy_sampled -- the same estimate from a random subsample of the stream (Sec. II.C:
+ * the corrected entropy may be computed from randomly selected samples). Sample i (0-based) is
+ * used when output i+1 of the splitmix64 generator started at sel_seed, shifted right by 11 bits,
+ * is below floor(fraction * 2^53); fraction = 1 uses every sample. The finite-size term follows
+ * the number of samples kept (rep->count). 0 < fraction <= 1, otherwise as qrng_minentropy;
+ * QRNG_EINVAL if no sample is kept.
+ */
+QRNG_API int qrng_minentropy_sampled(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps,
+                                     double fraction, uint64_t sel_seed, qrng_hmin_report* rep,
+                                     qrng_stream_t stream);
+
+/*
+ * qrng_minentropy_quantum -- classical-noise subtraction (Sec. II.B): the laser-off stream holds
+ * the classical noise alone, so the quantum noise variance is var_on - var_off and the ideal
+ * model of the quantum part is the Gaussian of that variance around the laser-on mean, rounded
+ * and clipped to codes. rep is the laser-on stream's report (counts, moments, empirical entropy,
+ * its distance to its own Gaussian model, finite-size term, correction) except
+ *   rep->h_model  = -log2 max of the quantum model,  rep->var = var_on - var_off,
+ *   rep->h_modify = max(0, rep->h_model - rep->delta_hm).
+ * *h_subtracted (may be NULL) receives the paper's H^{q+c} - H'^c: the model min-entropy of the
+ * laser-on stream minus that of the laser-off stream. A laser-off stream without spread leaves
+ * the plain estimate. QRNG_EINVAL when var_off >= var_on > 0. Synchronises `stream`.
+ */
+QRNG_API int qrng_minentropy_quantum(qrng_ctx* ctx, const void* samples_on, uint64_t count_on,
+                                     const void* samples_off, uint64_t count_off, int bits, double eps,
+                                     qrng_hmin_report* rep, double* h_subtracted, qrng_stream_t stream);
+
+/*
  * qrng_minentropy_noalloc -- the same estimate and report as qrng_minentropy, for callers that
  * cannot allocate device memory. The paper has no counterpart; this is a deployment variant.
  *

@@ -23,7 +23,8 @@ ALGO_NAMES = {QRNG_ALGO_AUTO: "auto", QRNG_ALGO_DIRECT: "direct", QRNG_ALGO_GEMM
 EXPORTED = ["qrng_create", "qrng_destroy", "qrng_last_error", "qrng_status_string", "qrng_minentropy",
             "qrng_output_length", "qrng_seed_bits", "qrng_toeplitz_extract", "qrng_postprocess_host",
             "qrng_get_stats", "qrng_reset_stats", "qrng_set_timing", "qrng_synchronize",
-            "qrng_minentropy_noalloc", "qrng_extract_batch", "qrng_set_autotune", "qrng_inject_fault"]
+            "qrng_minentropy_noalloc", "qrng_extract_batch", "qrng_set_autotune", "qrng_inject_fault",
+            "qrng_minentropy_sampled", "qrng_minentropy_quantum"]
 QRNG_FAULT_NONE, QRNG_FAULT_GEMM_NO_TMA = 0, 1
 
 
@@ -114,6 +115,9 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qrng_set_timing.argtypes = [vp, i32]
     lib.qrng_synchronize.argtypes = [vp, vp]
     lib.qrng_set_autotune.argtypes = [vp, i32]
+    lib.qrng_minentropy_sampled.argtypes = [vp, vp, u64, i32, dbl, dbl, u64, ctypes.POINTER(HminReport), vp]
+    lib.qrng_minentropy_quantum.argtypes = [vp, vp, u64, vp, u64, i32, dbl, ctypes.POINTER(HminReport),
+                                            ctypes.POINTER(dbl), vp]
     lib.qrng_inject_fault.argtypes = [vp, i32]
     lib.qrng_extract_batch.argtypes = [vp, ctypes.POINTER(Request), u64, i32, vp]
     lib.qrng_minentropy_noalloc.argtypes = [vp, u64, i32, dbl, ctypes.POINTER(HminReport), vp]
@@ -296,3 +300,30 @@ def qrng_set_autotune(ctx: Context, on: bool):
 
 def qrng_inject_fault(ctx: Context, fault: int):
     ctx.check(load_library().qrng_inject_fault(ctx.handle, fault), "qrng_inject_fault")
+
+
+def qrng_minentropy_sampled(ctx: Context, samples, count: int | None = None, bits: int = 8, eps: float = 1e-6,
+                            fraction: float = 1.0, sel_seed: int = 0, stream=None) -> dict:
+    """Min-entropy report of a random subsample (splitmix64 selection) of device samples."""
+    if count is None:
+        count = samples.numel()
+    rep = HminReport()
+    st = load_library().qrng_minentropy_sampled(ctx.handle, _ptr(samples), count, bits, eps, fraction,
+                                                sel_seed & (2**64 - 1), ctypes.byref(rep), _stream(stream))
+    ctx.check(st, "qrng_minentropy_sampled")
+    return rep.as_dict()
+
+
+def qrng_minentropy_quantum(ctx: Context, samples_on, samples_off, count_on: int | None = None,
+                            count_off: int | None = None, bits: int = 8, eps: float = 1e-6, stream=None):
+    """Classical-noise subtraction: (report of the quantum model, H^{q+c} - H'^c)."""
+    if count_on is None:
+        count_on = samples_on.numel()
+    if count_off is None:
+        count_off = samples_off.numel()
+    rep = HminReport()
+    hs = ctypes.c_double()
+    st = load_library().qrng_minentropy_quantum(ctx.handle, _ptr(samples_on), count_on, _ptr(samples_off), count_off,
+                                                bits, eps, ctypes.byref(rep), ctypes.byref(hs), _stream(stream))
+    ctx.check(st, "qrng_minentropy_quantum")
+    return rep.as_dict(), hs.value

@@ -172,16 +172,24 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
   return QRNG_OK;
 }
 
+// Histogram (all samples, or the random subsample when thr < 2^53) + FP64 finaliser, report read back.
 int minentropy_dev(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps, qrng_hmin_report* rep,
-                   cudaStream_t s) {
+                   cudaStream_t s, uint64_t thr = 1ull << 53, uint64_t sel_seed = 0, double var_sub = 0.0,
+                   double h_ref = 0.0, double* h_subtracted = nullptr) {
   const uint64_t K = 1ull << bits;
   uint32_t kernels = 0;
   QRNG_CUDA(ctx, ctx->hist.ensure((K + 1) * sizeof(unsigned long long)), "histogram workspace");
   QRNG_CUDA(ctx, ctx->result.ensure(sizeof(DevHminResult)), "result workspace");
-  QRNG_CUDA(ctx, launch_histogram(samples, count, bits, ctx->hist.as<unsigned long long>(), ctx->num_sms, s, &kernels),
-            "histogram kernel");
+  if (thr >= (1ull << 53)) {
+    QRNG_CUDA(ctx, launch_histogram(samples, count, bits, ctx->hist.as<unsigned long long>(), ctx->num_sms, s, &kernels),
+              "histogram kernel");
+  } else {
+    QRNG_CUDA(ctx, launch_histogram_sampled(samples, count, bits, thr, sel_seed, ctx->hist.as<unsigned long long>(),
+                                            ctx->num_sms, s, &kernels),
+              "sampled histogram kernel");
+  }
   QRNG_CUDA(ctx, launch_hmin_finalize(ctx->hist.as<unsigned long long>(), bits, eps, ctx->result.as<DevHminResult>(),
-                                      s, &kernels),
+                                      s, &kernels, var_sub, h_ref),
             "min-entropy finaliser kernel");
   QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->result_host, ctx->result.p, sizeof(DevHminResult), cudaMemcpyDeviceToHost, s),
             "report copy");
@@ -190,8 +198,12 @@ int minentropy_dev(qrng_ctx* ctx, const void* samples, uint64_t count, int bits,
   const DevHminResult& r = *ctx->result_host;
   if (r.out_of_range)
     return fail(ctx, QRNG_EINVAL, "qrng_minentropy: " + std::to_string(r.out_of_range) + " samples are >= 2^bits");
-  if (r.status != QRNG_OK) return fail(ctx, r.status, "qrng_minentropy: finaliser reported an error");
+  if (r.status != QRNG_OK)
+    return fail(ctx, r.status,
+                var_sub > 0.0 ? "qrng_minentropy_quantum: the laser-off variance is not below the laser-on variance"
+                              : "qrng_minentropy: finaliser reported an error (no sample selected?)");
   *rep = r.rep;
+  if (h_subtracted) *h_subtracted = r.h_subtracted;
   return QRNG_OK;
 }
 
@@ -661,6 +673,40 @@ int qrng_minentropy(qrng_ctx* ctx, const void* samples, uint64_t count, int bits
   if (st) return st;
   QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
   return minentropy_dev(ctx, samples, count, bits, eps, rep, static_cast<cudaStream_t>(stream));
+}
+
+int qrng_minentropy_sampled(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps, double fraction,
+                            uint64_t sel_seed, qrng_hmin_report* rep, qrng_stream_t stream) {
+  if (!ctx) return QRNG_EINVAL;
+  int st = check_minentropy_args(ctx, samples, count, bits, eps, rep);
+  if (st) return st;
+  if (!(fraction > 0.0 && fraction <= 1.0))
+    return fail(ctx, QRNG_EINVAL, "qrng_minentropy_sampled: fraction must be in (0, 1]");
+  QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+  const uint64_t thr = (uint64_t)floor(fraction * 9007199254740992.0);  // fraction * 2^53
+  return minentropy_dev(ctx, samples, count, bits, eps, rep, static_cast<cudaStream_t>(stream), thr, sel_seed);
+}
+
+int qrng_minentropy_quantum(qrng_ctx* ctx, const void* samples_on, uint64_t count_on, const void* samples_off,
+                            uint64_t count_off, int bits, double eps, qrng_hmin_report* rep, double* h_subtracted,
+                            qrng_stream_t stream) {
+  if (!ctx) return QRNG_EINVAL;
+  int st = check_minentropy_args(ctx, samples_on, count_on, bits, eps, rep);
+  if (st) return st;
+  qrng_hmin_report off{};
+  st = check_minentropy_args(ctx, samples_off, count_off, bits, eps, &off);
+  if (st) return st;
+  QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  st = minentropy_dev(ctx, samples_off, count_off, bits, eps, &off, s);
+  if (st) return st;
+  // var_sub > 0 selects the quantum model; a noiseless laser-off stream leaves the plain estimate
+  const double var_sub = off.var > 0.0 ? off.var : 0.0;
+  double hs = 0.0;
+  st = minentropy_dev(ctx, samples_on, count_on, bits, eps, rep, s, 1ull << 53, 0, var_sub, off.h_model, &hs);
+  if (st) return st;
+  if (h_subtracted) *h_subtracted = hs;
+  return QRNG_OK;
 }
 
 uint64_t qrng_output_length(uint64_t n, double h_per_sample, int bits, double eps_lhl) {

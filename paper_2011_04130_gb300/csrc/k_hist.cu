@@ -113,7 +113,8 @@ __device__ __forceinline__ double model_cell(uint32_t v, uint32_t K, double mu, 
 
 __global__ void __launch_bounds__(kFinThreads) hmin_finalize_kernel(const unsigned long long* __restrict__ hist,
                                                                      int bits, double eps,
-                                                                     DevHminResult* __restrict__ out) {
+                                                                     DevHminResult* __restrict__ out, double var_sub,
+                                                                     double h_ref) {
   typedef unsigned __int128 u128;
   __shared__ unsigned long long s_n[kFinThreads];
   __shared__ unsigned long long s_max[kFinThreads];
@@ -121,9 +122,10 @@ __global__ void __launch_bounds__(kFinThreads) hmin_finalize_kernel(const unsign
   __shared__ u128 s_s1[kFinThreads];
   __shared__ u128 s_s2[kFinThreads];
   __shared__ double s_pmax[kFinThreads];
+  __shared__ double s_pmax_full[kFinThreads];
   __shared__ double s_dsum[kFinThreads];
-  __shared__ double s_mu, s_sigma;
-  __shared__ int s_point;
+  __shared__ double s_mu, s_sigma, s_sigma_q;
+  __shared__ int s_point, s_bad_sub;
 
   const uint32_t K = 1u << bits;
   const int t = threadIdx.x;
@@ -171,6 +173,9 @@ __global__ void __launch_bounds__(kFinThreads) hmin_finalize_kernel(const unsign
     s_mu = mu;
     s_sigma = sqrt(var);
     s_point = (num == 0);
+    const double var_q = var - var_sub;
+    s_bad_sub = (var_sub > 0.0) && !(var_q > 0.0);
+    s_sigma_q = var_sub > 0.0 && var_q > 0.0 ? sqrt(var_q) : s_sigma;
     qrng_hmin_report& r = out->rep;
     r.count = N;
     r.max_count = s_max[0];
@@ -186,19 +191,23 @@ __global__ void __launch_bounds__(kFinThreads) hmin_finalize_kernel(const unsign
   // Pass 2: model cells, their maximum, and the distance to the measured distribution.
   const double mu = s_mu, sigma = s_sigma;
   const int point = s_point;
+  const bool sub = var_sub > 0.0 && !s_bad_sub;
   const uint32_t amax = s_arg[0];
-  double pmax = 0.0, dsum = 0.0;
+  double pmax = 0.0, pmax_full = 0.0, dsum = 0.0;
   for (uint32_t v = t; v < K; v += kFinThreads) {
-    double P = point ? (v == amax ? 1.0 : 0.0) : model_cell(v, K, mu, sigma);
-    pmax = fmax(pmax, P);
+    const double P = point ? (v == amax ? 1.0 : 0.0) : model_cell(v, K, mu, sigma);
+    pmax_full = fmax(pmax_full, P);
+    pmax = sub ? fmax(pmax, model_cell(v, K, mu, s_sigma_q)) : pmax_full;
     dsum += fabs((double)hist[v] / (double)N - P);
   }
   s_pmax[t] = pmax;
+  s_pmax_full[t] = pmax_full;
   s_dsum[t] = dsum;
   __syncthreads();
   for (int w = kFinThreads / 2; w > 0; w >>= 1) {
     if (t < w) {
       s_pmax[t] = fmax(s_pmax[t], s_pmax[t + w]);
+      s_pmax_full[t] = fmax(s_pmax_full[t], s_pmax_full[t + w]);
       s_dsum[t] += s_dsum[t + w];
     }
     __syncthreads();
@@ -206,6 +215,8 @@ __global__ void __launch_bounds__(kFinThreads) hmin_finalize_kernel(const unsign
   if (t == 0) {
     qrng_hmin_report& r = out->rep;
     r.h_model = -log2(s_pmax[0]);
+    out->h_subtracted = -log2(s_pmax_full[0]) - h_ref;
+    if (sub) r.var = s_sigma_q * s_sigma_q;
     r.d_u = 0.5 * s_dsum[0];
     double Pa = point ? 1.0 : model_cell(amax, K, mu, sigma);
     r.d_u_peak = 0.5 * fabs((double)s_max[0] / (double)N - Pa);
@@ -213,7 +224,39 @@ __global__ void __launch_bounds__(kFinThreads) hmin_finalize_kernel(const unsign
     r.delta_hm = log2((r.d_u + r.delta_fs) * ldexp(1.0, bits + 1) + 1.0);
     double h = r.h_model - r.delta_hm;
     r.h_modify = h > 0.0 ? h : 0.0;
-    out->status = out->out_of_range ? QRNG_EINVAL : QRNG_OK;
+    out->status = (out->out_of_range || s_bad_sub) ? QRNG_EINVAL : QRNG_OK;
+  }
+}
+
+// Random subsample (any width): counters in shared memory for up to 2^13 codes, else global.
+__global__ void __launch_bounds__(kHistThreads) hist_sampled_kernel(const void* __restrict__ samples, uint64_t count,
+                                                                     int bits, uint64_t thr, uint64_t sel_seed,
+                                                                     unsigned long long* __restrict__ hist) {
+  extern __shared__ uint32_t shs[];
+  const uint32_t K = 1u << bits;
+  const bool smem = bits <= 13;
+  if (smem) {
+    for (uint32_t i = threadIdx.x; i <= K; i += blockDim.x) shs[i] = 0;
+    __syncthreads();
+  }
+  const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t s = tid; s < count; s += nthreads) {
+    // splitmix64 output s+1 of the generator started at sel_seed
+    uint64_t z = sel_seed + (s + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    if ((z >> 11) >= thr) continue;
+    const uint32_t v = bits <= 8 ? static_cast<const uint8_t*>(samples)[s] : static_cast<const uint16_t*>(samples)[s];
+    const uint32_t c = v < K ? v : K;
+    if (smem) atomicAdd(&shs[c], 1u);
+    else atomicAdd(&hist[c], 1ull);
+  }
+  if (smem) {
+    __syncthreads();
+    for (uint32_t b = threadIdx.x; b <= K; b += blockDim.x)
+      if (shs[b]) atomicAdd(&hist[b], (unsigned long long)shs[b]);
   }
 }
 
@@ -240,9 +283,23 @@ cudaError_t launch_histogram(const void* samples, uint64_t count, int bits, unsi
   return cudaGetLastError();
 }
 
+cudaError_t launch_histogram_sampled(const void* samples, uint64_t count, int bits, uint64_t thr, uint64_t sel_seed,
+                                     unsigned long long* hist, int num_sms, cudaStream_t s, uint32_t* kernels) {
+  const uint32_t K = 1u << bits;
+  cudaError_t e = cudaMemsetAsync(hist, 0, (K + 1) * sizeof(unsigned long long), s);
+  if (e != cudaSuccess) return e;
+  uint64_t want = ceil_div(count, (uint64_t)kHistThreads * 16);
+  uint64_t cap = (uint64_t)num_sms * 4;
+  int grid = (int)(want < cap ? (want ? want : 1) : cap);
+  const size_t smem = bits <= 13 ? (K + 1) * sizeof(uint32_t) : 0;
+  hist_sampled_kernel<<<grid, kHistThreads, smem, s>>>(samples, count, bits, thr, sel_seed, hist);
+  ++*kernels;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_hmin_finalize(const unsigned long long* hist, int bits, double eps, DevHminResult* out,
-                                 cudaStream_t s, uint32_t* kernels) {
-  hmin_finalize_kernel<<<1, kFinThreads, 0, s>>>(hist, bits, eps, out);
+                                 cudaStream_t s, uint32_t* kernels, double var_sub, double h_ref) {
+  hmin_finalize_kernel<<<1, kFinThreads, 0, s>>>(hist, bits, eps, out, var_sub, h_ref);
   ++*kernels;
   return cudaGetLastError();
 }

@@ -56,14 +56,22 @@ struct DevHminResult {
   qrng_hmin_report rep;
   unsigned long long out_of_range;
   int status;
+  double h_subtracted;  // classical-noise route: model entropy of this stream minus h_ref
 };
 
 // ---- histogram + finaliser (k_hist.cu) ----
 // hist: (2^bits + 1) uint64 counters, the last one counts samples >= 2^bits. Zeroed by the launcher.
 cudaError_t launch_histogram(const void* samples, uint64_t count, int bits, unsigned long long* hist, int num_sms,
                              cudaStream_t s, uint32_t* kernels);
+// var_sub > 0: the model entropy is that of the Gaussian with the measured variance minus var_sub
+// (classical-noise subtraction), the distance stays the one to the measured-variance model, and
+// h_subtracted = (model entropy at the measured variance) - h_ref.
 cudaError_t launch_hmin_finalize(const unsigned long long* hist, int bits, double eps, DevHminResult* out,
-                                 cudaStream_t s, uint32_t* kernels);
+                                 cudaStream_t s, uint32_t* kernels, double var_sub = 0.0, double h_ref = 0.0);
+// Histogram of the samples kept by the random selection: sample i is kept when output i+1 of
+// splitmix64 started at sel_seed, shifted right by 11, is below thr (thr = 2^53 keeps all).
+cudaError_t launch_histogram_sampled(const void* samples, uint64_t count, int bits, uint64_t thr, uint64_t sel_seed,
+                                     unsigned long long* hist, int num_sms, cudaStream_t s, uint32_t* kernels);
 
 // ---- bit layout helpers (k_bits.cu) ----
 // Bit-reversed, padded copy of seed bits [0, L): word kSeedFrontWords+w, bit t holds a[L-1-(32w+t)]

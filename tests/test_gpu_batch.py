@@ -152,6 +152,26 @@ def test_batch_matches_single_block_calls(qlib, gpu):
     assert torch.equal(out, ref)
 
 
+@pytest.mark.parametrize("algo", [0, 1, 5, 3])
+def test_single_and_degenerate_requests(qlib, gpu, oracle_mod, algo):
+    """One-bit outputs, n = 1 and n = 2 blocks, m = n standard, m = n - 1 modified, on every route."""
+    shapes = [(1, 1, STD), (2, 1, MOD), (2, 2, STD), (33, 1, STD), (64, 63, MOD), (100, 100, STD)]
+    n = np.array([s[0] for s in shapes])
+    m = np.array([s[1] for s in shapes])
+    forms = np.array([s[2] for s in shapes])
+    raw_offs, pos = [], 3
+    for i in range(len(shapes)):
+        raw_offs.append(pos)
+        pos += int(n[i]) + 5
+    raw = W.random_bits(pos + 64, 8)
+    seeds = [W.random_bits(int(n[i] + m[i] - 1) if forms[i] == STD else int(n[i] - 1) or 1, 40 + i)
+             for i in range(len(shapes))]
+    out_offs = list(np.concatenate([[1], 1 + np.cumsum(m)[:-1]]))
+    batch = (n, m, forms, raw, raw_offs, seeds, [int(x) for x in out_offs], int(1 + m.sum()))
+    host, _ = _run(qlib, gpu, batch, algo=algo)
+    _check(oracle_mod, batch, host)
+
+
 def test_batch_bad_arguments(qlib, gpu):
     import torch
 

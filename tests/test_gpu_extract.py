@@ -263,6 +263,37 @@ def test_bad_arguments(qlib, gpu):
         qlib.qrng_toeplitz_extract(gpu, 0, 64, 8, t, STD, 1, 1, t)
 
 
+@pytest.mark.parametrize("bits,form", [(12, MOD), (5, STD)])
+def test_postprocess_host_other_widths(qlib, gpu, oracle_mod, bits, form):
+    """12-bit samples travel as little-endian uint16 and 5-bit ones as bytes; the raw stream is the
+    sample buffer's bytes either way."""
+    samples = W.adc_samples(300_000, 33 + bits, mu=(1 << bits) / 2, sigma=(1 << bits) / 12, bits=bits)
+    raw = samples.view(np.uint8)
+    n = 2048
+    seed = W.random_bits(2 * n - 1, 34)
+    out = np.zeros(raw.size, dtype=np.uint8)
+    m, B, rep = qlib.qrng_postprocess_host(gpu, samples, samples.size, bits, 1e-6, 2.0 ** -20, n, seed, 2 * n - 1,
+                                           form, qlib.QRNG_ALGO_AUTO, out, out.size)
+    ref = oracle_mod.minentropy(samples, bits, 1e-6)
+    want_m = oracle_mod.output_length(n, ref["h_modify"], bits, 2.0 ** -20)
+    if form == MOD:
+        want_m = min(want_m, n - 1)
+    assert m == want_m and B == raw.size * 8 // n
+    want = oracle_mod.toeplitz_blocks(raw, n, m, seed, form, B)
+    assert np.array_equal(out[:want.size], want)
+
+
+def test_postprocess_host_reports_zero_output(qlib, gpu):
+    """A corrected entropy that leaves no output bits is an error, with m = 0 reported."""
+    samples = W.adc_samples(2000, 3)  # few samples: the finite-size term swamps the entropy
+    seed = W.random_bits(8191, 1)
+    out = np.zeros(16, dtype=np.uint8)
+    with pytest.raises(qlib.QrngError) as e:
+        qlib.qrng_postprocess_host(gpu, samples, samples.size, 8, 1e-6, 2.0 ** -40, 4096, seed, 8191, STD,
+                                   qlib.QRNG_ALGO_AUTO, out, out.size)
+    assert e.value.status == qlib.QRNG_EINVAL
+
+
 def test_postprocess_host_pipeline(qlib, gpu, oracle_mod):
     """Host buffers in, host buffer out: entropy, sizing and extraction in one call."""
     c = W.CFG1

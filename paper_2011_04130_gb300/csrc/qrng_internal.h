@@ -166,7 +166,6 @@ cudaError_t launch_fft64(const DirectArgs& a, const uint8_t* seed, uint64_t L_t,
                          uint32_t* kernels);
 cudaError_t launch_ntt(const DirectArgs& a, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
                        uint32_t* kernels);
-struct BatchReq;
 // Requests reqs_dev[0..nr) (own seeds, all with transform length P) by NTT into their word-aligned
 // output staging.
 cudaError_t launch_ntt_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P,

@@ -22,7 +22,7 @@
 namespace qrng {
 namespace {
 
-constexpr int kR = 16;           // output words per warp (= outputs per lane)
+constexpr int kR = 32;           // output words per warp (= outputs per lane)
 constexpr int kWarpsPerCta = 4;
 
 // Parities of the 32R outputs i0 .. i0+32R-1 (i0 = 32 R tile) over raw words [w_begin, w_end) of

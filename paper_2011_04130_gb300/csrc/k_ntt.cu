@@ -137,6 +137,48 @@ __global__ void ntt_pass4_kernel(const uint32_t* __restrict__ x, uint32_t* __res
   yb[3 * L] = sub_mod(d02, d13);
 }
 
+// The same radix-4 pass with four consecutive butterflies (k .. k+3, same g) per thread, moved as
+// 16-byte vectors: four times the loads in flight per thread. Needs L >= 4 and P >= 16.
+__global__ void ntt_pass4_vec_kernel(const uint32_t* __restrict__ x, uint32_t* __restrict__ y,
+                                     const uint32_t* __restrict__ tw, uint64_t P, uint32_t logL, uint32_t logP,
+                                     int inverse, uint64_t total4) {
+  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= total4) return;
+  const uint64_t quarter = P >> 2, half = P >> 1;
+  const uint64_t b = idx >> (logP - 4);
+  const uint64_t j0 = (idx & ((quarter >> 2) - 1)) << 2;
+  const uint64_t L = 1ull << logL;
+  const uint64_t k0 = j0 & (L - 1);
+  const uint64_t g = j0 >> logL;
+  const uint32_t* xb = x + b * P;
+  uint4 v[4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) v[q] = *reinterpret_cast<const uint4*>(xb + j0 + q * quarter);
+  const uint32_t im = inverse ? kP - tw[quarter] : tw[quarter];
+  uint32_t o[4][4];
+#pragma unroll
+  for (int e = 0; e < 4; ++e) {
+    const uint64_t stride = (k0 + e) << (logP - 2 - logL);
+    uint32_t bq[4];
+    bq[0] = (&v[0].x)[e];
+#pragma unroll
+    for (int q = 1; q < 4; ++q) {
+      const uint64_t t = (uint64_t)q * stride;
+      const uint32_t w = inverse ? (t == 0 ? tw[0] : ntt_root(tw, half, P - t)) : ntt_root(tw, half, t);
+      bq[q] = mont_mul(w, (&v[q].x)[e]);
+    }
+    const uint32_t s02 = add_mod(bq[0], bq[2]), d02 = sub_mod(bq[0], bq[2]);
+    const uint32_t s13 = add_mod(bq[1], bq[3]), d13 = mont_mul(im, sub_mod(bq[1], bq[3]));
+    o[0][e] = add_mod(s02, s13);
+    o[1][e] = add_mod(d02, d13);
+    o[2][e] = sub_mod(s02, s13);
+    o[3][e] = sub_mod(d02, d13);
+  }
+  uint32_t* yb = y + b * P + (g << (logL + 2)) + k0;
+#pragma unroll
+  for (int r = 0; r < 4; ++r) *reinterpret_cast<uint4*>(yb + r * L) = make_uint4(o[r][0], o[r][1], o[r][2], o[r][3]);
+}
+
 __global__ void ntt_seed_kernel(const uint8_t* __restrict__ seed, uint64_t L, uint32_t* __restrict__ z, uint64_t P) {
   const uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= P) return;
@@ -204,8 +246,13 @@ cudaError_t run_ntt(uint32_t* a, uint32_t* b, const uint32_t* tw, uint64_t P, ui
   uint32_t* y = b;
   for (uint32_t logL = 0; logL < logP;) {
     if (logP - logL >= 2) {  // radix 4 while two factors of 2 remain, then one radix-2 pass
-      const uint64_t total = batch * (P >> 2);
-      ntt_pass4_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total);
+      if (logL >= 2 && logP >= 4) {
+        const uint64_t total4 = batch * (P >> 4);
+        ntt_pass4_vec_kernel<<<grid_for(total4, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total4);
+      } else {
+        const uint64_t total = batch * (P >> 2);
+        ntt_pass4_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total);
+      }
       logL += 2;
     } else {
       const uint64_t total = batch * (P >> 1);

@@ -184,9 +184,11 @@ enum {
   QRNG_ALGO_FFT64 = 3,    /* circulant embedding + FP64 FFT convolution per block (Sec. III.B-D) */
   QRNG_ALGO_FFT32_SEG = 4,/* FP32 FFT over short segments with a proven rounding bound, parities
                              of the segments XOR-combined                                          */
-  QRNG_ALGO_NTT = 5       /* the circulant convolution of Sec. III.B with a number-theoretic
+  QRNG_ALGO_NTT = 5,      /* the circulant convolution of Sec. III.B with a number-theoretic
                              transform mod 2013265921 (exact integers, integer pipes); lengths up
                              to 2^27                                                                */
+  QRNG_ALGO_GEMM_FP4 = 6  /* QRNG_ALGO_GEMM_TC with 4-bit operands (block-scaled E2M1, every scale
+                             2^0): half the operand bytes and the FP4 tensor rate; same limits     */
 };
 
 /* Seed length in bits: n+m-1 (standard) or n-1 (modified); 0 for an invalid shape. */

@@ -179,8 +179,10 @@ cudaError_t launch_fft32_seg(const DirectArgs& a, const uint8_t* seed, uint64_t 
 // ---- tensor-core block-batched extraction (k_gemm_tc.cu) ----
 // Same layout arguments as the direct kernel (splits unused). Exact for n_t <= kGemmMaxColumns.
 constexpr uint64_t kGemmMaxColumns = 1ull << 22;
-size_t gemm_tc_smem_bytes();
-cudaError_t launch_gemm_tc(const DirectArgs& a, int* err, int fault, int num_sms, cudaStream_t s, uint32_t* kernels);
+// fp4 selects the block-scaled E2M1 operand encoding (kind::mxf4) over E4M3 (kind::f8f6f4).
+size_t gemm_tc_smem_bytes(bool fp4);
+cudaError_t launch_gemm_tc(const DirectArgs& a, bool fp4, int* err, int fault, int num_sms, cudaStream_t s,
+                           uint32_t* kernels);
 
 }  // namespace qrng
 

@@ -14,7 +14,8 @@ from gpu_util import extract, spot_check
 pytestmark = pytest.mark.gpu
 
 STD, MOD = 0, 1
-ALGOS = {"direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4, "ntt": 5}
+ALGOS = {"direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4, "ntt": 5, "gemm_fp4": 6}
+GEMMS = {"gemm_tc": 2, "gemm_fp4": 6}
 
 
 def _seed_len(n, m, form):
@@ -83,19 +84,34 @@ def test_all_ones(qlib, gpu, oracle_mod, algo):
     assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, STD, ALGOS[algo], B), want)
 
 
-@pytest.mark.parametrize("n,m,B", [(1 << 16, 4096, 300), (1 << 22, 1024, 8)])
-def test_gemm_all_ones_largest_sums(qlib, gpu, oracle_mod, n, m, B):
+@pytest.mark.parametrize("gemm", list(GEMMS))
+@pytest.mark.parametrize("n,m,B", [(1 << 16, 4096, 300), (1 << 22, 1024, 8), ((1 << 22) - 96, 1000, 3)])
+def test_gemm_all_ones_largest_sums(qlib, gpu, oracle_mod, gemm, n, m, B):
     """All-ones raw and seed make every tensor-core sum equal to n, the largest count the FP32
     accumulator has to hold exactly; each output is the parity of n."""
     raw = np.full(n * B // 8, 0xFF, dtype=np.uint8)
     seed = W.pack_bits(np.ones(n + m - 1, dtype=np.uint8))
-    got = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_GEMM_TC, B)
+    got = extract(qlib, gpu, raw, n, m, seed, STD, GEMMS[gemm], B)
     want = np.zeros(m * B, dtype=np.uint8) + (n & 1)
     assert np.array_equal(np.unpackbits(got, bitorder="little")[:m * B], want)
     # and a random seed with all-ones raw bits: each output is the parity of a seed window
     seed = W.random_bits(n + m - 1, 5)
-    got = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_GEMM_TC, B)
+    got = extract(qlib, gpu, raw, n, m, seed, STD, GEMMS[gemm], B)
     spot_check(oracle_mod, raw, n, m, seed, STD, got, blocks=[0, B - 1], per_block=64)
+
+
+@pytest.mark.parametrize("gemm", list(GEMMS))
+def test_gemm_full_occupancy_repeated(qlib, gpu, gemm):
+    """Every SM busy (one or two tiles per CTA), long K (n = 2^16), repeated: the pipelines that
+    hand raw tiles and operand stages between warps are exercised at full speed. The output equals
+    the direct kernel's on every repetition."""
+    n = 1 << 16
+    for m, B in ((2048, 224 * 19), (4096, 256 * 19)):
+        raw = W.random_bits(n * B, 321 + m)
+        seed = W.random_bits(n + m - 1, 654 + m)
+        ref = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_DIRECT, B)
+        for _ in range(3):
+            assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, STD, GEMMS[gemm], B), ref)
 
 
 @pytest.mark.parametrize("algo", list(ALGOS))
@@ -174,12 +190,13 @@ def test_auto_tunes_once_per_shape(qlib, gpu, oracle_mod):
     qlib.qrng_set_autotune(gpu, True)
 
 
-def test_gemm_rejects_too_long_blocks(qlib, gpu):
+@pytest.mark.parametrize("gemm", list(GEMMS))
+def test_gemm_rejects_too_long_blocks(qlib, gpu, gemm):
     import torch
 
     t = torch.zeros(16, dtype=torch.uint8, device="cuda")
     with pytest.raises(qlib.QrngError) as e:
-        qlib.qrng_toeplitz_extract(gpu, t, (1 << 22) + 32, 8, t, STD, qlib.QRNG_ALGO_GEMM_TC, 1, t)
+        qlib.qrng_toeplitz_extract(gpu, t, (1 << 22) + 32, 8, t, STD, GEMMS[gemm], 1, t)
     assert e.value.status == qlib.QRNG_ENOTSUP
 
 

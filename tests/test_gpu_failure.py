@@ -13,7 +13,8 @@ from gpu_util import extract, to_dev
 pytestmark = pytest.mark.gpu
 
 
-def test_timeout_reported_and_context_recovers(qlib, gpu):
+@pytest.mark.parametrize("gemm", [2, 6])  # QRNG_ALGO_GEMM_TC, QRNG_ALGO_GEMM_FP4
+def test_timeout_reported_and_context_recovers(qlib, gpu, gemm):
     import torch
 
     n, m, B = 4096, 2048, 256
@@ -24,14 +25,14 @@ def test_timeout_reported_and_context_recovers(qlib, gpu):
     out = torch.zeros(m * B // 8, dtype=torch.uint8, device="cuda")
     qlib.qrng_inject_fault(gpu, qlib.QRNG_FAULT_GEMM_NO_TMA)
     t0 = time.monotonic()
-    qlib.qrng_toeplitz_extract(gpu, raw_p, n, m, seed_p, 0, qlib.QRNG_ALGO_GEMM_TC, B, out)
+    qlib.qrng_toeplitz_extract(gpu, raw_p, n, m, seed_p, 0, gemm, B, out)
     with pytest.raises(qlib.QrngError) as e:
         qlib.qrng_synchronize(gpu)
     assert e.value.status == qlib.QRNG_ETIMEOUT
     assert time.monotonic() - t0 < 60
     # the condition is cleared and the same context computes correctly again
     qlib.qrng_synchronize(gpu)
-    got = extract(qlib, gpu, raw, n, m, seed, 0, qlib.QRNG_ALGO_GEMM_TC, B)
+    got = extract(qlib, gpu, raw, n, m, seed, 0, gemm, B)
     ref = extract(qlib, gpu, raw, n, m, seed, 0, qlib.QRNG_ALGO_DIRECT, B)
     assert np.array_equal(got, ref)
 

@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--workload", default="laser", choices=["laser", "single", "sweep", "tc", "uneven", "forms"],
                    help="laser: the headline stream (default); single: one 4096-bit block; sweep: block-length "
                         "sweep on a 2^30-bit stream; tc: m=6144, n=8192, 4096 blocks; uneven: 10,000 requests")
-    p.add_argument("--sweep-algos", default="direct,gemm_tc,gemm_fp4,ntt,fft64",
+    p.add_argument("--sweep-algos", default="direct,gemm_tc,gemm_fp4,gemm_fp4_pair,ntt,fft64",
                    help="algorithms timed at each block length of the sweep")
     p.add_argument("--uneven-max-log2n", type=float, default=22.0,
                    help="upper end of the log-uniform n range of the uneven requests")
@@ -290,7 +290,8 @@ def run_ours(args, world, rank, local):
 
 
 DTYPES = {"gemm_tc": "e4m3 0/1 operands, f32 accumulate",
-          "gemm_fp4": "e2m1 0/1 operands (ue8m0 scales 2^0), f32 accumulate"}
+          "gemm_fp4": "e2m1 0/1 operands (ue8m0 scales 2^0), f32 accumulate",
+          "gemm_fp4_pair": "e2m1 0/1 operands (ue8m0 scales 2^0), f32 accumulate"}
 
 
 def measured_peaks():
@@ -336,14 +337,17 @@ def roofline_for(algo, num_blocks, m, n, kernel_ms):
                 "traffic": captured_traffic("gemm_tc_kernel", "k_gemm_tc.cu", num_blocks),
                 "kernel": "gemm_tc_kernel (tcgen05 kind::f8f6f4)", "kernel_ms": kernel_ms,
                 "peak_source": "FP8 = 2 x bf16 burst " + pk["source"]}
-    if algo == "gemm_fp4":
+    if algo in ("gemm_fp4", "gemm_fp4_pair"):
         pk = measured_peaks()
         peak = 6.0 * pk["bf16_tflops"]  # FP4 dense = bf16 measured x nominal ratio 13.5/2.25
         achieved = 2.0 * num_blocks * m * n / (kernel_ms / 1e3) / 1e12
+        pair = algo == "gemm_fp4_pair"
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": captured_traffic("gemm_fp4_kernel", "k_gemm_tc.cu", num_blocks),
-                "kernel": "gemm_tc_kernel<fp4> (tcgen05 kind::mxf4, block scale 2^0)", "kernel_ms": kernel_ms,
-                "peak_source": "FP4 = 6 x bf16 burst " + pk["source"]}
+                "traffic": (captured_traffic("gemm_pair_kernel", "k_gemm_pair.cu", num_blocks) if pair
+                            else captured_traffic("gemm_fp4_kernel", "k_gemm_tc.cu", num_blocks)),
+                "kernel": ("gemm_pair_kernel (tcgen05 cta_group::2 kind::mxf4, block scale 2^0)" if pair
+                           else "gemm_tc_kernel<fp4> (tcgen05 kind::mxf4, block scale 2^0)"),
+                "kernel_ms": kernel_ms, "peak_source": "FP4 = 6 x bf16 burst " + pk["source"]}
     return {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
             "kernel_ms": kernel_ms}
 
@@ -402,7 +406,8 @@ def run_reference(args, world, rank):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
-ALGOS = {"auto": 0, "direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4, "ntt": 5, "gemm_fp4": 6}
+ALGOS = {"auto": 0, "direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4, "ntt": 5, "gemm_fp4": 6,
+         "gemm_fp4_pair": 7}
 
 
 def _time_extract(q, ctx, raw, n, m, seed, form, algo, blocks, out, reps, warmup=1):
@@ -482,7 +487,7 @@ def run_forms(args):
                 L = n + m - 1 if form == 0 else n - 1
                 seed = torch.from_numpy(W.random_bits(L, 99)).cuda()
                 row[fname] = {"seed_bits": L}
-                for name in ("direct", "gemm_tc", "gemm_fp4", "ntt"):
+                for name in ("direct", "gemm_tc", "gemm_fp4", "gemm_fp4_pair", "ntt"):
                     kms, cms, _ = _time_extract(q, ctx, raw, n, m, seed, form, ALGOS[name], B, out, reps=2)
                     row[fname][name] = {"call_ms": cms, "gbps": B * m / (cms / 1e3) / 1e9}
             rows.append(row)
@@ -506,12 +511,12 @@ def run_tc(args):
     out = torch.empty(m * B // 8, dtype=torch.uint8, device="cuda")
     res = {"workload": "m=6144, n=8192, 4096 blocks, one standard seed", "unit": UNIT, "data": "synthetic"}
     pk = measured_peaks()
-    for name in ("gemm_fp4", "gemm_tc", "direct"):
+    for name in ("gemm_fp4_pair", "gemm_fp4", "gemm_tc", "direct"):
         kms, cms, _ = _time_extract(q, ctx, raw, n, m, seed, 0, ALGOS[name], B, out, reps=args.steps)
         res[name] = {"kernel_ms": kms, "gbps": B * m / (kms / 1e3) / 1e9}
         if name.startswith("gemm"):
             tf = 2.0 * m * n * B / (kms / 1e3) / 1e12
-            ratio = 6.0 if name == "gemm_fp4" else 2.0  # nominal FP4 / FP8 dense rates over bf16
+            ratio = 6.0 if name.startswith("gemm_fp4") else 2.0  # nominal FP4 / FP8 dense rates over bf16
             res[name].update({"tflops": tf, "frac_of_peak": tf / (ratio * pk["bf16_tflops"]),
                               "peak_source": f"{ratio:g} x bf16 burst {pk['source']}"})
     ctx.close()

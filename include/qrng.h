@@ -187,8 +187,10 @@ enum {
   QRNG_ALGO_NTT = 5,      /* the circulant convolution of Sec. III.B with a number-theoretic
                              transform mod 2013265921 (exact integers, integer pipes); lengths up
                              to 2^27                                                                */
-  QRNG_ALGO_GEMM_FP4 = 6  /* QRNG_ALGO_GEMM_TC with 4-bit operands (block-scaled E2M1, every scale
+  QRNG_ALGO_GEMM_FP4 = 6, /* QRNG_ALGO_GEMM_TC with 4-bit operands (block-scaled E2M1, every scale
                              2^0): half the operand bytes and the FP4 tensor rate; same limits     */
+  QRNG_ALGO_GEMM_FP4_PAIR = 7 /* QRNG_ALGO_GEMM_FP4 with each MMA spanning a pair of SMs (clusters
+                             of two CTAs, M = 256): fewer shared-memory bytes per MAC; same limits */
 };
 
 /* Seed length in bits: n+m-1 (standard) or n-1 (modified); 0 for an invalid shape. */

@@ -17,10 +17,10 @@ LIB_PATH = os.path.join(_PKG, "libqrng_gb300.so")
 QRNG_OK, QRNG_EINVAL, QRNG_ENOMEM, QRNG_ECUDA, QRNG_ETIMEOUT, QRNG_EPRECISION, QRNG_ENOTSUP = range(7)
 QRNG_FORM_STANDARD, QRNG_FORM_MODIFIED = 0, 1
 (QRNG_ALGO_AUTO, QRNG_ALGO_DIRECT, QRNG_ALGO_GEMM_TC, QRNG_ALGO_FFT64, QRNG_ALGO_FFT32_SEG, QRNG_ALGO_NTT,
- QRNG_ALGO_GEMM_FP4) = range(7)
+ QRNG_ALGO_GEMM_FP4, QRNG_ALGO_GEMM_FP4_PAIR) = range(8)
 ALGO_NAMES = {QRNG_ALGO_AUTO: "auto", QRNG_ALGO_DIRECT: "direct", QRNG_ALGO_GEMM_TC: "gemm_tc",
               QRNG_ALGO_FFT64: "fft64", QRNG_ALGO_FFT32_SEG: "fft32_seg", QRNG_ALGO_NTT: "ntt",
-              QRNG_ALGO_GEMM_FP4: "gemm_fp4"}
+              QRNG_ALGO_GEMM_FP4: "gemm_fp4", QRNG_ALGO_GEMM_FP4_PAIR: "gemm_fp4_pair"}
 
 EXPORTED = ["qrng_create", "qrng_destroy", "qrng_last_error", "qrng_status_string", "qrng_minentropy",
             "qrng_output_length", "qrng_seed_bits", "qrng_toeplitz_extract", "qrng_postprocess_host",

@@ -87,7 +87,7 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
 
   DirectArgs a{};
   // The tensor-core kernel loads raw tiles with TMA: 16-byte aligned rows, a multiple of 4 words apart.
-  const bool gemm = (algo == QRNG_ALGO_GEMM_TC || algo == QRNG_ALGO_GEMM_FP4);
+  const bool gemm = (algo == QRNG_ALGO_GEMM_TC || algo == QRNG_ALGO_GEMM_FP4 || algo == QRNG_ALGO_GEMM_FP4_PAIR);
   const bool raw_direct = gemm ? (n % 128 == 0) && ((reinterpret_cast<uintptr_t>(raw) & 15) == 0)
                                : (n % 32 == 0) && ((reinterpret_cast<uintptr_t>(raw) & 3) == 0);
   if (raw_direct) {
@@ -141,8 +141,11 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
     LaunchTimer timer(ctx, s);
     const int fault = ctx->fault;
     ctx->fault = 0;  // one-shot
-    QRNG_CUDA(ctx, launch_gemm_tc(a, algo == QRNG_ALGO_GEMM_FP4, ctx->dev_err.as<int>(), fault, ctx->num_sms, s,
-                                  kernels),
+    QRNG_CUDA(ctx,
+              algo == QRNG_ALGO_GEMM_FP4_PAIR
+                  ? launch_gemm_pair(a, ctx->dev_err.as<int>(), fault, ctx->num_sms, s, kernels)
+                  : launch_gemm_tc(a, algo == QRNG_ALGO_GEMM_FP4, ctx->dev_err.as<int>(), fault, ctx->num_sms, s,
+                                   kernels),
               "tensor-core extraction kernel");
     timer.done();
     if (!out_direct)
@@ -227,7 +230,7 @@ int check_extract_args(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m
                 "qrng_toeplitz_extract: need 1 <= m <= n (standard) or 1 <= m < n (modified), n <= 2^26");
   if (num_blocks == 0) return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: num_blocks must be >= 1");
   if (num_blocks > (1ull << 62) / n) return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: stream too long");
-  if (algo < QRNG_ALGO_AUTO || algo > QRNG_ALGO_GEMM_FP4)
+  if (algo < QRNG_ALGO_AUTO || algo > QRNG_ALGO_GEMM_FP4_PAIR)
     return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: unknown algorithm");
   return QRNG_OK;
 }
@@ -246,6 +249,10 @@ double model_seconds(int algo, uint64_t n_t, uint64_t m, uint64_t B) {
     case QRNG_ALGO_GEMM_FP4: {
       const double mp = (double)ceil_div(m, 256) * 256, bp = (double)ceil_div(B, 224) * 224;
       return mp * (double)n_t * bp / 3.0e15 + 1e-5;
+    }
+    case QRNG_ALGO_GEMM_FP4_PAIR: {
+      const double mp = (double)ceil_div(m, 256) * 256, bp = (double)ceil_div(B, 256) * 256;
+      return mp * (double)n_t * bp / 3.5e15 + 1e-5;
     }
     case QRNG_ALGO_FFT64: {
       const double P = (double)fft64_length(n_t, m), lg = log2(P), pairs = (double)ceil_div(B, 2);
@@ -270,6 +277,7 @@ bool algo_applicable(int algo, uint64_t n_t, uint64_t m, uint64_t B) {
       return true;
     case QRNG_ALGO_GEMM_TC:
     case QRNG_ALGO_GEMM_FP4:
+    case QRNG_ALGO_GEMM_FP4_PAIR:
       return n_t <= kGemmMaxColumns;
     case QRNG_ALGO_FFT64:
     case QRNG_ALGO_NTT:
@@ -291,8 +299,8 @@ int extract_one(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uint64_
 int choose_auto(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
                 uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels, int* chosen, bool* done) {
   const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
-  const int algos[6] = {QRNG_ALGO_DIRECT,  QRNG_ALGO_GEMM_TC,   QRNG_ALGO_GEMM_FP4,
-                        QRNG_ALGO_NTT,     QRNG_ALGO_FFT64,     QRNG_ALGO_FFT32_SEG};
+  const int algos[7] = {QRNG_ALGO_DIRECT, QRNG_ALGO_GEMM_TC, QRNG_ALGO_GEMM_FP4, QRNG_ALGO_GEMM_FP4_PAIR,
+                        QRNG_ALGO_NTT,    QRNG_ALGO_FFT64,   QRNG_ALGO_FFT32_SEG};
   double best_model = 1e30;
   int best_algo = QRNG_ALGO_DIRECT;
   for (int a : algos)
@@ -372,6 +380,7 @@ int extract_dispatch(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, 
       break;
     case QRNG_ALGO_GEMM_TC:
     case QRNG_ALGO_GEMM_FP4:
+    case QRNG_ALGO_GEMM_FP4_PAIR:
       if (n_t > kGemmMaxColumns)
         return fail(ctx, QRNG_ENOTSUP, "qrng_toeplitz_extract: the tensor-core path needs n (n-m modified) <= 2^22");
       st = extract_bitwise(ctx, used, raw, n, m, seed, form, num_blocks, out, s, &kernels);

@@ -1,0 +1,435 @@
+// Block-batched Toeplitz hashing on pairs of SMs (tcgen05 cta_group::2).
+//
+// The same exact GF(2) product as the single-SM tensor-core kernel,
+//     D[i][b] = sum_j T[i][j] X[b][j],   k_i(block b) = D[i][b] mod 2
+// (T the Toeplitz matrix of the shared seed, Sec. III.B / III.D; X the raw blocks, Sec. III.E), with
+// block-scaled E2M1 operands (0/1 as 1.0, every UE8M0 scale factor 2^0), issued as UMMAs of M = 256
+// that span a cluster of two CTAs on two SMs. Each CTA holds 128 of the 256 T rows and 128 of the
+// 256 X rows of a tile; the pair's tensor cores each read their own A half and both B halves, so per
+// SM the operand bytes read per MAC are 2/3 of the single-SM kernel's and the bytes written by the
+// producers 3/4 of them. Shared memory bandwidth is what bounds the single-SM kernel.
+//
+// Pair tile: 256 outputs x 256 blocks, K step 256 entries (one 128-byte swizzle row), 6 stages.
+//   warps 0-5   producers: warp s owns operand stage s and raw slot s, i.e. every 6th K step; it
+//               builds all 128 T rows of this CTA (funnel-shifted windows of the bit-reversed seed)
+//               and all 128 X rows (from the packed raw tile TMA put in slot s). One arrival per
+//               stage and CTA on the leader's barrier: the peer's is a cluster-scope release, whose
+//               memory barrier then costs each warp once per 6 K steps instead of once per step;
+//   warp 6      TMA: packed raw tiles (128 blocks x 32 bytes) of this CTA's blocks, in K-step order;
+//   warp 7      tensor memory allocation (both CTAs); in the leader CTA (rank 0) one lane issues the
+//               cta_group::2 MMAs and multicasts their completion to both CTAs' barriers;
+//   warps 8-11  epilogue: each CTA reads its 128 accumulator rows (its outputs) from its own tensor
+//               memory, parity, __ballot_sync into output words, identity XOR for the modified form.
+// Both epilogues signal the leader's accumulator barrier. Every wait is bounded (about one second of
+// clock): on timeout a CTA records an error code and stops; the leader still drains its MMAs, and
+// both CTAs meet at a cluster barrier before tensor memory is released.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qrng_internal.h"
+#include "tc_util.cuh"
+
+namespace qrng {
+namespace {
+
+using namespace tc;
+
+constexpr int PM = 256;                  // outputs per pair tile (UMMA M)
+constexpr int HM = 128;                  // outputs (T rows) per CTA
+constexpr int PN = 256;                  // blocks per pair tile (UMMA N)
+constexpr int HN = 128;                  // blocks (X rows) per CTA
+constexpr int BK = 256;                  // E2M1 entries per K step
+constexpr int KW = BK / 32;              // packed words per row and step
+constexpr int ROW_BYTES = 128;
+constexpr int STAGES = 6;
+constexpr int A_BYTES = HM * ROW_BYTES;  // 16 KB
+constexpr int B_BYTES = HN * ROW_BYTES;  // 16 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int PK_STAGES = 6;
+constexpr int PK_BYTES = HN * KW * 4;    // 4 KB
+constexpr int PRODUCER_WARPS = STAGES;   // warp s builds every use of operand stage s
+constexpr int ROWS_PER_LANE = HM / 32;   // lane l builds T rows and X rows l + 32 j
+constexpr int TMA_WARP = PRODUCER_WARPS;
+constexpr int MMA_WARP = TMA_WARP + 1;
+constexpr int EPI_WARP0 = MMA_WARP + 1;
+constexpr int EPI_WARPS = 4;
+constexpr int THREADS = (EPI_WARP0 + EPI_WARPS) * 32;  // 384
+constexpr int TMEM_COLS = 512;
+constexpr uint32_t SFA_COL = 448;        // scale factors (all 2^0) of A, then of B
+constexpr uint32_t SFB_COL = 480;
+constexpr uint16_t kPairMask = 0x3;      // both CTAs of the cluster
+// kind::mxf4: A = B = E2M1 (1 at bits 7 and 10), K-major, N >> 3 at bit 17, UE8M0 scales (bit 23),
+// M >> 7 at bit 27 (M = 256 over the pair), dense K = 64.
+constexpr uint32_t IDESC =
+    (1u << 7) | (1u << 10) | ((uint32_t)(PN >> 3) << 17) | (1u << 23) | ((uint32_t)(PM >> 7) << 27);
+static_assert(HM == HN && PK_STAGES == STAGES, "producer warp s owns operand stage s and raw slot s");
+static_assert(PN <= 256 && PN + 64 <= TMEM_COLS, "accumulator and scale factors must fit tensor memory");
+
+__device__ __forceinline__ void mma_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
+      " tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n}\n" ::"r"(
+          tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(tmem_d + SFA_COL), "r"(tmem_d + SFB_COL), "r"(accumulate)
+      : "memory");
+}
+
+// Arrives on the barrier at this offset in both CTAs once every MMA issued so far has completed.
+__device__ __forceinline__ void commit_both(uint64_t* bar) {
+  asm volatile(
+      "tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;" ::"r"(
+          smem_u32(bar)),
+      "h"(kPairMask)
+      : "memory");
+}
+
+__device__ __forceinline__ void commit_local(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+struct PairArgs {
+  const uint32_t* raw;
+  uint64_t raw_stride;
+  uint32_t nw_t;
+  uint32_t tail_mask;
+  uint32_t m;
+  uint32_t mw;
+  const uint32_t* seed_rev;
+  int modified;
+  uint32_t id_off;
+  uint32_t* out;
+  uint64_t out_stride;
+  uint64_t num_blocks;
+  uint32_t mtiles;
+  uint32_t ntiles;
+  uint32_t ksteps;
+  int* err;
+  int fault_no_tma;  // test hook: the loader publishes no raw tile, so every consumer's bounded wait runs out
+};
+
+__global__ void __launch_bounds__(THREADS, 1)
+    gemm_pair_kernel(const PairArgs a, const __grid_constant__ CUtensorMap raw_map) {
+  extern __shared__ uint8_t dyn_smem[];
+  __shared__ __align__(8) uint64_t full_bar[STAGES];       // leader: the owning producer warp of both CTAs
+  __shared__ __align__(8) uint64_t empty_bar[STAGES];      // both: the leader's MMA completion
+  __shared__ __align__(8) uint64_t pk_full_bar[PK_STAGES];
+  __shared__ __align__(8) uint64_t pk_empty_bar[PK_STAGES];
+  __shared__ __align__(8) uint64_t accum_full_bar;         // both: the leader's MMA completion
+  __shared__ __align__(8) uint64_t accum_empty_bar;        // leader: one arrival per epilogue warp of both CTAs
+  __shared__ __align__(8) uint64_t drain_bar;
+  __shared__ uint32_t tmem_slot;
+  __shared__ volatile int abort_flag;
+
+  const uint32_t warp = threadIdx.x >> 5;
+  const uint32_t lane = threadIdx.x & 31;
+  const uint32_t rank = cluster_ctarank();
+  const uint32_t smem_base = (smem_u32(dyn_smem) + 1023u) & ~1023u;
+  const uint32_t pk_base = smem_base + STAGES * STAGE_BYTES;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full_bar[s], 2);  // the owning warp of each CTA
+      mbar_init(&empty_bar[s], 1);
+    }
+    for (int s = 0; s < PK_STAGES; ++s) {
+      mbar_init(&pk_full_bar[s], 1);
+      mbar_init(&pk_empty_bar[s], 1);
+    }
+    mbar_init(&accum_full_bar, 1);
+    mbar_init(&accum_empty_bar, 2 * EPI_WARPS);
+    mbar_init(&drain_bar, 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  cluster_sync();  // both CTAs' barriers exist before any remote arrival
+  if (warp == MMA_WARP) {
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem_base = tmem_slot;
+  if (warp >= EPI_WARP0) {
+    // every scale factor is 2^0: fill the 64 scale-factor columns in all 128 lanes, whatever cells
+    // the MMAs read there
+    const uint32_t lanes = (32u * (warp & 3u)) << 16;
+    tmem_fill32(tmem_base + lanes + SFA_COL, kScaleOne);
+    tmem_fill32(tmem_base + lanes + SFB_COL, kScaleOne);
+    asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  cluster_sync();  // both CTAs' scale factors are in place before the first MMA
+  tc_fence_after();
+
+  const uint64_t ntile_total = (uint64_t)a.mtiles * a.ntiles;
+  const uint64_t first_tile = blockIdx.x >> 1;
+  const uint64_t tile_stride = gridDim.x >> 1;
+  if (warp < PRODUCER_WARPS) {
+    // ------------------------------------------------------------------ producers (warp = stage)
+    const uint32_t st = warp;
+    const uint32_t full_leader = mapa_shared(smem_u32(&full_bar[st]), 0);
+    const uint32_t sA = smem_base + st * STAGE_BYTES;
+    const uint32_t sB = sA + A_BYTES;
+    const uint32_t pk = pk_base + st * PK_BYTES;
+    uint32_t use = 0;   // uses of this stage so far
+    uint32_t base = 0;  // index of the tile's first K step modulo STAGES
+    for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
+      const uint32_t mt = (uint32_t)(tile % a.mtiles);
+      // T row i = mt*256 + rank*128 + lane + 32 j reads reversed-seed bits m-1-i+BK*ks .. +BK-1; rows 32
+      // apart start one word apart at the same shift (front padding keeps every index >= 0)
+      const int64_t ubase = (int64_t)a.m - 1 - ((int64_t)mt * PM + rank * HM + lane) + 32 * (int64_t)kSeedFrontWords;
+      const uint32_t sh = (uint32_t)(ubase & 31);
+      const uint32_t* seed_row = a.seed_rev + (ubase >> 5);
+      bool stop = false;
+      for (uint32_t ks = (st + STAGES - base) % STAGES; ks < a.ksteps; ks += STAGES) {
+        const uint32_t ph = use & 1u;
+        // the seed words do not depend on any barrier: issue all of them first
+        uint32_t sw[ROWS_PER_LANE][KW + 1];
+#pragma unroll
+        for (int j = 0; j < ROWS_PER_LANE; ++j)
+#pragma unroll
+          for (int k = 0; k <= KW; ++k) sw[j][k] = __ldg(seed_row - j + KW * ks + k);
+        if (!mbar_wait(&pk_full_bar[st], ph, &abort_flag, a.err, 1)) { stop = true; break; }
+        uint32_t xw[ROWS_PER_LANE][KW];
+#pragma unroll
+        for (int j = 0; j < ROWS_PER_LANE; ++j)
+#pragma unroll
+          for (int h = 0; h < KW / 4; ++h)
+            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                         : "=r"(xw[j][4 * h]), "=r"(xw[j][4 * h + 1]), "=r"(xw[j][4 * h + 2]), "=r"(xw[j][4 * h + 3])
+                         : "r"(pk + (lane + 32u * j) * (KW * 4) + 16 * h)
+                         : "memory");
+        if (KW * ks + KW > a.nw_t - 1) {  // words past the Toeplitz part (zero-filled) and its partial last word
+#pragma unroll
+          for (int w = 0; w < KW; ++w)
+            if (KW * ks + w == a.nw_t - 1) {
+#pragma unroll
+              for (int j = 0; j < ROWS_PER_LANE; ++j) xw[j][w] &= a.tail_mask;
+            }
+        }
+        if (!mbar_wait(&empty_bar[st], ph ^ 1u, &abort_flag, a.err, 2)) { stop = true; break; }
+#pragma unroll
+        for (int j = 0; j < ROWS_PER_LANE; ++j) {
+          const uint32_t r = lane + 32u * j;
+#pragma unroll
+          for (int w = 0; w < KW; ++w) {
+            store_word_e2m1(sA + r * ROW_BYTES, r, w, __funnelshift_r(sw[j][w], sw[j][w + 1], sh));
+            store_word_e2m1(sB + r * ROW_BYTES, r, w, xw[j][w]);
+          }
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&pk_empty_bar[st]);  // the raw words have been consumed by the stores above
+          if (rank == 0)
+            mbar_arrive(&full_bar[st]);
+          else
+            mbar_arrive_cluster(full_leader);
+        }
+        __syncwarp();
+        ++use;
+      }
+      if (stop) break;
+      base = (uint32_t)((base + a.ksteps) % STAGES);
+    }
+  } else if (warp == TMA_WARP) {
+    // ------------------------------------------------------------------ TMA loads of packed raw tiles
+    uint32_t pstage = 0, pphase = 0, issued = 0;
+    if (lane == 0) {
+      for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
+        const uint32_t nt = (uint32_t)(tile / a.mtiles);
+        for (uint32_t ks = 0; ks < a.ksteps; ++ks) {
+          if (!mbar_wait(&pk_empty_bar[pstage], pphase ^ 1u, &abort_flag, a.err, 3)) break;
+          if (!a.fault_no_tma) {
+            mbar_arrive_expect_tx(&pk_full_bar[pstage], PK_BYTES);
+            tma_load_2d(pk_base + pstage * PK_BYTES, &raw_map, (int)(KW * ks), (int)(nt * PN + rank * HN),
+                        &pk_full_bar[pstage]);
+            ++issued;
+          }
+          if (++pstage == PK_STAGES) { pstage = 0; pphase ^= 1u; }
+        }
+      }
+      // the loads still in flight must land before the CTA exits: wait for the last PK_STAGES slots
+      for (uint32_t k = 0; k < PK_STAGES && k < issued; ++k) {
+        if (pstage == 0) { pstage = PK_STAGES; pphase ^= 1u; }
+        --pstage;
+        mbar_drain(&pk_full_bar[pstage], pphase, a.err, 4);
+      }
+    }
+    __syncwarp();
+  } else if (warp == MMA_WARP) {
+    // ------------------------------------------------------------------ MMA issuer (leader CTA)
+    if (rank == 0) {
+      uint32_t stage = 0, phase = 0, acc_phase = 0;
+      bool issued = false;
+      for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
+        // both epilogues must have drained the previous tile's accumulators
+        if (tile != first_tile && !mbar_wait<true>(&accum_empty_bar, acc_phase ^ 1u, &abort_flag, a.err, 5)) break;
+        for (uint32_t ks = 0; ks < a.ksteps; ++ks) {
+          if (!mbar_wait<true>(&full_bar[stage], phase, &abort_flag, a.err, 6)) break;
+          tc_fence_after();
+          if (lane == 0) {
+            const uint32_t sA = smem_base + stage * STAGE_BYTES;
+            const uint32_t sB = sA + A_BYTES;
+#pragma unroll
+            for (int k = 0; k < ROW_BYTES / 32; ++k)
+              mma_pair(tmem_base, smem_desc_sw128(sA + 32 * k), smem_desc_sw128(sB + 32 * k), (ks | k) != 0);
+            commit_both(&empty_bar[stage]);  // frees the stage in both CTAs once these MMAs have read it
+            issued = true;
+          }
+          __syncwarp();
+          if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+        }
+        if (abort_flag) break;
+        if (lane == 0) commit_both(&accum_full_bar);
+        __syncwarp();
+        acc_phase ^= 1u;
+      }
+      // every MMA must finish before either CTA releases its tensor or shared memory
+      if (lane == 0 && issued) {
+        commit_local(&drain_bar);
+        mbar_drain(&drain_bar, 0, a.err, 7);
+      }
+      __syncwarp();
+    }
+  } else {
+    // ------------------------------------------------------------------ epilogue
+    const uint32_t q = warp & 3u;  // TMEM lane quarter this warp may access
+    const uint32_t accum_empty_leader = mapa_shared(smem_u32(&accum_empty_bar), 0);
+    uint32_t acc_phase = 0;
+    for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
+      const uint32_t mt = (uint32_t)(tile % a.mtiles);
+      const uint32_t nt = (uint32_t)(tile / a.mtiles);
+      if (!mbar_wait(&accum_full_bar, acc_phase, &abort_flag, a.err, 8)) break;
+      tc_fence_after();
+      const uint32_t ow = mt * (PM / 32) + rank * (HM / 32) + q;  // output word of every block in the tile
+      const uint32_t rem = (ow < a.mw) ? a.m - 32 * ow : 0u;
+      const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+      for (uint32_t g = 0; g < PN / 32; ++g) {
+        uint32_t v[32];
+        tmem_load32(tmem_base + ((32u * q) << 16) + 32u * g, v);
+        uint32_t mine = 0;
+#pragma unroll
+        for (int c = 0; c < 32; ++c) {
+          const uint32_t wrd = __ballot_sync(0xffffffffu, count_parity(v[c], 1.0f));
+          if (lane == (uint32_t)c) mine = wrd;
+        }
+        const uint64_t b = (uint64_t)nt * PN + 32u * g + lane;
+        if (ow < a.mw && b < a.num_blocks) {
+          mine &= omask;
+          if (a.modified) {
+            const uint64_t bit = (uint64_t)a.id_off + 32ull * ow;
+            const uint32_t* rr = a.raw + b * a.raw_stride;
+            const uint64_t rq = bit >> 5;
+            const uint32_t rs = (uint32_t)(bit & 31);
+            const uint32_t rlo = __ldg(rr + rq);
+            const uint32_t rhi = (rs && rq + 1 < a.raw_stride) ? __ldg(rr + rq + 1) : 0u;
+            mine ^= __funnelshift_r(rlo, rhi, rs) & omask;
+          }
+          a.out[b * a.out_stride + ow] = mine;
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive_cluster(accum_empty_leader);
+      acc_phase ^= 1u;
+    }
+  }
+
+  tc_fence_before();
+  cluster_sync();  // the leader's MMAs have drained; neither CTA touches the other's memory after this
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem_base), "r"(TMEM_COLS)
+                 : "memory");
+  }
+}
+
+}  // namespace
+
+typedef CUresult (*PFN_encodeTiled_pair)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                         const cuuint64_t*, const cuuint32_t*, const cuuint32_t*,
+                                         CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
+                                         CUtensorMapFloatOOBfill);
+
+size_t gemm_pair_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + (size_t)PK_STAGES * PK_BYTES + 1024; }
+
+cudaError_t launch_gemm_pair(const DirectArgs& d, int* err, int fault, int num_sms, cudaStream_t s,
+                             uint32_t* kernels) {
+  if ((reinterpret_cast<uintptr_t>(d.raw) & 15) != 0 || (d.raw_stride % 4) != 0) return cudaErrorInvalidValue;
+  PairArgs a{};
+  a.raw = d.raw;
+  a.raw_stride = d.raw_stride;
+  a.nw_t = d.nw_t;
+  a.tail_mask = d.tail_mask;
+  a.m = d.m;
+  a.mw = d.mw;
+  a.seed_rev = d.seed_rev;
+  a.modified = d.modified;
+  a.id_off = d.id_off;
+  a.out = d.out;
+  a.out_stride = d.out_stride;
+  a.num_blocks = d.num_blocks;
+  a.mtiles = (uint32_t)ceil_div(d.m, PM);
+  a.ntiles = (uint32_t)ceil_div(d.num_blocks, PN);
+  a.ksteps = (uint32_t)ceil_div((uint64_t)d.nw_t * 32, BK);
+  a.err = err;
+  a.fault_no_tma = (fault == QRNG_FAULT_GEMM_NO_TMA);
+
+  // Tensor map over the raw words: dim 0 = the Toeplitz part's words of a block (reads beyond it are
+  // zero-filled), dim 1 = blocks (rows past the last block are zero-filled); box 8 words x 128 blocks,
+  // every x coordinate a multiple of 8 words (32 bytes).
+  static PFN_encodeTiled_pair encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_encodeTiled_pair>(fn);
+  }
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {(cuuint64_t)d.nw_t, (cuuint64_t)d.num_blocks};
+  const cuuint64_t gstride[1] = {(cuuint64_t)d.raw_stride * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)KW, (cuuint32_t)HN};
+  const cuuint32_t estride[2] = {1, 1};
+  CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(d.raw), gdim, gstride, box,
+                      estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+
+  const size_t smem = gemm_pair_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(gemm_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const uint64_t tiles = (uint64_t)a.mtiles * a.ntiles;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * (tiles < (uint64_t)num_sms / 2 ? tiles : (uint64_t)num_sms / 2)));
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // one cluster per co-resident pair of SMs: every tile loop stride then runs concurrently
+  int clusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&clusters, gemm_pair_kernel, &cfg);
+  if (e != cudaSuccess) return e;
+  if (clusters < 1) return cudaErrorNotSupported;
+  const uint64_t pairs = tiles < (uint64_t)clusters ? tiles : (uint64_t)clusters;
+  cfg.gridDim = dim3((unsigned)(2 * pairs));
+  e = cudaLaunchKernelEx(&cfg, gemm_pair_kernel, a, map);
+  if (e != cudaSuccess) return e;
+  ++*kernels;
+  return cudaGetLastError();
+}
+
+}  // namespace qrng

@@ -34,9 +34,12 @@
 #include <stdint.h>
 
 #include "qrng_internal.h"
+#include "tc_util.cuh"
 
 namespace qrng {
 namespace {
+
+using namespace tc;
 
 constexpr int UM = 128;                 // UMMA M
 constexpr int BM = 2 * UM;              // outputs per CTA tile
@@ -52,9 +55,6 @@ constexpr int EPI_WARP0 = MMA_WARP + 1;
 constexpr int THREADS = (EPI_WARP0 + 4) * 32;  // 448
 constexpr int TMEM_COLS = 512;
 constexpr uint32_t kOneE4M3 = 0x08u;    // 2^-6
-constexpr uint32_t kOneE2M1 = 0x2u;     // 1.0
-constexpr uint32_t kScaleOne = 0x7F7F7F7Fu;  // four UE8M0 scale factors 2^0
-constexpr long long kWaitCycles = 2000000000ll;  // ~1 s at 2 GHz
 static_assert(PRODUCERS == BM, "one T row per producer thread");
 
 // Per-encoding tile shape and instruction descriptor.
@@ -81,78 +81,6 @@ struct Cfg {
   static_assert(MMA_K * (kFp4 ? 1 : 2) == 64, "each instruction consumes 32 bytes of a row");
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
-  asm volatile("mbarrier.arrive.release.cta.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
-}
-
-__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_test(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-
-// Bounded wait on phase `parity`; on timeout records `code` and raises the CTA abort flag.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag, int* err,
-                                          int code) {
-  if (mbar_test(bar, parity)) return true;
-  const long long t0 = clock64();
-  while (true) {
-    if (*abort_flag) return false;
-    if (mbar_test(bar, parity)) return true;
-    if (clock64() - t0 > kWaitCycles) {
-      *abort_flag = 1;
-      atomicCAS(err, 0, code);
-      return false;
-    }
-  }
-}
-
-// Bounded wait that ignores the abort flag (used to drain the CTA's own asynchronous work).
-__device__ __forceinline__ void mbar_drain(uint64_t* bar, uint32_t parity, int* err, int code) {
-  const long long t0 = clock64();
-  while (!mbar_test(bar, parity)) {
-    if (clock64() - t0 > kWaitCycles) {
-      atomicCAS(err, 0, code);
-      return;
-    }
-  }
-}
-
-__device__ __forceinline__ void fence_proxy_async_smem() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
-
-// K-major, SWIZZLE_128B shared-memory matrix descriptor (rows of 128 bytes, 8-row atoms 1024 B apart).
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: next 8-row atom
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
-  return d;
-}
-
 __device__ __forceinline__ void mma_f8(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
@@ -171,26 +99,9 @@ __device__ __forceinline__ void mma_f4(uint32_t tmem_d, uint64_t adesc, uint64_t
       : "memory");
 }
 
-// Fills 32 TMEM columns of this warp's 32 lanes with the value v.
-__device__ __forceinline__ void tmem_fill32(uint32_t taddr, uint32_t v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x32.b32 [%0], {%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,"
-      "%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1,%1};" ::"r"(taddr),
-      "r"(v)
-      : "memory");
-}
-
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
                : "memory");
-}
-
-__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
-          dst),
-      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
-      : "memory");
 }
 
 // Spreads 4 bits to 4 bytes: bit j -> byte j with value kOneE4M3 (the shifted copies x << 7k never
@@ -210,16 +121,6 @@ __device__ __forceinline__ void store_word_e4m3(uint32_t row_addr, uint32_t row,
                  "r"(nib_to_e4m3((y >> 12) & 0xFu))
                  : "memory");
   }
-}
-
-// Writes 32 bits of one row as one 16-byte chunk of E2M1 nibbles: chunk word q holds bits
-// q, q+4, ..., q+28 (one shift and one mask each; the permutation is the same for T and X).
-__device__ __forceinline__ void store_word_e2m1(uint32_t row_addr, uint32_t row, uint32_t w, uint32_t x) {
-  constexpr uint32_t kMask = kOneE2M1 * 0x11111111u;
-  const uint32_t addr = row_addr + (((w ^ (row & 7u)) & 7u) << 4);
-  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"((x << 1) & kMask), "r"(x & kMask),
-               "r"((x >> 1) & kMask), "r"((x >> 2) & kMask)
-               : "memory");
 }
 
 struct GemmArgs {
@@ -446,23 +347,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
         for (uint32_t g = 0; g < (uint32_t)BN / 32; ++g) {
           uint32_t v[32];
-          const uint32_t taddr = tmem_base + ((32u * q) << 16) + half * BN + 32u * g;
-          asm volatile(
-              "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-              "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-              : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-                "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
-                "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
-                "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
-                "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-              : "r"(taddr));
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          tmem_load32(tmem_base + ((32u * q) << 16) + half * BN + 32u * g, v);
           uint32_t mine = 0;
 #pragma unroll
           for (int c = 0; c < 32; ++c) {
-            // the count is an integer < 2^22: adding 1.5 * 2^23 leaves it in the low mantissa bits
-            const float cnt = __fmaf_rn(__uint_as_float(v[c]), C::COUNT_SCALE, 12582912.0f);
-            const uint32_t wrd = __ballot_sync(0xffffffffu, __float_as_uint(cnt) & 1u);
+            const uint32_t wrd = __ballot_sync(0xffffffffu, count_parity(v[c], C::COUNT_SCALE));
             if (lane == (uint32_t)c) mine = wrd;
           }
           const uint64_t b = (uint64_t)nt * BN + 32u * g + lane;

@@ -14,8 +14,8 @@ from gpu_util import extract, spot_check
 pytestmark = pytest.mark.gpu
 
 STD, MOD = 0, 1
-ALGOS = {"direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4, "ntt": 5, "gemm_fp4": 6}
-GEMMS = {"gemm_tc": 2, "gemm_fp4": 6}
+ALGOS = {"direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4, "ntt": 5, "gemm_fp4": 6, "gemm_fp4_pair": 7}
+GEMMS = {"gemm_tc": 2, "gemm_fp4": 6, "gemm_fp4_pair": 7}
 
 
 def _seed_len(n, m, form):

@@ -4,22 +4,28 @@
 //     D[i][b] = sum_j T[i][j] X[b][j],   k_i(block b) = D[i][b] mod 2
 // (T the Toeplitz matrix of the shared seed, Sec. III.B / III.D; X the raw blocks, Sec. III.E), with
 // block-scaled E2M1 operands (0/1 as 1.0, every UE8M0 scale factor 2^0), issued as UMMAs of M = 256
-// that span a cluster of two CTAs on two SMs. Each CTA holds 128 of the 256 T rows and 128 of the
-// 256 X rows of a tile; the pair's tensor cores each read their own A half and both B halves, so per
-// SM the operand bytes read per MAC are 2/3 of the single-SM kernel's and the bytes written by the
-// producers 3/4 of them. Shared memory bandwidth is what bounds the single-SM kernel.
+// that span a cluster of two CTAs on two SMs: each CTA holds 128 of the 256 T rows and half of the X
+// rows of a tile, and the pair's tensor cores each read their own T half and both X halves.
 //
-// Pair tile: 256 outputs x 256 blocks, K step 256 entries (one 128-byte swizzle row), 6 stages.
-//   warps 0-5   producers: warp s owns operand stage s and raw slot s, i.e. every 6th K step; it
-//               builds all 128 T rows of this CTA (funnel-shifted windows of the bit-reversed seed)
-//               and all 128 X rows (from the packed raw tile TMA put in slot s). One arrival per
+// T is Toeplitz: T[i + 256][j + 256] = T[i][j], so the T tile of output tile mt+1 at K step ks is the
+// T tile of output tile mt at K step ks-1. A pair tile therefore covers two output tiles (512 outputs,
+// two accumulators) x 224 blocks, and every stage carries one new T tile: at step e the MMAs are
+//     D0 += T(mt, e-1) X(e-1),   D1 += T(mt, e-2) X(e-1)      (e = 1 .. ksteps),
+// the second reading the previous stage's T tile; step e = 0 only builds T(mt, -1). Per MAC this
+// halves the operand bytes the producers write, the traffic that bounds the single-SM kernel.
+//
+// Pair tile: 512 outputs x 224 blocks, K step 256 entries (one 128-byte swizzle row), 6 stages.
+//   warps 0-5   producers: warp s owns operand stage s and raw slot s, i.e. every 6th step; it
+//               builds the 128 T rows of this CTA (funnel-shifted windows of the bit-reversed seed)
+//               and its 112 X rows (from the packed raw tile TMA put in slot s). One arrival per
 //               stage and CTA on the leader's barrier: the peer's is a cluster-scope release, whose
-//               memory barrier then costs each warp once per 6 K steps instead of once per step;
-//   warp 6      TMA: packed raw tiles (128 blocks x 32 bytes) of this CTA's blocks, in K-step order;
+//               memory barrier then costs a warp once per 6 steps;
+//   warp 6      TMA: packed raw tiles (112 blocks x 32 bytes) of this CTA's blocks, in step order;
 //   warp 7      tensor memory allocation (both CTAs); in the leader CTA (rank 0) one lane issues the
 //               cta_group::2 MMAs and multicasts their completion to both CTAs' barriers;
-//   warps 8-11  epilogue: each CTA reads its 128 accumulator rows (its outputs) from its own tensor
-//               memory, parity, __ballot_sync into output words, identity XOR for the modified form.
+//   warps 8-11  epilogue: each CTA reads its 128 rows of both accumulators (its outputs) from its own
+//               tensor memory, parity, __ballot_sync into output words, identity XOR for the
+//               modified form.
 // Both epilogues signal the leader's accumulator barrier. Every wait is bounded (about one second of
 // clock): on timeout a CTA records an error code and stops; the leader still drains its MMAs, and
 // both CTAs meet at a cluster barrier before tensor memory is released.
@@ -35,27 +41,29 @@ namespace {
 
 using namespace tc;
 
-constexpr int PM = 256;                  // outputs per pair tile (UMMA M)
-constexpr int HM = 128;                  // outputs (T rows) per CTA
-constexpr int PN = 256;                  // blocks per pair tile (UMMA N)
-constexpr int HN = 128;                  // blocks (X rows) per CTA
+constexpr int PM = 256;                  // outputs per output tile (UMMA M over the pair)
+constexpr int HM = 128;                  // T rows per CTA
+constexpr int PN = 224;                  // blocks per pair tile (UMMA N)
+constexpr int HN = PN / 2;               // X rows per CTA
 constexpr int BK = 256;                  // E2M1 entries per K step
 constexpr int KW = BK / 32;              // packed words per row and step
 constexpr int ROW_BYTES = 128;
 constexpr int STAGES = 6;
 constexpr int A_BYTES = HM * ROW_BYTES;  // 16 KB
-constexpr int B_BYTES = HN * ROW_BYTES;  // 16 KB
+constexpr int B_BYTES = HN * ROW_BYTES;  // 14 KB
 constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
-constexpr int PK_STAGES = 6;
-constexpr int PK_BYTES = HN * KW * 4;    // 4 KB
+constexpr int PK_STAGES = STAGES;
+constexpr int PK_BYTES = HN * KW * 4;    // 3.5 KB
 constexpr int PRODUCER_WARPS = STAGES;   // warp s builds every use of operand stage s
-constexpr int ROWS_PER_LANE = HM / 32;   // lane l builds T rows and X rows l + 32 j
+constexpr int T_ROWS = HM / 32;          // T rows lane + 32 j of a lane
+constexpr int X_ROWS = (HN + 31) / 32;   // X rows lane + 32 j < HN of a lane
 constexpr int TMA_WARP = PRODUCER_WARPS;
 constexpr int MMA_WARP = TMA_WARP + 1;
 constexpr int EPI_WARP0 = MMA_WARP + 1;
 constexpr int EPI_WARPS = 4;
 constexpr int THREADS = (EPI_WARP0 + EPI_WARPS) * 32;  // 384
 constexpr int TMEM_COLS = 512;
+constexpr uint32_t D1_COL = PN;          // second accumulator
 constexpr uint32_t SFA_COL = 448;        // scale factors (all 2^0) of A, then of B
 constexpr uint32_t SFB_COL = 480;
 constexpr uint16_t kPairMask = 0x3;      // both CTAs of the cluster
@@ -63,15 +71,17 @@ constexpr uint16_t kPairMask = 0x3;      // both CTAs of the cluster
 // M >> 7 at bit 27 (M = 256 over the pair), dense K = 64.
 constexpr uint32_t IDESC =
     (1u << 7) | (1u << 10) | ((uint32_t)(PN >> 3) << 17) | (1u << 23) | ((uint32_t)(PM >> 7) << 27);
-static_assert(HM == HN && PK_STAGES == STAGES, "producer warp s owns operand stage s and raw slot s");
-static_assert(PN <= 256 && PN + 64 <= TMEM_COLS, "accumulator and scale factors must fit tensor memory");
+static_assert(PK_STAGES == STAGES, "producer warp s owns operand stage s and raw slot s");
+static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0, "swizzle atoms must stay 1024-byte aligned");
+static_assert(HN % 8 == 0 && PN % 16 == 0 && 2 * PN <= (int)SFA_COL, "accumulators and scale factors must fit");
 
-__device__ __forceinline__ void mma_pair(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+__device__ __forceinline__ void mma_pair(uint32_t tmem_d, uint32_t tmem_base, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
       " tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n}\n" ::"r"(
           tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(tmem_d + SFA_COL), "r"(tmem_d + SFB_COL), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(tmem_base + SFA_COL), "r"(tmem_base + SFB_COL), "r"(accumulate)
       : "memory");
 }
 
@@ -102,7 +112,7 @@ struct PairArgs {
   uint32_t* out;
   uint64_t out_stride;
   uint64_t num_blocks;
-  uint32_t mtiles;
+  uint32_t mpairs;   // pairs of output tiles
   uint32_t ntiles;
   uint32_t ksteps;
   int* err;
@@ -166,9 +176,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   cluster_sync();  // both CTAs' scale factors are in place before the first MMA
   tc_fence_after();
 
-  const uint64_t ntile_total = (uint64_t)a.mtiles * a.ntiles;
+  const uint64_t ntile_total = (uint64_t)a.mpairs * a.ntiles;
   const uint64_t first_tile = blockIdx.x >> 1;
   const uint64_t tile_stride = gridDim.x >> 1;
+  const uint32_t nsteps = a.ksteps + 1;  // step 0 builds T(mt, -1) only
   if (warp < PRODUCER_WARPS) {
     // ------------------------------------------------------------------ producers (warp = stage)
     const uint32_t st = warp;
@@ -177,49 +188,66 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t sB = sA + A_BYTES;
     const uint32_t pk = pk_base + st * PK_BYTES;
     uint32_t use = 0;   // uses of this stage so far
-    uint32_t base = 0;  // index of the tile's first K step modulo STAGES
+    uint32_t base = 0;  // index of the tile's step 0 modulo STAGES
     for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
-      const uint32_t mt = (uint32_t)(tile % a.mtiles);
-      // T row i = mt*256 + rank*128 + lane + 32 j reads reversed-seed bits m-1-i+BK*ks .. +BK-1; rows 32
-      // apart start one word apart at the same shift (front padding keeps every index >= 0)
+      const uint32_t mt = 2u * (uint32_t)(tile % a.mpairs);
+      // T row i = mt*256 + rank*128 + lane + 32 j at step e reads reversed-seed bits
+      // m-1-i+BK*(e-1) .. +BK-1; rows 32 apart start one word apart at the same shift (the front
+      // padding keeps every index >= 0, also at e = 0)
       const int64_t ubase = (int64_t)a.m - 1 - ((int64_t)mt * PM + rank * HM + lane) + 32 * (int64_t)kSeedFrontWords;
       const uint32_t sh = (uint32_t)(ubase & 31);
-      const uint32_t* seed_row = a.seed_rev + (ubase >> 5);
+      const uint32_t* seed_row = a.seed_rev + ((ubase >> 5) - KW);  // the window of step 0
       bool stop = false;
-      for (uint32_t ks = (st + STAGES - base) % STAGES; ks < a.ksteps; ks += STAGES) {
+      for (uint32_t e = (st + STAGES - base) % STAGES; e < nsteps; e += STAGES) {
         const uint32_t ph = use & 1u;
-        // the seed words do not depend on any barrier: issue all of them first
-        uint32_t sw[ROWS_PER_LANE][KW + 1];
+        const uint32_t ks = e - 1;  // K step of the X rows (e >= 1)
+        // the seed words depend on no barrier: issue all of them first
+        uint32_t sw[T_ROWS][KW + 1];
 #pragma unroll
-        for (int j = 0; j < ROWS_PER_LANE; ++j)
+        for (int j = 0; j < T_ROWS; ++j)
 #pragma unroll
-          for (int k = 0; k <= KW; ++k) sw[j][k] = __ldg(seed_row - j + KW * ks + k);
+          for (int k = 0; k <= KW; ++k) sw[j][k] = __ldg(seed_row - j + KW * e + k);
         if (!mbar_wait(&pk_full_bar[st], ph, &abort_flag, a.err, 1)) { stop = true; break; }
-        uint32_t xw[ROWS_PER_LANE][KW];
+        uint32_t xw[X_ROWS][KW];
+        if (e > 0) {
 #pragma unroll
-        for (int j = 0; j < ROWS_PER_LANE; ++j)
+          for (int j = 0; j < X_ROWS; ++j) {
+            const uint32_t r = lane + 32u * j;
+            if (r < (uint32_t)HN) {
 #pragma unroll
-          for (int h = 0; h < KW / 4; ++h)
-            asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
-                         : "=r"(xw[j][4 * h]), "=r"(xw[j][4 * h + 1]), "=r"(xw[j][4 * h + 2]), "=r"(xw[j][4 * h + 3])
-                         : "r"(pk + (lane + 32u * j) * (KW * 4) + 16 * h)
-                         : "memory");
-        if (KW * ks + KW > a.nw_t - 1) {  // words past the Toeplitz part (zero-filled) and its partial last word
-#pragma unroll
-          for (int w = 0; w < KW; ++w)
-            if (KW * ks + w == a.nw_t - 1) {
-#pragma unroll
-              for (int j = 0; j < ROWS_PER_LANE; ++j) xw[j][w] &= a.tail_mask;
+              for (int h = 0; h < KW / 4; ++h)
+                asm volatile("ld.shared.v4.b32 {%0, %1, %2, %3}, [%4];"
+                             : "=r"(xw[j][4 * h]), "=r"(xw[j][4 * h + 1]), "=r"(xw[j][4 * h + 2]),
+                               "=r"(xw[j][4 * h + 3])
+                             : "r"(pk + r * (KW * 4) + 16 * h)
+                             : "memory");
             }
+          }
+          if (KW * ks + KW > a.nw_t - 1) {  // words past the Toeplitz part (zero-filled) and its partial last word
+#pragma unroll
+            for (int w = 0; w < KW; ++w)
+              if (KW * ks + w == a.nw_t - 1) {
+#pragma unroll
+                for (int j = 0; j < X_ROWS; ++j) xw[j][w] &= a.tail_mask;
+              }
+          }
         }
         if (!mbar_wait(&empty_bar[st], ph ^ 1u, &abort_flag, a.err, 2)) { stop = true; break; }
 #pragma unroll
-        for (int j = 0; j < ROWS_PER_LANE; ++j) {
+        for (int j = 0; j < T_ROWS; ++j) {
           const uint32_t r = lane + 32u * j;
 #pragma unroll
-          for (int w = 0; w < KW; ++w) {
+          for (int w = 0; w < KW; ++w)
             store_word_e2m1(sA + r * ROW_BYTES, r, w, __funnelshift_r(sw[j][w], sw[j][w + 1], sh));
-            store_word_e2m1(sB + r * ROW_BYTES, r, w, xw[j][w]);
+        }
+        if (e > 0) {
+#pragma unroll
+          for (int j = 0; j < X_ROWS; ++j) {
+            const uint32_t r = lane + 32u * j;
+            if (r < (uint32_t)HN) {
+#pragma unroll
+              for (int w = 0; w < KW; ++w) store_word_e2m1(sB + r * ROW_BYTES, r, w, xw[j][w]);
+            }
           }
         }
         fence_proxy_async_smem();
@@ -235,20 +263,22 @@ __global__ void __launch_bounds__(THREADS, 1)
         ++use;
       }
       if (stop) break;
-      base = (uint32_t)((base + a.ksteps) % STAGES);
+      base = (uint32_t)((base + nsteps) % STAGES);
     }
   } else if (warp == TMA_WARP) {
     // ------------------------------------------------------------------ TMA loads of packed raw tiles
+    // one load per step (step 0 loads the tile of K step 0 as well, unused), so that raw slot s and
+    // operand stage s advance together
     uint32_t pstage = 0, pphase = 0, issued = 0;
     if (lane == 0) {
       for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
-        const uint32_t nt = (uint32_t)(tile / a.mtiles);
-        for (uint32_t ks = 0; ks < a.ksteps; ++ks) {
+        const uint32_t nt = (uint32_t)(tile / a.mpairs);
+        for (uint32_t e = 0; e < nsteps; ++e) {
           if (!mbar_wait(&pk_empty_bar[pstage], pphase ^ 1u, &abort_flag, a.err, 3)) break;
           if (!a.fault_no_tma) {
             mbar_arrive_expect_tx(&pk_full_bar[pstage], PK_BYTES);
-            tma_load_2d(pk_base + pstage * PK_BYTES, &raw_map, (int)(KW * ks), (int)(nt * PN + rank * HN),
-                        &pk_full_bar[pstage]);
+            tma_load_2d(pk_base + pstage * PK_BYTES, &raw_map, (int)(KW * (e > 0 ? e - 1 : 0)),
+                        (int)(nt * PN + rank * HN), &pk_full_bar[pstage]);
             ++issued;
           }
           if (++pstage == PK_STAGES) { pstage = 0; pphase ^= 1u; }
@@ -265,28 +295,38 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------------ MMA issuer (leader CTA)
     if (rank == 0) {
-      uint32_t stage = 0, phase = 0, acc_phase = 0;
+      uint32_t stage = 0, phase = 0, acc_phase = 0, prev = 0;
       bool issued = false;
       for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
         // both epilogues must have drained the previous tile's accumulators
         if (tile != first_tile && !mbar_wait<true>(&accum_empty_bar, acc_phase ^ 1u, &abort_flag, a.err, 5)) break;
-        for (uint32_t ks = 0; ks < a.ksteps; ++ks) {
-          if (!mbar_wait<true>(&full_bar[stage], phase, &abort_flag, a.err, 6)) break;
+        bool done = true;
+        for (uint32_t e = 0; e < nsteps; ++e) {
+          if (!mbar_wait<true>(&full_bar[stage], phase, &abort_flag, a.err, 6)) { done = false; break; }
           tc_fence_after();
-          if (lane == 0) {
-            const uint32_t sA = smem_base + stage * STAGE_BYTES;
-            const uint32_t sB = sA + A_BYTES;
+          if (lane == 0 && e > 0) {
+            const uint32_t sA = smem_base + stage * STAGE_BYTES;  // T(mt, e-1)
+            const uint32_t sB = sA + A_BYTES;                      // X(e-1)
+            const uint32_t sP = smem_base + prev * STAGE_BYTES;   // T(mt, e-2) = T(mt+1, e-1)
 #pragma unroll
-            for (int k = 0; k < ROW_BYTES / 32; ++k)
-              mma_pair(tmem_base, smem_desc_sw128(sA + 32 * k), smem_desc_sw128(sB + 32 * k), (ks | k) != 0);
-            commit_both(&empty_bar[stage]);  // frees the stage in both CTAs once these MMAs have read it
+            for (int k = 0; k < ROW_BYTES / 32; ++k) {
+              const uint64_t bdesc = smem_desc_sw128(sB + 32 * k);
+              const uint32_t acc = (e > 1 || k > 0) ? 1u : 0u;
+              mma_pair(tmem_base, tmem_base, smem_desc_sw128(sA + 32 * k), bdesc, acc);
+              mma_pair(tmem_base + D1_COL, tmem_base, smem_desc_sw128(sP + 32 * k), bdesc, acc);
+            }
+            commit_both(&empty_bar[prev]);  // the previous stage's T tile is not read again
             issued = true;
           }
           __syncwarp();
+          prev = stage;
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
         }
-        if (abort_flag) break;
-        if (lane == 0) commit_both(&accum_full_bar);
+        if (!done || abort_flag) break;
+        if (lane == 0) {
+          commit_both(&empty_bar[prev]);  // the tile's last stage
+          commit_both(&accum_full_bar);
+        }
         __syncwarp();
         acc_phase ^= 1u;
       }
@@ -303,35 +343,37 @@ __global__ void __launch_bounds__(THREADS, 1)
     const uint32_t accum_empty_leader = mapa_shared(smem_u32(&accum_empty_bar), 0);
     uint32_t acc_phase = 0;
     for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
-      const uint32_t mt = (uint32_t)(tile % a.mtiles);
-      const uint32_t nt = (uint32_t)(tile / a.mtiles);
+      const uint32_t mt0 = 2u * (uint32_t)(tile % a.mpairs);
+      const uint32_t nt = (uint32_t)(tile / a.mpairs);
       if (!mbar_wait(&accum_full_bar, acc_phase, &abort_flag, a.err, 8)) break;
       tc_fence_after();
-      const uint32_t ow = mt * (PM / 32) + rank * (HM / 32) + q;  // output word of every block in the tile
-      const uint32_t rem = (ow < a.mw) ? a.m - 32 * ow : 0u;
-      const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
-      for (uint32_t g = 0; g < PN / 32; ++g) {
-        uint32_t v[32];
-        tmem_load32(tmem_base + ((32u * q) << 16) + 32u * g, v);
-        uint32_t mine = 0;
+      for (uint32_t h = 0; h < 2; ++h) {
+        const uint32_t ow = (mt0 + h) * (PM / 32) + rank * (HM / 32) + q;  // output word of every block
+        const uint32_t rem = (ow < a.mw) ? a.m - 32 * ow : 0u;
+        const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+        for (uint32_t g = 0; g < PN / 32; ++g) {
+          uint32_t v[32];
+          tmem_load32(tmem_base + ((32u * q) << 16) + h * D1_COL + 32u * g, v);
+          uint32_t mine = 0;
 #pragma unroll
-        for (int c = 0; c < 32; ++c) {
-          const uint32_t wrd = __ballot_sync(0xffffffffu, count_parity(v[c], 1.0f));
-          if (lane == (uint32_t)c) mine = wrd;
-        }
-        const uint64_t b = (uint64_t)nt * PN + 32u * g + lane;
-        if (ow < a.mw && b < a.num_blocks) {
-          mine &= omask;
-          if (a.modified) {
-            const uint64_t bit = (uint64_t)a.id_off + 32ull * ow;
-            const uint32_t* rr = a.raw + b * a.raw_stride;
-            const uint64_t rq = bit >> 5;
-            const uint32_t rs = (uint32_t)(bit & 31);
-            const uint32_t rlo = __ldg(rr + rq);
-            const uint32_t rhi = (rs && rq + 1 < a.raw_stride) ? __ldg(rr + rq + 1) : 0u;
-            mine ^= __funnelshift_r(rlo, rhi, rs) & omask;
+          for (int c = 0; c < 32; ++c) {
+            const uint32_t wrd = __ballot_sync(0xffffffffu, count_parity(v[c], 1.0f));
+            if (lane == (uint32_t)c) mine = wrd;
           }
-          a.out[b * a.out_stride + ow] = mine;
+          const uint64_t b = (uint64_t)nt * PN + 32u * g + lane;
+          if (ow < a.mw && b < a.num_blocks) {
+            mine &= omask;
+            if (a.modified) {
+              const uint64_t bit = (uint64_t)a.id_off + 32ull * ow;
+              const uint32_t* rr = a.raw + b * a.raw_stride;
+              const uint64_t rq = bit >> 5;
+              const uint32_t rs = (uint32_t)(bit & 31);
+              const uint32_t rlo = __ldg(rr + rq);
+              const uint32_t rhi = (rs && rq + 1 < a.raw_stride) ? __ldg(rr + rq + 1) : 0u;
+              mine ^= __funnelshift_r(rlo, rhi, rs) & omask;
+            }
+            a.out[b * a.out_stride + ow] = mine;
+          }
         }
       }
       tc_fence_before();
@@ -375,14 +417,14 @@ cudaError_t launch_gemm_pair(const DirectArgs& d, int* err, int fault, int num_s
   a.out = d.out;
   a.out_stride = d.out_stride;
   a.num_blocks = d.num_blocks;
-  a.mtiles = (uint32_t)ceil_div(d.m, PM);
+  a.mpairs = (uint32_t)ceil_div(ceil_div(d.m, PM), 2);
   a.ntiles = (uint32_t)ceil_div(d.num_blocks, PN);
   a.ksteps = (uint32_t)ceil_div((uint64_t)d.nw_t * 32, BK);
   a.err = err;
   a.fault_no_tma = (fault == QRNG_FAULT_GEMM_NO_TMA);
 
   // Tensor map over the raw words: dim 0 = the Toeplitz part's words of a block (reads beyond it are
-  // zero-filled), dim 1 = blocks (rows past the last block are zero-filled); box 8 words x 128 blocks,
+  // zero-filled), dim 1 = blocks (rows past the last block are zero-filled); box 8 words x 112 blocks,
   // every x coordinate a multiple of 8 words (32 bytes).
   static PFN_encodeTiled_pair encode = nullptr;
   if (!encode) {
@@ -406,7 +448,7 @@ cudaError_t launch_gemm_pair(const DirectArgs& d, int* err, int fault, int num_s
   const size_t smem = gemm_pair_smem_bytes();
   cudaError_t e = cudaFuncSetAttribute(gemm_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const uint64_t tiles = (uint64_t)a.mtiles * a.ntiles;
+  const uint64_t tiles = (uint64_t)a.mpairs * a.ntiles;
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;

@@ -572,7 +572,7 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int a
     for (uint64_t k = first_ntt; k < count;) {
       const uint64_t P = tlen[order[k]];
       const bool fp64 = (algo == QRNG_ALGO_FFT64);
-      const uint64_t per_req = fp64 ? 2 * P * 16 : 2 * 2 * P * sizeof(uint32_t);  // both ping-pong buffers
+      const uint64_t per_req = fp64 ? 2 * P * 16 : 2 * P * sizeof(uint32_t);  // FP64: both ping-pong buffers
       uint64_t cap = kFftWorkspaceBytes / per_req;
       if (cap < 1) cap = 1;
       uint64_t e = k, max_mw = 0;

@@ -8,10 +8,20 @@
 // field result IS the integer: there is no rounding to guard, and the transform runs on the integer
 // pipes (FP64 is the slowest unit of the GB300).
 //
-// Arithmetic: elements in [0, p); twiddles in Montgomery form (w 2^32 mod p) so that one Montgomery
-// product w (*) x = w x mod p returns ordinary residues. Radix-2 Stockham passes over global
-// memory, one launch per pass over a chunk of blocks (the same schedule as the FP64 route, with
-// 4-byte elements instead of 16).
+// Arithmetic: elements in [0, p); roots of unity in Montgomery form (w 2^32 mod p) so that one
+// Montgomery product w (*) x = w x mod p returns an ordinary residue.
+//
+// Schedule (four-step, in shared memory): with P = N1 N2, N2 = 2^L (L <= 12), index n = N2 n1 + n2
+// and frequency k = k1 + N1 k2,
+//   columns: for every n2, the length-N1 transform over n1 (decimation in frequency, so row
+//            position rr holds k1 = bitrev(rr)), on tiles of W adjacent columns in shared memory;
+//   rows:    for every row, multiply by w^(n2 k1), the length-N2 transform over n2 (position pos
+//            holds k2 = bitrev(pos)); then the pointwise product with the seed's spectrum (kept in
+//            the same permuted order), the inverse row transform (decimation in time) and
+//            w^(-n2 k1), all in one kernel;
+//   columns: the inverse length-N1 transforms, back to natural order.
+// Three passes over the block's P elements in global memory (plus packing and extraction) instead
+// of one pass per radix-4 stage.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -24,19 +34,35 @@ constexpr uint32_t kP = 2013265921u;        // 15 * 2^27 + 1
 constexpr uint32_t kPinvNeg = 2013265919u;  // -p^-1 mod 2^32
 constexpr uint32_t kGen = 31u;              // a generator of Z_p^*
 
+// For a, b < p: a + b < 2p < 2^32; min(s, s - p) over unsigned words subtracts p exactly when s >= p
+// (otherwise s - p wraps above s). Likewise a - b wraps when a < b, and then d + p is the smaller.
 __host__ __device__ __forceinline__ uint32_t add_mod(uint32_t a, uint32_t b) {
-  const uint32_t s = a + b;  // < 2p < 2^32
-  return s >= kP ? s - kP : s;
+  const uint32_t s = a + b;
+  const uint32_t t = s - kP;
+  return t < s ? t : s;
 }
 
-__host__ __device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b) { return a >= b ? a - b : a + kP - b; }
+__host__ __device__ __forceinline__ uint32_t sub_mod(uint32_t a, uint32_t b) {
+  const uint32_t d = a - b;
+  const uint32_t t = d + kP;
+  return t < d ? t : d;
+}
 
-// Montgomery product a b 2^-32 mod p, for a, b < p.
+// Montgomery product a b 2^-32 mod p, for a, b < p, in 32-bit words: with q = (a b mod 2^32)(-p^-1),
+// the low word of a b + q p is 0 and carries exactly when a b mod 2^32 != 0, so
+// (a b + q p) / 2^32 = hi(a b) + hi(q p) + carry < 2p.
 __host__ __device__ __forceinline__ uint32_t mont_mul(uint32_t a, uint32_t b) {
+#ifdef __CUDA_ARCH__
+  const uint32_t lo = a * b;
+  const uint32_t q = lo * kPinvNeg;
+  const uint32_t u = __umulhi(a, b) + __umulhi(q, kP) + (lo != 0u ? 1u : 0u);
+#else
   const uint64_t t = (uint64_t)a * b;
   const uint32_t q = (uint32_t)t * kPinvNeg;
-  const uint64_t u = (t + (uint64_t)q * kP) >> 32;  // < 2p
-  return u >= kP ? (uint32_t)(u - kP) : (uint32_t)u;
+  const uint32_t u = (uint32_t)((t + (uint64_t)q * kP) >> 32);
+#endif
+  const uint32_t r = u - kP;
+  return r < u ? r : u;
 }
 
 uint32_t pow_mod(uint64_t b, uint64_t e) {
@@ -73,110 +99,247 @@ __global__ void ntt_twiddle_kernel(uint32_t* __restrict__ tw, uint64_t half, uin
   }
 }
 
-// One radix-2 Stockham pass (see the FP64 route): y[g 2L + k] = x[j] + w x[j+P/2],
-// y[g 2L + k + L] = x[j] - w x[j+P/2], w = omega^(+-k P/(2L)); the inverse uses
-// omega^-q = -omega^(P/2 - q).
-__global__ void ntt_pass_kernel(const uint32_t* __restrict__ x, uint32_t* __restrict__ y,
-                                const uint32_t* __restrict__ tw, uint64_t P, uint32_t logL, uint32_t logP, int inverse,
-                                uint64_t total) {
-  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const uint64_t half = P >> 1;
-  const uint64_t b = idx >> (logP - 1);
-  const uint64_t j = idx & (half - 1);
-  const uint64_t L = 1ull << logL;
-  const uint64_t k = j & (L - 1);
-  const uint64_t g = j >> logL;
-  const uint64_t q = k << (logP - 1 - logL);
-  uint32_t w;
-  if (!inverse || q == 0) w = tw[q];
-  else w = kP - tw[half - q];
-  const uint32_t* xb = x + b * P;
-  uint32_t* yb = y + b * P;
-  const uint32_t a = xb[j];
-  const uint32_t t = mont_mul(w, xb[j + half]);
-  yb[(g << (logL + 1)) + k] = add_mod(a, t);
-  yb[(g << (logL + 1)) + k + L] = sub_mod(a, t);
-}
-
 // omega^t in Montgomery form for 0 <= t < P, from the half table (omega^(P/2) = -1).
 __device__ __forceinline__ uint32_t ntt_root(const uint32_t* __restrict__ tw, uint64_t half, uint64_t t) {
-  return t < half ? tw[t] : kP - tw[t - half];
+  return t < half ? __ldg(tw + t) : kP - __ldg(tw + (t - half));
 }
 
-// One radix-4 Stockham pass: with a_q = x[j + q P/4] and b_q = omega^(+-q k P/(4L)) a_q,
-// y[g 4L + k + r L] = sum_q b_q i^(qr), i = omega^(+-P/4) a primitive 4th root of unity.
-__global__ void ntt_pass4_kernel(const uint32_t* __restrict__ x, uint32_t* __restrict__ y,
-                                 const uint32_t* __restrict__ tw, uint64_t P, uint32_t logL, uint32_t logP,
-                                 int inverse, uint64_t total) {
-  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  const uint64_t quarter = P >> 2, half = P >> 1;
-  const uint64_t b = idx >> (logP - 2);
-  const uint64_t j = idx & (quarter - 1);
-  const uint64_t L = 1ull << logL;
-  const uint64_t k = j & (L - 1);
-  const uint64_t g = j >> logL;
-  const uint64_t stride = k << (logP - 2 - logL);  // k P / (4L)
-  const uint32_t* xb = x + b * P;
-  uint32_t bq[4];
-  bq[0] = xb[j];
-#pragma unroll
-  for (int q = 1; q < 4; ++q) {
-    const uint64_t t = (uint64_t)q * stride;
-    const uint32_t w = inverse ? (t == 0 ? tw[0] : ntt_root(tw, half, P - t)) : ntt_root(tw, half, t);
-    bq[q] = mont_mul(w, xb[j + q * quarter]);
+// omega^(-t) for 0 <= t < P.
+__device__ __forceinline__ uint32_t ntt_iroot(const uint32_t* __restrict__ tw, uint64_t half, uint64_t t) {
+  return t == 0 ? __ldg(tw) : ntt_root(tw, half, 2 * half - t);
+}
+
+// Transform shape: P = 2^(H+L); column tiles of 2^H rows x 2^logW columns.
+struct NttPlan {
+  uint32_t logP, L, H, logW;
+};
+
+NttPlan ntt_plan(uint32_t logP) {
+  NttPlan pl;
+  pl.logP = logP;
+  pl.L = logP < 12 ? logP : 12;
+  pl.H = logP - pl.L;
+  const uint32_t want = pl.H >= 14 ? 0u : 14u - pl.H;  // about 16384 elements (64 KB) per column tile
+  pl.logW = want < pl.L ? want : pl.L;
+  return pl;
+}
+
+// Stage roots: st[2^s + j] = w_(2^(s+1))^j and st[kStageEntries + 2^s + j] = w_(2^(s+1))^-j
+// (Montgomery form, s < 16, j < 2^s), where w_(2^(s+1)) = g^((p-1)/2^(s+1)) is the same root as
+// w_P^(P/2^(s+1)) for every transform length P. One stage reads a contiguous run.
+constexpr uint32_t kStageLog = 16;
+constexpr uint32_t kStageEntries = 1u << kStageLog;
+
+__device__ __forceinline__ uint32_t pow_m(uint32_t b, uint32_t e, uint32_t one_m) {
+  uint32_t acc = one_m;
+  for (; e; e >>= 1) {
+    if (e & 1) acc = mont_mul(acc, b);
+    b = mont_mul(b, b);
   }
-  const uint32_t im = inverse ? kP - tw[quarter] : tw[quarter];  // omega^(+-P/4)
-  const uint32_t s02 = add_mod(bq[0], bq[2]), d02 = sub_mod(bq[0], bq[2]);
-  const uint32_t s13 = add_mod(bq[1], bq[3]), d13 = mont_mul(im, sub_mod(bq[1], bq[3]));
-  uint32_t* yb = y + b * P + (g << (logL + 2)) + k;
-  yb[0] = add_mod(s02, s13);
-  yb[L] = add_mod(d02, d13);
-  yb[2 * L] = sub_mod(s02, s13);
-  yb[3 * L] = sub_mod(d02, d13);
+  return acc;
 }
 
-// The same radix-4 pass with four consecutive butterflies (k .. k+3, same g) per thread, moved as
-// 16-byte vectors: four times the loads in flight per thread. Needs L >= 4 and P >= 16.
-__global__ void ntt_pass4_vec_kernel(const uint32_t* __restrict__ x, uint32_t* __restrict__ y,
-                                     const uint32_t* __restrict__ tw, uint64_t P, uint32_t logL, uint32_t logP,
-                                     int inverse, uint64_t total4) {
-  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total4) return;
-  const uint64_t quarter = P >> 2, half = P >> 1;
-  const uint64_t b = idx >> (logP - 4);
-  const uint64_t j0 = (idx & ((quarter >> 2) - 1)) << 2;
-  const uint64_t L = 1ull << logL;
-  const uint64_t k0 = j0 & (L - 1);
-  const uint64_t g = j0 >> logL;
-  const uint32_t* xb = x + b * P;
-  uint4 v[4];
-#pragma unroll
-  for (int q = 0; q < 4; ++q) v[q] = *reinterpret_cast<const uint4*>(xb + j0 + q * quarter);
-  const uint32_t im = inverse ? kP - tw[quarter] : tw[quarter];
-  uint32_t o[4][4];
-#pragma unroll
-  for (int e = 0; e < 4; ++e) {
-    const uint64_t stride = (k0 + e) << (logP - 2 - logL);
-    uint32_t bq[4];
-    bq[0] = (&v[0].x)[e];
-#pragma unroll
-    for (int q = 1; q < 4; ++q) {
-      const uint64_t t = (uint64_t)q * stride;
-      const uint32_t w = inverse ? (t == 0 ? tw[0] : ntt_root(tw, half, P - t)) : ntt_root(tw, half, t);
-      bq[q] = mont_mul(w, (&v[q].x)[e]);
+// g_m = g, one_m = 1 in Montgomery form. Thread t = 2^s + j: w_(2^(s+1)) = g^((p-1)/2^(s+1)),
+// its inverse g^((p-1) - (p-1)/2^(s+1)), each to the power j.
+__global__ void ntt_stage_table_kernel(uint32_t* __restrict__ st, uint32_t g_m, uint32_t one_m) {
+  const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t == 0 || t >= kStageEntries) return;
+  const uint32_t s = 31 - __clz(t), j = t - (1u << s);
+  const uint32_t e = (kP - 1) >> (s + 1);
+  st[t] = pow_m(pow_m(g_m, e, one_m), j, one_m);
+  st[kStageEntries + t] = pow_m(pow_m(g_m, (kP - 1) - e, one_m), j, one_m);
+}
+
+// Radix-4 pass (stages s and s-1, h = 2^(s-1)) on four elements x0..x3 = x[i + q h]:
+// forward decimation in frequency, or inverse decimation in time (stages s-1 then s).
+template <bool kInverse>
+__device__ __forceinline__ void radix4(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3,
+                                       const uint32_t* __restrict__ st, uint32_t s, uint32_t j) {
+  const uint32_t h = 1u << (s - 1);
+  if (!kInverse) {
+    const uint32_t wa = __ldg(st + (1u << s) + j), wb = __ldg(st + (1u << s) + j + h);
+    const uint32_t wc = __ldg(st + h + j);
+    const uint32_t y0 = add_mod(x0, x2), y2 = mont_mul(wa, sub_mod(x0, x2));
+    const uint32_t y1 = add_mod(x1, x3), y3 = mont_mul(wb, sub_mod(x1, x3));
+    x0 = add_mod(y0, y1);
+    x1 = mont_mul(wc, sub_mod(y0, y1));
+    x2 = add_mod(y2, y3);
+    x3 = mont_mul(wc, sub_mod(y2, y3));
+  } else {
+    const uint32_t* it = st + kStageEntries;
+    const uint32_t wc = __ldg(it + h + j);
+    const uint32_t wa = __ldg(it + (1u << s) + j), wb = __ldg(it + (1u << s) + j + h);
+    uint32_t t = mont_mul(wc, x1);
+    const uint32_t y0 = add_mod(x0, t), y1 = sub_mod(x0, t);
+    t = mont_mul(wc, x3);
+    const uint32_t y2 = add_mod(x2, t), y3 = sub_mod(x2, t);
+    t = mont_mul(wa, y2);
+    x0 = add_mod(y0, t);
+    x2 = sub_mod(y0, t);
+    t = mont_mul(wb, y3);
+    x1 = add_mod(y1, t);
+    x3 = sub_mod(y1, t);
+  }
+}
+
+template <bool kInverse>
+__device__ __forceinline__ void radix2(uint32_t& x0, uint32_t& x1, const uint32_t* __restrict__ st, uint32_t s,
+                                       uint32_t j) {
+  if (!kInverse) {
+    const uint32_t w = __ldg(st + (1u << s) + j);
+    const uint32_t a = x0;
+    x0 = add_mod(a, x1);
+    x1 = mont_mul(w, sub_mod(a, x1));
+  } else {
+    const uint32_t t = mont_mul(__ldg(st + kStageEntries + (1u << s) + j), x1);
+    const uint32_t a = x0;
+    x0 = add_mod(a, t);
+    x1 = sub_mod(a, t);
+  }
+}
+
+// In-place length-2^K transforms of `cols` interleaved sequences in shared memory (element r of
+// column c at x[(r << logC) | c]): forward = decimation in frequency (natural in, bit-reversed out),
+// inverse = decimation in time with inverse roots (bit-reversed in, natural out). Radix-4 passes,
+// one radix-2 stage when K is odd (the widest span first going forward, last going back).
+template <bool kInverse>
+__device__ __forceinline__ void smem_transform(uint32_t* __restrict__ x, uint32_t K, uint32_t logC,
+                                               const uint32_t* __restrict__ st) {
+  if (K == 0) return;
+  const uint32_t C = 1u << logC;
+  const bool odd = K & 1u;
+  // forward: spans from 2^(K-1) down; inverse: up to 2^(K-1)
+  const uint32_t passes = K >> 1;
+  for (uint32_t it = 0; it < passes + (odd ? 1u : 0u); ++it) {
+    // pass order: forward [radix-2 at s = K-1 if odd], radix-4 at s = top, top-2, ...; inverse reversed
+    const uint32_t fit = kInverse ? passes + (odd ? 1u : 0u) - 1 - it : it;
+    if (odd && fit == 0) {
+      const uint32_t s = K - 1;
+      for (uint32_t u = threadIdx.x; u < (1u << (K - 1 + logC)); u += blockDim.x) {
+        const uint32_t c = u & (C - 1), v = u >> logC;
+        const uint32_t j = v & ((1u << s) - 1);
+        const uint32_t r0 = ((v >> s) << (s + 1)) | j;
+        uint32_t* p0 = x + ((r0 << logC) | c);
+        uint32_t a0 = p0[0], a1 = p0[(1u << s) << logC];
+        radix2<kInverse>(a0, a1, st, s, j);
+        p0[0] = a0;
+        p0[(1u << s) << logC] = a1;
+      }
+    } else {
+      const uint32_t s = K - 1 - 2 * fit + (odd ? 1u : 0u);  // stages s and s-1
+      const uint32_t h = 1u << (s - 1);
+      for (uint32_t u = threadIdx.x; u < (1u << (K - 2 + logC)); u += blockDim.x) {
+        const uint32_t c = u & (C - 1), v = u >> logC;
+        const uint32_t j = v & (h - 1);
+        const uint32_t r0 = ((v >> (s - 1)) << (s + 1)) | j;
+        uint32_t* p0 = x + ((r0 << logC) | c);
+        const uint32_t dh = h << logC;
+        uint32_t a0 = p0[0], a1 = p0[dh], a2 = p0[2 * dh], a3 = p0[3 * dh];
+        radix4<kInverse>(a0, a1, a2, a3, st, s, j);
+        p0[0] = a0;
+        p0[dh] = a1;
+        p0[2 * dh] = a2;
+        p0[3 * dh] = a3;
+      }
     }
-    const uint32_t s02 = add_mod(bq[0], bq[2]), d02 = sub_mod(bq[0], bq[2]);
-    const uint32_t s13 = add_mod(bq[1], bq[3]), d13 = mont_mul(im, sub_mod(bq[1], bq[3]));
-    o[0][e] = add_mod(s02, s13);
-    o[1][e] = add_mod(d02, d13);
-    o[2][e] = sub_mod(s02, s13);
-    o[3][e] = sub_mod(d02, d13);
+    __syncthreads();
   }
-  uint32_t* yb = y + b * P + (g << (logL + 2)) + k0;
-#pragma unroll
-  for (int r = 0; r < 4; ++r) *reinterpret_cast<uint4*>(yb + r * L) = make_uint4(o[r][0], o[r][1], o[r][2], o[r][3]);
+}
+
+// Length-2^H transforms down the columns of entries ent_off, ent_off + ent_stride, ... (row stride
+// 2^L); one CTA per tile of 2^H rows x 2^logW adjacent columns.
+template <bool kInverse>
+__global__ void __launch_bounds__(512) ntt_cols_kernel(uint32_t* __restrict__ z, const uint32_t* __restrict__ st,
+                                                       NttPlan pl, uint64_t ent_stride, uint64_t ent_off) {
+  extern __shared__ uint32_t col_sm[];
+  const uint32_t tiles_per_ent = 1u << (pl.L - pl.logW);
+  const uint64_t ent = (uint64_t)blockIdx.x / tiles_per_ent;
+  const uint32_t c0 = (blockIdx.x % tiles_per_ent) << pl.logW;
+  const uint64_t P = 1ull << pl.logP;
+  uint32_t* zb = z + (ent * ent_stride + ent_off) * P + c0;
+  const uint32_t W = 1u << pl.logW, n = 1u << (pl.H + pl.logW);
+  for (uint32_t e = threadIdx.x; e < n; e += blockDim.x)
+    col_sm[e] = zb[((uint64_t)(e >> pl.logW) << pl.L) + (e & (W - 1))];
+  __syncthreads();
+  smem_transform<kInverse>(col_sm, pl.H, pl.logW, st);
+  for (uint32_t e = threadIdx.x; e < n; e += blockDim.x)
+    zb[((uint64_t)(e >> pl.logW) << pl.L) + (e & (W - 1))] = col_sm[e];
+}
+
+// Multiplies row element n2 by w_P^(+-n2 k1): the power is built from two tables of the row,
+// w^(k1 b) (b < 2^lob) and w^(2^lob k1 a), one Montgomery product apart.
+__device__ __forceinline__ void ntt_row_twiddle(uint32_t* __restrict__ x, const uint32_t* __restrict__ tlo,
+                                                const uint32_t* __restrict__ thi, uint32_t L, uint32_t lob) {
+  for (uint32_t n2 = threadIdx.x; n2 < (1u << L); n2 += blockDim.x) {
+    const uint32_t w = mont_mul(thi[n2 >> lob], tlo[n2 & ((1u << lob) - 1)]);
+    x[n2] = mont_mul(w, x[n2]);
+  }
+  __syncthreads();
+}
+
+enum { kRowsForward = 0, kRowsConvolve = 1, kRowsPairs = 2 };
+
+// Rows of entries (one CTA per row, 2^L elements):
+//   kRowsForward:  twiddle + forward row transform (finishes a forward transform);
+//   kRowsConvolve: the same, times the spectrum spec (same permuted order), inverse row transform,
+//                  inverse twiddle;
+//   kRowsPairs:    entries 2r and 2r+1 (a request's seed and raw bits) both forward, their product
+//                  (*) factor, inverse row transform and twiddle, written to entry 2r+1.
+template <int kMode>
+__global__ void __launch_bounds__(512) ntt_rows_kernel(uint32_t* __restrict__ z, const uint32_t* __restrict__ spec,
+                                                       const uint32_t* __restrict__ tw,
+                                                       const uint32_t* __restrict__ st, NttPlan pl,
+                                                       uint32_t factor_m) {
+  extern __shared__ uint32_t row_sm[];
+  const uint32_t Lr = 1u << pl.L;
+  const uint32_t lob = pl.L < 6 ? pl.L : 6;
+  uint32_t* tlo = row_sm + (kMode == kRowsPairs ? 2 : 1) * Lr;  // w^(+-k1 b), b < 2^lob
+  uint32_t* thi = tlo + (1u << lob);                            // w^(+-2^lob k1 a)
+  const uint64_t P = 1ull << pl.logP, half = P >> 1;
+  const uint64_t rows = 1ull << pl.H;
+  const uint64_t ent = (uint64_t)blockIdx.x / rows;
+  const uint32_t rr = (uint32_t)(blockIdx.x % rows);
+  const uint32_t k1 = pl.H ? (__brev(rr) >> (32 - pl.H)) : 0u;
+  const uint64_t e0 = (kMode == kRowsPairs) ? 2 * ent : ent;
+  uint32_t* x = z + e0 * P + ((uint64_t)rr << pl.L);
+  uint32_t* x2 = x + P;  // kRowsPairs: the raw entry
+  for (uint32_t t = threadIdx.x; t < Lr; t += blockDim.x) {
+    row_sm[t] = x[t];
+    if (kMode == kRowsPairs) row_sm[Lr + t] = x2[t];
+  }
+  if (pl.H) {
+    for (uint32_t t = threadIdx.x; t < (1u << lob) + (Lr >> lob); t += blockDim.x) {
+      if (t < (1u << lob)) tlo[t] = ntt_root(tw, half, ((uint64_t)k1 * t) & (P - 1));
+      else thi[t - (1u << lob)] = ntt_root(tw, half, (((uint64_t)k1 * (t - (1u << lob))) << lob) & (P - 1));
+    }
+  }
+  __syncthreads();
+  if (pl.H) {
+    ntt_row_twiddle(row_sm, tlo, thi, pl.L, lob);
+    if (kMode == kRowsPairs) ntt_row_twiddle(row_sm + Lr, tlo, thi, pl.L, lob);
+  }
+  smem_transform<false>(row_sm, pl.L, 0, st);
+  if (kMode == kRowsPairs) smem_transform<false>(row_sm + Lr, pl.L, 0, st);
+  if (kMode == kRowsForward) {
+    for (uint32_t t = threadIdx.x; t < Lr; t += blockDim.x) x[t] = row_sm[t];
+    return;
+  }
+  const uint32_t* sp = spec + ((uint64_t)rr << pl.L);
+  for (uint32_t t = threadIdx.x; t < Lr; t += blockDim.x) {
+    if (kMode == kRowsConvolve) row_sm[t] = mont_mul(row_sm[t], __ldg(sp + t));
+    else row_sm[t] = mont_mul(mont_mul(row_sm[t], row_sm[Lr + t]), factor_m);
+  }
+  if (pl.H) {  // inverse twiddle tables (the forward ones were last read before the stage barriers)
+    for (uint32_t t = threadIdx.x; t < (1u << lob) + (Lr >> lob); t += blockDim.x) {
+      if (t < (1u << lob)) tlo[t] = ntt_iroot(tw, half, ((uint64_t)k1 * t) & (P - 1));
+      else thi[t - (1u << lob)] = ntt_iroot(tw, half, (((uint64_t)k1 * (t - (1u << lob))) << lob) & (P - 1));
+    }
+  }
+  __syncthreads();
+  smem_transform<true>(row_sm, pl.L, 0, st);
+  if (pl.H) ntt_row_twiddle(row_sm, tlo, thi, pl.L, lob);
+  uint32_t* dst = (kMode == kRowsPairs) ? x2 : x;
+  for (uint32_t t = threadIdx.x; t < Lr; t += blockDim.x) dst[t] = row_sm[t];
 }
 
 __global__ void ntt_seed_kernel(const uint8_t* __restrict__ seed, uint64_t L, uint32_t* __restrict__ z, uint64_t P) {
@@ -200,12 +363,6 @@ __global__ void ntt_pack_kernel(const uint32_t* __restrict__ raw, uint64_t strid
   const uint64_t bl = idx / P, t = idx - bl * P;
   const uint64_t b = b0 + bl;
   z[idx] = (t < n_t && b < num_blocks) ? ((raw[b * stride + (t >> 5)] >> (t & 31)) & 1u) : 0u;
-}
-
-__global__ void ntt_mul_kernel(uint32_t* __restrict__ z, const uint32_t* __restrict__ A, uint64_t P, uint64_t total) {
-  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= total) return;
-  z[idx] = mont_mul(z[idx], A[idx & (P - 1)]);
 }
 
 // Output word w of block b0+bl: parities of c[n_t - 1 + i] (exact integers), identity bits.
@@ -240,31 +397,54 @@ __global__ void ntt_extract_kernel(const uint32_t* __restrict__ z, uint64_t P, u
 
 inline unsigned grid_for(uint64_t total, int threads) { return (unsigned)ceil_div(total, (uint64_t)threads); }
 
-cudaError_t run_ntt(uint32_t* a, uint32_t* b, const uint32_t* tw, uint64_t P, uint32_t logP, uint64_t batch,
-                    int inverse, cudaStream_t s, uint32_t* kernels, uint32_t** result) {
-  uint32_t* x = a;
-  uint32_t* y = b;
-  for (uint32_t logL = 0; logL < logP;) {
-    if (logP - logL >= 2) {  // radix 4 while two factors of 2 remain, then one radix-2 pass
-      if (logL >= 2 && logP >= 4) {
-        const uint64_t total4 = batch * (P >> 4);
-        ntt_pass4_vec_kernel<<<grid_for(total4, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total4);
-      } else {
-        const uint64_t total = batch * (P >> 2);
-        ntt_pass4_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total);
-      }
-      logL += 2;
-    } else {
-      const uint64_t total = batch * (P >> 1);
-      ntt_pass_kernel<<<grid_for(total, 256), 256, 0, s>>>(x, y, tw, P, logL, logP, inverse, total);
-      logL += 1;
-    }
+constexpr int kNttThreads = 512;
+
+// Columns forward/inverse over the entries ent_off, ent_off + ent_stride, ... (num_ent of them).
+template <bool kInverse>
+cudaError_t ntt_columns(uint32_t* z, const uint32_t* st, const NttPlan& pl, uint64_t num_ent, uint64_t ent_stride,
+                        uint64_t ent_off, cudaStream_t s, uint32_t* kernels) {
+  if (pl.H == 0) return cudaSuccess;
+  const size_t smem = ((size_t)1 << (pl.H + pl.logW)) * sizeof(uint32_t);
+  cudaError_t e = cudaFuncSetAttribute(ntt_cols_kernel<kInverse>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  const uint64_t tiles = num_ent << (pl.L - pl.logW);
+  ntt_cols_kernel<kInverse><<<(unsigned)tiles, kNttThreads, smem, s>>>(z, st, pl, ent_stride, ent_off);
+  ++*kernels;
+  return cudaGetLastError();
+}
+
+template <int kMode>
+cudaError_t ntt_rows(uint32_t* z, const uint32_t* spec, const uint32_t* tw, const uint32_t* st, const NttPlan& pl,
+                     uint64_t num_rows_ent, uint32_t factor_m, cudaStream_t s, uint32_t* kernels) {
+  const uint32_t lob = pl.L < 6 ? pl.L : 6;
+  const size_t smem =
+      ((size_t)(kMode == kRowsPairs ? 2 : 1) * (1u << pl.L) + (1u << lob) + (1u << (pl.L - lob))) * sizeof(uint32_t);
+  cudaError_t e = cudaFuncSetAttribute(ntt_rows_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const uint64_t ctas = num_rows_ent << pl.H;
+  ntt_rows_kernel<kMode><<<(unsigned)ctas, kNttThreads, smem, s>>>(z, spec, tw, st, pl, factor_m);
+  ++*kernels;
+  return cudaGetLastError();
+}
+
+cudaError_t ensure_twiddles(FftWorkspace& ws, uint64_t P, cudaStream_t s, uint32_t* kernels) {
+  cudaError_t e;
+  if (!ws.ntt_stage.p) {
+    if ((e = ws.ntt_stage.ensure(2 * kStageEntries * sizeof(uint32_t))) != cudaSuccess) return e;
+    ntt_stage_table_kernel<<<kStageEntries / 256, 256, 0, s>>>(ws.ntt_stage.as<uint32_t>(), to_mont(kGen),
+                                                                 to_mont(1));
     ++*kernels;
-    uint32_t* t = x;
-    x = y;
-    y = t;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  *result = x;
+  if (ws.ntt_P == P) return cudaSuccess;
+  if ((e = ws.ntt_tw.ensure((P / 2) * sizeof(uint32_t))) != cudaSuccess) return e;
+  const uint32_t omega = pow_mod(kGen, (kP - 1) / P);  // primitive P-th root of unity
+  ntt_twiddle_kernel<<<grid_for(ceil_div(P / 2, 256), 128), 128, 0, s>>>(ws.ntt_tw.as<uint32_t>(), P / 2,
+                                                                        to_mont(omega), to_mont(1),
+                                                                        to_mont(pow_mod(omega, 256)));
+  ++*kernels;
+  ws.ntt_P = P;
   return cudaGetLastError();
 }
 
@@ -291,16 +471,8 @@ __global__ void ntt_batch_inputs_kernel(const BatchReq* __restrict__ reqs, uint6
   z[idx] = v;
 }
 
-// c_r = (S_2r (*) S_2r+1) (*) factor = A R / P  (Montgomery products; factor = P^-1 2^64 mod p).
-__global__ void ntt_batch_mul_kernel(const uint32_t* __restrict__ z, uint32_t* __restrict__ c, uint64_t P, uint64_t nr,
-                                     uint32_t factor_m) {
-  const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nr * P) return;
-  const uint64_t r = idx / P, t = idx - r * P;
-  c[idx] = mont_mul(mont_mul(z[(2 * r) * P + t], z[(2 * r + 1) * P + t]), factor_m);
-}
-
-// Output word w of chunk request r (one warp per word): parities of c[n_t - 1 + i], identity bits.
+// Output word w of chunk request r (one warp per word): parities of c[n_t - 1 + i] (entry 2r+1),
+// identity bits.
 __global__ void ntt_batch_extract_kernel(const BatchReq* __restrict__ reqs, uint64_t nr, uint64_t max_mw,
                                          const uint32_t* __restrict__ c, uint64_t P, uint32_t* __restrict__ out_stage) {
   const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -310,7 +482,7 @@ __global__ void ntt_batch_extract_kernel(const BatchReq* __restrict__ reqs, uint
   const BatchReq& q = reqs[r];
   if (w >= q.mw) return;  // warp-uniform
   const uint64_t i = 32 * w + lane;
-  const uint32_t bit = (i < q.m) ? (c[r * P + q.n_t - 1 + i] & 1u) : 0u;
+  const uint32_t bit = (i < q.m) ? (c[(2 * r + 1) * P + q.n_t - 1 + i] & 1u) : 0u;
   uint32_t word = __ballot_sync(0xffffffffu, bit);
   const uint32_t ident = (q.form == QRNG_FORM_MODIFIED && i < q.m) ? bit_at(q.raw, q.raw_bit_off + q.id_off + i) : 0u;
   word ^= __ballot_sync(0xffffffffu, ident);
@@ -324,31 +496,22 @@ cudaError_t launch_ntt_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P,
                              uint32_t* kernels) {
   uint32_t logP = 0;
   while ((1ull << logP) < P) ++logP;
+  const NttPlan pl = ntt_plan(logP);
   cudaError_t e;
-  if (ws.ntt_P != P) {
-    if ((e = ws.ntt_tw.ensure((P / 2) * sizeof(uint32_t))) != cudaSuccess) return e;
-    const uint32_t omega = pow_mod(kGen, (kP - 1) / P);
-    ntt_twiddle_kernel<<<grid_for(ceil_div(P / 2, 256), 128), 128, 0, s>>>(
-        ws.ntt_tw.as<uint32_t>(), P / 2, to_mont(omega), to_mont(1), to_mont(pow_mod(omega, 256)));
-    ++*kernels;
-    ws.ntt_P = P;
-  }
+  if ((e = ensure_twiddles(ws, P, s, kernels)) != cudaSuccess) return e;
   if ((e = ws.buf0.ensure(2 * nr * P * sizeof(uint32_t))) != cudaSuccess) return e;
-  if ((e = ws.buf1.ensure(2 * nr * P * sizeof(uint32_t))) != cudaSuccess) return e;
-  uint32_t* b0p = ws.buf0.as<uint32_t>();
-  uint32_t* b1p = ws.buf1.as<uint32_t>();
-  ntt_batch_inputs_kernel<<<grid_for(2 * nr * P, 256), 256, 0, s>>>(reqs_dev, nr, b0p, P);
+  uint32_t* z = ws.buf0.as<uint32_t>();
+  const uint32_t* tw = ws.ntt_tw.as<uint32_t>();
+  ntt_batch_inputs_kernel<<<grid_for(2 * nr * P, 256), 256, 0, s>>>(reqs_dev, nr, z, P);
   ++*kernels;
-  uint32_t* spec = nullptr;
-  if ((e = run_ntt(b0p, b1p, ws.ntt_tw.as<uint32_t>(), P, logP, 2 * nr, 0, s, kernels, &spec)) != cudaSuccess)
-    return e;
-  uint32_t* other = (spec == b0p) ? b1p : b0p;
+  // both entries of every request forward, then per row: the product (*) P^-1 2^64, inverse row
+  // transform into entry 2r+1, then the inverse columns of the odd entries
+  const uint32_t* st = ws.ntt_stage.as<uint32_t>();
+  if ((e = ntt_columns<false>(z, st, pl, 2 * nr, 1, 0, s, kernels)) != cudaSuccess) return e;
   const uint32_t factor_m = to_mont(to_mont(pow_mod(P % kP, kP - 2)));
-  ntt_batch_mul_kernel<<<grid_for(nr * P, 256), 256, 0, s>>>(spec, other, P, nr, factor_m);
-  ++*kernels;
-  uint32_t* res = nullptr;
-  if ((e = run_ntt(other, spec, ws.ntt_tw.as<uint32_t>(), P, logP, nr, 1, s, kernels, &res)) != cudaSuccess) return e;
-  ntt_batch_extract_kernel<<<grid_for(nr * max_mw * 32, 256), 256, 0, s>>>(reqs_dev, nr, max_mw, res, P, out_stage);
+  if ((e = ntt_rows<kRowsPairs>(z, nullptr, tw, st, pl, nr, factor_m, s, kernels)) != cudaSuccess) return e;
+  if ((e = ntt_columns<true>(z, st, pl, nr, 2, 1, s, kernels)) != cudaSuccess) return e;
+  ntt_batch_extract_kernel<<<grid_for(nr * max_mw * 32, 256), 256, 0, s>>>(reqs_dev, nr, max_mw, z, P, out_stage);
   ++*kernels;
   return cudaGetLastError();
 }
@@ -360,49 +523,37 @@ cudaError_t launch_ntt(const DirectArgs& d, const uint8_t* seed, uint64_t L_t, F
   if (P > (1ull << 27)) return cudaErrorInvalidValue;
   uint32_t logP = 0;
   while ((1ull << logP) < P) ++logP;
+  const NttPlan pl = ntt_plan(logP);
   cudaError_t e;
-  if (ws.ntt_P != P) {
-    if ((e = ws.ntt_tw.ensure((P / 2) * sizeof(uint32_t))) != cudaSuccess) return e;
-    const uint32_t omega = pow_mod(kGen, (kP - 1) / P);  // primitive P-th root of unity
-    const uint32_t omega_m = to_mont(omega);
-    const uint32_t step_m = to_mont(pow_mod(omega, 256));
-    ntt_twiddle_kernel<<<grid_for(ceil_div(P / 2, 256), 128), 128, 0, s>>>(ws.ntt_tw.as<uint32_t>(), P / 2, omega_m,
-                                                                          to_mont(1), step_m);
-    ++*kernels;
-    ws.ntt_P = P;
-  }
-  uint64_t chunk = kFftWorkspaceBytes / (2 * P * sizeof(uint32_t));
+  if ((e = ensure_twiddles(ws, P, s, kernels)) != cudaSuccess) return e;
+  uint64_t chunk = kFftWorkspaceBytes / (P * sizeof(uint32_t));
   if (chunk < 1) chunk = 1;
   if (chunk > d.num_blocks) chunk = d.num_blocks;
   if ((e = ws.buf0.ensure(chunk * P * sizeof(uint32_t))) != cudaSuccess) return e;
-  if ((e = ws.buf1.ensure(chunk * P * sizeof(uint32_t))) != cudaSuccess) return e;
   if ((e = ws.spec.ensure(P * sizeof(uint32_t))) != cudaSuccess) return e;
-  uint32_t* b0p = ws.buf0.as<uint32_t>();
-  uint32_t* b1p = ws.buf1.as<uint32_t>();
+  uint32_t* z = ws.buf0.as<uint32_t>();
+  uint32_t* spec = ws.spec.as<uint32_t>();
+  const uint32_t* tw = ws.ntt_tw.as<uint32_t>();
 
-  // seed spectrum, scaled by P^-1 and kept in Montgomery form
-  uint32_t* res = nullptr;
-  ntt_seed_kernel<<<grid_for(P, 256), 256, 0, s>>>(seed, L_t, b0p, P);
+  // seed spectrum (permuted order of the row transforms), scaled by P^-1, in Montgomery form
+  ntt_seed_kernel<<<grid_for(P, 256), 256, 0, s>>>(seed, L_t, spec, P);
   ++*kernels;
-  if ((e = run_ntt(b0p, b1p, ws.ntt_tw.as<uint32_t>(), P, logP, 1, 0, s, kernels, &res)) != cudaSuccess) return e;
+  const uint32_t* st = ws.ntt_stage.as<uint32_t>();
+  if ((e = ntt_columns<false>(spec, st, pl, 1, 1, 0, s, kernels)) != cudaSuccess) return e;
+  if ((e = ntt_rows<kRowsForward>(spec, nullptr, tw, st, pl, 1, 0, s, kernels)) != cudaSuccess) return e;
   const uint32_t pinv = pow_mod(P % kP, kP - 2);
   const uint32_t factor_m = to_mont(to_mont(pinv));  // P^-1 2^64 mod p: one product leaves P^-1 2^32
-  ntt_scale_kernel<<<grid_for(P, 256), 256, 0, s>>>(res, P, factor_m);
+  ntt_scale_kernel<<<grid_for(P, 256), 256, 0, s>>>(spec, P, factor_m);
   ++*kernels;
-  if ((e = cudaMemcpyAsync(ws.spec.p, res, P * sizeof(uint32_t), cudaMemcpyDeviceToDevice, s)) != cudaSuccess) return e;
 
   for (uint64_t bb = 0; bb < d.num_blocks; bb += chunk) {
     const uint64_t nb = (d.num_blocks - bb) < chunk ? (d.num_blocks - bb) : chunk;
-    ntt_pack_kernel<<<grid_for(nb * P, 256), 256, 0, s>>>(d.raw, d.raw_stride, n_t, d.num_blocks, bb, nb, b0p, P);
+    ntt_pack_kernel<<<grid_for(nb * P, 256), 256, 0, s>>>(d.raw, d.raw_stride, n_t, d.num_blocks, bb, nb, z, P);
     ++*kernels;
-    if ((e = run_ntt(b0p, b1p, ws.ntt_tw.as<uint32_t>(), P, logP, nb, 0, s, kernels, &res)) != cudaSuccess) return e;
-    ntt_mul_kernel<<<grid_for(nb * P, 256), 256, 0, s>>>(res, ws.spec.as<uint32_t>(), P, nb * P);
-    ++*kernels;
-    uint32_t* other = (res == b0p) ? b1p : b0p;
-    uint32_t* fin = nullptr;
-    if ((e = run_ntt(res, other, ws.ntt_tw.as<uint32_t>(), P, logP, nb, 1, s, kernels, &fin)) != cudaSuccess)
-      return e;
-    ntt_extract_kernel<<<grid_for(nb * d.mw * 32, 256), 256, 0, s>>>(fin, P, n_t, d.m, d.mw, d.raw, d.raw_stride,
+    if ((e = ntt_columns<false>(z, st, pl, nb, 1, 0, s, kernels)) != cudaSuccess) return e;
+    if ((e = ntt_rows<kRowsConvolve>(z, spec, tw, st, pl, nb, 0, s, kernels)) != cudaSuccess) return e;
+    if ((e = ntt_columns<true>(z, st, pl, nb, 1, 0, s, kernels)) != cudaSuccess) return e;
+    ntt_extract_kernel<<<grid_for(nb * d.mw * 32, 256), 256, 0, s>>>(z, P, n_t, d.m, d.mw, d.raw, d.raw_stride,
                                                                      d.modified, d.id_off, d.num_blocks, bb, nb,
                                                                      d.out, d.out_stride);
     ++*kernels;

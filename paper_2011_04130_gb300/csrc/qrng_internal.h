@@ -145,7 +145,7 @@ cudaError_t launch_batch_pack(const BatchReq* reqs, uint32_t nreq, uint64_t dst_
 // ---- FFT routes (k_fft.cu) ----
 constexpr uint64_t kFftWorkspaceBytes = 1ull << 31;  // budget for the FP64 ping-pong buffers
 struct FftWorkspace {
-  DevBuf buf0, buf1, spec, tw, tw32, ntt_tw;
+  DevBuf buf0, buf1, spec, tw, tw32, ntt_tw, ntt_stage;
   uint64_t tw_P = 0;                    // length the FP64 twiddle table holds
   uint64_t ntt_P = 0;                   // length the number-theoretic twiddle table holds
   unsigned long long* worst = nullptr;  // device: bits of the largest |s - round(s)| (a double)
@@ -156,6 +156,7 @@ struct FftWorkspace {
     tw.release();
     tw32.release();
     ntt_tw.release();
+    ntt_stage.release();
     tw_P = 0;
     ntt_P = 0;
   }

@@ -48,9 +48,11 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--blocks", type=int, default=0,
                    help="hash only the first BLOCKS blocks (a smaller case for profiler captures)")
-    p.add_argument("--workload", default="laser", choices=["laser", "single", "sweep", "tc", "uneven", "forms"],
+    p.add_argument("--workload", default="laser",
+                   choices=["laser", "single", "sweep", "tc", "uneven", "forms", "long"],
                    help="laser: the headline stream (default); single: one 4096-bit block; sweep: block-length "
-                        "sweep on a 2^30-bit stream; tc: m=6144, n=8192, 4096 blocks; uneven: 10,000 requests")
+                        "sweep on a 2^30-bit stream; tc: m=6144, n=8192, 4096 blocks; uneven: 10,000 requests; "
+                        "long: 64 blocks of 2^22 bits (the transform route's profiling case)")
     p.add_argument("--sweep-algos", default="direct,gemm_tc,gemm_fp4,gemm_fp4_pair,ntt,fft64",
                    help="algorithms timed at each block length of the sweep")
     p.add_argument("--uneven-max-log2n", type=float, default=22.0,
@@ -523,6 +525,28 @@ def run_tc(args):
     return res
 
 
+def run_long(args):
+    """64 blocks of n = 2^22 raw bits, m = 0.75 n, modified form, one seed: a 2^28-bit stream on the
+    long-block route (--algo, default ntt), small enough for a profiler capture."""
+    import torch
+
+    import paper_2011_04130_gb300 as q
+
+    torch.cuda.set_device(0)
+    ctx = q.Context(0)
+    c = W.CFG3
+    n, B = 1 << 22, 64
+    m = int(n * c["ratio"])
+    raw = torch.from_numpy(W.random_bits(n * B, c["raw_seed"])).cuda()
+    seed = torch.from_numpy(W.random_bits(n - 1, c["seed_seed"] + 22)).cuda()
+    out = torch.empty(m * B // 8, dtype=torch.uint8, device="cuda")
+    name = "ntt" if args.algo == "auto" else args.algo
+    kms, cms, _ = _time_extract(q, ctx, raw, n, m, seed, 1, ALGOS[name], B, out, reps=args.steps, warmup=args.warmup)
+    ctx.close()
+    return {"workload": "64 blocks of 2^22 bits, m = 0.75n, modified form", "algo": name, "unit": UNIT,
+            "call_ms": cms, "gbps": B * m / (cms / 1e3) / 1e9, "data": "synthetic"}
+
+
 def run_single(args):
     """One 4096-bit block, m = 2048, plus the min-entropy of 65,536 samples: latency."""
     import torch
@@ -617,7 +641,7 @@ def main():
         res = run_reference(args, world, rank)
     elif args.workload != "laser":
         res = {"sweep": run_sweep, "tc": run_tc, "single": run_single, "uneven": run_uneven,
-               "forms": run_forms}[args.workload](args)
+               "forms": run_forms, "long": run_long}[args.workload](args)
     else:
         res = run_ours(args, world, rank, local)
     if rank == 0 and res is not None:

@@ -124,9 +124,10 @@ NttPlan ntt_plan(uint32_t logP) {
   return pl;
 }
 
-// Stage roots: st[2^s + j] = w_(2^(s+1))^j and st[kStageEntries + 2^s + j] = w_(2^(s+1))^-j
-// (Montgomery form, s < 16, j < 2^s), where w_(2^(s+1)) = g^((p-1)/2^(s+1)) is the same root as
-// w_P^(P/2^(s+1)) for every transform length P. One stage reads a contiguous run.
+// Stage roots for the radix-16/4/2 passes, in ordinary form with Shoup quotients: for t = 2^s + j
+// (s < 16, j < 2^s), st[t] = w_(2^(s+1))^j, st[E + t] = floor(st[t] 2^32 / p), st[2E + t] and
+// st[3E + t] the same for the inverse root (E = kStageEntries). w_(2^(s+1)) = g^((p-1)/2^(s+1)) is the
+// same root as w_P^(P/2^(s+1)) for every transform length P; one stage reads contiguous runs.
 constexpr uint32_t kStageLog = 16;
 constexpr uint32_t kStageEntries = 1u << kStageLog;
 
@@ -139,110 +140,106 @@ __device__ __forceinline__ uint32_t pow_m(uint32_t b, uint32_t e, uint32_t one_m
   return acc;
 }
 
-// g_m = g, one_m = 1 in Montgomery form. Thread t = 2^s + j: w_(2^(s+1)) = g^((p-1)/2^(s+1)),
-// its inverse g^((p-1) - (p-1)/2^(s+1)), each to the power j.
+// g_m = g and one_m = 1 in Montgomery form (a Montgomery product with 1 returns the ordinary residue).
 __global__ void ntt_stage_table_kernel(uint32_t* __restrict__ st, uint32_t g_m, uint32_t one_m) {
   const uint32_t t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t == 0 || t >= kStageEntries) return;
   const uint32_t s = 31 - __clz(t), j = t - (1u << s);
   const uint32_t e = (kP - 1) >> (s + 1);
-  st[t] = pow_m(pow_m(g_m, e, one_m), j, one_m);
-  st[kStageEntries + t] = pow_m(pow_m(g_m, (kP - 1) - e, one_m), j, one_m);
+  const uint32_t w = mont_mul(pow_m(pow_m(g_m, e, one_m), j, one_m), 1u);
+  const uint32_t wi = mont_mul(pow_m(pow_m(g_m, (kP - 1) - e, one_m), j, one_m), 1u);
+  st[t] = w;
+  st[kStageEntries + t] = (uint32_t)(((uint64_t)w << 32) / kP);
+  st[2 * kStageEntries + t] = wi;
+  st[3 * kStageEntries + t] = (uint32_t)(((uint64_t)wi << 32) / kP);
 }
 
-// Radix-4 pass (stages s and s-1, h = 2^(s-1)) on four elements x0..x3 = x[i + q h]:
-// forward decimation in frequency, or inverse decimation in time (stages s-1 then s).
+// x w mod p for a constant w < p with its Shoup quotient wq = floor(w 2^32 / p): q = floor(x wq / 2^32)
+// is floor(x w / p) or one less, so x w - q p (exact in 32 bits) lies in [0, 2p).
+__device__ __forceinline__ uint32_t shoup_mul(uint32_t x, uint32_t w, uint32_t wq) {
+  const uint32_t r = x * w - __umulhi(x, wq) * kP;
+  const uint32_t t = r - kP;
+  return t < r ? t : r;
+}
+
+// Butterflies of one stage: forward (decimation in frequency) a' = a + b, b' = (a - b) w; inverse
+// (decimation in time) t = b w^-1, a' = a + t, b' = a - t. The root index k selects w_(2^(s+1))^j.
 template <bool kInverse>
-__device__ __forceinline__ void radix4(uint32_t& x0, uint32_t& x1, uint32_t& x2, uint32_t& x3,
-                                       const uint32_t* __restrict__ st, uint32_t s, uint32_t j) {
-  const uint32_t h = 1u << (s - 1);
+__device__ __forceinline__ void bfly(uint32_t& a, uint32_t& b, const uint32_t* __restrict__ st, uint32_t k) {
   if (!kInverse) {
-    const uint32_t wa = __ldg(st + (1u << s) + j), wb = __ldg(st + (1u << s) + j + h);
-    const uint32_t wc = __ldg(st + h + j);
-    const uint32_t y0 = add_mod(x0, x2), y2 = mont_mul(wa, sub_mod(x0, x2));
-    const uint32_t y1 = add_mod(x1, x3), y3 = mont_mul(wb, sub_mod(x1, x3));
-    x0 = add_mod(y0, y1);
-    x1 = mont_mul(wc, sub_mod(y0, y1));
-    x2 = add_mod(y2, y3);
-    x3 = mont_mul(wc, sub_mod(y2, y3));
+    const uint32_t w = __ldg(st + k), wq = __ldg(st + kStageEntries + k);
+    const uint32_t s0 = add_mod(a, b);
+    b = shoup_mul(sub_mod(a, b), w, wq);
+    a = s0;
   } else {
-    const uint32_t* it = st + kStageEntries;
-    const uint32_t wc = __ldg(it + h + j);
-    const uint32_t wa = __ldg(it + (1u << s) + j), wb = __ldg(it + (1u << s) + j + h);
-    uint32_t t = mont_mul(wc, x1);
-    const uint32_t y0 = add_mod(x0, t), y1 = sub_mod(x0, t);
-    t = mont_mul(wc, x3);
-    const uint32_t y2 = add_mod(x2, t), y3 = sub_mod(x2, t);
-    t = mont_mul(wa, y2);
-    x0 = add_mod(y0, t);
-    x2 = sub_mod(y0, t);
-    t = mont_mul(wb, y3);
-    x1 = add_mod(y1, t);
-    x3 = sub_mod(y1, t);
+    const uint32_t w = __ldg(st + 2 * kStageEntries + k), wq = __ldg(st + 3 * kStageEntries + k);
+    const uint32_t t = shoup_mul(b, w, wq);
+    b = sub_mod(a, t);
+    a = add_mod(a, t);
   }
 }
 
-template <bool kInverse>
-__device__ __forceinline__ void radix2(uint32_t& x0, uint32_t& x1, const uint32_t* __restrict__ st, uint32_t s,
-                                       uint32_t j) {
-  if (!kInverse) {
-    const uint32_t w = __ldg(st + (1u << s) + j);
-    const uint32_t a = x0;
-    x0 = add_mod(a, x1);
-    x1 = mont_mul(w, sub_mod(a, x1));
-  } else {
-    const uint32_t t = mont_mul(__ldg(st + kStageEntries + (1u << s) + j), x1);
-    const uint32_t a = x0;
-    x0 = add_mod(a, t);
-    x1 = sub_mod(a, t);
+// One pass of R = 2^G stages s, s-1, .., s-G+1 on R elements x[q] = X[i0 + q h], h = 2^(s-G+1),
+// j = i0 mod h: forward from the widest span down, inverse from the narrowest up. The stage of span
+// 2^t pairs q with q + 2^(t-s+G-1) and uses root index 2^t + j + (q mod 2^(t-s+G-1)) h.
+template <bool kInverse, int G>
+__device__ __forceinline__ void radix_pass(uint32_t (&x)[1 << G], const uint32_t* __restrict__ st, uint32_t s,
+                                           uint32_t j) {
+  constexpr int R = 1 << G;
+  const uint32_t h = 1u << (s - G + 1);
+#pragma unroll
+  for (int gi = 0; gi < G; ++gi) {
+    const int g = kInverse ? gi : G - 1 - gi;  // local span 2^g
+    const uint32_t base = (1u << (s - G + 1 + g)) + j;
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      if (q & (1 << g)) continue;
+      bfly<kInverse>(x[q], x[q + (1 << g)], st, base + (uint32_t)(q & ((1 << g) - 1)) * h);
+    }
   }
 }
 
 // In-place length-2^K transforms of `cols` interleaved sequences in shared memory (element r of
 // column c at x[(r << logC) | c]): forward = decimation in frequency (natural in, bit-reversed out),
-// inverse = decimation in time with inverse roots (bit-reversed in, natural out). Radix-4 passes,
-// one radix-2 stage when K is odd (the widest span first going forward, last going back).
+// inverse = decimation in time with inverse roots (bit-reversed in, natural out). The stages are
+// grouped from the widest span down into radix-16 passes, then one radix-4 and one radix-2 pass as
+// needed; the inverse runs the same groups in the opposite order.
+template <bool kInverse, int G>
+__device__ __forceinline__ void smem_pass(uint32_t* __restrict__ x, uint32_t K, uint32_t logC, uint32_t s,
+                                          const uint32_t* __restrict__ st) {
+  constexpr int R = 1 << G;
+  const uint32_t C = 1u << logC;
+  const uint32_t lh = s - G + 1;  // log2 h
+  for (uint32_t u = threadIdx.x; u < (1u << (K - G + logC)); u += blockDim.x) {
+    const uint32_t c = u & (C - 1), v = u >> logC;
+    const uint32_t j = v & ((1u << lh) - 1);
+    const uint32_t r0 = ((v >> lh) << (s + 1)) | j;
+    uint32_t* p0 = x + ((r0 << logC) | c);
+    const uint32_t dh = 1u << (lh + logC);
+    uint32_t a[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) a[q] = p0[q * dh];
+    radix_pass<kInverse, G>(a, st, s, j);
+#pragma unroll
+    for (int q = 0; q < R; ++q) p0[q * dh] = a[q];
+  }
+  __syncthreads();
+}
+
 template <bool kInverse>
 __device__ __forceinline__ void smem_transform(uint32_t* __restrict__ x, uint32_t K, uint32_t logC,
                                                const uint32_t* __restrict__ st) {
-  if (K == 0) return;
-  const uint32_t C = 1u << logC;
-  const bool odd = K & 1u;
-  // forward: spans from 2^(K-1) down; inverse: up to 2^(K-1)
-  const uint32_t passes = K >> 1;
-  for (uint32_t it = 0; it < passes + (odd ? 1u : 0u); ++it) {
-    // pass order: forward [radix-2 at s = K-1 if odd], radix-4 at s = top, top-2, ...; inverse reversed
-    const uint32_t fit = kInverse ? passes + (odd ? 1u : 0u) - 1 - it : it;
-    if (odd && fit == 0) {
-      const uint32_t s = K - 1;
-      for (uint32_t u = threadIdx.x; u < (1u << (K - 1 + logC)); u += blockDim.x) {
-        const uint32_t c = u & (C - 1), v = u >> logC;
-        const uint32_t j = v & ((1u << s) - 1);
-        const uint32_t r0 = ((v >> s) << (s + 1)) | j;
-        uint32_t* p0 = x + ((r0 << logC) | c);
-        uint32_t a0 = p0[0], a1 = p0[(1u << s) << logC];
-        radix2<kInverse>(a0, a1, st, s, j);
-        p0[0] = a0;
-        p0[(1u << s) << logC] = a1;
-      }
+  const uint32_t n16 = K / 4, rem = K % 4;  // radix-16 passes, then radix-4 (rem >= 2), radix-2 (odd)
+  const uint32_t npass = n16 + (rem >= 2 ? 1u : 0u) + (rem & 1u);
+  for (uint32_t it = 0; it < npass; ++it) {
+    const uint32_t p = kInverse ? npass - 1 - it : it;  // pass p covers the p-th group from the top
+    if (p < n16) {
+      smem_pass<kInverse, 4>(x, K, logC, K - 1 - 4 * p, st);
+    } else if (p == n16 && rem >= 2) {
+      smem_pass<kInverse, 2>(x, K, logC, K - 1 - 4 * n16, st);
     } else {
-      const uint32_t s = K - 1 - 2 * fit + (odd ? 1u : 0u);  // stages s and s-1
-      const uint32_t h = 1u << (s - 1);
-      for (uint32_t u = threadIdx.x; u < (1u << (K - 2 + logC)); u += blockDim.x) {
-        const uint32_t c = u & (C - 1), v = u >> logC;
-        const uint32_t j = v & (h - 1);
-        const uint32_t r0 = ((v >> (s - 1)) << (s + 1)) | j;
-        uint32_t* p0 = x + ((r0 << logC) | c);
-        const uint32_t dh = h << logC;
-        uint32_t a0 = p0[0], a1 = p0[dh], a2 = p0[2 * dh], a3 = p0[3 * dh];
-        radix4<kInverse>(a0, a1, a2, a3, st, s, j);
-        p0[0] = a0;
-        p0[dh] = a1;
-        p0[2 * dh] = a2;
-        p0[3 * dh] = a3;
-      }
+      smem_pass<kInverse, 1>(x, K, logC, 0, st);
     }
-    __syncthreads();
   }
 }
 
@@ -286,7 +283,7 @@ enum { kRowsForward = 0, kRowsConvolve = 1, kRowsPairs = 2 };
 //   kRowsPairs:    entries 2r and 2r+1 (a request's seed and raw bits) both forward, their product
 //                  (*) factor, inverse row transform and twiddle, written to entry 2r+1.
 template <int kMode>
-__global__ void __launch_bounds__(512) ntt_rows_kernel(uint32_t* __restrict__ z, const uint32_t* __restrict__ spec,
+__global__ void __launch_bounds__(256) ntt_rows_kernel(uint32_t* __restrict__ z, const uint32_t* __restrict__ spec,
                                                        const uint32_t* __restrict__ tw,
                                                        const uint32_t* __restrict__ st, NttPlan pl,
                                                        uint32_t factor_m) {
@@ -397,7 +394,8 @@ __global__ void ntt_extract_kernel(const uint32_t* __restrict__ z, uint64_t P, u
 
 inline unsigned grid_for(uint64_t total, int threads) { return (unsigned)ceil_div(total, (uint64_t)threads); }
 
-constexpr int kNttThreads = 512;
+constexpr int kNttThreads = 512;     // column tiles
+constexpr int kNttRowThreads = 256;  // rows: 2^12 elements, 256 radix-16 items
 
 // Columns forward/inverse over the entries ent_off, ent_off + ent_stride, ... (num_ent of them).
 template <bool kInverse>
@@ -423,7 +421,7 @@ cudaError_t ntt_rows(uint32_t* z, const uint32_t* spec, const uint32_t* tw, cons
   cudaError_t e = cudaFuncSetAttribute(ntt_rows_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const uint64_t ctas = num_rows_ent << pl.H;
-  ntt_rows_kernel<kMode><<<(unsigned)ctas, kNttThreads, smem, s>>>(z, spec, tw, st, pl, factor_m);
+  ntt_rows_kernel<kMode><<<(unsigned)ctas, kNttRowThreads, smem, s>>>(z, spec, tw, st, pl, factor_m);
   ++*kernels;
   return cudaGetLastError();
 }
@@ -431,7 +429,7 @@ cudaError_t ntt_rows(uint32_t* z, const uint32_t* spec, const uint32_t* tw, cons
 cudaError_t ensure_twiddles(FftWorkspace& ws, uint64_t P, cudaStream_t s, uint32_t* kernels) {
   cudaError_t e;
   if (!ws.ntt_stage.p) {
-    if ((e = ws.ntt_stage.ensure(2 * kStageEntries * sizeof(uint32_t))) != cudaSuccess) return e;
+    if ((e = ws.ntt_stage.ensure(4 * kStageEntries * sizeof(uint32_t))) != cudaSuccess) return e;
     ntt_stage_table_kernel<<<kStageEntries / 256, 256, 0, s>>>(ws.ntt_stage.as<uint32_t>(), to_mont(kGen),
                                                                  to_mont(1));
     ++*kernels;

@@ -204,7 +204,11 @@ __device__ __forceinline__ void radix_pass(uint32_t (&x)[1 << G], const uint32_t
 // inverse = decimation in time with inverse roots (bit-reversed in, natural out). The stages are
 // grouped from the widest span down into radix-16 passes, then one radix-4 and one radix-2 pass as
 // needed; the inverse runs the same groups in the opposite order.
-template <bool kInverse, int G>
+// Shared-memory position of element t in a padded row (one spare word after every 16): the
+// elements 16 apart that the last radix-16 pass gives each thread then fall in distinct banks.
+__device__ __forceinline__ uint32_t pad16(uint32_t t) { return t + (t >> 4); }
+
+template <bool kInverse, int G, bool kPad>
 __device__ __forceinline__ void smem_pass(uint32_t* __restrict__ x, uint32_t K, uint32_t logC, uint32_t s,
                                           const uint32_t* __restrict__ st) {
   constexpr int R = 1 << G;
@@ -214,19 +218,27 @@ __device__ __forceinline__ void smem_pass(uint32_t* __restrict__ x, uint32_t K, 
     const uint32_t c = u & (C - 1), v = u >> logC;
     const uint32_t j = v & ((1u << lh) - 1);
     const uint32_t r0 = ((v >> lh) << (s + 1)) | j;
-    uint32_t* p0 = x + ((r0 << logC) | c);
-    const uint32_t dh = 1u << (lh + logC);
     uint32_t a[R];
+    if (kPad) {  // rows only (logC = 0)
 #pragma unroll
-    for (int q = 0; q < R; ++q) a[q] = p0[q * dh];
-    radix_pass<kInverse, G>(a, st, s, j);
+      for (int q = 0; q < R; ++q) a[q] = x[pad16(r0 + ((uint32_t)q << lh))];
+      radix_pass<kInverse, G>(a, st, s, j);
 #pragma unroll
-    for (int q = 0; q < R; ++q) p0[q * dh] = a[q];
+      for (int q = 0; q < R; ++q) x[pad16(r0 + ((uint32_t)q << lh))] = a[q];
+    } else {
+      uint32_t* p0 = x + ((r0 << logC) | c);
+      const uint32_t dh = 1u << (lh + logC);
+#pragma unroll
+      for (int q = 0; q < R; ++q) a[q] = p0[q * dh];
+      radix_pass<kInverse, G>(a, st, s, j);
+#pragma unroll
+      for (int q = 0; q < R; ++q) p0[q * dh] = a[q];
+    }
   }
   __syncthreads();
 }
 
-template <bool kInverse>
+template <bool kInverse, bool kPad = false>
 __device__ __forceinline__ void smem_transform(uint32_t* __restrict__ x, uint32_t K, uint32_t logC,
                                                const uint32_t* __restrict__ st) {
   const uint32_t n16 = K / 4, rem = K % 4;  // radix-16 passes, then radix-4 (rem >= 2), radix-2 (odd)
@@ -234,42 +246,80 @@ __device__ __forceinline__ void smem_transform(uint32_t* __restrict__ x, uint32_
   for (uint32_t it = 0; it < npass; ++it) {
     const uint32_t p = kInverse ? npass - 1 - it : it;  // pass p covers the p-th group from the top
     if (p < n16) {
-      smem_pass<kInverse, 4>(x, K, logC, K - 1 - 4 * p, st);
+      smem_pass<kInverse, 4, kPad>(x, K, logC, K - 1 - 4 * p, st);
     } else if (p == n16 && rem >= 2) {
-      smem_pass<kInverse, 2>(x, K, logC, K - 1 - 4 * n16, st);
+      smem_pass<kInverse, 2, kPad>(x, K, logC, K - 1 - 4 * n16, st);
     } else {
-      smem_pass<kInverse, 1>(x, K, logC, 0, st);
+      smem_pass<kInverse, 1, kPad>(x, K, logC, 0, st);
     }
   }
 }
 
+// Column I/O: entries in z both ways; raw bits in (forward: the block's bits become the entries,
+// no packed copy); parity bits out (inverse: bit i of the block's parity array = entry i mod 2,
+// stored a byte per 8 columns of a row, instead of the entries).
+enum { kColsZ = 0, kColsFromBits = 1, kColsToParity = 2 };
+
+struct ColsIO {
+  const uint32_t* raw;   // kColsFromBits: block b's bits at raw + b stride (words), first n_t of them
+  uint64_t stride;
+  uint64_t n_t;
+  uint64_t b0;           // block of entry 0
+  uint64_t num_blocks;
+  uint8_t* parity;       // kColsToParity: P / 8 bytes per entry
+};
+
 // Length-2^H transforms down the columns of entries ent_off, ent_off + ent_stride, ... (row stride
 // 2^L); one CTA per tile of 2^H rows x 2^logW adjacent columns.
-template <bool kInverse>
+template <bool kInverse, int kIO>
 __global__ void __launch_bounds__(512) ntt_cols_kernel(uint32_t* __restrict__ z, const uint32_t* __restrict__ st,
-                                                       NttPlan pl, uint64_t ent_stride, uint64_t ent_off) {
+                                                       NttPlan pl, uint64_t ent_stride, uint64_t ent_off, ColsIO io) {
   extern __shared__ uint32_t col_sm[];
   const uint32_t tiles_per_ent = 1u << (pl.L - pl.logW);
-  const uint64_t ent = (uint64_t)blockIdx.x / tiles_per_ent;
-  const uint32_t c0 = (blockIdx.x % tiles_per_ent) << pl.logW;
-  const uint64_t P = 1ull << pl.logP;
-  uint32_t* zb = z + (ent * ent_stride + ent_off) * P + c0;
+  const uint64_t ent = (uint64_t)blockIdx.x >> (pl.L - pl.logW);
+  const uint32_t c0 = (blockIdx.x & (tiles_per_ent - 1)) << pl.logW;
+  const uint64_t eidx = ent * ent_stride + ent_off;
+  uint32_t* zb = z + (eidx << pl.logP) + c0;
   const uint32_t W = 1u << pl.logW, n = 1u << (pl.H + pl.logW);
-  for (uint32_t e = threadIdx.x; e < n; e += blockDim.x)
-    col_sm[e] = zb[((uint64_t)(e >> pl.logW) << pl.L) + (e & (W - 1))];
+  if (kIO == kColsFromBits) {
+    const uint64_t b = io.b0 + eidx;
+    const uint32_t* rb = io.raw + b * io.stride;
+    const bool live = b < io.num_blocks;
+    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
+      const uint64_t i = ((uint64_t)(e >> pl.logW) << pl.L) + c0 + (e & (W - 1));
+      col_sm[e] = (live && i < io.n_t) ? ((__ldg(rb + (i >> 5)) >> (i & 31)) & 1u) : 0u;
+    }
+  } else {
+    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x)
+      col_sm[e] = zb[((uint64_t)(e >> pl.logW) << pl.L) + (e & (W - 1))];
+  }
   __syncthreads();
   smem_transform<kInverse>(col_sm, pl.H, pl.logW, st);
-  for (uint32_t e = threadIdx.x; e < n; e += blockDim.x)
-    zb[((uint64_t)(e >> pl.logW) << pl.L) + (e & (W - 1))] = col_sm[e];
+  if (kIO == kColsToParity) {
+    // the tile's W columns of row r are entries (r << L) + c0 .. + W - 1: W / 8 bytes of parity bits
+    uint8_t* pb = io.parity + (eidx << (pl.logP - 3)) + (c0 >> 3);
+    const uint32_t bytes_per_row = W >> 3;
+    for (uint32_t u = threadIdx.x; u < (n >> 3); u += blockDim.x) {
+      const uint32_t r = u / bytes_per_row, k = u - r * bytes_per_row;
+      const uint32_t* src = col_sm + (r << pl.logW) + 8 * k;
+      uint32_t byte = 0;
+#pragma unroll
+      for (int t = 0; t < 8; ++t) byte |= (src[t] & 1u) << t;
+      pb[((uint64_t)r << (pl.L - 3)) + k] = (uint8_t)byte;
+    }
+  } else {
+    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x)
+      zb[((uint64_t)(e >> pl.logW) << pl.L) + (e & (W - 1))] = col_sm[e];
+  }
 }
 
-// Multiplies row element n2 by w_P^(+-n2 k1): the power is built from two tables of the row,
-// w^(k1 b) (b < 2^lob) and w^(2^lob k1 a), one Montgomery product apart.
+// Multiplies row element n2 (padded layout) by w_P^(+-n2 k1): the power is built from two tables of
+// the row, w^(k1 b) (b < 2^lob) and w^(2^lob k1 a), one Montgomery product apart.
 __device__ __forceinline__ void ntt_row_twiddle(uint32_t* __restrict__ x, const uint32_t* __restrict__ tlo,
                                                 const uint32_t* __restrict__ thi, uint32_t L, uint32_t lob) {
   for (uint32_t n2 = threadIdx.x; n2 < (1u << L); n2 += blockDim.x) {
     const uint32_t w = mont_mul(thi[n2 >> lob], tlo[n2 & ((1u << lob) - 1)]);
-    x[n2] = mont_mul(w, x[n2]);
+    x[pad16(n2)] = mont_mul(w, x[pad16(n2)]);
   }
   __syncthreads();
 }
@@ -289,20 +339,21 @@ __global__ void __launch_bounds__(256) ntt_rows_kernel(uint32_t* __restrict__ z,
                                                        uint32_t factor_m) {
   extern __shared__ uint32_t row_sm[];
   const uint32_t Lr = 1u << pl.L;
+  const uint32_t Lp = Lr + (Lr >> 4);  // padded row
   const uint32_t lob = pl.L < 6 ? pl.L : 6;
-  uint32_t* tlo = row_sm + (kMode == kRowsPairs ? 2 : 1) * Lr;  // w^(+-k1 b), b < 2^lob
+  uint32_t* tlo = row_sm + (kMode == kRowsPairs ? 2 : 1) * Lp;  // w^(+-k1 b), b < 2^lob
   uint32_t* thi = tlo + (1u << lob);                            // w^(+-2^lob k1 a)
+  uint32_t* row2 = row_sm + Lp;                                 // kRowsPairs: the raw entry's row
   const uint64_t P = 1ull << pl.logP, half = P >> 1;
-  const uint64_t rows = 1ull << pl.H;
-  const uint64_t ent = (uint64_t)blockIdx.x / rows;
-  const uint32_t rr = (uint32_t)(blockIdx.x % rows);
+  const uint64_t ent = (uint64_t)blockIdx.x >> pl.H;
+  const uint32_t rr = (uint32_t)(blockIdx.x & ((1u << pl.H) - 1));
   const uint32_t k1 = pl.H ? (__brev(rr) >> (32 - pl.H)) : 0u;
   const uint64_t e0 = (kMode == kRowsPairs) ? 2 * ent : ent;
-  uint32_t* x = z + e0 * P + ((uint64_t)rr << pl.L);
+  uint32_t* x = z + (e0 << pl.logP) + ((uint64_t)rr << pl.L);
   uint32_t* x2 = x + P;  // kRowsPairs: the raw entry
   for (uint32_t t = threadIdx.x; t < Lr; t += blockDim.x) {
-    row_sm[t] = x[t];
-    if (kMode == kRowsPairs) row_sm[Lr + t] = x2[t];
+    row_sm[pad16(t)] = x[t];
+    if (kMode == kRowsPairs) row2[pad16(t)] = x2[t];
   }
   if (pl.H) {
     for (uint32_t t = threadIdx.x; t < (1u << lob) + (Lr >> lob); t += blockDim.x) {
@@ -313,18 +364,19 @@ __global__ void __launch_bounds__(256) ntt_rows_kernel(uint32_t* __restrict__ z,
   __syncthreads();
   if (pl.H) {
     ntt_row_twiddle(row_sm, tlo, thi, pl.L, lob);
-    if (kMode == kRowsPairs) ntt_row_twiddle(row_sm + Lr, tlo, thi, pl.L, lob);
+    if (kMode == kRowsPairs) ntt_row_twiddle(row2, tlo, thi, pl.L, lob);
   }
-  smem_transform<false>(row_sm, pl.L, 0, st);
-  if (kMode == kRowsPairs) smem_transform<false>(row_sm + Lr, pl.L, 0, st);
+  smem_transform<false, true>(row_sm, pl.L, 0, st);
+  if (kMode == kRowsPairs) smem_transform<false, true>(row2, pl.L, 0, st);
   if (kMode == kRowsForward) {
-    for (uint32_t t = threadIdx.x; t < Lr; t += blockDim.x) x[t] = row_sm[t];
+    for (uint32_t t = threadIdx.x; t < Lr; t += blockDim.x) x[t] = row_sm[pad16(t)];
     return;
   }
   const uint32_t* sp = spec + ((uint64_t)rr << pl.L);
   for (uint32_t t = threadIdx.x; t < Lr; t += blockDim.x) {
-    if (kMode == kRowsConvolve) row_sm[t] = mont_mul(row_sm[t], __ldg(sp + t));
-    else row_sm[t] = mont_mul(mont_mul(row_sm[t], row_sm[Lr + t]), factor_m);
+    const uint32_t pt = pad16(t);
+    if (kMode == kRowsConvolve) row_sm[pt] = mont_mul(row_sm[pt], __ldg(sp + t));
+    else row_sm[pt] = mont_mul(mont_mul(row_sm[pt], row2[pt]), factor_m);
   }
   if (pl.H) {  // inverse twiddle tables (the forward ones were last read before the stage barriers)
     for (uint32_t t = threadIdx.x; t < (1u << lob) + (Lr >> lob); t += blockDim.x) {
@@ -333,10 +385,10 @@ __global__ void __launch_bounds__(256) ntt_rows_kernel(uint32_t* __restrict__ z,
     }
   }
   __syncthreads();
-  smem_transform<true>(row_sm, pl.L, 0, st);
+  smem_transform<true, true>(row_sm, pl.L, 0, st);
   if (pl.H) ntt_row_twiddle(row_sm, tlo, thi, pl.L, lob);
   uint32_t* dst = (kMode == kRowsPairs) ? x2 : x;
-  for (uint32_t t = threadIdx.x; t < Lr; t += blockDim.x) dst[t] = row_sm[t];
+  for (uint32_t t = threadIdx.x; t < Lr; t += blockDim.x) dst[t] = row_sm[pad16(t)];
 }
 
 __global__ void ntt_seed_kernel(const uint8_t* __restrict__ seed, uint64_t L, uint32_t* __restrict__ z, uint64_t P) {
@@ -354,12 +406,47 @@ __global__ void ntt_scale_kernel(uint32_t* __restrict__ z, uint64_t P, uint32_t 
 }
 
 __global__ void ntt_pack_kernel(const uint32_t* __restrict__ raw, uint64_t stride, uint64_t n_t, uint64_t num_blocks,
-                                uint64_t b0, uint64_t nb, uint32_t* __restrict__ z, uint64_t P) {
+                                uint64_t b0, uint64_t nb, uint32_t* __restrict__ z, uint32_t logP) {
   const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= nb * P) return;
-  const uint64_t bl = idx / P, t = idx - bl * P;
+  if (idx >= (nb << logP)) return;
+  const uint64_t bl = idx >> logP, t = idx & ((1ull << logP) - 1);
   const uint64_t b = b0 + bl;
   z[idx] = (t < n_t && b < num_blocks) ? ((raw[b * stride + (t >> 5)] >> (t & 31)) & 1u) : 0u;
+}
+
+// Output word w of block b0+bl from the block's parity bits (bit i = entry i mod 2 of the inverse
+// transform): bits n_t - 1 + 32 w .. + 31, one funnel shift of two words; identity bits for the
+// modified form.
+__global__ void ntt_parity_extract_kernel(const uint32_t* __restrict__ par, uint32_t logP, uint64_t n_t, uint64_t m,
+                                          uint64_t mw, const uint32_t* __restrict__ raw, uint64_t stride,
+                                          int modified, uint64_t id_off, uint64_t num_blocks, uint64_t b0,
+                                          uint64_t nb, uint32_t* __restrict__ out, uint64_t out_stride) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nb * mw) return;
+  const uint64_t bl = g / mw, w = g - bl * mw;
+  const uint64_t b = b0 + bl;
+  if (b >= num_blocks) return;
+  const uint64_t words = 1ull << (logP - 5);
+  const uint32_t* pb = par + bl * words;
+  const uint64_t pos = n_t - 1 + 32 * w;
+  const uint64_t q = pos >> 5;
+  const uint32_t sh = (uint32_t)(pos & 31);
+  const uint32_t lo = __ldg(pb + q);
+  const uint32_t hi = (sh && q + 1 < words) ? __ldg(pb + q + 1) : 0u;
+  uint32_t word = __funnelshift_r(lo, hi, sh);
+  const uint64_t rem = m - 32 * w;
+  const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+  word &= omask;
+  if (modified) {
+    const uint32_t* rr = raw + b * stride;
+    const uint64_t ip = id_off + 32 * w;
+    const uint64_t rq = ip >> 5;
+    const uint32_t rs = (uint32_t)(ip & 31);
+    const uint32_t rlo = __ldg(rr + rq);
+    const uint32_t rhi = (rs && rq + 1 < stride) ? __ldg(rr + rq + 1) : 0u;
+    word ^= __funnelshift_r(rlo, rhi, rs) & omask;
+  }
+  out[b * out_stride + w] = word;
 }
 
 // Output word w of block b0+bl: parities of c[n_t - 1 + i] (exact integers), identity bits.
@@ -398,16 +485,16 @@ constexpr int kNttThreads = 512;     // column tiles
 constexpr int kNttRowThreads = 256;  // rows: 2^12 elements, 256 radix-16 items
 
 // Columns forward/inverse over the entries ent_off, ent_off + ent_stride, ... (num_ent of them).
-template <bool kInverse>
+template <bool kInverse, int kIO>
 cudaError_t ntt_columns(uint32_t* z, const uint32_t* st, const NttPlan& pl, uint64_t num_ent, uint64_t ent_stride,
-                        uint64_t ent_off, cudaStream_t s, uint32_t* kernels) {
+                        uint64_t ent_off, const ColsIO& io, cudaStream_t s, uint32_t* kernels) {
   if (pl.H == 0) return cudaSuccess;
   const size_t smem = ((size_t)1 << (pl.H + pl.logW)) * sizeof(uint32_t);
-  cudaError_t e = cudaFuncSetAttribute(ntt_cols_kernel<kInverse>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+  cudaError_t e = cudaFuncSetAttribute(ntt_cols_kernel<kInverse, kIO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
   const uint64_t tiles = num_ent << (pl.L - pl.logW);
-  ntt_cols_kernel<kInverse><<<(unsigned)tiles, kNttThreads, smem, s>>>(z, st, pl, ent_stride, ent_off);
+  ntt_cols_kernel<kInverse, kIO><<<(unsigned)tiles, kNttThreads, smem, s>>>(z, st, pl, ent_stride, ent_off, io);
   ++*kernels;
   return cudaGetLastError();
 }
@@ -416,8 +503,9 @@ template <int kMode>
 cudaError_t ntt_rows(uint32_t* z, const uint32_t* spec, const uint32_t* tw, const uint32_t* st, const NttPlan& pl,
                      uint64_t num_rows_ent, uint32_t factor_m, cudaStream_t s, uint32_t* kernels) {
   const uint32_t lob = pl.L < 6 ? pl.L : 6;
+  const size_t padded = (1u << pl.L) + ((1u << pl.L) >> 4);
   const size_t smem =
-      ((size_t)(kMode == kRowsPairs ? 2 : 1) * (1u << pl.L) + (1u << lob) + (1u << (pl.L - lob))) * sizeof(uint32_t);
+      ((size_t)(kMode == kRowsPairs ? 2 : 1) * padded + (1u << lob) + (1u << (pl.L - lob))) * sizeof(uint32_t);
   cudaError_t e = cudaFuncSetAttribute(ntt_rows_kernel<kMode>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const uint64_t ctas = num_rows_ent << pl.H;
@@ -455,10 +543,10 @@ __device__ __forceinline__ uint32_t bit_at(const uint8_t* __restrict__ p, uint64
 // Entry 2r of the chunk holds request r's seed bits [0, L_t), entry 2r+1 its raw bits [0, n_t),
 // both zero-padded to P.
 __global__ void ntt_batch_inputs_kernel(const BatchReq* __restrict__ reqs, uint64_t nr, uint32_t* __restrict__ z,
-                                        uint64_t P) {
+                                        uint32_t logP) {
   const uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= 2 * nr * P) return;
-  const uint64_t e = idx / P, t = idx - e * P;
+  if (idx >= ((2 * nr) << logP)) return;
+  const uint64_t e = idx >> logP, t = idx & ((1ull << logP) - 1);
   const BatchReq& q = reqs[e >> 1];
   uint32_t v = 0;
   if (e & 1) {
@@ -500,15 +588,16 @@ cudaError_t launch_ntt_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P,
   if ((e = ws.buf0.ensure(2 * nr * P * sizeof(uint32_t))) != cudaSuccess) return e;
   uint32_t* z = ws.buf0.as<uint32_t>();
   const uint32_t* tw = ws.ntt_tw.as<uint32_t>();
-  ntt_batch_inputs_kernel<<<grid_for(2 * nr * P, 256), 256, 0, s>>>(reqs_dev, nr, z, P);
+  ntt_batch_inputs_kernel<<<grid_for(2 * nr * P, 256), 256, 0, s>>>(reqs_dev, nr, z, logP);
   ++*kernels;
   // both entries of every request forward, then per row: the product (*) P^-1 2^64, inverse row
   // transform into entry 2r+1, then the inverse columns of the odd entries
   const uint32_t* st = ws.ntt_stage.as<uint32_t>();
-  if ((e = ntt_columns<false>(z, st, pl, 2 * nr, 1, 0, s, kernels)) != cudaSuccess) return e;
+  const ColsIO none{};
+  if ((e = ntt_columns<false, kColsZ>(z, st, pl, 2 * nr, 1, 0, none, s, kernels)) != cudaSuccess) return e;
   const uint32_t factor_m = to_mont(to_mont(pow_mod(P % kP, kP - 2)));
   if ((e = ntt_rows<kRowsPairs>(z, nullptr, tw, st, pl, nr, factor_m, s, kernels)) != cudaSuccess) return e;
-  if ((e = ntt_columns<true>(z, st, pl, nr, 2, 1, s, kernels)) != cudaSuccess) return e;
+  if ((e = ntt_columns<true, kColsZ>(z, st, pl, nr, 2, 1, none, s, kernels)) != cudaSuccess) return e;
   ntt_batch_extract_kernel<<<grid_for(nr * max_mw * 32, 256), 256, 0, s>>>(reqs_dev, nr, max_mw, z, P, out_stage);
   ++*kernels;
   return cudaGetLastError();
@@ -537,20 +626,43 @@ cudaError_t launch_ntt(const DirectArgs& d, const uint8_t* seed, uint64_t L_t, F
   ntt_seed_kernel<<<grid_for(P, 256), 256, 0, s>>>(seed, L_t, spec, P);
   ++*kernels;
   const uint32_t* st = ws.ntt_stage.as<uint32_t>();
-  if ((e = ntt_columns<false>(spec, st, pl, 1, 1, 0, s, kernels)) != cudaSuccess) return e;
+  const ColsIO none{};
+  if ((e = ntt_columns<false, kColsZ>(spec, st, pl, 1, 1, 0, none, s, kernels)) != cudaSuccess) return e;
   if ((e = ntt_rows<kRowsForward>(spec, nullptr, tw, st, pl, 1, 0, s, kernels)) != cudaSuccess) return e;
   const uint32_t pinv = pow_mod(P % kP, kP - 2);
   const uint32_t factor_m = to_mont(to_mont(pinv));  // P^-1 2^64 mod p: one product leaves P^-1 2^32
   ntt_scale_kernel<<<grid_for(P, 256), 256, 0, s>>>(spec, P, factor_m);
   ++*kernels;
 
+  // the block's raw bits go straight into the forward columns and the inverse columns write packed
+  // parity bits, when the column tiles are at least a byte wide
+  const bool fused = pl.H > 0 && pl.logW >= 3;
+  if (fused && (e = ws.buf1.ensure(chunk * (P / 8))) != cudaSuccess) return e;
   for (uint64_t bb = 0; bb < d.num_blocks; bb += chunk) {
     const uint64_t nb = (d.num_blocks - bb) < chunk ? (d.num_blocks - bb) : chunk;
-    ntt_pack_kernel<<<grid_for(nb * P, 256), 256, 0, s>>>(d.raw, d.raw_stride, n_t, d.num_blocks, bb, nb, z, P);
+    if (fused) {
+      ColsIO in{};
+      in.raw = d.raw;
+      in.stride = d.raw_stride;
+      in.n_t = n_t;
+      in.b0 = bb;
+      in.num_blocks = d.num_blocks;
+      if ((e = ntt_columns<false, kColsFromBits>(z, st, pl, nb, 1, 0, in, s, kernels)) != cudaSuccess) return e;
+      if ((e = ntt_rows<kRowsConvolve>(z, spec, tw, st, pl, nb, 0, s, kernels)) != cudaSuccess) return e;
+      ColsIO outp{};
+      outp.parity = ws.buf1.as<uint8_t>();
+      if ((e = ntt_columns<true, kColsToParity>(z, st, pl, nb, 1, 0, outp, s, kernels)) != cudaSuccess) return e;
+      ntt_parity_extract_kernel<<<grid_for(nb * d.mw, 256), 256, 0, s>>>(
+          ws.buf1.as<uint32_t>(), logP, n_t, d.m, d.mw, d.raw, d.raw_stride, d.modified, d.id_off, d.num_blocks, bb,
+          nb, d.out, d.out_stride);
+      ++*kernels;
+      continue;
+    }
+    ntt_pack_kernel<<<grid_for(nb * P, 256), 256, 0, s>>>(d.raw, d.raw_stride, n_t, d.num_blocks, bb, nb, z, logP);
     ++*kernels;
-    if ((e = ntt_columns<false>(z, st, pl, nb, 1, 0, s, kernels)) != cudaSuccess) return e;
+    if ((e = ntt_columns<false, kColsZ>(z, st, pl, nb, 1, 0, none, s, kernels)) != cudaSuccess) return e;
     if ((e = ntt_rows<kRowsConvolve>(z, spec, tw, st, pl, nb, 0, s, kernels)) != cudaSuccess) return e;
-    if ((e = ntt_columns<true>(z, st, pl, nb, 1, 0, s, kernels)) != cudaSuccess) return e;
+    if ((e = ntt_columns<true, kColsZ>(z, st, pl, nb, 1, 0, none, s, kernels)) != cudaSuccess) return e;
     ntt_extract_kernel<<<grid_for(nb * d.mw * 32, 256), 256, 0, s>>>(z, P, n_t, d.m, d.mw, d.raw, d.raw_stride,
                                                                      d.modified, d.id_off, d.num_blocks, bb, nb,
                                                                      d.out, d.out_stride);

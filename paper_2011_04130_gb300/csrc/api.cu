@@ -258,9 +258,9 @@ double model_seconds(int algo, uint64_t n_t, uint64_t m, uint64_t B) {
       const double P = (double)fft64_length(n_t, m), lg = log2(P), pairs = (double)ceil_div(B, 2);
       return pairs * (10.0 * P * lg / 6e11 + 64.0 * P * lg / 6e12) + 2.0 * lg * 4e-6;
     }
-    case QRNG_ALGO_NTT: {  // measured: about 1.5 ps per element and log2 P per block (two transforms)
+    case QRNG_ALGO_NTT: {  // measured: about 0.9 ps per element and log2 P per block (two transforms)
       const double P = (double)fft64_length(n_t, m), lg = log2(P);
-      return (double)B * P * lg * 1.5e-12 + 6e-5;
+      return (double)B * P * lg * 0.9e-12 + 6e-5;
     }
     case QRNG_ALGO_FFT32_SEG: {
       const double S = (double)fft32_segment(), N = 2 * S;
@@ -430,13 +430,13 @@ cudaError_t ensure_batch(qrng_ctx* ctx, DevBuf& b, size_t bytes) {
 constexpr size_t kMaxGraphs = 4;
 
 // Batch routing: a request goes to the transform route when its modelled time there is below the
-// direct kernel's (the number-theoretic transform costs about P log2 P x 2.3 ps per request, three
+// direct kernel's (the number-theoretic transform costs about P log2 P x 1.3 ps per request, three
 // transforms of the P-point padded seed and raw bits; the direct kernel m n_t / 5.6e14 s).
 bool batch_prefers_ntt(uint64_t n_t, uint64_t m) {
   const uint64_t P = fft64_length(n_t, m);
   if (P > (1ull << 27)) return false;
   const double lg = log2((double)P);
-  return (double)P * lg * 2.3e-12 < (double)m * (double)n_t / 5.6e14;
+  return (double)P * lg * 1.3e-12 < (double)m * (double)n_t / 5.6e14;
 }
 
 int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int algo, cudaStream_t s) {

@@ -255,6 +255,10 @@ __device__ __forceinline__ void smem_transform(uint32_t* __restrict__ x, uint32_
   }
 }
 
+__device__ __forceinline__ uint32_t bit_at(const uint8_t* __restrict__ p, uint64_t bit) {
+  return (p[bit >> 3] >> (bit & 7)) & 1u;
+}
+
 // Column I/O: entries in z both ways; raw bits in (forward: the block's bits become the entries,
 // no packed copy); parity bits out (inverse: bit i of the block's parity array = entry i mod 2,
 // stored a byte per 8 columns of a row, instead of the entries).
@@ -266,7 +270,9 @@ struct ColsIO {
   uint64_t n_t;
   uint64_t b0;           // block of entry 0
   uint64_t num_blocks;
-  uint8_t* parity;       // kColsToParity: P / 8 bytes per entry
+  const BatchReq* reqs;  // kColsFromBits for uneven requests: entry 2r = request r's seed bits (L_t of
+                         // them), entry 2r+1 its raw bits (n_t from raw_bit_off); replaces raw..num_blocks
+  uint8_t* parity;       // kColsToParity: P / 8 bytes per launched entry
 };
 
 // Length-2^H transforms down the columns of entries ent_off, ent_off + ent_stride, ... (row stride
@@ -281,7 +287,15 @@ __global__ void __launch_bounds__(512) ntt_cols_kernel(uint32_t* __restrict__ z,
   const uint64_t eidx = ent * ent_stride + ent_off;
   uint32_t* zb = z + (eidx << pl.logP) + c0;
   const uint32_t W = 1u << pl.logW, n = 1u << (pl.H + pl.logW);
-  if (kIO == kColsFromBits) {
+  if (kIO == kColsFromBits && io.reqs) {
+    const BatchReq& q = io.reqs[eidx >> 1];
+    const uint8_t* src = (eidx & 1) ? q.raw : q.seed;
+    const uint64_t off = (eidx & 1) ? q.raw_bit_off : 0, len = (eidx & 1) ? q.n_t : q.L_t;
+    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {
+      const uint64_t i = ((uint64_t)(e >> pl.logW) << pl.L) + c0 + (e & (W - 1));
+      col_sm[e] = i < len ? bit_at(src, off + i) : 0u;
+    }
+  } else if (kIO == kColsFromBits) {
     const uint64_t b = io.b0 + eidx;
     const uint32_t* rb = io.raw + b * io.stride;
     const bool live = b < io.num_blocks;
@@ -297,7 +311,7 @@ __global__ void __launch_bounds__(512) ntt_cols_kernel(uint32_t* __restrict__ z,
   smem_transform<kInverse>(col_sm, pl.H, pl.logW, st);
   if (kIO == kColsToParity) {
     // the tile's W columns of row r are entries (r << L) + c0 .. + W - 1: W / 8 bytes of parity bits
-    uint8_t* pb = io.parity + (eidx << (pl.logP - 3)) + (c0 >> 3);
+    uint8_t* pb = io.parity + (ent << (pl.logP - 3)) + (c0 >> 3);
     const uint32_t bytes_per_row = W >> 3;
     for (uint32_t u = threadIdx.x; u < (n >> 3); u += blockDim.x) {
       const uint32_t r = u / bytes_per_row, k = u - r * bytes_per_row;
@@ -536,9 +550,6 @@ cudaError_t ensure_twiddles(FftWorkspace& ws, uint64_t P, cudaStream_t s, uint32
 
 // ---- uneven batches: requests with their own seeds, grouped by transform length P ----
 
-__device__ __forceinline__ uint32_t bit_at(const uint8_t* __restrict__ p, uint64_t bit) {
-  return (p[bit >> 3] >> (bit & 7)) & 1u;
-}
 
 // Entry 2r of the chunk holds request r's seed bits [0, L_t), entry 2r+1 its raw bits [0, n_t),
 // both zero-padded to P.
@@ -575,6 +586,42 @@ __global__ void ntt_batch_extract_kernel(const BatchReq* __restrict__ reqs, uint
   if (lane == 0) out_stage[q.out_stage_off + w] = word;
 }
 
+// nbits <= 32 bits of a byte buffer from bit `bit` on (LSB-first), reading only the bytes they span.
+__device__ __forceinline__ uint32_t bits_at(const uint8_t* __restrict__ p, uint64_t bit, uint32_t nbits) {
+  const uint8_t* b = p + (bit >> 3);
+  const uint32_t sh = (uint32_t)(bit & 7);
+  const uint32_t nbytes = (sh + nbits + 7) >> 3;  // <= 5
+  uint64_t v = 0;
+  for (uint32_t k = 0; k < nbytes; ++k) v |= (uint64_t)b[k] << (8 * k);
+  v >>= sh;
+  return nbits >= 32 ? (uint32_t)v : (uint32_t)v & ((1u << nbits) - 1u);
+}
+
+// Output word w of chunk request r from its parity bits (one thread per word): bits n_t - 1 + 32 w
+// .. + 31 of the product's inverse transform, identity bits for the modified form.
+__global__ void ntt_batch_parity_extract_kernel(const BatchReq* __restrict__ reqs, uint64_t nr, uint64_t max_mw,
+                                                const uint32_t* __restrict__ par, uint32_t logP,
+                                                uint32_t* __restrict__ out_stage) {
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (g >= nr * max_mw) return;
+  const uint64_t r = g / max_mw, w = g - r * max_mw;
+  const BatchReq& q = reqs[r];
+  if (w >= q.mw) return;
+  const uint64_t words = 1ull << (logP - 5);
+  const uint32_t* pb = par + r * words;
+  const uint64_t pos = q.n_t - 1 + 32 * w;
+  const uint64_t qw = pos >> 5;
+  const uint32_t sh = (uint32_t)(pos & 31);
+  const uint32_t lo = __ldg(pb + qw);
+  const uint32_t hi = (sh && qw + 1 < words) ? __ldg(pb + qw + 1) : 0u;
+  const uint64_t rem = q.m - 32 * w;
+  const uint32_t nb = rem >= 32 ? 32u : (uint32_t)rem;
+  const uint32_t omask = nb >= 32 ? 0xffffffffu : ((1u << nb) - 1u);
+  uint32_t word = __funnelshift_r(lo, hi, sh) & omask;
+  if (q.form == QRNG_FORM_MODIFIED) word ^= bits_at(q.raw, q.raw_bit_off + q.id_off + 32 * w, nb);
+  out_stage[q.out_stage_off + w] = word;
+}
+
 }  // namespace
 
 cudaError_t launch_ntt_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P,
@@ -588,14 +635,31 @@ cudaError_t launch_ntt_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P,
   if ((e = ws.buf0.ensure(2 * nr * P * sizeof(uint32_t))) != cudaSuccess) return e;
   uint32_t* z = ws.buf0.as<uint32_t>();
   const uint32_t* tw = ws.ntt_tw.as<uint32_t>();
+  const uint32_t* st = ws.ntt_stage.as<uint32_t>();
+  const uint32_t factor_m = to_mont(to_mont(pow_mod(P % kP, kP - 2)));
+  if (pl.H > 0 && pl.logW >= 3) {
+    // every request's seed and raw bits straight into the forward columns; parity bits out of the
+    // inverse columns of the products (entries 2r+1)
+    if ((e = ws.buf1.ensure(nr * (P / 8))) != cudaSuccess) return e;
+    ColsIO in{};
+    in.reqs = reqs_dev;
+    if ((e = ntt_columns<false, kColsFromBits>(z, st, pl, 2 * nr, 1, 0, in, s, kernels)) != cudaSuccess) return e;
+    if ((e = ntt_rows<kRowsPairs>(z, nullptr, tw, st, pl, nr, factor_m, s, kernels)) != cudaSuccess) return e;
+    ColsIO outp{};
+    outp.parity = ws.buf1.as<uint8_t>();
+    if ((e = ntt_columns<true, kColsToParity>(z, st, pl, nr, 2, 1, outp, s, kernels)) != cudaSuccess) return e;
+    ntt_batch_parity_extract_kernel<<<grid_for(nr * max_mw, 256), 256, 0, s>>>(reqs_dev, nr, max_mw,
+                                                                               ws.buf1.as<uint32_t>(), logP,
+                                                                               out_stage);
+    ++*kernels;
+    return cudaGetLastError();
+  }
   ntt_batch_inputs_kernel<<<grid_for(2 * nr * P, 256), 256, 0, s>>>(reqs_dev, nr, z, logP);
   ++*kernels;
   // both entries of every request forward, then per row: the product (*) P^-1 2^64, inverse row
   // transform into entry 2r+1, then the inverse columns of the odd entries
-  const uint32_t* st = ws.ntt_stage.as<uint32_t>();
   const ColsIO none{};
   if ((e = ntt_columns<false, kColsZ>(z, st, pl, 2 * nr, 1, 0, none, s, kernels)) != cudaSuccess) return e;
-  const uint32_t factor_m = to_mont(to_mont(pow_mod(P % kP, kP - 2)));
   if ((e = ntt_rows<kRowsPairs>(z, nullptr, tw, st, pl, nr, factor_m, s, kernels)) != cudaSuccess) return e;
   if ((e = ntt_columns<true, kColsZ>(z, st, pl, nr, 2, 1, none, s, kernels)) != cudaSuccess) return e;
   ntt_batch_extract_kernel<<<grid_for(nr * max_mw * 32, 256), 256, 0, s>>>(reqs_dev, nr, max_mw, z, P, out_stage);

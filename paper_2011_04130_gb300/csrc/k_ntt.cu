@@ -310,16 +310,22 @@ __global__ void __launch_bounds__(512) ntt_cols_kernel(uint32_t* __restrict__ z,
   __syncthreads();
   smem_transform<kInverse>(col_sm, pl.H, pl.logW, st);
   if (kIO == kColsToParity) {
-    // the tile's W columns of row r are entries (r << L) + c0 .. + W - 1: W / 8 bytes of parity bits
+    // the tile's W columns of row r are entries (r << L) + c0 .. + W - 1. A warp takes 32 consecutive
+    // tile elements (rows of W >= 8 columns, in order) and gathers their parities with one ballot; the
+    // lane at the start of each row's run (or of each 32 columns) stores that run's bits.
     uint8_t* pb = io.parity + (ent << (pl.logP - 3)) + (c0 >> 3);
-    const uint32_t bytes_per_row = W >> 3;
-    for (uint32_t u = threadIdx.x; u < (n >> 3); u += blockDim.x) {
-      const uint32_t r = u / bytes_per_row, k = u - r * bytes_per_row;
-      const uint32_t* src = col_sm + (r << pl.logW) + 8 * k;
-      uint32_t byte = 0;
-#pragma unroll
-      for (int t = 0; t < 8; ++t) byte |= (src[t] & 1u) << t;
-      pb[((uint64_t)r << (pl.L - 3)) + k] = (uint8_t)byte;
+    const uint32_t lane = threadIdx.x & 31;
+    for (uint32_t e = threadIdx.x; e < n; e += blockDim.x) {  // n is a multiple of 32 when logW >= 3
+      const uint32_t bits = __ballot_sync(0xffffffffu, col_sm[e] & 1u);
+      const uint32_t r = e >> pl.logW, c = e & (W - 1);
+      uint8_t* dst = pb + ((uint64_t)r << (pl.L - 3)) + (c >> 3);
+      if (W >= 32) {
+        if (lane == 0) *reinterpret_cast<uint32_t*>(dst) = bits;
+      } else if (c == 0) {
+        const uint32_t field = bits >> lane;  // this row's W bits
+        if (W == 16) *reinterpret_cast<uint16_t*>(dst) = (uint16_t)field;
+        else *dst = (uint8_t)field;
+      }
     }
   } else {
     for (uint32_t e = threadIdx.x; e < n; e += blockDim.x)

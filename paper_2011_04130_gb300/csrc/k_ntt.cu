@@ -11,7 +11,7 @@
 // Arithmetic: elements in [0, p); roots of unity in Montgomery form (w 2^32 mod p) so that one
 // Montgomery product w (*) x = w x mod p returns an ordinary residue.
 //
-// Schedule (four-step, in shared memory): with P = N1 N2, N2 = 2^L (L <= 12), index n = N2 n1 + n2
+// Schedule (four-step, in shared memory): with P = N1 N2, N2 = 2^L (L <= 13), index n = N2 n1 + n2
 // and frequency k = k1 + N1 k2,
 //   columns: for every n2, the length-N1 transform over n1 (decimation in frequency, so row
 //            position rr holds k1 = bitrev(rr)), on tiles of W adjacent columns in shared memory;
@@ -117,7 +117,8 @@ struct NttPlan {
 NttPlan ntt_plan(uint32_t logP) {
   NttPlan pl;
   pl.logP = logP;
-  pl.L = logP < 12 ? logP : 12;
+  // rows of 2^12 entries (2^13 from P = 2^24 on, so that column tiles stay at least 8 columns wide)
+  pl.L = logP < 12 ? logP : (logP >= 24 ? 13 : 12);
   pl.H = logP - pl.L;
   const uint32_t want = pl.H >= 14 ? 0u : 14u - pl.H;  // about 16384 elements (64 KB) per column tile
   pl.logW = want < pl.L ? want : pl.L;

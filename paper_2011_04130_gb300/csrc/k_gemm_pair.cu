@@ -43,45 +43,51 @@ using namespace tc;
 
 constexpr int PM = 256;                  // outputs per output tile (UMMA M over the pair)
 constexpr int HM = 128;                  // T rows per CTA
-constexpr int PN = 224;                  // blocks per pair tile (UMMA N)
-constexpr int HN = PN / 2;               // X rows per CTA
 constexpr int BK = 256;                  // E2M1 entries per K step
 constexpr int KW = BK / 32;              // packed words per row and step
 constexpr int ROW_BYTES = 128;
 constexpr int STAGES = 6;
 constexpr int A_BYTES = HM * ROW_BYTES;  // 16 KB
-constexpr int B_BYTES = HN * ROW_BYTES;  // 14 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int PK_STAGES = STAGES;
-constexpr int PK_BYTES = HN * KW * 4;    // 3.5 KB
 constexpr int PRODUCER_WARPS = STAGES;   // warp s builds every use of operand stage s
 constexpr int T_ROWS = HM / 32;          // T rows lane + 32 j of a lane
-constexpr int X_ROWS = (HN + 31) / 32;   // X rows lane + 32 j < HN of a lane
 constexpr int TMA_WARP = PRODUCER_WARPS;
 constexpr int MMA_WARP = TMA_WARP + 1;
 constexpr int EPI_WARP0 = MMA_WARP + 1;
 constexpr int EPI_WARPS = 4;
 constexpr int THREADS = (EPI_WARP0 + EPI_WARPS) * 32;  // 384
 constexpr int TMEM_COLS = 512;
-constexpr uint32_t D1_COL = PN;          // second accumulator
 constexpr uint32_t SFA_COL = 448;        // scale factors (all 2^0) of A, then of B
 constexpr uint32_t SFB_COL = 480;
 constexpr uint16_t kPairMask = 0x3;      // both CTAs of the cluster
-// kind::mxf4: A = B = E2M1 (1 at bits 7 and 10), K-major, N >> 3 at bit 17, UE8M0 scales (bit 23),
-// M >> 7 at bit 27 (M = 256 over the pair), dense K = 64.
-constexpr uint32_t IDESC =
-    (1u << 7) | (1u << 10) | ((uint32_t)(PN >> 3) << 17) | (1u << 23) | ((uint32_t)(PM >> 7) << 27);
 static_assert(PK_STAGES == STAGES, "producer warp s owns operand stage s and raw slot s");
-static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0, "swizzle atoms must stay 1024-byte aligned");
-static_assert(HN % 8 == 0 && PN % 16 == 0 && 2 * PN <= (int)SFA_COL, "accumulators and scale factors must fit");
+
+// Blocks per pair tile (UMMA N, 112 or 96 X rows per CTA); the launcher picks the width that wastes
+// the fewest block columns over whole rounds of tiles.
+template <int kPN>
+struct PairShape {
+  static constexpr int PN = kPN;
+  static constexpr int HN = PN / 2;                      // X rows per CTA
+  static constexpr int B_BYTES = HN * ROW_BYTES;
+  static constexpr int STAGE_BYTES = A_BYTES + B_BYTES;
+  static constexpr int PK_BYTES = HN * KW * 4;
+  static constexpr int X_ROWS = (HN + 31) / 32;          // X rows lane + 32 j < HN of a lane
+  static constexpr uint32_t D1_COL = PN;                 // second accumulator
+  // kind::mxf4: A = B = E2M1 (1 at bits 7 and 10), K-major, N >> 3 at bit 17, UE8M0 scales (bit
+  // 23), M >> 7 at bit 27 (M = 256 over the pair), dense K = 64.
+  static constexpr uint32_t IDESC =
+      (1u << 7) | (1u << 10) | ((uint32_t)(PN >> 3) << 17) | (1u << 23) | ((uint32_t)(PM >> 7) << 27);
+  static_assert(STAGE_BYTES % 1024 == 0 && A_BYTES % 1024 == 0, "swizzle atoms must stay 1024-byte aligned");
+  static_assert(HN % 8 == 0 && PN % 16 == 0 && 2 * PN <= (int)SFA_COL, "accumulators and scale factors must fit");
+};
 
 __device__ __forceinline__ void mma_pair(uint32_t tmem_d, uint32_t tmem_base, uint64_t adesc, uint64_t bdesc,
-                                         uint32_t accumulate) {
+                                         uint32_t idesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %6, 0;\n"
       " tcgen05.mma.cta_group::2.kind::mxf4.block_scale.scale_vec::2X [%0], %1, %2, %3, [%4], [%5], p;\n}\n" ::"r"(
           tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(tmem_base + SFA_COL), "r"(tmem_base + SFB_COL), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(tmem_base + SFA_COL), "r"(tmem_base + SFB_COL), "r"(accumulate)
       : "memory");
 }
 
@@ -119,8 +125,12 @@ struct PairArgs {
   int fault_no_tma;  // test hook: the loader publishes no raw tile, so every consumer's bounded wait runs out
 };
 
+template <int kPN>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_pair_kernel(const PairArgs a, const __grid_constant__ CUtensorMap raw_map) {
+  using S = PairShape<kPN>;
+  constexpr int PN = S::PN, HN = S::HN, STAGE_BYTES = S::STAGE_BYTES, PK_BYTES = S::PK_BYTES, X_ROWS = S::X_ROWS;
+  constexpr uint32_t D1_COL = S::D1_COL;
   extern __shared__ uint8_t dyn_smem[];
   __shared__ __align__(8) uint64_t full_bar[STAGES];       // leader: the owning producer warp of both CTAs
   __shared__ __align__(8) uint64_t empty_bar[STAGES];      // both: the leader's MMA completion
@@ -312,8 +322,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             for (int k = 0; k < ROW_BYTES / 32; ++k) {
               const uint64_t bdesc = smem_desc_sw128(sB + 32 * k);
               const uint32_t acc = (e > 1 || k > 0) ? 1u : 0u;
-              mma_pair(tmem_base, tmem_base, smem_desc_sw128(sA + 32 * k), bdesc, acc);
-              mma_pair(tmem_base + D1_COL, tmem_base, smem_desc_sw128(sP + 32 * k), bdesc, acc);
+              mma_pair(tmem_base, tmem_base, smem_desc_sw128(sA + 32 * k), bdesc, S::IDESC, acc);
+              mma_pair(tmem_base + D1_COL, tmem_base, smem_desc_sw128(sP + 32 * k), bdesc, S::IDESC, acc);
             }
             commit_both(&empty_bar[prev]);  // the previous stage's T tile is not read again
             issued = true;
@@ -399,7 +409,71 @@ typedef CUresult (*PFN_encodeTiled_pair)(CUtensorMap*, CUtensorMapDataType, cuui
                                          CUtensorMapInterleave, CUtensorMapSwizzle, CUtensorMapL2promotion,
                                          CUtensorMapFloatOOBfill);
 
-size_t gemm_pair_smem_bytes() { return (size_t)STAGES * STAGE_BYTES + (size_t)PK_STAGES * PK_BYTES + 1024; }
+template <int kPN>
+static size_t pair_smem_bytes() {
+  return (size_t)STAGES * PairShape<kPN>::STAGE_BYTES + (size_t)PK_STAGES * PairShape<kPN>::PK_BYTES + 1024;
+}
+
+size_t gemm_pair_smem_bytes() { return pair_smem_bytes<224>(); }
+
+template <int kPN>
+static cudaError_t launch_pair(const PairArgs& a0, const DirectArgs& d, int num_sms, cudaStream_t s,
+                               uint32_t* kernels) {
+  using S = PairShape<kPN>;
+  PairArgs a = a0;
+  a.ntiles = (uint32_t)ceil_div(d.num_blocks, S::PN);
+
+  // Tensor map over the raw words: dim 0 = the Toeplitz part's words of a block (reads beyond it are
+  // zero-filled), dim 1 = blocks (rows past the last block are zero-filled); box 8 words x HN blocks,
+  // every x coordinate a multiple of 8 words (32 bytes).
+  static PFN_encodeTiled_pair encode = nullptr;
+  if (!encode) {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess || !fn)
+      return cudaErrorNotSupported;
+    encode = reinterpret_cast<PFN_encodeTiled_pair>(fn);
+  }
+  CUtensorMap map;
+  const cuuint64_t gdim[2] = {(cuuint64_t)d.nw_t, (cuuint64_t)d.num_blocks};
+  const cuuint64_t gstride[1] = {(cuuint64_t)d.raw_stride * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)KW, (cuuint32_t)S::HN};
+  const cuuint32_t estride[2] = {1, 1};
+  CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(d.raw), gdim, gstride, box,
+                      estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+
+  const size_t smem = pair_smem_bytes<kPN>();
+  cudaError_t e =
+      cudaFuncSetAttribute(gemm_pair_kernel<kPN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const uint64_t tiles = (uint64_t)a.mpairs * a.ntiles;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(2 * (tiles < (uint64_t)num_sms / 2 ? tiles : (uint64_t)num_sms / 2)));
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  // one cluster per co-resident pair of SMs: every tile loop stride then runs concurrently
+  int clusters = 0;
+  e = cudaOccupancyMaxActiveClusters(&clusters, gemm_pair_kernel<kPN>, &cfg);
+  if (e != cudaSuccess) return e;
+  if (clusters < 1) return cudaErrorNotSupported;
+  const uint64_t pairs = tiles < (uint64_t)clusters ? tiles : (uint64_t)clusters;
+  cfg.gridDim = dim3((unsigned)(2 * pairs));
+  e = cudaLaunchKernelEx(&cfg, gemm_pair_kernel<kPN>, a, map);
+  if (e != cudaSuccess) return e;
+  ++*kernels;
+  return cudaGetLastError();
+}
 
 cudaError_t launch_gemm_pair(const DirectArgs& d, int* err, int fault, int num_sms, cudaStream_t s,
                              uint32_t* kernels) {
@@ -418,60 +492,19 @@ cudaError_t launch_gemm_pair(const DirectArgs& d, int* err, int fault, int num_s
   a.out_stride = d.out_stride;
   a.num_blocks = d.num_blocks;
   a.mpairs = (uint32_t)ceil_div(ceil_div(d.m, PM), 2);
-  a.ntiles = (uint32_t)ceil_div(d.num_blocks, PN);
   a.ksteps = (uint32_t)ceil_div((uint64_t)d.nw_t * 32, BK);
   a.err = err;
   a.fault_no_tma = (fault == QRNG_FAULT_GEMM_NO_TMA);
-
-  // Tensor map over the raw words: dim 0 = the Toeplitz part's words of a block (reads beyond it are
-  // zero-filled), dim 1 = blocks (rows past the last block are zero-filled); box 8 words x 112 blocks,
-  // every x coordinate a multiple of 8 words (32 bytes).
-  static PFN_encodeTiled_pair encode = nullptr;
-  if (!encode) {
-    void* fn = nullptr;
-    cudaDriverEntryPointQueryResult q;
-    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
-        q != cudaDriverEntryPointSuccess || !fn)
-      return cudaErrorNotSupported;
-    encode = reinterpret_cast<PFN_encodeTiled_pair>(fn);
-  }
-  CUtensorMap map;
-  const cuuint64_t gdim[2] = {(cuuint64_t)d.nw_t, (cuuint64_t)d.num_blocks};
-  const cuuint64_t gstride[1] = {(cuuint64_t)d.raw_stride * 4};
-  const cuuint32_t box[2] = {(cuuint32_t)KW, (cuuint32_t)HN};
-  const cuuint32_t estride[2] = {1, 1};
-  CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(d.raw), gdim, gstride, box,
-                      estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
-
-  const size_t smem = gemm_pair_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(gemm_pair_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  const uint64_t tiles = (uint64_t)a.mpairs * a.ntiles;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeClusterDimension;
-  attr[0].val.clusterDim.x = 2;
-  attr[0].val.clusterDim.y = 1;
-  attr[0].val.clusterDim.z = 1;
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((unsigned)(2 * (tiles < (uint64_t)num_sms / 2 ? tiles : (uint64_t)num_sms / 2)));
-  cfg.blockDim = dim3(THREADS);
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  // one cluster per co-resident pair of SMs: every tile loop stride then runs concurrently
-  int clusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&clusters, gemm_pair_kernel, &cfg);
-  if (e != cudaSuccess) return e;
-  if (clusters < 1) return cudaErrorNotSupported;
-  const uint64_t pairs = tiles < (uint64_t)clusters ? tiles : (uint64_t)clusters;
-  cfg.gridDim = dim3((unsigned)(2 * pairs));
-  e = cudaLaunchKernelEx(&cfg, gemm_pair_kernel, a, map);
-  if (e != cudaSuccess) return e;
-  ++*kernels;
-  return cudaGetLastError();
+  // tile width: block columns computed over whole rounds of tiles (one round = one tile per cluster
+  // of the pairs that fit), the narrower tile's columns weighted by its measured cost per column
+  // (more operand bytes per MAC: 1.07x on the 2^29-bit laser stream)
+  const uint64_t rounds_cap = (uint64_t)(num_sms / 2 > 0 ? num_sms / 2 : 1);
+  auto cost = [&](uint64_t pn, double per_col) {
+    const uint64_t tiles = (uint64_t)a.mpairs * ceil_div(d.num_blocks, pn);
+    return (double)(ceil_div(tiles, rounds_cap) * pn) * per_col;
+  };
+  if (cost(192, 1.07) < cost(224, 1.0)) return launch_pair<192>(a, d, num_sms, s, kernels);
+  return launch_pair<224>(a, d, num_sms, s, kernels);
 }
 
 }  // namespace qrng

@@ -414,8 +414,6 @@ static size_t pair_smem_bytes() {
   return (size_t)STAGES * PairShape<kPN>::STAGE_BYTES + (size_t)PK_STAGES * PairShape<kPN>::PK_BYTES + 1024;
 }
 
-size_t gemm_pair_smem_bytes() { return pair_smem_bytes<224>(); }
-
 template <int kPN>
 static cudaError_t launch_pair(const PairArgs& a0, const DirectArgs& d, int num_sms, cudaStream_t s,
                                uint32_t* kernels) {

@@ -395,8 +395,6 @@ static size_t smem_bytes() {
   return (size_t)STAGES * Cfg<kFp4>::STAGE_BYTES + (size_t)PK_STAGES * Cfg<kFp4>::PK_BYTES + 1024;
 }
 
-size_t gemm_tc_smem_bytes(bool fp4) { return fp4 ? smem_bytes<true>() : smem_bytes<false>(); }
-
 bool gemm_tc_layout_ok(const DirectArgs& d) {
   return (reinterpret_cast<uintptr_t>(d.raw) & 15) == 0 && (d.raw_stride % 4) == 0;
 }

@@ -181,11 +181,9 @@ cudaError_t launch_fft32_seg(const DirectArgs& a, const uint8_t* seed, uint64_t 
 // Same layout arguments as the direct kernel (splits unused). Exact for n_t <= kGemmMaxColumns.
 constexpr uint64_t kGemmMaxColumns = 1ull << 22;
 // fp4 selects the block-scaled E2M1 operand encoding (kind::mxf4) over E4M3 (kind::f8f6f4).
-size_t gemm_tc_smem_bytes(bool fp4);
 cudaError_t launch_gemm_tc(const DirectArgs& a, bool fp4, int* err, int fault, int num_sms, cudaStream_t s,
                            uint32_t* kernels);
 // The FP4 product on SM pairs (k_gemm_pair.cu): clusters of two CTAs, cta_group::2 MMAs.
-size_t gemm_pair_smem_bytes();
 cudaError_t launch_gemm_pair(const DirectArgs& a, int* err, int fault, int num_sms, cudaStream_t s, uint32_t* kernels);
 
 }  // namespace qrng

@@ -118,6 +118,26 @@ def test_mixed_routes_long_requests(qlib, gpu, oracle_mod):
     assert np.array_equal(host, direct)
 
 
+def test_transform_route_length_2_25(qlib, gpu, oracle_mod):
+    """One request long enough for a 2^25-point transform (the route without the fused bit input and
+    parity output) among short ones, all forced onto the transform route."""
+    shapes = [(1 << 24, 100, STD), (5000, 3000, MOD), (70000, 40000, STD)]
+    n = np.array([x[0] for x in shapes])
+    m = np.array([x[1] for x in shapes])
+    forms = np.array([x[2] for x in shapes])
+    raw_offs, pos = [], 5
+    for i in range(len(shapes)):
+        raw_offs.append(pos)
+        pos += int(n[i]) + 11
+    raw = W.random_bits(pos + 64, 81)
+    seeds = [W.random_bits(int(n[i] + m[i] - 1) if forms[i] == STD else int(n[i] - 1), 90 + i)
+             for i in range(len(shapes))]
+    out_offs = [3, 3 + int(m[0]), 3 + int(m[0] + m[1])]
+    batch = (n, m, forms, raw, raw_offs, seeds, out_offs, int(3 + m.sum()))
+    host, _ = _run(qlib, gpu, batch, algo=qlib.QRNG_ALGO_NTT)
+    _check(oracle_mod, batch, host)
+
+
 def test_graph_replay_sees_new_data(qlib, gpu, oracle_mod):
     """An identical request table replays the cached graph; the kernels read the buffers anew."""
     import torch

@@ -155,6 +155,18 @@ def test_ntt_block_length_sweep_point(qlib, gpu, oracle_mod, log2n):
     spot_check(oracle_mod, raw, n, m, seed, MOD, got, blocks=[0, B - 1], per_block=128)
 
 
+def test_ntt_transform_length_2_25(qlib, gpu, oracle_mod):
+    """n = 2^24 in the standard form needs P = 2^25: rows of 2^13 entries and column tiles narrower
+    than a byte, i.e. the route that packs the bits into entries and extracts the output from them."""
+    n, m, B = 1 << 24, 4096, 2
+    raw = W.random_bits(n * B, 71)
+    seed = W.random_bits(n + m - 1, 72)
+    got = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_NTT, B)
+    ref = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_FFT64, B)
+    assert np.array_equal(got, ref)
+    spot_check(oracle_mod, raw, n, m, seed, STD, got, blocks=[0, B - 1], per_block=32)
+
+
 @pytest.mark.parametrize("log2n", [12, 16, 20])
 def test_fft64_block_length_sweep_point(qlib, gpu, oracle_mod, log2n):
     """The paper's FFT route on the fixed 2^30-bit stream, modified form, m = 0.75 n."""

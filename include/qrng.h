@@ -269,7 +269,10 @@ QRNG_API int qrng_extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_
  *   m_out, num_blocks_out, rep   host; receive m, the number of blocks and the entropy report
  *                  (any of them may be NULL).
  * Returns QRNG_EINVAL when m comes out 0 or a capacity is too small (m_out / num_blocks_out
- * are still written). Synchronises `stream`.
+ * are still written). Synchronises `stream`. When n is a multiple of 128 and there are at least
+ * 64 blocks, the blocks are hashed in two parts (the first about 7/8 of them) and the first part's
+ * output is copied to the host (on a stream of the context) while the second is hashed; out_host
+ * belongs to the call until it returns, like every other buffer.
  */
 QRNG_API int qrng_postprocess_host(qrng_ctx* ctx, const void* samples_host, uint64_t count, int bits, double eps,
                           double eps_lhl, uint64_t n, const uint8_t* seed_host, uint64_t seed_capacity_bits,

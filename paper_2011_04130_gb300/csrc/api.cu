@@ -629,7 +629,17 @@ int qrng_create(qrng_ctx** out, int device) {
     delete ctx;
     return QRNG_ENOMEM;
   }
-  if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->copy_ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->copy_done, cudaEventDisableTiming) != cudaSuccess) {
+    if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
+    if (ctx->copy_ready) cudaEventDestroy(ctx->copy_ready);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+    if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->copy_ready) cudaEventDestroy(ctx->copy_ready);
+  if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
     cudaFreeHost(ctx->result_host);
     ctx->dev_err.release();
     ctx->fft_worst.release();
@@ -662,6 +672,9 @@ void qrng_destroy(qrng_ctx* ctx) {
   ctx->batch_out.release();
   ctx->batch_counter.release();
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
+  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
+  if (ctx->copy_ready) cudaEventDestroy(ctx->copy_ready);
+  if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
   if (ctx->result_host) cudaFreeHost(ctx->result_host);
   for (cudaEvent_t e : ctx->ev_start) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->ev_end) cudaEventDestroy(e);
@@ -802,10 +815,35 @@ int qrng_postprocess_host(qrng_ctx* ctx, const void* samples_host, uint64_t coun
   QRNG_CUDA(ctx, ctx->seed_dev.ensure(ceil_div(L, 8)), "seed workspace");
   QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->seed_dev.p, seed_host, ceil_div(L, 8), cudaMemcpyHostToDevice, s), "seed upload");
   QRNG_CUDA(ctx, ctx->out_dev.ensure(out_bytes), "output workspace");
-  st = extract_dispatch(ctx, ctx->samples_dev.as<uint8_t>(), n, m, ctx->seed_dev.as<uint8_t>(), form, algo,
-                        num_blocks, ctx->out_dev.as<uint8_t>(), s);
+  // Two parts when the split keeps both raw and output chunks aligned (n a multiple of 128 bits, the
+  // first part a multiple of 32 blocks): the first 7/8 of the blocks' output travels to the host on the
+  // copy stream while the last 1/8 is hashed, so only 1/8 of the download is left after the last kernel.
+  const uint64_t first = ((num_blocks * 7) / 8) & ~31ull;
+  const bool split = (n % 128 == 0) && num_blocks >= 64 && first >= 32 && first < num_blocks;
+  const uint64_t b0 = split ? first : num_blocks;
+  uint8_t* out_d = ctx->out_dev.as<uint8_t>();
+  st = extract_dispatch(ctx, ctx->samples_dev.as<uint8_t>(), n, m, ctx->seed_dev.as<uint8_t>(), form, algo, b0, out_d,
+                        s);
   if (st) return st;
-  QRNG_CUDA(ctx, cudaMemcpyAsync(out_host, ctx->out_dev.p, out_bytes, cudaMemcpyDeviceToHost, s), "output download");
+  if (split) {
+    const uint64_t bytes0 = b0 * m / 8;  // b0 m is a multiple of 32 bits
+    QRNG_CUDA(ctx, cudaEventRecord(ctx->copy_ready, s), "copy event");
+    QRNG_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->copy_ready, 0), "copy stream wait");
+    QRNG_CUDA(ctx, cudaMemcpyAsync(out_host, out_d, bytes0, cudaMemcpyDeviceToHost, ctx->copy_stream),
+              "output download");
+    QRNG_CUDA(ctx, cudaEventRecord(ctx->copy_done, ctx->copy_stream), "copy event");
+    st = extract_dispatch(ctx, ctx->samples_dev.as<uint8_t>() + b0 * n / 8, n, m, ctx->seed_dev.as<uint8_t>(), form,
+                          algo, num_blocks - b0, out_d + bytes0, s);
+    if (st) {
+      cudaStreamSynchronize(ctx->copy_stream);
+      return st;
+    }
+    QRNG_CUDA(ctx, cudaMemcpyAsync(out_host + bytes0, out_d + bytes0, out_bytes - bytes0, cudaMemcpyDeviceToHost, s),
+              "output download");
+    QRNG_CUDA(ctx, cudaStreamWaitEvent(s, ctx->copy_done, 0), "copy join");
+  } else {
+    QRNG_CUDA(ctx, cudaMemcpyAsync(out_host, out_d, out_bytes, cudaMemcpyDeviceToHost, s), "output download");
+  }
   return qrng_synchronize(ctx, stream);
 }
 

@@ -200,6 +200,8 @@ struct qrng_ctx {
   qrng::DevBuf batch_meta, batch_raw, batch_rev, batch_out, batch_counter;
   uint64_t batch_generation = 0;  // bumped whenever a batch buffer moves (invalidates cached graphs)
   cudaStream_t capture_stream = nullptr;
+  cudaStream_t copy_stream = nullptr;      // host pipeline: output download beside the extraction
+  cudaEvent_t copy_ready = nullptr, copy_done = nullptr;
   struct BatchGraph {
     uint64_t key = 0, generation = 0, stamp = 0;
     cudaGraph_t graph = nullptr;

@@ -93,133 +93,186 @@ __global__ void __launch_bounds__(kHistThreads) hist_u16_global_kernel(const uin
 
 constexpr int kFinThreads = 512;
 
-// Phi(z) - Phi(y) for y < z (either may be infinite) without cancellation: tails as differences
-// of tail masses on their own side of the mean, a cell across the mean as a sum of central masses.
-// (Subtracting two CDF values near 1/2 would lose ~1e-16 absolute, i.e. ~1e-12 relative for the
-// 6e-5 cells of a 16-bit ADC.)
-__device__ __forceinline__ double std_normal_mass(double y, double z) {
-  if (y >= 0.0) return 0.5 * (erfc(y * M_SQRT1_2) - erfc(z * M_SQRT1_2));
-  if (z <= 0.0) return 0.5 * (erfc(-z * M_SQRT1_2) - erfc(-y * M_SQRT1_2));
-  return 0.5 * (erf(z * M_SQRT1_2) - erf(y * M_SQRT1_2));
+typedef unsigned __int128 u128_t;
+
+__device__ __forceinline__ u128_t shfl_down_u128(u128_t v, int d) {
+  const uint64_t lo = __shfl_down_sync(0xffffffffu, (uint64_t)v, d);
+  const uint64_t hi = __shfl_down_sync(0xffffffffu, (uint64_t)(v >> 64), d);
+  return ((u128_t)hi << 64) | lo;
 }
 
-// Model probability of code v under N(mu, sigma^2): the real line between v - 1/2 and v + 1/2,
-// the end codes also taking the tails (the ADC rounds and clips).
-__device__ __forceinline__ double model_cell(uint32_t v, uint32_t K, double mu, double sigma) {
-  const double lo = (v == 0) ? -CUDART_INF : ((double)v - 0.5 - mu) / sigma;
-  const double hi = (v == K - 1) ? CUDART_INF : ((double)v + 0.5 - mu) / sigma;
-  return std_normal_mass(lo, hi);
+// Largest count, lowest code on ties (arg 0xffffffff = none).
+__device__ __forceinline__ void max_arg_merge(unsigned long long& mx, uint32_t& arg, unsigned long long m2,
+                                              uint32_t a2) {
+  if (a2 != 0xffffffffu && (arg == 0xffffffffu || m2 > mx || (m2 == mx && a2 < arg))) {
+    mx = m2;
+    arg = a2;
+  }
+}
+
+// Phi(hi) - Phi(lo) without cancellation: a cell on one side of the mean is a difference of the
+// tails c = erfc(|z| / sqrt 2) of its boundaries (computed once per boundary); the one cell across
+// the mean is a difference of central masses, erf(hi / sqrt 2) - erf(lo / sqrt 2). (One minus the
+// two tails, or two CDF values near 1/2 subtracted, would lose ~1e-16 absolute, i.e. ~1e-12
+// relative for the 6e-5 cells of a 16-bit ADC.)
+__device__ __forceinline__ double cell_from_tails(double lo, double hi, double c_lo, double c_hi) {
+  if (lo >= 0.0) return 0.5 * (c_lo - c_hi);
+  if (hi <= 0.0) return 0.5 * (c_hi - c_lo);
+  return 0.5 * (erf(hi * M_SQRT1_2) - erf(lo * M_SQRT1_2));
+}
+
+constexpr uint32_t kFinChunk = 2048;  // cells per shared-memory chunk of boundary tails
+
+// Model cells of codes [0, K) under N(mu, sigma^2) (boundaries v +- 1/2, end codes take the tails):
+// each boundary's tail is computed once per chunk; returns this thread's largest cell, its sum of
+// |hist/N - P| (when dist) and, for code `want`, its cell in *p_want.
+__device__ void model_cells(const unsigned long long* __restrict__ hist, uint32_t K, unsigned long long N, double mu,
+                            double sigma, bool dist, uint32_t want, double* __restrict__ s_tail, double& pmax,
+                            double& dsum, double* p_want) {
+  for (uint32_t c0 = 0; c0 < K; c0 += kFinChunk) {
+    const uint32_t ncell = (K - c0) < kFinChunk ? (K - c0) : kFinChunk;
+    // s_tail[i] = tail of boundary c0 - 1 + i, i = 0 .. ncell (boundary j lies between codes j, j + 1)
+    for (uint32_t i = threadIdx.x; i <= ncell; i += blockDim.x) {
+      const int64_t j = (int64_t)c0 - 1 + i;
+      const double z = (j < 0 || j >= (int64_t)K - 1) ? CUDART_INF : (((double)j + 0.5 - mu) / sigma);
+      s_tail[i] = erfc(fabs(z) * M_SQRT1_2);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < ncell; i += blockDim.x) {
+      const uint32_t v = c0 + i;
+      const double lo = (v == 0) ? -CUDART_INF : ((double)v - 0.5 - mu) / sigma;
+      const double hi = (v == K - 1) ? CUDART_INF : ((double)v + 0.5 - mu) / sigma;
+      const double P = cell_from_tails(lo, hi, s_tail[i], s_tail[i + 1]);
+      pmax = fmax(pmax, P);
+      if (dist) dsum += fabs((double)hist[v] / (double)N - P);
+      if (v == want) *p_want = P;
+    }
+    __syncthreads();
+  }
 }
 
 __global__ void __launch_bounds__(kFinThreads) hmin_finalize_kernel(const unsigned long long* __restrict__ hist,
                                                                      int bits, double eps,
                                                                      DevHminResult* __restrict__ out, double var_sub,
                                                                      double h_ref) {
-  typedef unsigned __int128 u128;
-  __shared__ unsigned long long s_n[kFinThreads];
-  __shared__ unsigned long long s_max[kFinThreads];
-  __shared__ uint32_t s_arg[kFinThreads];
-  __shared__ u128 s_s1[kFinThreads];
-  __shared__ u128 s_s2[kFinThreads];
-  __shared__ double s_pmax[kFinThreads];
-  __shared__ double s_pmax_full[kFinThreads];
-  __shared__ double s_dsum[kFinThreads];
-  __shared__ double s_mu, s_sigma, s_sigma_q;
+  constexpr int kWarps = kFinThreads / 32;
+  __shared__ unsigned long long w_n[kWarps], w_max[kWarps];
+  __shared__ uint32_t w_arg[kWarps];
+  __shared__ u128_t w_s1[kWarps], w_s2[kWarps];
+  __shared__ double w_pmax[kWarps], w_pmax_full[kWarps], w_dsum[kWarps];
+  __shared__ double s_tail[kFinChunk + 1];
+  __shared__ double s_mu, s_sigma, s_sigma_q, s_pa;
+  __shared__ unsigned long long s_N, s_max;
+  __shared__ uint32_t s_arg;
   __shared__ int s_point, s_bad_sub;
 
   const uint32_t K = 1u << bits;
-  const int t = threadIdx.x;
+  const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
 
   // Pass 1: count, exact first and second moments, largest bin (lowest code on ties).
   unsigned long long n = 0, mx = 0;
   uint32_t arg = 0xffffffffu;
-  u128 s1 = 0, s2 = 0;
+  u128_t s1 = 0, s2 = 0;
   for (uint32_t v = t; v < K; v += kFinThreads) {
-    unsigned long long h = hist[v];
+    const unsigned long long h = hist[v];
     n += h;
-    s1 += (u128)v * h;
-    s2 += (u128)((unsigned long long)v * v) * h;
+    s1 += (u128_t)v * h;
+    s2 += (u128_t)((unsigned long long)v * v) * h;
     if (arg == 0xffffffffu || h > mx) {  // codes visited in increasing order: ties keep the lowest
       mx = h;
       arg = v;
     }
   }
-  s_n[t] = n; s_max[t] = mx; s_arg[t] = arg; s_s1[t] = s1; s_s2[t] = s2;
+  for (int d = 16; d > 0; d >>= 1) {
+    n += __shfl_down_sync(0xffffffffu, n, d);
+    s1 += shfl_down_u128(s1, d);
+    s2 += shfl_down_u128(s2, d);
+    max_arg_merge(mx, arg, __shfl_down_sync(0xffffffffu, mx, d), __shfl_down_sync(0xffffffffu, arg, d));
+  }
+  if (lane == 0) {
+    w_n[wid] = n; w_s1[wid] = s1; w_s2[wid] = s2; w_max[wid] = mx; w_arg[wid] = arg;
+  }
   __syncthreads();
-  for (int w = kFinThreads / 2; w > 0; w >>= 1) {
-    if (t < w) {
-      s_n[t] += s_n[t + w];
-      s_s1[t] += s_s1[t + w];
-      s_s2[t] += s_s2[t + w];
-      unsigned long long m2 = s_max[t + w];
-      uint32_t a2 = s_arg[t + w];
-      if (a2 != 0xffffffffu && (s_arg[t] == 0xffffffffu || m2 > s_max[t] || (m2 == s_max[t] && a2 < s_arg[t]))) {
-        s_max[t] = m2;
-        s_arg[t] = a2;
-      }
-    }
-    __syncthreads();
-  }
-  const unsigned long long N = s_n[0];
-  if (N == 0) {
-    if (t == 0) out->status = QRNG_EINVAL;
-    return;
-  }
   if (t == 0) {
-    const u128 S1 = s_s1[0], S2 = s_s2[0];
-    const u128 num = (u128)N * S2 - S1 * S1;  // N^2 * population variance, exact
-    const double mu = (double)S1 / (double)N;
-    const double var = (double)num / ((double)N * (double)N);
-    s_mu = mu;
-    s_sigma = sqrt(var);
-    s_point = (num == 0);
-    const double var_q = var - var_sub;
-    s_bad_sub = (var_sub > 0.0) && !(var_q > 0.0);
-    s_sigma_q = var_sub > 0.0 && var_q > 0.0 ? sqrt(var_q) : s_sigma;
-    qrng_hmin_report& r = out->rep;
-    r.count = N;
-    r.max_count = s_max[0];
-    r.argmax = s_arg[0];
-    r.bits = (uint32_t)bits;
-    r.mean = mu;
-    r.var = var;
-    r.h_emp = -log2((double)s_max[0] / (double)N);
-    out->out_of_range = hist[K];
+    unsigned long long N = 0, M = 0;
+    uint32_t A = 0xffffffffu;
+    u128_t S1 = 0, S2 = 0;
+    for (int w = 0; w < kWarps; ++w) {
+      N += w_n[w]; S1 += w_s1[w]; S2 += w_s2[w];
+      max_arg_merge(M, A, w_max[w], w_arg[w]);
+    }
+    s_N = N; s_max = M; s_arg = A;
+    if (N == 0) {
+      out->status = QRNG_EINVAL;
+    } else {
+      const u128_t num = (u128_t)N * S2 - S1 * S1;  // N^2 * population variance, exact
+      const double mu = (double)S1 / (double)N;
+      const double var = (double)num / ((double)N * (double)N);
+      s_mu = mu;
+      s_sigma = sqrt(var);
+      s_point = (num == 0);
+      const double var_q = var - var_sub;
+      s_bad_sub = (var_sub > 0.0) && !(var_q > 0.0);
+      s_sigma_q = var_sub > 0.0 && var_q > 0.0 ? sqrt(var_q) : s_sigma;
+      qrng_hmin_report& r = out->rep;
+      r.count = N;
+      r.max_count = M;
+      r.argmax = A;
+      r.bits = (uint32_t)bits;
+      r.mean = mu;
+      r.var = var;
+      r.h_emp = -log2((double)M / (double)N);
+      out->out_of_range = hist[K];
+    }
   }
   __syncthreads();
+  const unsigned long long N = s_N;
+  if (N == 0) return;
 
   // Pass 2: model cells, their maximum, and the distance to the measured distribution.
   const double mu = s_mu, sigma = s_sigma;
-  const int point = s_point;
   const bool sub = var_sub > 0.0 && !s_bad_sub;
-  const uint32_t amax = s_arg[0];
-  double pmax = 0.0, pmax_full = 0.0, dsum = 0.0;
-  for (uint32_t v = t; v < K; v += kFinThreads) {
-    const double P = point ? (v == amax ? 1.0 : 0.0) : model_cell(v, K, mu, sigma);
-    pmax_full = fmax(pmax_full, P);
-    pmax = sub ? fmax(pmax, model_cell(v, K, mu, s_sigma_q)) : pmax_full;
-    dsum += fabs((double)hist[v] / (double)N - P);
-  }
-  s_pmax[t] = pmax;
-  s_pmax_full[t] = pmax_full;
-  s_dsum[t] = dsum;
-  __syncthreads();
-  for (int w = kFinThreads / 2; w > 0; w >>= 1) {
-    if (t < w) {
-      s_pmax[t] = fmax(s_pmax[t], s_pmax[t + w]);
-      s_pmax_full[t] = fmax(s_pmax_full[t], s_pmax_full[t + w]);
-      s_dsum[t] += s_dsum[t + w];
+  const uint32_t amax = s_arg;
+  double pmax_full = 0.0, dsum = 0.0, pmax = 0.0;
+  if (s_point) {  // every sample on one code: the model is that point mass
+    for (uint32_t v = t; v < K; v += kFinThreads) {
+      const double P = (v == amax) ? 1.0 : 0.0;
+      pmax_full = fmax(pmax_full, P);
+      dsum += fabs((double)hist[v] / (double)N - P);
     }
-    __syncthreads();
+    if (t == 0) s_pa = 1.0;
+    pmax = pmax_full;
+  } else {
+    double pa = 0.0;
+    model_cells(hist, K, N, mu, sigma, true, amax, s_tail, pmax_full, dsum, &pa);
+    if (amax % (uint32_t)kFinThreads == (uint32_t)t) s_pa = pa;  // the thread that visited code amax
+    if (sub) {
+      double unused_d = 0.0, unused_p = 0.0;
+      model_cells(hist, K, N, mu, s_sigma_q, false, K, s_tail, pmax, unused_d, &unused_p);
+    } else {
+      pmax = pmax_full;
+    }
   }
+  for (int d = 16; d > 0; d >>= 1) {
+    pmax = fmax(pmax, __shfl_down_sync(0xffffffffu, pmax, d));
+    pmax_full = fmax(pmax_full, __shfl_down_sync(0xffffffffu, pmax_full, d));
+    dsum += __shfl_down_sync(0xffffffffu, dsum, d);
+  }
+  if (lane == 0) {
+    w_pmax[wid] = pmax; w_pmax_full[wid] = pmax_full; w_dsum[wid] = dsum;
+  }
+  __syncthreads();
   if (t == 0) {
+    double PM = 0.0, PF = 0.0, DS = 0.0;
+    for (int w = 0; w < kWarps; ++w) {
+      PM = fmax(PM, w_pmax[w]); PF = fmax(PF, w_pmax_full[w]); DS += w_dsum[w];
+    }
     qrng_hmin_report& r = out->rep;
-    r.h_model = -log2(s_pmax[0]);
-    out->h_subtracted = -log2(s_pmax_full[0]) - h_ref;
+    r.h_model = -log2(PM);
+    out->h_subtracted = -log2(PF) - h_ref;
     if (sub) r.var = s_sigma_q * s_sigma_q;
-    r.d_u = 0.5 * s_dsum[0];
-    double Pa = point ? 1.0 : model_cell(amax, K, mu, sigma);
-    r.d_u_peak = 0.5 * fabs((double)s_max[0] / (double)N - Pa);
+    r.d_u = 0.5 * DS;
+    r.d_u_peak = 0.5 * fabs((double)s_max / (double)N - s_pa);
     r.delta_fs = 0.5 * sqrt(2.0 * ((double)K * M_LN2 + log(1.0 / eps)) / (double)N);
     r.delta_hm = log2((r.d_u + r.delta_fs) * ldexp(1.0, bits + 1) + 1.0);
     double h = r.h_model - r.delta_hm;

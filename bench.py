@@ -53,7 +53,7 @@ def parse():
                    help="laser: the headline stream (default); single: one 4096-bit block; sweep: block-length "
                         "sweep on a 2^30-bit stream; tc: m=6144, n=8192, 4096 blocks; uneven: 10,000 requests; "
                         "long: 64 blocks of 2^22 bits (the transform route's profiling case)")
-    p.add_argument("--sweep-algos", default="direct,gemm_tc,gemm_fp4,gemm_fp4_pair,ntt,fft64",
+    p.add_argument("--sweep-algos", default="direct,gemm_tc,gemm_fp4,gemm_fp4_pair,gemm_karatsuba,ntt,fft64",
                    help="algorithms timed at each block length of the sweep")
     p.add_argument("--uneven-max-log2n", type=float, default=22.0,
                    help="upper end of the log-uniform n range of the uneven requests")
@@ -242,7 +242,8 @@ def run_ours(args, world, rank, local):
     m = step()
     torch.cuda.synchronize()
 
-    roofline = roofline_for(used_algo, num_blocks, m, n, kernel_ms)
+    plan = q.qrng_karatsuba_plan(ctx, n, m, q.QRNG_FORM_STANDARD, num_blocks) if used_algo == "gemm_karatsuba" else None
+    roofline = roofline_for(used_algo, num_blocks, m, n, kernel_ms, plan)
 
     # end to end through the host-buffer entry point (pinned host memory, copies inside the timed region)
     e2e = None
@@ -293,7 +294,8 @@ def run_ours(args, world, rank, local):
 
 DTYPES = {"gemm_tc": "e4m3 0/1 operands, f32 accumulate",
           "gemm_fp4": "e2m1 0/1 operands (ue8m0 scales 2^0), f32 accumulate",
-          "gemm_fp4_pair": "e2m1 0/1 operands (ue8m0 scales 2^0), f32 accumulate"}
+          "gemm_fp4_pair": "e2m1 0/1 operands (ue8m0 scales 2^0), f32 accumulate",
+          "gemm_karatsuba": "e2m1 0/1 operands (ue8m0 scales 2^0), f32 accumulate"}
 
 
 def measured_peaks():
@@ -322,7 +324,7 @@ def captured_traffic(kernel: str, source: str, units: int):
     return int(rec["dram_bytes"] * units / rec["blocks"])
 
 
-def roofline_for(algo, num_blocks, m, n, kernel_ms):
+def roofline_for(algo, num_blocks, m, n, kernel_ms, plan=None):
     """Roofline of the dominant (extraction) kernel from its algorithmic work and live event time."""
     if algo == "direct":
         achieved = num_blocks * m * n / (kernel_ms / 1e3) / 1e12
@@ -350,6 +352,20 @@ def roofline_for(algo, num_blocks, m, n, kernel_ms):
                 "kernel": ("gemm_pair_kernel (tcgen05 cta_group::2 kind::mxf4, block scale 2^0)" if pair
                            else "gemm_tc_kernel<fp4> (tcgen05 kind::mxf4, block scale 2^0)"),
                 "kernel_ms": kernel_ms, "peak_source": "FP4 = 6 x bf16 burst " + pk["source"]}
+    if algo == "gemm_karatsuba":
+        # the product kernel's own work: 3^L dense sub-products of mq x kq per block (the plan the
+        # library ran, from qrng_karatsuba_plan)
+        pk = measured_peaks()
+        peak = 6.0 * pk["bf16_tflops"]
+        plan = plan or {}
+        flops = 2.0 * num_blocks * plan["groups"] * plan["mq"] * plan["kq"]
+        achieved = flops / (kernel_ms / 1e3) / 1e12
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": captured_traffic("gemm_pair_kara_kernel", "k_gemm_pair.cu", num_blocks),
+                "kernel": "gemm_pair_kernel<kKara> (tcgen05 cta_group::2 kind::mxf4 on the block-Karatsuba "
+                          "sub-products)", "kernel_ms": kernel_ms,
+                "plan": plan, "equivalent_plain_tflops": 2.0 * num_blocks * m * n / (kernel_ms / 1e3) / 1e12,
+                "peak_source": "FP4 = 6 x bf16 burst " + pk["source"]}
     return {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
             "kernel_ms": kernel_ms}
 
@@ -409,7 +425,7 @@ def run_reference(args, world, rank):
 
 
 ALGOS = {"auto": 0, "direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4, "ntt": 5, "gemm_fp4": 6,
-         "gemm_fp4_pair": 7}
+         "gemm_fp4_pair": 7, "gemm_karatsuba": 8}
 
 
 def _time_extract(q, ctx, raw, n, m, seed, form, algo, blocks, out, reps, warmup=1):
@@ -489,7 +505,7 @@ def run_forms(args):
                 L = n + m - 1 if form == 0 else n - 1
                 seed = torch.from_numpy(W.random_bits(L, 99)).cuda()
                 row[fname] = {"seed_bits": L}
-                for name in ("direct", "gemm_tc", "gemm_fp4", "gemm_fp4_pair", "ntt"):
+                for name in ("direct", "gemm_tc", "gemm_fp4", "gemm_fp4_pair", "gemm_karatsuba", "ntt"):
                     kms, cms, _ = _time_extract(q, ctx, raw, n, m, seed, form, ALGOS[name], B, out, reps=2)
                     row[fname][name] = {"call_ms": cms, "gbps": B * m / (cms / 1e3) / 1e9}
             rows.append(row)
@@ -513,10 +529,15 @@ def run_tc(args):
     out = torch.empty(m * B // 8, dtype=torch.uint8, device="cuda")
     res = {"workload": "m=6144, n=8192, 4096 blocks, one standard seed", "unit": UNIT, "data": "synthetic"}
     pk = measured_peaks()
-    for name in ("gemm_fp4_pair", "gemm_fp4", "gemm_tc", "direct"):
+    for name in ("gemm_karatsuba", "gemm_fp4_pair", "gemm_fp4", "gemm_tc", "direct"):
         kms, cms, _ = _time_extract(q, ctx, raw, n, m, seed, 0, ALGOS[name], B, out, reps=args.steps)
-        res[name] = {"kernel_ms": kms, "gbps": B * m / (kms / 1e3) / 1e9}
-        if name.startswith("gemm"):
+        res[name] = {"kernel_ms": kms, "call_ms": cms, "gbps": B * m / (cms / 1e3) / 1e9}
+        if name == "gemm_karatsuba":
+            plan = q.qrng_karatsuba_plan(ctx, n, m, 0, B)
+            tf = 2.0 * plan["groups"] * plan["mq"] * plan["kq"] * B / (kms / 1e3) / 1e12
+            res[name].update({"plan": plan, "tflops": tf, "frac_of_peak": tf / (6.0 * pk["bf16_tflops"]),
+                              "peak_source": f"6 x bf16 burst {pk['source']}"})
+        elif name.startswith("gemm"):
             tf = 2.0 * m * n * B / (kms / 1e3) / 1e12
             ratio = 6.0 if name.startswith("gemm_fp4") else 2.0  # nominal FP4 / FP8 dense rates over bf16
             res[name].update({"tflops": tf, "frac_of_peak": tf / (ratio * pk["bf16_tflops"]),

@@ -189,8 +189,12 @@ enum {
                              to 2^27                                                                */
   QRNG_ALGO_GEMM_FP4 = 6, /* QRNG_ALGO_GEMM_TC with 4-bit operands (block-scaled E2M1, every scale
                              2^0): half the operand bytes and the FP4 tensor rate; same limits     */
-  QRNG_ALGO_GEMM_FP4_PAIR = 7 /* QRNG_ALGO_GEMM_FP4 with each MMA spanning a pair of SMs (clusters
+  QRNG_ALGO_GEMM_FP4_PAIR = 7,/* QRNG_ALGO_GEMM_FP4 with each MMA spanning a pair of SMs (clusters
                              of two CTAs, M = 256): fewer shared-memory bytes per MAC; same limits */
+  QRNG_ALGO_GEMM_KARATSUBA = 8 /* QRNG_ALGO_GEMM_FP4_PAIR on the 3^L sub-products of L rounds of
+                             block Karatsuba over GF(2) (2x2 Toeplitz blocks need three products:
+                             (3/4)^L of the multiply-adds, plus three memory-bound passes and
+                             workspace of about 3^L (m + n) / 2^(L+3) bytes per block); same limits */
 };
 
 /* Seed length in bits: n+m-1 (standard) or n-1 (modified); 0 for an invalid shape. */
@@ -316,6 +320,29 @@ QRNG_API int qrng_inject_fault(qrng_ctx* ctx, int fault);
 /* Autotuning of QRNG_ALGO_AUTO (on = 1, the default; off = 0 uses the cost model alone and never
  * synchronises). Changing it forgets the shapes tuned so far. */
 QRNG_API int qrng_set_autotune(qrng_ctx* ctx, int on);
+
+/* Block Karatsuba settings of QRNG_ALGO_GEMM_KARATSUBA (0 = chosen by the cost model, the default):
+ *   levels          rounds of the 2x2 block split, 1..3;
+ *   block_bits      h, the side of the square Toeplitz blocks: 512, 1024, 2048, 4096 or 8192;
+ *   max_workspace   device bytes for the derived operands and sub-product parities of one pass
+ *                   (the blocks are processed in passes that fit it; 0 = 1 GiB).
+ * Returns QRNG_EINVAL for values outside those sets. Forgets the shapes autotuned so far. */
+QRNG_API int qrng_set_karatsuba(qrng_ctx* ctx, int levels, uint64_t block_bits, uint64_t max_workspace);
+
+/* The block Karatsuba plan QRNG_ALGO_GEMM_KARATSUBA would run for this shape under the context's
+ * settings (no GPU work): levels (0 when no plan fits), block side h in bits, the number of
+ * sub-products (3^levels), each sub-product's rows and columns (multiples of h), blocks per pass
+ * and the cost model's seconds for all blocks. Returns QRNG_EINVAL for an invalid shape. */
+typedef struct {
+  int levels;
+  uint64_t block_bits;
+  uint64_t products;
+  uint64_t rows, cols;
+  uint64_t blocks_per_pass;
+  double model_seconds;
+} qrng_karatsuba_plan_info;
+QRNG_API int qrng_karatsuba_plan(qrng_ctx* ctx, uint64_t n, uint64_t m, int form, uint64_t num_blocks,
+                                 qrng_karatsuba_plan_info* out);
 
 /* Timing of the main extraction kernel of each qrng_toeplitz_extract call (on = 1, off = 0):
  * a CUDA event pair is recorded around that one launch on the caller's stream and summed into

@@ -17,16 +17,17 @@ LIB_PATH = os.path.join(_PKG, "libqrng_gb300.so")
 QRNG_OK, QRNG_EINVAL, QRNG_ENOMEM, QRNG_ECUDA, QRNG_ETIMEOUT, QRNG_EPRECISION, QRNG_ENOTSUP = range(7)
 QRNG_FORM_STANDARD, QRNG_FORM_MODIFIED = 0, 1
 (QRNG_ALGO_AUTO, QRNG_ALGO_DIRECT, QRNG_ALGO_GEMM_TC, QRNG_ALGO_FFT64, QRNG_ALGO_FFT32_SEG, QRNG_ALGO_NTT,
- QRNG_ALGO_GEMM_FP4, QRNG_ALGO_GEMM_FP4_PAIR) = range(8)
+ QRNG_ALGO_GEMM_FP4, QRNG_ALGO_GEMM_FP4_PAIR, QRNG_ALGO_GEMM_KARATSUBA) = range(9)
 ALGO_NAMES = {QRNG_ALGO_AUTO: "auto", QRNG_ALGO_DIRECT: "direct", QRNG_ALGO_GEMM_TC: "gemm_tc",
               QRNG_ALGO_FFT64: "fft64", QRNG_ALGO_FFT32_SEG: "fft32_seg", QRNG_ALGO_NTT: "ntt",
-              QRNG_ALGO_GEMM_FP4: "gemm_fp4", QRNG_ALGO_GEMM_FP4_PAIR: "gemm_fp4_pair"}
+              QRNG_ALGO_GEMM_FP4: "gemm_fp4", QRNG_ALGO_GEMM_FP4_PAIR: "gemm_fp4_pair",
+              QRNG_ALGO_GEMM_KARATSUBA: "gemm_karatsuba"}
 
 EXPORTED = ["qrng_create", "qrng_destroy", "qrng_last_error", "qrng_status_string", "qrng_minentropy",
             "qrng_output_length", "qrng_seed_bits", "qrng_toeplitz_extract", "qrng_postprocess_host",
             "qrng_get_stats", "qrng_reset_stats", "qrng_set_timing", "qrng_synchronize",
             "qrng_minentropy_noalloc", "qrng_extract_batch", "qrng_set_autotune", "qrng_inject_fault",
-            "qrng_minentropy_sampled", "qrng_minentropy_quantum"]
+            "qrng_minentropy_sampled", "qrng_minentropy_quantum", "qrng_set_karatsuba", "qrng_karatsuba_plan"]
 QRNG_FAULT_NONE, QRNG_FAULT_GEMM_NO_TMA = 0, 1
 
 
@@ -85,6 +86,18 @@ class Stats(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class KaratsubaPlan(ctypes.Structure):
+    _fields_ = [
+        ("levels", ctypes.c_int),
+        ("block_bits", ctypes.c_uint64),
+        ("products", ctypes.c_uint64),
+        ("rows", ctypes.c_uint64),
+        ("cols", ctypes.c_uint64),
+        ("blocks_per_pass", ctypes.c_uint64),
+        ("model_seconds", ctypes.c_double),
+    ]
+
+
 _lib = None
 
 
@@ -117,6 +130,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qrng_set_timing.argtypes = [vp, i32]
     lib.qrng_synchronize.argtypes = [vp, vp]
     lib.qrng_set_autotune.argtypes = [vp, i32]
+    lib.qrng_set_karatsuba.argtypes = [vp, i32, u64, u64]
+    lib.qrng_karatsuba_plan.argtypes = [vp, u64, u64, i32, u64, ctypes.POINTER(KaratsubaPlan)]
     lib.qrng_minentropy_sampled.argtypes = [vp, vp, u64, i32, dbl, dbl, u64, ctypes.POINTER(HminReport), vp]
     lib.qrng_minentropy_quantum.argtypes = [vp, vp, u64, vp, u64, i32, dbl, ctypes.POINTER(HminReport),
                                             ctypes.POINTER(dbl), vp]
@@ -298,6 +313,20 @@ def qrng_extract_batch(ctx: Context, requests, algo: int = QRNG_ALGO_AUTO, strea
 
 def qrng_set_autotune(ctx: Context, on: bool):
     ctx.check(load_library().qrng_set_autotune(ctx.handle, 1 if on else 0), "qrng_set_autotune")
+
+
+def qrng_set_karatsuba(ctx: Context, levels: int = 0, block_bits: int = 0, max_workspace: int = 0):
+    """Block Karatsuba settings of QRNG_ALGO_GEMM_KARATSUBA (0 = chosen by the cost model)."""
+    ctx.check(load_library().qrng_set_karatsuba(ctx.handle, levels, block_bits, max_workspace), "qrng_set_karatsuba")
+
+
+def qrng_karatsuba_plan(ctx: Context, n: int, m: int, form: int, num_blocks: int) -> dict:
+    """The block Karatsuba plan of QRNG_ALGO_GEMM_KARATSUBA for this shape (no GPU work)."""
+    info = KaratsubaPlan()
+    ctx.check(load_library().qrng_karatsuba_plan(ctx.handle, n, m, form, num_blocks, ctypes.byref(info)),
+              "qrng_karatsuba_plan")
+    return {"levels": info.levels, "h": info.block_bits, "groups": info.products, "mq": info.rows,
+            "kq": info.cols, "blocks_per_pass": info.blocks_per_pass, "model_s": info.model_seconds}
 
 
 def qrng_inject_fault(ctx: Context, fault: int):

@@ -37,12 +37,16 @@ constexpr size_t kMaxTimed = 4096;
 // Largest distance of an FFT convolution sum from its integer that still counts as exact.
 constexpr double kFftRoundGuard = 0.25;
 
-// Brackets one launch with a CUDA event pair on its stream when timing is on.
+// Brackets one launch with a CUDA event pair on its stream when timing is on. With
+// record_now = false the events are handed to a launcher that records them around its main
+// kernel itself (start_event / end_event; null when timing is off), and done(false) keeps them.
 struct LaunchTimer {
   qrng_ctx* ctx;
   cudaStream_t s;
   size_t slot = (size_t)-1;
-  LaunchTimer(qrng_ctx* c, cudaStream_t st) : ctx(c), s(st) {
+  cudaEvent_t start_event() const { return slot == (size_t)-1 ? nullptr : ctx->ev_start[slot]; }
+  cudaEvent_t end_event() const { return slot == (size_t)-1 ? nullptr : ctx->ev_end[slot]; }
+  LaunchTimer(qrng_ctx* c, cudaStream_t st, bool record_now = true) : ctx(c), s(st) {
     if (!ctx->timing || ctx->ev_used >= kMaxTimed) return;
     if (ctx->ev_used == ctx->ev_start.size()) {
       cudaEvent_t a, b;
@@ -55,11 +59,11 @@ struct LaunchTimer {
       ctx->ev_end.push_back(b);
     }
     slot = ctx->ev_used;
-    if (cudaEventRecord(ctx->ev_start[slot], s) != cudaSuccess) slot = (size_t)-1;
+    if (record_now && cudaEventRecord(ctx->ev_start[slot], s) != cudaSuccess) slot = (size_t)-1;
   }
-  void done() {
+  void done(bool record_end = true) {
     if (slot == (size_t)-1) return;
-    if (cudaEventRecord(ctx->ev_end[slot], s) == cudaSuccess) ctx->ev_used = slot + 1;
+    if (!record_end || cudaEventRecord(ctx->ev_end[slot], s) == cudaSuccess) ctx->ev_used = slot + 1;
     slot = (size_t)-1;
   }
 };
@@ -87,7 +91,8 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
 
   DirectArgs a{};
   // The tensor-core kernel loads raw tiles with TMA: 16-byte aligned rows, a multiple of 4 words apart.
-  const bool gemm = (algo == QRNG_ALGO_GEMM_TC || algo == QRNG_ALGO_GEMM_FP4 || algo == QRNG_ALGO_GEMM_FP4_PAIR);
+  const bool gemm = (algo == QRNG_ALGO_GEMM_TC || algo == QRNG_ALGO_GEMM_FP4 || algo == QRNG_ALGO_GEMM_FP4_PAIR ||
+                     algo == QRNG_ALGO_GEMM_KARATSUBA);
   const bool raw_direct = gemm ? (n % 128 == 0) && ((reinterpret_cast<uintptr_t>(raw) & 15) == 0)
                                : (n % 32 == 0) && ((reinterpret_cast<uintptr_t>(raw) & 3) == 0);
   if (raw_direct) {
@@ -138,16 +143,27 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
   }
   if (gemm) {
     QRNG_CUDA(ctx, ctx->dev_err.ensure(sizeof(int)), "error word");
-    LaunchTimer timer(ctx, s);
+    LaunchTimer timer(ctx, s, algo != QRNG_ALGO_GEMM_KARATSUBA);
     const int fault = ctx->fault;
     ctx->fault = 0;  // one-shot
-    QRNG_CUDA(ctx,
-              algo == QRNG_ALGO_GEMM_FP4_PAIR
-                  ? launch_gemm_pair(a, ctx->dev_err.as<int>(), fault, ctx->num_sms, s, kernels)
-                  : launch_gemm_tc(a, algo == QRNG_ALGO_GEMM_FP4, ctx->dev_err.as<int>(), fault, ctx->num_sms, s,
-                                   kernels),
-              "tensor-core extraction kernel");
-    timer.done();
+    if (algo == QRNG_ALGO_GEMM_KARATSUBA) {
+      const KaraPlan plan = karatsuba_plan(n_t, m, num_blocks, ctx->num_sms, ctx->kara_levels, ctx->kara_h,
+                                           ctx->kara_workspace);
+      if (plan.levels == 0) return fail(ctx, QRNG_ENOTSUP, "qrng_toeplitz_extract: no block Karatsuba plan fits");
+      QRNG_CUDA(ctx,
+                launch_gemm_karatsuba(a, plan, ctx->kara, ctx->dev_err.as<int>(), fault, ctx->num_sms, s, kernels,
+                                      timer.start_event(), timer.end_event()),
+                "block Karatsuba extraction");
+      timer.done(false);  // the launcher recorded the pair around its product kernel
+    } else {
+      QRNG_CUDA(ctx,
+                algo == QRNG_ALGO_GEMM_FP4_PAIR
+                    ? launch_gemm_pair(a, ctx->dev_err.as<int>(), fault, ctx->num_sms, s, kernels)
+                    : launch_gemm_tc(a, algo == QRNG_ALGO_GEMM_FP4, ctx->dev_err.as<int>(), fault, ctx->num_sms, s,
+                                     kernels),
+                "tensor-core extraction kernel");
+      timer.done();
+    }
     if (!out_direct)
       QRNG_CUDA(ctx, launch_pack_blocks(out_w, mw, m, num_blocks, out, s, kernels), "output pack");
     return QRNG_OK;
@@ -230,14 +246,14 @@ int check_extract_args(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m
                 "qrng_toeplitz_extract: need 1 <= m <= n (standard) or 1 <= m < n (modified), n <= 2^26");
   if (num_blocks == 0) return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: num_blocks must be >= 1");
   if (num_blocks > (1ull << 62) / n) return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: stream too long");
-  if (algo < QRNG_ALGO_AUTO || algo > QRNG_ALGO_GEMM_FP4_PAIR)
+  if (algo < QRNG_ALGO_AUTO || algo > QRNG_ALGO_GEMM_KARATSUBA)
     return fail(ctx, QRNG_EINVAL, "qrng_toeplitz_extract: unknown algorithm");
   return QRNG_OK;
 }
 
 // Rough time model (seconds) of each algorithm, used to prune the autotuner's candidates and as
 // the choice when autotuning is off. Rates are the ones measured on GB300 for these kernels.
-double model_seconds(int algo, uint64_t n_t, uint64_t m, uint64_t B) {
+double model_seconds(const qrng_ctx* ctx, int algo, uint64_t n_t, uint64_t m, uint64_t B) {
   const double bm = (double)m * (double)n_t * (double)B;
   switch (algo) {
     case QRNG_ALGO_DIRECT:
@@ -253,6 +269,10 @@ double model_seconds(int algo, uint64_t n_t, uint64_t m, uint64_t B) {
     case QRNG_ALGO_GEMM_FP4_PAIR: {
       const double mp = (double)ceil_div(m, 256) * 256, bp = (double)ceil_div(B, 256) * 256;
       return mp * (double)n_t * bp / 3.5e15 + 1e-5;
+    }
+    case QRNG_ALGO_GEMM_KARATSUBA: {
+      const KaraPlan p = karatsuba_plan(n_t, m, B, ctx->num_sms, ctx->kara_levels, ctx->kara_h, ctx->kara_workspace);
+      return p.levels ? p.model_s : 1e30;
     }
     case QRNG_ALGO_FFT64: {
       const double P = (double)fft64_length(n_t, m), lg = log2(P), pairs = (double)ceil_div(B, 2);
@@ -278,6 +298,7 @@ bool algo_applicable(int algo, uint64_t n_t, uint64_t m, uint64_t B) {
     case QRNG_ALGO_GEMM_TC:
     case QRNG_ALGO_GEMM_FP4:
     case QRNG_ALGO_GEMM_FP4_PAIR:
+    case QRNG_ALGO_GEMM_KARATSUBA:
       return n_t <= kGemmMaxColumns;
     case QRNG_ALGO_FFT64:
     case QRNG_ALGO_NTT:
@@ -299,13 +320,13 @@ int extract_one(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uint64_
 int choose_auto(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
                 uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels, int* chosen, bool* done) {
   const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
-  const int algos[7] = {QRNG_ALGO_DIRECT, QRNG_ALGO_GEMM_TC, QRNG_ALGO_GEMM_FP4, QRNG_ALGO_GEMM_FP4_PAIR,
-                        QRNG_ALGO_NTT,    QRNG_ALGO_FFT64,   QRNG_ALGO_FFT32_SEG};
+  const int algos[8] = {QRNG_ALGO_DIRECT, QRNG_ALGO_GEMM_TC,     QRNG_ALGO_GEMM_FP4,  QRNG_ALGO_GEMM_FP4_PAIR,
+                        QRNG_ALGO_GEMM_KARATSUBA, QRNG_ALGO_NTT, QRNG_ALGO_FFT64, QRNG_ALGO_FFT32_SEG};
   double best_model = 1e30;
   int best_algo = QRNG_ALGO_DIRECT;
   for (int a : algos)
     if (algo_applicable(a, n_t, m, num_blocks)) {
-      const double t = model_seconds(a, n_t, m, num_blocks);
+      const double t = model_seconds(ctx, a, n_t, m, num_blocks);
       if (t < best_model) { best_model = t; best_algo = a; }
     }
   *done = false;
@@ -324,7 +345,7 @@ int choose_auto(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const
   int best = -1;
   float best_ms = 0.f;
   for (int a : algos) {
-    if (!algo_applicable(a, n_t, m, num_blocks) || model_seconds(a, n_t, m, num_blocks) > 4.0 * best_model) continue;
+    if (!algo_applicable(a, n_t, m, num_blocks) || model_seconds(ctx, a, n_t, m, num_blocks) > 4.0 * best_model) continue;
     cudaEvent_t e0, e1;
     QRNG_CUDA(ctx, cudaEventCreate(&e0), "autotune event");
     QRNG_CUDA(ctx, cudaEventCreate(&e1), "autotune event");
@@ -381,6 +402,7 @@ int extract_dispatch(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, 
     case QRNG_ALGO_GEMM_TC:
     case QRNG_ALGO_GEMM_FP4:
     case QRNG_ALGO_GEMM_FP4_PAIR:
+    case QRNG_ALGO_GEMM_KARATSUBA:
       if (n_t > kGemmMaxColumns)
         return fail(ctx, QRNG_ENOTSUP, "qrng_toeplitz_extract: the tensor-core path needs n (n-m modified) <= 2^22");
       st = extract_bitwise(ctx, used, raw, n, m, seed, form, num_blocks, out, s, &kernels);
@@ -665,6 +687,7 @@ void qrng_destroy(qrng_ctx* ctx) {
   ctx->dev_err.release();
   ctx->fft_worst.release();
   ctx->fft.release();
+  ctx->kara.release();
   drop_all_graphs(ctx);
   ctx->batch_meta.release();
   ctx->batch_raw.release();
@@ -907,6 +930,36 @@ int qrng_set_autotune(qrng_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) return QRNG_EINVAL;
   ctx->autotune = (on == 1);
   ctx->tuned.clear();
+  return QRNG_OK;
+}
+
+int qrng_set_karatsuba(qrng_ctx* ctx, int levels, uint64_t block_bits, uint64_t max_workspace) {
+  if (!ctx) return QRNG_EINVAL;
+  if (levels < 0 || levels > 3) return fail(ctx, QRNG_EINVAL, "qrng_set_karatsuba: levels must be 0..3");
+  if (block_bits != 0 && (block_bits < 512 || block_bits > 8192 || (block_bits & (block_bits - 1)) != 0))
+    return fail(ctx, QRNG_EINVAL, "qrng_set_karatsuba: block_bits must be 0 or a power of two in [512, 8192]");
+  ctx->kara_levels = levels;
+  ctx->kara_h = block_bits;
+  ctx->kara_workspace = max_workspace;
+  ctx->tuned.clear();
+  return QRNG_OK;
+}
+
+int qrng_karatsuba_plan(qrng_ctx* ctx, uint64_t n, uint64_t m, int form, uint64_t num_blocks,
+                        qrng_karatsuba_plan_info* out) {
+  if (!ctx || !out) return QRNG_EINVAL;
+  if (!shape_ok(n, m, form) || num_blocks == 0) return fail(ctx, QRNG_EINVAL, "qrng_karatsuba_plan: invalid shape");
+  const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
+  const KaraPlan p = karatsuba_plan(n_t, m, num_blocks, ctx->num_sms, ctx->kara_levels, ctx->kara_h,
+                                    ctx->kara_workspace);
+  *out = qrng_karatsuba_plan_info{};
+  out->levels = (int)p.levels;
+  out->block_bits = p.h;
+  out->products = p.groups;
+  out->rows = p.mq;
+  out->cols = p.kq;
+  out->blocks_per_pass = p.chunk_blocks;
+  out->model_seconds = p.model_s;
   return QRNG_OK;
 }
 

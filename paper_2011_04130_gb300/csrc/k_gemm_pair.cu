@@ -23,9 +23,11 @@
 //   warp 6      TMA: packed raw tiles (112 blocks x 32 bytes) of this CTA's blocks, in step order;
 //   warp 7      tensor memory allocation (both CTAs); in the leader CTA (rank 0) one lane issues the
 //               cta_group::2 MMAs and multicasts their completion to both CTAs' barriers;
-//   warps 8-11  epilogue: each CTA reads its 128 rows of both accumulators (its outputs) from its own
-//               tensor memory, parity, __ballot_sync into output words, identity XOR for the
-//               modified form.
+//   warps 8-15  epilogue: two warps per TMEM lane quarter, one per accumulator; each CTA reads its
+//               128 rows of both accumulators (its outputs) from its own tensor memory in 16-column
+//               loads double-buffered against the parity __ballot_sync of the previous load, and
+//               hands the accumulators back as soon as its last load has landed; identity XOR for
+//               the modified form.
 // Both epilogues signal the leader's accumulator barrier. Every wait is bounded (about one second of
 // clock): on timeout a CTA records an error code and stops; the leader still drains its MMAs, and
 // both CTAs meet at a cluster barrier before tensor memory is released.
@@ -54,8 +56,8 @@ constexpr int T_ROWS = HM / 32;          // T rows lane + 32 j of a lane
 constexpr int TMA_WARP = PRODUCER_WARPS;
 constexpr int MMA_WARP = TMA_WARP + 1;
 constexpr int EPI_WARP0 = MMA_WARP + 1;
-constexpr int EPI_WARPS = 4;
-constexpr int THREADS = (EPI_WARP0 + EPI_WARPS) * 32;  // 384
+constexpr int EPI_WARPS = 8;                           // two per TMEM lane quarter: one per accumulator
+constexpr int THREADS = (EPI_WARP0 + EPI_WARPS) * 32;  // 512
 constexpr int TMEM_COLS = 512;
 constexpr uint32_t SFA_COL = 448;        // scale factors (all 2^0) of A, then of B
 constexpr uint32_t SFB_COL = 480;
@@ -120,12 +122,49 @@ struct PairArgs {
   uint64_t num_blocks;
   uint32_t mpairs;   // pairs of output tiles
   uint32_t ntiles;
-  uint32_t ksteps;
+  uint32_t ksteps;   // K steps per K block (plain product: all of them, one K block)
   int* err;
   int fault_no_tma;  // test hook: the loader publishes no raw tile, so every consumer's bounded wait runs out
+  // block Karatsuba sub-products (kKara): group z of `groups` is the product of derived seed z
+  // (seed_rev + z * seed_stride) with derived raw operand z (rows z * num_blocks + b of the raw
+  // map); its rows and columns are the h-blocks of every span-th position of a Toeplitz matrix, so
+  // each K block of h columns starts with a step that builds only the T tile left of it, and each
+  // K block / row block shifts the seed window by span - h bits.
+  uint32_t seed_front;   // front padding (words) of every seed buffer
+  uint32_t kblocks;      // K blocks of h columns (plain: 1)
+  uint32_t seed_kshift;  // (span - h) / 32: seed words skipped per K block
+  uint32_t xk_kwords;    // h / 32: raw-operand words per K block
+  uint32_t log2h;
+  uint32_t row_shift;    // span - h: seed bits skipped per row block
+  uint32_t groups;
+  uint64_t seed_stride;  // words per derived seed
+  uint32_t* qpar;        // parities of the sub-products: word (z * num_blocks + b) * mwq + row / 32
+  uint32_t mwq;
 };
 
-template <int kPN>
+struct TileCoord {
+  uint32_t mt;  // first output tile of the pair (rows mt*256 .. mt*256 + 511)
+  uint32_t nt;  // block column tile
+  uint32_t z;   // sub-product (Karatsuba groups; 0 otherwise)
+};
+
+// Row pairs fastest, then block tiles, then groups: tiles that run together share raw operand tiles.
+template <bool kKara>
+__device__ __forceinline__ TileCoord tile_coord(const PairArgs& a, uint64_t tile) {
+  TileCoord t;
+  t.mt = 2u * (uint32_t)(tile % a.mpairs);
+  const uint64_t rest = tile / a.mpairs;
+  if (kKara) {
+    t.nt = (uint32_t)(rest % a.ntiles);
+    t.z = (uint32_t)(rest / a.ntiles);
+  } else {
+    t.nt = (uint32_t)rest;
+    t.z = 0;
+  }
+  return t;
+}
+
+template <int kPN, bool kKara>
 __global__ void __launch_bounds__(THREADS, 1)
     gemm_pair_kernel(const PairArgs a, const __grid_constant__ CUtensorMap raw_map) {
   using S = PairShape<kPN>;
@@ -140,6 +179,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __shared__ __align__(8) uint64_t accum_empty_bar;        // leader: one arrival per epilogue warp of both CTAs
   __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_slot;
+  __shared__ uint32_t epi_words[EPI_WARPS][kPN / 32][32];  // an epilogue warp's output words of a tile
   __shared__ volatile int abort_flag;
 
   const uint32_t warp = threadIdx.x >> 5;
@@ -174,7 +214,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem_base = tmem_slot;
-  if (warp >= EPI_WARP0) {
+  if (warp >= EPI_WARP0 && warp < EPI_WARP0 + 4) {
     // every scale factor is 2^0: fill the 64 scale-factor columns in all 128 lanes, whatever cells
     // the MMAs read there
     const uint32_t lanes = (32u * (warp & 3u)) << 16;
@@ -186,10 +226,11 @@ __global__ void __launch_bounds__(THREADS, 1)
   cluster_sync();  // both CTAs' scale factors are in place before the first MMA
   tc_fence_after();
 
-  const uint64_t ntile_total = (uint64_t)a.mpairs * a.ntiles;
+  const uint64_t ntile_total = (uint64_t)a.mpairs * a.ntiles * (kKara ? a.groups : 1u);
   const uint64_t first_tile = blockIdx.x >> 1;
   const uint64_t tile_stride = gridDim.x >> 1;
-  const uint32_t nsteps = a.ksteps + 1;  // step 0 builds T(mt, -1) only
+  const uint32_t spb = a.ksteps + 1;  // steps per K block: the first builds T(mt, -1) of the block only
+  const uint32_t nsteps = spb * (kKara ? a.kblocks : 1u);
   if (warp < PRODUCER_WARPS) {
     // ------------------------------------------------------------------ producers (warp = stage)
     const uint32_t st = warp;
@@ -200,26 +241,33 @@ __global__ void __launch_bounds__(THREADS, 1)
     uint32_t use = 0;   // uses of this stage so far
     uint32_t base = 0;  // index of the tile's step 0 modulo STAGES
     for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
-      const uint32_t mt = 2u * (uint32_t)(tile % a.mpairs);
-      // T row i = mt*256 + rank*128 + lane + 32 j at step e reads reversed-seed bits
-      // m-1-i+BK*(e-1) .. +BK-1; rows 32 apart start one word apart at the same shift (the front
-      // padding keeps every index >= 0, also at e = 0)
-      const int64_t ubase = (int64_t)a.m - 1 - ((int64_t)mt * PM + rank * HM + lane) + 32 * (int64_t)kSeedFrontWords;
+      const TileCoord tc = tile_coord<kKara>(a, tile);
+      const uint32_t r0 = tc.mt * PM;
+      // T row i = r0 + rank*128 + lane + 32 j at K step ks reads reversed-seed bits
+      // m-1-i+BK*ks .. +BK-1 (Karatsuba: minus row_shift per row block, plus row_shift per K block);
+      // rows 32 apart start one word apart at the same shift (the front padding keeps every index
+      // >= 0, also for the window left of a K block)
+      const int64_t vshift = kKara ? (int64_t)(r0 >> a.log2h) * a.row_shift : 0;
+      const int64_t ubase = (int64_t)a.m - 1 - ((int64_t)r0 + rank * HM + lane) - vshift + 32 * (int64_t)a.seed_front;
       const uint32_t sh = (uint32_t)(ubase & 31);
-      const uint32_t* seed_row = a.seed_rev + ((ubase >> 5) - KW);  // the window of step 0
+      const uint32_t* seed_row = a.seed_rev + (kKara ? tc.z * a.seed_stride : 0) + ((ubase >> 5) - KW);
       bool stop = false;
       for (uint32_t e = (st + STAGES - base) % STAGES; e < nsteps; e += STAGES) {
         const uint32_t ph = use & 1u;
-        const uint32_t ks = e - 1;  // K step of the X rows (e >= 1)
+        const uint32_t c = kKara ? e / spb : 0u;  // K block
+        const uint32_t el = e - c * spb;          // step within it (0: the window left of the block)
+        const uint32_t E = c * a.ksteps + el;     // K step of the X rows + 1 (el >= 1)
         // the seed words depend on no barrier: issue all of them first
+        const uint32_t* win = seed_row + KW * E + (kKara ? a.seed_kshift * c : 0u);
         uint32_t sw[T_ROWS][KW + 1];
 #pragma unroll
         for (int j = 0; j < T_ROWS; ++j)
 #pragma unroll
-          for (int k = 0; k <= KW; ++k) sw[j][k] = __ldg(seed_row - j + KW * e + k);
+          for (int k = 0; k <= KW; ++k) sw[j][k] = __ldg(win - j + k);
         if (!mbar_wait(&pk_full_bar[st], ph, &abort_flag, a.err, 1)) { stop = true; break; }
         uint32_t xw[X_ROWS][KW];
-        if (e > 0) {
+        if (el > 0) {
+          const uint32_t ks = E - 1;
 #pragma unroll
           for (int j = 0; j < X_ROWS; ++j) {
             const uint32_t r = lane + 32u * j;
@@ -233,7 +281,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                              : "memory");
             }
           }
-          if (KW * ks + KW > a.nw_t - 1) {  // words past the Toeplitz part (zero-filled) and its partial last word
+          // words past the Toeplitz part (zero-filled) and its partial last word; the Karatsuba
+          // operands are zero past it already
+          if (!kKara && KW * ks + KW > a.nw_t - 1) {
 #pragma unroll
             for (int w = 0; w < KW; ++w)
               if (KW * ks + w == a.nw_t - 1) {
@@ -250,7 +300,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           for (int w = 0; w < KW; ++w)
             store_word_e2m1(sA + r * ROW_BYTES, r, w, __funnelshift_r(sw[j][w], sw[j][w + 1], sh));
         }
-        if (e > 0) {
+        if (el > 0) {
 #pragma unroll
           for (int j = 0; j < X_ROWS; ++j) {
             const uint32_t r = lane + 32u * j;
@@ -277,18 +327,22 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else if (warp == TMA_WARP) {
     // ------------------------------------------------------------------ TMA loads of packed raw tiles
-    // one load per step (step 0 loads the tile of K step 0 as well, unused), so that raw slot s and
-    // operand stage s advance together
+    // one load per step (the first step of a K block loads the block's first tile as well,
+    // unused), so that raw slot s and operand stage s advance together
     uint32_t pstage = 0, pphase = 0, issued = 0;
     if (lane == 0) {
       for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
-        const uint32_t nt = (uint32_t)(tile / a.mpairs);
+        const TileCoord tc = tile_coord<kKara>(a, tile);
+        const int row = (int)((kKara ? (uint64_t)tc.z * a.num_blocks : 0ull) + (uint64_t)tc.nt * PN + rank * HN);
         for (uint32_t e = 0; e < nsteps; ++e) {
+          const uint32_t c = kKara ? e / spb : 0u;
+          const uint32_t el = e - c * spb;
           if (!mbar_wait(&pk_empty_bar[pstage], pphase ^ 1u, &abort_flag, a.err, 3)) break;
           if (!a.fault_no_tma) {
             mbar_arrive_expect_tx(&pk_full_bar[pstage], PK_BYTES);
-            tma_load_2d(pk_base + pstage * PK_BYTES, &raw_map, (int)(KW * (e > 0 ? e - 1 : 0)),
-                        (int)(nt * PN + rank * HN), &pk_full_bar[pstage]);
+            tma_load_2d(pk_base + pstage * PK_BYTES, &raw_map,
+                        (int)((kKara ? c * a.xk_kwords : 0u) + KW * (el > 0 ? el - 1 : 0)), row,
+                        &pk_full_bar[pstage]);
             ++issued;
           }
           if (++pstage == PK_STAGES) { pstage = 0; pphase ^= 1u; }
@@ -315,15 +369,20 @@ __global__ void __launch_bounds__(THREADS, 1)
           if (!mbar_wait<true>(&full_bar[stage], phase, &abort_flag, a.err, 6)) { done = false; break; }
           tc_fence_after();
           if (lane == 0 && e > 0) {
-            const uint32_t sA = smem_base + stage * STAGE_BYTES;  // T(mt, e-1)
-            const uint32_t sB = sA + A_BYTES;                      // X(e-1)
-            const uint32_t sP = smem_base + prev * STAGE_BYTES;   // T(mt, e-2) = T(mt+1, e-1)
+            const uint32_t c = kKara ? e / spb : 0u;
+            const uint32_t el = e - c * spb;
+            if (el > 0) {  // else: the block's first step, which only builds T(mt, -1) of the block
+              const uint32_t E = c * a.ksteps + el;
+              const uint32_t sA = smem_base + stage * STAGE_BYTES;  // T(mt, ks)
+              const uint32_t sB = sA + A_BYTES;                      // X(ks)
+              const uint32_t sP = smem_base + prev * STAGE_BYTES;   // T(mt, ks-1) = T(mt+1, ks)
 #pragma unroll
-            for (int k = 0; k < ROW_BYTES / 32; ++k) {
-              const uint64_t bdesc = smem_desc_sw128(sB + 32 * k);
-              const uint32_t acc = (e > 1 || k > 0) ? 1u : 0u;
-              mma_pair(tmem_base, tmem_base, smem_desc_sw128(sA + 32 * k), bdesc, S::IDESC, acc);
-              mma_pair(tmem_base + D1_COL, tmem_base, smem_desc_sw128(sP + 32 * k), bdesc, S::IDESC, acc);
+              for (int k = 0; k < ROW_BYTES / 32; ++k) {
+                const uint64_t bdesc = smem_desc_sw128(sB + 32 * k);
+                const uint32_t acc = (E > 1 || k > 0) ? 1u : 0u;
+                mma_pair(tmem_base, tmem_base, smem_desc_sw128(sA + 32 * k), bdesc, S::IDESC, acc);
+                mma_pair(tmem_base + D1_COL, tmem_base, smem_desc_sw128(sP + 32 * k), bdesc, S::IDESC, acc);
+              }
             }
             commit_both(&empty_bar[prev]);  // the previous stage's T tile is not read again
             issued = true;
@@ -349,46 +408,76 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ------------------------------------------------------------------ epilogue
+    // warp EPI_WARP0 + 4 hs + q drains accumulator hs (D0 or D1) in TMEM lanes 32 q .. 32 q + 31:
+    // 16-column loads double-buffered against the parity ballots of the previous load (two loads
+    // make one output word per lane: lane c holds column c of the pair), and the accumulator handed
+    // back to the MMA issuer as soon as its last load has landed
     const uint32_t q = warp & 3u;  // TMEM lane quarter this warp may access
+    const uint32_t hs = (warp - EPI_WARP0) >> 2;
+    constexpr uint32_t NH = PN / 16;  // 16-column loads per accumulator (even)
     const uint32_t accum_empty_leader = mapa_shared(smem_u32(&accum_empty_bar), 0);
     uint32_t acc_phase = 0;
     for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
-      const uint32_t mt0 = 2u * (uint32_t)(tile % a.mpairs);
-      const uint32_t nt = (uint32_t)(tile / a.mpairs);
+      const TileCoord tc = tile_coord<kKara>(a, tile);
+      const uint32_t nt = tc.nt;
       if (!mbar_wait(&accum_full_bar, acc_phase, &abort_flag, a.err, 8)) break;
       tc_fence_after();
-      for (uint32_t h = 0; h < 2; ++h) {
-        const uint32_t ow = (mt0 + h) * (PM / 32) + rank * (HM / 32) + q;  // output word of every block
-        const uint32_t rem = (ow < a.mw) ? a.m - 32 * ow : 0u;
-        const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
-        for (uint32_t g = 0; g < PN / 32; ++g) {
-          uint32_t v[32];
-          tmem_load32(tmem_base + ((32u * q) << 16) + h * D1_COL + 32u * g, v);
-          uint32_t mine = 0;
+      const uint32_t ow = (tc.mt + hs) * (PM / 32) + rank * (HM / 32) + q;  // output word of every block
+      const uint32_t rem = (ow < a.mw) ? a.m - 32 * ow : 0u;
+      const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+      const uint32_t taddr = tmem_base + ((32u * q) << 16) + hs * D1_COL;
+      uint32_t mine = 0;
+      uint32_t* words = &epi_words[warp - EPI_WARP0][0][0];  // [word][lane]
+      auto ballots = [&](const uint32_t(&v)[16], uint32_t half) {
 #pragma unroll
-          for (int c = 0; c < 32; ++c) {
-            const uint32_t wrd = __ballot_sync(0xffffffffu, count_parity(v[c], 1.0f));
-            if (lane == (uint32_t)c) mine = wrd;
-          }
-          const uint64_t b = (uint64_t)nt * PN + 32u * g + lane;
-          if (ow < a.mw && b < a.num_blocks) {
-            mine &= omask;
-            if (a.modified) {
-              const uint64_t bit = (uint64_t)a.id_off + 32ull * ow;
-              const uint32_t* rr = a.raw + b * a.raw_stride;
-              const uint64_t rq = bit >> 5;
-              const uint32_t rs = (uint32_t)(bit & 31);
-              const uint32_t rlo = __ldg(rr + rq);
-              const uint32_t rhi = (rs && rq + 1 < a.raw_stride) ? __ldg(rr + rq + 1) : 0u;
-              mine ^= __funnelshift_r(rlo, rhi, rs) & omask;
-            }
-            a.out[b * a.out_stride + ow] = mine;
-          }
+        for (int c = 0; c < 16; ++c) {
+          const uint32_t wrd = __ballot_sync(0xffffffffu, count_parity(v[c], 1.0f));
+          if (lane == 16u * half + (uint32_t)c) mine = wrd;
         }
+      };
+      auto store = [&](uint32_t g, uint32_t word) {  // lane c: column 32 g + c of the tile
+        const uint64_t b = (uint64_t)nt * PN + 32u * g + lane;
+        if (kKara) {  // every row of a sub-product is kept: the combining pass selects and masks
+          if (b < a.num_blocks) a.qpar[((uint64_t)tc.z * a.num_blocks + b) * a.mwq + ow] = word;
+        } else if (ow < a.mw && b < a.num_blocks) {
+          uint32_t w = word & omask;
+          if (a.modified) {
+            const uint64_t bit = (uint64_t)a.id_off + 32ull * ow;
+            const uint32_t* rr = a.raw + b * a.raw_stride;
+            const uint64_t rq = bit >> 5;
+            const uint32_t rs = (uint32_t)(bit & 31);
+            const uint32_t rlo = __ldg(rr + rq);
+            const uint32_t rhi = (rs && rq + 1 < a.raw_stride) ? __ldg(rr + rq + 1) : 0u;
+            w ^= __funnelshift_r(rlo, rhi, rs) & omask;
+          }
+          a.out[b * a.out_stride + ow] = w;
+        }
+      };
+      auto release = [&]() {  // every TMEM load of this warp has completed
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(accum_empty_leader);
+      };
+      // the output words stay in registers until the accumulator is released, so that the
+      // release does not wait for global stores
+      uint32_t va[16], vb[16];
+      tmem_load16_async(taddr, va);
+      tmem_wait_ld(va);
+#pragma unroll 1
+      for (uint32_t k = 0; k < NH; k += 2) {  // loads k (in va, landed) and k + 1 form output word k / 2
+        tmem_load16_async(taddr + 16u * (k + 1), vb);
+        ballots(va, 0);
+        tmem_wait_ld(vb);
+        if (k + 2 < NH)
+          tmem_load16_async(taddr + 16u * (k + 2), va);
+        else
+          release();
+        ballots(vb, 1);
+        words[(k / 2) * 32 + lane] = mine;
+        if (k + 2 < NH) tmem_wait_ld(va);
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive_cluster(accum_empty_leader);
+#pragma unroll 1
+      for (uint32_t g = 0; g < NH / 2; ++g) store(g, words[g * 32 + lane]);
       acc_phase ^= 1u;
     }
   }
@@ -414,16 +503,11 @@ static size_t pair_smem_bytes() {
   return (size_t)STAGES * PairShape<kPN>::STAGE_BYTES + (size_t)PK_STAGES * PairShape<kPN>::PK_BYTES + 1024;
 }
 
-template <int kPN>
-static cudaError_t launch_pair(const PairArgs& a0, const DirectArgs& d, int num_sms, cudaStream_t s,
-                               uint32_t* kernels) {
-  using S = PairShape<kPN>;
-  PairArgs a = a0;
-  a.ntiles = (uint32_t)ceil_div(d.num_blocks, S::PN);
-
-  // Tensor map over the raw words: dim 0 = the Toeplitz part's words of a block (reads beyond it are
-  // zero-filled), dim 1 = blocks (rows past the last block are zero-filled); box 8 words x HN blocks,
-  // every x coordinate a multiple of 8 words (32 bytes).
+// Tensor map over 32-bit words: dim 0 = `words` words of a row (reads beyond them are zero-filled),
+// dim 1 = `rows` rows `stride_words` apart (rows past the last are zero-filled); box 8 words x
+// `box_rows` rows, every x coordinate a multiple of 8 words (32 bytes).
+static cudaError_t encode_words_map(CUtensorMap* map, const uint32_t* base, uint64_t words, uint64_t rows,
+                                    uint64_t stride_words, uint32_t box_rows) {
   static PFN_encodeTiled_pair encode = nullptr;
   if (!encode) {
     void* fn = nullptr;
@@ -433,21 +517,27 @@ static cudaError_t launch_pair(const PairArgs& a0, const DirectArgs& d, int num_
       return cudaErrorNotSupported;
     encode = reinterpret_cast<PFN_encodeTiled_pair>(fn);
   }
-  CUtensorMap map;
-  const cuuint64_t gdim[2] = {(cuuint64_t)d.nw_t, (cuuint64_t)d.num_blocks};
-  const cuuint64_t gstride[1] = {(cuuint64_t)d.raw_stride * 4};
-  const cuuint32_t box[2] = {(cuuint32_t)KW, (cuuint32_t)S::HN};
+  const cuuint64_t gdim[2] = {(cuuint64_t)words, (cuuint64_t)rows};
+  const cuuint64_t gstride[1] = {(cuuint64_t)stride_words * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)KW, (cuuint32_t)box_rows};
   const cuuint32_t estride[2] = {1, 1};
-  CUresult r = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(d.raw), gdim, gstride, box,
+  CUresult r = encode(map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 2, const_cast<uint32_t*>(base), gdim, gstride, box,
                       estride, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                       CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
 
+template <int kPN, bool kKara>
+static cudaError_t launch_pair(const PairArgs& a0, const CUtensorMap& map, int num_sms, cudaStream_t s,
+                               uint32_t* kernels) {
+  using S = PairShape<kPN>;
+  PairArgs a = a0;
+  a.ntiles = (uint32_t)ceil_div(a.num_blocks, S::PN);
   const size_t smem = pair_smem_bytes<kPN>();
   cudaError_t e =
-      cudaFuncSetAttribute(gemm_pair_kernel<kPN>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+      cudaFuncSetAttribute(gemm_pair_kernel<kPN, kKara>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  const uint64_t tiles = (uint64_t)a.mpairs * a.ntiles;
+  const uint64_t tiles = (uint64_t)a.mpairs * a.ntiles * (kKara ? a.groups : 1u);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
@@ -462,20 +552,30 @@ static cudaError_t launch_pair(const PairArgs& a0, const DirectArgs& d, int num_
   cfg.numAttrs = 1;
   // one cluster per co-resident pair of SMs: every tile loop stride then runs concurrently
   int clusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&clusters, gemm_pair_kernel<kPN>, &cfg);
+  e = cudaOccupancyMaxActiveClusters(&clusters, gemm_pair_kernel<kPN, kKara>, &cfg);
   if (e != cudaSuccess) return e;
   if (clusters < 1) return cudaErrorNotSupported;
   const uint64_t pairs = tiles < (uint64_t)clusters ? tiles : (uint64_t)clusters;
   cfg.gridDim = dim3((unsigned)(2 * pairs));
-  e = cudaLaunchKernelEx(&cfg, gemm_pair_kernel<kPN>, a, map);
+  e = cudaLaunchKernelEx(&cfg, gemm_pair_kernel<kPN, kKara>, a, map);
   if (e != cudaSuccess) return e;
   ++*kernels;
   return cudaGetLastError();
 }
 
-cudaError_t launch_gemm_pair(const DirectArgs& d, int* err, int fault, int num_sms, cudaStream_t s,
-                             uint32_t* kernels) {
-  if ((reinterpret_cast<uintptr_t>(d.raw) & 15) != 0 || (d.raw_stride % 4) != 0) return cudaErrorInvalidValue;
+// Tile width: block columns computed over whole rounds of tiles (one round = one tile per cluster
+// of the pairs that fit), the narrower tile's columns weighted by its measured cost per column
+// (more operand bytes per MAC: 1.07x on the 2^29-bit laser stream).
+static bool pair_prefers_192(uint64_t row_tiles, uint64_t num_blocks, int num_sms) {
+  const uint64_t rounds_cap = (uint64_t)(num_sms / 2 > 0 ? num_sms / 2 : 1);
+  auto cost = [&](uint64_t pn, double per_col) {
+    const uint64_t tiles = row_tiles * ceil_div(num_blocks, pn);
+    return (double)(ceil_div(tiles, rounds_cap) * pn) * per_col;
+  };
+  return cost(192, 1.07) < cost(224, 1.0);
+}
+
+static PairArgs pair_args_from(const DirectArgs& d, int* err, int fault) {
   PairArgs a{};
   a.raw = d.raw;
   a.raw_stride = d.raw_stride;
@@ -489,20 +589,57 @@ cudaError_t launch_gemm_pair(const DirectArgs& d, int* err, int fault, int num_s
   a.out = d.out;
   a.out_stride = d.out_stride;
   a.num_blocks = d.num_blocks;
-  a.mpairs = (uint32_t)ceil_div(ceil_div(d.m, PM), 2);
-  a.ksteps = (uint32_t)ceil_div((uint64_t)d.nw_t * 32, BK);
   a.err = err;
   a.fault_no_tma = (fault == QRNG_FAULT_GEMM_NO_TMA);
-  // tile width: block columns computed over whole rounds of tiles (one round = one tile per cluster
-  // of the pairs that fit), the narrower tile's columns weighted by its measured cost per column
-  // (more operand bytes per MAC: 1.07x on the 2^29-bit laser stream)
-  const uint64_t rounds_cap = (uint64_t)(num_sms / 2 > 0 ? num_sms / 2 : 1);
-  auto cost = [&](uint64_t pn, double per_col) {
-    const uint64_t tiles = (uint64_t)a.mpairs * ceil_div(d.num_blocks, pn);
-    return (double)(ceil_div(tiles, rounds_cap) * pn) * per_col;
-  };
-  if (cost(192, 1.07) < cost(224, 1.0)) return launch_pair<192>(a, d, num_sms, s, kernels);
-  return launch_pair<224>(a, d, num_sms, s, kernels);
+  a.seed_front = kSeedFrontWords;
+  a.kblocks = 1;
+  a.groups = 1;
+  return a;
+}
+
+cudaError_t launch_gemm_pair(const DirectArgs& d, int* err, int fault, int num_sms, cudaStream_t s,
+                             uint32_t* kernels) {
+  if ((reinterpret_cast<uintptr_t>(d.raw) & 15) != 0 || (d.raw_stride % 4) != 0) return cudaErrorInvalidValue;
+  PairArgs a = pair_args_from(d, err, fault);
+  a.mpairs = (uint32_t)ceil_div(ceil_div(d.m, PM), 2);
+  a.ksteps = (uint32_t)ceil_div((uint64_t)d.nw_t * 32, BK);
+  CUtensorMap map;
+  const bool narrow = pair_prefers_192(a.mpairs, d.num_blocks, num_sms);
+  cudaError_t e = encode_words_map(&map, d.raw, d.nw_t, d.num_blocks, d.raw_stride, narrow ? 96 : 112);
+  if (e != cudaSuccess) return e;
+  return narrow ? launch_pair<192, false>(a, map, num_sms, s, kernels)
+                : launch_pair<224, false>(a, map, num_sms, s, kernels);
+}
+
+cudaError_t launch_gemm_pair_kara(const DirectArgs& d, const PairKara& k, int* err, int fault, int num_sms,
+                                  cudaStream_t s, uint32_t* kernels) {
+  if ((reinterpret_cast<uintptr_t>(k.xk) & 15) != 0 || (k.xk_words % 8) != 0 || k.h % 512 != 0 ||
+      (k.h & (k.h - 1)) != 0 || k.mq % k.h != 0 || k.kq % k.h != 0 || k.span % k.h != 0)
+    return cudaErrorInvalidValue;
+  if ((uint64_t)k.groups * d.num_blocks >= (1ull << 31)) return cudaErrorInvalidValue;
+  PairArgs a = pair_args_from(d, err, fault);
+  a.seed_rev = k.seeds;
+  a.seed_front = k.seed_front;
+  a.mpairs = (uint32_t)(k.mq / (2 * PM));
+  a.ksteps = (uint32_t)(k.h / BK);
+  a.kblocks = (uint32_t)(k.kq / k.h);
+  a.seed_kshift = (uint32_t)((k.span - k.h) / 32);
+  a.xk_kwords = (uint32_t)(k.h / 32);
+  uint32_t lg = 0;
+  while ((1ull << lg) < k.h) ++lg;
+  a.log2h = lg;
+  a.row_shift = (uint32_t)(k.span - k.h);
+  a.groups = k.groups;
+  a.seed_stride = k.seed_stride;
+  a.qpar = k.qpar;
+  a.mwq = (uint32_t)(k.mq / 32);
+  CUtensorMap map;
+  const bool narrow = pair_prefers_192((uint64_t)a.mpairs * k.groups, d.num_blocks, num_sms);
+  cudaError_t e = encode_words_map(&map, k.xk, k.xk_words, (uint64_t)k.groups * d.num_blocks, k.xk_words,
+                                   narrow ? 96 : 112);
+  if (e != cudaSuccess) return e;
+  return narrow ? launch_pair<192, true>(a, map, num_sms, s, kernels)
+                : launch_pair<224, true>(a, map, num_sms, s, kernels);
 }
 
 }  // namespace qrng

@@ -1,0 +1,298 @@
+// Block Karatsuba over GF(2) for the block-batched Toeplitz product (Sec. III.B, III.E).
+//
+// The hash of every block is k = T x over GF(2) with T the m x n_t Toeplitz matrix of the shared
+// seed, T[i][j] = a[n_t - 1 + i - j]. Pad T with zero seed bits to M x K (multiples of
+// span = h << levels) and x with zero bits; cut T into h x h blocks: block (r, c) depends on
+// d = c - r alone (T_d, itself Toeplitz). A 2 x 2 group of blocks [[T_d, T_d+1], [T_d-1, T_d]]
+// times (x0, x1) needs three block products instead of four, because over GF(2)
+//     y0 = T_d x0 + T_d+1 x1 = T_d (x0 ^ x1) + (T_d+1 ^ T_d) x1     (A + B)
+//     y1 = T_d-1 x0 + T_d x1 = T_d (x0 ^ x1) + (T_d-1 ^ T_d) x0     (A + C).
+// The grid of A products (and of B, of C) is again block Toeplitz, with blocks of every other
+// diagonal, so the split repeats: after `levels` rounds there are 3^levels sub-products, each an
+// mq x kq product (mq = M / 2^levels, kq = K / 2^levels). In the reversed-seed form the kernels use
+// (rho(p) = a[L-1-p], zero outside [0, L)), T_d+1 ^ T_d is the Toeplitz matrix of
+// rho(p) ^ rho(p + s) and T_d-1 ^ T_d that of rho(p) ^ rho(p - s), s = h << (level - 1). Sub-product
+// z = (z_1 .. z_levels) in base 3 (0 = A, 1 = B, 2 = C, level 1 least significant) reads the XOR
+// of raw h-blocks 2^levels C + q over the q whose bit l-1 is 0 or 1 for A, 1 for B, 0 for C, and
+// output h-block 2^levels R + q is the XOR of the 2^levels sub-products whose digit l is A or (B if
+// bit l-1 of q is 0, else C). Parities add, so each sub-product is one exact integer product whose
+// parity is taken once; the combining pass XORs words.
+//
+// Work: 3^levels mq kq against m n_t multiply-adds per block (9/16 at two levels), for three
+// cheap memory-bound passes: the derived seeds (3^levels short bit strings), the derived raw
+// operands (3^levels x K/2^levels bits per block) and the combination (2^levels words read per
+// output word).
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cmath>
+
+#include "qrng_internal.h"
+
+namespace qrng {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr uint64_t kDefaultWorkspace = 1ull << 30;  // derived operands + sub-product parities per pass
+
+__host__ __device__ inline uint32_t pow3(uint32_t l) {
+  uint32_t r = 1;
+  for (uint32_t i = 0; i < l; ++i) r *= 3;
+  return r;
+}
+
+// Derived reversed seeds: word w of seed z holds bits p = 32 (w - front) .. +31 of
+// rho_z = XOR of rho shifted by the offsets that z's digits select.
+__global__ void kara_seed_kernel(const uint32_t* __restrict__ rev, uint64_t rev_words, uint32_t levels, uint32_t hw,
+                                 uint32_t front, uint64_t words, uint32_t* __restrict__ seeds, uint64_t stride) {
+  const uint32_t z = blockIdx.y;
+  int64_t offs[8];
+  uint32_t n = 1;
+  offs[0] = 0;
+  uint32_t zz = z;
+  for (uint32_t l = 0; l < levels; ++l) {
+    const uint32_t d = zz % 3;
+    zz /= 3;
+    const int64_t s = (int64_t)hw << l;
+    if (d != 0) {
+      for (uint32_t i = 0; i < n; ++i) offs[n + i] = offs[i] + (d == 1 ? s : -s);
+      n *= 2;
+    }
+  }
+  for (uint64_t w = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; w < words; w += (uint64_t)gridDim.x * blockDim.x) {
+    uint32_t v = 0;
+    for (uint32_t i = 0; i < n; ++i) {
+      const int64_t q = (int64_t)w - (int64_t)front + offs[i] + kSeedFrontWords;
+      if (q >= 0 && q < (int64_t)rev_words) v ^= __ldg(rev + q);
+    }
+    seeds[(uint64_t)z * stride + w] = v;
+  }
+}
+
+// Derived raw operands: thread (b, c, w) reads word w of raw h-blocks 2^L c + q (zero past the
+// Toeplitz part) and writes word c * hw + w of every sub-product's operand row z * nb + b.
+template <int L>
+__global__ void kara_split_kernel(const uint32_t* __restrict__ raw, uint64_t raw_stride, uint32_t nw_t,
+                                  uint32_t tail_mask, uint64_t nb, uint32_t hw, uint32_t kblocks, uint64_t xk_words,
+                                  uint32_t* __restrict__ xk) {
+  constexpr int Q = 1 << L;
+  constexpr int G = L == 1 ? 3 : L == 2 ? 9 : 27;
+  uint32_t take[G];  // bit q: raw h-block q of the group enters sub-product z
+#pragma unroll
+  for (int z = 0; z < G; ++z) {
+    uint32_t mask = 0;
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      bool in = true;
+      int zz = z;
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        const int d = zz % 3;
+        zz /= 3;
+        const int bit = (q >> l) & 1;
+        in = in && (d == 0 || (d == 1 && bit == 1) || (d == 2 && bit == 0));
+      }
+      if (in) mask |= 1u << q;
+    }
+    take[z] = mask;
+  }
+  const uint64_t total = nb * kblocks * hw;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t w = (uint32_t)(idx % hw);
+    const uint64_t t = idx / hw;
+    const uint32_t c = (uint32_t)(t % kblocks);
+    const uint64_t b = t / kblocks;
+    uint32_t src[Q];
+#pragma unroll
+    for (int q = 0; q < Q; ++q) {
+      const uint64_t i = ((uint64_t)c << L) * hw + (uint64_t)q * hw + w;
+      uint32_t v = i < nw_t ? __ldg(raw + b * raw_stride + i) : 0u;
+      if (i == (uint64_t)nw_t - 1) v &= tail_mask;
+      src[q] = v;
+    }
+#pragma unroll
+    for (int z = 0; z < G; ++z) {
+      uint32_t v = 0;
+#pragma unroll
+      for (int q = 0; q < Q; ++q)
+        if ((take[z] >> q) & 1u) v ^= src[q];
+      xk[((uint64_t)z * nb + b) * xk_words + (uint64_t)c * hw + w] = v;
+    }
+  }
+}
+
+// Output word ow of block b (rows 32 ow .. 32 ow + 31, inside one h-block r = (R << L) + q): the
+// XOR of the 2^L sub-product words of rows R h + (32 ow mod h); then the tail mask and, for the
+// modified form, the identity part x[n - m + i].
+template <int L>
+__global__ void kara_combine_kernel(const uint32_t* __restrict__ qpar, uint64_t mwq, uint32_t log2h, uint64_t nb,
+                                    uint32_t* __restrict__ out, uint64_t out_stride, uint32_t mw, uint32_t m,
+                                    int modified, uint32_t id_off, const uint32_t* __restrict__ raw,
+                                    uint64_t raw_stride) {
+  const uint64_t total = nb * mw;
+  const uint32_t hmask = (1u << log2h) - 1u;
+  for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
+       idx += (uint64_t)gridDim.x * blockDim.x) {
+    const uint32_t ow = (uint32_t)(idx % mw);
+    const uint64_t b = idx / mw;
+    const uint32_t v0 = 32u * ow;
+    const uint32_t r = v0 >> log2h;
+    const uint32_t R = r >> L, q = r & ((1u << L) - 1u);
+    const uint64_t row_word = ((uint64_t)R << (log2h - 5)) + ((v0 & hmask) >> 5);
+    uint32_t acc = 0;
+#pragma unroll
+    for (int t = 0; t < (1 << L); ++t) {
+      uint32_t z = 0, p3 = 1;
+#pragma unroll
+      for (int l = 0; l < L; ++l) {
+        if ((t >> l) & 1) z += (1u + ((q >> l) & 1u)) * p3;
+        p3 *= 3;
+      }
+      acc ^= __ldg(qpar + ((uint64_t)z * nb + b) * mwq + row_word);
+    }
+    const uint32_t rem = m - v0;
+    const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+    acc &= omask;
+    if (modified) {
+      const uint64_t bit = (uint64_t)id_off + v0;
+      const uint32_t* rr = raw + b * raw_stride;
+      const uint64_t rq = bit >> 5;
+      const uint32_t rs = (uint32_t)(bit & 31);
+      const uint32_t rlo = __ldg(rr + rq);
+      const uint32_t rhi = (rs && rq + 1 < raw_stride) ? __ldg(rr + rq + 1) : 0u;
+      acc ^= __funnelshift_r(rlo, rhi, rs) & omask;
+    }
+    out[b * out_stride + ow] = acc;
+  }
+}
+
+unsigned grid_for(uint64_t items, int num_sms) {
+  const uint64_t want = ceil_div(items, kThreads);
+  const uint64_t cap = (uint64_t)(num_sms > 0 ? num_sms : 1) * 16;
+  return (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
+}
+
+}  // namespace
+
+KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_sms, int forced_levels,
+                        uint64_t forced_h, uint64_t max_workspace) {
+  KaraPlan best;
+  if (n_t == 0 || m == 0 || num_blocks == 0 || n_t > kGemmMaxColumns) return best;
+  const uint64_t budget = max_workspace ? max_workspace : kDefaultWorkspace;
+  const double clusters = (double)(num_sms / 2 > 0 ? num_sms / 2 : 1);
+  for (uint32_t L = 1; L <= 3; ++L) {
+    if (forced_levels && (uint32_t)forced_levels != L) continue;
+    for (uint32_t lg = 9; lg <= 13; ++lg) {
+      const uint64_t h = 1ull << lg;
+      if (forced_h ? forced_h != h : lg > 12) continue;
+      const uint64_t span = h << L;
+      const uint32_t G = pow3(L);
+      const uint64_t mq = ceil_div(m, span) * h, kq = ceil_div(n_t, span) * h;
+      const uint64_t per_block = (uint64_t)G * (mq + kq) / 8;
+      uint64_t chunk = budget / per_block;
+      chunk = chunk >= 224 ? chunk / 224 * 224 : 224;
+      if (chunk > num_blocks) chunk = num_blocks;
+      while ((uint64_t)G * chunk >= (1ull << 31)) chunk /= 2;
+      if (chunk == 0) continue;
+      // pair tiles of 512 sub-product rows x 224 blocks over whole rounds of one tile per cluster;
+      // a tile takes kq/256 product steps (about 0.49 us each on GB300) plus one build-only step per
+      // K block (about a quarter of a step); the passes around it move their bytes at ~5 TB/s
+      const uint64_t passes = ceil_div(num_blocks, chunk);
+      const double tiles = (double)G * (double)(mq / 512) * std::ceil((double)chunk / 224.0);
+      const double steps = (double)(kq / 256) + 0.25 * (double)(kq / h);
+      const double kernel_s = (double)passes * std::ceil(tiles / clusters) * steps * 0.49e-6;
+      const double bytes =
+          (double)num_blocks * ((double)n_t / 8 + 2.0 * G * (double)kq / 8 + (double)G * mq / 8 +
+                                (double)(1u << L) * (double)m / 8 + (double)m / 8);
+      const double t = kernel_s + bytes / 5e12 + (double)passes * 2e-5;
+      if (best.levels == 0 || t < best.model_s) {
+        best.levels = L;
+        best.h = h;
+        best.span = span;
+        best.groups = G;
+        best.mq = mq;
+        best.kq = kq;
+        best.seed_front = (uint32_t)(span / 32 + 16);
+        best.seed_stride = best.seed_front + ceil_div(m + ceil_div(n_t, span) * span, 32) + 16;
+        best.chunk_blocks = chunk;
+        best.model_s = t;
+      }
+    }
+  }
+  return best;
+}
+
+cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWorkspace& ws, int* err, int fault,
+                                  int num_sms, cudaStream_t s, uint32_t* kernels, cudaEvent_t ev_start,
+                                  cudaEvent_t ev_end) {
+  if (p.levels < 1 || p.levels > 3) return cudaErrorInvalidValue;
+  const uint32_t G = p.groups;
+  const uint32_t hw = (uint32_t)(p.h / 32);
+  uint32_t log2h = 0;
+  while ((1ull << log2h) < p.h) ++log2h;
+  const uint64_t xk_words = p.kq / 32, mwq = p.mq / 32;
+  const uint64_t chunk = p.chunk_blocks < d.num_blocks ? p.chunk_blocks : d.num_blocks;
+  cudaError_t e = ws.seeds.ensure((size_t)G * p.seed_stride * 4);
+  if (e != cudaSuccess) return e;
+  if ((e = ws.xk.ensure((size_t)G * chunk * xk_words * 4)) != cudaSuccess) return e;
+  if ((e = ws.qpar.ensure((size_t)G * chunk * mwq * 4)) != cudaSuccess) return e;
+
+  const uint64_t L_t = d.n_t + d.m - 1;
+  const uint64_t rev_words = kSeedFrontWords + ceil_div(L_t, 32) + kSeedBackWords;
+  kara_seed_kernel<<<dim3((unsigned)ceil_div(p.seed_stride, kThreads), G), kThreads, 0, s>>>(
+      d.seed_rev, rev_words, p.levels, hw, p.seed_front, p.seed_stride, ws.seeds.as<uint32_t>(), p.seed_stride);
+  ++*kernels;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+
+  PairKara k{};
+  k.seeds = ws.seeds.as<uint32_t>();
+  k.seed_stride = p.seed_stride;
+  k.seed_front = p.seed_front;
+  k.xk = ws.xk.as<uint32_t>();
+  k.xk_words = xk_words;
+  k.qpar = ws.qpar.as<uint32_t>();
+  k.h = p.h;
+  k.span = p.span;
+  k.mq = p.mq;
+  k.kq = p.kq;
+  k.groups = G;
+  const uint32_t kblocks = (uint32_t)(p.kq / p.h);
+  for (uint64_t b0 = 0; b0 < d.num_blocks; b0 += chunk) {
+    const uint64_t nb = d.num_blocks - b0 < chunk ? d.num_blocks - b0 : chunk;
+    DirectArgs dc = d;
+    dc.raw = d.raw + b0 * d.raw_stride;
+    dc.out = d.out + b0 * d.out_stride;
+    dc.num_blocks = nb;
+    const unsigned gs = grid_for(nb * kblocks * hw, num_sms);
+    if (p.levels == 1)
+      kara_split_kernel<1><<<gs, kThreads, 0, s>>>(dc.raw, d.raw_stride, d.nw_t, d.tail_mask, nb, hw, kblocks,
+                                                   xk_words, ws.xk.as<uint32_t>());
+    else if (p.levels == 2)
+      kara_split_kernel<2><<<gs, kThreads, 0, s>>>(dc.raw, d.raw_stride, d.nw_t, d.tail_mask, nb, hw, kblocks,
+                                                   xk_words, ws.xk.as<uint32_t>());
+    else
+      kara_split_kernel<3><<<gs, kThreads, 0, s>>>(dc.raw, d.raw_stride, d.nw_t, d.tail_mask, nb, hw, kblocks,
+                                                   xk_words, ws.xk.as<uint32_t>());
+    ++*kernels;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (b0 == 0 && ev_start && (e = cudaEventRecord(ev_start, s)) != cudaSuccess) return e;
+    if ((e = launch_gemm_pair_kara(dc, k, err, fault, num_sms, s, kernels)) != cudaSuccess) return e;
+    if (b0 + nb >= d.num_blocks && ev_end && (e = cudaEventRecord(ev_end, s)) != cudaSuccess) return e;
+    const unsigned gc = grid_for(nb * d.mw, num_sms);
+    if (p.levels == 1)
+      kara_combine_kernel<1><<<gc, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, dc.out, d.out_stride, d.mw, d.m,
+                                                     d.modified, d.id_off, dc.raw, d.raw_stride);
+    else if (p.levels == 2)
+      kara_combine_kernel<2><<<gc, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, dc.out, d.out_stride, d.mw, d.m,
+                                                     d.modified, d.id_off, dc.raw, d.raw_stride);
+    else
+      kara_combine_kernel<3><<<gc, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, dc.out, d.out_stride, d.mw, d.m,
+                                                     d.modified, d.id_off, dc.raw, d.raw_stride);
+    ++*kernels;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace qrng

@@ -186,6 +186,55 @@ cudaError_t launch_gemm_tc(const DirectArgs& a, bool fp4, int* err, int fault, i
 // The FP4 product on SM pairs (k_gemm_pair.cu): clusters of two CTAs, cta_group::2 MMAs.
 cudaError_t launch_gemm_pair(const DirectArgs& a, int* err, int fault, int num_sms, cudaStream_t s, uint32_t* kernels);
 
+// ---- block Karatsuba over GF(2) on the SM-pair product (k_karatsuba.cu, k_gemm_pair.cu) ----
+// The zero-padded Toeplitz matrix, cut into h x h blocks, is block Toeplitz; `levels` rounds of the
+// 2x2 split [[T_d, T_d+1], [T_d-1, T_d]] (three products: T_d (x0^x1), (T_d+1 ^ T_d) x1,
+// (T_d-1 ^ T_d) x0) leave 3^levels sub-products of mq x kq, each a Toeplitz matrix of a derived
+// seed restricted to every span-th h-block (span = h << levels); output block r = (R << levels) + q
+// is the XOR of the 2^levels sub-products that level l's bit of q selects (A and, by that bit, B or C).
+struct KaraPlan {
+  uint32_t levels = 0;   // 0: no plan (the plain product)
+  uint64_t h = 0, span = 0;
+  uint32_t groups = 0;   // 3^levels
+  uint64_t mq = 0, kq = 0;          // rows and columns of every sub-product (multiples of h)
+  uint32_t seed_front = 0;          // front padding (words) of every derived seed
+  uint64_t seed_stride = 0;         // words per derived seed
+  uint64_t chunk_blocks = 0;        // blocks per pass (bounds the workspace)
+  double model_s = 0;               // modelled seconds for all blocks
+};
+// forced_levels / forced_h = 0 choose by the cost model; max_workspace = 0 takes 1 GiB for the
+// derived operands and sub-product parities of one pass. The plan is empty when nothing fits.
+KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_sms, int forced_levels,
+                        uint64_t forced_h, uint64_t max_workspace);
+struct KaraWorkspace {
+  DevBuf seeds, xk, qpar;
+  void release() {
+    seeds.release();
+    xk.release();
+    qpar.release();
+  }
+};
+// The pair kernel on the sub-products: derived seeds (seed_stride words each, front padding
+// seed_front), derived raw operands xk (row z * num_blocks + b, kq / 32 words), sub-product
+// parities into qpar (row z * num_blocks + b, mq / 32 words).
+struct PairKara {
+  const uint32_t* seeds;
+  uint64_t seed_stride;
+  uint32_t seed_front;
+  const uint32_t* xk;
+  uint64_t xk_words;
+  uint32_t* qpar;
+  uint64_t h, span, mq, kq;
+  uint32_t groups;
+};
+cudaError_t launch_gemm_pair_kara(const DirectArgs& a, const PairKara& k, int* err, int fault, int num_sms,
+                                  cudaStream_t s, uint32_t* kernels);
+// The whole Karatsuba extraction of a.num_blocks blocks (chunked by plan.chunk_blocks). ev_start /
+// ev_end (may be null) are recorded before the first and after the last product-kernel launch.
+cudaError_t launch_gemm_karatsuba(const DirectArgs& a, const KaraPlan& plan, KaraWorkspace& ws, int* err, int fault,
+                                  int num_sms, cudaStream_t s, uint32_t* kernels, cudaEvent_t ev_start = nullptr,
+                                  cudaEvent_t ev_end = nullptr);
+
 }  // namespace qrng
 
 struct qrng_ctx {
@@ -196,6 +245,10 @@ struct qrng_ctx {
   qrng::DevBuf dev_err;  // int error word written by kernels with bounded waits (0 = no error)
   qrng::DevBuf fft_worst;  // double bits of the worst FFT rounding distance since the last reset
   qrng::FftWorkspace fft;
+  qrng::KaraWorkspace kara;
+  int kara_levels = 0;       // 0 = chosen by the cost model
+  uint64_t kara_h = 0;
+  uint64_t kara_workspace = 0;  // 0 = the default budget
   // uneven-batch workspace and its captured graphs (see api.cu)
   qrng::DevBuf batch_meta, batch_raw, batch_rev, batch_out, batch_counter;
   uint64_t batch_generation = 0;  // bumped whenever a batch buffer moves (invalidates cached graphs)

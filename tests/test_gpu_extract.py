@@ -14,8 +14,9 @@ from gpu_util import extract, spot_check
 pytestmark = pytest.mark.gpu
 
 STD, MOD = 0, 1
-ALGOS = {"direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4, "ntt": 5, "gemm_fp4": 6, "gemm_fp4_pair": 7}
-GEMMS = {"gemm_tc": 2, "gemm_fp4": 6, "gemm_fp4_pair": 7}
+ALGOS = {"direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4, "ntt": 5, "gemm_fp4": 6, "gemm_fp4_pair": 7,
+         "gemm_karatsuba": 8}
+GEMMS = {"gemm_tc": 2, "gemm_fp4": 6, "gemm_fp4_pair": 7, "gemm_karatsuba": 8}
 
 
 def _seed_len(n, m, form):
@@ -280,7 +281,7 @@ def test_bad_arguments(qlib, gpu):
         (0, 0, STD, 1, 1),
         (64, 8, 7, 1, 1),      # unknown form
         (64, 8, STD, 9, 1),    # unknown algorithm
-        (64, 8, STD, 8, 1),    # unknown algorithm
+        (64, 8, STD, 10, 1),   # unknown algorithm
         (64, 8, STD, -1, 1),   # unknown algorithm
         (64, 8, STD, 1, 0),    # no blocks
         ((1 << 26) + 1, 8, STD, 1, 1),

@@ -13,7 +13,8 @@ from gpu_util import extract, to_dev
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("gemm", [2, 6, 7])  # QRNG_ALGO_GEMM_TC, QRNG_ALGO_GEMM_FP4, QRNG_ALGO_GEMM_FP4_PAIR
+# QRNG_ALGO_GEMM_TC, QRNG_ALGO_GEMM_FP4, QRNG_ALGO_GEMM_FP4_PAIR, QRNG_ALGO_GEMM_KARATSUBA
+@pytest.mark.parametrize("gemm", [2, 6, 7, 8])
 def test_timeout_reported_and_context_recovers(qlib, gpu, gemm):
     import torch
 

@@ -1,0 +1,105 @@
+"""GPU parity of the block-Karatsuba route (QRNG_ALGO_GEMM_KARATSUBA) against the oracle, for
+every split depth and block side the route accepts. The route reorganises the GF(2) product of
+Sec. III.B / III.D (2x2 Toeplitz blocks in three products, parities XOR-combined), so its output
+must equal the definition bit for bit. Shapes: ragged m and n (zero-padded rows and columns),
+several row blocks (the seed window moves by span - h per block), several block-column tiles
+(B > 224) and passes split by a small workspace budget."""
+import numpy as np
+import pytest
+
+import workloads as W
+from gpu_util import extract, spot_check
+
+pytestmark = pytest.mark.gpu
+
+STD, MOD = 0, 1
+KARA = 8  # QRNG_ALGO_GEMM_KARATSUBA
+
+
+def _case(n, m, form, B, s):
+    raw = W.random_bits(n * B, 4000 + s)
+    seed = W.random_bits(n + m - 1 if form == STD else n - 1, 5000 + s)
+    return raw, seed
+
+
+@pytest.fixture
+def kara(qlib, gpu):
+    yield lambda levels, h, ws=0: qlib.qrng_set_karatsuba(gpu, levels, h, ws)
+    qlib.qrng_set_karatsuba(gpu, 0, 0, 0)
+
+
+SPLITS = [(1, 512), (2, 512), (3, 512), (1, 1024), (2, 1024), (3, 1024), (1, 2048), (2, 2048), (1, 4096),
+          (1, 8192)]
+SHAPES = [(5000, 3100, STD, 3), (5000, 3100, MOD, 230), (9000, 5000, STD, 2), (4500, 1700, MOD, 5),
+          (3000, 2900, STD, 4), (2048, 1024, STD, 1), (700, 300, MOD, 3), (1, 1, STD, 2), (33, 17, MOD, 2)]
+
+
+@pytest.mark.parametrize("levels,h", SPLITS)
+@pytest.mark.parametrize("n,m,form,B", SHAPES)
+def test_forced_splits_bit_exact(qlib, gpu, oracle_mod, kara, levels, h, n, m, form, B):
+    kara(levels, h)
+    raw, seed = _case(n, m, form, B, n + 7 * m + B + levels)
+    want = oracle_mod.toeplitz_blocks(raw, n, m, seed, form, B)
+    got = extract(qlib, gpu, raw, n, m, seed, form, KARA, B)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("levels,h", [(2, 1024), (3, 512), (2, 512)])
+def test_laser_shape_several_blocks(qlib, gpu, oracle_mod, kara, levels, h):
+    """The laser-stream block shape (n = 2^16, m = 36,473): nine row blocks of 1024 at two levels,
+    sixteen K blocks; the sub-product sums reach 2^14 per accumulator."""
+    n, m, B = 1 << 16, 36473, 3
+    kara(levels, h)
+    raw, seed = _case(n, m, STD, B, 77 + levels)
+    want = oracle_mod.toeplitz_blocks(raw, n, m, seed, STD, B)
+    assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, STD, KARA, B), want)
+
+
+def test_chunked_passes(qlib, gpu, oracle_mod, kara):
+    """A workspace budget of one 224-block pass: 700 blocks run in four passes whose outputs land
+    at their blocks' places."""
+    n, m, B = 4096, 3000, 700
+    kara(2, 512, 1)  # below one block's need: the pass holds the minimum of 224 blocks
+    raw, seed = _case(n, m, MOD, B, 11)
+    want = oracle_mod.toeplitz_blocks(raw, n, m, seed, MOD, B)
+    assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, MOD, KARA, B), want)
+
+
+def test_many_blocks_match_direct(qlib, gpu, kara):
+    """Full occupancy: 76 clusters with several tiles each, repeated; equal to the direct kernel."""
+    n, m, B = 1 << 14, 12000, 224 * 9 + 5
+    raw, seed = _case(n, m, STD, B, 13)
+    ref = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_DIRECT, B)
+    for levels, h in ((2, 1024), (3, 512), (0, 0)):
+        kara(levels, h)
+        for _ in range(2):
+            assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, STD, KARA, B), ref)
+
+
+def test_all_ones_derived_operands(qlib, gpu, oracle_mod, kara):
+    """All-ones raw and seed: every derived operand of a B or C product and every XOR of two raw
+    blocks is zero inside the matrix, so the output is the parity of n on every row."""
+    n, m, B = 1 << 16, 20000, 4
+    raw = np.full(n * B // 8, 0xFF, dtype=np.uint8)
+    seed = W.pack_bits(np.ones(n + m - 1, dtype=np.uint8))
+    for levels, h in ((1, 512), (2, 1024), (3, 2048)):
+        kara(levels, h)
+        got = extract(qlib, gpu, raw, n, m, seed, STD, KARA, B)
+        assert np.array_equal(np.unpackbits(got, bitorder="little")[:m * B], np.zeros(m * B, np.uint8) + (n & 1))
+
+
+def test_long_blocks_spot_checked(qlib, gpu, oracle_mod, kara):
+    """n_t = 2^22 - 96 (the tensor-core limit, ragged), one row block."""
+    n, m, B = (1 << 22) - 96, 1000, 2
+    raw, seed = _case(n, m, STD, B, 17)
+    for levels, h in ((0, 0), (2, 512)):
+        kara(levels, h)
+        got = extract(qlib, gpu, raw, n, m, seed, STD, KARA, B)
+        spot_check(oracle_mod, raw, n, m, seed, STD, got, blocks=[0, B - 1], per_block=96)
+
+
+@pytest.mark.parametrize("levels,h", [(-1, 0), (4, 0), (1, 256), (1, 3000), (2, 16384)])
+def test_bad_settings_rejected(qlib, gpu, levels, h):
+    with pytest.raises(qlib.QrngError) as e:
+        qlib.qrng_set_karatsuba(gpu, levels, h, 0)
+    assert e.value.status == qlib.QRNG_EINVAL

@@ -257,13 +257,13 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t c = kKara ? e / spb : 0u;  // K block
         const uint32_t el = e - c * spb;          // step within it (0: the window left of the block)
         const uint32_t E = c * a.ksteps + el;     // K step of the X rows + 1 (el >= 1)
-        // the seed words depend on no barrier: issue all of them first
-        const uint32_t* win = seed_row + KW * E + (kKara ? a.seed_kshift * c : 0u);
-        uint32_t sw[T_ROWS][KW + 1];
+        // the seed words depend on no barrier: issue all of them first. Word k of row lane + 32 j is
+        // the funnel shift of seed words win + k - j and win + k - j + 1, so the lane's T_ROWS rows
+        // read KW + T_ROWS distinct words and share KW + T_ROWS - 1 shifted words.
+        const uint32_t* win = seed_row + KW * E + (kKara ? a.seed_kshift * c : 0u) - (T_ROWS - 1);
+        uint32_t sw[KW + T_ROWS];
 #pragma unroll
-        for (int j = 0; j < T_ROWS; ++j)
-#pragma unroll
-          for (int k = 0; k <= KW; ++k) sw[j][k] = __ldg(win - j + k);
+        for (int t = 0; t < KW + T_ROWS; ++t) sw[t] = __ldg(win + t);
         if (!mbar_wait(&pk_full_bar[st], ph, &abort_flag, a.err, 1)) { stop = true; break; }
         uint32_t xw[X_ROWS][KW];
         if (el > 0) {
@@ -294,11 +294,16 @@ __global__ void __launch_bounds__(THREADS, 1)
         }
         if (!mbar_wait(&empty_bar[st], ph ^ 1u, &abort_flag, a.err, 2)) { stop = true; break; }
 #pragma unroll
-        for (int j = 0; j < T_ROWS; ++j) {
-          const uint32_t r = lane + 32u * j;
+        for (int t = 0; t < KW + T_ROWS - 1; ++t) {  // shifted word t: word k = t - (T_ROWS - 1) + j of row j
+          const E2m1Chunk ch = e2m1_chunk(__funnelshift_r(sw[t], sw[t + 1], sh));
 #pragma unroll
-          for (int w = 0; w < KW; ++w)
-            store_word_e2m1(sA + r * ROW_BYTES, r, w, __funnelshift_r(sw[j][w], sw[j][w + 1], sh));
+          for (int j = 0; j < T_ROWS; ++j) {
+            const int k = t - (T_ROWS - 1) + j;
+            if (k >= 0 && k < KW) {
+              const uint32_t r = lane + 32u * j;
+              store_chunk_e2m1(sA + r * ROW_BYTES, r, (uint32_t)k, ch);
+            }
+          }
         }
         if (el > 0) {
 #pragma unroll
@@ -409,13 +414,15 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {
     // ------------------------------------------------------------------ epilogue
     // warp EPI_WARP0 + 4 hs + q drains accumulator hs (D0 or D1) in TMEM lanes 32 q .. 32 q + 31:
-    // 16-column loads double-buffered against the parity ballots of the previous load (two loads
-    // make one output word per lane: lane c holds column c of the pair), and the accumulator handed
-    // back to the MMA issuer as soon as its last load has landed
+    // 32-column loads double-buffered against the parity ballots of the previous load (lane c takes
+    // column c's ballot: one output word per lane and load), and the accumulator handed back to the
+    // MMA issuer as soon as its last load has landed; the output words wait in shared memory until
+    // then, so that the release does not wait for global stores
     const uint32_t q = warp & 3u;  // TMEM lane quarter this warp may access
     const uint32_t hs = (warp - EPI_WARP0) >> 2;
-    constexpr uint32_t NH = PN / 16;  // 16-column loads per accumulator (even)
+    constexpr uint32_t NW = PN / 32;  // 32-column loads (output words) per accumulator
     const uint32_t accum_empty_leader = mapa_shared(smem_u32(&accum_empty_bar), 0);
+    uint32_t* words = &epi_words[warp - EPI_WARP0][0][0];  // [word][lane]
     uint32_t acc_phase = 0;
     for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
       const TileCoord tc = tile_coord<kKara>(a, tile);
@@ -426,16 +433,52 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t rem = (ow < a.mw) ? a.m - 32 * ow : 0u;
       const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
       const uint32_t taddr = tmem_base + ((32u * q) << 16) + hs * D1_COL;
-      uint32_t mine = 0;
-      uint32_t* words = &epi_words[warp - EPI_WARP0][0][0];  // [word][lane]
-      auto ballots = [&](const uint32_t(&v)[16], uint32_t half) {
+      // lane r packs the parities of its row for the 32 columns (bit c = column c); a 32 x 32 bit
+      // transpose across the warp then leaves column c's 32 rows in lane c: stage j exchanges bit j
+      // of the row and column indices (one shuffle and a few logic operations per stage)
+      auto ballots = [&](const uint32_t(&v)[32], uint32_t g) {
+        uint32_t x = 0;
 #pragma unroll
-        for (int c = 0; c < 16; ++c) {
-          const uint32_t wrd = __ballot_sync(0xffffffffu, count_parity(v[c], 1.0f));
-          if (lane == 16u * half + (uint32_t)c) mine = wrd;
+        for (int c = 0; c < 32; ++c) x |= count_parity(v[c], 1.0f) << c;
+#pragma unroll
+        for (int l = 4; l >= 0; --l) {
+          const uint32_t j = 1u << l;
+          const uint32_t m = l == 4 ? 0x0000FFFFu : l == 3 ? 0x00FF00FFu : l == 2 ? 0x0F0F0F0Fu
+                             : l == 1 ? 0x33333333u : 0x55555555u;  // columns with bit l clear
+          const uint32_t t = __shfl_xor_sync(0xffffffffu, x, j);
+          x = (lane & j) ? ((x & ~m) | ((t >> j) & m)) : ((x & m) | ((t << j) & ~m));
         }
+        words[g * 32 + lane] = x;
       };
-      auto store = [&](uint32_t g, uint32_t word) {  // lane c: column 32 g + c of the tile
+      auto release = [&]() {  // every TMEM load of this warp has completed
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster(accum_empty_leader);
+      };
+      uint32_t va[32], vb[32];
+      tmem_load32_async(taddr, va);
+      tmem_wait_ld(va);
+#pragma unroll 1
+      for (uint32_t g = 0; g < NW; g += 2) {  // load g is in va and has landed
+        if (g + 1 < NW)
+          tmem_load32_async(taddr + 32u * (g + 1), vb);
+        else
+          release();
+        ballots(va, g);
+        if (g + 1 < NW) {
+          tmem_wait_ld(vb);
+          if (g + 2 < NW)
+            tmem_load32_async(taddr + 32u * (g + 2), va);
+          else
+            release();
+          ballots(vb, g + 1);
+          if (g + 2 < NW) tmem_wait_ld(va);
+        }
+      }
+      __syncwarp();
+#pragma unroll 1
+      for (uint32_t g = 0; g < NW; ++g) {  // lane c: column 32 g + c of the tile
+        const uint32_t word = words[g * 32 + lane];
         const uint64_t b = (uint64_t)nt * PN + 32u * g + lane;
         if (kKara) {  // every row of a sub-product is kept: the combining pass selects and masks
           if (b < a.num_blocks) a.qpar[((uint64_t)tc.z * a.num_blocks + b) * a.mwq + ow] = word;
@@ -452,32 +495,8 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           a.out[b * a.out_stride + ow] = w;
         }
-      };
-      auto release = [&]() {  // every TMEM load of this warp has completed
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive_cluster(accum_empty_leader);
-      };
-      // the output words stay in registers until the accumulator is released, so that the
-      // release does not wait for global stores
-      uint32_t va[16], vb[16];
-      tmem_load16_async(taddr, va);
-      tmem_wait_ld(va);
-#pragma unroll 1
-      for (uint32_t k = 0; k < NH; k += 2) {  // loads k (in va, landed) and k + 1 form output word k / 2
-        tmem_load16_async(taddr + 16u * (k + 1), vb);
-        ballots(va, 0);
-        tmem_wait_ld(vb);
-        if (k + 2 < NH)
-          tmem_load16_async(taddr + 16u * (k + 2), va);
-        else
-          release();
-        ballots(vb, 1);
-        words[(k / 2) * 32 + lane] = mine;
-        if (k + 2 < NH) tmem_wait_ld(va);
       }
-#pragma unroll 1
-      for (uint32_t g = 0; g < NH / 2; ++g) store(g, words[g * 32 + lane]);
+      __syncwarp();
       acc_phase ^= 1u;
     }
   }

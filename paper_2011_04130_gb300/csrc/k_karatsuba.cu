@@ -122,48 +122,59 @@ __global__ void kara_split_kernel(const uint32_t* __restrict__ raw, uint64_t raw
   }
 }
 
-// Output word ow of block b (rows 32 ow .. 32 ow + 31, inside one h-block r = (R << L) + q): the
-// XOR of the 2^L sub-product words of rows R h + (32 ow mod h); then the tail mask and, for the
-// modified form, the identity part x[n - m + i].
+// Output words of block b at row-word position (R, lw): for each q < 2^L, word
+// ow = ((R << L) + q) h/32 + lw (rows 32 ow .. 32 ow + 31, inside h-block (R << L) + q) is the XOR
+// of the 2^L sub-product words of rows R h + 32 lw that q selects. The thread loads the 3^L
+// sub-product words once and writes all 2^L outputs; then the tail mask and, for the modified
+// form, the identity part x[n - m + i].
 template <int L>
 __global__ void kara_combine_kernel(const uint32_t* __restrict__ qpar, uint64_t mwq, uint32_t log2h, uint64_t nb,
-                                    uint32_t* __restrict__ out, uint64_t out_stride, uint32_t mw, uint32_t m,
-                                    int modified, uint32_t id_off, const uint32_t* __restrict__ raw,
+                                    uint32_t rblocks, uint32_t* __restrict__ out, uint64_t out_stride, uint32_t mw,
+                                    uint32_t m, int modified, uint32_t id_off, const uint32_t* __restrict__ raw,
                                     uint64_t raw_stride) {
-  const uint64_t total = nb * mw;
-  const uint32_t hmask = (1u << log2h) - 1u;
+  constexpr int G = L == 1 ? 3 : L == 2 ? 9 : 27;
+  const uint32_t hw = 1u << (log2h - 5);
+  const uint64_t total = nb * rblocks * hw;
   for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
        idx += (uint64_t)gridDim.x * blockDim.x) {
-    const uint32_t ow = (uint32_t)(idx % mw);
-    const uint64_t b = idx / mw;
-    const uint32_t v0 = 32u * ow;
-    const uint32_t r = v0 >> log2h;
-    const uint32_t R = r >> L, q = r & ((1u << L) - 1u);
-    const uint64_t row_word = ((uint64_t)R << (log2h - 5)) + ((v0 & hmask) >> 5);
-    uint32_t acc = 0;
+    const uint32_t lw = (uint32_t)(idx % hw);
+    const uint64_t t = idx / hw;
+    const uint32_t R = (uint32_t)(t % rblocks);
+    const uint64_t b = t / rblocks;
+    const uint64_t row_word = (uint64_t)R * hw + lw;
+    uint32_t qz[G];
 #pragma unroll
-    for (int t = 0; t < (1 << L); ++t) {
-      uint32_t z = 0, p3 = 1;
+    for (int z = 0; z < G; ++z) qz[z] = __ldg(qpar + ((uint64_t)z * nb + b) * mwq + row_word);
+    const uint32_t* rr = raw + b * raw_stride;
 #pragma unroll
-      for (int l = 0; l < L; ++l) {
-        if ((t >> l) & 1) z += (1u + ((q >> l) & 1u)) * p3;
-        p3 *= 3;
+    for (int q = 0; q < (1 << L); ++q) {
+      const uint32_t ow = (((R << L) + (uint32_t)q) << (log2h - 5)) + lw;
+      if (ow >= mw) break;  // ow grows with q
+      uint32_t acc = 0;
+#pragma unroll
+      for (int s = 0; s < (1 << L); ++s) {  // subset s of the levels whose digit is B or C
+        int z = 0, p3 = 1;
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+          if ((s >> l) & 1) z += (1 + ((q >> l) & 1)) * p3;
+          p3 *= 3;
+        }
+        acc ^= qz[z];
       }
-      acc ^= __ldg(qpar + ((uint64_t)z * nb + b) * mwq + row_word);
+      const uint32_t v0 = 32u * ow;
+      const uint32_t rem = m - v0;
+      const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+      acc &= omask;
+      if (modified) {
+        const uint64_t bit = (uint64_t)id_off + v0;
+        const uint64_t rq = bit >> 5;
+        const uint32_t rs = (uint32_t)(bit & 31);
+        const uint32_t rlo = __ldg(rr + rq);
+        const uint32_t rhi = (rs && rq + 1 < raw_stride) ? __ldg(rr + rq + 1) : 0u;
+        acc ^= __funnelshift_r(rlo, rhi, rs) & omask;
+      }
+      out[b * out_stride + ow] = acc;
     }
-    const uint32_t rem = m - v0;
-    const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
-    acc &= omask;
-    if (modified) {
-      const uint64_t bit = (uint64_t)id_off + v0;
-      const uint32_t* rr = raw + b * raw_stride;
-      const uint64_t rq = bit >> 5;
-      const uint32_t rs = (uint32_t)(bit & 31);
-      const uint32_t rlo = __ldg(rr + rq);
-      const uint32_t rhi = (rs && rq + 1 < raw_stride) ? __ldg(rr + rq + 1) : 0u;
-      acc ^= __funnelshift_r(rlo, rhi, rs) & omask;
-    }
-    out[b * out_stride + ow] = acc;
   }
 }
 
@@ -279,15 +290,16 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
     if (b0 == 0 && ev_start && (e = cudaEventRecord(ev_start, s)) != cudaSuccess) return e;
     if ((e = launch_gemm_pair_kara(dc, k, err, fault, num_sms, s, kernels)) != cudaSuccess) return e;
     if (b0 + nb >= d.num_blocks && ev_end && (e = cudaEventRecord(ev_end, s)) != cudaSuccess) return e;
-    const unsigned gc = grid_for(nb * d.mw, num_sms);
+    const uint32_t rblocks = (uint32_t)ceil_div(d.m, p.span);
+    const unsigned gc = grid_for(nb * rblocks * hw, num_sms);
     if (p.levels == 1)
-      kara_combine_kernel<1><<<gc, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, dc.out, d.out_stride, d.mw, d.m,
+      kara_combine_kernel<1><<<gc, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, rblocks, dc.out, d.out_stride, d.mw, d.m,
                                                      d.modified, d.id_off, dc.raw, d.raw_stride);
     else if (p.levels == 2)
-      kara_combine_kernel<2><<<gc, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, dc.out, d.out_stride, d.mw, d.m,
+      kara_combine_kernel<2><<<gc, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, rblocks, dc.out, d.out_stride, d.mw, d.m,
                                                      d.modified, d.id_off, dc.raw, d.raw_stride);
     else
-      kara_combine_kernel<3><<<gc, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, dc.out, d.out_stride, d.mw, d.m,
+      kara_combine_kernel<3><<<gc, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, rblocks, dc.out, d.out_stride, d.mw, d.m,
                                                      d.modified, d.id_off, dc.raw, d.raw_stride);
     ++*kernels;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -183,6 +183,20 @@ __device__ __forceinline__ void store_word_e2m1(uint32_t row_addr, uint32_t row,
                : "memory");
 }
 
+// The same chunk computed once (e2m1_chunk) and stored to several rows (store_chunk_e2m1).
+struct E2m1Chunk {
+  uint32_t a, b, c, d;
+};
+__device__ __forceinline__ E2m1Chunk e2m1_chunk(uint32_t x) {
+  constexpr uint32_t kMask = kOneE2M1 * 0x11111111u;
+  return E2m1Chunk{(x << 1) & kMask, x & kMask, (x >> 1) & kMask, (x >> 2) & kMask};
+}
+__device__ __forceinline__ void store_chunk_e2m1(uint32_t row_addr, uint32_t row, uint32_t w, const E2m1Chunk& c) {
+  const uint32_t addr = row_addr + (((w ^ (row & 7u)) & 7u) << 4);
+  asm volatile("st.shared.v4.b32 [%0], {%1, %2, %3, %4};" ::"r"(addr), "r"(c.a), "r"(c.b), "r"(c.c), "r"(c.d)
+               : "memory");
+}
+
 // Parity of the integer count held (scaled by `scale`) in an FP32 accumulator: adding 1.5 * 2^23
 // leaves the count, < 2^22, in the low mantissa bits.
 __device__ __forceinline__ uint32_t count_parity(uint32_t acc_bits, float scale) {

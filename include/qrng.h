@@ -323,7 +323,9 @@ QRNG_API int qrng_set_autotune(qrng_ctx* ctx, int on);
 
 /* Block Karatsuba settings of QRNG_ALGO_GEMM_KARATSUBA (0 = chosen by the cost model, the default):
  *   levels          rounds of the 2x2 block split, 1..3;
- *   block_bits      h, the side of the square Toeplitz blocks: 512, 1024, 2048, 4096 or 8192;
+ *   block_bits      h, the side of the square Toeplitz blocks: 256, 512, 1024, 2048, 4096 or 8192
+ *                   (256 lets the two output tiles of a pair tile share T tiles across blocks: no
+ *                   extra operand build per block);
  *   max_workspace   device bytes for the derived operands and sub-product parities of one pass
  *                   (the blocks are processed in passes that fit it; 0 = 1 GiB).
  * Returns QRNG_EINVAL for values outside those sets. Forgets the shapes autotuned so far. */

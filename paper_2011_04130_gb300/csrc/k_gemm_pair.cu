@@ -131,6 +131,7 @@ struct PairArgs {
   // each K block of h columns starts with a step that builds only the T tile left of it, and each
   // K block / row block shifts the seed window by span - h bits.
   uint32_t seed_front;   // front padding (words) of every seed buffer
+  uint32_t seed_kstep;   // seed words per K step: KW, or span / 32 when every K step is one h-block
   uint32_t kblocks;      // K blocks of h columns (plain: 1)
   uint32_t seed_kshift;  // (span - h) / 32: seed words skipped per K block
   uint32_t xk_kwords;    // h / 32: raw-operand words per K block
@@ -250,7 +251,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const int64_t vshift = kKara ? (int64_t)(r0 >> a.log2h) * a.row_shift : 0;
       const int64_t ubase = (int64_t)a.m - 1 - ((int64_t)r0 + rank * HM + lane) - vshift + 32 * (int64_t)a.seed_front;
       const uint32_t sh = (uint32_t)(ubase & 31);
-      const uint32_t* seed_row = a.seed_rev + (kKara ? tc.z * a.seed_stride : 0) + ((ubase >> 5) - KW);
+      const uint32_t* seed_row = a.seed_rev + (kKara ? tc.z * a.seed_stride : 0) + (ubase >> 5);
       bool stop = false;
       for (uint32_t e = (st + STAGES - base) % STAGES; e < nsteps; e += STAGES) {
         const uint32_t ph = use & 1u;
@@ -260,7 +261,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         // the seed words depend on no barrier: issue all of them first. Word k of row lane + 32 j is
         // the funnel shift of seed words win + k - j and win + k - j + 1, so the lane's T_ROWS rows
         // read KW + T_ROWS distinct words and share KW + T_ROWS - 1 shifted words.
-        const uint32_t* win = seed_row + KW * E + (kKara ? a.seed_kshift * c : 0u) - (T_ROWS - 1);
+        const uint32_t* win =
+            seed_row + (int64_t)a.seed_kstep * ((int64_t)E - 1) + (kKara ? a.seed_kshift * c : 0u) - (T_ROWS - 1);
         uint32_t sw[KW + T_ROWS];
 #pragma unroll
         for (int t = 0; t < KW + T_ROWS; ++t) sw[t] = __ldg(win + t);
@@ -611,6 +613,7 @@ static PairArgs pair_args_from(const DirectArgs& d, int* err, int fault) {
   a.err = err;
   a.fault_no_tma = (fault == QRNG_FAULT_GEMM_NO_TMA);
   a.seed_front = kSeedFrontWords;
+  a.seed_kstep = KW;
   a.kblocks = 1;
   a.groups = 1;
   return a;
@@ -632,17 +635,27 @@ cudaError_t launch_gemm_pair(const DirectArgs& d, int* err, int fault, int num_s
 
 cudaError_t launch_gemm_pair_kara(const DirectArgs& d, const PairKara& k, int* err, int fault, int num_sms,
                                   cudaStream_t s, uint32_t* kernels) {
-  if ((reinterpret_cast<uintptr_t>(k.xk) & 15) != 0 || (k.xk_words % 8) != 0 || k.h % 512 != 0 ||
-      (k.h & (k.h - 1)) != 0 || k.mq % k.h != 0 || k.kq % k.h != 0 || k.span % k.h != 0)
+  if ((reinterpret_cast<uintptr_t>(k.xk) & 15) != 0 || (k.xk_words % 8) != 0 || k.h < 256 ||
+      (k.h & (k.h - 1)) != 0 || k.mq % 512 != 0 || k.mq % k.h != 0 || k.kq % k.h != 0 || k.span % k.h != 0)
     return cudaErrorInvalidValue;
   if ((uint64_t)k.groups * d.num_blocks >= (1ull << 31)) return cudaErrorInvalidValue;
   PairArgs a = pair_args_from(d, err, fault);
   a.seed_rev = k.seeds;
   a.seed_front = k.seed_front;
   a.mpairs = (uint32_t)(k.mq / (2 * PM));
-  a.ksteps = (uint32_t)(k.h / BK);
-  a.kblocks = (uint32_t)(k.kq / k.h);
-  a.seed_kshift = (uint32_t)((k.span - k.h) / 32);
+  if (k.h == BK) {
+    // every tile row block and every K step is a whole h-block: block (R+1, c) = block (R, c-1), so
+    // the two output tiles share T tiles along the block diagonal like the plain product, one K
+    // sequence with the seed window moving span bits per step
+    a.ksteps = (uint32_t)(k.kq / BK);
+    a.kblocks = 1;
+    a.seed_kshift = 0;
+    a.seed_kstep = (uint32_t)(k.span / 32);
+  } else {
+    a.ksteps = (uint32_t)(k.h / BK);
+    a.kblocks = (uint32_t)(k.kq / k.h);
+    a.seed_kshift = (uint32_t)((k.span - k.h) / 32);
+  }
   a.xk_kwords = (uint32_t)(k.h / 32);
   uint32_t lg = 0;
   while ((1ull << lg) < k.h) ++lg;

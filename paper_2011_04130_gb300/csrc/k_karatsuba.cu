@@ -194,12 +194,14 @@ KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_s
   const double clusters = (double)(num_sms / 2 > 0 ? num_sms / 2 : 1);
   for (uint32_t L = 1; L <= 3; ++L) {
     if (forced_levels && (uint32_t)forced_levels != L) continue;
-    for (uint32_t lg = 9; lg <= 13; ++lg) {
+    for (uint32_t lg = 8; lg <= 13; ++lg) {
       const uint64_t h = 1ull << lg;
       if (forced_h ? forced_h != h : lg > 12) continue;
       const uint64_t span = h << L;
       const uint32_t G = pow3(L);
-      const uint64_t mq = ceil_div(m, span) * h, kq = ceil_div(n_t, span) * h;
+      // h = 256: pair tiles take two row blocks, so their number is rounded up to even
+      const uint64_t rblocks = h == 256 ? ceil_div(m, 2 * span) * 2 : ceil_div(m, span);
+      const uint64_t mq = rblocks * h, kq = ceil_div(n_t, span) * h;
       const uint64_t per_block = (uint64_t)G * (mq + kq) / 8;
       uint64_t chunk = budget / per_block;
       chunk = chunk >= 224 ? chunk / 224 * 224 : 224;
@@ -208,10 +210,11 @@ KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_s
       if (chunk == 0) continue;
       // pair tiles of 512 sub-product rows x 224 blocks over whole rounds of one tile per cluster;
       // a tile takes kq/256 product steps (about 0.49 us each on GB300) plus one build-only step per
-      // K block (about a quarter of a step); the passes around it move their bytes at ~5 TB/s
+      // K block (about half a step; one per tile when h = 256) and its accumulator hand-back (about
+      // five steps); the passes around it move their bytes at ~5 TB/s
       const uint64_t passes = ceil_div(num_blocks, chunk);
       const double tiles = (double)G * (double)(mq / 512) * std::ceil((double)chunk / 224.0);
-      const double steps = (double)(kq / 256) + 0.25 * (double)(kq / h);
+      const double steps = (double)(kq / 256) + 0.5 * (double)(h == 256 ? 1 : kq / h) + 5.0;
       const double kernel_s = (double)passes * std::ceil(tiles / clusters) * steps * 0.49e-6;
       const double bytes =
           (double)num_blocks * ((double)n_t / 8 + 2.0 * G * (double)kq / 8 + (double)G * mq / 8 +
@@ -224,7 +227,7 @@ KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_s
         best.groups = G;
         best.mq = mq;
         best.kq = kq;
-        best.seed_front = (uint32_t)(span / 32 + 16);
+        best.seed_front = (uint32_t)(2 * span / 32 + 16);
         best.seed_stride = best.seed_front + ceil_div(m + ceil_div(n_t, span) * span, 32) + 16;
         best.chunk_blocks = chunk;
         best.model_s = t;

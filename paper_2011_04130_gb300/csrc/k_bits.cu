@@ -75,18 +75,22 @@ __global__ void pack_blocks_kernel(const uint32_t* __restrict__ src, uint64_t st
   uint32_t v = 0;
   uint64_t g = 32 * D;
   const uint64_t gend = (32 * D + 32 < total) ? 32 * D + 32 : total;
+  // the block of bit g: a 32-bit division when every index fits (the common case), else 64-bit
+  uint64_t b = total < (1ull << 32) ? (uint64_t)((uint32_t)g / (uint32_t)m) : g / m;
+  uint64_t i = g - b * m;
   while (g < gend) {
-    uint64_t b = g / m, i = g - b * m;
     uint32_t take = (uint32_t)((m - i) < (gend - g) ? (m - i) : (gend - g));  // bits from this block
     const uint32_t* row = src + b * stride_w;
     uint64_t q = i >> 5;
     uint32_t sh = (uint32_t)(i & 31);
-    uint32_t lo = row[q];
-    uint32_t hi = (sh && q + 1 < stride_w) ? row[q + 1] : 0u;
+    uint32_t lo = __ldg(row + q);
+    uint32_t hi = (sh && q + 1 < stride_w) ? __ldg(row + q + 1) : 0u;
     uint32_t bits = __funnelshift_r(lo, hi, sh);
     if (take < 32) bits &= (1u << take) - 1u;
     v |= bits << (uint32_t)(g - 32 * D);
     g += take;
+    ++b;  // the next bits, if any, start the next block
+    i = 0;
   }
   const uint64_t nbytes = (total + 7) >> 3;
   uint8_t* p = dst + 4 * D;

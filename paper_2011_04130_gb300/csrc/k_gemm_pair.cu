@@ -555,9 +555,18 @@ static cudaError_t launch_pair(const PairArgs& a0, const CUtensorMap& map, int n
   PairArgs a = a0;
   a.ntiles = (uint32_t)ceil_div(a.num_blocks, S::PN);
   const size_t smem = pair_smem_bytes<kPN>();
-  cudaError_t e =
-      cudaFuncSetAttribute(gemm_pair_kernel<kPN, kKara>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  // the shared-memory attribute and the number of co-resident clusters are set and queried once
+  // per device (they do not change), so that the launch adds no driver round trips to a call
+  constexpr int kMaxDev = 64;
+  static int clusters_of[kMaxDev] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
+  const bool cached = dev >= 0 && dev < kMaxDev && clusters_of[dev] > 0;
+  if (!cached) {
+    e = cudaFuncSetAttribute(gemm_pair_kernel<kPN, kKara>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
   const uint64_t tiles = (uint64_t)a.mpairs * a.ntiles * (kKara ? a.groups : 1u);
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
@@ -572,10 +581,14 @@ static cudaError_t launch_pair(const PairArgs& a0, const CUtensorMap& map, int n
   cfg.attrs = attr;
   cfg.numAttrs = 1;
   // one cluster per co-resident pair of SMs: every tile loop stride then runs concurrently
-  int clusters = 0;
-  e = cudaOccupancyMaxActiveClusters(&clusters, gemm_pair_kernel<kPN, kKara>, &cfg);
-  if (e != cudaSuccess) return e;
-  if (clusters < 1) return cudaErrorNotSupported;
+  int clusters = cached ? clusters_of[dev] : 0;
+  if (!cached) {
+    cfg.gridDim = dim3((unsigned)(num_sms / 2 > 0 ? 2 * (num_sms / 2) : 2));
+    e = cudaOccupancyMaxActiveClusters(&clusters, gemm_pair_kernel<kPN, kKara>, &cfg);
+    if (e != cudaSuccess) return e;
+    if (clusters < 1) return cudaErrorNotSupported;
+    if (dev >= 0 && dev < kMaxDev) clusters_of[dev] = clusters;
+  }
   const uint64_t pairs = tiles < (uint64_t)clusters ? tiles : (uint64_t)clusters;
   cfg.gridDim = dim3((unsigned)(2 * pairs));
   e = cudaLaunchKernelEx(&cfg, gemm_pair_kernel<kPN, kKara>, a, map);

@@ -104,3 +104,25 @@ def test_bad_settings_rejected(qlib, gpu, levels, h):
     with pytest.raises(qlib.QrngError) as e:
         qlib.qrng_set_karatsuba(gpu, levels, h, 0)
     assert e.value.status == qlib.QRNG_EINVAL
+
+
+def test_plan_query(qlib, gpu, kara):
+    """qrng_karatsuba_plan reports the shape the route runs: 3^L sub-products whose sides are the
+    h-blocks of every span-th position of the padded matrix (an even number of row blocks when
+    h = 256), and the forced settings when they are set."""
+    n, m, B = 1 << 16, 36473, 8192
+    p = qlib.qrng_karatsuba_plan(gpu, n, m, STD, B)
+    L, h = p["levels"], p["h"]
+    span = h << L
+    assert 1 <= L <= 3 and p["groups"] == 3 ** L
+    rblocks = -(-m // span)
+    if h == 256:
+        rblocks += rblocks & 1
+    assert p["mq"] == rblocks * h and p["kq"] == -(-n // span) * h
+    assert p["blocks_per_pass"] == B and p["model_s"] > 0
+    kara(2, 1024)
+    p = qlib.qrng_karatsuba_plan(gpu, n, m, MOD, B)
+    assert (p["levels"], p["h"], p["groups"], p["mq"], p["kq"]) == (2, 1024, 9, 9 * 1024, 8 * 1024)
+    with pytest.raises(qlib.QrngError) as e:
+        qlib.qrng_karatsuba_plan(gpu, 64, 65, STD, 1)
+    assert e.value.status == qlib.QRNG_EINVAL

@@ -255,7 +255,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool stop = false;
       for (uint32_t e = (st + STAGES - base) % STAGES; e < nsteps; e += STAGES) {
         const uint32_t ph = use & 1u;
-        const uint32_t c = kKara ? e / spb : 0u;  // K block
+        const uint32_t c = (kKara && a.kblocks > 1) ? e / spb : 0u;  // K block
         const uint32_t el = e - c * spb;          // step within it (0: the window left of the block)
         const uint32_t E = c * a.ksteps + el;     // K step of the X rows + 1 (el >= 1)
         // the seed words depend on no barrier: issue all of them first. Word k of row lane + 32 j is
@@ -342,7 +342,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const TileCoord tc = tile_coord<kKara>(a, tile);
         const int row = (int)((kKara ? (uint64_t)tc.z * a.num_blocks : 0ull) + (uint64_t)tc.nt * PN + rank * HN);
         for (uint32_t e = 0; e < nsteps; ++e) {
-          const uint32_t c = kKara ? e / spb : 0u;
+          const uint32_t c = (kKara && a.kblocks > 1) ? e / spb : 0u;
           const uint32_t el = e - c * spb;
           if (!mbar_wait(&pk_empty_bar[pstage], pphase ^ 1u, &abort_flag, a.err, 3)) break;
           if (!a.fault_no_tma) {
@@ -365,54 +365,53 @@ __global__ void __launch_bounds__(THREADS, 1)
     __syncwarp();
   } else if (warp == MMA_WARP) {
     // ------------------------------------------------------------------ MMA issuer (leader CTA)
-    if (rank == 0) {
+    // One thread runs the whole issue loop: the tensor pipe's queue is shallow, so every
+    // instruction between two steps' MMAs can leave it idle (no warp-wide waits, no per-step
+    // warp synchronisation, descriptors as per-stage bases plus 2 k).
+    if (rank == 0 && lane == 0) {
       uint32_t stage = 0, phase = 0, acc_phase = 0, prev = 0;
       bool issued = false;
       for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
         // both epilogues must have drained the previous tile's accumulators
         if (tile != first_tile && !mbar_wait<true>(&accum_empty_bar, acc_phase ^ 1u, &abort_flag, a.err, 5)) break;
         bool done = true;
+        uint32_t c = 0, el = 0;  // K block and step within it (0: the build-only step)
         for (uint32_t e = 0; e < nsteps; ++e) {
           if (!mbar_wait<true>(&full_bar[stage], phase, &abort_flag, a.err, 6)) { done = false; break; }
           tc_fence_after();
-          if (lane == 0 && e > 0) {
-            const uint32_t c = kKara ? e / spb : 0u;
-            const uint32_t el = e - c * spb;
-            if (el > 0) {  // else: the block's first step, which only builds T(mt, -1) of the block
+          if (e > 0) {
+            if (el > 0) {
               const uint32_t E = c * a.ksteps + el;
               const uint32_t sA = smem_base + stage * STAGE_BYTES;  // T(mt, ks)
-              const uint32_t sB = sA + A_BYTES;                      // X(ks)
-              const uint32_t sP = smem_base + prev * STAGE_BYTES;   // T(mt, ks-1) = T(mt+1, ks)
+              const uint64_t dA = kDescSw128Hi | (uint64_t)((sA & 0x3FFFFu) >> 4);
+              const uint64_t dB = kDescSw128Hi | (uint64_t)(((sA + A_BYTES) & 0x3FFFFu) >> 4);  // X(ks)
+              const uint64_t dP = kDescSw128Hi | (uint64_t)(((smem_base + prev * STAGE_BYTES) & 0x3FFFFu) >> 4);
 #pragma unroll
-              for (int k = 0; k < ROW_BYTES / 32; ++k) {
-                const uint64_t bdesc = smem_desc_sw128(sB + 32 * k);
+              for (int k = 0; k < ROW_BYTES / 32; ++k) {  // 32 bytes = 2 descriptor units per K chunk
                 const uint32_t acc = (E > 1 || k > 0) ? 1u : 0u;
-                mma_pair(tmem_base, tmem_base, smem_desc_sw128(sA + 32 * k), bdesc, S::IDESC, acc);
-                mma_pair(tmem_base + D1_COL, tmem_base, smem_desc_sw128(sP + 32 * k), bdesc, S::IDESC, acc);
+                mma_pair(tmem_base, tmem_base, dA + 2 * k, dB + 2 * k, S::IDESC, acc);
+                mma_pair(tmem_base + D1_COL, tmem_base, dP + 2 * k, dB + 2 * k, S::IDESC, acc);  // T(mt+1, ks)
               }
             }
             commit_both(&empty_bar[prev]);  // the previous stage's T tile is not read again
             issued = true;
           }
-          __syncwarp();
           prev = stage;
           if (++stage == STAGES) { stage = 0; phase ^= 1u; }
+          if (++el == spb) { el = 0; ++c; }  // the next step's place in its K block
         }
         if (!done || abort_flag) break;
-        if (lane == 0) {
-          commit_both(&empty_bar[prev]);  // the tile's last stage
-          commit_both(&accum_full_bar);
-        }
-        __syncwarp();
+        commit_both(&empty_bar[prev]);  // the tile's last stage
+        commit_both(&accum_full_bar);
         acc_phase ^= 1u;
       }
       // every MMA must finish before either CTA releases its tensor or shared memory
-      if (lane == 0 && issued) {
+      if (issued) {
         commit_local(&drain_bar);
         mbar_drain(&drain_bar, 0, a.err, 7);
       }
-      __syncwarp();
     }
+    __syncwarp();
   } else {
     // ------------------------------------------------------------------ epilogue
     // warp EPI_WARP0 + 4 hs + q drains accumulator hs (D0 or D1) in TMEM lanes 32 q .. 32 q + 31:

@@ -87,15 +87,14 @@ __device__ __forceinline__ void fence_proxy_async_smem() {
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 
-// K-major, SWIZZLE_128B shared-memory matrix descriptor (rows of 128 bytes, 8-row atoms 1024 B apart).
+// K-major, SWIZZLE_128B shared-memory matrix descriptor (rows of 128 bytes, 8-row atoms 1024 B apart):
+// every field but the start address (bits 0-13, address >> 4)
+constexpr uint64_t kDescSw128Hi = ((uint64_t)(16u >> 4) << 16)     // leading byte offset (unused for swizzled K-major)
+                                  | ((uint64_t)(1024u >> 4) << 32)  // stride byte offset: next 8-row atom
+                                  | ((uint64_t)1 << 46)             // descriptor version
+                                  | ((uint64_t)2 << 61);            // SWIZZLE_128B
 __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)(16u >> 4) << 16;    // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024u >> 4) << 32;  // stride byte offset: next 8-row atom
-  d |= (uint64_t)1 << 46;             // descriptor version
-  d |= (uint64_t)2 << 61;             // SWIZZLE_128B
-  return d;
+  return kDescSw128Hi | (uint64_t)((addr & 0x3FFFFu) >> 4);
 }
 
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint64_t* bar) {

@@ -268,7 +268,7 @@ double model_seconds(const qrng_ctx* ctx, int algo, uint64_t n_t, uint64_t m, ui
     }
     case QRNG_ALGO_GEMM_FP4_PAIR: {
       const double mp = (double)ceil_div(m, 256) * 256, bp = (double)ceil_div(B, 256) * 256;
-      return mp * (double)n_t * bp / 3.5e15 + 1e-5;
+      return mp * (double)n_t * bp / 4.5e15 + 1e-5;
     }
     case QRNG_ALGO_GEMM_KARATSUBA: {
       const KaraPlan p = karatsuba_plan(n_t, m, B, ctx->num_sms, ctx->kara_levels, ctx->kara_h, ctx->kara_workspace);

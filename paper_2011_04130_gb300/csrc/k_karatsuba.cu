@@ -209,13 +209,13 @@ KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_s
       while ((uint64_t)G * chunk >= (1ull << 31)) chunk /= 2;
       if (chunk == 0) continue;
       // pair tiles of 512 sub-product rows x 224 blocks over whole rounds of one tile per cluster;
-      // a tile takes kq/256 product steps (about 0.49 us each on GB300) plus one build-only step per
-      // K block (about half a step; one per tile when h = 256) and its accumulator hand-back (about
-      // five steps); the passes around it move their bytes at ~5 TB/s
+      // a tile takes kq/256 product steps (0.46 us each on GB300) plus one build-only step per K
+      // block (about half a step; one per tile when h = 256) and its accumulator hand-back (about
+      // six steps); the passes around it move their bytes at ~5 TB/s
       const uint64_t passes = ceil_div(num_blocks, chunk);
       const double tiles = (double)G * (double)(mq / 512) * std::ceil((double)chunk / 224.0);
-      const double steps = (double)(kq / 256) + 0.5 * (double)(h == 256 ? 1 : kq / h) + 5.0;
-      const double kernel_s = (double)passes * std::ceil(tiles / clusters) * steps * 0.49e-6;
+      const double steps = (double)(kq / 256) + 0.5 * (double)(h == 256 ? 1 : kq / h) + 6.0;
+      const double kernel_s = (double)passes * std::ceil(tiles / clusters) * steps * 0.46e-6;
       const double bytes =
           (double)num_blocks * ((double)n_t / 8 + 2.0 * G * (double)kq / 8 + (double)G * mq / 8 +
                                 (double)(1u << L) * (double)m / 8 + (double)m / 8);

@@ -1,0 +1,48 @@
+"""The bench's roofline arithmetic on CPU: algorithmic work from the plan and the live kernel time,
+the peak from the measured peaks, and the captured DRAM traffic only while the kernel's source
+still matches the capture."""
+import hashlib
+import json
+import os
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_karatsuba_roofline_counts_the_sub_products():
+    import bench
+
+    plan = {"levels": 3, "h": 256, "groups": 27, "mq": 4608, "kq": 8192}
+    n, m, B, ms = 1 << 16, 36473, 8192, 2.0
+    r = bench.roofline_for("gemm_karatsuba", B, m, n, ms, plan)
+    flops = 2.0 * B * 27 * 4608 * 8192
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - flops / (ms / 1e3) / 1e12) < 1e-6 * r["achieved"]
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    assert abs(r["peak"] - 6.0 * bench.measured_peaks()["bf16_tflops"]) < 1e-9
+    # the plain product the route replaces, reported beside it
+    assert abs(r["equivalent_plain_tflops"] - 2.0 * B * m * n / (ms / 1e3) / 1e12) < 1e-6 * r["achieved"]
+
+
+def test_traffic_record_tracks_the_kernel_source():
+    import bench
+
+    with open(os.path.join(ROOT, "profiles", "ncu_traffic.json")) as f:
+        rec = json.load(f)["gemm_pair_kara_kernel"]
+    with open(os.path.join(ROOT, "paper_2011_04130_gb300", "csrc", "k_gemm_pair.cu"), "rb") as f:
+        current = hashlib.sha256(f.read()).hexdigest()
+    got = bench.captured_traffic("gemm_pair_kara_kernel", "k_gemm_pair.cu", rec["blocks"])
+    if rec["source_sha256"] == current:
+        assert got == rec["dram_bytes"]
+    else:
+        assert got is None  # a stale capture is never reported
+    # scaled by the blocks of the launch
+    if got is not None:
+        assert bench.captured_traffic("gemm_pair_kara_kernel", "k_gemm_pair.cu", rec["blocks"] // 2) == \
+            rec["dram_bytes"] // 2
+
+
+def test_unknown_route_has_no_roofline():
+    import bench
+
+    r = bench.roofline_for("fft64", 10, 10, 10, 1.0)
+    assert r["bound"] is None and r["frac"] is None

@@ -8,6 +8,10 @@ Expected values come from closed forms and special cases, not from the oracle's 
   * reflection and shift invariance of the Gaussian model (catches a half-cell offset or a tail
     put in the wrong end code);
   * the histogram equals numpy's bincount;
+  * the distance over U = {argmax P'} (Sec. II.C) on a histogram whose empirical peak is not the
+    model's peak, and the lowest-code rule for equal peaks;
+  * the finite-size term: multinomial draws from a known distribution stay within it at least
+    a 1 - eps fraction of the time, and it is where Weissman's L1 tail bound reaches eps;
   * the worked example of Sec. II.B (loose pin, values in tests/golden/).
 """
 import json
@@ -105,6 +109,72 @@ def test_one_bit_source_closed_form(oracle_mod, h0, h1):
     assert abs(rep["h_modify"] - max(0.0, rep["h_model"] - dhm)) < TOL
     if h0 == h1:
         assert abs(rep["h_model"] - 1.0) < TOL and rep["d_u"] < TOL
+
+
+def _model_cell(hist, code):
+    """Mass of code `code` under the Gaussian with the histogram's mean and population variance
+    (exact integer moments), the cell [code - 1/2, code + 1/2] (scipy's normal CDF)."""
+    from scipy.stats import norm
+
+    hh = [int(x) for x in hist]
+    N = sum(hh)
+    s1 = sum(v * c for v, c in enumerate(hh))
+    s2 = sum(v * v * c for v, c in enumerate(hh))
+    mu = s1 / N
+    sigma = math.sqrt((N * s2 - s1 * s1) / (N * N))
+    return float(norm.cdf((code + 0.5 - mu) / sigma) - norm.cdf((code - 0.5 - mu) / sigma))
+
+
+def test_peak_distance_closed_form(oracle_mod):
+    """Sec. II.C restricted to U = {argmax P'}: d = |P'(x*) - P(x*)| / 2 at the empirical peak x*.
+    Here the measured peak (code 2, 40 %) is not the model's (the mean is 2.95, so code 3), so a
+    distance taken at the model's peak, or without the 1/2, differs."""
+    h = np.zeros(8, dtype=np.uint64)
+    h[2], h[3], h[4] = 40, 25, 35
+    rep = oracle_mod.minentropy_from_hist(h, 3, 1e-6)
+    assert rep["argmax"] == 2 and rep["max_count"] == 40
+    assert abs(rep["mean"] - 2.95) < TOL
+    p2, p3 = _model_cell(h, 2), _model_cell(h, 3)
+    assert p3 > p2  # the model's own peak sits elsewhere
+    assert abs(rep["h_model"] - (-math.log2(p3))) < TOL
+    assert abs(rep["d_u_peak"] - 0.5 * abs(0.40 - p2)) < TOL
+
+
+def test_argmax_lowest_code_on_ties(oracle_mod):
+    """Two codes share the largest count: H_min does not depend on which is reported, and the
+    report takes the lower code, so d over U = {argmax P'} is taken there."""
+    h = np.zeros(8, dtype=np.uint64)
+    h[1], h[2], h[3], h[5] = 30, 15, 30, 25
+    rep = oracle_mod.minentropy_from_hist(h, 3, 1e-6)
+    assert rep["argmax"] == 1 and rep["max_count"] == 30
+    assert abs(rep["h_emp"] - (-math.log2(0.30))) < TOL
+    p1, p3 = _model_cell(h, 1), _model_cell(h, 3)
+    assert abs(p1 - p3) > 1e-3  # an asymmetric histogram: the two ties have different model cells
+    assert abs(rep["d_u_peak"] - 0.5 * abs(0.30 - p1)) < TOL
+
+
+@pytest.mark.parametrize("bits,N,eps", [(4, 400, 0.05), (3, 2000, 0.1)])
+def test_finite_size_term_covers_multinomial_deviation(oracle_mod, bits, N, eps):
+    """The finite-size term is read as a confidence bound on the statistical distance between
+    the empirical distribution of N samples and the true one. Drawn N samples at a time from a
+    known distribution, the distance exceeds it in at most an eps fraction of the draws; and it is
+    the deviation at which Weissman et al.'s tail bound P(||p^ - p||_1 >= t) <= (2^K - 2)
+    exp(-N t^2 / 2) (K codes, t = twice the statistical distance) comes down to eps, up to
+    replacing 2^K - 2 by 2^K."""
+    K = 1 << bits
+    g = np.random.Generator(np.random.PCG64(17 + bits))
+    p = g.uniform(0.5, 1.5, K)
+    p /= p.sum()
+    draws = g.multinomial(N, p, size=6000)
+    tv = 0.5 * np.abs(draws / N - p).sum(axis=1)
+    h = np.zeros(K, dtype=np.uint64)
+    h[0] = N  # delta depends on N, K and eps only
+    delta = oracle_mod.minentropy_from_hist(h, bits, eps)["delta_fs"]
+    assert np.mean(tv > delta) <= eps
+    assert np.mean(tv > 0.5 * delta) > eps  # and it is not vacuous by a factor of two
+    tail = (2.0 ** K - 2) * math.exp(-N * (2 * delta) ** 2 / 2)
+    assert tail <= eps * (1 + 1e-12)
+    assert tail >= eps * (2.0 ** K - 2) / 2.0 ** K * (1 - 1e-12)
 
 
 @pytest.mark.parametrize("seed", [1, 2, 3])

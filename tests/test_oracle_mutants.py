@@ -34,6 +34,14 @@ MUTANTS = {
     "correction_wrong_power": ("ldexp(1.0, -bits - 1)", "ldexp(1.0, -bits)"),
     "finite_size_term_dropped": ("rep->delta_hm = log2((rep->d_u + rep->delta_fs)",
                                  "rep->delta_hm = log2((rep->d_u)"),
+    "peak_distance_at_model_peak": ("rep->d_u_peak = 0.5 * fabs((double)maxc / (double)N - P[argmax]);",
+                                    "rep->d_u_peak = 0.5 * fabs((double)maxc / (double)N - pmax);"),
+    "peak_distance_missing_half": ("rep->d_u_peak = 0.5 * fabs(", "rep->d_u_peak = 1.0 * fabs("),
+    "argmax_highest_code_on_ties": ("if (hist[v] > maxc) { maxc = hist[v];", "if (hist[v] >= maxc) { maxc = hist[v];"),
+    "finite_size_without_code_count": ("2.0 * ((double)K * log(2.0) + log(1.0 / eps))", "2.0 * (log(1.0 / eps))"),
+    "finite_size_without_confidence": ("2.0 * ((double)K * log(2.0) + log(1.0 / eps))", "2.0 * ((double)K * log(2.0))"),
+    "finite_size_bits_for_codes": ("2.0 * ((double)K * log(2.0) + log(1.0 / eps))",
+                                   "2.0 * ((double)bits * log(2.0) + log(1.0 / eps))"),
     # entropy-side extensions
     "quantum_variance_added": ("double var_q = rep->var - off.var;", "double var_q = rep->var + off.var;"),
     "subsample_wrong_bits": (">> 11) >= thr) continue;", ">> 10) >= thr) continue;"),
@@ -50,6 +58,9 @@ PINS = [
     (E.test_one_bit_source_closed_form, dict(h0=123456, h1=654321)),
     (E.test_reflection_invariance, dict(seed=2)),
     (E.test_flat_histogram_has_bits_of_entropy, dict(bits=8)),
+    (E.test_peak_distance_closed_form, dict()),
+    (E.test_argmax_lowest_code_on_ties, dict()),
+    (E.test_finite_size_term_covers_multinomial_deviation, dict(bits=4, N=400, eps=0.05)),
     (X.test_splitmix64_published_outputs, dict()),
     (X.test_quantum_model_closed_form, dict()),
     (X.test_subsample_is_binomial_and_matches_selection, dict(fraction=0.5, seed=1)),

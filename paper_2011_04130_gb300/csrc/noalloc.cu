@@ -14,8 +14,12 @@
 //     exits, whether or not this entry point is used;
 //   - all calls on a device share the same arrays: calls whose work overlaps on the GPU (for
 //     example on two streams at once) race and give wrong reports; serialise them;
-//   - the first call on each device resolves the arrays' device addresses (no allocation); make
-//     that first call before any stream capture is started on that device.
+//   - the first call on each device resolves the arrays' device addresses. With CUDA's lazy
+//     module loading (the default), that first use is also when the driver loads this library's
+//     device code and places its arrays in device memory, so make the first call during set-up,
+//     before streaming starts and before any stream capture on that device (or run with
+//     CUDA_MODULE_LOADING=EAGER, which places them when the context is created). Later calls
+//     allocate nothing.
 #include <cuda_runtime.h>
 #include <stdint.h>
 

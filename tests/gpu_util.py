@@ -45,3 +45,42 @@ def spot_check(oracle, raw, n, m, seed, form, out, blocks, per_block=256, rng_se
         got = bits[b * m + idx.astype(np.int64)]
         bad = np.nonzero(got != want)[0]
         assert bad.size == 0, f"block {b}: {bad.size} of {idx.size} sampled bits differ (first at k_{idx[bad[0]]})"
+
+
+def host_threads() -> int:
+    import os
+
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def check_every_block(oracle, raw, n, m, seed, form, out, num_blocks, per_block=8, rng_seed=0, out_bit0=0,
+                      raw_bit0=0, threads=None):
+    """Exact oracle values of `per_block` output bits of EVERY block (the first and the last bit
+    and random ones), each computed on its own in O(n), spread over the host's cores (the oracle
+    is plain C called through ctypes, which releases the interpreter lock). Returns the number of
+    bits checked; raises AssertionError naming the first block that differs."""
+    import concurrent.futures
+
+    g = W.rng(rng_seed)
+    idx_all = g.integers(0, m, size=(num_blocks, max(0, per_block - 2)), dtype=np.int64)
+    bits = np.unpackbits(out, bitorder="little")
+
+    def run(b0, b1):
+        for b in range(b0, b1):
+            idx = np.unique(np.concatenate([[0, m - 1], idx_all[b]])).astype(np.uint64)
+            want = oracle.toeplitz_bits(raw, n, m, seed, form, idx, raw_off=raw_bit0 + b * n)
+            got = bits[out_bit0 + b * m + idx.astype(np.int64)]
+            bad = np.nonzero(got != want)[0]
+            if bad.size:
+                return b, int(idx[bad[0]]), bad.size
+        return None
+
+    t = threads or host_threads()
+    step = max(1, -(-num_blocks // (4 * t)))
+    with concurrent.futures.ThreadPoolExecutor(max_workers=t) as ex:
+        for r in ex.map(lambda b0: run(b0, min(num_blocks, b0 + step)), range(0, num_blocks, step)):
+            assert r is None, f"block {r[0]}: {r[2]} sampled bits differ (first at k_{r[1]})"
+    return num_blocks * per_block

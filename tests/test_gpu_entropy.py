@@ -71,6 +71,24 @@ def test_point_mass_and_flat(qlib, gpu, oracle_mod):
     assert abs(got["h_emp"] - 8.0) < TOL
 
 
+@pytest.mark.parametrize("counts", [
+    {1: 30, 2: 15, 3: 30, 5: 25},     # two codes share the largest count: the lower one is reported
+    {2: 40, 3: 25, 4: 35},            # the measured peak (code 2) is not the model's (code 3)
+    {0: 7, 1: 7},                     # 1-bit tie
+])
+@pytest.mark.parametrize("scale", [1, 1000, 100_003])
+def test_ties_and_peak_distance(qlib, gpu, oracle_mod, counts, scale):
+    """argmax (lowest code on ties) and the distance over U = {argmax P'}, with the samples in a
+    random order and the counts large enough to spread over many CTAs."""
+    bits = 1 if max(counts) < 2 else 3
+    s = np.concatenate([np.full(c * scale, v, dtype=np.uint8) for v, c in counts.items()])
+    W.rng(scale).shuffle(s)
+    got = _run(qlib, gpu, s, bits, 1e-6)
+    want = oracle_mod.minentropy(s, bits, 1e-6)
+    _compare(got, want)
+    assert got["argmax"] == min(v for v, c in counts.items() if c == max(counts.values()))
+
+
 def test_out_of_range_sample_rejected(qlib, gpu):
     s = W.adc_samples(1000, 5, mu=8.0, sigma=3.0, bits=4)
     s[123] = 200

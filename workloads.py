@@ -106,3 +106,24 @@ def uneven_requests(count: int, seed: int, log2n_lo: float = 12, log2n_hi: float
     m = np.clip(np.floor(rho * n).astype(np.int64), 1, n - 1)
     p = g.uniform(p_lo, p_hi, count)
     return n, m, p
+
+
+def uneven_batch(c: dict = CFG5, log2n_hi: float | None = None):
+    """Host data of the uneven batch: request shapes from `uneven_requests`, every request's raw
+    bits Bernoulli(p_r) at a 32-bit aligned offset of one stream, its own uniform seed of n+m-1
+    bits at a byte offset of one seed buffer, and its m output bits back to back in one output
+    stream. Returns a dict of the shapes (n, m, p), the offsets (raw_off and out_off in bits,
+    seed_off in bytes) and the packed raw and seed buffers."""
+    n, m, p = uneven_requests(c["requests"], c["seed"], c["log2n_lo"], c["log2n_hi"] if log2n_hi is None else log2n_hi,
+                              c["rho_lo"], c["rho_hi"], c["p_lo"], c["p_hi"])
+    raw_off = np.concatenate([[0], np.cumsum(((n + 31) // 32) * 32)[:-1]]).astype(np.int64)
+    raw = np.zeros(int(raw_off[-1] + n[-1] + 64 + 7) // 8, dtype=np.uint8)
+    for i in range(n.size):
+        bits = random_bits(int(n[i]), 10_000 + i, float(p[i]))
+        raw[raw_off[i] // 8:raw_off[i] // 8 + bits.size] = bits
+    seed_len = (n + m - 1 + 7) // 8
+    seed_off = np.concatenate([[0], np.cumsum(seed_len)[:-1]]).astype(np.int64)
+    seeds = rng(c["seed"] + 7).integers(0, 256, int(seed_off[-1] + seed_len[-1]), dtype=np.uint8)
+    out_off = np.concatenate([[0], np.cumsum(m)[:-1]]).astype(np.int64)
+    return dict(n=n, m=m, p=p, raw_off=raw_off, seed_off=seed_off, seed_len=seed_len, out_off=out_off, raw=raw,
+                seeds=seeds, out_bits=int(out_off[-1] + m[-1]))

@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -29,12 +30,42 @@ import workloads as W  # noqa: E402
 METRIC = "extracted random Gbit/s on 1 GB300 (bit-exact), batched form vs plain per-block"
 UNIT = "Gbit/s"
 L2_FLUSH_BYTES = 256 << 20
-# integer-pipe peak of the direct kernel: 64 LOP3/clk/SM (measured on GB300), 32 bit-products per
-# LOP3, 152 SMs, 2070 MHz maximum SM clock
+# Integer-pipe rate of the direct kernel's LOP3: 64 results per clock per SM (the 32-bit bitwise
+# throughput of the CUDA arithmetic-instruction table; a LOP3 throughput loop on this GB300 gave
+# 1.888e13 LOP3/s at 1.99 GHz on 152 SMs = 62.4 per clock per SM), 32 bit-products per LOP3.
 LOP3_PER_CLK_SM = 64
-SMS = 152
-SM_MAX_MHZ = 2070.0
-ALU_PEAK_TBITMAC = LOP3_PER_CLK_SM * 32 * SMS * SM_MAX_MHZ * 1e6 / 1e12
+FP32_FMA_PER_CLK_SM = 128
+FP64_TFLOPS_NOMINAL = 1.25  # GB300 FP64 (non-tensor) nominal
+
+
+def device_caps(dev=0):
+    """SM count of the device (read at run time) and the maximum SM clock (MEASURED_PEAKS.json,
+    else GB300's 2070 MHz)."""
+    import torch
+
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz = 2070.0
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            mhz = float(json.load(f).get("sm_max_mhz", mhz))
+    except (OSError, ValueError):
+        pass
+    return {"sms": sms, "sm_max_mhz": mhz}
+
+
+def alu_peak_tbitmac(caps):
+    return LOP3_PER_CLK_SM * 32 * caps["sms"] * caps["sm_max_mhz"] * 1e6 / 1e12
+
+
+def fp32_peak_tflops(caps):
+    return 2 * FP32_FMA_PER_CLK_SM * caps["sms"] * caps["sm_max_mhz"] * 1e6 / 1e12
+
+
+def host_cores() -> int:
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
 
 
 def parse():
@@ -48,8 +79,10 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--blocks", type=int, default=0,
                    help="hash only the first BLOCKS blocks (a smaller case for profiler captures)")
+    p.add_argument("--headline-only", action="store_true",
+                   help="skip the per-configuration sub-records after the headline measurement")
     p.add_argument("--workload", default="laser",
-                   choices=["laser", "single", "sweep", "tc", "uneven", "forms", "long"],
+                   choices=["laser", "single", "sweep", "tc", "uneven", "forms", "long", "hist"],
                    help="laser: the headline stream (default); single: one 4096-bit block; sweep: block-length "
                         "sweep on a 2^30-bit stream; tc: m=6144, n=8192, 4096 blocks; uneven: 10,000 requests; "
                         "long: 64 blocks of 2^22 bits (the transform route's profiling case)")
@@ -224,6 +257,7 @@ def run_ours(args, world, rank, local):
     value = job_throughput(world, out_bits, args.steps, t_total)
     kernel_ms = stats["timed_ms"] / max(1, stats["timed_launches"])
     used_algo = q.ALGO_NAMES.get(stats["last_algo"], str(stats["last_algo"]))
+    caps = device_caps(local)
 
     # plain per-block direct kernel on the same inputs, same timing method
     plain = None
@@ -241,9 +275,10 @@ def run_ours(args, world, rank, local):
     # step again after the plain run so the final output is the measured algorithm's
     m = step()
     torch.cuda.synchronize()
+    out_host = out[:(num_blocks * m + 7) // 8].cpu().numpy()
 
     plan = q.qrng_karatsuba_plan(ctx, n, m, q.QRNG_FORM_STANDARD, num_blocks) if used_algo == "gemm_karatsuba" else None
-    roofline = roofline_for(used_algo, num_blocks, m, n, kernel_ms, plan)
+    roofline = roofline_for(used_algo, num_blocks, m, n, kernel_ms, plan, caps)
 
     # end to end through the host-buffer entry point (pinned host memory, copies inside the timed region)
     e2e = None
@@ -283,9 +318,13 @@ def run_ours(args, world, rank, local):
         "plain_per_block": plain,
         "e2e": e2e,
         "clocks": clocks.summary(),
+        "device": {"sms": caps["sms"], "sm_max_mhz": caps["sm_max_mhz"]},
     }
+    if rank == 0 and not args.headline_only:
+        result["configs"] = run_subrecords(q, ctx, local, caps, flush, (samples, seed, n, m, num_blocks, out))
     if rank == 0 and not args.no_cpu_baseline:
-        result["cpu_baseline"] = cpu_baseline(samples_h, seed_h, n, m, eps)
+        result["cpu_baseline"], result["oracle_check"] = cpu_baseline(samples_h, seed_h, n, m, eps, out_host,
+                                                                      num_blocks)
     ctx.close()
     if world > 1:
         torch.distributed.destroy_process_group()
@@ -324,19 +363,32 @@ def captured_traffic(kernel: str, source: str, units: int):
     return int(rec["dram_bytes"] * units / rec["blocks"])
 
 
-def roofline_for(algo, num_blocks, m, n, kernel_ms, plan=None):
-    """Roofline of the dominant (extraction) kernel from its algorithmic work and live event time."""
+def hbm_record(bytes_moved, ms):
+    pk = measured_peaks()
+    gbs = bytes_moved / (ms / 1e3) / 1e9
+    return {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+            "algorithmic_bytes": int(bytes_moved), "peak_source": "copy bandwidth " + pk["source"]}
+
+
+def roofline_for(algo, num_blocks, m, n_t, kernel_ms, plan=None, caps=None, n=None):
+    """Roofline of the dominant (extraction) kernel from its algorithmic work and live event time.
+    n_t is the Toeplitz width (n, or n - m for the modified form); n the block length."""
+    if caps is None and algo in ("direct", "fft32_seg"):
+        caps = device_caps()
+    n = n or n_t
+    io_bytes = num_blocks * (n + m) / 8  # raw bits in, output bits out
     if algo == "direct":
-        achieved = num_blocks * m * n / (kernel_ms / 1e3) / 1e12
-        return {"bound": "alu", "achieved": achieved, "peak": ALU_PEAK_TBITMAC, "unit": "Tbit-MAC/s",
-                "frac": achieved / ALU_PEAK_TBITMAC,
+        peak = alu_peak_tbitmac(caps)
+        achieved = num_blocks * m * n_t / (kernel_ms / 1e3) / 1e12
+        return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "Tbit-MAC/s", "frac": achieved / peak,
                 "traffic": captured_traffic("direct_kernel", "k_direct.cu", num_blocks),
                 "kernel": "direct_kernel<32>", "kernel_ms": kernel_ms,
-                "peak_source": "derived: 64 LOP3/clk/SM x 32 bit-MACs x 152 SMs x 2070 MHz"}
+                "peak_source": f"derived: {LOP3_PER_CLK_SM} LOP3/clk/SM x 32 bit-MACs x {caps['sms']} SMs x "
+                               f"{caps['sm_max_mhz']:g} MHz"}
     if algo == "gemm_tc":
         pk = measured_peaks()
         peak = 2.0 * pk["bf16_tflops"]  # FP8 dense = bf16 measured x nominal ratio 4.5/2.25
-        achieved = 2.0 * num_blocks * m * n / (kernel_ms / 1e3) / 1e12
+        achieved = 2.0 * num_blocks * m * n_t / (kernel_ms / 1e3) / 1e12
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": captured_traffic("gemm_tc_kernel", "k_gemm_tc.cu", num_blocks),
                 "kernel": "gemm_tc_kernel (tcgen05 kind::f8f6f4)", "kernel_ms": kernel_ms,
@@ -344,7 +396,7 @@ def roofline_for(algo, num_blocks, m, n, kernel_ms, plan=None):
     if algo in ("gemm_fp4", "gemm_fp4_pair"):
         pk = measured_peaks()
         peak = 6.0 * pk["bf16_tflops"]  # FP4 dense = bf16 measured x nominal ratio 13.5/2.25
-        achieved = 2.0 * num_blocks * m * n / (kernel_ms / 1e3) / 1e12
+        achieved = 2.0 * num_blocks * m * n_t / (kernel_ms / 1e3) / 1e12
         pair = algo == "gemm_fp4_pair"
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": (captured_traffic("gemm_pair_kernel", "k_gemm_pair.cu", num_blocks) if pair
@@ -364,34 +416,81 @@ def roofline_for(algo, num_blocks, m, n, kernel_ms, plan=None):
                 "traffic": captured_traffic("gemm_pair_kara_kernel", "k_gemm_pair.cu", num_blocks),
                 "kernel": "gemm_pair_kernel<kKara> (tcgen05 cta_group::2 kind::mxf4 on the block-Karatsuba "
                           "sub-products)", "kernel_ms": kernel_ms,
-                "plan": plan, "equivalent_plain_tflops": 2.0 * num_blocks * m * n / (kernel_ms / 1e3) / 1e12,
+                "plan": plan, "equivalent_plain_tflops": 2.0 * num_blocks * m * n_t / (kernel_ms / 1e3) / 1e12,
                 "peak_source": "FP4 = 6 x bf16 burst " + pk["source"]}
+    if algo == "fft64":
+        # two P-point complex FP64 transforms per pair of blocks (5 P log2 P flops each) and the
+        # spectrum product (6 P)
+        P = 1 << max(1, (n_t + m - 2).bit_length())
+        flops = (num_blocks + 1) // 2 * (2 * 5.0 * P * math.log2(P) + 6.0 * P)
+        achieved = flops / (kernel_ms / 1e3) / 1e12
+        return {"bound": "fp64", "achieved": achieved, "peak": FP64_TFLOPS_NOMINAL, "unit": "TFLOP/s",
+                "frac": achieved / FP64_TFLOPS_NOMINAL, "kernel": "stockham_pass4_kernel et al. (FP64)",
+                "kernel_ms": kernel_ms, "hbm": hbm_record(io_bytes, kernel_ms),
+                "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s"}
+    if algo == "fft32_seg":
+        return {"bound": "fp32", "achieved": None, "peak": fp32_peak_tflops(caps), "unit": "TFLOP/s", "frac": None,
+                "kernel": "seg_conv_kernel (FP32)", "kernel_ms": kernel_ms, "hbm": hbm_record(io_bytes, kernel_ms),
+                "peak_source": f"derived: {FP32_FMA_PER_CLK_SM} FMA/clk/SM x 2 x {caps['sms']} SMs x "
+                               f"{caps['sm_max_mhz']:g} MHz"}
+    if algo == "ntt":
+        r = hbm_record(io_bytes, kernel_ms)
+        r.update({"kernel": "ntt_cols_kernel + ntt_rows_kernel (integer issue bound)", "kernel_ms": kernel_ms,
+                  "traffic": None})
+        return r
     return {"bound": None, "achieved": None, "peak": None, "unit": None, "frac": None, "traffic": None,
             "kernel_ms": kernel_ms}
 
 
-def cpu_baseline(samples_h, seed_h, n, m, eps, blocks=2):
-    """The oracle as it stands, one thread: min-entropy of the whole stream plus the full
-    Toeplitz hash of `blocks` blocks of it."""
+def cpu_baseline(samples_h, seed_h, n, m, eps, out_host=None, num_blocks=0):
+    """The oracle as it stands on the host's cores: min-entropy of the whole stream (one C call)
+    plus the full Toeplitz hash of one block per core, the blocks on threads (the oracle is plain C
+    called through ctypes, which releases the interpreter lock); and the same with one block on one
+    thread. When the timed output is given, the oracle's Freivalds check of every block of it."""
+    import concurrent.futures
+
     import oracle
 
-    t0 = time.perf_counter()
-    rep = oracle.minentropy(samples_h, 8, eps)
-    m_or = oracle.output_length(n, rep["h_modify"], 8, 1.0)
-    seed_o = seed_h[: (n + m_or - 1 + 7) // 8].copy()
-    raw = samples_h[: blocks * n // 8].copy()
-    oracle.toeplitz_blocks(raw, n, m_or, seed_o, 0, blocks)
-    dt = time.perf_counter() - t0
-    return {"value": blocks * m_or / dt / 1e9, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"min-entropy of all {samples_h.size} samples + full hash of {blocks} of "
-                      f"{samples_h.size * 8 // n} blocks (n={n}, m={m_or})", "seconds": dt}
+    cores = host_cores()
+
+    def sample(blocks, threads):
+        t0 = time.perf_counter()
+        rep = oracle.minentropy(samples_h, 8, eps)
+        m_or = oracle.output_length(n, rep["h_modify"], 8, 1.0)
+        seed_o = seed_h[: (n + m_or - 1 + 7) // 8].copy()
+
+        def one(b):
+            oracle.toeplitz(samples_h, n, m_or, seed_o, 0, raw_off=b * n)
+
+        with concurrent.futures.ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(one, range(blocks)))
+        return m_or, time.perf_counter() - t0
+
+    m1, dt1 = sample(1, 1)
+    mall, dtall = sample(cores, cores)
+    res = {"value": cores * mall / dtall / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": f"min-entropy of all {samples_h.size} samples (one thread) + full hash of {cores} of the "
+                     f"{samples_h.size * 8 // n} blocks, one per thread (n={n}, m={mall})", "seconds": dtall,
+           "single_thread": {"value": m1 / dt1 / 1e9, "unit": UNIT, "cores": 1, "seconds": dt1,
+                             "sample": "min-entropy of the whole stream + full hash of one block"}}
+    check = None
+    if out_host is not None:
+        t0 = time.perf_counter()
+        seed_o = seed_h[: (n + m - 1 + 7) // 8].copy()
+        mism = oracle.freivalds(samples_h, n, m, seed_o, 0, num_blocks, out_host, rng_seed=2024)
+        check = {"oracle_m": mall, "gpu_m": m, "m_equal": mall == m, "blocks": num_blocks,
+                 "freivalds_failures": int(np.count_nonzero(mism)), "escape_probability_per_block": "2^-64",
+                 "seconds": time.perf_counter() - t0}
+    return res, check
 
 
 def run_reference(args, world, rank):
-    """The CPU oracle on the same workload, each step a bounded sample (min-entropy of the full
-    stream + one block's full hash)."""
+    """The CPU oracle on the same workload on the host's cores, each step a bounded sample: the
+    min-entropy of the full stream, then the full hash of one block per core (one thread each)."""
     if rank != 0:
         return None
+    import concurrent.futures
+
     import oracle
 
     oracle.build()
@@ -399,18 +498,21 @@ def run_reference(args, world, rank):
     n, eps = c["n"], c["eps"]
     samples_h = W.adc_samples(c["samples"], c["sample_seed"])
     seed_h = W.random_bits(2 * n - 1, c["seed_seed"])
+    cores = host_cores()
+    nblk = samples_h.size * 8 // n
     times, bits_out = [], 0
-    for i in range(args.warmup + args.steps):
-        t0 = time.perf_counter()
-        rep = oracle.minentropy(samples_h, 8, eps)
-        m = oracle.output_length(n, rep["h_modify"], 8, 1.0)
-        blk = i % (samples_h.size * 8 // n)
-        raw = samples_h[blk * n // 8:(blk + 1) * n // 8].copy()
-        oracle.toeplitz(raw, n, m, seed_h[: (n + m - 1 + 7) // 8].copy(), 0)
-        dt = time.perf_counter() - t0
-        if i >= args.warmup:
-            times.append(dt)
-            bits_out += m
+    with concurrent.futures.ThreadPoolExecutor(max_workers=cores) as ex:
+        for i in range(args.warmup + args.steps):
+            t0 = time.perf_counter()
+            rep = oracle.minentropy(samples_h, 8, eps)
+            m = oracle.output_length(n, rep["h_modify"], 8, 1.0)
+            seed_o = seed_h[: (n + m - 1 + 7) // 8].copy()
+            blocks = [(i * cores + k) % nblk for k in range(cores)]
+            list(ex.map(lambda b: oracle.toeplitz(samples_h, n, m, seed_o, 0, raw_off=b * n), blocks))
+            dt = time.perf_counter() - t0
+            if i >= args.warmup:
+                times.append(dt)
+                bits_out += m * cores
     total = sum(times)
     value = bits_out / total / 1e9
     return {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -419,8 +521,9 @@ def run_reference(args, world, rank):
             "data": "synthetic",
             "config": {"workload": "laser-phase-noise stream: 2^26 uint8 ADC samples, n=2^16, one shared seed",
                        "n": n, "m": m},
-            "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                             "sample": "per step: min-entropy of all 2^26 samples + the full hash of one block"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"per step: min-entropy of all 2^26 samples (one thread) + the full hash "
+                                       f"of {cores} blocks, one per thread"},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
@@ -428,8 +531,9 @@ ALGOS = {"auto": 0, "direct": 1, "gemm_tc": 2, "fft64": 3, "fft32_seg": 4, "ntt"
          "gemm_fp4_pair": 7, "gemm_karatsuba": 8}
 
 
-def _time_extract(q, ctx, raw, n, m, seed, form, algo, blocks, out, reps, warmup=1):
-    """Mean CUDA-event time (ms) of the main extraction kernel and of the whole call."""
+def _time_extract(q, ctx, raw, n, m, seed, form, algo, blocks, out, reps, warmup=1, flush=None):
+    """Mean CUDA-event time (ms) of the main extraction kernel and of the whole call (L2 flushed
+    before each call when `flush` is given; the flush is outside both timings)."""
     import torch
 
     stream = torch.cuda.current_stream()
@@ -438,27 +542,214 @@ def _time_extract(q, ctx, raw, n, m, seed, form, algo, blocks, out, reps, warmup
     torch.cuda.synchronize()
     q.qrng_reset_stats(ctx)
     q.qrng_set_timing(ctx, True)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record(stream)
-    for _ in range(reps):
+    call_ms = 0.0
+    for i in range(reps):
+        if flush is not None:
+            flush.fill_(i & 0xFF)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
         q.qrng_toeplitz_extract(ctx, raw, n, m, seed, form, algo, blocks, out, stream=stream)
-    b.record(stream)
-    b.synchronize()
+        b.record(stream)
+        b.synchronize()
+        call_ms += a.elapsed_time(b)
     q.qrng_synchronize(ctx)
     st = q.qrng_get_stats(ctx)
     q.qrng_set_timing(ctx, False)
-    return st["timed_ms"] / max(1, st["timed_launches"]), a.elapsed_time(b) / reps, st
+    return st["timed_ms"] / max(1, reps), call_ms / reps, st
+
+
+def clocked(local, fn, *a, **kw):
+    """Runs fn under the clock sampler; the record gets the clocks of its own region."""
+    clocks = ClockSampler(local).start()
+    t0 = time.time()
+    res = fn(*a, **kw)
+    clocks.mark(t0, time.time())
+    clocks.stop()
+    res["clocks"] = clocks.summary()
+    return res
+
+
+def sub_single(q, ctx, caps, reps=20):
+    """Config 1: one 4096-bit block, m = 2048, plus the min-entropy of 65,536 samples: latency."""
+    import torch
+
+    c = W.CFG1
+    samples_h = W.adc_samples(c["samples"], c["sample_seed"])
+    samples = torch.from_numpy(samples_h).cuda()
+    n, m = c["n"], c["m"]
+    raw = torch.from_numpy(W.random_bits(n, c["raw_seed"])).cuda()
+    seed = torch.from_numpy(W.random_bits(n + m - 1, c["seed_seed"])).cuda()
+    out = torch.empty(m // 8, dtype=torch.uint8, device="cuda")
+    for _ in range(3):
+        q.qrng_minentropy(ctx, samples, bits=8, eps=c["eps"])
+    q.qrng_reset_stats(ctx)
+    q.qrng_set_timing(ctx, True)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        q.qrng_minentropy(ctx, samples, bits=8, eps=c["eps"])
+    ent_us = (time.perf_counter() - t0) / reps * 1e6
+    st = q.qrng_get_stats(ctx)
+    q.qrng_set_timing(ctx, False)
+    hist_us = st["hist_timed_ms"] / max(1, st["hist_timed_launches"]) * 1e3
+    kms, cms, _ = _time_extract(q, ctx, raw, n, m, seed, 0, ALGOS["direct"], 1, out, reps=reps, warmup=3)
+    return {"workload": "65,536 uint8 samples + one block n=4096, m=2048, standard seed", "bound": "latency",
+            "minentropy_call_us_host": ent_us, "histogram_kernel_us": hist_us, "extract_kernel_us": kms * 1e3,
+            "extract_call_us": cms * 1e3, "gbps": m / (cms / 1e3) / 1e9,
+            "roofline": roofline_for("direct", 1, m, n, kms, caps=caps)}
+
+
+def sub_histogram(q, ctx, flush, reps=10):
+    """The histogram kernel alone on the laser stream's 2^26 uint8 samples and on 2^26 uint16
+    samples of a 16-bit ADC (clip(round(N(2^15, 4096^2)))): HBM bytes over kernel time."""
+    import torch
+
+    res = {"workload": "histogram kernel: 2^26 uint8 samples (8-bit ADC) and 2^26 uint16 samples (16-bit ADC)"}
+    c = W.CFG2
+    for bits, samples_h in ((8, W.adc_samples(c["samples"], c["sample_seed"])),
+                            (16, W.adc_samples(c["samples"], 41, mu=32768.0, sigma=4096.0, bits=16))):
+        samples = torch.from_numpy(samples_h.view(np.uint8)).cuda()
+        for _ in range(3):
+            q.qrng_minentropy(ctx, samples, count=samples_h.size, bits=bits, eps=1e-6)
+        q.qrng_reset_stats(ctx)
+        q.qrng_set_timing(ctx, True)
+        for i in range(reps):
+            flush.fill_(i & 0xFF)
+            q.qrng_minentropy(ctx, samples, count=samples_h.size, bits=bits, eps=1e-6)
+        st = q.qrng_get_stats(ctx)
+        q.qrng_set_timing(ctx, False)
+        ms = st["hist_timed_ms"] / max(1, st["hist_timed_launches"])
+        r = hbm_record(samples_h.nbytes, ms)
+        r["kernel_us"] = ms * 1e3
+        r["kernel"] = "hist_u8_kernel" if bits <= 8 else "hist_u16 kernel"
+        res[f"bits{bits}"] = r
+    return res
+
+
+def sub_sweep(q, ctx, caps, flush, reps=2):
+    """Config 3: a fixed 2^30-bit Bernoulli(0.5) stream, n = 2^10 .. 2^24, m = 0.75 n, modified
+    form, one (n-1)-bit seed per n: AUTO's choice per n against the plain per-block direct kernel."""
+    import torch
+
+    c = W.CFG3
+    raw = torch.from_numpy(W.random_bits(c["stream_bits"], c["raw_seed"])).cuda()
+    out = torch.empty(c["stream_bits"] // 8, dtype=torch.uint8, device="cuda")
+    rows = []
+    for n in c["n_list"]:
+        m = int(n * c["ratio"])
+        B = c["stream_bits"] // n
+        seed = torch.from_numpy(W.random_bits(n - 1, c["seed_seed"] + n.bit_length() - 1)).cuda()
+        kms, cms, st = _time_extract(q, ctx, raw, n, m, seed, 1, ALGOS["auto"], B, out, reps=reps, flush=flush)
+        algo = q.ALGO_NAMES.get(st["last_algo"], str(st["last_algo"]))
+        plan = q.qrng_karatsuba_plan(ctx, n, m, 1, B) if algo == "gemm_karatsuba" else None
+        rl = roofline_for(algo, B, m, n - m, kms, plan, caps, n=n)
+        row = {"n": n, "m": m, "blocks": B, "algo": algo, "call_ms": cms, "kernel_ms": kms,
+               "gbps": B * m / (cms / 1e3) / 1e9, "frac": rl.get("frac"), "bound": rl.get("bound")}
+        if n <= (1 << 20):
+            dk, dc, _ = _time_extract(q, ctx, raw, n, m, seed, 1, ALGOS["direct"], B, out, reps=1, flush=flush)
+            row["direct"] = {"call_ms": dc, "gbps": B * m / (dc / 1e3) / 1e9,
+                             "frac": roofline_for("direct", B, m, n - m, dk, caps=caps)["frac"]}
+        rows.append(row)
+    return {"workload": "block-length sweep: 2^30-bit Bernoulli(0.5) stream, n = 2^10..2^24, m = 0.75n, modified "
+                        "form, AUTO vs the plain per-block direct kernel (n <= 2^20)", "unit": UNIT, "rows": rows}
+
+
+def sub_tc(q, ctx, caps, flush, reps=5):
+    """Config 4: one standard seed, m = 6144, n = 8192, 4096 blocks: the tensor-core products."""
+    import torch
+
+    c = W.CFG4
+    n, m, B = c["n"], c["m"], c["blocks"]
+    raw = torch.from_numpy(W.random_bits(n * B, c["raw_seed"])).cuda()
+    seed = torch.from_numpy(W.random_bits(n + m - 1, c["seed_seed"])).cuda()
+    out = torch.empty(m * B // 8, dtype=torch.uint8, device="cuda")
+    res = {"workload": "m=6144, n=8192, 4096 blocks, one standard seed (T 6144x8192 times X 8192x4096)",
+           "unit": UNIT}
+    for name in ("gemm_karatsuba", "gemm_fp4_pair", "gemm_fp4", "gemm_tc", "direct"):
+        kms, cms, _ = _time_extract(q, ctx, raw, n, m, seed, 0, ALGOS[name], B, out, reps=reps, flush=flush)
+        plan = q.qrng_karatsuba_plan(ctx, n, m, 0, B) if name == "gemm_karatsuba" else None
+        rl = roofline_for(name, B, m, n, kms, plan, caps)
+        res[name] = {"kernel_ms": kms, "call_ms": cms, "gbps": B * m / (cms / 1e3) / 1e9, "achieved": rl["achieved"],
+                     "unit": rl["unit"], "frac": rl["frac"]}
+    return res
+
+
+def sub_fft_routes(q, ctx, caps, samples, seed, n, m, num_blocks, out, flush, reps=2):
+    """The transform routes on the laser stream (the paper's FP64 circulant FFT, the FP32 segmented
+    FFT and the exact number-theoretic transform) with their rounding evidence."""
+    res = {"workload": "laser stream, n=2^16, standard form"}
+    for name in ("ntt", "fft64", "fft32_seg"):
+        kms, cms, st = _time_extract(q, ctx, samples, n, m, seed, 0, ALGOS[name], num_blocks, out, reps=reps,
+                                     flush=flush)
+        rl = roofline_for(name, num_blocks, m, n, kms, caps=caps)
+        res[name] = {"kernel_ms": kms, "call_ms": cms, "gbps": num_blocks * m / (cms / 1e3) / 1e9,
+                     "worst_round_err": st["worst_fft_round_err"] if name != "ntt" else 0.0, "roofline": rl}
+    return res
+
+
+def sub_uneven(q, ctx, caps, routes=("auto",)):
+    """Config 5: 10,000 uneven requests (n log-uniform in [2^12, 2^22], m/n uniform in [0.5, 0.9],
+    per-request seeds, raw Bernoulli(p), p uniform in [0.45, 0.55])."""
+    import torch
+
+    b = W.uneven_batch()
+    raw = torch.from_numpy(b["raw"]).cuda()
+    seeds = torch.from_numpy(b["seeds"]).cuda()
+    out = torch.empty((b["out_bits"] + 7) // 8 + 8, dtype=torch.uint8, device="cuda")
+    reqs = [(raw.data_ptr(), int(b["raw_off"][i]), int(b["n"][i]), int(b["m"][i]),
+             seeds.data_ptr() + int(b["seed_off"][i]), 0, out.data_ptr(), int(b["out_off"][i]))
+            for i in range(b["n"].size)]
+    n, m = b["n"].astype(np.float64), b["m"].astype(np.float64)
+    res = {"workload": f"{n.size} uneven requests, n log-uniform in [2^12, 2^22], m/n uniform in [0.5, 0.9], "
+                       "per-request standard seeds, Bernoulli(p) raw bits", "unit": UNIT,
+           "output_gbit": float(m.sum()) / 1e9, "bitmacs": float((m * n).sum())}
+    stream = torch.cuda.current_stream()
+    for route in routes:
+        algo = ALGOS[route]
+        q.qrng_extract_batch(ctx, reqs, algo=algo)  # capture + first run
+        q.qrng_synchronize(ctx)
+        q.qrng_reset_stats(ctx)
+        q.qrng_set_timing(ctx, True)
+        a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        q.qrng_extract_batch(ctx, reqs, algo=algo)  # graph replay
+        e.record(stream)
+        e.synchronize()
+        q.qrng_synchronize(ctx)
+        st = q.qrng_get_stats(ctx)
+        q.qrng_set_timing(ctx, False)
+        ms = a.elapsed_time(e)
+        r = {"ms": ms, "gbps": res["output_gbit"] / (ms / 1e3), "graph_ms": st["batch_graph_ms"],
+             "transform_ms": st["batch_transform_ms"], "kernels_per_call": st["last_kernels"],
+             "worst_round_err": st["worst_fft_round_err"]}
+        r["direct_equivalent_tbitmac_per_s"] = res["bitmacs"] / (ms / 1e3) / 1e12
+        if route == "direct":
+            r["frac_of_lop3_peak"] = res["bitmacs"] / (st["batch_graph_ms"] / 1e3) / 1e12 / alu_peak_tbitmac(caps)
+        res[route] = r
+    return res
+
+
+def run_subrecords(q, ctx, local, caps, flush, laser):
+    subs = {}
+    subs["single"] = clocked(local, sub_single, q, ctx, caps)
+    subs["histogram"] = clocked(local, sub_histogram, q, ctx, flush)
+    subs["fft_routes"] = clocked(local, sub_fft_routes, q, ctx, caps, *laser, flush)
+    subs["tc"] = clocked(local, sub_tc, q, ctx, caps, flush)
+    subs["sweep"] = clocked(local, sub_sweep, q, ctx, caps, flush)
+    subs["uneven"] = clocked(local, sub_uneven, q, ctx, caps)
+    return subs
 
 
 def run_sweep(args):
     """Block-length sweep (the paper's Fig. 6 question on GB300): a fixed 2^30-bit Bernoulli(0.5)
-    stream, n = 2^10 .. 2^24, m = 0.75 n, modified form, one (n-1)-bit seed per n."""
+    stream, n = 2^10 .. 2^24, m = 0.75 n, modified form, one (n-1)-bit seed per n; every algorithm
+    of --sweep-algos at every n."""
     import torch
 
     import paper_2011_04130_gb300 as q
 
     torch.cuda.set_device(0)
     ctx = q.Context(0)
+    caps = device_caps()
     c = W.CFG3
     raw = torch.from_numpy(W.random_bits(c["stream_bits"], c["raw_seed"])).cuda()
     out = torch.empty(c["stream_bits"] // 8, dtype=torch.uint8, device="cuda")
@@ -471,7 +762,10 @@ def run_sweep(args):
         for name in args.sweep_algos.split(","):
             try:
                 kms, cms, st = _time_extract(q, ctx, raw, n, m, seed, 1, ALGOS[name], B, out, reps=2)
-                row[name] = {"kernel_ms": kms, "call_ms": cms, "gbps": B * m / (cms / 1e3) / 1e9}
+                plan = q.qrng_karatsuba_plan(ctx, n, m, 1, B) if name == "gemm_karatsuba" else None
+                rl = roofline_for(name, B, m, n - m, kms, plan, caps, n=n)
+                row[name] = {"kernel_ms": kms, "call_ms": cms, "gbps": B * m / (cms / 1e3) / 1e9,
+                             "frac": rl.get("frac"), "bound": rl.get("bound")}
                 if name.startswith("fft"):
                     row[name]["worst_round_err"] = st["worst_fft_round_err"]
             except q.QrngError as e:
@@ -514,38 +808,6 @@ def run_forms(args):
     return {"workload": "standard vs modified Toeplitz on a 2^30-bit stream", "unit": UNIT, "rows": rows}
 
 
-def run_tc(args):
-    """One standard seed, m = 6144, n = 8192, 4096 blocks: tensor-core product vs the direct kernel."""
-    import torch
-
-    import paper_2011_04130_gb300 as q
-
-    torch.cuda.set_device(0)
-    ctx = q.Context(0)
-    c = W.CFG4
-    n, m, B = c["n"], c["m"], c["blocks"]
-    raw = torch.from_numpy(W.random_bits(n * B, c["raw_seed"])).cuda()
-    seed = torch.from_numpy(W.random_bits(n + m - 1, c["seed_seed"])).cuda()
-    out = torch.empty(m * B // 8, dtype=torch.uint8, device="cuda")
-    res = {"workload": "m=6144, n=8192, 4096 blocks, one standard seed", "unit": UNIT, "data": "synthetic"}
-    pk = measured_peaks()
-    for name in ("gemm_karatsuba", "gemm_fp4_pair", "gemm_fp4", "gemm_tc", "direct"):
-        kms, cms, _ = _time_extract(q, ctx, raw, n, m, seed, 0, ALGOS[name], B, out, reps=args.steps)
-        res[name] = {"kernel_ms": kms, "call_ms": cms, "gbps": B * m / (cms / 1e3) / 1e9}
-        if name == "gemm_karatsuba":
-            plan = q.qrng_karatsuba_plan(ctx, n, m, 0, B)
-            tf = 2.0 * plan["groups"] * plan["mq"] * plan["kq"] * B / (kms / 1e3) / 1e12
-            res[name].update({"plan": plan, "tflops": tf, "frac_of_peak": tf / (6.0 * pk["bf16_tflops"]),
-                              "peak_source": f"6 x bf16 burst {pk['source']}"})
-        elif name.startswith("gemm"):
-            tf = 2.0 * m * n * B / (kms / 1e3) / 1e12
-            ratio = 6.0 if name.startswith("gemm_fp4") else 2.0  # nominal FP4 / FP8 dense rates over bf16
-            res[name].update({"tflops": tf, "frac_of_peak": tf / (ratio * pk["bf16_tflops"]),
-                              "peak_source": f"{ratio:g} x bf16 burst {pk['source']}"})
-    ctx.close()
-    return res
-
-
 def run_long(args):
     """64 blocks of n = 2^22 raw bits, m = 0.75 n, modified form, one seed: a 2^28-bit stream on the
     long-block route (--algo, default ntt), small enough for a profiler capture."""
@@ -568,91 +830,27 @@ def run_long(args):
             "call_ms": cms, "gbps": B * m / (cms / 1e3) / 1e9, "data": "synthetic"}
 
 
-def run_single(args):
-    """One 4096-bit block, m = 2048, plus the min-entropy of 65,536 samples: latency."""
-    import torch
+def _standalone(fn):
+    """One sub-record workload on its own (--workload single|tc|uneven|hist)."""
+    def run(args):
+        import torch
 
-    import paper_2011_04130_gb300 as q
+        import paper_2011_04130_gb300 as q
 
-    torch.cuda.set_device(0)
-    ctx = q.Context(0)
-    c = W.CFG1
-    samples = torch.from_numpy(W.adc_samples(c["samples"], c["sample_seed"])).cuda()
-    n, m = c["n"], c["m"]
-    raw = torch.from_numpy(W.random_bits(n, c["raw_seed"])).cuda()
-    seed = torch.from_numpy(W.random_bits(n + m - 1, c["seed_seed"])).cuda()
-    out = torch.empty(m // 8, dtype=torch.uint8, device="cuda")
-    for _ in range(args.warmup):
-        q.qrng_minentropy(ctx, samples, bits=8, eps=c["eps"])
-    t0 = time.perf_counter()
-    for _ in range(args.steps):
-        q.qrng_minentropy(ctx, samples, bits=8, eps=c["eps"])
-    ent_us = (time.perf_counter() - t0) / args.steps * 1e6
-    kms, cms, _ = _time_extract(q, ctx, raw, n, m, seed, 0, ALGOS["direct"], 1, out, reps=args.steps)
-    ctx.close()
-    return {"workload": "65,536 samples + one block n=4096, m=2048", "minentropy_us_host": ent_us,
-            "extract_kernel_us": kms * 1e3, "extract_call_us": cms * 1e3, "gbps": m / (cms / 1e3) / 1e9}
-
-
-def run_uneven(args):
-    """10,000 uneven requests (n log-uniform, m/n uniform in [0.5, 0.9], per-request seeds, raw
-    Bernoulli(p), p uniform in [0.45, 0.55]) in one persistent launch under a CUDA graph."""
-    import torch
-
-    import paper_2011_04130_gb300 as q
-
-    torch.cuda.set_device(0)
-    ctx = q.Context(0)
-    c = W.CFG5
-    n, m, p = W.uneven_requests(c["requests"], c["seed"], c["log2n_lo"], args.uneven_max_log2n, c["rho_lo"],
-                                c["rho_hi"], c["p_lo"], c["p_hi"])
-    raw_off = np.concatenate([[0], np.cumsum(((n + 31) // 32) * 32)[:-1]])
-    total_raw = int(raw_off[-1] + n[-1] + 64)
-    seed_off = np.concatenate([[0], np.cumsum(((n + m + 7) // 8) * 8)[:-1]])  # byte-aligned seeds
-    out_off = np.concatenate([[0], np.cumsum(m)[:-1]])
-    g = W.rng(c["seed"] + 7)
-    raw = torch.empty((total_raw + 7) // 8, dtype=torch.uint8, device="cuda")
-    # raw bits per request are Bernoulli(p_r): fill in chunks of requests to bound host memory
-    for i in range(len(n)):
-        bits = W.random_bits(int(n[i]), 10_000 + i, float(p[i]))
-        raw[raw_off[i] // 8:raw_off[i] // 8 + bits.size] = torch.from_numpy(bits).cuda()
-    seeds = torch.from_numpy(g.integers(0, 256, int(seed_off[-1] + (n[-1] + m[-1] + 7) // 8), dtype=np.uint8)).cuda()
-    out = torch.empty(int((out_off[-1] + m[-1] + 7) // 8 + 8), dtype=torch.uint8, device="cuda")
-    table = (q.Request * len(n))()
-    for i in range(len(n)):
-        table[i] = q.Request(raw.data_ptr(), int(raw_off[i]), int(n[i]), int(m[i]),
-                             seeds.data_ptr() + int(seed_off[i]) // 8, 0, out.data_ptr(), int(out_off[i]))
-    lib = q.load_library()
-    stream = torch.cuda.current_stream()
-    sp = stream.cuda_stream
-
-    def call():
-        ctx.check(lib.qrng_extract_batch(ctx.handle, table, len(n), ALGOS[args.algo], sp), "qrng_extract_batch")
-
-    call()  # capture + first run
-    q.qrng_synchronize(ctx)
-    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    t0 = time.perf_counter()
-    a.record(stream)
-    for _ in range(max(1, args.steps)):
-        call()  # graph replay (the request table is hashed on the host each call)
-    b.record(stream)
-    b.synchronize()
-    host_ms = (time.perf_counter() - t0) * 1e3 / max(1, args.steps)
-    q.qrng_synchronize(ctx)
-    ms = a.elapsed_time(b) / max(1, args.steps)
-    bitmacs = float(np.sum(m.astype(np.float64) * n))
-    st = q.qrng_get_stats(ctx)
-    ctx.close()
-    res = {"workload": f"{len(n)} uneven requests, n log-uniform in [2^12, 2^{args.uneven_max_log2n:g}], "
-                       "m/n uniform in [0.5, 0.9], per-request seeds", "algo": args.algo, "ms": ms,
-           "host_wall_ms": host_ms, "output_gbit": float(np.sum(m)) / 1e9,
-           "gbps": float(np.sum(m)) / (ms / 1e3) / 1e9, "kernels_per_call": st["last_kernels"],
-           "route": q.ALGO_NAMES.get(st["last_algo"], "mixed") if st["last_algo"] else "mixed (direct + ntt)",
-           "direct_equivalent_tbitmac_per_s": bitmacs / (ms / 1e3) / 1e12}
-    if st["last_algo"] == q.QRNG_ALGO_DIRECT:
-        res["frac_of_lop3_peak"] = res["direct_equivalent_tbitmac_per_s"] / ALU_PEAK_TBITMAC
-    return res
+        torch.cuda.set_device(0)
+        ctx = q.Context(0)
+        caps = device_caps()
+        flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+        if fn is sub_uneven:
+            routes = ("auto", "ntt", "fft64", "direct") if args.algo == "all" else (args.algo,)
+            res = clocked(0, fn, q, ctx, caps, routes)
+        elif fn is sub_histogram:
+            res = clocked(0, fn, q, ctx, flush)
+        else:
+            res = clocked(0, fn, q, ctx, caps, flush) if fn is not sub_single else clocked(0, fn, q, ctx, caps)
+        ctx.close()
+        return res
+    return run
 
 
 def main():
@@ -661,8 +859,9 @@ def main():
     if args.impl == "reference":
         res = run_reference(args, world, rank)
     elif args.workload != "laser":
-        res = {"sweep": run_sweep, "tc": run_tc, "single": run_single, "uneven": run_uneven,
-               "forms": run_forms, "long": run_long}[args.workload](args)
+        res = {"sweep": run_sweep, "forms": run_forms, "long": run_long, "single": _standalone(sub_single),
+               "tc": _standalone(sub_tc), "uneven": _standalone(sub_uneven),
+               "hist": _standalone(sub_histogram)}[args.workload](args)
     else:
         res = run_ours(args, world, rank, local)
     if rank == 0 and res is not None:

@@ -157,7 +157,11 @@ QRNG_API int qrng_minentropy_quantum(qrng_ctx* ctx, const void* samples_on, uint
  * >= 2^bits, QRNG_ECUDA when a CUDA call fails.
  * Every call on a device shares the one scratch area (cleared at the start of each call): calls
  * whose GPU work overlaps, e.g. on two streams at once, race and return wrong reports. The first
- * call on a device looks up the scratch's device address; make it before any stream capture.
+ * call on a device looks up the scratch's device address; under CUDA's default lazy module
+ * loading it is also the moment the driver loads the library's device code and places the
+ * scratch, so make that first call during set-up, before streaming starts and before any stream
+ * capture (CUDA_MODULE_LOADING=EAGER places it when the context is created instead). Later calls
+ * allocate nothing.
  */
 QRNG_API int qrng_minentropy_noalloc(const void* samples, uint64_t count, int bits, double eps,
                                      qrng_hmin_report* rep, qrng_stream_t stream);
@@ -182,8 +186,15 @@ enum {
   QRNG_ALGO_DIRECT = 1,   /* bit-packed AND/XOR + parity, each block on its own (Sec. III.B, O(mn)) */
   QRNG_ALGO_GEMM_TC = 2,  /* all blocks as one GF(2) matrix product T X on tcgen05 tensor cores   */
   QRNG_ALGO_FFT64 = 3,    /* circulant embedding + FP64 FFT convolution per block (Sec. III.B-D) */
-  QRNG_ALGO_FFT32_SEG = 4,/* FP32 FFT over short segments with a proven rounding bound, parities
-                             of the segments XOR-combined                                          */
+  QRNG_ALGO_FFT32_SEG = 4,/* FP32 FFT over segments of S bits (S = 2048, 4096 or 8192; the
+                             autotuner picks S with the route): every segment and seed window is
+                             transformed once, T segment-window products are summed in the
+                             frequency domain per inverse transform, T from a proven rounding bound
+                             (qrng_fft32_terms_bound), each sum rounded to its exact integer and the
+                             parities XOR-combined; if an observed rounding distance reaches 0.25,
+                             or a sum reaches 2^20 (FP32 cannot show its rounding there), which only
+                             happens with T forced past the bound, the exact direct kernel
+                             recomputes the call on the GPU                                        */
   QRNG_ALGO_NTT = 5,      /* the circulant convolution of Sec. III.B with a number-theoretic
                              transform mod 2013265921 (exact integers, integer pipes); lengths up
                              to 2^27                                                                */
@@ -294,6 +305,16 @@ typedef struct {
   double worst_fft_round_err;    /* max |s - round(s)| seen by the FFT paths since the reset    */
   uint64_t timed_launches;       /* main extraction kernels timed since the reset (see below)   */
   double timed_ms;               /* their summed device time, from CUDA events on their stream  */
+  uint64_t hist_timed_launches;  /* histogram kernels of qrng_minentropy timed since the reset  */
+  double hist_timed_ms;          /* their summed device time                                    */
+  double batch_graph_ms;         /* qrng_extract_batch: device time of its graph replays        */
+  uint64_t batch_requests[4];    /* requests of the last qrng_extract_batch call per route: the
+                                    persistent direct kernel, the number-theoretic transform,
+                                    the FP64 FFT and the FP32 segmented FFT                      */
+  double worst_fft32_round_err;  /* the FP32 segmented route's part of worst_fft_round_err      */
+  uint64_t fft32_recomputed;     /* FP32 segmented calls whose rounding guard tripped and whose
+                                    output the exact direct kernel recomputed                   */
+  uint64_t last_fft32_segment;   /* segment length S of the last FP32 segmented call            */
 } qrng_stats;
 
 /* Statistics since creation or the last reset. When timing is on, this call waits for the
@@ -346,10 +367,29 @@ typedef struct {
 QRNG_API int qrng_karatsuba_plan(qrng_ctx* ctx, uint64_t n, uint64_t m, int form, uint64_t num_blocks,
                                  qrng_karatsuba_plan_info* out);
 
-/* Timing of the main extraction kernel of each qrng_toeplitz_extract call (on = 1, off = 0):
- * a CUDA event pair is recorded around that one launch on the caller's stream and summed into
- * timed_ms / timed_launches. At most 4096 launches are kept between two qrng_get_stats calls;
- * later ones are not timed. */
+/* FP32 segmented FFT settings of QRNG_ALGO_FFT32_SEG (Sec. III.B circulant route on segments):
+ *   segment_bits   S: 2048, 4096 or 8192, or 0 (the default) to choose S per shape (the
+ *                  autotuner times each S; without autotuning the cost model picks);
+ *   terms          segment-window products summed per inverse transform, or 0 (the default) for
+ *                  qrng_fft32_terms_bound(S). A larger value is allowed (a test of the rounding
+ *                  guard): results stay exact, because a tripped guard makes the direct kernel
+ *                  recompute the call, counted in qrng_stats.fft32_recomputed.
+ * QRNG_EINVAL for other values. Forgets the shapes autotuned so far. */
+QRNG_API int qrng_set_fft32(qrng_ctx* ctx, uint64_t segment_bits, int terms);
+
+/* The largest number of product terms per inverse transform for which the FP32 rounding bound of
+ * QRNG_ALGO_FFT32_SEG keeps every convolution sum within 0.45 of its integer: T with
+ * T sqrt((2S-1) S) (eps_k + T u) <= 0.45, u = 2^-24, k = log2(2S), eps_k Percival's factor for
+ * radix-2 transforms of length 2^k with twiddles rounded once (16, 8 and 3 for S = 2048, 4096,
+ * 8192). 0 for another S. Pure host arithmetic. */
+QRNG_API int qrng_fft32_terms_bound(uint64_t segment_bits);
+
+/* Timing (on = 1, off = 0): CUDA event pairs on the caller's stream around the main extraction
+ * kernel of each qrng_toeplitz_extract call (one pair per launch; the block-Karatsuba route
+ * launches its product kernel once per pass), summed into timed_ms / timed_launches; around the
+ * histogram kernel of qrng_minentropy (hist_timed_*); and around the two parts of each
+ * qrng_extract_batch call (batch_graph_ms, batch_transform_ms). At most 4096 pairs are kept
+ * between two qrng_get_stats calls; later ones are not timed. */
 QRNG_API int qrng_set_timing(qrng_ctx* ctx, int on);
 
 #ifdef __cplusplus

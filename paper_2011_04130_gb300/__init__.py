@@ -27,7 +27,8 @@ EXPORTED = ["qrng_create", "qrng_destroy", "qrng_last_error", "qrng_status_strin
             "qrng_output_length", "qrng_seed_bits", "qrng_toeplitz_extract", "qrng_postprocess_host",
             "qrng_get_stats", "qrng_reset_stats", "qrng_set_timing", "qrng_synchronize",
             "qrng_minentropy_noalloc", "qrng_extract_batch", "qrng_set_autotune", "qrng_inject_fault",
-            "qrng_minentropy_sampled", "qrng_minentropy_quantum", "qrng_set_karatsuba", "qrng_karatsuba_plan"]
+            "qrng_minentropy_sampled", "qrng_minentropy_quantum", "qrng_set_karatsuba", "qrng_karatsuba_plan",
+            "qrng_set_fft32", "qrng_fft32_terms_bound"]
 QRNG_FAULT_NONE, QRNG_FAULT_GEMM_NO_TMA = 0, 1
 
 
@@ -80,10 +81,19 @@ class Stats(ctypes.Structure):
         ("worst_fft_round_err", ctypes.c_double),
         ("timed_launches", ctypes.c_uint64),
         ("timed_ms", ctypes.c_double),
+        ("hist_timed_launches", ctypes.c_uint64),
+        ("hist_timed_ms", ctypes.c_double),
+        ("batch_graph_ms", ctypes.c_double),
+        ("batch_requests", ctypes.c_uint64 * 4),
+        ("worst_fft32_round_err", ctypes.c_double),
+        ("fft32_recomputed", ctypes.c_uint64),
+        ("last_fft32_segment", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        d = {name: getattr(self, name) for name, _ in self._fields_}
+        d["batch_requests"] = dict(zip(("direct", "ntt", "fft64", "fft32_seg"), list(self.batch_requests)))
+        return d
 
 
 class KaratsubaPlan(ctypes.Structure):
@@ -131,6 +141,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qrng_synchronize.argtypes = [vp, vp]
     lib.qrng_set_autotune.argtypes = [vp, i32]
     lib.qrng_set_karatsuba.argtypes = [vp, i32, u64, u64]
+    lib.qrng_set_fft32.argtypes = [vp, u64, i32]
+    lib.qrng_fft32_terms_bound.argtypes = [u64]
     lib.qrng_karatsuba_plan.argtypes = [vp, u64, u64, i32, u64, ctypes.POINTER(KaratsubaPlan)]
     lib.qrng_minentropy_sampled.argtypes = [vp, vp, u64, i32, dbl, dbl, u64, ctypes.POINTER(HminReport), vp]
     lib.qrng_minentropy_quantum.argtypes = [vp, vp, u64, vp, u64, i32, dbl, ctypes.POINTER(HminReport),
@@ -318,6 +330,15 @@ def qrng_set_autotune(ctx: Context, on: bool):
 def qrng_set_karatsuba(ctx: Context, levels: int = 0, block_bits: int = 0, max_workspace: int = 0):
     """Block Karatsuba settings of QRNG_ALGO_GEMM_KARATSUBA (0 = chosen by the cost model)."""
     ctx.check(load_library().qrng_set_karatsuba(ctx.handle, levels, block_bits, max_workspace), "qrng_set_karatsuba")
+
+
+def qrng_set_fft32(ctx: Context, segment_bits: int = 0, terms: int = 0):
+    """FP32 segmented FFT settings (0 = chosen per shape / the proven bound)."""
+    ctx.check(load_library().qrng_set_fft32(ctx.handle, segment_bits, terms), "qrng_set_fft32")
+
+
+def qrng_fft32_terms_bound(segment_bits: int) -> int:
+    return int(load_library().qrng_fft32_terms_bound(segment_bits))
 
 
 def qrng_karatsuba_plan(ctx: Context, n: int, m: int, form: int, num_blocks: int) -> dict:

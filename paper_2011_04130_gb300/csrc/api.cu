@@ -37,36 +37,61 @@ constexpr size_t kMaxTimed = 4096;
 // Largest distance of an FFT convolution sum from its integer that still counts as exact.
 constexpr double kFftRoundGuard = 0.25;
 
-// Brackets one launch with a CUDA event pair on its stream when timing is on. With
-// record_now = false the events are handed to a launcher that records them around its main
-// kernel itself (start_event / end_event; null when timing is off), and done(false) keeps them.
+// CUDA-event timing of selected launches (qrng_set_timing): a begin/end pair on the launch's
+// stream becomes one timed entry of a kind (summed per kind by qrng_get_stats). At most kMaxTimed
+// entries are kept between two qrng_get_stats calls; later pairs are not timed.
+enum TimeKind { kTimeExtract = 0, kTimeHist = 1, kTimeBatchGraph = 2 };
+
+void timing_begin(qrng_ctx* ctx, int kind, cudaStream_t s) {
+  ctx->ev_pending = (size_t)-1;
+  if (!ctx->timing || ctx->ev_used >= kMaxTimed) return;
+  if (ctx->ev_used == ctx->ev_start.size()) {
+    cudaEvent_t a, b;
+    if (cudaEventCreate(&a) != cudaSuccess) return;
+    if (cudaEventCreate(&b) != cudaSuccess) {
+      cudaEventDestroy(a);
+      return;
+    }
+    ctx->ev_start.push_back(a);
+    ctx->ev_end.push_back(b);
+    ctx->ev_kind.push_back(0);
+  }
+  const size_t slot = ctx->ev_used;
+  if (cudaEventRecord(ctx->ev_start[slot], s) != cudaSuccess) return;
+  ctx->ev_kind[slot] = kind;
+  ctx->ev_pending = slot;
+}
+
+void timing_end(qrng_ctx* ctx, cudaStream_t s) {
+  const size_t slot = ctx->ev_pending;
+  ctx->ev_pending = (size_t)-1;
+  if (slot == (size_t)-1) return;
+  if (cudaEventRecord(ctx->ev_end[slot], s) == cudaSuccess) ctx->ev_used = slot + 1;
+}
+
+// Times one launch: the pair brackets the object's lifetime up to done().
 struct LaunchTimer {
   qrng_ctx* ctx;
   cudaStream_t s;
-  size_t slot = (size_t)-1;
-  cudaEvent_t start_event() const { return slot == (size_t)-1 ? nullptr : ctx->ev_start[slot]; }
-  cudaEvent_t end_event() const { return slot == (size_t)-1 ? nullptr : ctx->ev_end[slot]; }
-  LaunchTimer(qrng_ctx* c, cudaStream_t st, bool record_now = true) : ctx(c), s(st) {
-    if (!ctx->timing || ctx->ev_used >= kMaxTimed) return;
-    if (ctx->ev_used == ctx->ev_start.size()) {
-      cudaEvent_t a, b;
-      if (cudaEventCreate(&a) != cudaSuccess) return;
-      if (cudaEventCreate(&b) != cudaSuccess) {
-        cudaEventDestroy(a);
-        return;
-      }
-      ctx->ev_start.push_back(a);
-      ctx->ev_end.push_back(b);
-    }
-    slot = ctx->ev_used;
-    if (record_now && cudaEventRecord(ctx->ev_start[slot], s) != cudaSuccess) slot = (size_t)-1;
+  bool open;
+  LaunchTimer(qrng_ctx* c, cudaStream_t st, int kind = kTimeExtract) : ctx(c), s(st), open(true) {
+    timing_begin(ctx, kind, s);
   }
-  void done(bool record_end = true) {
-    if (slot == (size_t)-1) return;
-    if (!record_end || cudaEventRecord(ctx->ev_end[slot], s) == cudaSuccess) ctx->ev_used = slot + 1;
-    slot = (size_t)-1;
+  void done() {
+    if (open) timing_end(ctx, s);
+    open = false;
   }
 };
+
+// Hook for launchers that run their main kernel several times (one timed pair per launch).
+TimingHook extract_hook(qrng_ctx* ctx) {
+  TimingHook h;
+  if (!ctx->timing) return h;
+  h.user = ctx;
+  h.begin = [](void* u, cudaStream_t st) { timing_begin(static_cast<qrng_ctx*>(u), kTimeExtract, st); };
+  h.end = [](void* u, cudaStream_t st) { timing_end(static_cast<qrng_ctx*>(u), st); };
+  return h;
+}
 
 bool shape_ok(uint64_t n, uint64_t m, int form) {
   if (n == 0 || m == 0 || n > kMaxBlockBits) return false;
@@ -76,13 +101,32 @@ bool shape_ok(uint64_t n, uint64_t m, int form) {
 }
 
 // Bit-packed extraction (direct kernel or tensor-core GEMM) of word-aligned or arbitrary layouts.
+// FP32 segment length for a shape: the context's setting, else the cost model's best.
+int fft32_pick_log_s(const qrng_ctx* ctx, uint64_t n_t, uint64_t m, uint64_t B) {
+  if (ctx->fft32_log_s) return ctx->fft32_log_s;
+  int best = 12;
+  double best_t = 1e300;
+  for (int ls = 11; ls <= 13; ++ls) {
+    const int T = ctx->fft32_terms ? ctx->fft32_terms : fft32_terms_bound(ls);
+    const double t = fft32_model_seconds(n_t, m, B, ls, T);
+    if (t < best_t) {
+      best_t = t;
+      best = ls;
+    }
+  }
+  return best;
+}
+
 int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed,
-                    int form, uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels) {
+                    int form, uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels,
+                    int fft32_log_s = 0) {
   const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
   const uint64_t L_t = n_t + m - 1;
   const bool fft = (algo == QRNG_ALGO_FFT64 || algo == QRNG_ALGO_FFT32_SEG || algo == QRNG_ALGO_NTT);
 
-  if (!fft) {  // the bit-packed kernels read Toeplitz rows as windows of the reversed seed
+  // the bit-packed kernels read Toeplitz rows as windows of the reversed seed (the FP32 route keeps
+  // one for its exact recomputation)
+  if (!fft || algo == QRNG_ALGO_FFT32_SEG) {
     const uint64_t rev_words = kSeedFrontWords + ceil_div(L_t, 32) + kSeedBackWords;
     QRNG_CUDA(ctx, ctx->seed_rev.ensure(rev_words * 4), "seed workspace");
     QRNG_CUDA(ctx, launch_seed_reverse(seed, L_t, ctx->seed_rev.as<uint32_t>(), rev_words, s, kernels),
@@ -127,35 +171,55 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
   a.out = out_w;
   a.out_stride = mw;
   a.num_blocks = num_blocks;
+  if (algo == QRNG_ALGO_FFT32_SEG) {
+    const int log_s = fft32_log_s ? fft32_log_s : fft32_pick_log_s(ctx, n_t, m, num_blocks);
+    const int T = ctx->fft32_terms ? ctx->fft32_terms : fft32_terms_bound(log_s);
+    ctx->fft.worst = ctx->fft_worst.as<unsigned long long>() + 1;  // its own word: a trip is repaired
+    int* flag = ctx->fft32_guard.as<int>();
+    QRNG_CUDA(ctx, cudaMemsetAsync(flag, 0, sizeof(int), s), "guard clear");
+    LaunchTimer timer(ctx, s);
+    const cudaError_t e = launch_fft32_seg(a, seed, L_t, log_s, T, ctx->fft, flag, s, kernels);
+    timer.done();
+    QRNG_CUDA(ctx, e, "FP32 segmented FFT extraction");
+    // exact recomputation by the direct kernel, which returns at once unless the guard tripped
+    DirectArgs r = a;
+    r.tiles = (uint32_t)ceil_div(m, (uint64_t)direct_outputs_per_warp());
+    r.splits = 1;
+    r.words_per_split = a.nw_t;
+    r.guard = flag;
+    r.repairs = reinterpret_cast<unsigned long long*>(ctx->fft32_guard.as<char>() + 8);
+    QRNG_CUDA(ctx, launch_direct(r, s, kernels), "FP32 route recomputation");
+    ctx->last_fft32_log_s = log_s;
+    if (!out_direct)
+      QRNG_CUDA(ctx, launch_pack_blocks(out_w, mw, m, num_blocks, out, s, kernels), "output pack");
+    return QRNG_OK;
+  }
   if (fft) {
     ctx->fft.worst = ctx->fft_worst.as<unsigned long long>();
     LaunchTimer timer(ctx, s);
     const cudaError_t e = algo == QRNG_ALGO_FFT64 ? launch_fft64(a, seed, L_t, ctx->fft, s, kernels)
-                          : algo == QRNG_ALGO_NTT ? launch_ntt(a, seed, L_t, ctx->fft, s, kernels)
-                                                  : launch_fft32_seg(a, seed, L_t, ctx->fft, s, kernels);
+                                                  : launch_ntt(a, seed, L_t, ctx->fft, s, kernels);
     timer.done();
-    QRNG_CUDA(ctx, e, algo == QRNG_ALGO_FFT64 ? "FP64 FFT extraction"
-                      : algo == QRNG_ALGO_NTT ? "number-theoretic transform extraction"
-                                              : "FP32 segmented FFT extraction");
+    QRNG_CUDA(ctx, e, algo == QRNG_ALGO_FFT64 ? "FP64 FFT extraction" : "number-theoretic transform extraction");
     if (!out_direct)
       QRNG_CUDA(ctx, launch_pack_blocks(out_w, mw, m, num_blocks, out, s, kernels), "output pack");
     return QRNG_OK;
   }
   if (gemm) {
     QRNG_CUDA(ctx, ctx->dev_err.ensure(sizeof(int)), "error word");
-    LaunchTimer timer(ctx, s, algo != QRNG_ALGO_GEMM_KARATSUBA);
     const int fault = ctx->fault;
     ctx->fault = 0;  // one-shot
     if (algo == QRNG_ALGO_GEMM_KARATSUBA) {
       const KaraPlan plan = karatsuba_plan(n_t, m, num_blocks, ctx->num_sms, ctx->kara_levels, ctx->kara_h,
                                            ctx->kara_workspace);
       if (plan.levels == 0) return fail(ctx, QRNG_ENOTSUP, "qrng_toeplitz_extract: no block Karatsuba plan fits");
+      // one timed pair around each pass's product kernel
       QRNG_CUDA(ctx,
                 launch_gemm_karatsuba(a, plan, ctx->kara, ctx->dev_err.as<int>(), fault, ctx->num_sms, s, kernels,
-                                      timer.start_event(), timer.end_event()),
+                                      extract_hook(ctx)),
                 "block Karatsuba extraction");
-      timer.done(false);  // the launcher recorded the pair around its product kernel
     } else {
+      LaunchTimer timer(ctx, s);
       QRNG_CUDA(ctx,
                 algo == QRNG_ALGO_GEMM_FP4_PAIR
                     ? launch_gemm_pair(a, ctx->dev_err.as<int>(), fault, ctx->num_sms, s, kernels)
@@ -201,8 +265,10 @@ int minentropy_dev(qrng_ctx* ctx, const void* samples, uint64_t count, int bits,
   QRNG_CUDA(ctx, ctx->hist.ensure((K + 1) * sizeof(unsigned long long)), "histogram workspace");
   QRNG_CUDA(ctx, ctx->result.ensure(sizeof(DevHminResult)), "result workspace");
   if (thr >= (1ull << 53)) {
+    LaunchTimer timer(ctx, s, kTimeHist);
     QRNG_CUDA(ctx, launch_histogram(samples, count, bits, ctx->hist.as<unsigned long long>(), ctx->num_sms, s, &kernels),
               "histogram kernel");
+    timer.done();
   } else {
     QRNG_CUDA(ctx, launch_histogram_sampled(samples, count, bits, thr, sel_seed, ctx->hist.as<unsigned long long>(),
                                             ctx->num_sms, s, &kernels),
@@ -283,9 +349,8 @@ double model_seconds(const qrng_ctx* ctx, int algo, uint64_t n_t, uint64_t m, ui
       return (double)B * P * lg * 0.9e-12 + 6e-5;
     }
     case QRNG_ALGO_FFT32_SEG: {
-      const double S = (double)fft32_segment(), N = 2 * S;
-      const double pairs = (double)B * (double)ceil_div(m, (uint64_t)S) * ceil((double)ceil_div(n_t, (uint64_t)S) / 2);
-      return pairs * 10.0 * N * log2(N) / 1.5e13 + 2e-5;
+      const int ls = fft32_pick_log_s(ctx, n_t, m, B);
+      return fft32_model_seconds(n_t, m, B, ls, ctx->fft32_terms ? ctx->fft32_terms : fft32_terms_bound(ls));
     }
   }
   return 1e30;
@@ -310,28 +375,44 @@ bool algo_applicable(int algo, uint64_t n_t, uint64_t m, uint64_t B) {
 }
 
 int extract_one(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
-                uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels) {
-  return extract_bitwise(ctx, algo, raw, n, m, seed, form, num_blocks, out, s, kernels);
+                uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels, int fft32_log_s = 0) {
+  return extract_bitwise(ctx, algo, raw, n, m, seed, form, num_blocks, out, s, kernels, fft32_log_s);
 }
 
 // QRNG_ALGO_AUTO: the candidates within 4x of the best modelled time are each run once on the
 // call's own data (they give identical bits), timed with CUDA events, and the fastest is kept for
-// this shape; later calls of the shape use it directly.
+// this shape; later calls of the shape use it directly. The FP32 route is a candidate once per
+// segment length (unless the context fixes it), so the segment length is tuned with it.
 int choose_auto(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
-                uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels, int* chosen, bool* done) {
+                uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels, int* chosen, int* chosen_log_s,
+                bool* done) {
   const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
-  const int algos[8] = {QRNG_ALGO_DIRECT, QRNG_ALGO_GEMM_TC,     QRNG_ALGO_GEMM_FP4,  QRNG_ALGO_GEMM_FP4_PAIR,
-                        QRNG_ALGO_GEMM_KARATSUBA, QRNG_ALGO_NTT, QRNG_ALGO_FFT64, QRNG_ALGO_FFT32_SEG};
-  double best_model = 1e30;
-  int best_algo = QRNG_ALGO_DIRECT;
+  struct Cand {
+    int algo, log_s;
+    double model;
+  };
+  std::vector<Cand> cands;
+  const int algos[7] = {QRNG_ALGO_DIRECT, QRNG_ALGO_GEMM_TC, QRNG_ALGO_GEMM_FP4, QRNG_ALGO_GEMM_FP4_PAIR,
+                        QRNG_ALGO_GEMM_KARATSUBA, QRNG_ALGO_NTT, QRNG_ALGO_FFT64};
   for (int a : algos)
-    if (algo_applicable(a, n_t, m, num_blocks)) {
-      const double t = model_seconds(ctx, a, n_t, m, num_blocks);
-      if (t < best_model) { best_model = t; best_algo = a; }
+    if (algo_applicable(a, n_t, m, num_blocks)) cands.push_back({a, 0, model_seconds(ctx, a, n_t, m, num_blocks)});
+  for (int ls = 11; ls <= 13; ++ls) {
+    if (ctx->fft32_log_s && ctx->fft32_log_s != ls) continue;
+    const int T = ctx->fft32_terms ? ctx->fft32_terms : fft32_terms_bound(ls);
+    cands.push_back({QRNG_ALGO_FFT32_SEG, ls, fft32_model_seconds(n_t, m, num_blocks, ls, T)});
+  }
+  double best_model = 1e300;
+  Cand best_c{QRNG_ALGO_DIRECT, 0, 0.0};
+  for (const Cand& c : cands)
+    if (c.model < best_model) {
+      best_model = c.model;
+      best_c = c;
     }
   *done = false;
+  *chosen_log_s = 0;
   if (!ctx->autotune) {
-    *chosen = best_algo;
+    *chosen = best_c.algo;
+    *chosen_log_s = best_c.log_s;
     return QRNG_OK;
   }
   uint32_t lb = 0;
@@ -339,32 +420,44 @@ int choose_auto(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const
   const qrng_ctx::TuneKey key{n, m, lb, form};
   for (const auto& e : ctx->tuned)
     if (e.first == key) {
-      *chosen = e.second;
+      *chosen = e.second.algo;
+      *chosen_log_s = e.second.fft32_log_s;
       return QRNG_OK;
     }
-  int best = -1;
+  int best = -1, best_ls = 0;
   float best_ms = 0.f;
-  for (int a : algos) {
-    if (!algo_applicable(a, n_t, m, num_blocks) || model_seconds(ctx, a, n_t, m, num_blocks) > 4.0 * best_model) continue;
+  bool last_ok = true;
+  for (const Cand& c : cands) {
+    if (c.model > 4.0 * best_model) continue;
     cudaEvent_t e0, e1;
     QRNG_CUDA(ctx, cudaEventCreate(&e0), "autotune event");
     QRNG_CUDA(ctx, cudaEventCreate(&e1), "autotune event");
     QRNG_CUDA(ctx, cudaEventRecord(e0, s), "autotune event");
-    const int st = extract_one(ctx, a, raw, n, m, seed, form, num_blocks, out, s, kernels);
+    const int st = extract_one(ctx, c.algo, raw, n, m, seed, form, num_blocks, out, s, kernels, c.log_s);
     QRNG_CUDA(ctx, cudaEventRecord(e1, s), "autotune event");
     QRNG_CUDA(ctx, cudaEventSynchronize(e1), "autotune wait");
     float ms = 0.f;
     cudaEventElapsedTime(&ms, e0, e1);
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    last_ok = (st == QRNG_OK);
     if (st == QRNG_OK && (best < 0 || ms < best_ms)) {
-      best = a;
+      best = c.algo;
+      best_ls = c.log_s;
       best_ms = ms;
     }
   }
   if (best < 0) best = QRNG_ALGO_DIRECT;
-  ctx->tuned.push_back({key, best});
+  if (best != QRNG_ALGO_FFT32_SEG) best_ls = 0;
+  // every candidate that succeeds writes the same bits; a failed last candidate may have left a
+  // partial output, so the winner runs once more then
+  if (!last_ok) {
+    const int st = extract_one(ctx, best, raw, n, m, seed, form, num_blocks, out, s, kernels, best_ls);
+    if (st != QRNG_OK) return st;
+  }
+  ctx->tuned.push_back({key, {best, best_ls}});
   *chosen = best;
+  *chosen_log_s = best_ls;
   *done = true;  // the output already holds the result (every candidate writes the same bits)
   return QRNG_OK;
 }
@@ -374,10 +467,10 @@ int extract_dispatch(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, 
   uint32_t kernels = 0;
   int st;
   const uint64_t n_t = (form == QRNG_FORM_MODIFIED) ? n - m : n;
-  int used = algo;
+  int used = algo, used_log_s = 0;
   if (used == QRNG_ALGO_AUTO) {
     bool done = false;
-    st = choose_auto(ctx, raw, n, m, seed, form, num_blocks, out, s, &kernels, &used, &done);
+    st = choose_auto(ctx, raw, n, m, seed, form, num_blocks, out, s, &kernels, &used, &used_log_s, &done);
     if (st != QRNG_OK) return st;
     if (done) {
       ctx->stats.kernels_launched += kernels;
@@ -392,7 +485,7 @@ int extract_dispatch(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, 
       break;
     case QRNG_ALGO_FFT64:
     case QRNG_ALGO_FFT32_SEG:
-      st = extract_bitwise(ctx, used, raw, n, m, seed, form, num_blocks, out, s, &kernels);
+      st = extract_bitwise(ctx, used, raw, n, m, seed, form, num_blocks, out, s, &kernels, used_log_s);
       break;
     case QRNG_ALGO_NTT:
       if (fft64_length(n_t, m) > (1ull << 27))
@@ -439,10 +532,12 @@ void drop_all_graphs(qrng_ctx* ctx) {
   ctx->graphs.clear();
 }
 
-// Grows a batch buffer; any move invalidates the graphs that captured the old address.
+// Grows a buffer a batch graph uses; any move invalidates the graphs that captured the old address.
 cudaError_t ensure_batch(qrng_ctx* ctx, DevBuf& b, size_t bytes) {
   if (bytes <= b.cap) return cudaSuccess;
   cudaError_t e = cudaStreamSynchronize(ctx->capture_stream);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceSynchronize();  // a replay may still read the old buffer
   if (e != cudaSuccess) return e;
   drop_all_graphs(ctx);
   ++ctx->batch_generation;
@@ -450,93 +545,389 @@ cudaError_t ensure_batch(qrng_ctx* ctx, DevBuf& b, size_t bytes) {
 }
 
 constexpr size_t kMaxGraphs = 4;
+constexpr uint64_t kFft32BatchBudget = 1ull << 30;  // bytes of FP32 spectra per group
 
-// Batch routing: a request goes to the transform route when its modelled time there is below the
-// direct kernel's (the number-theoretic transform costs about P log2 P x 1.3 ps per request, three
-// transforms of the P-point padded seed and raw bits; the direct kernel m n_t / 5.6e14 s).
-bool batch_prefers_ntt(uint64_t n_t, uint64_t m) {
+// ---- uneven batches ----
+//
+// A call is planned on the host: every request gets a route (the persistent direct kernel, or one
+// of the batched circulant routes: number-theoretic transform, FP64 FFT, FP32 segmented FFT);
+// direct requests come first in the device table (largest work first), then the transform
+// requests in groups (one transform length, or one FP32 segment length, per group, within a
+// workspace budget). One launch sequence runs the plan: table upload, staging of the direct
+// requests, every transform group, the persistent kernel, and the merge of all outputs into the
+// callers' bit offsets. The sequence is captured once into a CUDA graph cached on the context, so
+// every call is one graph replay; the transform workspace belongs to the batch path alone and is
+// sized before capture, and each group recomputes its twiddle tables inside the graph.
+
+struct BatchGroup {
+  uint64_t begin, end;  // device-table range
+  int route;
+  uint64_t P;           // transform length (NTT, FP64)
+  int log_s;            // FP32 segment length
+  uint64_t max_mw, spec_items, mac_ctas, spec_rows;
+};
+
+struct BatchPlan {
+  std::vector<BatchReq> reqs;  // device order
+  std::vector<BatchGroup> groups;
+  uint64_t raw_total = 0, rev_total = 0, out_total = 0, items = 0, dst_total = 0, direct_out = 0;
+  size_t buf0 = 0, buf1 = 0, spec = 0, ntt_tw = 0, tw = 0, tw32 = 0;  // transform workspace needs
+  uint64_t routes[4] = {0, 0, 0, 0};
+};
+
+uint64_t ilog2_ceil(uint64_t x) {
+  uint64_t l = 0;
+  while ((1ull << l) < x) ++l;
+  return l;
+}
+
+// Modelled seconds of one request on a route (prunes the autotuner's candidates; the choice when
+// autotuning is off). Rates measured on GB300 for the batched kernels.
+double route_model(int route, uint64_t n_t, uint64_t m, int log_s) {
   const uint64_t P = fft64_length(n_t, m);
-  if (P > (1ull << 27)) return false;
   const double lg = log2((double)P);
-  return (double)P * lg * 1.3e-12 < (double)m * (double)n_t / 5.6e14;
+  switch (route) {
+    case kRouteDirect:
+      return (double)m * (double)n_t / 5.6e14 + 2e-8;
+    case kRouteNtt:
+      return P > (1ull << 27) ? 1e30 : (double)P * lg * 1.3e-12;
+    case kRouteFft64:
+      return P > (1ull << 27) ? 1e30 : (double)P * lg * 1.6e-11;
+    case kRouteFft32:
+      return fft32_model_seconds(n_t, m, 1, log_s, fft32_terms_bound(log_s)) - 2e-5;
+  }
+  return 1e30;
+}
+
+BatchReq base_request(const qrng_request& r) {
+  BatchReq q{};
+  q.raw = r.raw;
+  q.raw_bit_off = r.raw_bit_off;
+  q.n = r.n;
+  q.m = r.m;
+  q.seed = r.seed;
+  q.form = r.form;
+  q.out = r.out;
+  q.out_bit_off = r.out_bit_off;
+  q.n_t = r.form == QRNG_FORM_MODIFIED ? r.n - r.m : r.n;
+  q.L_t = q.n_t + r.m - 1;
+  q.nw_t = (uint32_t)ceil_div(q.n_t, 32);
+  q.tail_mask = (q.n_t % 32) ? ((1u << (q.n_t % 32)) - 1u) : 0xffffffffu;
+  q.mw = (uint32_t)ceil_div(r.m, 32);
+  q.id_off = (uint32_t)(r.n - r.m);
+  const uint64_t first = (reinterpret_cast<uintptr_t>(r.out) * 8 + r.out_bit_off);
+  q.dst_word0 = first / 32;
+  q.dst_words = (first + r.m - 1) / 32 - q.dst_word0 + 1;
+  return q;
+}
+
+// Plan of the requests idx[...] (indices into reqs) with routes route[i] and FP32 segment lengths log_s[i].
+BatchPlan make_plan(const qrng_request* reqs, const std::vector<uint64_t>& idx, const std::vector<int>& route,
+                    const std::vector<int>& log_s) {
+  BatchPlan p;
+  std::vector<BatchReq> t;
+  std::vector<uint64_t> key;  // group key of transform requests
+  t.reserve(idx.size());
+  for (uint64_t i : idx) {
+    BatchReq q = base_request(reqs[i]);
+    q.route = route[i];
+    if (q.route == kRouteDirect) {
+      q.tiles = (uint32_t)ceil_div(q.m, (uint64_t)direct_outputs_per_warp());
+      q.splits = (uint32_t)ceil_div(q.nw_t, kBatchWordsPerSplit);
+      q.raw_words = ceil_div(q.n, 32);
+      q.rev_words = kSeedFrontWords + ceil_div(q.L_t, 32) + kSeedBackWords;
+    } else if (q.route == kRouteFft32) {
+      const uint64_t S = 1ull << log_s[i];
+      q.seg_ns = (uint32_t)ceil_div(q.n_t, S);
+      q.seg_nq = (uint32_t)ceil_div(q.m, S);
+    }
+    t.push_back(q);
+    key.push_back(q.route == kRouteFft32 ? (uint64_t)log_s[i] : fft64_length(q.n_t, q.m));
+  }
+  std::vector<uint64_t> order(t.size());
+  for (uint64_t k = 0; k < order.size(); ++k) order[k] = k;
+  std::stable_sort(order.begin(), order.end(), [&](uint64_t x, uint64_t y) {
+    const bool dx = t[x].route == kRouteDirect, dy = t[y].route == kRouteDirect;
+    if (dx != dy) return dx;                                         // direct requests first
+    if (!dx && t[x].route != t[y].route) return t[x].route < t[y].route;
+    if (!dx && key[x] != key[y]) return key[x] > key[y];              // transforms grouped
+    return t[x].m * t[x].n_t > t[y].m * t[y].n_t;                     // largest work first
+  });
+  p.reqs.resize(t.size());
+  for (uint64_t k = 0; k < order.size(); ++k) {
+    BatchReq q = t[order[k]];
+    ++p.routes[q.route];
+    q.raw_stage_off = p.raw_total;
+    p.raw_total += q.raw_words;
+    q.rev_off = p.rev_total;
+    p.rev_total += q.rev_words;
+    q.out_stage_off = p.out_total;
+    p.out_total += q.mw;
+    q.item_begin = p.items;
+    p.items += (uint64_t)q.tiles * q.splits;
+    q.dst_begin = p.dst_total;
+    p.dst_total += q.dst_words;
+    if (q.route == kRouteDirect) p.direct_out = p.out_total;
+    p.reqs[k] = q;
+  }
+  // transform groups within the workspace budget
+  for (uint64_t k = 0; k < p.reqs.size();) {
+    BatchReq& q0 = p.reqs[k];
+    if (q0.route == kRouteDirect) {
+      ++k;
+      continue;
+    }
+    BatchGroup g{};
+    g.begin = k;
+    g.route = q0.route;
+    const uint64_t gk = key[order[k]];
+    if (g.route == kRouteFft32) g.log_s = (int)gk;
+    else g.P = gk;
+    const uint64_t S = g.route == kRouteFft32 ? (1ull << g.log_s) : 0;
+    const int qt = g.route == kRouteFft32 ? fft32_batch_tiles(g.log_s) : 1;
+    uint64_t e = k, bytes = 0;
+    while (e < p.reqs.size() && p.reqs[e].route == g.route && key[order[e]] == gk) {
+      BatchReq& q = p.reqs[e];
+      uint64_t need;
+      if (g.route == kRouteFft32) need = ((uint64_t)q.seg_nq + 2ull * q.seg_ns - 1) * S * 8;
+      else if (g.route == kRouteNtt) need = 2 * g.P * 4;
+      else need = 2 * g.P * 16;
+      const uint64_t budget = g.route == kRouteFft32 ? kFft32BatchBudget : kFftWorkspaceBytes;
+      if (e > k && bytes + need > budget) break;
+      if (g.route == kRouteFft32) {
+        q.spec_row = g.spec_rows;
+        q.spec_item_begin = g.spec_items;
+        q.mac_cta_begin = g.mac_ctas;
+        const uint64_t rows = (uint64_t)q.seg_nq + 2ull * q.seg_ns - 1;
+        g.spec_rows += rows;
+        g.spec_items += rows;
+        g.mac_ctas += ceil_div(q.seg_nq, (uint64_t)qt);
+      }
+      if (q.mw > g.max_mw) g.max_mw = q.mw;
+      bytes += need;
+      ++e;
+    }
+    g.end = e;
+    const uint64_t nr = e - k;
+    if (g.route == kRouteNtt) {
+      p.buf0 = std::max<size_t>(p.buf0, 2 * nr * g.P * 4);
+      p.buf1 = std::max<size_t>(p.buf1, nr * (g.P / 8));
+      p.ntt_tw = std::max<size_t>(p.ntt_tw, (g.P / 2) * 4);
+    } else if (g.route == kRouteFft64) {
+      p.buf0 = std::max<size_t>(p.buf0, nr * g.P * 16);
+      p.buf1 = std::max<size_t>(p.buf1, nr * g.P * 16);
+      p.tw = std::max<size_t>(p.tw, (g.P / 2) * 16);
+    } else {
+      p.spec = std::max<size_t>(p.spec, g.spec_rows * S * 8);
+      p.tw32 = std::max<size_t>(p.tw32, S * 8);
+    }
+    p.groups.push_back(g);
+    k = e;
+  }
+  return p;
+}
+
+// Buffers of a plan (grown before any capture; a move drops the cached graphs).
+int ensure_plan(qrng_ctx* ctx, const BatchPlan& p) {
+  FftWorkspace& w = ctx->batch_fft;
+  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_meta, p.reqs.size() * sizeof(BatchReq)), "batch table workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_raw, (p.raw_total ? p.raw_total : 1) * 4), "batch raw workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_rev, (p.rev_total ? p.rev_total : 1) * 4), "batch seed workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_out, (p.out_total ? p.out_total : 1) * 4), "batch output workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_counter, sizeof(unsigned long long)), "batch counter");
+  QRNG_CUDA(ctx, ensure_batch(ctx, w.buf0, p.buf0 ? p.buf0 : 1), "batch transform workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, w.buf1, p.buf1 ? p.buf1 : 1), "batch transform workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, w.spec, p.spec ? p.spec : 1), "batch spectra workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, w.ntt_tw, p.ntt_tw ? p.ntt_tw : 1), "batch twiddle workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, w.tw, p.tw ? p.tw : 1), "batch twiddle workspace");
+  QRNG_CUDA(ctx, ensure_batch(ctx, w.tw32, p.tw32 ? p.tw32 : 1), "batch twiddle workspace");
+  for (const BatchGroup& g : p.groups)
+    if (g.route == kRouteNtt && !w.ntt_stage.p) {
+      // the NTT's constant stage table, once, outside any capture (its buffer never moves)
+      uint32_t k = 0;
+      QRNG_CUDA(ctx, ntt_prepare(w, g.P, ctx->capture_stream, &k), "batch NTT tables");
+      QRNG_CUDA(ctx, cudaStreamSynchronize(ctx->capture_stream), "batch NTT tables");
+    }
+  return QRNG_OK;
+}
+
+// The launch sequence of a plan on stream cs; its request table is uploaded from pinned `meta_host`.
+cudaError_t run_plan(qrng_ctx* ctx, const BatchPlan& p, const void* meta_host, bool merge, cudaStream_t cs,
+                     uint32_t* kernels) {
+  const uint32_t count = (uint32_t)p.reqs.size();
+  BatchReq* meta = ctx->batch_meta.as<BatchReq>();
+  cudaError_t e = cudaMemcpyAsync(meta, meta_host, count * sizeof(BatchReq), cudaMemcpyHostToDevice, cs);
+  if (e == cudaSuccess) e = cudaMemsetAsync(ctx->batch_counter.p, 0, sizeof(unsigned long long), cs);
+  if (e == cudaSuccess && p.direct_out) e = cudaMemsetAsync(ctx->batch_out.p, 0, p.direct_out * 4, cs);
+  if (e == cudaSuccess && p.raw_total)
+    e = launch_batch_layout(meta, count, p.raw_total, p.rev_total, ctx->batch_raw.as<uint32_t>(),
+                            ctx->batch_rev.as<uint32_t>(), cs, kernels);
+  FftWorkspace& w = ctx->batch_fft;
+  w.worst = ctx->fft_worst.as<unsigned long long>();  // a batch trip is reported by qrng_synchronize
+  for (const BatchGroup& g : p.groups) {
+    if (e != cudaSuccess) break;
+    const uint64_t nr = g.end - g.begin;
+    if (g.route == kRouteNtt) {
+      w.ntt_P = 0;  // the group's twiddles are computed inside the sequence
+      e = launch_ntt_batch(meta + g.begin, nr, g.P, g.max_mw, w, ctx->batch_out.as<uint32_t>(), cs, kernels);
+    } else if (g.route == kRouteFft64) {
+      w.tw_P = 0;
+      e = launch_fft64_batch(meta + g.begin, nr, g.P, g.max_mw, w, ctx->batch_out.as<uint32_t>(), cs, kernels);
+    } else {
+      w.tw32_S = 0;
+      e = launch_fft32_batch(meta + g.begin, nr, g.spec_items, g.mac_ctas, g.log_s, fft32_terms_bound(g.log_s), w,
+                             ctx->batch_out.as<uint32_t>(), cs, kernels);
+    }
+  }
+  if (e == cudaSuccess && p.items)
+    e = launch_batch_direct(meta, count, p.items, ctx->batch_raw.as<uint32_t>(), ctx->batch_rev.as<uint32_t>(),
+                            ctx->batch_out.as<uint32_t>(), ctx->batch_counter.as<unsigned long long>(), ctx->num_sms,
+                            cs, kernels);
+  if (e == cudaSuccess && merge)
+    e = launch_batch_pack(meta, count, p.dst_total, ctx->batch_out.as<uint32_t>(), cs, kernels);
+  return e;
+}
+
+// Pinned host staging of at least `bytes` for a tuner's table.
+int tune_staging(qrng_ctx* ctx, size_t bytes) {
+  if (bytes <= ctx->tune_host_cap) return QRNG_OK;
+  if (ctx->tune_host) cudaFreeHost(ctx->tune_host);
+  ctx->tune_host = nullptr;
+  ctx->tune_host_cap = 0;
+  QRNG_CUDA(ctx, cudaMallocHost(&ctx->tune_host, bytes), "pinned tuner table");
+  ctx->tune_host_cap = bytes;
+  return QRNG_OK;
+}
+
+// QRNG_ALGO_AUTO: the route of each shape class (transform length P). A class seen for the first
+// time has the routes the cost model keeps (within 4x of its best) each run once on the class's
+// requests of this call, timed with CUDA events; the fastest is kept on the context.
+int tune_classes(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, std::vector<int>& route,
+                 std::vector<int>& log_s) {
+  std::vector<uint64_t> cls(count);
+  for (uint64_t i = 0; i < count; ++i) {
+    const BatchReq q = base_request(reqs[i]);
+    cls[i] = fft64_length(q.n_t, q.m);
+  }
+  std::vector<uint64_t> todo;
+  for (uint64_t i = 0; i < count; ++i) {
+    bool known = false;
+    for (const auto& bt : ctx->batch_tuned) known = known || bt.P == cls[i];
+    for (uint64_t c : todo) known = known || c == cls[i];
+    if (!known) todo.push_back(cls[i]);
+  }
+  cudaStream_t cs = ctx->capture_stream;
+  for (uint64_t P : todo) {
+    std::vector<uint64_t> members;
+    for (uint64_t i = 0; i < count; ++i)
+      if (cls[i] == P) members.push_back(i);
+    struct Cand {
+      int route, log_s;
+      double model;
+    };
+    std::vector<Cand> cands;
+    for (int r = kRouteDirect; r <= kRouteFft32; ++r) {
+      for (int ls = 11; ls <= (r == kRouteFft32 ? 13 : 11); ++ls) {
+        double t = 0;
+        for (uint64_t i : members) {
+          const BatchReq q = base_request(reqs[i]);
+          t += route_model(r, q.n_t, q.m, ls);
+        }
+        cands.push_back({r, r == kRouteFft32 ? ls : 0, t});
+      }
+    }
+    double best_model = 1e300;
+    for (const Cand& c : cands) best_model = std::min(best_model, c.model);
+    int best_r = kRouteDirect, best_ls = 0;
+    float best_ms = -1.f;
+    for (const Cand& c : cands) {
+      if (c.model > 4.0 * best_model || c.model >= 1e29) continue;
+      std::vector<int> r2(count, c.route), l2(count, c.log_s);
+      const BatchPlan sub = make_plan(reqs, members, r2, l2);
+      int st = ensure_plan(ctx, sub);
+      if (st) return st;
+      st = tune_staging(ctx, sub.reqs.size() * sizeof(BatchReq));
+      if (st) return st;
+      QRNG_CUDA(ctx, cudaStreamSynchronize(cs), "batch tuner");
+      memcpy(ctx->tune_host, sub.reqs.data(), sub.reqs.size() * sizeof(BatchReq));
+      cudaEvent_t e0, e1;
+      QRNG_CUDA(ctx, cudaEventCreate(&e0), "batch tuner event");
+      QRNG_CUDA(ctx, cudaEventCreate(&e1), "batch tuner event");
+      uint32_t k = 0;
+      QRNG_CUDA(ctx, cudaEventRecord(e0, cs), "batch tuner event");
+      const cudaError_t e = run_plan(ctx, sub, ctx->tune_host, false, cs, &k);
+      QRNG_CUDA(ctx, cudaEventRecord(e1, cs), "batch tuner event");
+      QRNG_CUDA(ctx, cudaEventSynchronize(e1), "batch tuner wait");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      ctx->stats.kernels_launched += k;
+      if (e == cudaSuccess && (best_ms < 0 || ms < best_ms)) {
+        best_ms = ms;
+        best_r = c.route;
+        best_ls = c.log_s;
+      }
+    }
+    ctx->batch_tuned.push_back({P, best_r, best_ls});
+  }
+  for (uint64_t i = 0; i < count; ++i)
+    for (const auto& bt : ctx->batch_tuned)
+      if (bt.P == cls[i]) {
+        route[i] = bt.route;
+        log_s[i] = bt.log_s;
+      }
+  return QRNG_OK;
 }
 
 int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int algo, cudaStream_t s) {
-  // Request table in device layout: direct requests first (largest work first), then the requests
-  // routed to the transform, grouped by transform length.
-  std::vector<BatchReq> t(count);
-  std::vector<uint64_t> order(count);
-  std::vector<uint64_t> tlen(count, 0);  // transform length, 0 = direct
+  std::vector<int> route(count, kRouteDirect), log_s(count, 0);
   for (uint64_t i = 0; i < count; ++i) {
-    const qrng_request& r = reqs[i];
-    BatchReq& q = t[i];
-    q = BatchReq{};
-    q.raw = r.raw;
-    q.raw_bit_off = r.raw_bit_off;
-    q.n = r.n;
-    q.m = r.m;
-    q.seed = r.seed;
-    q.form = r.form;
-    q.out = r.out;
-    q.out_bit_off = r.out_bit_off;
-    q.n_t = r.form == QRNG_FORM_MODIFIED ? r.n - r.m : r.n;
-    q.L_t = q.n_t + r.m - 1;
-    q.nw_t = (uint32_t)ceil_div(q.n_t, 32);
-    q.tail_mask = (q.n_t % 32) ? ((1u << (q.n_t % 32)) - 1u) : 0xffffffffu;
-    q.mw = (uint32_t)ceil_div(r.m, 32);
-    q.tiles = (uint32_t)ceil_div(r.m, (uint64_t)direct_outputs_per_warp());
-    q.splits = (uint32_t)ceil_div(q.nw_t, kBatchWordsPerSplit);
-    q.id_off = (uint32_t)(r.n - r.m);
-    q.raw_words = ceil_div(r.n, 32);
-    q.rev_words = kSeedFrontWords + ceil_div(q.L_t, 32) + kSeedBackWords;
-    const uint64_t first = (reinterpret_cast<uintptr_t>(r.out) * 8 + r.out_bit_off);
-    q.dst_word0 = first / 32;
-    q.dst_words = (first + r.m - 1) / 32 - q.dst_word0 + 1;
-    const bool ntt = ((algo == QRNG_ALGO_NTT || algo == QRNG_ALGO_FFT64) && fft64_length(q.n_t, r.m) <= (1ull << 27)) ||
-                     (algo == QRNG_ALGO_AUTO && batch_prefers_ntt(q.n_t, r.m));
-    if (ntt) {  // no direct work, no staging of raw bits or reversed seed
-      tlen[i] = fft64_length(q.n_t, r.m);
-      q.tiles = 0;
-      q.raw_words = 0;
-      q.rev_words = 0;
+    const BatchReq q = base_request(reqs[i]);
+    const bool fits = fft64_length(q.n_t, q.m) <= (1ull << 27);
+    if (algo == QRNG_ALGO_NTT && fits) route[i] = kRouteNtt;
+    else if (algo == QRNG_ALGO_FFT64 && fits) route[i] = kRouteFft64;
+    else if (algo == QRNG_ALGO_FFT32_SEG) {
+      route[i] = kRouteFft32;
+      int best = 12;
+      double bt = 1e300;
+      for (int ls = 11; ls <= 13; ++ls) {
+        if (ctx->fft32_log_s && ctx->fft32_log_s != ls) continue;
+        const double t = route_model(kRouteFft32, q.n_t, q.m, ls);
+        if (t < bt) {
+          bt = t;
+          best = ls;
+        }
+      }
+      log_s[i] = best;
     }
-    order[i] = i;
   }
-  std::stable_sort(order.begin(), order.end(), [&](uint64_t x, uint64_t y) {
-    if ((tlen[x] != 0) != (tlen[y] != 0)) return tlen[x] == 0;        // direct requests first
-    if (tlen[x] != tlen[y]) return tlen[x] > tlen[y];                  // transforms grouped by length
-    return t[x].m * t[x].n_t > t[y].m * t[y].n_t;                      // largest work first
-  });
-  std::vector<BatchReq> sorted(count);
-  uint64_t raw_total = 0, rev_total = 0, out_total = 0, items = 0, dst_total = 0, direct_out = 0;
-  uint64_t first_ntt = count;
-  for (uint64_t k = 0; k < count; ++k) {
-    BatchReq q = t[order[k]];
-    if (tlen[order[k]] != 0 && first_ntt == count) {
-      first_ntt = k;
-      direct_out = out_total;  // the direct requests' staging is [0, direct_out)
+  if (algo == QRNG_ALGO_AUTO) {
+    if (ctx->autotune) {
+      const int st = tune_classes(ctx, reqs, count, route, log_s);
+      if (st) return st;
+    } else {
+      for (uint64_t i = 0; i < count; ++i) {  // the cost model alone
+        const BatchReq q = base_request(reqs[i]);
+        double bt = 1e300;
+        for (int r = kRouteDirect; r <= kRouteFft32; ++r)
+          for (int ls = 11; ls <= (r == kRouteFft32 ? 13 : 11); ++ls) {
+            const double t = route_model(r, q.n_t, q.m, ls);
+            if (t < bt) {
+              bt = t;
+              route[i] = r;
+              log_s[i] = r == kRouteFft32 ? ls : 0;
+            }
+          }
+      }
     }
-    q.raw_stage_off = raw_total;
-    raw_total += q.raw_words;
-    q.rev_off = rev_total;
-    rev_total += q.rev_words;
-    q.out_stage_off = out_total;
-    out_total += q.mw;
-    q.item_begin = items;
-    items += (uint64_t)q.tiles * q.splits;
-    q.dst_begin = dst_total;
-    dst_total += q.dst_words;
-    sorted[k] = q;
   }
-  if (first_ntt == count) direct_out = out_total;
-
-  const uint64_t key = fnv1a(sorted.data(), sorted.size() * sizeof(BatchReq), fnv1a(&count, sizeof(count)));
-  uint32_t kernels = 0;
-  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_meta, count * sizeof(BatchReq)), "batch table workspace");
-  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_raw, (raw_total ? raw_total : 1) * 4), "batch raw workspace");
-  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_rev, (rev_total ? rev_total : 1) * 4), "batch seed workspace");
-  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_out, out_total * 4), "batch output workspace");
-  QRNG_CUDA(ctx, ensure_batch(ctx, ctx->batch_counter, sizeof(unsigned long long)), "batch counter");
+  std::vector<uint64_t> all(count);
+  for (uint64_t i = 0; i < count; ++i) all[i] = i;
+  const BatchPlan plan = make_plan(reqs, all, route, log_s);
+  const uint64_t key = fnv1a(plan.reqs.data(), plan.reqs.size() * sizeof(BatchReq), fnv1a(&count, sizeof(count)));
+  int st = ensure_plan(ctx, plan);
+  if (st) return st;
 
   qrng_ctx::BatchGraph* hit = nullptr;
   for (auto& g : ctx->graphs)
@@ -553,24 +944,14 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int a
     qrng_ctx::BatchGraph g;
     g.key = key;
     g.generation = ctx->batch_generation;
+    for (int r = 0; r < 4; ++r) g.routes[r] = plan.routes[r];
     QRNG_CUDA(ctx, cudaMallocHost(&g.meta_host, count * sizeof(BatchReq)), "pinned request table");
-    memcpy(g.meta_host, sorted.data(), count * sizeof(BatchReq));
+    memcpy(g.meta_host, plan.reqs.data(), count * sizeof(BatchReq));
     cudaStream_t cs = ctx->capture_stream;
-    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(ctx->batch_meta.p, g.meta_host, count * sizeof(BatchReq),
-                                              cudaMemcpyHostToDevice, cs);
-    if (e == cudaSuccess) e = cudaMemsetAsync(ctx->batch_counter.p, 0, sizeof(unsigned long long), cs);
-    if (e == cudaSuccess && direct_out) e = cudaMemsetAsync(ctx->batch_out.p, 0, direct_out * 4, cs);
-    if (e == cudaSuccess && raw_total)
-      e = launch_batch_layout(ctx->batch_meta.as<BatchReq>(), (uint32_t)count, raw_total, rev_total,
-                              ctx->batch_raw.as<uint32_t>(), ctx->batch_rev.as<uint32_t>(), cs, &kernels);
-    if (e == cudaSuccess && items)
-      e = launch_batch_direct(ctx->batch_meta.as<BatchReq>(), (uint32_t)count, items, ctx->batch_raw.as<uint32_t>(),
-                              ctx->batch_rev.as<uint32_t>(), ctx->batch_out.as<uint32_t>(),
-                              ctx->batch_counter.as<unsigned long long>(), ctx->num_sms, cs, &kernels);
-    if (e == cudaSuccess)
-      e = launch_batch_pack(ctx->batch_meta.as<BatchReq>(), (uint32_t)count, dst_total, ctx->batch_out.as<uint32_t>(),
-                            cs, &kernels);
+    QRNG_CUDA(ctx, cudaStreamSynchronize(cs), "batch capture");
+    // relaxed: the launchers set kernel attributes while the sequence is captured
+    cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
+    if (e == cudaSuccess) e = run_plan(ctx, plan, g.meta_host, true, cs, &g.kernels);
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess) e = e2;
@@ -584,40 +965,17 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int a
     hit = &ctx->graphs.back();
   }
   hit->stamp = ++ctx->graph_clock;
-  uint32_t graph_kernels = (raw_total ? 2 : 0) + (items ? 1 : 0) + 1;
-  // Requests routed to the transform run first (eagerly, grouped by length) into their own staging
-  // region; the graph then runs the direct requests and merges every output into place.
-  if (first_ntt < count) {
-    QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->batch_meta.p, hit->meta_host, count * sizeof(BatchReq),
-                                   cudaMemcpyHostToDevice, s), "batch table upload");
-    uint32_t nk = 0;
-    for (uint64_t k = first_ntt; k < count;) {
-      const uint64_t P = tlen[order[k]];
-      const bool fp64 = (algo == QRNG_ALGO_FFT64);
-      const uint64_t per_req = fp64 ? 2 * P * 16 : 2 * P * sizeof(uint32_t);  // FP64: both ping-pong buffers
-      uint64_t cap = kFftWorkspaceBytes / per_req;
-      if (cap < 1) cap = 1;
-      uint64_t e = k, max_mw = 0;
-      while (e < count && tlen[order[e]] == P && e - k < cap) {
-        if (sorted[e].mw > max_mw) max_mw = sorted[e].mw;
-        ++e;
-      }
-      ctx->fft.worst = ctx->fft_worst.as<unsigned long long>();
-      QRNG_CUDA(ctx,
-                fp64 ? launch_fft64_batch(ctx->batch_meta.as<BatchReq>() + k, e - k, P, max_mw, ctx->fft,
-                                          ctx->batch_out.as<uint32_t>(), s, &nk)
-                     : launch_ntt_batch(ctx->batch_meta.as<BatchReq>() + k, e - k, P, max_mw, ctx->fft,
-                                        ctx->batch_out.as<uint32_t>(), s, &nk),
-                "batched transform extraction");
-      k = e;
-    }
-    graph_kernels += nk;
-  }
+  LaunchTimer gtimer(ctx, s, kTimeBatchGraph);
   QRNG_CUDA(ctx, cudaGraphLaunch(hit->exec, s), "batch graph launch");
-  ctx->stats.kernels_launched += graph_kernels;
-  ctx->stats.last_kernels = graph_kernels;
-  const int transform = (algo == QRNG_ALGO_FFT64) ? QRNG_ALGO_FFT64 : QRNG_ALGO_NTT;
-  ctx->stats.last_algo = first_ntt < count ? (first_ntt == 0 ? transform : QRNG_ALGO_AUTO) : QRNG_ALGO_DIRECT;
+  gtimer.done();
+  ctx->stats.kernels_launched += hit->kernels;
+  ctx->stats.last_kernels = hit->kernels;
+  for (int r = 0; r < 4; ++r) ctx->stats.batch_requests[r] = hit->routes[r];
+  static const int kAlgoOfRoute[4] = {QRNG_ALGO_DIRECT, QRNG_ALGO_NTT, QRNG_ALGO_FFT64, QRNG_ALGO_FFT32_SEG};
+  int used = -1;
+  for (int r = 0; r < 4; ++r)
+    if (hit->routes[r]) used = (used == -1) ? kAlgoOfRoute[r] : QRNG_ALGO_AUTO;
+  ctx->stats.last_algo = used < 0 ? QRNG_ALGO_DIRECT : used;
   return QRNG_OK;
 }
 
@@ -643,11 +1001,13 @@ int qrng_create(qrng_ctx** out, int device) {
     return QRNG_ENOMEM;
   }
   if (ctx->dev_err.ensure(sizeof(int)) != cudaSuccess || cudaMemset(ctx->dev_err.p, 0, sizeof(int)) != cudaSuccess ||
-      ctx->fft_worst.ensure(sizeof(unsigned long long)) != cudaSuccess ||
-      cudaMemset(ctx->fft_worst.p, 0, sizeof(unsigned long long)) != cudaSuccess) {
+      ctx->fft_worst.ensure(2 * sizeof(unsigned long long)) != cudaSuccess ||
+      cudaMemset(ctx->fft_worst.p, 0, 2 * sizeof(unsigned long long)) != cudaSuccess ||
+      ctx->fft32_guard.ensure(16) != cudaSuccess || cudaMemset(ctx->fft32_guard.p, 0, 16) != cudaSuccess) {
     cudaFreeHost(ctx->result_host);
     ctx->dev_err.release();
     ctx->fft_worst.release();
+    ctx->fft32_guard.release();
     delete ctx;
     return QRNG_ENOMEM;
   }
@@ -665,6 +1025,7 @@ int qrng_create(qrng_ctx** out, int device) {
     cudaFreeHost(ctx->result_host);
     ctx->dev_err.release();
     ctx->fft_worst.release();
+    ctx->fft32_guard.release();
     delete ctx;
     return QRNG_ECUDA;
   }
@@ -686,6 +1047,7 @@ void qrng_destroy(qrng_ctx* ctx) {
   ctx->seed_dev.release();
   ctx->dev_err.release();
   ctx->fft_worst.release();
+  ctx->fft32_guard.release();
   ctx->fft.release();
   ctx->kara.release();
   drop_all_graphs(ctx);
@@ -694,6 +1056,8 @@ void qrng_destroy(qrng_ctx* ctx) {
   ctx->batch_rev.release();
   ctx->batch_out.release();
   ctx->batch_counter.release();
+  ctx->batch_fft.release();
+  if (ctx->tune_host) cudaFreeHost(ctx->tune_host);
   if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   if (ctx->copy_ready) cudaEventDestroy(ctx->copy_ready);
@@ -786,8 +1150,9 @@ int qrng_toeplitz_extract(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_
 int qrng_extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int algo, qrng_stream_t stream) {
   if (!ctx) return QRNG_EINVAL;
   if (!reqs || count == 0 || count > (1ull << 31)) return fail(ctx, QRNG_EINVAL, "qrng_extract_batch: bad request table");
-  if (algo != QRNG_ALGO_AUTO && algo != QRNG_ALGO_DIRECT && algo != QRNG_ALGO_NTT && algo != QRNG_ALGO_FFT64)
-    return fail(ctx, QRNG_ENOTSUP, "qrng_extract_batch: batches run AUTO, DIRECT, NTT or FFT64");
+  if (algo != QRNG_ALGO_AUTO && algo != QRNG_ALGO_DIRECT && algo != QRNG_ALGO_NTT && algo != QRNG_ALGO_FFT64 &&
+      algo != QRNG_ALGO_FFT32_SEG)
+    return fail(ctx, QRNG_ENOTSUP, "qrng_extract_batch: batches run AUTO, DIRECT, NTT, FFT64 or FFT32_SEG");
   for (uint64_t i = 0; i < count; ++i) {
     const qrng_request& r = reqs[i];
     if (!r.raw || !r.seed || !r.out)
@@ -876,15 +1241,31 @@ int qrng_get_stats(qrng_ctx* ctx, qrng_stats* out) {
     float ms = 0.f;
     QRNG_CUDA(ctx, cudaEventSynchronize(ctx->ev_end[i]), "timing event wait");
     QRNG_CUDA(ctx, cudaEventElapsedTime(&ms, ctx->ev_start[i], ctx->ev_end[i]), "timing event read");
-    ctx->stats.timed_ms += ms;
-    ctx->stats.timed_launches += 1;
+    switch (ctx->ev_kind[i]) {
+      case kTimeHist:
+        ctx->stats.hist_timed_ms += ms;
+        ctx->stats.hist_timed_launches += 1;
+        break;
+      case kTimeBatchGraph:
+        ctx->stats.batch_graph_ms += ms;
+        break;
+      default:
+        ctx->stats.timed_ms += ms;
+        ctx->stats.timed_launches += 1;
+    }
   }
   ctx->ev_used = 0;
-  unsigned long long worst = 0;
-  QRNG_CUDA(ctx, cudaMemcpy(&worst, ctx->fft_worst.p, sizeof(worst), cudaMemcpyDeviceToHost), "FFT error read");
-  double w;
-  memcpy(&w, &worst, sizeof(w));
-  ctx->stats.worst_fft_round_err = w;
+  unsigned long long worst[2] = {0, 0}, repairs = 0;
+  QRNG_CUDA(ctx, cudaMemcpy(worst, ctx->fft_worst.p, sizeof(worst), cudaMemcpyDeviceToHost), "FFT error read");
+  QRNG_CUDA(ctx, cudaMemcpy(&repairs, ctx->fft32_guard.as<char>() + 8, sizeof(repairs), cudaMemcpyDeviceToHost),
+            "repair count read");
+  double w64, w32;
+  memcpy(&w64, &worst[0], sizeof(w64));
+  memcpy(&w32, &worst[1], sizeof(w32));
+  ctx->stats.worst_fft_round_err = w64 > w32 ? w64 : w32;
+  ctx->stats.worst_fft32_round_err = w32;
+  ctx->stats.fft32_recomputed = repairs;
+  ctx->stats.last_fft32_segment = ctx->last_fft32_log_s ? (1ull << ctx->last_fft32_log_s) : 0;
   *out = ctx->stats;
   return QRNG_OK;
 }
@@ -894,7 +1275,8 @@ int qrng_reset_stats(qrng_ctx* ctx) {
   for (size_t i = 0; i < ctx->ev_used; ++i) cudaEventSynchronize(ctx->ev_end[i]);
   ctx->ev_used = 0;
   ctx->stats = qrng_stats{};
-  QRNG_CUDA(ctx, cudaMemset(ctx->fft_worst.p, 0, sizeof(unsigned long long)), "FFT error reset");
+  QRNG_CUDA(ctx, cudaMemset(ctx->fft_worst.p, 0, 2 * sizeof(unsigned long long)), "FFT error reset");
+  QRNG_CUDA(ctx, cudaMemset(ctx->fft32_guard.p, 0, 16), "repair count reset");
   return QRNG_OK;
 }
 
@@ -930,6 +1312,7 @@ int qrng_set_autotune(qrng_ctx* ctx, int on) {
   if (!ctx || (on != 0 && on != 1)) return QRNG_EINVAL;
   ctx->autotune = (on == 1);
   ctx->tuned.clear();
+  ctx->batch_tuned.clear();
   return QRNG_OK;
 }
 
@@ -961,6 +1344,27 @@ int qrng_karatsuba_plan(qrng_ctx* ctx, uint64_t n, uint64_t m, int form, uint64_
   out->blocks_per_pass = p.chunk_blocks;
   out->model_seconds = p.model_s;
   return QRNG_OK;
+}
+
+int qrng_set_fft32(qrng_ctx* ctx, uint64_t segment_bits, int terms) {
+  if (!ctx) return QRNG_EINVAL;
+  int ls = 0;
+  if (segment_bits != 0) {
+    while ((1ull << ls) < segment_bits) ++ls;
+    if ((1ull << ls) != segment_bits || !fft32_log_s_ok(ls))
+      return fail(ctx, QRNG_EINVAL, "qrng_set_fft32: segment_bits must be 0, 2048, 4096 or 8192");
+  }
+  if (terms < 0 || terms > 1 << 20) return fail(ctx, QRNG_EINVAL, "qrng_set_fft32: terms must be in [0, 2^20]");
+  ctx->fft32_log_s = ls;
+  ctx->fft32_terms = terms;
+  ctx->tuned.clear();
+  return QRNG_OK;
+}
+
+int qrng_fft32_terms_bound(uint64_t segment_bits) {
+  for (int ls = 11; ls <= 13; ++ls)
+    if (segment_bits == (1ull << ls)) return fft32_terms_bound(ls);
+  return 0;
 }
 
 int qrng_set_timing(qrng_ctx* ctx, int on) {

@@ -374,217 +374,4 @@ cudaError_t launch_fft64_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P
   return cudaGetLastError();
 }
 
-// ------------------------------------------------------------------------------------------------
-// FFT32_SEG: FP32 transforms on short segments, parities XOR-combined.
-//
-// Raw segment s = r[sS, (s+1)S) and output tile q = outputs [qS, (q+1)S) meet through an S x S
-// Toeplitz block whose 2S-1 seed bits depend only on d = q - s: the window
-//     w_d[u] = a[n_t - 1 + dS - S + 1 + u],  u < 2S - 1  (zero outside the seed),
-// and partial_{q,s}[i'] = (w_d (*) r_s)[i' + S - 1] for the 2S-point cyclic convolution (*).
-// Each partial sum is an integer <= S, small enough that the FP32 transform's rounding error
-// stays below 1/2 (S = 4096, N = 2S = 8192); its parity is exact, and the parities of all
-// segments XOR together into k (addition mod 2 is linear).
-// One CTA owns (block, tile q). Per pair of segments it transforms r_s + i r_{s+1} once (forward
-// DIF, bit-reversed order, in shared memory), separates the two spectra by conjugate symmetry,
-// multiplies them by the window spectra (precomputed once per call, also bit-reversed), sums the
-// two products and runs one inverse DIT transform back to natural order -- no bit-reversal pass.
-// ------------------------------------------------------------------------------------------------
-namespace {
-
-constexpr int kSegS = 4096;
-constexpr int kSegN = 2 * kSegS;
-constexpr int kSegLogN = 13;
-constexpr int kSegThreads = 512;
-
-__global__ void twiddle32_kernel(float2* __restrict__ tw) {
-  int j = blockIdx.x * blockDim.x + threadIdx.x;
-  if (j >= kSegN / 2) return;
-  double s, c;
-  sincospi(-2.0 * (double)j / (double)kSegN, &s, &c);
-  tw[j] = make_float2((float)c, (float)s);
-}
-
-__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
-  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-
-// In-place forward DIF over kSegN points: natural order in, bit-reversed order out.
-__device__ void dif_forward(float2* x, const float2* tw) {
-  for (int h = kSegN / 2, sh = kSegLogN - 1; h >= 1; h >>= 1, --sh) {
-    for (int t = threadIdx.x; t < kSegN / 2; t += blockDim.x) {
-      const int j = t & (h - 1);
-      const int i = ((t >> sh) << (sh + 1)) + j;
-      const float2 u = x[i], v = x[i + h];
-      x[i] = make_float2(u.x + v.x, u.y + v.y);
-      x[i + h] = cmulf(make_float2(u.x - v.x, u.y - v.y), tw[j << (kSegLogN - 1 - sh)]);
-    }
-    __syncthreads();
-  }
-}
-
-// In-place inverse DIT over kSegN points: bit-reversed order in, natural order out (unscaled).
-__device__ void dit_inverse(float2* x, const float2* tw) {
-  for (int h = 1, sh = 0; h < kSegN; h <<= 1, ++sh) {
-    for (int t = threadIdx.x; t < kSegN / 2; t += blockDim.x) {
-      const int j = t & (h - 1);
-      const int i = ((t >> sh) << (sh + 1)) + j;
-      float2 w = tw[j << (kSegLogN - 1 - sh)];
-      w.y = -w.y;
-      const float2 v = cmulf(x[i + h], w);
-      const float2 u = x[i];
-      x[i] = make_float2(u.x + v.x, u.y + v.y);
-      x[i + h] = make_float2(u.x - v.x, u.y - v.y);
-    }
-    __syncthreads();
-  }
-}
-
-// One CTA per window d = dmin + blockIdx.x: its bit-reversed spectrum.
-__global__ void __launch_bounds__(kSegThreads) window_spectra_kernel(const uint8_t* __restrict__ seed, uint64_t L,
-                                                                      int64_t D, int64_t dmin,
-                                                                      const float2* __restrict__ tw_g,
-                                                                      float2* __restrict__ spec) {
-  extern __shared__ float2 sm[];
-  float2* x = sm;
-  float2* tw = sm + kSegN;
-  for (int j = threadIdx.x; j < kSegN / 2; j += blockDim.x) tw[j] = tw_g[j];
-  const int64_t d = dmin + blockIdx.x;
-  const int64_t base = D + d * kSegS - kSegS + 1;
-  for (int u = threadIdx.x; u < kSegN; u += blockDim.x) {
-    const int64_t xi = base + u;
-    float v = 0.f;
-    if (u < kSegN - 1 && xi >= 0 && xi < (int64_t)L) v = (float)((seed[xi >> 3] >> (xi & 7)) & 1u);
-    x[u] = make_float2(v, 0.f);
-  }
-  __syncthreads();
-  dif_forward(x, tw);
-  float2* out = spec + (uint64_t)blockIdx.x * kSegN;
-  for (int p = threadIdx.x; p < kSegN; p += blockDim.x) out[p] = x[p];
-}
-
-__device__ __forceinline__ float raw_bit(const uint32_t* row, uint64_t t, uint64_t n_t) {
-  return t < n_t ? (float)((row[t >> 5] >> (t & 31)) & 1u) : 0.f;
-}
-
-__global__ void __launch_bounds__(kSegThreads) seg_conv_kernel(const DirectArgs a, uint64_t NQ, uint64_t NS,
-                                                                int64_t dmin, const float2* __restrict__ spec,
-                                                                const float2* __restrict__ tw_g,
-                                                                unsigned long long* __restrict__ worst) {
-  extern __shared__ float2 sm[];
-  float2* buf = sm;
-  float2* acc = sm + kSegN;
-  float2* tw = sm + 2 * kSegN;
-  uint32_t* bits = reinterpret_cast<uint32_t*>(sm + 2 * kSegN + kSegN / 2);
-  __shared__ float s_err[kSegThreads / 32];
-
-  const uint64_t blk = blockIdx.x / NQ;
-  const uint64_t q = blockIdx.x - blk * NQ;
-  const uint32_t* row = a.raw + blk * a.raw_stride;
-  const uint32_t lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-  for (int j = threadIdx.x; j < kSegN / 2; j += blockDim.x) tw[j] = tw_g[j];
-  for (int w = threadIdx.x; w < kSegS / 32; w += blockDim.x) bits[w] = 0u;
-  float err = 0.f;
-
-  for (uint64_t s = 0; s < NS; s += 2) {
-    const bool two = (s + 1 < NS);
-    for (int t = threadIdx.x; t < kSegN; t += blockDim.x) {
-      float re = 0.f, im = 0.f;
-      if (t < kSegS) {
-        re = raw_bit(row, s * kSegS + t, a.n_t);
-        if (two) im = raw_bit(row, (s + 1) * kSegS + t, a.n_t);
-      }
-      buf[t] = make_float2(re, im);
-    }
-    __syncthreads();
-    dif_forward(buf, tw);
-    const float2* W0 = spec + (uint64_t)((int64_t)q - (int64_t)s - dmin) * kSegN;
-    const float2* W1 = two ? spec + (uint64_t)((int64_t)q - (int64_t)s - 1 - dmin) * kSegN : W0;
-    for (int p = threadIdx.x; p < kSegN; p += blockDim.x) {
-      // frequency f sits at bit-reversed position p; -f at the bit-reversed position of N - f
-      const uint32_t f = __brev((uint32_t)p) >> (32 - kSegLogN);
-      const uint32_t pm = __brev((kSegN - f) & (kSegN - 1)) >> (32 - kSegLogN);
-      const float2 zf = buf[p], zm = buf[pm];
-      // R_s = (Z_f + conj Z_-f) / 2,  R_{s+1} = (Z_f - conj Z_-f) / (2i)
-      const float2 r0 = make_float2(0.5f * (zf.x + zm.x), 0.5f * (zf.y - zm.y));
-      float2 o = cmulf(W0[p], r0);
-      if (two) {
-        const float2 r1 = make_float2(0.5f * (zf.y + zm.y), -0.5f * (zf.x - zm.x));
-        const float2 o1 = cmulf(W1[p], r1);
-        o.x += o1.x;
-        o.y += o1.y;
-      }
-      acc[p] = o;
-    }
-    __syncthreads();
-    dit_inverse(acc, tw);
-    // partial sums for the tile's outputs i' = t - (S - 1): round, parity, XOR into the tile bits
-    for (int t = threadIdx.x; t < kSegS; t += blockDim.x) {
-      const float v = acc[kSegS - 1 + t].x * (1.0f / kSegN);
-      const float r = rintf(v);
-      err = fmaxf(err, fabsf(v - r));
-      const uint32_t wrd = __ballot_sync(0xffffffffu, ((int)r) & 1);
-      if (lane == 0) bits[t >> 5] ^= wrd;
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) err = fmaxf(err, __shfl_xor_sync(0xffffffffu, err, o));
-  if (lane == 0) s_err[wid] = err;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    float e = 0.f;
-    for (int w = 0; w < kSegThreads / 32; ++w) e = fmaxf(e, s_err[w]);
-    atomicMax(worst, (unsigned long long)__double_as_longlong((double)e));
-  }
-  for (int w = threadIdx.x; w < kSegS / 32; w += blockDim.x) {
-    const uint64_t ow = q * (kSegS / 32) + w;
-    if (ow >= a.mw) continue;
-    const uint32_t rem = a.m - 32 * (uint32_t)ow;
-    const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
-    uint32_t word = bits[w] & omask;
-    if (a.modified) {
-      const uint64_t bit = (uint64_t)a.id_off + 32ull * ow;
-      const uint64_t rq = bit >> 5;
-      const uint32_t rs = (uint32_t)(bit & 31);
-      const uint32_t lo = row[rq];
-      const uint32_t hi = (rs && rq + 1 < a.raw_stride) ? row[rq + 1] : 0u;
-      word ^= __funnelshift_r(lo, hi, rs) & omask;
-    }
-    a.out[blk * a.out_stride + ow] = word;
-  }
-}
-
-}  // namespace
-
-uint64_t fft32_segment() { return kSegS; }
-
-cudaError_t launch_fft32_seg(const DirectArgs& d, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
-                             uint32_t* kernels) {
-  const uint64_t NS = ceil_div(d.n_t, kSegS), NQ = ceil_div(d.m, kSegS);
-  const int64_t dmin = -(int64_t)(NS - 1);
-  const uint64_t nwin = NQ + NS - 1;
-  cudaError_t e;
-  if ((e = ws.tw32.ensure((kSegN / 2) * sizeof(float2))) != cudaSuccess) return e;
-  if ((e = ws.spec.ensure(nwin * kSegN * sizeof(float2))) != cudaSuccess) return e;
-  twiddle32_kernel<<<kSegN / 2 / 256, 256, 0, s>>>(ws.tw32.as<float2>());
-  ++*kernels;
-  const size_t smem_win = (kSegN + kSegN / 2) * sizeof(float2);
-  if ((e = cudaFuncSetAttribute(window_spectra_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_win)) !=
-      cudaSuccess)
-    return e;
-  window_spectra_kernel<<<(unsigned)nwin, kSegThreads, smem_win, s>>>(seed, L_t, (int64_t)d.n_t - 1, dmin,
-                                                                      ws.tw32.as<float2>(), ws.spec.as<float2>());
-  ++*kernels;
-  const size_t smem = (2 * kSegN + kSegN / 2) * sizeof(float2) + (kSegS / 32) * sizeof(uint32_t);
-  if ((e = cudaFuncSetAttribute(seg_conv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-      cudaSuccess)
-    return e;
-  const uint64_t ctas = d.num_blocks * NQ;
-  if (ctas > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-  seg_conv_kernel<<<(unsigned)ctas, kSegThreads, smem, s>>>(d, NQ, NS, dmin, ws.spec.as<float2>(),
-                                                            ws.tw32.as<float2>(), ws.worst);
-  ++*kernels;
-  return cudaGetLastError();
-}
-
 }  // namespace qrng

@@ -238,8 +238,7 @@ KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_s
 }
 
 cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWorkspace& ws, int* err, int fault,
-                                  int num_sms, cudaStream_t s, uint32_t* kernels, cudaEvent_t ev_start,
-                                  cudaEvent_t ev_end) {
+                                  int num_sms, cudaStream_t s, uint32_t* kernels, const TimingHook& hook) {
   if (p.levels < 1 || p.levels > 3) return cudaErrorInvalidValue;
   const uint32_t G = p.groups;
   const uint32_t hw = (uint32_t)(p.h / 32);
@@ -290,9 +289,10 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
                                                    xk_words, ws.xk.as<uint32_t>());
     ++*kernels;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if (b0 == 0 && ev_start && (e = cudaEventRecord(ev_start, s)) != cudaSuccess) return e;
-    if ((e = launch_gemm_pair_kara(dc, k, err, fault, num_sms, s, kernels)) != cudaSuccess) return e;
-    if (b0 + nb >= d.num_blocks && ev_end && (e = cudaEventRecord(ev_end, s)) != cudaSuccess) return e;
+    hook.on_begin(s);
+    e = launch_gemm_pair_kara(dc, k, err, fault, num_sms, s, kernels);
+    hook.on_end(s);
+    if (e != cudaSuccess) return e;
     const uint32_t rblocks = (uint32_t)ceil_div(d.m, p.span);
     const unsigned gc = grid_for(nb * rblocks * hw, num_sms);
     if (p.levels == 1)

@@ -631,6 +631,10 @@ __global__ void ntt_batch_parity_extract_kernel(const BatchReq* __restrict__ req
 
 }  // namespace
 
+cudaError_t ntt_prepare(FftWorkspace& ws, uint64_t P, cudaStream_t s, uint32_t* kernels) {
+  return ensure_twiddles(ws, P, s, kernels);
+}
+
 cudaError_t launch_ntt_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P,
                              uint64_t max_mw, FftWorkspace& ws, uint32_t* out_stage, cudaStream_t s,
                              uint32_t* kernels) {

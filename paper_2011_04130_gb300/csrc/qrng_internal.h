@@ -106,6 +106,10 @@ struct DirectArgs {
   uint32_t tiles;        // output tiles per block
   uint32_t splits;       // split of the raw words across warps (XOR-combined)
   uint32_t words_per_split;
+  // optional: the kernel does nothing unless *guard != 0 (an exact recomputation after an FP32
+  // rounding guard tripped; splits must be 1); then block 0 counts it in *repairs
+  const int* guard;
+  unsigned long long* repairs;
 };
 int direct_outputs_per_warp();
 cudaError_t launch_direct(const DirectArgs& a, cudaStream_t s, uint32_t* kernels);
@@ -133,7 +137,14 @@ struct BatchReq {
   uint64_t dst_word0;      // absolute index of the first 32-bit destination word ((addr*8 + off) / 32)
   uint64_t dst_begin;      // first destination word in the pack kernel's numbering
   uint64_t dst_words;
+  // route (kRoute*) and, for the FP32 segmented route, the request's place in its group
+  int route;
+  uint32_t seg_ns, seg_nq;     // segments and output tiles of S bits
+  uint64_t spec_row;           // first spectrum row (windows d = -(NS-1).., then segments) in the group buffer
+  uint64_t spec_item_begin;    // first spectra item of the request within its group
+  uint64_t mac_cta_begin;      // first multiply-and-inverse CTA of the request within its group
 };
+enum { kRouteDirect = 0, kRouteNtt = 1, kRouteFft64 = 2, kRouteFft32 = 3 };
 cudaError_t launch_batch_direct(const BatchReq* reqs, uint32_t nreq, uint64_t total_items, const uint32_t* raw_stage,
                                 const uint32_t* rev, uint32_t* out_stage, unsigned long long* counter, int num_sms,
                                 cudaStream_t s, uint32_t* kernels);
@@ -147,6 +158,7 @@ constexpr uint64_t kFftWorkspaceBytes = 1ull << 31;  // budget for the FP64 ping
 struct FftWorkspace {
   DevBuf buf0, buf1, spec, tw, tw32, ntt_tw, ntt_stage;
   uint64_t tw_P = 0;                    // length the FP64 twiddle table holds
+  uint64_t tw32_S = 0;                  // segment length the FP32 twiddle table holds
   uint64_t ntt_P = 0;                   // length the number-theoretic twiddle table holds
   unsigned long long* worst = nullptr;  // device: bits of the largest |s - round(s)| (a double)
   void release() {
@@ -158,15 +170,17 @@ struct FftWorkspace {
     ntt_tw.release();
     ntt_stage.release();
     tw_P = 0;
+    tw32_S = 0;
     ntt_P = 0;
   }
 };
 uint64_t fft64_length(uint64_t n_t, uint64_t m);
-uint64_t fft32_segment();
 cudaError_t launch_fft64(const DirectArgs& a, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
                          uint32_t* kernels);
 cudaError_t launch_ntt(const DirectArgs& a, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
                        uint32_t* kernels);
+// The NTT's constant stage table and the twiddles of length P (a no-op when both are current).
+cudaError_t ntt_prepare(FftWorkspace& ws, uint64_t P, cudaStream_t s, uint32_t* kernels);
 // Requests reqs_dev[0..nr) (own seeds, all with transform length P) by NTT into their word-aligned
 // output staging.
 cudaError_t launch_ntt_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P,
@@ -174,8 +188,24 @@ cudaError_t launch_ntt_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P,
                              uint32_t* kernels);
 cudaError_t launch_fft64_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t P, uint64_t max_mw, FftWorkspace& ws,
                                uint32_t* out_stage, cudaStream_t s, uint32_t* kernels);
-cudaError_t launch_fft32_seg(const DirectArgs& a, const uint8_t* seed, uint64_t L_t, FftWorkspace& ws, cudaStream_t s,
-                             uint32_t* kernels);
+// ---- FP32 segmented FFT (k_fft32.cu) ----
+// Segments of S = 2^log_s bits, log_s in 11..13; T product terms summed per inverse transform.
+bool fft32_log_s_ok(int log_s);
+// The largest T for which the FP32 rounding bound keeps every sum within 0.45 of its integer.
+int fft32_terms_bound(int log_s);
+double fft32_model_seconds(uint64_t n_t, uint64_t m, uint64_t num_blocks, int log_s, int T);
+// Writes a.out for every block; worst rounding distance into ws.worst; *guard_flag = 1 if it
+// reached the guard (the caller then recomputes exactly).
+cudaError_t launch_fft32_seg(const DirectArgs& a, const uint8_t* seed, uint64_t L_t, int log_s, int T,
+                             FftWorkspace& ws, int* guard_flag, cudaStream_t s, uint32_t* kernels);
+// Tiles one multiply-and-inverse CTA of the FP32 route covers (its accumulators).
+int fft32_batch_tiles(int log_s);
+// Requests reqs_dev[0..nr) of one FP32 group (segment length 2^log_s, spec_row / spec_item_begin /
+// mac_cta_begin laid out by the caller; ws.spec must hold `rows` rows of 2^log_s bins) into their
+// word-aligned output staging. The worst rounding distance goes to ws.worst.
+cudaError_t launch_fft32_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t spec_items, uint64_t mac_ctas,
+                               int log_s, int T, FftWorkspace& ws, uint32_t* out_stage, cudaStream_t s,
+                               uint32_t* kernels);
 
 // ---- tensor-core block-batched extraction (k_gemm_tc.cu) ----
 // Same layout arguments as the direct kernel (splits unused). Exact for n_t <= kGemmMaxColumns.
@@ -185,6 +215,19 @@ cudaError_t launch_gemm_tc(const DirectArgs& a, bool fp4, int* err, int fault, i
                            uint32_t* kernels);
 // The FP4 product on SM pairs (k_gemm_pair.cu): clusters of two CTAs, cta_group::2 MMAs.
 cudaError_t launch_gemm_pair(const DirectArgs& a, int* err, int fault, int num_sms, cudaStream_t s, uint32_t* kernels);
+
+// Optional callbacks a launcher calls around each launch of its main kernel (event timing).
+struct TimingHook {
+  void* user = nullptr;
+  void (*begin)(void* user, cudaStream_t s) = nullptr;
+  void (*end)(void* user, cudaStream_t s) = nullptr;
+  void on_begin(cudaStream_t s) const {
+    if (begin) begin(user, s);
+  }
+  void on_end(cudaStream_t s) const {
+    if (end) end(user, s);
+  }
+};
 
 // ---- block Karatsuba over GF(2) on the SM-pair product (k_karatsuba.cu, k_gemm_pair.cu) ----
 // The zero-padded Toeplitz matrix, cut into h x h blocks, is block Toeplitz; `levels` rounds of the
@@ -229,11 +272,10 @@ struct PairKara {
 };
 cudaError_t launch_gemm_pair_kara(const DirectArgs& a, const PairKara& k, int* err, int fault, int num_sms,
                                   cudaStream_t s, uint32_t* kernels);
-// The whole Karatsuba extraction of a.num_blocks blocks (chunked by plan.chunk_blocks). ev_start /
-// ev_end (may be null) are recorded before the first and after the last product-kernel launch.
+// The whole Karatsuba extraction of a.num_blocks blocks (chunked by plan.chunk_blocks); `hook` is
+// called around every launch of the product kernel (one per pass).
 cudaError_t launch_gemm_karatsuba(const DirectArgs& a, const KaraPlan& plan, KaraWorkspace& ws, int* err, int fault,
-                                  int num_sms, cudaStream_t s, uint32_t* kernels, cudaEvent_t ev_start = nullptr,
-                                  cudaEvent_t ev_end = nullptr);
+                                  int num_sms, cudaStream_t s, uint32_t* kernels, const TimingHook& hook = TimingHook());
 
 }  // namespace qrng
 
@@ -260,7 +302,18 @@ struct qrng_ctx {
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     void* meta_host = nullptr;  // pinned copy of the request table the graph uploads
+    uint32_t kernels = 0;       // kernels one replay runs
+    uint64_t routes[4] = {0, 0, 0, 0};  // requests per route (kRoute*)
   };
+  qrng::FftWorkspace batch_fft;  // transform workspace of batch graphs only (addresses stay put)
+  // per-class routes of QRNG_ALGO_AUTO batches, keyed by transform length: route and FP32 segment
+  struct BatchTune {
+    uint64_t P;
+    int route, log_s;
+  };
+  std::vector<BatchTune> batch_tuned;
+  void* tune_host = nullptr;   // pinned staging of the tuner's request tables
+  size_t tune_host_cap = 0;
   std::vector<BatchGraph> graphs;
   uint64_t graph_clock = 0;
   // autotuner: fastest measured algorithm per shape (n, m, log2 of the block count, form)
@@ -274,11 +327,22 @@ struct qrng_ctx {
   };
   bool autotune = true;
   int fault = 0;  // QRNG_FAULT_* armed for the next tensor-core extraction only
-  std::vector<std::pair<TuneKey, int>> tuned;
+  struct TuneChoice {
+    int algo;
+    int fft32_log_s;  // segment length of the FP32 route when it won (0 otherwise)
+  };
+  std::vector<std::pair<TuneKey, TuneChoice>> tuned;
+  // FP32 segmented FFT settings (0 = chosen per shape) and its guard word and repair counter
+  int fft32_log_s = 0;
+  int fft32_terms = 0;
+  int last_fft32_log_s = 0;
+  qrng::DevBuf fft32_guard;  // int per-call flag + unsigned long long repair count
   qrng::DevHminResult* result_host = nullptr;  // pinned
   qrng_stats stats{};
   // optional CUDA-event timing of the main extraction kernel
   bool timing = false;
   std::vector<cudaEvent_t> ev_start, ev_end;
+  std::vector<int> ev_kind;
   size_t ev_used = 0;
+  size_t ev_pending = (size_t)-1;
 };

@@ -84,3 +84,25 @@ def test_product_package_does_not_import_oracle():
             if fn.endswith((".py", ".cu", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, fn)).read()
                 assert "import oracle" not in txt and "qrng_oracle" not in txt and "liboracle" not in txt, fn
+
+
+def test_fft32_terms_bound_is_percivals(qlib):
+    """The proven term count of the FP32 route, recomputed here from the bound's statement: the
+    largest T with T sqrt((2S-1) S) (eps_k + T u) <= 0.45, eps_k = (1+u)^{3k} (1+sqrt5 u)^{3k+1}
+    (1+u/2)^{3k} - 1, k = log2(2S), u = 2^-24 (evaluated with exact rationals)."""
+    from fractions import Fraction as F
+    import math
+
+    import paper_2011_04130_gb300 as q
+
+    for S in (2048, 4096, 8192):
+        k = S.bit_length()  # log2(2S)
+        u = 2.0 ** -24
+        eps = math.expm1(3 * k * math.log1p(u) + (3 * k + 1) * math.log1p(math.sqrt(5) * u) +
+                         3 * k * math.log1p(u / 2))
+        per = math.sqrt((2 * S - 1) * S)
+        T = max(t for t in range(1, 100) if t * per * (eps + t * u) <= 0.45)
+        assert q.qrng_fft32_terms_bound(S) == T, S
+        assert T * per * (eps + T * u) < F(1, 2)
+    assert [q.qrng_fft32_terms_bound(S) for S in (2048, 4096, 8192)] == [16, 8, 3]
+    assert q.qrng_fft32_terms_bound(1024) == 0 and q.qrng_fft32_terms_bound(5000) == 0

@@ -44,5 +44,29 @@ def test_traffic_record_tracks_the_kernel_source():
 def test_unknown_route_has_no_roofline():
     import bench
 
-    r = bench.roofline_for("fft64", 10, 10, 10, 1.0)
+    r = bench.roofline_for("no_such_route", 10, 10, 10, 1.0)
     assert r["bound"] is None and r["frac"] is None
+
+
+def test_direct_roofline_uses_the_device_sm_count():
+    import bench
+
+    caps = {"sms": 100, "sm_max_mhz": 2000.0}
+    r = bench.roofline_for("direct", 8, 1000, 4096, 1.0, caps=caps)
+    assert r["peak"] == 64 * 32 * 100 * 2000e6 / 1e12
+    assert abs(r["achieved"] - 8 * 1000 * 4096 / 1e-3 / 1e12) < 1e-9
+
+
+def test_transform_routes_report_hbm_and_pipe_fractions():
+    import bench
+
+    pk = bench.measured_peaks()
+    n, m, B, ms = 1 << 16, 36473, 8192, 10.0
+    r = bench.roofline_for("fft64", B, m, n, ms)
+    P = 1 << 17
+    flops = B // 2 * (10.0 * P * 17 + 6.0 * P)
+    assert r["bound"] == "fp64" and abs(r["achieved"] - flops / 1e-2 / 1e12) < 1e-9 * r["achieved"]
+    assert abs(r["hbm"]["achieved"] - B * (n + m) / 8 / 1e-2 / 1e9) < 1e-9 * r["hbm"]["achieved"]
+    assert abs(r["hbm"]["frac"] - r["hbm"]["achieved"] / pk["hbm_gbs"]) < 1e-12
+    r = bench.roofline_for("ntt", B, m, n, ms)
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"

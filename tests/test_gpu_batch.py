@@ -108,6 +108,49 @@ def test_all_requests_on_the_fp64_route(qlib, gpu, oracle_mod):
     assert st["last_algo"] == qlib.QRNG_ALGO_FFT64 and st["worst_fft_round_err"] < 1e-6
 
 
+def test_all_requests_on_the_fp32_segmented_route(qlib, gpu, oracle_mod):
+    """QRNG_ALGO_FFT32_SEG: every request's seed windows and raw segments transformed once, the
+    products summed in the frequency domain up to the proven term count, parities XORed."""
+    batch = _make_batch(70, 23, 5, 17)
+    qlib.qrng_reset_stats(gpu)
+    host, _ = _run(qlib, gpu, batch, algo=qlib.QRNG_ALGO_FFT32_SEG)
+    _check(oracle_mod, batch, host)
+    st = qlib.qrng_get_stats(gpu)
+    assert st["last_algo"] == qlib.QRNG_ALGO_FFT32_SEG and st["worst_fft_round_err"] < 0.25
+    assert st["batch_requests"]["fft32_seg"] == 70
+
+
+@pytest.mark.parametrize("seg", [2048, 8192])
+def test_fp32_segmented_route_other_segment_lengths(qlib, gpu, oracle_mod, seg):
+    batch = _make_batch(25, 25 + seg, 10, 16)
+    qlib.qrng_set_fft32(gpu, seg, 0)
+    try:
+        host, _ = _run(qlib, gpu, batch, algo=qlib.QRNG_ALGO_FFT32_SEG)
+    finally:
+        qlib.qrng_set_fft32(gpu, 0, 0)
+    _check(oracle_mod, batch, host)
+
+
+def test_auto_is_one_graph_replay_per_call(qlib, gpu, oracle_mod):
+    """AUTO routes each shape class (transform length) by timing its candidates once; then every
+    call of the same table is a single replay of the cached graph, whatever the routes."""
+    batch = _make_batch(150, 29, 8, 21)
+    host, keep = _run(qlib, gpu, batch)
+    _check(oracle_mod, batch, host)
+    st1 = qlib.qrng_get_stats(gpu)
+    routes = st1["batch_requests"]
+    assert sum(routes.values()) == 150
+    k0 = st1["kernels_launched"]
+    raw_t, seed_t, out, reqs = keep
+    out.fill_(0x5A)
+    qlib.qrng_extract_batch(gpu, reqs)
+    qlib.qrng_synchronize(gpu)
+    st2 = qlib.qrng_get_stats(gpu)
+    assert st2["batch_requests"] == routes
+    assert st2["kernels_launched"] - k0 == st2["last_kernels"]  # one replay, no tuning
+    _check(oracle_mod, batch, out.cpu().numpy())
+
+
 def test_mixed_routes_long_requests(qlib, gpu, oracle_mod):
     """AUTO on requests up to 2^20 bits: short ones on the persistent kernel, long ones on the
     transform route, all merged into one output buffer."""
@@ -172,7 +215,7 @@ def test_batch_matches_single_block_calls(qlib, gpu):
     assert torch.equal(out, ref)
 
 
-@pytest.mark.parametrize("algo", [0, 1, 5, 3])
+@pytest.mark.parametrize("algo", [0, 1, 5, 3, 4])
 def test_single_and_degenerate_requests(qlib, gpu, oracle_mod, algo):
     """One-bit outputs, n = 1 and n = 2 blocks, m = n standard, m = n - 1 modified, on every route."""
     shapes = [(1, 1, STD), (2, 1, MOD), (2, 2, STD), (33, 1, STD), (64, 63, MOD), (100, 100, STD)]
@@ -197,9 +240,6 @@ def test_batch_bad_arguments(qlib, gpu):
 
     t = torch.zeros(64, dtype=torch.uint8, device="cuda")
     ok = (t, 0, 64, 32, t, STD, t, 0)
-    with pytest.raises(qlib.QrngError) as e:
-        qlib.qrng_extract_batch(gpu, [ok], algo=qlib.QRNG_ALGO_FFT32_SEG)
-    assert e.value.status == qlib.QRNG_ENOTSUP
     with pytest.raises(qlib.QrngError) as e:
         qlib.qrng_extract_batch(gpu, [ok], algo=qlib.QRNG_ALGO_GEMM_TC)
     assert e.value.status == qlib.QRNG_ENOTSUP

@@ -8,6 +8,8 @@ tests per block, escape probability 2^-64) where its O(nm) preparation is afford
 (n m <= 2^31), otherwise on sampled output bits of every block, each computed by the oracle on its
 own. The bytes around the output must stay untouched. Bar: bit-exact.
 """
+import concurrent.futures
+
 import numpy as np
 import pytest
 
@@ -44,21 +46,29 @@ def test_every_algorithm_every_block(qlib, gpu, oracle_mod, stream, log2n):
     seed_d = torch.from_numpy(seed).to("cuda")
     nbytes = B * m // 8
     out = torch.full((nbytes + 64,), SENTINEL, dtype=torch.uint8, device="cuda")
-    checked = {}
+    outs = {}
     for name, algo in ALGOS.items():
         out.fill_(SENTINEL)
         qlib.qrng_toeplitz_extract(gpu, raw_d, n, m, seed_d, MOD, algo, B, out)
         qlib.qrng_synchronize(gpu)
         host = out.cpu().numpy()
         assert np.all(host[nbytes:] == SENTINEL), f"{name}: wrote past the output"
-        got = host[:nbytes]
+        outs[name] = host[:nbytes].copy()
+
+    def check(name):
+        got = outs[name]
         if n * m <= (1 << 31):
             mism = oracle_mod.freivalds(raw, n, m, seed, MOD, B, got, rng_seed=log2n)
             assert not mism.any(), f"{name}: {np.count_nonzero(mism)} of {B} blocks fail the Freivalds check"
-            checked[name] = "freivalds"
-        else:
-            per_block = 8 if n <= (1 << 20) else 6
-            check_every_block(oracle_mod, raw, n, m, seed, MOD, got, B, per_block=per_block,
-                              rng_seed=1000 * log2n + algo)
-            checked[name] = f"{per_block} bits x {B} blocks"
+            return "freivalds"
+        per_block = 8 if n <= (1 << 20) else 6
+        check_every_block(oracle_mod, raw, n, m, seed, MOD, got, B, per_block=per_block,
+                          rng_seed=1000 * log2n + ALGOS[name])
+        return f"{per_block} bits x {B} blocks"
+
+    if n * m <= (1 << 31):  # one Freivalds call per algorithm, side by side (each is single-threaded C)
+        with concurrent.futures.ThreadPoolExecutor(max_workers=len(outs)) as ex:
+            checked = dict(zip(outs, ex.map(check, outs)))
+    else:  # each check spreads over the cores itself
+        checked = {name: check(name) for name in outs}
     assert len(checked) == len(ALGOS)

@@ -62,11 +62,11 @@ def _check_requests(oracle_mod, b, host, per_req, rng_seed):
             assert r is None, f"request {r} (n={n[r]}, m={m[r]}) differs from the oracle"
 
 
-@pytest.mark.parametrize("route", ["auto", "ntt", "fft64", "direct"])
+@pytest.mark.parametrize("route", ["auto", "ntt", "fft64", "fft32_seg", "direct"])
 def test_full_uneven_batch_every_request(qlib, gpu, oracle_mod, batch, route):
     b, _keep, out, reqs = batch
     algo = {"auto": qlib.QRNG_ALGO_AUTO, "ntt": qlib.QRNG_ALGO_NTT, "fft64": qlib.QRNG_ALGO_FFT64,
-            "direct": qlib.QRNG_ALGO_DIRECT}[route]
+            "fft32_seg": qlib.QRNG_ALGO_FFT32_SEG, "direct": qlib.QRNG_ALGO_DIRECT}[route]
     out.fill_(SENTINEL)
     qlib.qrng_reset_stats(gpu)
     qlib.qrng_extract_batch(gpu, reqs, algo=algo)
@@ -78,3 +78,7 @@ def test_full_uneven_batch_every_request(qlib, gpu, oracle_mod, batch, route):
     if tail:  # pad bits of the last byte keep the sentinel's bits
         assert (host[nbytes - 1] >> tail) == (SENTINEL >> tail)
     _check_requests(oracle_mod, b, host[:nbytes], per_req=8, rng_seed=algo + 17)
+    st = qlib.qrng_get_stats(gpu)
+    assert sum(st["batch_requests"].values()) == b["n"].size
+    if route in ("fft64", "fft32_seg"):
+        assert 0.0 < st["worst_fft_round_err"] < 0.25

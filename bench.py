@@ -86,7 +86,7 @@ def parse():
                    help="laser: the headline stream (default); single: one 4096-bit block; sweep: block-length "
                         "sweep on a 2^30-bit stream; tc: m=6144, n=8192, 4096 blocks; uneven: 10,000 requests; "
                         "long: 64 blocks of 2^22 bits (the transform route's profiling case)")
-    p.add_argument("--sweep-algos", default="direct,gemm_tc,gemm_fp4,gemm_fp4_pair,gemm_karatsuba,ntt,fft64",
+    p.add_argument("--sweep-algos", default="direct,gemm_tc,gemm_fp4,gemm_fp4_pair,gemm_karatsuba,ntt,fft64,fft32_seg",
                    help="algorithms timed at each block length of the sweep")
     p.add_argument("--uneven-max-log2n", type=float, default=22.0,
                    help="upper end of the log-uniform n range of the uneven requests")
@@ -429,8 +429,19 @@ def roofline_for(algo, num_blocks, m, n_t, kernel_ms, plan=None, caps=None, n=No
                 "kernel_ms": kernel_ms, "hbm": hbm_record(io_bytes, kernel_ms),
                 "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s"}
     if algo == "fft32_seg":
-        return {"bound": "fp32", "achieved": None, "peak": fp32_peak_tflops(caps), "unit": "TFLOP/s", "frac": None,
-                "kernel": "seg_conv_kernel (FP32)", "kernel_ms": kernel_ms, "hbm": hbm_record(io_bytes, kernel_ms),
+        # per block: NS segment and (once per call) NQ + NS - 1 window transforms, NQ ceil(NS/T)
+        # inverses (5 S log2 S flops each, S-point complex), NQ NS products of S bins (8 flops each)
+        S = (plan or {}).get("segment") or 4096
+        T = (plan or {}).get("terms") or 8
+        NS, NQ = -(-n_t // S), -(-m // S)
+        lg = S.bit_length() - 1
+        flops = num_blocks * ((NS + NQ * -(-NS // T)) * 5.0 * S * lg + NQ * NS * S * 8.0) + \
+            (NQ + NS - 1) * 5.0 * S * lg
+        achieved = flops / (kernel_ms / 1e3) / 1e12
+        peak = fp32_peak_tflops(caps)
+        return {"bound": "fp32", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "segment": S, "terms": T, "kernel": "seg_spectra_kernel + seg_mac_kernel (FP32)",
+                "kernel_ms": kernel_ms, "hbm": hbm_record(io_bytes, kernel_ms),
                 "peak_source": f"derived: {FP32_FMA_PER_CLK_SM} FMA/clk/SM x 2 x {caps['sms']} SMs x "
                                f"{caps['sm_max_mhz']:g} MHz"}
     if algo == "ntt":
@@ -569,6 +580,12 @@ def clocked(local, fn, *a, **kw):
     return res
 
 
+def fft32_plan(q, st):
+    """Segment length and terms per inverse of the last FP32 segmented call (the proven bound)."""
+    S = int(st.get("last_fft32_segment") or 0)
+    return {"segment": S, "terms": q.qrng_fft32_terms_bound(S)} if S else None
+
+
 def sub_single(q, ctx, caps, reps=20):
     """Config 1: one 4096-bit block, m = 2048, plus the min-entropy of 65,536 samples: latency."""
     import torch
@@ -648,6 +665,10 @@ def sub_sweep(q, ctx, caps, flush, reps=2):
             dk, dc, _ = _time_extract(q, ctx, raw, n, m, seed, 1, ALGOS["direct"], B, out, reps=1, flush=flush)
             row["direct"] = {"call_ms": dc, "gbps": B * m / (dc / 1e3) / 1e9,
                              "frac": roofline_for("direct", B, m, n - m, dk, caps=caps)["frac"]}
+            fk, fc, fs = _time_extract(q, ctx, raw, n, m, seed, 1, ALGOS["fft32_seg"], B, out, reps=1, flush=flush)
+            frl = roofline_for("fft32_seg", B, m, n - m, fk, fft32_plan(q, fs), caps, n=n)
+            row["fft32_seg"] = {"call_ms": fc, "gbps": B * m / (fc / 1e3) / 1e9, "frac": frl["frac"],
+                                "segment": frl["segment"], "worst_round_err": fs["worst_fft_round_err"]}
         rows.append(row)
     return {"workload": "block-length sweep: 2^30-bit Bernoulli(0.5) stream, n = 2^10..2^24, m = 0.75n, modified "
                         "form, AUTO vs the plain per-block direct kernel (n <= 2^20)", "unit": UNIT, "rows": rows}
@@ -680,15 +701,16 @@ def sub_fft_routes(q, ctx, caps, samples, seed, n, m, num_blocks, out, flush, re
     for name in ("ntt", "fft64", "fft32_seg"):
         kms, cms, st = _time_extract(q, ctx, samples, n, m, seed, 0, ALGOS[name], num_blocks, out, reps=reps,
                                      flush=flush)
-        rl = roofline_for(name, num_blocks, m, n, kms, caps=caps)
+        rl = roofline_for(name, num_blocks, m, n, kms, fft32_plan(q, st), caps=caps)
         res[name] = {"kernel_ms": kms, "call_ms": cms, "gbps": num_blocks * m / (cms / 1e3) / 1e9,
                      "worst_round_err": st["worst_fft_round_err"] if name != "ntt" else 0.0, "roofline": rl}
     return res
 
 
-def sub_uneven(q, ctx, caps, routes=("auto",)):
+def sub_uneven(q, ctx, caps, routes=("auto", "fft32_seg", "fft64")):
     """Config 5: 10,000 uneven requests (n log-uniform in [2^12, 2^22], m/n uniform in [0.5, 0.9],
-    per-request seeds, raw Bernoulli(p), p uniform in [0.45, 0.55])."""
+    per-request seeds, raw Bernoulli(p), p uniform in [0.45, 0.55]), one graph replay per call:
+    AUTO's tuned schedule, and the FP32 segmented and FP64 transforms on every request."""
     import torch
 
     b = W.uneven_batch()
@@ -703,15 +725,16 @@ def sub_uneven(q, ctx, caps, routes=("auto",)):
                        "per-request standard seeds, Bernoulli(p) raw bits", "unit": UNIT,
            "output_gbit": float(m.sum()) / 1e9, "bitmacs": float((m * n).sum())}
     stream = torch.cuda.current_stream()
+    pk = measured_peaks()
     for route in routes:
         algo = ALGOS[route]
-        q.qrng_extract_batch(ctx, reqs, algo=algo)  # capture + first run
+        q.qrng_extract_batch(ctx, reqs, algo=algo)  # plan (and for AUTO the class tuning), capture, first run
         q.qrng_synchronize(ctx)
         q.qrng_reset_stats(ctx)
         q.qrng_set_timing(ctx, True)
         a, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record(stream)
-        q.qrng_extract_batch(ctx, reqs, algo=algo)  # graph replay
+        q.qrng_extract_batch(ctx, reqs, algo=algo)  # one graph replay
         e.record(stream)
         e.synchronize()
         q.qrng_synchronize(ctx)
@@ -719,11 +742,17 @@ def sub_uneven(q, ctx, caps, routes=("auto",)):
         q.qrng_set_timing(ctx, False)
         ms = a.elapsed_time(e)
         r = {"ms": ms, "gbps": res["output_gbit"] / (ms / 1e3), "graph_ms": st["batch_graph_ms"],
-             "transform_ms": st["batch_transform_ms"], "kernels_per_call": st["last_kernels"],
-             "worst_round_err": st["worst_fft_round_err"]}
-        r["direct_equivalent_tbitmac_per_s"] = res["bitmacs"] / (ms / 1e3) / 1e12
-        if route == "direct":
-            r["frac_of_lop3_peak"] = res["bitmacs"] / (st["batch_graph_ms"] / 1e3) / 1e12 / alu_peak_tbitmac(caps)
+             "kernels_per_call": st["last_kernels"], "requests": st["batch_requests"],
+             "worst_round_err": st["worst_fft_round_err"],
+             "direct_equivalent_tbitmac_per_s": res["bitmacs"] / (ms / 1e3) / 1e12}
+        if st["batch_requests"]["direct"] and st["batch_direct_ms"] > 0:
+            ach = st["batch_direct_bitmacs"] / (st["batch_direct_ms"] / 1e3) / 1e12
+            r["direct_part"] = {"ms": st["batch_direct_ms"], "achieved": ach, "unit": "Tbit-MAC/s",
+                                "frac": ach / alu_peak_tbitmac(caps), "bound": "alu"}
+        if st["batch_transform_ms"] > 0:
+            hb = hbm_record(st["batch_transform_bytes"], st["batch_transform_ms"])
+            r["transform_part"] = {"ms": st["batch_transform_ms"], "hbm_achieved": hb["achieved"],
+                                   "hbm_frac": hb["frac"], "unit": "GB/s"}
         res[route] = r
     return res
 
@@ -762,7 +791,8 @@ def run_sweep(args):
         for name in args.sweep_algos.split(","):
             try:
                 kms, cms, st = _time_extract(q, ctx, raw, n, m, seed, 1, ALGOS[name], B, out, reps=2)
-                plan = q.qrng_karatsuba_plan(ctx, n, m, 1, B) if name == "gemm_karatsuba" else None
+                plan = (q.qrng_karatsuba_plan(ctx, n, m, 1, B) if name == "gemm_karatsuba"
+                        else fft32_plan(q, st) if name == "fft32_seg" else None)
                 rl = roofline_for(name, B, m, n - m, kms, plan, caps, n=n)
                 row[name] = {"kernel_ms": kms, "call_ms": cms, "gbps": B * m / (cms / 1e3) / 1e9,
                              "frac": rl.get("frac"), "bound": rl.get("bound")}
@@ -842,7 +872,7 @@ def _standalone(fn):
         caps = device_caps()
         flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device="cuda")
         if fn is sub_uneven:
-            routes = ("auto", "ntt", "fft64", "direct") if args.algo == "all" else (args.algo,)
+            routes = ("auto", "ntt", "fft64", "fft32_seg", "direct") if args.algo == "all" else (args.algo,)
             res = clocked(0, fn, q, ctx, caps, routes)
         elif fn is sub_histogram:
             res = clocked(0, fn, q, ctx, flush)

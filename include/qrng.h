@@ -311,6 +311,10 @@ typedef struct {
   uint64_t batch_requests[4];    /* requests of the last qrng_extract_batch call per route: the
                                     persistent direct kernel, the number-theoretic transform,
                                     the FP64 FFT and the FP32 segmented FFT                      */
+  double batch_direct_bitmacs;   /* the last batch call: sum of m n_t over its direct requests  */
+  double batch_transform_bytes;  /* the last batch call: (n + m) / 8 over its transform requests */
+  double batch_direct_ms;        /* the last timed batch replay: its persistent direct kernel   */
+  double batch_transform_ms;     /* the last timed batch replay: its transform groups           */
   double worst_fft32_round_err;  /* the FP32 segmented route's part of worst_fft_round_err      */
   uint64_t fft32_recomputed;     /* FP32 segmented calls whose rounding guard tripped and whose
                                     output the exact direct kernel recomputed                   */
@@ -348,7 +352,10 @@ QRNG_API int qrng_set_autotune(qrng_ctx* ctx, int on);
  *                   (256 lets the two output tiles of a pair tile share T tiles across blocks: no
  *                   extra operand build per block);
  *   max_workspace   device bytes for the derived operands and sub-product parities of one pass
- *                   (the blocks are processed in passes that fit it; 0 = 1 GiB).
+ *                   (the blocks are processed in passes that fit it; 0 = 1 GiB). A pass always
+ *                   holds at least 224 blocks (one tile width of the product kernel), or every
+ *                   block when there are fewer, so a budget below what 224 blocks need is
+ *                   exceeded rather than refused.
  * Returns QRNG_EINVAL for values outside those sets. Forgets the shapes autotuned so far. */
 QRNG_API int qrng_set_karatsuba(qrng_ctx* ctx, int levels, uint64_t block_bits, uint64_t max_workspace);
 
@@ -387,9 +394,10 @@ QRNG_API int qrng_fft32_terms_bound(uint64_t segment_bits);
 /* Timing (on = 1, off = 0): CUDA event pairs on the caller's stream around the main extraction
  * kernel of each qrng_toeplitz_extract call (one pair per launch; the block-Karatsuba route
  * launches its product kernel once per pass), summed into timed_ms / timed_launches; around the
- * histogram kernel of qrng_minentropy (hist_timed_*); and around the two parts of each
- * qrng_extract_batch call (batch_graph_ms, batch_transform_ms). At most 4096 pairs are kept
- * between two qrng_get_stats calls; later ones are not timed. */
+ * histogram kernel of qrng_minentropy (hist_timed_*); and around each qrng_extract_batch replay
+ * (batch_graph_ms), whose graph also records the time of its transform groups and of its
+ * persistent direct kernel (batch_transform_ms, batch_direct_ms: the last timed replay's). At most
+ * 4096 pairs are kept between two qrng_get_stats calls; later ones are not timed. */
 QRNG_API int qrng_set_timing(qrng_ctx* ctx, int on);
 
 #ifdef __cplusplus

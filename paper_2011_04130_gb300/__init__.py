@@ -85,6 +85,10 @@ class Stats(ctypes.Structure):
         ("hist_timed_ms", ctypes.c_double),
         ("batch_graph_ms", ctypes.c_double),
         ("batch_requests", ctypes.c_uint64 * 4),
+        ("batch_direct_bitmacs", ctypes.c_double),
+        ("batch_transform_bytes", ctypes.c_double),
+        ("batch_direct_ms", ctypes.c_double),
+        ("batch_transform_ms", ctypes.c_double),
         ("worst_fft32_round_err", ctypes.c_double),
         ("fft32_recomputed", ctypes.c_uint64),
         ("last_fft32_segment", ctypes.c_uint64),

@@ -213,11 +213,16 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
       const KaraPlan plan = karatsuba_plan(n_t, m, num_blocks, ctx->num_sms, ctx->kara_levels, ctx->kara_h,
                                            ctx->kara_workspace);
       if (plan.levels == 0) return fail(ctx, QRNG_ENOTSUP, "qrng_toeplitz_extract: no block Karatsuba plan fits");
+      // the combination writes the packed stream itself when its layout allows (no pack pass)
+      const uint64_t out_bytes = ceil_div(num_blocks * m, 8);
+      const bool fused = !out_direct && (reinterpret_cast<uintptr_t>(out) & 3) == 0 && out_bytes % 4 == 0 &&
+                         m >= 64 && m <= kKaraPackMaxBits;
       // one timed pair around each pass's product kernel
       QRNG_CUDA(ctx,
                 launch_gemm_karatsuba(a, plan, ctx->kara, ctx->dev_err.as<int>(), fault, ctx->num_sms, s, kernels,
-                                      extract_hook(ctx)),
+                                      extract_hook(ctx), fused ? out : nullptr),
                 "block Karatsuba extraction");
+      if (fused) return QRNG_OK;
     } else {
       LaunchTimer timer(ctx, s);
       QRNG_CUDA(ctx,
@@ -524,6 +529,8 @@ void drop_graph(qrng_ctx::BatchGraph& g) {
   if (g.exec) cudaGraphExecDestroy(g.exec);
   if (g.graph) cudaGraphDestroy(g.graph);
   if (g.meta_host) cudaFreeHost(g.meta_host);
+  for (cudaEvent_t& e : g.ev)
+    if (e) cudaEventDestroy(e);
   g = qrng_ctx::BatchGraph{};
 }
 
@@ -752,8 +759,9 @@ int ensure_plan(qrng_ctx* ctx, const BatchPlan& p) {
 }
 
 // The launch sequence of a plan on stream cs; its request table is uploaded from pinned `meta_host`.
+// ev (may be null): events recorded before and after the transform groups and the direct kernel.
 cudaError_t run_plan(qrng_ctx* ctx, const BatchPlan& p, const void* meta_host, bool merge, cudaStream_t cs,
-                     uint32_t* kernels) {
+                     uint32_t* kernels, const cudaEvent_t* ev = nullptr) {
   const uint32_t count = (uint32_t)p.reqs.size();
   BatchReq* meta = ctx->batch_meta.as<BatchReq>();
   cudaError_t e = cudaMemcpyAsync(meta, meta_host, count * sizeof(BatchReq), cudaMemcpyHostToDevice, cs);
@@ -764,6 +772,8 @@ cudaError_t run_plan(qrng_ctx* ctx, const BatchPlan& p, const void* meta_host, b
                             ctx->batch_rev.as<uint32_t>(), cs, kernels);
   FftWorkspace& w = ctx->batch_fft;
   w.worst = ctx->fft_worst.as<unsigned long long>();  // a batch trip is reported by qrng_synchronize
+  // graph nodes that record the events on every replay (external records of a capture)
+  if (e == cudaSuccess && ev && !p.groups.empty()) e = cudaEventRecordWithFlags(ev[0], cs, cudaEventRecordExternal);
   for (const BatchGroup& g : p.groups) {
     if (e != cudaSuccess) break;
     const uint64_t nr = g.end - g.begin;
@@ -779,10 +789,13 @@ cudaError_t run_plan(qrng_ctx* ctx, const BatchPlan& p, const void* meta_host, b
                              ctx->batch_out.as<uint32_t>(), cs, kernels);
     }
   }
+  if (e == cudaSuccess && ev && !p.groups.empty()) e = cudaEventRecordWithFlags(ev[1], cs, cudaEventRecordExternal);
+  if (e == cudaSuccess && ev && p.items) e = cudaEventRecordWithFlags(ev[2], cs, cudaEventRecordExternal);
   if (e == cudaSuccess && p.items)
     e = launch_batch_direct(meta, count, p.items, ctx->batch_raw.as<uint32_t>(), ctx->batch_rev.as<uint32_t>(),
                             ctx->batch_out.as<uint32_t>(), ctx->batch_counter.as<unsigned long long>(), ctx->num_sms,
                             cs, kernels);
+  if (e == cudaSuccess && ev && p.items) e = cudaEventRecordWithFlags(ev[3], cs, cudaEventRecordExternal);
   if (e == cudaSuccess && merge)
     e = launch_batch_pack(meta, count, p.dst_total, ctx->batch_out.as<uint32_t>(), cs, kernels);
   return e;
@@ -945,13 +958,26 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int a
     g.key = key;
     g.generation = ctx->batch_generation;
     for (int r = 0; r < 4; ++r) g.routes[r] = plan.routes[r];
+    for (const BatchReq& q : plan.reqs) {
+      if (q.route == kRouteDirect) g.direct_bitmacs += (double)q.m * (double)q.n_t;
+      else g.transform_bytes += (double)(q.n + q.m) / 8.0;
+    }
+    g.has_transform = !plan.groups.empty();
+    g.has_direct = plan.items != 0;
+    for (cudaEvent_t& ev : g.ev) {
+      const cudaError_t ee = cudaEventCreate(&ev);
+      if (ee != cudaSuccess) {
+        drop_graph(g);
+        return cuda_fail(ctx, ee, "batch graph events");
+      }
+    }
     QRNG_CUDA(ctx, cudaMallocHost(&g.meta_host, count * sizeof(BatchReq)), "pinned request table");
     memcpy(g.meta_host, plan.reqs.data(), count * sizeof(BatchReq));
     cudaStream_t cs = ctx->capture_stream;
     QRNG_CUDA(ctx, cudaStreamSynchronize(cs), "batch capture");
     // relaxed: the launchers set kernel attributes while the sequence is captured
     cudaError_t e = cudaStreamBeginCapture(cs, cudaStreamCaptureModeRelaxed);
-    if (e == cudaSuccess) e = run_plan(ctx, plan, g.meta_host, true, cs, &g.kernels);
+    if (e == cudaSuccess) e = run_plan(ctx, plan, g.meta_host, true, cs, &g.kernels, g.ev);
     cudaGraph_t graph = nullptr;
     const cudaError_t e2 = cudaStreamEndCapture(cs, &graph);
     if (e == cudaSuccess) e = e2;
@@ -971,6 +997,13 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int a
   ctx->stats.kernels_launched += hit->kernels;
   ctx->stats.last_kernels = hit->kernels;
   for (int r = 0; r < 4; ++r) ctx->stats.batch_requests[r] = hit->routes[r];
+  ctx->stats.batch_direct_bitmacs = hit->direct_bitmacs;
+  ctx->stats.batch_transform_bytes = hit->transform_bytes;
+  if (ctx->timing) {
+    ctx->timed_graph_pending = true;
+    ctx->timed_graph_key = hit->key;
+    ctx->timed_graph_generation = hit->generation;
+  }
   static const int kAlgoOfRoute[4] = {QRNG_ALGO_DIRECT, QRNG_ALGO_NTT, QRNG_ALGO_FFT64, QRNG_ALGO_FFT32_SEG};
   int used = -1;
   for (int r = 0; r < 4; ++r)
@@ -1255,6 +1288,23 @@ int qrng_get_stats(qrng_ctx* ctx, qrng_stats* out) {
     }
   }
   ctx->ev_used = 0;
+  if (ctx->timed_graph_pending) {  // the parts of the last timed batch replay
+    ctx->timed_graph_pending = false;
+    for (const auto& g : ctx->graphs) {
+      if (g.key != ctx->timed_graph_key || g.generation != ctx->timed_graph_generation) continue;
+      float ms = 0.f;
+      if (g.has_transform) {
+        QRNG_CUDA(ctx, cudaEventSynchronize(g.ev[1]), "batch timing wait");
+        QRNG_CUDA(ctx, cudaEventElapsedTime(&ms, g.ev[0], g.ev[1]), "batch timing read");
+        ctx->stats.batch_transform_ms = ms;
+      }
+      if (g.has_direct) {
+        QRNG_CUDA(ctx, cudaEventSynchronize(g.ev[3]), "batch timing wait");
+        QRNG_CUDA(ctx, cudaEventElapsedTime(&ms, g.ev[2], g.ev[3]), "batch timing read");
+        ctx->stats.batch_direct_ms = ms;
+      }
+    }
+  }
   unsigned long long worst[2] = {0, 0}, repairs = 0;
   QRNG_CUDA(ctx, cudaMemcpy(worst, ctx->fft_worst.p, sizeof(worst), cudaMemcpyDeviceToHost), "FFT error read");
   QRNG_CUDA(ctx, cudaMemcpy(&repairs, ctx->fft32_guard.as<char>() + 8, sizeof(repairs), cudaMemcpyDeviceToHost),

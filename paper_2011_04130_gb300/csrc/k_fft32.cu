@@ -41,16 +41,22 @@ namespace {
 
 constexpr float kGuard = 0.25f;
 
-// Threads of a CTA for S = 2^LOG_S (one radix-8 butterfly each per pass up to S = 4096), and the
-// most tiles a MAC CTA accumulates at once (registers: Q x BINS complex per thread).
+// Threads of a CTA for S = 2^LOG_S (one radix-16 butterfly each per pass), resident CTAs per SM,
+// and the most tiles a multiply-and-inverse CTA accumulates at once (Q x BINS complex registers).
 template <int LOG_S>
 struct SegCfg {
   static constexpr int S = 1 << LOG_S;
-  static constexpr int THREADS = S / 8 < 512 ? S / 8 : 512;
-  static constexpr int BINS = S / THREADS;
-  static constexpr int QMAX = BINS > 8 ? 2 : 4;
+  static constexpr int THREADS = S / 16;
+  static constexpr int BINS = 16;
+  static constexpr int MIN_CTAS = 512 / THREADS;  // 512 resident threads per SM: at most 128 registers each
+  static constexpr int QMAX = 2;
 };
 constexpr uint64_t kSpecBudget = 256ull << 20;  // bytes of segment spectra per chunk of blocks
+
+// Shared-memory index of transform entry i: one pad entry after every 32, so that the strided
+// writes of the first Stockham passes (consecutive butterflies 16 entries apart) spread over the
+// banks instead of landing on one. A buffer of S entries takes SPAD(S) slots.
+__host__ __device__ constexpr int SPAD(int i) { return i + (i >> 5); }
 
 __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
@@ -114,6 +120,39 @@ __device__ __forceinline__ void dft8(float2* b) {  // y[r] = sum_q b[q] exp(DIR 
   }
 }
 
+// y[r] = sum_q b[q] exp(DIR 2 pi i q r / 16) as 4 x 4: DFT4 over q1 of b[4 q1 + q2], times
+// exp(DIR 2 pi i q2 r1 / 16), then DFT4 over q2 into y[r1 + 4 r2].
+template <int DIR>
+__device__ __forceinline__ void dft16(float2* b) {
+  float2 c[4][4];
+#pragma unroll
+  for (int q2 = 0; q2 < 4; ++q2) {
+    float2 t[4] = {b[q2], b[4 + q2], b[8 + q2], b[12 + q2]};
+    dft4<DIR>(t);
+#pragma unroll
+    for (int r1 = 0; r1 < 4; ++r1) c[q2][r1] = t[r1];
+  }
+  const float c1 = 0.92387953251128676f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+  // exp(DIR 2 pi i k / 16) = (C_k, DIR S_k) for k = q2 r1 in {1, 2, 3, 4, 6, 9}
+  auto rot = [](float2 a, float C, float Sd) { return make_float2(a.x * C - a.y * Sd, a.x * Sd + a.y * C); };
+  c[1][1] = rot(c[1][1], c1, DIR * s1);
+  c[1][2] = rot(c[1][2], h, DIR * h);
+  c[1][3] = rot(c[1][3], s1, DIR * c1);
+  c[2][1] = rot(c[2][1], h, DIR * h);
+  c[2][2] = mul_i<DIR>(c[2][2]);
+  c[2][3] = rot(c[2][3], -h, DIR * h);
+  c[3][1] = rot(c[3][1], s1, DIR * c1);
+  c[3][2] = rot(c[3][2], -h, DIR * h);
+  c[3][3] = rot(c[3][3], -c1, -DIR * s1);
+#pragma unroll
+  for (int r1 = 0; r1 < 4; ++r1) {
+    float2 t[4] = {c[0][r1], c[1][r1], c[2][r1], c[3][r1]};
+    dft4<DIR>(t);
+#pragma unroll
+    for (int r2 = 0; r2 < 4; ++r2) b[r1 + 4 * r2] = t[r2];
+  }
+}
+
 // One in-place Stockham pass of radix R over the S points in shared memory, L = length of the
 // sub-transforms done so far: butterfly j = iL + k reads x[j + q S/R] (q < R), multiplies input q
 // by exp(DIR 2 pi i q k / (R L)), and writes output r to x[i R L + k + r L]. Every thread reads all
@@ -127,7 +166,7 @@ __device__ __forceinline__ void stockham_pass(float2* x, const float2* __restric
   for (int p = 0; p < PER; ++p) {
     const int j = threadIdx.x + p * THREADS;
 #pragma unroll
-    for (int q = 0; q < R; ++q) v[p][q] = x[j + q * NB];
+    for (int q = 0; q < R; ++q) v[p][q] = x[SPAD(j + q * NB)];
   }
   __syncthreads();
 #pragma unroll
@@ -138,12 +177,13 @@ __device__ __forceinline__ void stockham_pass(float2* x, const float2* __restric
     const int step = k * (S / (R * L));
 #pragma unroll
     for (int q = 1; q < R; ++q) v[p][q] = cmul(v[p][q], root_s<S, DIR>(tw, q * step));
-    if (R == 8) dft8<DIR>(v[p]);
+    if (R == 16) dft16<DIR>(v[p]);
+    else if (R == 8) dft8<DIR>(v[p]);
     else if (R == 4) dft4<DIR>(v[p]);
     else dft2<DIR>(v[p]);
-    float2* y = x + i * R * L + k;
+    const int y0 = i * R * L + k;
 #pragma unroll
-    for (int r = 0; r < R; ++r) y[r * L] = v[p][r];
+    for (int r = 0; r < R; ++r) x[SPAD(y0 + r * L)] = v[p][r];
   }
   __syncthreads();
 }
@@ -156,7 +196,10 @@ __device__ void fft_s(float2* x, const float2* __restrict__ tw) {
 #pragma unroll 1
   while (L < S) {
     const int rest = S / L;
-    if (rest >= 8) {
+    if (rest >= 16) {
+      stockham_pass<S, THREADS, 16, DIR>(x, tw, L);
+      L *= 16;
+    } else if (rest == 8) {
       stockham_pass<S, THREADS, 8, DIR>(x, tw, L);
       L *= 8;
     } else if (rest == 4) {
@@ -185,31 +228,49 @@ struct SpecArgs {
   const float2* tw;
 };
 
+// Bits [base, base + 2S - 1) of a seed of L bits (zero outside it) as z[n] = x[2n] + i x[2n+1]
+// into sx: the bytes are staged in shared memory first (one load per byte).
+template <int S, int THREADS, int BINS>
+__device__ __forceinline__ void stage_window(const uint8_t* __restrict__ seed, uint64_t L, int64_t base, float2* sx,
+                                             uint8_t* sb) {
+  const int64_t byte0 = base >= 0 ? base / 8 : -((-base + 7) / 8);
+  const int64_t lbytes = (int64_t)((L + 7) / 8);
+  for (int i = threadIdx.x; i < S / 4 + 2; i += THREADS) {
+    const int64_t bi = byte0 + i;
+    sb[i] = (bi >= 0 && bi < lbytes) ? __ldg(seed + bi) : (uint8_t)0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int p = 0; p < BINS; ++p) {
+    const int n = threadIdx.x + p * THREADS;
+    float v[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int u = 2 * n + h;
+      const int64_t xi = base + u;
+      v[h] = (u < 2 * S - 1 && xi >= 0 && xi < (int64_t)L) ? (float)((sb[(xi >> 3) - byte0] >> (xi & 7)) & 1u) : 0.f;
+    }
+    sx[SPAD(n)] = make_float2(v[0], v[1]);
+  }
+}
+
 template <int LOG_S>
-__global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS) seg_spectra_kernel(const SpecArgs a) {
+__global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS, SegCfg<LOG_S>::MIN_CTAS) seg_spectra_kernel(const SpecArgs a) {
   constexpr int S = SegCfg<LOG_S>::S, THREADS = SegCfg<LOG_S>::THREADS, BINS = SegCfg<LOG_S>::BINS;
   extern __shared__ float2 sx[];
+  uint32_t* sw = reinterpret_cast<uint32_t*>(sx + SPAD(S));  // staged input bits
   const uint64_t item = blockIdx.x;
   if (item >= a.items) return;
   // z[n] = x[2n] + i x[2n+1] of the real length-2S input
   if (a.seed) {
     const int64_t base = a.D + (a.dmin + (int64_t)item) * S - S + 1;
-#pragma unroll
-    for (int p = 0; p < BINS; ++p) {
-      const int n = threadIdx.x + p * THREADS;
-      float v[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int u = 2 * n + h;
-        const int64_t xi = base + u;
-        v[h] = (u < 2 * S - 1 && xi >= 0 && xi < (int64_t)a.L) ? (float)((__ldg(a.seed + (xi >> 3)) >> (xi & 7)) & 1u)
-                                                                : 0.f;
-      }
-      sx[n] = make_float2(v[0], v[1]);
-    }
+    stage_window<S, THREADS, BINS>(a.seed, a.L, base, sx, reinterpret_cast<uint8_t*>(sw));
   } else {
     const uint64_t b = item / a.NS, s = item - b * a.NS;
     const uint32_t* row = a.raw + b * a.raw_stride;
+    const uint64_t w0 = s * (S / 32);
+    for (int w = threadIdx.x; w < S / 32; w += THREADS) sw[w] = w0 + w < a.raw_stride ? __ldg(row + w0 + w) : 0u;
+    __syncthreads();
 #pragma unroll
     for (int p = 0; p < BINS; ++p) {
       const int n = threadIdx.x + p * THREADS;
@@ -217,11 +278,11 @@ __global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS) seg_spectra_kernel(con
       if (2 * n < S) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const uint64_t t = s * S + 2 * n + h;
-          v[h] = t < a.n_t ? (float)((__ldg(row + (t >> 5)) >> (t & 31)) & 1u) : 0.f;
+          const int u = 2 * n + h;
+          v[h] = s * S + u < a.n_t ? (float)((sw[u >> 5] >> (u & 31)) & 1u) : 0.f;
         }
       }
-      sx[n] = make_float2(v[0], v[1]);
+      sx[SPAD(n)] = make_float2(v[0], v[1]);
     }
   }
   __syncthreads();
@@ -231,12 +292,12 @@ __global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS) seg_spectra_kernel(con
 #pragma unroll
   for (int p = 0; p < BINS; ++p) {
     const int k = threadIdx.x + p * THREADS;
-    const float2 zk = sx[k];
+    const float2 zk = sx[SPAD(k)];
     float2 X;
     if (k == 0) {
       X = make_float2(zk.x + zk.y, zk.x - zk.y);  // (DC, Nyquist)
     } else {
-      const float2 zm = cconj(sx[S - k]);
+      const float2 zm = cconj(sx[SPAD(S - k)]);
       const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
       const float2 d = csub(zk, zm);
       const float2 o = make_float2(0.5f * d.y, -0.5f * d.x);
@@ -312,7 +373,7 @@ __device__ float mac_tiles(const float2* __restrict__ segs, const float2* __rest
     for (int j = 0; j < Q; ++j) {
       if ((uint32_t)j >= nq) break;
 #pragma unroll
-      for (int p = 0; p < BINS; ++p) sx[threadIdx.x + p * THREADS] = acc[j][p];
+      for (int p = 0; p < BINS; ++p) sx[SPAD(threadIdx.x + p * THREADS)] = acc[j][p];
       __syncthreads();
       // inverse split: Z_k = E_k + i O_k, E = (X_k + conj X_{S-k}) / 2, O = (X_k - conj X_{S-k}) / 2 e^{+2 pi i k / N}
       float2 zv[BINS];
@@ -321,11 +382,11 @@ __device__ float mac_tiles(const float2* __restrict__ segs, const float2* __rest
         const int k = threadIdx.x + p * THREADS;
         float2 xk, xm;
         if (k == 0) {
-          xk = make_float2(sx[0].x, 0.f);
-          xm = make_float2(sx[0].y, 0.f);  // the Nyquist bin, partner of DC
+          xk = make_float2(sx[SPAD(0)].x, 0.f);
+          xm = make_float2(sx[SPAD(0)].y, 0.f);  // the Nyquist bin, partner of DC
         } else {
-          xk = sx[k];
-          xm = sx[S - k];
+          xk = sx[SPAD(k)];
+          xm = sx[SPAD(S - k)];
         }
         xm = cconj(xm);
         const float2 e = make_float2(0.5f * (xk.x + xm.x), 0.5f * (xk.y + xm.y));
@@ -335,7 +396,7 @@ __device__ float mac_tiles(const float2* __restrict__ segs, const float2* __rest
       }
       __syncthreads();
 #pragma unroll
-      for (int p = 0; p < BINS; ++p) sx[threadIdx.x + p * THREADS] = zv[p];
+      for (int p = 0; p < BINS; ++p) sx[SPAD(threadIdx.x + p * THREADS)] = zv[p];
       __syncthreads();
       fft_s<S, THREADS, +1>(sx, tw);
       // c[t], t = S - 1 + i': even t in z[t/2].x, odd t in z[(t-1)/2].y (scale 1/S)
@@ -344,7 +405,7 @@ __device__ float mac_tiles(const float2* __restrict__ segs, const float2* __rest
       for (int p = 0; p < BINS; ++p) {
         const int ip = threadIdx.x + p * THREADS;
         const int t = S - 1 + ip;
-        const float2 z = sx[t >> 1];
+        const float2 z = sx[SPAD(t >> 1)];
         const float v = ((t & 1) ? z.y : z.x) * (1.0f / (float)S);
         const float r = rintf(v);
         // a sum of 2^20 or more (FP32 spacing 1/8 and coarser) cannot show its rounding distance:
@@ -376,10 +437,10 @@ __device__ void report_err(float err, unsigned long long* worst, int* guard_flag
 }
 
 template <int LOG_S, int Q>
-__global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS) seg_mac_kernel(const MacArgs a) {
+__global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS, SegCfg<LOG_S>::MIN_CTAS) seg_mac_kernel(const MacArgs a) {
   constexpr int S = SegCfg<LOG_S>::S, THREADS = SegCfg<LOG_S>::THREADS, WORDS = S / 32;
   extern __shared__ float2 sx[];
-  uint32_t* bits = reinterpret_cast<uint32_t*>(sx + S);  // Q x WORDS tile bits
+  uint32_t* bits = reinterpret_cast<uint32_t*>(sx + SPAD(S));  // Q x WORDS tile bits
   const uint64_t b = blockIdx.x / a.NQG;
   const uint32_t q0 = (uint32_t)(blockIdx.x - b * a.NQG) * Q;
   const uint32_t nq = min((uint32_t)Q, a.NQ - q0);
@@ -439,31 +500,28 @@ __device__ __forceinline__ uint32_t find_request(const BatchReq* __restrict__ re
 // One CTA per spectra item of a group: request r's windows d = -(NS-1) .. NQ-1 first, then its
 // segments, each into row spec_row + local item.
 template <int LOG_S>
-__global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS) seg_batch_spectra_kernel(const BatchReq* __restrict__ reqs,
-                                                                                   uint32_t nr, float2* __restrict__ spec,
-                                                                                   const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS, SegCfg<LOG_S>::MIN_CTAS)
+    seg_batch_spectra_kernel(const BatchReq* __restrict__ reqs, uint32_t nr, float2* __restrict__ spec,
+                             const float2* __restrict__ tw) {
   constexpr int S = SegCfg<LOG_S>::S, THREADS = SegCfg<LOG_S>::THREADS, BINS = SegCfg<LOG_S>::BINS;
   extern __shared__ float2 sx[];
+  uint8_t* sb = reinterpret_cast<uint8_t*>(sx + SPAD(S));  // staged input bytes
   const uint64_t item = blockIdx.x;
   const BatchReq& q = reqs[find_request<&BatchReq::spec_item_begin>(reqs, nr, item)];
   const uint64_t local = item - q.spec_item_begin;
   const uint64_t nw = (uint64_t)q.seg_nq + q.seg_ns - 1;
   if (local < nw) {
     const int64_t base = (int64_t)q.n_t - 1 + ((int64_t)local - (int64_t)(q.seg_ns - 1)) * S - S + 1;
-#pragma unroll
-    for (int p = 0; p < BINS; ++p) {
-      const int n = threadIdx.x + p * THREADS;
-      float v[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int u = 2 * n + h;
-        const int64_t xi = base + u;
-        v[h] = (u < 2 * S - 1 && xi >= 0 && xi < (int64_t)q.L_t) ? (float)byte_bit(q.seed, (uint64_t)xi) : 0.f;
-      }
-      sx[n] = make_float2(v[0], v[1]);
-    }
+    stage_window<S, THREADS, BINS>(q.seed, q.L_t, base, sx, sb);
   } else {
+    // the segment's bits: only the bytes holding raw bits [sg S, min(n_t, (sg+1) S)) are read
     const uint64_t sg = local - nw;
+    const uint64_t bit0 = q.raw_bit_off + sg * S;
+    const uint64_t end = q.raw_bit_off + (q.n_t < (sg + 1) * S ? q.n_t : (sg + 1) * S);
+    const uint64_t byte0 = bit0 >> 3, byte_end = (end + 7) >> 3;
+    for (uint64_t i = threadIdx.x; i < (uint64_t)S / 8 + 1; i += THREADS)
+      sb[i] = byte0 + i < byte_end ? __ldg(q.raw + byte0 + i) : (uint8_t)0;
+    __syncthreads();
 #pragma unroll
     for (int p = 0; p < BINS; ++p) {
       const int n = threadIdx.x + p * THREADS;
@@ -471,11 +529,12 @@ __global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS) seg_batch_spectra_kern
       if (2 * n < S) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-          const uint64_t t = sg * S + 2 * n + h;
-          v[h] = t < q.n_t ? (float)byte_bit(q.raw, q.raw_bit_off + t) : 0.f;
+          const uint64_t u = 2 * n + h;
+          const uint64_t g = bit0 + u;
+          v[h] = sg * S + u < q.n_t ? (float)((sb[(g >> 3) - byte0] >> (g & 7)) & 1u) : 0.f;
         }
       }
-      sx[n] = make_float2(v[0], v[1]);
+      sx[SPAD(n)] = make_float2(v[0], v[1]);
     }
   }
   __syncthreads();
@@ -484,12 +543,12 @@ __global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS) seg_batch_spectra_kern
 #pragma unroll
   for (int p = 0; p < BINS; ++p) {
     const int k = threadIdx.x + p * THREADS;
-    const float2 zk = sx[k];
+    const float2 zk = sx[SPAD(k)];
     float2 X;
     if (k == 0) {
       X = make_float2(zk.x + zk.y, zk.x - zk.y);
     } else {
-      const float2 zm = cconj(sx[S - k]);
+      const float2 zm = cconj(sx[SPAD(S - k)]);
       const float2 e = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y + zm.y));
       const float2 d = csub(zk, zm);
       const float2 o = make_float2(0.5f * d.y, -0.5f * d.x);
@@ -501,14 +560,14 @@ __global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS) seg_batch_spectra_kern
 
 // One CTA per (request, group of Q tiles) of a group; output words into the request's staging.
 template <int LOG_S, int Q>
-__global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS) seg_batch_mac_kernel(const BatchReq* __restrict__ reqs,
+__global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS, SegCfg<LOG_S>::MIN_CTAS) seg_batch_mac_kernel(const BatchReq* __restrict__ reqs,
                                                                                uint32_t nr, const float2* __restrict__ spec,
                                                                                const float2* __restrict__ tw, uint32_t T,
                                                                                uint32_t* __restrict__ out_stage,
                                                                                unsigned long long* __restrict__ worst) {
   constexpr int S = SegCfg<LOG_S>::S, THREADS = SegCfg<LOG_S>::THREADS, WORDS = S / 32;
   extern __shared__ float2 sx[];
-  uint32_t* bits = reinterpret_cast<uint32_t*>(sx + S);
+  uint32_t* bits = reinterpret_cast<uint32_t*>(sx + SPAD(S));
   const BatchReq& q = reqs[find_request<&BatchReq::mac_cta_begin>(reqs, nr, blockIdx.x)];
   const uint32_t q0 = (uint32_t)(blockIdx.x - q.mac_cta_begin) * Q;
   const uint32_t nq = min((uint32_t)Q, q.seg_nq - q0);
@@ -532,7 +591,7 @@ __global__ void __launch_bounds__(SegCfg<LOG_S>::THREADS) seg_batch_mac_kernel(c
 
 template <int LOG_S>
 size_t mac_smem(int Q) {
-  return (size_t)(1 << LOG_S) * sizeof(float2) + (size_t)Q * ((1 << LOG_S) / 32) * sizeof(uint32_t);
+  return (size_t)SPAD(1 << LOG_S) * sizeof(float2) + (size_t)Q * ((1 << LOG_S) / 32) * sizeof(uint32_t);
 }
 
 template <int LOG_S, int Q>
@@ -544,9 +603,15 @@ cudaError_t launch_mac(const MacArgs& m, unsigned ctas, cudaStream_t s) {
   return cudaGetLastError();
 }
 
+// the transform buffer and the staged input bits (S/4 + 2 bytes of a seed window at most)
+template <int LOG_S>
+size_t spectra_smem() {
+  return (size_t)SPAD(1 << LOG_S) * sizeof(float2) + (size_t)(1 << LOG_S) / 4 + 16;
+}
+
 template <int LOG_S>
 cudaError_t launch_spectra(const SpecArgs& sa, cudaStream_t s) {
-  const size_t smem = (size_t)(1 << LOG_S) * sizeof(float2);
+  const size_t smem = spectra_smem<LOG_S>();
   cudaError_t e = cudaFuncSetAttribute(seg_spectra_kernel<LOG_S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)smem);
   if (e != cudaSuccess) return e;
@@ -555,19 +620,9 @@ cudaError_t launch_spectra(const SpecArgs& sa, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-// Tiles per MAC CTA: the largest Q <= qmax that leaves the fewest idle accumulators.
-int pick_q(uint32_t NQ, int qmax) {
-  int best = 1;
-  uint64_t best_waste = ~0ull;
-  for (int q = qmax; q >= 1; --q) {
-    const uint64_t waste = ceil_div(NQ, q) * q - NQ;
-    if (waste < best_waste) {
-      best = q;
-      best_waste = waste;
-    }
-  }
-  return best;
-}
+// Tiles per multiply-and-inverse CTA: as many as its accumulators hold (each segment spectrum the
+// CTA loads then serves that many tiles).
+int pick_q(uint32_t NQ, int qmax) { return (int)(NQ < (uint32_t)qmax ? NQ : (uint32_t)qmax); }
 
 template <int LOG_S>
 cudaError_t run_fft32(const DirectArgs& d, const uint8_t* seed, uint64_t L_t, int T, FftWorkspace& ws,
@@ -638,15 +693,8 @@ cudaError_t run_fft32(const DirectArgs& d, const uint8_t* seed, uint64_t L_t, in
     m.guard_flag = guard_flag;
     const uint64_t ctas = nb * NQG;
     if (ctas > 0x7fffffffull) return cudaErrorInvalidConfiguration;
-    if constexpr (SegCfg<LOG_S>::QMAX >= 4) {
-      if (Q == 4) e = launch_mac<LOG_S, 4>(m, (unsigned)ctas, s);
-      else if (Q == 3) e = launch_mac<LOG_S, 3>(m, (unsigned)ctas, s);
-      else if (Q == 2) e = launch_mac<LOG_S, 2>(m, (unsigned)ctas, s);
-      else e = launch_mac<LOG_S, 1>(m, (unsigned)ctas, s);
-    } else {
-      if (Q == 2) e = launch_mac<LOG_S, 2>(m, (unsigned)ctas, s);
-      else e = launch_mac<LOG_S, 1>(m, (unsigned)ctas, s);
-    }
+    if (Q == 2) e = launch_mac<LOG_S, 2>(m, (unsigned)ctas, s);
+    else e = launch_mac<LOG_S, 1>(m, (unsigned)ctas, s);
     if (e != cudaSuccess) return e;
     ++*kernels;
   }
@@ -678,7 +726,7 @@ cudaError_t run_fft32_batch(const BatchReq* reqs, uint64_t nr, uint64_t spec_ite
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     ws.tw32_S = S;
   }
-  const size_t smem = (size_t)S * sizeof(float2);
+  const size_t smem = spectra_smem<LOG_S>();
   if ((e = cudaFuncSetAttribute(seg_batch_spectra_kernel<LOG_S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 (int)smem)) != cudaSuccess)
     return e;
@@ -695,7 +743,7 @@ cudaError_t run_fft32_batch(const BatchReq* reqs, uint64_t nr, uint64_t spec_ite
 
 }  // namespace
 
-int fft32_batch_tiles(int log_s) { return log_s >= 13 ? SegCfg<13>::QMAX : SegCfg<12>::QMAX; }
+int fft32_batch_tiles(int) { return SegCfg<12>::QMAX; }
 
 cudaError_t launch_fft32_batch(const BatchReq* reqs_dev, uint64_t nr, uint64_t spec_items, uint64_t mac_ctas,
                                int log_s, int T, FftWorkspace& ws, uint32_t* out_stage, cudaStream_t s,
@@ -727,7 +775,7 @@ double fft32_model_seconds(uint64_t n_t, uint64_t m, uint64_t B, int log_s, int 
   // operand from L2 at ~12 TB/s, a segment's shared by the Q tiles of a CTA)
   const double S = ldexp(1.0, log_s);
   const double NS = (double)ceil_div(n_t, (uint64_t)S), NQ = (double)ceil_div(m, (uint64_t)S);
-  const double Q = (double)pick_q((uint32_t)NQ, log_s >= 13 ? 2 : 4);
+  const double Q = (double)pick_q((uint32_t)NQ, 2);
   const double ffts = NS + NQ * std::ceil(NS / (double)T);
   const double flops_fft = ffts * 5.0 * S * log_s;
   const double flops_mac = NQ * NS * S * 8.0;

@@ -1,8 +1,10 @@
 // Min-entropy estimate of an ADC sample stream (Sec. II of the paper):
-//   1. exact histogram of the codes (warp-privatised shared-memory counters, one pass over HBM);
-//   2. a one-CTA FP64 finaliser: H_min of the measured distribution (Sec. II.A), the Gaussian
-//      model fixed by the measured mean and variance (Sec. II.B), the statistical distance d_U,
-//      the finite-size term, Delta H_m and H_modify (Sec. II.C).
+//   1. exact histogram of the codes (privatised shared-memory counters, one pass over HBM);
+//   2. an FP64 finaliser in two kernels: exact integer moments, H_min of the measured distribution
+//      (Sec. II.A) and the Gaussian model fixed by the measured mean and variance (Sec. II.B) in
+//      one CTA; the model cells, the statistical distance d_U, the finite-size term, Delta H_m and
+//      H_modify (Sec. II.C) over many CTAs (FP64 runs at a few operations per clock per SM).
+#include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <math_constants.h>
@@ -17,7 +19,9 @@ constexpr int kHistThreads = 256;
 constexpr int kHistWarps = kHistThreads / 32;
 
 // bits <= 8: each warp owns 256 counters; codes >= 2^bits land in counters the merge step
-// adds to the out-of-range total.
+// adds to the out-of-range total. One shared-memory atomic per sample: on GB300 the atomics, at
+// about 9 per clock per SM, bound the kernel (copies per lane, which remove every bank conflict and
+// every collision inside a warp, were measured slower: they cost occupancy and instructions).
 __global__ void __launch_bounds__(kHistThreads) hist_u8_kernel(const uint8_t* __restrict__ samples, uint64_t count,
                                                                 int bits, unsigned long long* __restrict__ hist) {
   __shared__ uint32_t sh[kHistWarps][256];
@@ -55,18 +59,26 @@ __global__ void __launch_bounds__(kHistThreads) hist_u8_kernel(const uint8_t* __
   }
 }
 
+// Sample i of a little-endian uint16 stream at any byte address (two byte loads when it is odd).
+__device__ __forceinline__ uint32_t load_u16(const void* __restrict__ p, uint64_t i, bool odd) {
+  if (!odd) return __ldcs(static_cast<const uint16_t*>(p) + i);
+  const uint8_t* b = static_cast<const uint8_t*>(p) + 2 * i;
+  return (uint32_t)__ldcs(b) | ((uint32_t)__ldcs(b + 1) << 8);
+}
+
 // 9 <= bits <= 13: one shared histogram per CTA (<= 8192 counters + one out-of-range counter).
-__global__ void __launch_bounds__(kHistThreads) hist_u16_smem_kernel(const uint16_t* __restrict__ samples,
+__global__ void __launch_bounds__(kHistThreads) hist_u16_smem_kernel(const void* __restrict__ samples,
                                                                       uint64_t count, int bits,
                                                                       unsigned long long* __restrict__ hist) {
   extern __shared__ uint32_t shc[];
   const uint32_t K = 1u << bits;
+  const bool odd = reinterpret_cast<uintptr_t>(samples) & 1;
   for (uint32_t i = threadIdx.x; i <= K; i += blockDim.x) shc[i] = 0;
   __syncthreads();
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t s = tid; s < count; s += nthreads) {
-    uint32_t v = __ldcs(samples + s);
+    uint32_t v = load_u16(samples, s, odd);
     atomicAdd(&shc[v < K ? v : K], 1u);
   }
   __syncthreads();
@@ -74,17 +86,82 @@ __global__ void __launch_bounds__(kHistThreads) hist_u16_smem_kernel(const uint1
     if (shc[b]) atomicAdd(&hist[b], (unsigned long long)shc[b]);
 }
 
-// 14 <= bits <= 16: counters straight in global memory.
-__global__ void __launch_bounds__(kHistThreads) hist_u16_global_kernel(const uint16_t* __restrict__ samples,
-                                                                        uint64_t count, int bits,
-                                                                        unsigned long long* __restrict__ hist) {
-  const uint32_t K = 1u << bits;
+// 14 <= bits <= 16: every CTA counts all 2^bits codes in shared memory as 16-bit halves of 32-bit
+// words (2^15 words for 16 bits), one atomic per sample. A half that wraps past 0xffff is fixed up
+// at once: the atomic's old value shows the wrap, so exactly one thread takes the 2^16 out of the
+// word (a carry into the upper half is subtracted) and adds it to the global counter. Two CTAs form
+// a cluster: after a cluster barrier each adds one half of the codes over both CTAs' shared
+// memory (distributed shared-memory loads) to the global histogram, so only one flush per pair of
+// SMs reaches global atomics. No scratch beyond the 2^bits + 1 output counters.
+constexpr int kH16Threads = 1024;
+
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kH16Threads, 1)
+    hist_u16_cluster_kernel(const void* __restrict__ samples_v, uint64_t count, int bits,
+                            unsigned long long* __restrict__ hist) {
+  extern __shared__ uint32_t shw[];  // 2^(bits-1) words, codes 2w and 2w+1
+  namespace cg = cooperative_groups;
+  cg::cluster_group cluster = cg::this_cluster();
+  const uint32_t K = 1u << bits, W = K / 2;
+  for (uint32_t i = threadIdx.x; i < W; i += blockDim.x) shw[i] = 0u;
+  cluster.sync();
+  unsigned long long bad = 0;
+  auto add = [&](uint32_t v) {
+    if (v >= K) {
+      ++bad;
+      return;
+    }
+    const uint32_t sh = (v & 1u) << 4;
+    const uint32_t old = atomicAdd(&shw[v >> 1], 1u << sh);
+    if (((old >> sh) & 0xffffu) == 0xffffu) {  // this add wrapped the half: move 2^16 to global memory
+      if (sh == 0) atomicSub(&shw[v >> 1], 0x10000u);
+      atomicAdd(&hist[v], 65536ull);
+    }
+  };
   const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const uint64_t nthreads = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t s = tid; s < count; s += nthreads) {
-    uint32_t v = __ldcs(samples + s);
-    atomicAdd(&hist[v < K ? v : K], 1ull);
+  if (reinterpret_cast<uintptr_t>(samples_v) & 1) {  // an odd address: one sample from two bytes at a time
+    for (uint64_t i = tid; i < count; i += nthreads) add(load_u16(samples_v, i, true));
+    count = 0;
   }
+  const uint16_t* samples = static_cast<const uint16_t*>(samples_v);
+  const uint64_t head = ((16 - (reinterpret_cast<uintptr_t>(samples) & 15)) & 15) / 2;
+  const uint64_t nhead = head < count ? head : count;
+  if (tid < nhead) add(samples[tid]);
+  const uint64_t nvec = (count - nhead) / 8;
+  const uint4* vec = reinterpret_cast<const uint4*>(samples + nhead);
+  for (uint64_t v = tid; v < nvec; v += 2 * nthreads) {
+    const uint4 x0 = __ldcs(vec + v);
+    const uint4 x1 = v + nthreads < nvec ? __ldcs(vec + v + nthreads) : make_uint4(0u, 0u, 0u, 0u);
+    const uint32_t w0[4] = {x0.x, x0.y, x0.z, x0.w};
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      add(w0[q] & 0xffffu);
+      add(w0[q] >> 16);
+    }
+    if (v + nthreads < nvec) {
+      const uint32_t w1[4] = {x1.x, x1.y, x1.z, x1.w};
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        add(w1[q] & 0xffffu);
+        add(w1[q] >> 16);
+      }
+    }
+  }
+  const uint64_t tail0 = nhead + nvec * 8;
+  if (tail0 + tid < count) add(samples[tail0 + tid]);
+  if (bad) atomicAdd(&hist[K], bad);
+  cluster.sync();  // both CTAs' counts are complete
+  const uint32_t r = cluster.block_rank(), per = W / 2;
+  const uint32_t* mine = shw;
+  const uint32_t* peer = cluster.map_shared_rank(shw, r ^ 1u);
+  for (uint32_t i = threadIdx.x; i < per; i += blockDim.x) {
+    const uint32_t wi = r * per + i;
+    const uint32_t a = mine[wi], b = peer[wi];
+    const uint32_t lo = (a & 0xffffu) + (b & 0xffffu), hi = (a >> 16) + (b >> 16);
+    if (lo) atomicAdd(&hist[2 * wi], (unsigned long long)lo);
+    if (hi) atomicAdd(&hist[2 * wi + 1], (unsigned long long)hi);
+  }
+  cluster.sync();  // the peer has read this CTA's counts before either exits
 }
 
 // ------------------------------------------------------------------------------------------------
@@ -121,55 +198,18 @@ __device__ __forceinline__ double cell_from_tails(double lo, double hi, double c
   return 0.5 * (erf(hi * M_SQRT1_2) - erf(lo * M_SQRT1_2));
 }
 
-constexpr uint32_t kFinChunk = 2048;  // cells per shared-memory chunk of boundary tails
-
-// Model cells of codes [0, K) under N(mu, sigma^2) (boundaries v +- 1/2, end codes take the tails):
-// each boundary's tail is computed once per chunk; returns this thread's largest cell, its sum of
-// |hist/N - P| (when dist) and, for code `want`, its cell in *p_want.
-__device__ void model_cells(const unsigned long long* __restrict__ hist, uint32_t K, unsigned long long N, double mu,
-                            double sigma, bool dist, uint32_t want, double* __restrict__ s_tail, double& pmax,
-                            double& dsum, double* p_want) {
-  for (uint32_t c0 = 0; c0 < K; c0 += kFinChunk) {
-    const uint32_t ncell = (K - c0) < kFinChunk ? (K - c0) : kFinChunk;
-    // s_tail[i] = tail of boundary c0 - 1 + i, i = 0 .. ncell (boundary j lies between codes j, j + 1)
-    for (uint32_t i = threadIdx.x; i <= ncell; i += blockDim.x) {
-      const int64_t j = (int64_t)c0 - 1 + i;
-      const double z = (j < 0 || j >= (int64_t)K - 1) ? CUDART_INF : (((double)j + 0.5 - mu) / sigma);
-      s_tail[i] = erfc(fabs(z) * M_SQRT1_2);
-    }
-    __syncthreads();
-    for (uint32_t i = threadIdx.x; i < ncell; i += blockDim.x) {
-      const uint32_t v = c0 + i;
-      const double lo = (v == 0) ? -CUDART_INF : ((double)v - 0.5 - mu) / sigma;
-      const double hi = (v == K - 1) ? CUDART_INF : ((double)v + 0.5 - mu) / sigma;
-      const double P = cell_from_tails(lo, hi, s_tail[i], s_tail[i + 1]);
-      pmax = fmax(pmax, P);
-      if (dist) dsum += fabs((double)hist[v] / (double)N - P);
-      if (v == want) *p_want = P;
-    }
-    __syncthreads();
-  }
-}
-
-__global__ void __launch_bounds__(kFinThreads) hmin_finalize_kernel(const unsigned long long* __restrict__ hist,
-                                                                     int bits, double eps,
-                                                                     DevHminResult* __restrict__ out, double var_sub,
-                                                                     double h_ref) {
+// Pass 1, one CTA: count, exact first and second moments (128-bit integers), largest bin (lowest
+// code on ties), mean, population variance, the model's sigma (and the quantum model's), the
+// report's integer and moment fields and its status; clears the accumulators of pass 2.
+__global__ void __launch_bounds__(kFinThreads) hmin_moments_kernel(const unsigned long long* __restrict__ hist,
+                                                                    int bits, DevHminResult* __restrict__ out,
+                                                                    double var_sub) {
   constexpr int kWarps = kFinThreads / 32;
   __shared__ unsigned long long w_n[kWarps], w_max[kWarps];
   __shared__ uint32_t w_arg[kWarps];
   __shared__ u128_t w_s1[kWarps], w_s2[kWarps];
-  __shared__ double w_pmax[kWarps], w_pmax_full[kWarps], w_dsum[kWarps];
-  __shared__ double s_tail[kFinChunk + 1];
-  __shared__ double s_mu, s_sigma, s_sigma_q, s_pa;
-  __shared__ unsigned long long s_N, s_max;
-  __shared__ uint32_t s_arg;
-  __shared__ int s_point, s_bad_sub;
-
   const uint32_t K = 1u << bits;
   const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
-
-  // Pass 1: count, exact first and second moments, largest bin (lowest code on ties).
   unsigned long long n = 0, mx = 0;
   uint32_t arg = 0xffffffffu;
   u128_t s1 = 0, s2 = 0;
@@ -193,92 +233,142 @@ __global__ void __launch_bounds__(kFinThreads) hmin_finalize_kernel(const unsign
     w_n[wid] = n; w_s1[wid] = s1; w_s2[wid] = s2; w_max[wid] = mx; w_arg[wid] = arg;
   }
   __syncthreads();
-  if (t == 0) {
-    unsigned long long N = 0, M = 0;
-    uint32_t A = 0xffffffffu;
-    u128_t S1 = 0, S2 = 0;
-    for (int w = 0; w < kWarps; ++w) {
-      N += w_n[w]; S1 += w_s1[w]; S2 += w_s2[w];
-      max_arg_merge(M, A, w_max[w], w_arg[w]);
-    }
-    s_N = N; s_max = M; s_arg = A;
-    if (N == 0) {
-      out->status = QRNG_EINVAL;
-    } else {
-      const u128_t num = (u128_t)N * S2 - S1 * S1;  // N^2 * population variance, exact
-      const double mu = (double)S1 / (double)N;
-      const double var = (double)num / ((double)N * (double)N);
-      s_mu = mu;
-      s_sigma = sqrt(var);
-      s_point = (num == 0);
-      const double var_q = var - var_sub;
-      s_bad_sub = (var_sub > 0.0) && !(var_q > 0.0);
-      s_sigma_q = var_sub > 0.0 && var_q > 0.0 ? sqrt(var_q) : s_sigma;
-      qrng_hmin_report& r = out->rep;
-      r.count = N;
-      r.max_count = M;
-      r.argmax = A;
-      r.bits = (uint32_t)bits;
-      r.mean = mu;
-      r.var = var;
-      r.h_emp = -log2((double)M / (double)N);
-      out->out_of_range = hist[K];
-    }
+  if (t != 0) return;
+  unsigned long long N = 0, M = 0;
+  uint32_t A = 0xffffffffu;
+  u128_t S1 = 0, S2 = 0;
+  for (int w = 0; w < kWarps; ++w) {
+    N += w_n[w]; S1 += w_s1[w]; S2 += w_s2[w];
+    max_arg_merge(M, A, w_max[w], w_arg[w]);
   }
-  __syncthreads();
-  const unsigned long long N = s_N;
-  if (N == 0) return;
+  out->n = N;
+  out->out_of_range = hist[K];
+  out->pmax_bits = 0;
+  out->pmax_full_bits = 0;
+  out->dsum_fixed = 0;
+  out->p_argmax = 0.0;
+  out->done = 0;
+  if (N == 0) {
+    out->status = QRNG_EINVAL;
+    return;
+  }
+  const u128_t num = (u128_t)N * S2 - S1 * S1;  // N^2 * population variance, exact
+  const double mu = (double)S1 / (double)N;
+  const double var = (double)num / ((double)N * (double)N);
+  const double var_q = var - var_sub;
+  const int bad_sub = (var_sub > 0.0) && !(var_q > 0.0);
+  out->mu = mu;
+  out->sigma = sqrt(var);
+  out->point = (num == 0);
+  out->bad_sub = bad_sub;
+  out->sigma_q = var_sub > 0.0 && var_q > 0.0 ? sqrt(var_q) : out->sigma;
+  qrng_hmin_report& r = out->rep;
+  r.count = N;
+  r.max_count = M;
+  r.argmax = A;
+  r.bits = (uint32_t)bits;
+  r.mean = mu;
+  r.var = (var_sub > 0.0 && !bad_sub) ? var_q : var;
+  r.h_emp = -log2((double)M / (double)N);
+  out->status = (hist[K] || bad_sub) ? QRNG_EINVAL : QRNG_OK;
+}
 
-  // Pass 2: model cells, their maximum, and the distance to the measured distribution.
-  const double mu = s_mu, sigma = s_sigma;
-  const bool sub = var_sub > 0.0 && !s_bad_sub;
-  const uint32_t amax = s_arg;
-  double pmax_full = 0.0, dsum = 0.0, pmax = 0.0;
-  if (s_point) {  // every sample on one code: the model is that point mass
-    for (uint32_t v = t; v < K; v += kFinThreads) {
-      const double P = (v == amax) ? 1.0 : 0.0;
-      pmax_full = fmax(pmax_full, P);
-      dsum += fabs((double)hist[v] / (double)N - P);
-    }
-    if (t == 0) s_pa = 1.0;
-    pmax = pmax_full;
-  } else {
-    double pa = 0.0;
-    model_cells(hist, K, N, mu, sigma, true, amax, s_tail, pmax_full, dsum, &pa);
-    if (amax % (uint32_t)kFinThreads == (uint32_t)t) s_pa = pa;  // the thread that visited code amax
-    if (sub) {
-      double unused_d = 0.0, unused_p = 0.0;
-      model_cells(hist, K, N, mu, s_sigma_q, false, K, s_tail, pmax, unused_d, &unused_p);
-    } else {
-      pmax = pmax_full;
-    }
-  }
-  for (int d = 16; d > 0; d >>= 1) {
-    pmax = fmax(pmax, __shfl_down_sync(0xffffffffu, pmax, d));
-    pmax_full = fmax(pmax_full, __shfl_down_sync(0xffffffffu, pmax_full, d));
-    dsum += __shfl_down_sync(0xffffffffu, dsum, d);
-  }
-  if (lane == 0) {
-    w_pmax[wid] = pmax; w_pmax_full[wid] = pmax_full; w_dsum[wid] = dsum;
+constexpr int kCellThreads = 64;  // model cells per CTA of pass 2
+
+// Cell v = c0 + threadIdx.x of the model N(mu, sg^2) (boundaries v +- 1/2, end codes take the
+// tails): the CTA's kCellThreads + 1 boundary tails are computed once into s_tail.
+__device__ __forceinline__ double cta_cell(uint32_t c0, uint32_t K, double mu, double sg, double* s_tail) {
+  for (uint32_t i = threadIdx.x; i <= (uint32_t)kCellThreads; i += blockDim.x) {
+    const int64_t j = (int64_t)c0 - 1 + i;  // boundary j lies between codes j and j + 1
+    const double z = (j < 0 || j >= (int64_t)K - 1) ? CUDART_INF : (((double)j + 0.5 - mu) / sg);
+    s_tail[i] = erfc(fabs(z) * M_SQRT1_2);
   }
   __syncthreads();
-  if (t == 0) {
-    double PM = 0.0, PF = 0.0, DS = 0.0;
-    for (int w = 0; w < kWarps; ++w) {
-      PM = fmax(PM, w_pmax[w]); PF = fmax(PF, w_pmax_full[w]); DS += w_dsum[w];
-    }
-    qrng_hmin_report& r = out->rep;
-    r.h_model = -log2(PM);
-    out->h_subtracted = -log2(PF) - h_ref;
-    if (sub) r.var = s_sigma_q * s_sigma_q;
-    r.d_u = 0.5 * DS;
-    r.d_u_peak = 0.5 * fabs((double)s_max / (double)N - s_pa);
-    r.delta_fs = 0.5 * sqrt(2.0 * ((double)K * M_LN2 + log(1.0 / eps)) / (double)N);
-    r.delta_hm = log2((r.d_u + r.delta_fs) * ldexp(1.0, bits + 1) + 1.0);
-    double h = r.h_model - r.delta_hm;
-    r.h_modify = h > 0.0 ? h : 0.0;
-    out->status = (out->out_of_range || s_bad_sub) ? QRNG_EINVAL : QRNG_OK;
+  const uint32_t v = c0 + threadIdx.x;
+  double P = 0.0;
+  if (v < K) {
+    const double lo = (v == 0) ? -CUDART_INF : ((double)v - 0.5 - mu) / sg;
+    const double hi = (v == K - 1) ? CUDART_INF : ((double)v + 0.5 - mu) / sg;
+    P = cell_from_tails(lo, hi, s_tail[threadIdx.x], s_tail[threadIdx.x + 1]);
   }
+  __syncthreads();
+  return P;
+}
+
+// Pass 2, ceil(K / kCellThreads) CTAs (the FP64 tails spread over the SMs): model cells, their
+// maximum and the distance to the measured distribution, folded into the result by atomics (the
+// distance as a 2^-62 fixed-point integer, so the sum does not depend on the order of the CTAs);
+// the last CTA to finish completes the report.
+__global__ void __launch_bounds__(kCellThreads) hmin_cells_kernel(const unsigned long long* __restrict__ hist,
+                                                                   int bits, double eps,
+                                                                   DevHminResult* __restrict__ out, double var_sub,
+                                                                   double h_ref) {
+  __shared__ double s_tail[kCellThreads + 1];
+  __shared__ double s_pm[kCellThreads / 32], s_pf[kCellThreads / 32];
+  __shared__ unsigned long long s_ds[kCellThreads / 32];
+  __shared__ int s_last;
+  const uint32_t K = 1u << bits;
+  const unsigned long long N = out->n;
+  if (N == 0) return;
+  const double mu = out->mu, sigma = out->sigma;
+  const uint32_t amax = out->rep.argmax;
+  const bool sub = var_sub > 0.0 && !out->bad_sub;
+  const uint32_t c0 = blockIdx.x * kCellThreads, v = c0 + threadIdx.x;
+  double P;
+  if (out->point) {  // every sample on one code: the model is that point mass
+    P = (v < K && v == amax) ? 1.0 : 0.0;
+  } else {
+    P = cta_cell(c0, K, mu, sigma, s_tail);
+  }
+  double pf = P, pm = P;
+  unsigned long long ds = 0;
+  if (v < K) {
+    ds = (unsigned long long)llrint(fabs((double)hist[v] / (double)N - P) * 0x1p62);
+    if (v == amax) out->p_argmax = out->point ? 1.0 : P;
+  }
+  if (sub && !out->point) pm = cta_cell(c0, K, mu, out->sigma_q, s_tail);
+  for (int d = 16; d > 0; d >>= 1) {
+    pm = fmax(pm, __shfl_down_sync(0xffffffffu, pm, d));
+    pf = fmax(pf, __shfl_down_sync(0xffffffffu, pf, d));
+    ds += __shfl_down_sync(0xffffffffu, ds, d);
+  }
+  if ((threadIdx.x & 31) == 0) {
+    s_pm[threadIdx.x >> 5] = pm;
+    s_pf[threadIdx.x >> 5] = pf;
+    s_ds[threadIdx.x >> 5] = ds;
+  }
+  __threadfence();  // p_argmax before the ticket
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double PM = 0.0, PF = 0.0;
+    unsigned long long DS = 0;
+    for (int w = 0; w < kCellThreads / 32; ++w) {
+      PM = fmax(PM, s_pm[w]);
+      PF = fmax(PF, s_pf[w]);
+      DS += s_ds[w];
+    }
+    atomicMax(&out->pmax_bits, (unsigned long long)__double_as_longlong(PM));  // non-negative doubles
+    atomicMax(&out->pmax_full_bits, (unsigned long long)__double_as_longlong(PF));
+    atomicAdd(&out->dsum_fixed, DS);
+    __threadfence();
+    s_last = atomicAdd(&out->done, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  const double PM = __longlong_as_double((long long)atomicAdd(&out->pmax_bits, 0ull));
+  const double PF = __longlong_as_double((long long)atomicAdd(&out->pmax_full_bits, 0ull));
+  const double DS = (double)atomicAdd(&out->dsum_fixed, 0ull) * 0x1p-62;
+  const double pa = *(volatile double*)&out->p_argmax;
+  qrng_hmin_report& r = out->rep;
+  r.h_model = -log2(PM);
+  out->h_subtracted = -log2(PF) - h_ref;
+  r.d_u = 0.5 * DS;
+  r.d_u_peak = 0.5 * fabs((double)r.max_count / (double)N - pa);
+  r.delta_fs = 0.5 * sqrt(2.0 * ((double)K * M_LN2 + log(1.0 / eps)) / (double)N);
+  r.delta_hm = log2((r.d_u + r.delta_fs) * ldexp(1.0, bits + 1) + 1.0);
+  const double h = r.h_model - r.delta_hm;
+  r.h_modify = h > 0.0 ? h : 0.0;
 }
 
 // Random subsample (any width): counters in shared memory for up to 2^13 codes, else global.
@@ -301,7 +391,8 @@ __global__ void __launch_bounds__(kHistThreads) hist_sampled_kernel(const void* 
     z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
     z ^= z >> 31;
     if ((z >> 11) >= thr) continue;
-    const uint32_t v = bits <= 8 ? static_cast<const uint8_t*>(samples)[s] : static_cast<const uint16_t*>(samples)[s];
+    const uint32_t v = bits <= 8 ? static_cast<const uint8_t*>(samples)[s]
+                                 : load_u16(samples, s, reinterpret_cast<uintptr_t>(samples) & 1);
     const uint32_t c = v < K ? v : K;
     if (smem) atomicAdd(&shs[c], 1u);
     else atomicAdd(&hist[c], 1ull);
@@ -320,18 +411,31 @@ cudaError_t launch_histogram(const void* samples, uint64_t count, int bits, unsi
   const uint32_t K = 1u << bits;
   cudaError_t e = cudaMemsetAsync(hist, 0, (K + 1) * sizeof(unsigned long long), s);
   if (e != cudaSuccess) return e;
-  const uint64_t per_cta = bits <= 8 ? 16ull * kHistThreads * 8 : (uint64_t)kHistThreads * 16;
-  uint64_t want = ceil_div(count, per_cta);
-  uint64_t cap = (uint64_t)num_sms * (bits <= 8 ? 6 : 4);
-  int grid = (int)(want < cap ? (want ? want : 1) : cap);
   if (bits <= 8) {
+    const uint64_t want = ceil_div(count, 16ull * kHistThreads * 8);
+    const uint64_t cap = (uint64_t)num_sms * 6;
+    const int grid = (int)(want < cap ? (want ? want : 1) : cap);
     hist_u8_kernel<<<grid, kHistThreads, 0, s>>>(static_cast<const uint8_t*>(samples), count, bits, hist);
-  } else if (bits <= 13) {
-    hist_u16_smem_kernel<<<grid, kHistThreads, (K + 1) * sizeof(uint32_t), s>>>(
-        static_cast<const uint16_t*>(samples), count, bits, hist);
-  } else {
-    hist_u16_global_kernel<<<grid, kHistThreads, 0, s>>>(static_cast<const uint16_t*>(samples), count, bits, hist);
+    ++*kernels;
+    return cudaGetLastError();
   }
+  if (bits <= 13) {
+    const uint64_t want = ceil_div(count, (uint64_t)kHistThreads * 16);
+    const uint64_t cap = (uint64_t)num_sms * 4;
+    const int grid = (int)(want < cap ? (want ? want : 1) : cap);
+    hist_u16_smem_kernel<<<grid, kHistThreads, (K + 1) * sizeof(uint32_t), s>>>(samples, count, bits, hist);
+    ++*kernels;
+    return cudaGetLastError();
+  }
+  // 14..16 bits: one CTA per SM, clusters of two (an even grid)
+  const size_t smem = (K / 2) * sizeof(uint32_t);
+  if ((e = cudaFuncSetAttribute(hist_u16_cluster_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
+      cudaSuccess)
+    return e;
+  const uint64_t want = ceil_div(count, (uint64_t)kH16Threads * 16);
+  uint64_t grid = (uint64_t)(num_sms > 1 ? num_sms : 2) & ~1ull;
+  if (want < grid) grid = want < 2 ? 2 : (want + 1) & ~1ull;
+  hist_u16_cluster_kernel<<<(unsigned)grid, kH16Threads, smem, s>>>(samples, count, bits, hist);
   ++*kernels;
   return cudaGetLastError();
 }
@@ -352,7 +456,13 @@ cudaError_t launch_histogram_sampled(const void* samples, uint64_t count, int bi
 
 cudaError_t launch_hmin_finalize(const unsigned long long* hist, int bits, double eps, DevHminResult* out,
                                  cudaStream_t s, uint32_t* kernels, double var_sub, double h_ref) {
-  hmin_finalize_kernel<<<1, kFinThreads, 0, s>>>(hist, bits, eps, out, var_sub, h_ref);
+  hmin_moments_kernel<<<1, kFinThreads, 0, s>>>(hist, bits, out, var_sub);
+  ++*kernels;
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  const uint32_t K = 1u << bits;
+  hmin_cells_kernel<<<(unsigned)ceil_div(K, (uint64_t)kCellThreads), kCellThreads, 0, s>>>(hist, bits, eps, out,
+                                                                                            var_sub, h_ref);
   ++*kernels;
   return cudaGetLastError();
 }

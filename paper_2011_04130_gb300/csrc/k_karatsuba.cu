@@ -21,7 +21,7 @@
 // Work: 3^levels mq kq against m n_t multiply-adds per block (9/16 at two levels), for three
 // cheap memory-bound passes: the derived seeds (3^levels short bit strings), the derived raw
 // operands (3^levels x K/2^levels bits per block) and the combination (2^levels words read per
-// output word).
+// output word), which writes the bit-contiguous output stream directly when its layout allows.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -178,6 +178,88 @@ __global__ void kara_combine_kernel(const uint32_t* __restrict__ qpar, uint64_t 
   }
 }
 
+// The same combination for one block per CTA, written straight into the bit-contiguous stream:
+// the block's words are assembled in shared memory, then its bit range [b m, (b+1) m) is stored
+// in place -- words inside the range with plain stores, the (at most two) words it shares with its
+// neighbours with an AND that clears its own bits and an OR that sets them (the neighbours' bits
+// are disjoint, so the order of the four operations does not matter). The stream's last block also
+// clears the pad bits of the last word. Needs a 4-byte aligned stream whose byte length is a
+// multiple of 4 and m >= 64 (a word then holds bits of at most two blocks).
+template <int L>
+__global__ void kara_combine_pack_kernel(const uint32_t* __restrict__ qpar, uint64_t mwq, uint32_t log2h, uint64_t nb,
+                                         uint32_t rblocks, uint32_t* __restrict__ stream, uint64_t block0,
+                                         uint64_t total_blocks, uint32_t mw, uint32_t m, int modified, uint32_t id_off,
+                                         const uint32_t* __restrict__ raw, uint64_t raw_stride) {
+  constexpr int G = L == 1 ? 3 : L == 2 ? 9 : 27;
+  extern __shared__ uint32_t sw[];  // the block's mw output words
+  const uint32_t hw = 1u << (log2h - 5);
+  const uint64_t b = blockIdx.x;
+  const uint32_t* rr = raw + b * raw_stride;
+  for (uint32_t item = threadIdx.x; item < rblocks * hw; item += blockDim.x) {
+    const uint32_t R = item / hw, lw = item - R * hw;
+    const uint64_t row_word = (uint64_t)R * hw + lw;
+    uint32_t qz[G];
+#pragma unroll
+    for (int z = 0; z < G; ++z) qz[z] = __ldg(qpar + ((uint64_t)z * nb + b) * mwq + row_word);
+#pragma unroll
+    for (int q = 0; q < (1 << L); ++q) {
+      const uint32_t ow = (((R << L) + (uint32_t)q) << (log2h - 5)) + lw;
+      if (ow >= mw) break;
+      uint32_t acc = 0;
+#pragma unroll
+      for (int s = 0; s < (1 << L); ++s) {
+        int z = 0, p3 = 1;
+#pragma unroll
+        for (int l = 0; l < L; ++l) {
+          if ((s >> l) & 1) z += (1 + ((q >> l) & 1)) * p3;
+          p3 *= 3;
+        }
+        acc ^= qz[z];
+      }
+      const uint32_t v0 = 32u * ow;
+      const uint32_t rem = m - v0;
+      const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+      acc &= omask;
+      if (modified) {
+        const uint64_t bit = (uint64_t)id_off + v0;
+        const uint64_t rq = bit >> 5;
+        const uint32_t rs = (uint32_t)(bit & 31);
+        const uint32_t rlo = __ldg(rr + rq);
+        const uint32_t rhi = (rs && rq + 1 < raw_stride) ? __ldg(rr + rq + 1) : 0u;
+        acc ^= __funnelshift_r(rlo, rhi, rs) & omask;
+      }
+      sw[ow] = acc;
+    }
+  }
+  __syncthreads();
+  const uint64_t gb = block0 + b;
+  const uint64_t bm = gb * m;
+  const uint64_t d0 = bm >> 5, d1 = (bm + m - 1) >> 5;
+  const bool last = gb + 1 == total_blocks;
+  for (uint64_t D = d0 + threadIdx.x; D <= d1; D += blockDim.x) {
+    const int64_t off = (int64_t)(32 * D) - (int64_t)bm;  // block bit of the word's bit 0
+    uint32_t v, mask;
+    if (off >= 0) {
+      const uint32_t q = (uint32_t)(off >> 5), sh = (uint32_t)(off & 31);
+      const uint32_t lo = sw[q], hi = (sh && q + 1 < mw) ? sw[q + 1] : 0u;
+      v = __funnelshift_r(lo, hi, sh);
+      const uint64_t rem = m - (uint64_t)off;
+      mask = (rem >= 32 || last) ? 0xffffffffu : ((1u << rem) - 1u);  // the last block owns the pad bits
+    } else {
+      const uint32_t k0 = (uint32_t)(-off);  // 1..31: the word starts inside the previous block
+      v = sw[0] << k0;
+      mask = 0xffffffffu << k0;
+    }
+    v &= mask;
+    if (mask == 0xffffffffu) {
+      stream[D] = v;
+    } else {
+      atomicAnd(stream + D, ~mask);
+      atomicOr(stream + D, v);
+    }
+  }
+}
+
 unsigned grid_for(uint64_t items, int num_sms) {
   const uint64_t want = ceil_div(items, kThreads);
   const uint64_t cap = (uint64_t)(num_sms > 0 ? num_sms : 1) * 16;
@@ -204,6 +286,8 @@ KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_s
       const uint64_t mq = rblocks * h, kq = ceil_div(n_t, span) * h;
       const uint64_t per_block = (uint64_t)G * (mq + kq) / 8;
       uint64_t chunk = budget / per_block;
+      // whole tile widths of the product kernel; never fewer than one (224 blocks), even when the
+      // budget is smaller than that needs
       chunk = chunk >= 224 ? chunk / 224 * 224 : 224;
       if (chunk > num_blocks) chunk = num_blocks;
       while ((uint64_t)G * chunk >= (1ull << 31)) chunk /= 2;
@@ -238,7 +322,8 @@ KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_s
 }
 
 cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWorkspace& ws, int* err, int fault,
-                                  int num_sms, cudaStream_t s, uint32_t* kernels, const TimingHook& hook) {
+                                  int num_sms, cudaStream_t s, uint32_t* kernels, const TimingHook& hook,
+                                  uint8_t* packed_out) {
   if (p.levels < 1 || p.levels > 3) return cudaErrorInvalidValue;
   const uint32_t G = p.groups;
   const uint32_t hw = (uint32_t)(p.h / 32);
@@ -294,6 +379,25 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
     hook.on_end(s);
     if (e != cudaSuccess) return e;
     const uint32_t rblocks = (uint32_t)ceil_div(d.m, p.span);
+    if (packed_out) {  // combine and pack in one pass, one CTA per block
+      uint32_t* stream = reinterpret_cast<uint32_t*>(packed_out);
+      const size_t smem = (size_t)d.mw * sizeof(uint32_t);
+      if (p.levels == 1)
+        kara_combine_pack_kernel<1><<<(unsigned)nb, kThreads, smem, s>>>(k.qpar, mwq, log2h, nb, rblocks, stream, b0,
+                                                                        d.num_blocks, d.mw, d.m, d.modified, d.id_off,
+                                                                        dc.raw, d.raw_stride);
+      else if (p.levels == 2)
+        kara_combine_pack_kernel<2><<<(unsigned)nb, kThreads, smem, s>>>(k.qpar, mwq, log2h, nb, rblocks, stream, b0,
+                                                                        d.num_blocks, d.mw, d.m, d.modified, d.id_off,
+                                                                        dc.raw, d.raw_stride);
+      else
+        kara_combine_pack_kernel<3><<<(unsigned)nb, kThreads, smem, s>>>(k.qpar, mwq, log2h, nb, rblocks, stream, b0,
+                                                                        d.num_blocks, d.mw, d.m, d.modified, d.id_off,
+                                                                        dc.raw, d.raw_stride);
+      ++*kernels;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      continue;
+    }
     const unsigned gc = grid_for(nb * rblocks * hw, num_sms);
     if (p.levels == 1)
       kara_combine_kernel<1><<<gc, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, rblocks, dc.out, d.out_stride, d.mw, d.m,

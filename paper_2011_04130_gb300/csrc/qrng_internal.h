@@ -57,6 +57,15 @@ struct DevHminResult {
   unsigned long long out_of_range;
   int status;
   double h_subtracted;  // classical-noise route: model entropy of this stream minus h_ref
+  // handed from the moments kernel to the cells kernels
+  unsigned long long n;
+  double mu, sigma, sigma_q;
+  int point, bad_sub;
+  // accumulated by the cells kernels: bits of the largest cells (non-negative doubles), the
+  // distance sum in units of 2^-62, the cell of the argmax code, the count of finished CTAs
+  unsigned long long pmax_bits, pmax_full_bits, dsum_fixed;
+  double p_argmax;
+  unsigned int done;
 };
 
 // ---- histogram + finaliser (k_hist.cu) ----
@@ -273,9 +282,13 @@ struct PairKara {
 cudaError_t launch_gemm_pair_kara(const DirectArgs& a, const PairKara& k, int* err, int fault, int num_sms,
                                   cudaStream_t s, uint32_t* kernels);
 // The whole Karatsuba extraction of a.num_blocks blocks (chunked by plan.chunk_blocks); `hook` is
-// called around every launch of the product kernel (one per pass).
+// called around every launch of the product kernel (one per pass). With packed_out the output goes
+// straight into that bit-contiguous stream (block b at bit b m; 4-byte aligned, a whole number of
+// 4-byte words long, m >= 64, m <= kKaraPackMaxBits) instead of the word-aligned a.out.
+constexpr uint64_t kKaraPackMaxBits = 1ull << 18;  // 32 KB of output words per CTA
 cudaError_t launch_gemm_karatsuba(const DirectArgs& a, const KaraPlan& plan, KaraWorkspace& ws, int* err, int fault,
-                                  int num_sms, cudaStream_t s, uint32_t* kernels, const TimingHook& hook = TimingHook());
+                                  int num_sms, cudaStream_t s, uint32_t* kernels, const TimingHook& hook = TimingHook(),
+                                  uint8_t* packed_out = nullptr);
 
 }  // namespace qrng
 
@@ -304,7 +317,13 @@ struct qrng_ctx {
     void* meta_host = nullptr;  // pinned copy of the request table the graph uploads
     uint32_t kernels = 0;       // kernels one replay runs
     uint64_t routes[4] = {0, 0, 0, 0};  // requests per route (kRoute*)
+    double direct_bitmacs = 0, transform_bytes = 0;
+    // recorded by the graph: transform groups [0, 1), persistent direct kernel [2, 3)
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    bool has_transform = false, has_direct = false;
   };
+  uint64_t timed_graph_key = 0, timed_graph_generation = 0;  // the last replay made while timing
+  bool timed_graph_pending = false;
   qrng::FftWorkspace batch_fft;  // transform workspace of batch graphs only (addresses stay put)
   // per-class routes of QRNG_ALGO_AUTO batches, keyed by transform length: route and FP32 segment
   struct BatchTune {

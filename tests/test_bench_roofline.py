@@ -70,3 +70,17 @@ def test_transform_routes_report_hbm_and_pipe_fractions():
     assert abs(r["hbm"]["frac"] - r["hbm"]["achieved"] / pk["hbm_gbs"]) < 1e-12
     r = bench.roofline_for("ntt", B, m, n, ms)
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+
+
+def test_fft32_roofline_counts_transforms_and_products():
+    import bench
+
+    caps = {"sms": 152, "sm_max_mhz": 2070.0}
+    n_t, m, B, ms, S, T = 1 << 16, 36473, 64, 2.0, 4096, 8
+    r = bench.roofline_for("fft32_seg", B, m, n_t, ms, {"segment": S, "terms": T}, caps)
+    NS, NQ = 16, 9
+    per_block = (NS + NQ * 2) * 5.0 * S * 12 + NQ * NS * S * 8.0
+    flops = B * per_block + (NQ + NS - 1) * 5.0 * S * 12
+    assert r["bound"] == "fp32" and r["segment"] == S and r["terms"] == T
+    assert abs(r["achieved"] - flops / 2e-3 / 1e12) < 1e-9 * r["achieved"]
+    assert abs(r["peak"] - 2 * 128 * 152 * 2070e6 / 1e12) < 1e-9

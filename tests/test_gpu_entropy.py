@@ -52,6 +52,26 @@ def test_unaligned_and_ragged(qlib, gpu, oracle_mod, offset, count):
     _compare(_run(qlib, gpu, s, 8, 1e-3, offset), oracle_mod.minentropy(s, 8, 1e-3))
 
 
+@pytest.mark.parametrize("bits", [10, 13, 14, 15, 16])
+@pytest.mark.parametrize("offset", [1, 2, 6, 14])
+@pytest.mark.parametrize("count", [1, 7, 9, 100_003])
+def test_wide_samples_unaligned_and_ragged(qlib, gpu, oracle_mod, bits, offset, count):
+    """uint16 samples at any byte address (odd ones included) and counts that leave a ragged head
+    and tail around the 16-byte vectors."""
+    s = W.adc_samples(count, 7 * bits + count, mu=(1 << bits) / 3, sigma=(1 << bits) / 9, bits=bits)
+    _compare(_run(qlib, gpu, s, bits, 1e-6, offset), oracle_mod.minentropy(s, bits, 1e-6))
+
+
+@pytest.mark.parametrize("bits", [8, 16])
+def test_one_code_holds_every_sample(qlib, gpu, oracle_mod, bits):
+    """Every sample on one code: the per-lane 16-bit copies (8-bit) and the cluster counters (16-bit)
+    must carry counts far above 2^16 into the totals."""
+    s = np.full(3_000_001, 200 if bits == 8 else 40000, dtype=np.uint8 if bits == 8 else np.uint16)
+    got = _run(qlib, gpu, s, bits, 1e-6)
+    _compare(got, oracle_mod.minentropy(s, bits, 1e-6))
+    assert got["max_count"] == s.size
+
+
 @pytest.mark.parametrize("bits", [1, 2, 5, 7, 9, 12, 13, 14, 16])
 def test_bit_widths(qlib, gpu, oracle_mod, bits):
     mu = (1 << bits) / 2.0

@@ -126,3 +126,36 @@ def test_plan_query(qlib, gpu, kara):
     with pytest.raises(qlib.QrngError) as e:
         qlib.qrng_karatsuba_plan(gpu, 64, 65, STD, 1)
     assert e.value.status == qlib.QRNG_EINVAL
+
+
+@pytest.mark.parametrize("levels,h", [(0, 0), (1, 256), (2, 512), (3, 256)])
+@pytest.mark.parametrize("n,m,form,B", [
+    (4096, 100, STD, 32), (5000, 3100, STD, 8), (1 << 16, 36473, STD, 32), (4500, 1700, MOD, 16),
+    (3000, 99, STD, 31),  # 3069 output bits: the last byte has three pad bits
+])
+def test_combination_writes_the_packed_stream(qlib, gpu, oracle_mod, kara, levels, h, n, m, form, B):
+    """Shapes whose packed output is 4-byte aligned and a whole number of words long with m not a
+    multiple of 32: the combination pass writes the bit stream in place, blocks meeting inside
+    words (AND/OR on the shared words), the pad bits of the last byte zeroed, nothing written past
+    the stream."""
+    kara(levels, h)
+    raw, seed = _case(n, m, form, B, 3 * m + B + levels)
+    assert ((B * m + 7) // 8) % 4 == 0
+    got = extract(qlib, gpu, raw, n, m, seed, form, KARA, B)
+    if n * m <= 1 << 24:
+        assert np.array_equal(got, oracle_mod.toeplitz_blocks(raw, n, m, seed, form, B))
+    else:  # the laser shape: every block by Freivalds, block edges and pad bits bit by bit
+        assert not oracle_mod.freivalds(raw, n, m, seed, form, B, got).any()
+        spot_check(oracle_mod, raw, n, m, seed, form, got, blocks=range(B), per_block=16)
+        tail = (B * m) % 8
+        if tail:
+            assert got[-1] >> tail == 0
+
+
+def test_packed_stream_over_passes(qlib, gpu, oracle_mod, kara):
+    """The in-place combination over several passes (blocks numbered across passes)."""
+    n, m, B = 4096, 1000, 704  # 88,000 bytes; a pass holds 224 blocks
+    kara(2, 256, 1)
+    raw, seed = _case(n, m, STD, B, 19)
+    want = oracle_mod.toeplitz_blocks(raw, n, m, seed, STD, B)
+    assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, STD, KARA, B), want)

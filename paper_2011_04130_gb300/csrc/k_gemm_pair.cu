@@ -24,8 +24,9 @@
 //   warp 7      tensor memory allocation (both CTAs); in the leader CTA (rank 0) one lane issues the
 //               cta_group::2 MMAs and multicasts their completion to both CTAs' barriers;
 //   warps 8-15  epilogue: two warps per TMEM lane quarter, one per accumulator; each CTA reads its
-//               128 rows of both accumulators (its outputs) from its own tensor memory in 16-column
-//               loads double-buffered against the parity __ballot_sync of the previous load, and
+//               128 rows of both accumulators (its outputs) from its own tensor memory in 32-column
+//               loads double-buffered against the parity words of the previous load (one add and
+//               one funnel shift per count, then a 32 x 32 bit transpose across the warp), and
 //               hands the accumulators back as soon as its last load has landed; identity XOR for
 //               the modified form.
 // Both epilogues signal the leader's accumulator barrier. Every wait is bounded (about one second of
@@ -415,8 +416,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {
     // ------------------------------------------------------------------ epilogue
     // warp EPI_WARP0 + 4 hs + q drains accumulator hs (D0 or D1) in TMEM lanes 32 q .. 32 q + 31:
-    // 32-column loads double-buffered against the parity ballots of the previous load (lane c takes
-    // column c's ballot: one output word per lane and load), and the accumulator handed back to the
+    // 32-column loads double-buffered against the parity words of the previous load (lane c ends
+    // with column c's word: one output word per lane and load), and the accumulator handed back to the
     // MMA issuer as soon as its last load has landed; the output words wait in shared memory until
     // then, so that the release does not wait for global stores
     const uint32_t q = warp & 3u;  // TMEM lane quarter this warp may access
@@ -424,6 +425,18 @@ __global__ void __launch_bounds__(THREADS, 1)
     constexpr uint32_t NW = PN / 32;  // 32-column loads (output words) per accumulator
     const uint32_t accum_empty_leader = mapa_shared(smem_u32(&accum_empty_bar), 0);
     uint32_t* words = &epi_words[warp - EPI_WARP0][0][0];  // [word][lane]
+    // transpose stage l (j = 2^l): a lane keeps the columns whose bit l equals its own lane bit l
+    // and takes the others from lane ^ j, whose word is rotated by j towards them; the bits a
+    // rotation wraps around fall in the kept columns
+    uint32_t xkeep[5], xrot[5];
+#pragma unroll
+    for (int l = 0; l < 5; ++l) {
+      const uint32_t j = 1u << l;
+      const uint32_t m = l == 4 ? 0x0000FFFFu : l == 3 ? 0x00FF00FFu : l == 2 ? 0x0F0F0F0Fu
+                         : l == 1 ? 0x33333333u : 0x55555555u;  // columns with bit l clear
+      xkeep[l] = (lane & j) ? ~m : m;
+      xrot[l] = (lane & j) ? 32u - j : j;
+    }
     uint32_t acc_phase = 0;
     for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
       const TileCoord tc = tile_coord<kKara>(a, tile);
@@ -436,18 +449,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t taddr = tmem_base + ((32u * q) << 16) + hs * D1_COL;
       // lane r packs the parities of its row for the 32 columns (bit c = column c); a 32 x 32 bit
       // transpose across the warp then leaves column c's 32 rows in lane c: stage j exchanges bit j
-      // of the row and column indices (one shuffle and a few logic operations per stage)
-      auto ballots = [&](const uint32_t(&v)[32], uint32_t g) {
-        uint32_t x = 0;
-#pragma unroll
-        for (int c = 0; c < 32; ++c) x |= count_parity(v[c], 1.0f) << c;
+      // of the row and column indices (one shuffle, one rotate and one select per stage)
+      auto parity_words = [&](const uint32_t(&v)[32], uint32_t g) {
+        uint32_t x = pack_parities32(v);
 #pragma unroll
         for (int l = 4; l >= 0; --l) {
-          const uint32_t j = 1u << l;
-          const uint32_t m = l == 4 ? 0x0000FFFFu : l == 3 ? 0x00FF00FFu : l == 2 ? 0x0F0F0F0Fu
-                             : l == 1 ? 0x33333333u : 0x55555555u;  // columns with bit l clear
-          const uint32_t t = __shfl_xor_sync(0xffffffffu, x, j);
-          x = (lane & j) ? ((x & ~m) | ((t >> j) & m)) : ((x & m) | ((t << j) & ~m));
+          const uint32_t t = __shfl_xor_sync(0xffffffffu, x, 1u << l);
+          const uint32_t r = __funnelshift_l(t, t, xrot[l]);
+          x = (x & xkeep[l]) | (r & ~xkeep[l]);
         }
         words[g * 32 + lane] = x;
       };
@@ -465,14 +474,14 @@ __global__ void __launch_bounds__(THREADS, 1)
           tmem_load32_async(taddr + 32u * (g + 1), vb);
         else
           release();
-        ballots(va, g);
+        parity_words(va, g);
         if (g + 1 < NW) {
           tmem_wait_ld(vb);
           if (g + 2 < NW)
             tmem_load32_async(taddr + 32u * (g + 2), va);
           else
             release();
-          ballots(vb, g + 1);
+          parity_words(vb, g + 1);
           if (g + 2 < NW) tmem_wait_ld(va);
         }
       }

@@ -202,6 +202,21 @@ __device__ __forceinline__ uint32_t count_parity(uint32_t acc_bits, float scale)
   return __float_as_uint(__fmaf_rn(__uint_as_float(acc_bits), scale, 12582912.0f)) & 1u;
 }
 
+// The parities of 32 unscaled counts (FP32 accumulators, each an integer below 2^22) as one word,
+// bit c = parity of v[c]. After the 1.5 * 2^23 addition the parity is bit 0 of the sum's encoding;
+// a funnel shift by one moves it into the top of a word being filled, so each count costs one add
+// and one shift. Two chains of 16 (columns 0-15 and 16-31 end in the upper halves) are joined by
+// one byte permutation.
+__device__ __forceinline__ uint32_t pack_parities32(const uint32_t (&v)[32]) {
+  uint32_t lo = 0, hi = 0;
+#pragma unroll
+  for (int c = 0; c < 16; ++c) {
+    lo = __funnelshift_r(lo, __float_as_uint(__uint_as_float(v[c]) + 12582912.0f), 1);
+    hi = __funnelshift_r(hi, __float_as_uint(__uint_as_float(v[c + 16]) + 12582912.0f), 1);
+  }
+  return __byte_perm(lo, hi, 0x7632);
+}
+
 // ---- clusters of two CTAs (the SM-pair kernel) ----
 
 __device__ __forceinline__ uint32_t cluster_ctarank() {

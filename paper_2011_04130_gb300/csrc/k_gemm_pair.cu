@@ -25,10 +25,10 @@
 //               cta_group::2 MMAs and multicasts their completion to both CTAs' barriers;
 //   warps 8-15  epilogue: two warps per TMEM lane quarter, one per accumulator; each CTA reads its
 //               128 rows of both accumulators (its outputs) from its own tensor memory in 32-column
-//               loads double-buffered against the parity words of the previous load (one add and
-//               one funnel shift per count, then a 32 x 32 bit transpose across the warp), and
-//               hands the accumulators back as soon as its last load has landed; identity XOR for
-//               the modified form.
+//               loads double-buffered against the parity packing of the previous load (one add and
+//               one funnel shift per count), hands the accumulators back as soon as its last load
+//               has landed, and only then transposes the packed words (32 x 32 bits across the
+//               warp) and stores them; identity XOR for the modified form.
 // Both epilogues signal the leader's accumulator barrier. Every wait is bounded (about one second of
 // clock): on timeout a CTA records an error code and stops; the leader still drains its MMAs, and
 // both CTAs meet at a cluster barrier before tensor memory is released.
@@ -181,7 +181,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   __shared__ __align__(8) uint64_t accum_empty_bar;        // leader: one arrival per epilogue warp of both CTAs
   __shared__ __align__(8) uint64_t drain_bar;
   __shared__ uint32_t tmem_slot;
-  __shared__ uint32_t epi_words[EPI_WARPS][kPN / 32][32];  // an epilogue warp's output words of a tile
+  __shared__ uint32_t epi_words[EPI_WARPS][kPN / 32][32];  // an epilogue warp's packed parity rows of a tile
   __shared__ volatile int abort_flag;
 
   const uint32_t warp = threadIdx.x >> 5;
@@ -416,15 +416,15 @@ __global__ void __launch_bounds__(THREADS, 1)
   } else {
     // ------------------------------------------------------------------ epilogue
     // warp EPI_WARP0 + 4 hs + q drains accumulator hs (D0 or D1) in TMEM lanes 32 q .. 32 q + 31:
-    // 32-column loads double-buffered against the parity words of the previous load (lane c ends
-    // with column c's word: one output word per lane and load), and the accumulator handed back to the
-    // MMA issuer as soon as its last load has landed; the output words wait in shared memory until
-    // then, so that the release does not wait for global stores
+    // 32-column loads double-buffered against the parity packing of the previous load, and the
+    // accumulator handed back to the MMA issuer as soon as its last load has landed; the
+    // transposes (lane c ends with column c's word: one output word per lane and load) and the
+    // global stores follow, overlapping the next tile's MMAs
     const uint32_t q = warp & 3u;  // TMEM lane quarter this warp may access
     const uint32_t hs = (warp - EPI_WARP0) >> 2;
     constexpr uint32_t NW = PN / 32;  // 32-column loads (output words) per accumulator
     const uint32_t accum_empty_leader = mapa_shared(smem_u32(&accum_empty_bar), 0);
-    uint32_t* words = &epi_words[warp - EPI_WARP0][0][0];  // [word][lane]
+    uint32_t* words = &epi_words[warp - EPI_WARP0][0][0];  // [word][lane]: packed rows until the transpose
     // transpose stage l (j = 2^l): a lane keeps the columns whose bit l equals its own lane bit l
     // and takes the others from lane ^ j, whose word is rotated by j towards them; the bits a
     // rotation wraps around fall in the kept columns
@@ -447,19 +447,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t rem = (ow < a.mw) ? a.m - 32 * ow : 0u;
       const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
       const uint32_t taddr = tmem_base + ((32u * q) << 16) + hs * D1_COL;
-      // lane r packs the parities of its row for the 32 columns (bit c = column c); a 32 x 32 bit
-      // transpose across the warp then leaves column c's 32 rows in lane c: stage j exchanges bit j
-      // of the row and column indices (one shuffle, one rotate and one select per stage)
-      auto parity_words = [&](const uint32_t(&v)[32], uint32_t g) {
-        uint32_t x = pack_parities32(v);
-#pragma unroll
-        for (int l = 4; l >= 0; --l) {
-          const uint32_t t = __shfl_xor_sync(0xffffffffu, x, 1u << l);
-          const uint32_t r = __funnelshift_l(t, t, xrot[l]);
-          x = (x & xkeep[l]) | (r & ~xkeep[l]);
-        }
-        words[g * 32 + lane] = x;
-      };
+      // Lane r packs the parities of its row for each 32-column load (bit c = column c) as soon as
+      // the load lands, the next load in flight meanwhile; the accumulator goes back to the MMA
+      // issuer when the last load has landed. Only then does a 32 x 32 bit transpose across the
+      // warp leave column c's 32 rows in lane c (stage j exchanges bit j of the row and column
+      // indices: one shuffle, one rotate and one select), for all NW words at once, so that the
+      // shuffles of different words overlap and none of it delays the next tile's MMAs.
       auto release = [&]() {  // every TMEM load of this warp has completed
         tc_fence_before();
         __syncwarp();
@@ -474,21 +467,32 @@ __global__ void __launch_bounds__(THREADS, 1)
           tmem_load32_async(taddr + 32u * (g + 1), vb);
         else
           release();
-        parity_words(va, g);
+        words[g * 32 + lane] = pack_parities32(va);
         if (g + 1 < NW) {
           tmem_wait_ld(vb);
           if (g + 2 < NW)
             tmem_load32_async(taddr + 32u * (g + 2), va);
           else
             release();
-          parity_words(vb, g + 1);
+          words[(g + 1) * 32 + lane] = pack_parities32(vb);
           if (g + 2 < NW) tmem_wait_ld(va);
         }
       }
-      __syncwarp();
-#pragma unroll 1
+      uint32_t xw[NW];
+#pragma unroll
+      for (uint32_t g = 0; g < NW; ++g) xw[g] = words[g * 32 + lane];
+#pragma unroll
+      for (int l = 4; l >= 0; --l) {
+#pragma unroll
+        for (uint32_t g = 0; g < NW; ++g) {
+          const uint32_t t = __shfl_xor_sync(0xffffffffu, xw[g], 1u << l);
+          const uint32_t r = __funnelshift_l(t, t, xrot[l]);
+          xw[g] = (xw[g] & xkeep[l]) | (r & ~xkeep[l]);
+        }
+      }
+#pragma unroll
       for (uint32_t g = 0; g < NW; ++g) {  // lane c: column 32 g + c of the tile
-        const uint32_t word = words[g * 32 + lane];
+        const uint32_t word = xw[g];
         const uint64_t b = (uint64_t)nt * PN + 32u * g + lane;
         if (kKara) {  // every row of a sub-product is kept: the combining pass selects and masks
           if (b < a.num_blocks) a.qpar[((uint64_t)tc.z * a.num_blocks + b) * a.mwq + ow] = word;

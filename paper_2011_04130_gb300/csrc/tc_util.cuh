@@ -205,16 +205,19 @@ __device__ __forceinline__ uint32_t count_parity(uint32_t acc_bits, float scale)
 // The parities of 32 unscaled counts (FP32 accumulators, each an integer below 2^22) as one word,
 // bit c = parity of v[c]. After the 1.5 * 2^23 addition the parity is bit 0 of the sum's encoding;
 // a funnel shift by one moves it into the top of a word being filled, so each count costs one add
-// and one shift. Two chains of 16 (columns 0-15 and 16-31 end in the upper halves) are joined by
-// one byte permutation.
+// and one shift. Four independent chains of 8 (columns 8k .. 8k+7 end in the top byte of chain k)
+// keep the dependent shifts short; three byte permutations join them.
 __device__ __forceinline__ uint32_t pack_parities32(const uint32_t (&v)[32]) {
-  uint32_t lo = 0, hi = 0;
+  uint32_t c[4] = {0u, 0u, 0u, 0u};
 #pragma unroll
-  for (int c = 0; c < 16; ++c) {
-    lo = __funnelshift_r(lo, __float_as_uint(__uint_as_float(v[c]) + 12582912.0f), 1);
-    hi = __funnelshift_r(hi, __float_as_uint(__uint_as_float(v[c + 16]) + 12582912.0f), 1);
+  for (int i = 0; i < 8; ++i) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k)
+      c[k] = __funnelshift_r(c[k], __float_as_uint(__uint_as_float(v[8 * k + i]) + 12582912.0f), 1);
   }
-  return __byte_perm(lo, hi, 0x7632);
+  const uint32_t lo = __byte_perm(c[0], c[1], 0x0073);  // byte 3 of chain 0, byte 3 of chain 1
+  const uint32_t hi = __byte_perm(c[2], c[3], 0x0073);
+  return __byte_perm(lo, hi, 0x5410);
 }
 
 // ---- clusters of two CTAs (the SM-pair kernel) ----

@@ -453,10 +453,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       // warp leave column c's 32 rows in lane c (stage j exchanges bit j of the row and column
       // indices: one shuffle, one rotate and one select), for all NW words at once, so that the
       // shuffles of different words overlap and none of it delays the next tile's MMAs.
-      auto release = [&]() {  // every TMEM load of this warp has completed
+      auto release = [&]() {  // every TMEM load of this warp has completed (the values are in registers)
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive_cluster(accum_empty_leader);
+        if (lane == 0) mbar_arrive_cluster_relaxed(accum_empty_leader);
       };
       uint32_t va[32], vb[32];
       tmem_load32_async(taddr, va);

@@ -140,7 +140,7 @@ struct PairArgs {
   uint32_t row_shift;    // span - h: seed bits skipped per row block
   uint32_t groups;
   uint64_t seed_stride;  // words per derived seed
-  uint32_t* qpar;        // parities of the sub-products: word (z * num_blocks + b) * mwq + row / 32
+  uint32_t* qpar;        // parities of the sub-products: word (b * groups + z) * mwq + row / 32
   uint32_t mwq;
 };
 
@@ -495,7 +495,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         const uint32_t word = xw[g];
         const uint64_t b = (uint64_t)nt * PN + 32u * g + lane;
         if (kKara) {  // every row of a sub-product is kept: the combining pass selects and masks
-          if (b < a.num_blocks) a.qpar[((uint64_t)tc.z * a.num_blocks + b) * a.mwq + ow] = word;
+          if (b < a.num_blocks) a.qpar[((uint64_t)b * a.groups + tc.z) * a.mwq + ow] = word;
         } else if (ow < a.mw && b < a.num_blocks) {
           uint32_t w = word & omask;
           if (a.modified) {

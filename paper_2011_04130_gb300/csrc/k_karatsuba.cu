@@ -33,6 +33,8 @@ namespace qrng {
 namespace {
 
 constexpr int kThreads = 256;
+constexpr int kPackThreads = 128;  // combine-and-pack CTAs (one block each; most of the work is the staging)
+constexpr uint32_t kPackSmemWords = 12288;  // 48 KB of shared memory per combine-and-pack CTA
 constexpr uint64_t kDefaultWorkspace = 1ull << 30;  // derived operands + sub-product parities per pass
 
 __host__ __device__ inline uint32_t pow3(uint32_t l) {
@@ -144,7 +146,7 @@ __global__ void kara_combine_kernel(const uint32_t* __restrict__ qpar, uint64_t 
     const uint64_t row_word = (uint64_t)R * hw + lw;
     uint32_t qz[G];
 #pragma unroll
-    for (int z = 0; z < G; ++z) qz[z] = __ldg(qpar + ((uint64_t)z * nb + b) * mwq + row_word);
+    for (int z = 0; z < G; ++z) qz[z] = __ldg(qpar + (b * G + (uint64_t)z) * mwq + row_word);
     const uint32_t* rr = raw + b * raw_stride;
 #pragma unroll
     for (int q = 0; q < (1 << L); ++q) {
@@ -178,60 +180,74 @@ __global__ void kara_combine_kernel(const uint32_t* __restrict__ qpar, uint64_t 
   }
 }
 
-// The same combination for one block per CTA, written straight into the bit-contiguous stream:
-// the block's words are assembled in shared memory, then its bit range [b m, (b+1) m) is stored
-// in place -- words inside the range with plain stores, the (at most two) words it shares with its
-// neighbours with an AND that clears its own bits and an OR that sets them (the neighbours' bits
-// are disjoint, so the order of the four operations does not matter). The stream's last block also
-// clears the pad bits of the last word. Needs a 4-byte aligned stream whose byte length is a
-// multiple of 4 and m >= 64 (a word then holds bits of at most two blocks).
+// The same combination for one block per CTA, written straight into the bit-contiguous stream.
+// The block's sub-product parities (G rows of mwq words, contiguous) are staged in shared memory
+// with 16-byte loads, `cw` row words of every sub-product at a time; the block's output words are
+// assembled in shared memory, then its bit range [b m, (b+1) m) is stored in place -- words inside
+// the range with plain stores, the (at most two) words it shares with its neighbours with an AND
+// that clears its own bits and an OR that sets them (the neighbours' bits are disjoint, so the
+// order of the four operations does not matter). The stream's last block also clears the pad bits
+// of the last word. Needs a 4-byte aligned stream whose byte length is a multiple of 4, m >= 64 (a
+// word then holds bits of at most two blocks), and mwq and cw multiples of 4.
 template <int L>
-__global__ void kara_combine_pack_kernel(const uint32_t* __restrict__ qpar, uint64_t mwq, uint32_t log2h, uint64_t nb,
-                                         uint32_t rblocks, uint32_t* __restrict__ stream, uint64_t block0,
-                                         uint64_t total_blocks, uint32_t mw, uint32_t m, int modified, uint32_t id_off,
-                                         const uint32_t* __restrict__ raw, uint64_t raw_stride) {
+__global__ void __launch_bounds__(kPackThreads) kara_combine_pack_kernel(
+    const uint32_t* __restrict__ qpar, uint64_t mwq, uint32_t log2h, uint32_t cw, uint32_t* __restrict__ stream,
+    uint64_t block0, uint64_t total_blocks, uint32_t mw, uint32_t m, int modified, uint32_t id_off,
+    const uint32_t* __restrict__ raw, uint64_t raw_stride) {
   constexpr int G = L == 1 ? 3 : L == 2 ? 9 : 27;
-  extern __shared__ uint32_t sw[];  // the block's mw output words
+  extern __shared__ __align__(16) uint32_t smem_words[];
+  uint32_t* qs = smem_words;           // [G][cw]: the staged parity row words
+  uint32_t* sw = smem_words + G * cw;  // the block's mw output words
   const uint32_t hw = 1u << (log2h - 5);
   const uint64_t b = blockIdx.x;
+  const uint32_t* qb = qpar + b * G * mwq;
   const uint32_t* rr = raw + b * raw_stride;
-  for (uint32_t item = threadIdx.x; item < rblocks * hw; item += blockDim.x) {
-    const uint32_t R = item / hw, lw = item - R * hw;
-    const uint64_t row_word = (uint64_t)R * hw + lw;
-    uint32_t qz[G];
-#pragma unroll
-    for (int z = 0; z < G; ++z) qz[z] = __ldg(qpar + ((uint64_t)z * nb + b) * mwq + row_word);
-#pragma unroll
-    for (int q = 0; q < (1 << L); ++q) {
-      const uint32_t ow = (((R << L) + (uint32_t)q) << (log2h - 5)) + lw;
-      if (ow >= mw) break;
-      uint32_t acc = 0;
-#pragma unroll
-      for (int s = 0; s < (1 << L); ++s) {
-        int z = 0, p3 = 1;
-#pragma unroll
-        for (int l = 0; l < L; ++l) {
-          if ((s >> l) & 1) z += (1 + ((q >> l) & 1)) * p3;
-          p3 *= 3;
-        }
-        acc ^= qz[z];
-      }
-      const uint32_t v0 = 32u * ow;
-      const uint32_t rem = m - v0;
-      const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
-      acc &= omask;
-      if (modified) {
-        const uint64_t bit = (uint64_t)id_off + v0;
-        const uint64_t rq = bit >> 5;
-        const uint32_t rs = (uint32_t)(bit & 31);
-        const uint32_t rlo = __ldg(rr + rq);
-        const uint32_t rhi = (rs && rq + 1 < raw_stride) ? __ldg(rr + rq + 1) : 0u;
-        acc ^= __funnelshift_r(rlo, rhi, rs) & omask;
-      }
-      sw[ow] = acc;
+  for (uint32_t rw0 = 0; rw0 < (uint32_t)mwq; rw0 += cw) {
+    const uint32_t n = (uint32_t)mwq - rw0 < cw ? (uint32_t)mwq - rw0 : cw;  // a multiple of 4
+    const uint32_t nv = n / 4;
+    for (uint32_t i = threadIdx.x; i < G * nv; i += blockDim.x) {
+      const uint32_t z = i / nv, k = i - z * nv;
+      reinterpret_cast<uint4*>(qs + z * cw)[k] = __ldcs(reinterpret_cast<const uint4*>(qb + z * mwq + rw0) + k);
     }
+    __syncthreads();
+    for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
+      const uint32_t row_word = rw0 + t;  // = R * hw + lw
+      const uint32_t R = row_word / hw, lw = row_word - R * hw;
+      uint32_t qz[G];
+#pragma unroll
+      for (int z = 0; z < G; ++z) qz[z] = qs[z * cw + t];
+#pragma unroll
+      for (int q = 0; q < (1 << L); ++q) {
+        const uint32_t ow = (((R << L) + (uint32_t)q) << (log2h - 5)) + lw;
+        if (ow >= mw) break;
+        uint32_t acc = 0;
+#pragma unroll
+        for (int s = 0; s < (1 << L); ++s) {
+          int z = 0, p3 = 1;
+#pragma unroll
+          for (int l = 0; l < L; ++l) {
+            if ((s >> l) & 1) z += (1 + ((q >> l) & 1)) * p3;
+            p3 *= 3;
+          }
+          acc ^= qz[z];
+        }
+        const uint32_t v0 = 32u * ow;
+        const uint32_t rem = m - v0;
+        const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+        acc &= omask;
+        if (modified) {
+          const uint64_t bit = (uint64_t)id_off + v0;
+          const uint64_t rq = bit >> 5;
+          const uint32_t rs = (uint32_t)(bit & 31);
+          const uint32_t rlo = __ldg(rr + rq);
+          const uint32_t rhi = (rs && rq + 1 < raw_stride) ? __ldg(rr + rq + 1) : 0u;
+          acc ^= __funnelshift_r(rlo, rhi, rs) & omask;
+        }
+        sw[ow] = acc;
+      }
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const uint64_t gb = block0 + b;
   const uint64_t bm = gb * m;
   const uint64_t d0 = bm >> 5, d1 = (bm + m - 1) >> 5;
@@ -381,19 +397,19 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
     const uint32_t rblocks = (uint32_t)ceil_div(d.m, p.span);
     if (packed_out) {  // combine and pack in one pass, one CTA per block
       uint32_t* stream = reinterpret_cast<uint32_t*>(packed_out);
-      const size_t smem = (size_t)d.mw * sizeof(uint32_t);
+      // staged row words per sub-product: as many as fit beside the output words (multiples of 4)
+      const uint32_t room = (kPackSmemWords - (uint32_t)d.mw) / (uint32_t)G;
+      const uint32_t cw = (uint32_t)(mwq < (uint64_t)room ? mwq : (uint64_t)room) & ~3u;
+      const size_t smem = ((size_t)G * cw + d.mw) * sizeof(uint32_t);
       if (p.levels == 1)
-        kara_combine_pack_kernel<1><<<(unsigned)nb, kThreads, smem, s>>>(k.qpar, mwq, log2h, nb, rblocks, stream, b0,
-                                                                        d.num_blocks, d.mw, d.m, d.modified, d.id_off,
-                                                                        dc.raw, d.raw_stride);
+        kara_combine_pack_kernel<1><<<(unsigned)nb, kPackThreads, smem, s>>>(
+            k.qpar, mwq, log2h, cw, stream, b0, d.num_blocks, d.mw, d.m, d.modified, d.id_off, dc.raw, d.raw_stride);
       else if (p.levels == 2)
-        kara_combine_pack_kernel<2><<<(unsigned)nb, kThreads, smem, s>>>(k.qpar, mwq, log2h, nb, rblocks, stream, b0,
-                                                                        d.num_blocks, d.mw, d.m, d.modified, d.id_off,
-                                                                        dc.raw, d.raw_stride);
+        kara_combine_pack_kernel<2><<<(unsigned)nb, kPackThreads, smem, s>>>(
+            k.qpar, mwq, log2h, cw, stream, b0, d.num_blocks, d.mw, d.m, d.modified, d.id_off, dc.raw, d.raw_stride);
       else
-        kara_combine_pack_kernel<3><<<(unsigned)nb, kThreads, smem, s>>>(k.qpar, mwq, log2h, nb, rblocks, stream, b0,
-                                                                        d.num_blocks, d.mw, d.m, d.modified, d.id_off,
-                                                                        dc.raw, d.raw_stride);
+        kara_combine_pack_kernel<3><<<(unsigned)nb, kPackThreads, smem, s>>>(
+            k.qpar, mwq, log2h, cw, stream, b0, d.num_blocks, d.mw, d.m, d.modified, d.id_off, dc.raw, d.raw_stride);
       ++*kernels;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       continue;

@@ -268,7 +268,8 @@ struct KaraWorkspace {
 };
 // The pair kernel on the sub-products: derived seeds (seed_stride words each, front padding
 // seed_front), derived raw operands xk (row z * num_blocks + b, kq / 32 words), sub-product
-// parities into qpar (row z * num_blocks + b, mq / 32 words).
+// parities into qpar (row b * groups + z, mq / 32 words: a block's parities are contiguous, so
+// the combining pass reads each block's share in one stream).
 struct PairKara {
   const uint32_t* seeds;
   uint64_t seed_stride;

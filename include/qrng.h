@@ -347,7 +347,7 @@ QRNG_API int qrng_inject_fault(qrng_ctx* ctx, int fault);
 QRNG_API int qrng_set_autotune(qrng_ctx* ctx, int on);
 
 /* Block Karatsuba settings of QRNG_ALGO_GEMM_KARATSUBA (0 = chosen by the cost model, the default):
- *   levels          rounds of the 2x2 block split, 1..3;
+ *   levels          rounds of the 2x2 block split, 1..4 (3^levels sub-products);
  *   block_bits      h, the side of the square Toeplitz blocks: 256, 512, 1024, 2048, 4096 or 8192
  *                   (256 lets the two output tiles of a pair tile share T tiles across blocks: no
  *                   extra operand build per block);

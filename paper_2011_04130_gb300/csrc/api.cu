@@ -1368,7 +1368,7 @@ int qrng_set_autotune(qrng_ctx* ctx, int on) {
 
 int qrng_set_karatsuba(qrng_ctx* ctx, int levels, uint64_t block_bits, uint64_t max_workspace) {
   if (!ctx) return QRNG_EINVAL;
-  if (levels < 0 || levels > 3) return fail(ctx, QRNG_EINVAL, "qrng_set_karatsuba: levels must be 0..3");
+  if (levels < 0 || levels > (int)kMaxLevels) return fail(ctx, QRNG_EINVAL, "qrng_set_karatsuba: levels must be 0..4");
   if (block_bits != 0 && (block_bits < 256 || block_bits > 8192 || (block_bits & (block_bits - 1)) != 0))
     return fail(ctx, QRNG_EINVAL, "qrng_set_karatsuba: block_bits must be 0 or a power of two in [256, 8192]");
   ctx->kara_levels = levels;

@@ -37,6 +37,8 @@ constexpr int kPackThreads = 128;  // combine-and-pack CTAs (one block each; mos
 constexpr uint32_t kPackSmemWords = 12288;  // 48 KB of shared memory per combine-and-pack CTA
 constexpr uint64_t kDefaultWorkspace = 1ull << 30;  // derived operands + sub-product parities per pass
 
+__host__ __device__ constexpr int pow3c(int l) { return l == 0 ? 1 : 3 * pow3c(l - 1); }
+
 __host__ __device__ inline uint32_t pow3(uint32_t l) {
   uint32_t r = 1;
   for (uint32_t i = 0; i < l; ++i) r *= 3;
@@ -48,7 +50,7 @@ __host__ __device__ inline uint32_t pow3(uint32_t l) {
 __global__ void kara_seed_kernel(const uint32_t* __restrict__ rev, uint64_t rev_words, uint32_t levels, uint32_t hw,
                                  uint32_t front, uint64_t words, uint32_t* __restrict__ seeds, uint64_t stride) {
   const uint32_t z = blockIdx.y;
-  int64_t offs[8];
+  int64_t offs[1 << kMaxLevels];
   uint32_t n = 1;
   offs[0] = 0;
   uint32_t zz = z;
@@ -78,7 +80,7 @@ __global__ void kara_split_kernel(const uint32_t* __restrict__ raw, uint64_t raw
                                   uint32_t tail_mask, uint64_t nb, uint32_t hw, uint32_t kblocks, uint64_t xk_words,
                                   uint32_t* __restrict__ xk) {
   constexpr int Q = 1 << L;
-  constexpr int G = L == 1 ? 3 : L == 2 ? 9 : 27;
+  constexpr int G = pow3c(L);
   uint32_t take[G];  // bit q: raw h-block q of the group enters sub-product z
 #pragma unroll
   for (int z = 0; z < G; ++z) {
@@ -134,7 +136,7 @@ __global__ void kara_combine_kernel(const uint32_t* __restrict__ qpar, uint64_t 
                                     uint32_t rblocks, uint32_t* __restrict__ out, uint64_t out_stride, uint32_t mw,
                                     uint32_t m, int modified, uint32_t id_off, const uint32_t* __restrict__ raw,
                                     uint64_t raw_stride) {
-  constexpr int G = L == 1 ? 3 : L == 2 ? 9 : 27;
+  constexpr int G = pow3c(L);
   const uint32_t hw = 1u << (log2h - 5);
   const uint64_t total = nb * rblocks * hw;
   for (uint64_t idx = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; idx < total;
@@ -194,7 +196,7 @@ __global__ void __launch_bounds__(kPackThreads) kara_combine_pack_kernel(
     const uint32_t* __restrict__ qpar, uint64_t mwq, uint32_t log2h, uint32_t cw, uint32_t* __restrict__ stream,
     uint64_t block0, uint64_t total_blocks, uint32_t mw, uint32_t m, int modified, uint32_t id_off,
     const uint32_t* __restrict__ raw, uint64_t raw_stride) {
-  constexpr int G = L == 1 ? 3 : L == 2 ? 9 : 27;
+  constexpr int G = pow3c(L);
   extern __shared__ __align__(16) uint32_t smem_words[];
   uint32_t* qs = smem_words;           // [G][cw]: the staged parity row words
   uint32_t* sw = smem_words + G * cw;  // the block's mw output words
@@ -213,23 +215,20 @@ __global__ void __launch_bounds__(kPackThreads) kara_combine_pack_kernel(
     for (uint32_t t = threadIdx.x; t < n; t += blockDim.x) {
       const uint32_t row_word = rw0 + t;  // = R * hw + lw
       const uint32_t R = row_word / hw, lw = row_word - R * hw;
-      uint32_t qz[G];
-#pragma unroll
-      for (int z = 0; z < G; ++z) qz[z] = qs[z * cw + t];
 #pragma unroll
       for (int q = 0; q < (1 << L); ++q) {
         const uint32_t ow = (((R << L) + (uint32_t)q) << (log2h - 5)) + lw;
         if (ow >= mw) break;
         uint32_t acc = 0;
 #pragma unroll
-        for (int s = 0; s < (1 << L); ++s) {
+        for (int s = 0; s < (1 << L); ++s) {  // subset s of the levels whose digit is B or C
           int z = 0, p3 = 1;
 #pragma unroll
           for (int l = 0; l < L; ++l) {
             if ((s >> l) & 1) z += (1 + ((q >> l) & 1)) * p3;
             p3 *= 3;
           }
-          acc ^= qz[z];
+          acc ^= qs[z * cw + t];
         }
         const uint32_t v0 = 32u * ow;
         const uint32_t rem = m - v0;
@@ -282,6 +281,27 @@ unsigned grid_for(uint64_t items, int num_sms) {
   return (unsigned)(want < cap ? (want > 0 ? want : 1) : cap);
 }
 
+template <int L>
+void launch_split(unsigned grid, cudaStream_t s, const DirectArgs& dc, const DirectArgs& d, uint64_t nb, uint32_t hw,
+                  uint32_t kblocks, uint64_t xk_words, KaraWorkspace& ws) {
+  kara_split_kernel<L><<<grid, kThreads, 0, s>>>(dc.raw, d.raw_stride, d.nw_t, d.tail_mask, nb, hw, kblocks, xk_words,
+                                                 ws.xk.as<uint32_t>());
+}
+
+template <int L>
+void launch_combine_pack(uint64_t nb, size_t smem, cudaStream_t s, const PairKara& k, uint64_t mwq, uint32_t log2h,
+                         uint32_t cw, uint32_t* stream, uint64_t b0, const DirectArgs& d, const DirectArgs& dc) {
+  kara_combine_pack_kernel<L><<<(unsigned)nb, kPackThreads, smem, s>>>(
+      k.qpar, mwq, log2h, cw, stream, b0, d.num_blocks, d.mw, d.m, d.modified, d.id_off, dc.raw, d.raw_stride);
+}
+
+template <int L>
+void launch_combine(unsigned grid, cudaStream_t s, const PairKara& k, uint64_t mwq, uint32_t log2h, uint64_t nb,
+                    uint32_t rblocks, const DirectArgs& d, const DirectArgs& dc) {
+  kara_combine_kernel<L><<<grid, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, rblocks, dc.out, d.out_stride, d.mw, d.m,
+                                                   d.modified, d.id_off, dc.raw, d.raw_stride);
+}
+
 }  // namespace
 
 KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_sms, int forced_levels,
@@ -290,7 +310,7 @@ KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_s
   if (n_t == 0 || m == 0 || num_blocks == 0 || n_t > kGemmMaxColumns) return best;
   const uint64_t budget = max_workspace ? max_workspace : kDefaultWorkspace;
   const double clusters = (double)(num_sms / 2 > 0 ? num_sms / 2 : 1);
-  for (uint32_t L = 1; L <= 3; ++L) {
+  for (uint32_t L = 1; L <= kMaxLevels; ++L) {
     if (forced_levels && (uint32_t)forced_levels != L) continue;
     for (uint32_t lg = 8; lg <= 13; ++lg) {
       const uint64_t h = 1ull << lg;
@@ -309,17 +329,17 @@ KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_s
       while ((uint64_t)G * chunk >= (1ull << 31)) chunk /= 2;
       if (chunk == 0) continue;
       // pair tiles of 512 sub-product rows x 224 blocks over whole rounds of one tile per cluster;
-      // a tile takes kq/256 product steps (0.46 us each on GB300) plus one build-only step per K
+      // a tile takes kq/256 product steps (0.477 us each on GB300) plus one build-only step per K
       // block (about half a step; one per tile when h = 256) and its accumulator hand-back (about
-      // six steps); the passes around it move their bytes at ~5 TB/s
+      // 2.8 steps); the passes around it (derived operands written and read, parities written and
+      // read once, the raw bits and the output) move their bytes at ~6 TB/s, part of them in L2
       const uint64_t passes = ceil_div(num_blocks, chunk);
       const double tiles = (double)G * (double)(mq / 512) * std::ceil((double)chunk / 224.0);
-      const double steps = (double)(kq / 256) + 0.5 * (double)(h == 256 ? 1 : kq / h) + 6.0;
-      const double kernel_s = (double)passes * std::ceil(tiles / clusters) * steps * 0.46e-6;
+      const double steps = (double)(kq / 256) + 0.5 * (double)(h == 256 ? 1 : kq / h) + 2.8;
+      const double kernel_s = (double)passes * std::ceil(tiles / clusters) * steps * 0.477e-6;
       const double bytes =
-          (double)num_blocks * ((double)n_t / 8 + 2.0 * G * (double)kq / 8 + (double)G * mq / 8 +
-                                (double)(1u << L) * (double)m / 8 + (double)m / 8);
-      const double t = kernel_s + bytes / 5e12 + (double)passes * 2e-5;
+          (double)num_blocks * ((double)n_t / 8 + 2.0 * G * (double)kq / 8 + 2.0 * G * (double)mq / 8 + (double)m / 8);
+      const double t = kernel_s + bytes / 6e12 + (double)passes * 2e-5;
       if (best.levels == 0 || t < best.model_s) {
         best.levels = L;
         best.h = h;
@@ -340,7 +360,7 @@ KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_s
 cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWorkspace& ws, int* err, int fault,
                                   int num_sms, cudaStream_t s, uint32_t* kernels, const TimingHook& hook,
                                   uint8_t* packed_out) {
-  if (p.levels < 1 || p.levels > 3) return cudaErrorInvalidValue;
+  if (p.levels < 1 || p.levels > kMaxLevels) return cudaErrorInvalidValue;
   const uint32_t G = p.groups;
   const uint32_t hw = (uint32_t)(p.h / 32);
   uint32_t log2h = 0;
@@ -379,15 +399,12 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
     dc.out = d.out + b0 * d.out_stride;
     dc.num_blocks = nb;
     const unsigned gs = grid_for(nb * kblocks * hw, num_sms);
-    if (p.levels == 1)
-      kara_split_kernel<1><<<gs, kThreads, 0, s>>>(dc.raw, d.raw_stride, d.nw_t, d.tail_mask, nb, hw, kblocks,
-                                                   xk_words, ws.xk.as<uint32_t>());
-    else if (p.levels == 2)
-      kara_split_kernel<2><<<gs, kThreads, 0, s>>>(dc.raw, d.raw_stride, d.nw_t, d.tail_mask, nb, hw, kblocks,
-                                                   xk_words, ws.xk.as<uint32_t>());
-    else
-      kara_split_kernel<3><<<gs, kThreads, 0, s>>>(dc.raw, d.raw_stride, d.nw_t, d.tail_mask, nb, hw, kblocks,
-                                                   xk_words, ws.xk.as<uint32_t>());
+    switch (p.levels) {
+      case 1: launch_split<1>(gs, s, dc, d, nb, hw, kblocks, xk_words, ws); break;
+      case 2: launch_split<2>(gs, s, dc, d, nb, hw, kblocks, xk_words, ws); break;
+      case 3: launch_split<3>(gs, s, dc, d, nb, hw, kblocks, xk_words, ws); break;
+      default: launch_split<4>(gs, s, dc, d, nb, hw, kblocks, xk_words, ws); break;
+    }
     ++*kernels;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
     hook.on_begin(s);
@@ -401,29 +418,23 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
       const uint32_t room = (kPackSmemWords - (uint32_t)d.mw) / (uint32_t)G;
       const uint32_t cw = (uint32_t)(mwq < (uint64_t)room ? mwq : (uint64_t)room) & ~3u;
       const size_t smem = ((size_t)G * cw + d.mw) * sizeof(uint32_t);
-      if (p.levels == 1)
-        kara_combine_pack_kernel<1><<<(unsigned)nb, kPackThreads, smem, s>>>(
-            k.qpar, mwq, log2h, cw, stream, b0, d.num_blocks, d.mw, d.m, d.modified, d.id_off, dc.raw, d.raw_stride);
-      else if (p.levels == 2)
-        kara_combine_pack_kernel<2><<<(unsigned)nb, kPackThreads, smem, s>>>(
-            k.qpar, mwq, log2h, cw, stream, b0, d.num_blocks, d.mw, d.m, d.modified, d.id_off, dc.raw, d.raw_stride);
-      else
-        kara_combine_pack_kernel<3><<<(unsigned)nb, kPackThreads, smem, s>>>(
-            k.qpar, mwq, log2h, cw, stream, b0, d.num_blocks, d.mw, d.m, d.modified, d.id_off, dc.raw, d.raw_stride);
+      switch (p.levels) {
+        case 1: launch_combine_pack<1>(nb, smem, s, k, mwq, log2h, cw, stream, b0, d, dc); break;
+        case 2: launch_combine_pack<2>(nb, smem, s, k, mwq, log2h, cw, stream, b0, d, dc); break;
+        case 3: launch_combine_pack<3>(nb, smem, s, k, mwq, log2h, cw, stream, b0, d, dc); break;
+        default: launch_combine_pack<4>(nb, smem, s, k, mwq, log2h, cw, stream, b0, d, dc); break;
+      }
       ++*kernels;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
       continue;
     }
     const unsigned gc = grid_for(nb * rblocks * hw, num_sms);
-    if (p.levels == 1)
-      kara_combine_kernel<1><<<gc, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, rblocks, dc.out, d.out_stride, d.mw, d.m,
-                                                     d.modified, d.id_off, dc.raw, d.raw_stride);
-    else if (p.levels == 2)
-      kara_combine_kernel<2><<<gc, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, rblocks, dc.out, d.out_stride, d.mw, d.m,
-                                                     d.modified, d.id_off, dc.raw, d.raw_stride);
-    else
-      kara_combine_kernel<3><<<gc, kThreads, 0, s>>>(k.qpar, mwq, log2h, nb, rblocks, dc.out, d.out_stride, d.mw, d.m,
-                                                     d.modified, d.id_off, dc.raw, d.raw_stride);
+    switch (p.levels) {
+      case 1: launch_combine<1>(gc, s, k, mwq, log2h, nb, rblocks, d, dc); break;
+      case 2: launch_combine<2>(gc, s, k, mwq, log2h, nb, rblocks, d, dc); break;
+      case 3: launch_combine<3>(gc, s, k, mwq, log2h, nb, rblocks, d, dc); break;
+      default: launch_combine<4>(gc, s, k, mwq, log2h, nb, rblocks, d, dc); break;
+    }
     ++*kernels;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }

@@ -244,6 +244,7 @@ struct TimingHook {
 // (T_d-1 ^ T_d) x0) leave 3^levels sub-products of mq x kq, each a Toeplitz matrix of a derived
 // seed restricted to every span-th h-block (span = h << levels); output block r = (R << levels) + q
 // is the XOR of the 2^levels sub-products that level l's bit of q selects (A and, by that bit, B or C).
+constexpr uint32_t kMaxLevels = 4;  // rounds of the 2 x 2 block split (3^4 = 81 sub-products at most)
 struct KaraPlan {
   uint32_t levels = 0;   // 0: no plan (the plain product)
   uint64_t h = 0, span = 0;

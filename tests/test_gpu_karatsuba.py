@@ -28,8 +28,8 @@ def kara(qlib, gpu):
     qlib.qrng_set_karatsuba(gpu, 0, 0, 0)
 
 
-SPLITS = [(1, 256), (2, 256), (3, 256), (1, 512), (2, 512), (3, 512), (1, 1024), (2, 1024), (3, 1024),
-          (1, 2048), (2, 2048), (1, 4096), (1, 8192)]
+SPLITS = [(1, 256), (2, 256), (3, 256), (4, 256), (1, 512), (2, 512), (3, 512), (4, 512), (1, 1024), (2, 1024),
+          (3, 1024), (1, 2048), (2, 2048), (1, 4096), (1, 8192)]
 SHAPES = [(5000, 3100, STD, 3), (5000, 3100, MOD, 230), (9000, 5000, STD, 2), (4500, 1700, MOD, 5),
           (3000, 2900, STD, 4), (2048, 1024, STD, 1), (700, 300, MOD, 3), (1, 1, STD, 2), (33, 17, MOD, 2)]
 
@@ -44,7 +44,7 @@ def test_forced_splits_bit_exact(qlib, gpu, oracle_mod, kara, levels, h, n, m, f
     assert np.array_equal(got, want)
 
 
-@pytest.mark.parametrize("levels,h", [(2, 1024), (3, 512), (2, 512), (3, 256), (2, 256)])
+@pytest.mark.parametrize("levels,h", [(2, 1024), (3, 512), (2, 512), (3, 256), (2, 256), (4, 256)])
 def test_laser_shape_several_blocks(qlib, gpu, oracle_mod, kara, levels, h):
     """The laser-stream block shape (n = 2^16, m = 36,473): nine row blocks of 1024 at two levels,
     sixteen K blocks; the sub-product sums reach 2^14 per accumulator."""
@@ -55,12 +55,12 @@ def test_laser_shape_several_blocks(qlib, gpu, oracle_mod, kara, levels, h):
     assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, STD, KARA, B), want)
 
 
-@pytest.mark.parametrize("h", [512, 256])
-def test_chunked_passes(qlib, gpu, oracle_mod, kara, h):
+@pytest.mark.parametrize("levels,h", [(2, 512), (2, 256), (4, 256)])
+def test_chunked_passes(qlib, gpu, oracle_mod, kara, levels, h):
     """A workspace budget of one 224-block pass: 700 blocks run in four passes whose outputs land
     at their blocks' places."""
     n, m, B = 4096, 3000, 700
-    kara(2, h, 1)  # below one block's need: the pass holds the minimum of 224 blocks
+    kara(levels, h, 1)  # below one block's need: the pass holds the minimum of 224 blocks
     raw, seed = _case(n, m, MOD, B, 11)
     want = oracle_mod.toeplitz_blocks(raw, n, m, seed, MOD, B)
     assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, MOD, KARA, B), want)
@@ -71,7 +71,7 @@ def test_many_blocks_match_direct(qlib, gpu, kara):
     n, m, B = 1 << 14, 12000, 224 * 9 + 5
     raw, seed = _case(n, m, STD, B, 13)
     ref = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_DIRECT, B)
-    for levels, h in ((2, 1024), (3, 512), (3, 256), (0, 0)):
+    for levels, h in ((2, 1024), (3, 512), (3, 256), (4, 256), (0, 0)):
         kara(levels, h)
         for _ in range(2):
             assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, STD, KARA, B), ref)
@@ -83,7 +83,7 @@ def test_all_ones_derived_operands(qlib, gpu, oracle_mod, kara):
     n, m, B = 1 << 16, 20000, 4
     raw = np.full(n * B // 8, 0xFF, dtype=np.uint8)
     seed = W.pack_bits(np.ones(n + m - 1, dtype=np.uint8))
-    for levels, h in ((1, 512), (2, 1024), (3, 2048), (3, 256)):
+    for levels, h in ((1, 512), (2, 1024), (3, 2048), (3, 256), (4, 256)):
         kara(levels, h)
         got = extract(qlib, gpu, raw, n, m, seed, STD, KARA, B)
         assert np.array_equal(np.unpackbits(got, bitorder="little")[:m * B], np.zeros(m * B, np.uint8) + (n & 1))
@@ -93,13 +93,13 @@ def test_long_blocks_spot_checked(qlib, gpu, oracle_mod, kara):
     """n_t = 2^22 - 96 (the tensor-core limit, ragged), one row block."""
     n, m, B = (1 << 22) - 96, 1000, 2
     raw, seed = _case(n, m, STD, B, 17)
-    for levels, h in ((0, 0), (2, 512), (2, 256)):
+    for levels, h in ((0, 0), (2, 512), (2, 256), (4, 256)):
         kara(levels, h)
         got = extract(qlib, gpu, raw, n, m, seed, STD, KARA, B)
         spot_check(oracle_mod, raw, n, m, seed, STD, got, blocks=[0, B - 1], per_block=96)
 
 
-@pytest.mark.parametrize("levels,h", [(-1, 0), (4, 0), (1, 128), (1, 3000), (2, 16384)])
+@pytest.mark.parametrize("levels,h", [(-1, 0), (5, 0), (1, 128), (1, 3000), (2, 16384)])
 def test_bad_settings_rejected(qlib, gpu, levels, h):
     with pytest.raises(qlib.QrngError) as e:
         qlib.qrng_set_karatsuba(gpu, levels, h, 0)
@@ -114,7 +114,7 @@ def test_plan_query(qlib, gpu, kara):
     p = qlib.qrng_karatsuba_plan(gpu, n, m, STD, B)
     L, h = p["levels"], p["h"]
     span = h << L
-    assert 1 <= L <= 3 and p["groups"] == 3 ** L
+    assert 1 <= L <= 4 and p["groups"] == 3 ** L
     rblocks = -(-m // span)
     if h == 256:
         rblocks += rblocks & 1
@@ -128,7 +128,7 @@ def test_plan_query(qlib, gpu, kara):
     assert e.value.status == qlib.QRNG_EINVAL
 
 
-@pytest.mark.parametrize("levels,h", [(0, 0), (1, 256), (2, 512), (3, 256)])
+@pytest.mark.parametrize("levels,h", [(0, 0), (1, 256), (2, 512), (3, 256), (4, 256)])
 @pytest.mark.parametrize("n,m,form,B", [
     (4096, 100, STD, 32), (5000, 3100, STD, 8), (1 << 16, 36473, STD, 32), (4500, 1700, MOD, 16),
     (3000, 99, STD, 31),  # 3069 output bits: the last byte has three pad bits

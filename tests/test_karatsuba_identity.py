@@ -83,7 +83,7 @@ def _karatsuba_hash(a, x, n_t, m, L, h, b_shift=-1):
     return y[:m]
 
 
-@pytest.mark.parametrize("L,h", [(1, 4), (2, 4), (3, 4), (1, 8), (2, 16), (3, 8), (2, 32)])
+@pytest.mark.parametrize("L,h", [(1, 4), (2, 4), (3, 4), (1, 8), (2, 16), (3, 8), (2, 32), (4, 4), (4, 8)])
 @pytest.mark.parametrize("n,m,form", [(300, 170, STD), (300, 170, MOD), (257, 257, STD), (129, 40, MOD),
                                       (64, 63, MOD), (1, 1, STD)])
 def test_block_karatsuba_equals_definition(oracle_mod, L, h, n, m, form):
@@ -99,7 +99,7 @@ def test_block_karatsuba_equals_definition(oracle_mod, L, h, n, m, form):
     assert np.array_equal(y, want)
 
 
-@pytest.mark.parametrize("L", [1, 2, 3])
+@pytest.mark.parametrize("L", [1, 2, 3, 4])
 def test_a_wrong_shift_sign_is_caught(oracle_mod, L):
     """The identity test is sensitive to the seed-shift direction: B and C shifts swapped fail."""
     n, m = 300, 170

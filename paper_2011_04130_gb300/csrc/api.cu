@@ -268,7 +268,10 @@ int minentropy_dev(qrng_ctx* ctx, const void* samples, uint64_t count, int bits,
   const uint64_t K = 1ull << bits;
   uint32_t kernels = 0;
   QRNG_CUDA(ctx, ctx->hist.ensure((K + 1) * sizeof(unsigned long long)), "histogram workspace");
+  const bool fresh_result = ctx->result.cap < sizeof(DevHminResult);
   QRNG_CUDA(ctx, ctx->result.ensure(sizeof(DevHminResult)), "result workspace");
+  // the finaliser's accumulators start at zero once; every finaliser run leaves them so
+  if (fresh_result) QRNG_CUDA(ctx, cudaMemsetAsync(ctx->result.p, 0, sizeof(DevHminResult), s), "result clear");
   if (thr >= (1ull << 53)) {
     LaunchTimer timer(ctx, s, kTimeHist);
     QRNG_CUDA(ctx, launch_histogram(samples, count, bits, ctx->hist.as<unsigned long long>(), ctx->num_sms, s, &kernels),

@@ -369,6 +369,164 @@ __global__ void __launch_bounds__(kCellThreads) hmin_cells_kernel(const unsigned
   r.delta_hm = log2((r.d_u + r.delta_fs) * ldexp(1.0, bits + 1) + 1.0);
   const double h = r.h_model - r.delta_hm;
   r.h_modify = h > 0.0 ? h : 0.0;
+  // leave the accumulators at zero for the next finaliser on this buffer (the fused kernel below
+  // does not clear them first)
+  out->pmax_bits = 0;
+  out->pmax_full_bits = 0;
+  out->dsum_fixed = 0;
+  out->done = 0;
+}
+
+// ------------------------------------------------------------------------------------------------
+// Fused finaliser for up to 2^kSmallMaxBits codes: ceil(K / kSmallCells) CTAs of one warp. Every
+// CTA recomputes the exact integer moments and the largest bin from the (small) histogram, so no
+// second launch hands them over; lanes 0 .. kSmallCells evaluate the CTA's boundary tails at once,
+// lanes below kSmallCells its cells. The accumulators (largest cells, distance sum, CTA count)
+// are zero on entry -- every finaliser leaves them so -- and the last CTA completes the report
+// with its final logarithms on separate lanes.
+// ------------------------------------------------------------------------------------------------
+constexpr int kSmallMaxBits = 10;
+constexpr int kSmallCells = 16;
+
+__device__ __forceinline__ u128_t shfl_xor_u128(u128_t v, int d) {
+  const uint64_t lo = __shfl_xor_sync(0xffffffffu, (uint64_t)v, d);
+  const uint64_t hi = __shfl_xor_sync(0xffffffffu, (uint64_t)(v >> 64), d);
+  return ((u128_t)hi << 64) | lo;
+}
+
+// Cell v = c0 + lane of N(mu, sg^2) for lanes below kSmallCells (boundaries v +- 1/2, end codes
+// take the tails); lane i <= kSmallCells computes the tail of boundary c0 - 1 + i.
+__device__ __forceinline__ double warp_cell(uint32_t c0, uint32_t K, double mu, double sg, uint32_t lane) {
+  const int64_t j = (int64_t)c0 - 1 + lane;  // boundary j lies between codes j and j + 1
+  const double z = (lane > (uint32_t)kSmallCells || j < 0 || j >= (int64_t)K - 1) ? CUDART_INF
+                                                                                  : (((double)j + 0.5 - mu) / sg);
+  const double t = erfc(fabs(z) * M_SQRT1_2);
+  const double t_hi = __shfl_down_sync(0xffffffffu, t, 1);
+  const uint32_t v = c0 + lane;
+  double P = 0.0;
+  if (lane < (uint32_t)kSmallCells && v < K) {
+    const double lo = (v == 0) ? -CUDART_INF : ((double)v - 0.5 - mu) / sg;
+    const double hi = (v == K - 1) ? CUDART_INF : ((double)v + 0.5 - mu) / sg;
+    P = cell_from_tails(lo, hi, t, t_hi);
+  }
+  return P;
+}
+
+__global__ void __launch_bounds__(32) hmin_small_kernel(const unsigned long long* __restrict__ hist, int bits,
+                                                        double eps, DevHminResult* __restrict__ out, double var_sub,
+                                                        double h_ref) {
+  const uint32_t K = 1u << bits;
+  const uint32_t lane = threadIdx.x;
+  // exact count, first and second moments (128-bit integers), largest bin (lowest code on ties)
+  unsigned long long n = 0, mx = 0;
+  uint32_t arg = 0xffffffffu;
+  u128_t s1 = 0, s2 = 0;
+  for (uint32_t v = lane; v < K; v += 32) {
+    const unsigned long long h = hist[v];
+    n += h;
+    s1 += (u128_t)v * h;
+    s2 += (u128_t)((unsigned long long)v * v) * h;
+    if (arg == 0xffffffffu || h > mx) {  // codes visited in increasing order: ties keep the lowest
+      mx = h;
+      arg = v;
+    }
+  }
+  for (int d = 16; d > 0; d >>= 1) {  // butterfly: every lane ends with the totals
+    n += __shfl_xor_sync(0xffffffffu, n, d);
+    s1 += shfl_xor_u128(s1, d);
+    s2 += shfl_xor_u128(s2, d);
+    max_arg_merge(mx, arg, __shfl_xor_sync(0xffffffffu, mx, d), __shfl_xor_sync(0xffffffffu, arg, d));
+  }
+  const unsigned long long N = n;
+  const unsigned long long oor = hist[K];
+  if (N == 0) {
+    if (blockIdx.x == 0 && lane == 0) {
+      out->n = 0;
+      out->out_of_range = oor;
+      out->status = QRNG_EINVAL;
+    }
+    return;
+  }
+  const u128_t num = (u128_t)N * s2 - s1 * s1;  // N^2 * population variance, exact
+  const double mu = (double)s1 / (double)N;
+  const double var = (double)num / ((double)N * (double)N);
+  const double var_q = var - var_sub;
+  const bool bad_sub = (var_sub > 0.0) && !(var_q > 0.0);
+  const bool point = (num == 0);
+  const double sigma = sqrt(var);
+  const double sigma_q = var_sub > 0.0 && var_q > 0.0 ? sqrt(var_q) : sigma;
+  const bool sub = var_sub > 0.0 && !bad_sub;
+  const uint32_t c0 = blockIdx.x * kSmallCells, v = c0 + lane;
+
+  double P;
+  if (point)  // every sample on one code: the model is that point mass
+    P = (lane < (uint32_t)kSmallCells && v < K && v == arg) ? 1.0 : 0.0;
+  else
+    P = warp_cell(c0, K, mu, sigma, lane);
+  double pf = P, pm = P;
+  unsigned long long ds = 0;
+  if (lane < (uint32_t)kSmallCells && v < K) {
+    ds = (unsigned long long)llrint(fabs((double)hist[v] / (double)N - P) * 0x1p62);
+    if (v == arg) out->p_argmax = P;
+  }
+  if (sub && !point) pm = warp_cell(c0, K, mu, sigma_q, lane);
+  // the finite-size term depends on N, K and eps only: computed before the hand-over
+  const double delta_fs = 0.5 * sqrt(2.0 * ((double)K * M_LN2 + log(1.0 / eps)) / (double)N);
+  for (int d = 16; d > 0; d >>= 1) {
+    pm = fmax(pm, __shfl_xor_sync(0xffffffffu, pm, d));
+    pf = fmax(pf, __shfl_xor_sync(0xffffffffu, pf, d));
+    ds += __shfl_xor_sync(0xffffffffu, ds, d);
+  }
+  uint32_t last = 0;
+  if (lane == 0) {
+    atomicMax(&out->pmax_bits, (unsigned long long)__double_as_longlong(pm));  // non-negative doubles
+    atomicMax(&out->pmax_full_bits, (unsigned long long)__double_as_longlong(pf));
+    atomicAdd(&out->dsum_fixed, ds);
+    __threadfence();
+    last = atomicAdd(&out->done, 1u) == gridDim.x - 1;
+  }
+  if (!__shfl_sync(0xffffffffu, last, 0)) return;
+  __threadfence();
+  const double PM = __longlong_as_double((long long)*(volatile unsigned long long*)&out->pmax_bits);
+  const double PF = __longlong_as_double((long long)*(volatile unsigned long long*)&out->pmax_full_bits);
+  const double d_u = 0.5 * (double)*(volatile unsigned long long*)&out->dsum_fixed * 0x1p-62;
+  const double pa = *(volatile double*)&out->p_argmax;
+  // the four logarithms of the report at once, one per lane
+  const double larg = lane == 0 ? PM : lane == 1 ? PF : lane == 2 ? (double)mx / (double)N
+                                                                    : (d_u + delta_fs) * ldexp(1.0, bits + 1) + 1.0;
+  const double lg = log2(larg);
+  const double l_pm = __shfl_sync(0xffffffffu, lg, 0), l_pf = __shfl_sync(0xffffffffu, lg, 1);
+  const double l_emp = __shfl_sync(0xffffffffu, lg, 2), l_hm = __shfl_sync(0xffffffffu, lg, 3);
+  __syncwarp();
+  if (lane != 0) return;
+  qrng_hmin_report& r = out->rep;
+  out->n = N;
+  out->out_of_range = oor;
+  out->mu = mu;
+  out->sigma = sigma;
+  out->sigma_q = sigma_q;
+  out->point = point;
+  out->bad_sub = bad_sub;
+  r.count = N;
+  r.max_count = mx;
+  r.argmax = arg;
+  r.bits = (uint32_t)bits;
+  r.mean = mu;
+  r.var = sub ? var_q : var;
+  r.h_emp = -l_emp;
+  r.h_model = -l_pm;
+  out->h_subtracted = -l_pf - h_ref;
+  r.d_u = d_u;
+  r.d_u_peak = 0.5 * fabs((double)mx / (double)N - pa);
+  r.delta_fs = delta_fs;
+  r.delta_hm = l_hm;
+  const double h = r.h_model - r.delta_hm;
+  r.h_modify = h > 0.0 ? h : 0.0;
+  out->status = (oor || bad_sub) ? QRNG_EINVAL : QRNG_OK;
+  out->pmax_bits = 0;
+  out->pmax_full_bits = 0;
+  out->dsum_fixed = 0;
+  out->done = 0;
 }
 
 // Random subsample (any width): counters in shared memory for up to 2^13 codes, else global.
@@ -456,6 +614,12 @@ cudaError_t launch_histogram_sampled(const void* samples, uint64_t count, int bi
 
 cudaError_t launch_hmin_finalize(const unsigned long long* hist, int bits, double eps, DevHminResult* out,
                                  cudaStream_t s, uint32_t* kernels, double var_sub, double h_ref) {
+  if (bits <= kSmallMaxBits) {
+    const uint32_t ctas = (uint32_t)ceil_div(1u << bits, (uint64_t)kSmallCells);
+    hmin_small_kernel<<<ctas, 32, 0, s>>>(hist, bits, eps, out, var_sub, h_ref);
+    ++*kernels;
+    return cudaGetLastError();
+  }
   hmin_moments_kernel<<<1, kFinThreads, 0, s>>>(hist, bits, out, var_sub);
   ++*kernels;
   cudaError_t e = cudaGetLastError();

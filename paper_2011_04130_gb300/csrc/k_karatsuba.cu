@@ -28,6 +28,7 @@
 #include <cmath>
 
 #include "qrng_internal.h"
+#include "tc_util.cuh"
 
 namespace qrng {
 namespace {
@@ -35,6 +36,7 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kPackThreads = 128;  // combine-and-pack CTAs (one block each; most of the work is the staging)
 constexpr uint32_t kPackSmemWords = 12288;  // 48 KB of shared memory per combine-and-pack CTA
+constexpr size_t kPackBulkMaxSmem = 112 * 1024;  // double-buffered combination: at least two CTAs per SM
 constexpr uint64_t kDefaultWorkspace = 1ull << 30;  // derived operands + sub-product parities per pass
 
 __host__ __device__ constexpr int pow3c(int l) { return l == 0 ? 1 : 3 * pow3c(l - 1); }
@@ -275,6 +277,122 @@ __global__ void __launch_bounds__(kPackThreads) kara_combine_pack_kernel(
   }
 }
 
+// The combination for blocks whose parities fit twice in shared memory: persistent CTAs loop over
+// blocks; a block's 3^L parity rows (one contiguous run of G mwq words) arrive by one bulk copy into
+// one of two buffers while the previous block is combined and written, so every CTA keeps a copy in
+// flight through its compute and store phases. Same output as kara_combine_pack_kernel. Waits are
+// bounded: on a timeout the CTA records `err`, waits (again bounded) for its copy in flight and
+// returns.
+template <int L>
+__global__ void __launch_bounds__(kPackThreads) kara_combine_pack_bulk_kernel(
+    const uint32_t* __restrict__ qpar, uint32_t mwq, uint32_t log2h, uint32_t* __restrict__ stream, uint64_t nb,
+    uint64_t block0, uint64_t total_blocks, uint32_t mw, uint32_t m, int modified, uint32_t id_off,
+    const uint32_t* __restrict__ raw, uint64_t raw_stride, int* err) {
+  using namespace tc;
+  constexpr int G = pow3c(L);
+  extern __shared__ __align__(16) uint32_t smem_words[];
+  __shared__ __align__(8) uint64_t full[2];
+  __shared__ volatile int abort_flag;
+  const uint32_t qwords = (uint32_t)G * mwq;  // a multiple of 8: 32-byte runs
+  const uint32_t bytes = qwords * 4u;
+  uint32_t* sw = smem_words + 2 * qwords;     // the block's mw output words
+  const uint32_t hw = 1u << (log2h - 5);
+  if (threadIdx.x == 0) {
+    mbar_init(&full[0], 1);
+    mbar_init(&full[1], 1);
+    abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  auto issue = [&](uint64_t blk, uint32_t slot) {
+    fence_proxy_async_smem();  // the buffer's earlier generic reads before the async-proxy write
+    mbar_arrive_expect_tx(&full[slot], bytes);
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(smem_words + slot * qwords)),
+        "l"(qpar + blk * qwords), "r"(bytes), "r"(smem_u32(&full[slot]))
+        : "memory");
+  };
+  if (threadIdx.x == 0 && blockIdx.x < nb) issue(blockIdx.x, 0);
+  uint32_t it = 0;
+  for (uint64_t b = blockIdx.x; b < nb; b += gridDim.x, ++it) {
+    const uint32_t slot = it & 1u;
+    const uint64_t bn = b + gridDim.x;
+    if (threadIdx.x == 0 && bn < nb) issue(bn, slot ^ 1u);  // that buffer's last reader passed the barrier below
+    mbar_wait(&full[slot], (it >> 1) & 1u, &abort_flag, err, 11);
+    __syncthreads();
+    if (abort_flag) {  // the copies this CTA issued must land before it exits
+      if (threadIdx.x == 0) {
+        mbar_drain(&full[slot], (it >> 1) & 1u, err, 12);
+        if (bn < nb) mbar_drain(&full[slot ^ 1u], ((it + 1) >> 1) & 1u, err, 12);
+      }
+      return;
+    }
+    const uint32_t* qs = smem_words + slot * qwords;
+    const uint32_t* rr = raw + b * raw_stride;
+    for (uint32_t t = threadIdx.x; t < mwq; t += blockDim.x) {
+      const uint32_t R = t / hw, lw = t - R * hw;  // row word t = R * hw + lw
+#pragma unroll
+      for (int q = 0; q < (1 << L); ++q) {
+        const uint32_t ow = (((R << L) + (uint32_t)q) << (log2h - 5)) + lw;
+        if (ow >= mw) break;
+        uint32_t acc = 0;
+#pragma unroll
+        for (int s = 0; s < (1 << L); ++s) {  // subset s of the levels whose digit is B or C
+          int z = 0, p3 = 1;
+#pragma unroll
+          for (int l = 0; l < L; ++l) {
+            if ((s >> l) & 1) z += (1 + ((q >> l) & 1)) * p3;
+            p3 *= 3;
+          }
+          acc ^= qs[z * mwq + t];
+        }
+        const uint32_t v0 = 32u * ow;
+        const uint32_t rem = m - v0;
+        const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
+        acc &= omask;
+        if (modified) {
+          const uint64_t bit = (uint64_t)id_off + v0;
+          const uint64_t rq = bit >> 5;
+          const uint32_t rs = (uint32_t)(bit & 31);
+          const uint32_t rlo = __ldg(rr + rq);
+          const uint32_t rhi = (rs && rq + 1 < raw_stride) ? __ldg(rr + rq + 1) : 0u;
+          acc ^= __funnelshift_r(rlo, rhi, rs) & omask;
+        }
+        sw[ow] = acc;
+      }
+    }
+    __syncthreads();
+    const uint64_t gb = block0 + b;
+    const uint64_t bm = gb * m;
+    const uint64_t d0 = bm >> 5, d1 = (bm + m - 1) >> 5;
+    const bool last = gb + 1 == total_blocks;
+    for (uint64_t D = d0 + threadIdx.x; D <= d1; D += blockDim.x) {
+      const int64_t off = (int64_t)(32 * D) - (int64_t)bm;  // block bit of the word's bit 0
+      uint32_t v, mask;
+      if (off >= 0) {
+        const uint32_t q = (uint32_t)(off >> 5), sh = (uint32_t)(off & 31);
+        const uint32_t lo = sw[q], hi = (sh && q + 1 < mw) ? sw[q + 1] : 0u;
+        v = __funnelshift_r(lo, hi, sh);
+        const uint64_t rem = m - (uint64_t)off;
+        mask = (rem >= 32 || last) ? 0xffffffffu : ((1u << rem) - 1u);  // the last block owns the pad bits
+      } else {
+        const uint32_t k0 = (uint32_t)(-off);  // 1..31: the word starts inside the previous block
+        v = sw[0] << k0;
+        mask = 0xffffffffu << k0;
+      }
+      v &= mask;
+      if (mask == 0xffffffffu) {
+        stream[D] = v;
+      } else {
+        atomicAnd(stream + D, ~mask);
+        atomicOr(stream + D, v);
+      }
+    }
+    __syncthreads();  // sw and this buffer are free again
+  }
+}
+
 unsigned grid_for(uint64_t items, int num_sms) {
   const uint64_t want = ceil_div(items, kThreads);
   const uint64_t cap = (uint64_t)(num_sms > 0 ? num_sms : 1) * 16;
@@ -293,6 +411,28 @@ void launch_combine_pack(uint64_t nb, size_t smem, cudaStream_t s, const PairKar
                          uint32_t cw, uint32_t* stream, uint64_t b0, const DirectArgs& d, const DirectArgs& dc) {
   kara_combine_pack_kernel<L><<<(unsigned)nb, kPackThreads, smem, s>>>(
       k.qpar, mwq, log2h, cw, stream, b0, d.num_blocks, d.mw, d.m, d.modified, d.id_off, dc.raw, d.raw_stride);
+}
+
+template <int L>
+cudaError_t launch_combine_pack_bulk(unsigned grid, size_t smem, cudaStream_t s, const PairKara& k, uint32_t mwq,
+                                     uint32_t log2h, uint32_t* stream, uint64_t nb, uint64_t b0, const DirectArgs& d,
+                                     const DirectArgs& dc, int* err) {
+  // the shared-memory attribute is set once per device and level count
+  constexpr int kMaxDev = 64;
+  static size_t set_to[kMaxDev] = {};
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDev || set_to[dev] < smem) {
+    e = cudaFuncSetAttribute(kara_combine_pack_bulk_kernel<L>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)kPackBulkMaxSmem);
+    if (e != cudaSuccess) return e;
+    if (dev >= 0 && dev < kMaxDev) set_to[dev] = kPackBulkMaxSmem;
+  }
+  kara_combine_pack_bulk_kernel<L><<<grid, kPackThreads, smem, s>>>(k.qpar, mwq, log2h, stream, nb, b0, d.num_blocks,
+                                                                     d.mw, d.m, d.modified, d.id_off, dc.raw,
+                                                                     d.raw_stride, err);
+  return cudaGetLastError();
 }
 
 template <int L>
@@ -412,8 +552,24 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
     hook.on_end(s);
     if (e != cudaSuccess) return e;
     const uint32_t rblocks = (uint32_t)ceil_div(d.m, p.span);
-    if (packed_out) {  // combine and pack in one pass, one CTA per block
+    if (packed_out) {  // combine and pack in one pass
       uint32_t* stream = reinterpret_cast<uint32_t*>(packed_out);
+      const size_t bulk_smem = ((size_t)2 * G * mwq + d.mw) * sizeof(uint32_t);
+      if (bulk_smem <= kPackBulkMaxSmem) {  // persistent CTAs, one bulk copy per block, double-buffered
+        const uint64_t per_sm = (227 * 1024) / (bulk_smem + 1024);
+        const uint64_t ctas = (uint64_t)(num_sms > 0 ? num_sms : 1) * (per_sm < 8 ? per_sm : 8);
+        const unsigned grid = (unsigned)(ctas < nb ? ctas : nb);
+        switch (p.levels) {
+          case 1: e = launch_combine_pack_bulk<1>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err); break;
+          case 2: e = launch_combine_pack_bulk<2>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err); break;
+          case 3: e = launch_combine_pack_bulk<3>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err); break;
+          default: e = launch_combine_pack_bulk<4>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err); break;
+        }
+        ++*kernels;
+        if (e != cudaSuccess) return e;
+        continue;
+      }
+      // one CTA per block, the parity rows staged in chunks
       // staged row words per sub-product: as many as fit beside the output words (multiples of 4)
       const uint32_t room = (kPackSmemWords - (uint32_t)d.mw) / (uint32_t)G;
       const uint32_t cw = (uint32_t)(mwq < (uint64_t)room ? mwq : (uint64_t)room) & ~3u;

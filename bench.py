@@ -3,8 +3,8 @@
 Workload (the laser-phase-noise stream): 2^26 uint8 ADC samples ~ clip(round(N(128, 16^2))),
 whose bytes are also the 2^29-bit raw stream; blocks of n = 2^16 bits; m = floor(n H_modify / 8)
 from the corrected min-entropy (eps = 1e-6); one standard Toeplitz seed of n+m-1 bits shared by
-every block. One step = min-entropy estimate (histogram + FP64 finaliser, report read back)
-+ extraction of all 8192 blocks. Metric: extracted output Gbit/s, bit-exact.
+every block. One step = one qrng_postprocess call: min-entropy estimate (histogram + FP64
+finaliser, report read back) + extraction of all 8192 blocks. Metric: extracted output Gbit/s, bit-exact.
 
 Prints one JSON line (rank 0). `--impl reference` times the CPU oracle instead.
 """
@@ -222,9 +222,9 @@ def run_ours(args, world, rank, local):
     flush = torch.empty(L2_FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
     def step(a=algo):
-        rep = q.qrng_minentropy(ctx, samples, bits=bits, eps=eps, stream=stream)
-        m = q.qrng_output_length(n, rep["h_modify"], bits, 1.0)
-        q.qrng_toeplitz_extract(ctx, samples, n, m, seed, q.QRNG_FORM_STANDARD, a, num_blocks, out, stream=stream)
+        # the whole path in one call: estimate (read back to size m), then the hash of every block
+        m, _, _ = q.qrng_postprocess(ctx, samples, num_blocks * n // 8, bits, eps, 1.0, n, seed, 2 * n - 1,
+                                     q.QRNG_FORM_STANDARD, a, out, out.numel(), stream=stream)
         return m
 
     for _ in range(args.warmup):

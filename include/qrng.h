@@ -25,7 +25,8 @@
  *
  * Streams: `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
  * Extraction calls are asynchronous: they return after enqueueing the work on `stream`.
- * Calls that return host results (qrng_minentropy, qrng_postprocess_host) synchronise `stream`.
+ * Calls that return host results (qrng_minentropy, qrng_postprocess, qrng_postprocess_host) synchronise
+ * `stream` (qrng_postprocess only up to its estimate).
  *
  * Errors: every int-returning function returns a qrng_status; on failure the context keeps a
  * message (qrng_last_error). No function aborts or raises; a kernel never traps.
@@ -268,8 +269,35 @@ QRNG_API int qrng_extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_
                                 qrng_stream_t stream);
 
 /* ----------------------------------------------------------------------------------------------
- * Whole pipeline on host buffers
+ * Whole pipeline
  * --------------------------------------------------------------------------------------------*/
+
+/*
+ * qrng_postprocess -- the post-processing of Sec. II + III on device buffers: estimate H_modify of
+ * the ADC samples (as qrng_minentropy), size the output m = qrng_output_length(n, H_modify, bits,
+ * eps_lhl) (m <= n - 1 for the modified form of Sec. III.D), treat the sample bytes as the raw bit
+ * stream (sample s occupies raw bits [8s, 8s+8) for bits <= 8, [16s, 16s+16) otherwise) and hash
+ * its floor(total_bits / n) whole n-bit blocks with `seed` (as qrng_toeplitz_extract with the
+ * given form and algo) into `out`.
+ *
+ *   samples        device; count samples as for qrng_minentropy (also the raw stream).
+ *   seed           device; at least seed_capacity_bits bits; must cover qrng_seed_bits(n, m, form).
+ *   out            device; out_capacity_bytes bytes; must hold ceil(num_blocks*m/8) bytes, written
+ *                  as by qrng_toeplitz_extract.
+ *   m_out, num_blocks_out, rep   host; receive m, the number of blocks and the entropy report
+ *                  (any of them may be NULL).
+ * Returns QRNG_EINVAL when m comes out 0 or a capacity is too small (m_out / num_blocks_out are
+ * still written). The estimate synchronises `stream` (m is needed on the host to plan the hash);
+ * the hash is enqueued on `stream` and the call returns without waiting for it. When the previous
+ * call on this context had the same n, count, bits and form and its hash ran on the block-Karatsuba
+ * route, the derived raw operands of that route (which do not depend on m in the standard form)
+ * are computed on a second stream of the context while the estimate runs; a different m only
+ * costs computing them again. The buffers belong to the call until `stream` reaches its end.
+ */
+QRNG_API int qrng_postprocess(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps,
+                              double eps_lhl, uint64_t n, const uint8_t* seed, uint64_t seed_capacity_bits, int form,
+                              int algo, uint8_t* out, uint64_t out_capacity_bytes, uint64_t* m_out,
+                              uint64_t* num_blocks_out, qrng_hmin_report* rep, qrng_stream_t stream);
 
 /*
  * qrng_postprocess_host -- the post-processing of Sec. II + III on host memory: copy the ADC
@@ -319,6 +347,9 @@ typedef struct {
   uint64_t fft32_recomputed;     /* FP32 segmented calls whose rounding guard tripped and whose
                                     output the exact direct kernel recomputed                   */
   uint64_t last_fft32_segment;   /* segment length S of the last FP32 segmented call            */
+  uint64_t kara_presplits;       /* qrng_postprocess / _host: derived operands of the block-
+                                    Karatsuba route computed beside the estimate                 */
+  uint64_t kara_presplits_used;  /* ... and taken by the hash (the rest were computed again)     */
 } qrng_stats;
 
 /* Statistics since creation or the last reset. When timing is on, this call waits for the

@@ -24,7 +24,7 @@ ALGO_NAMES = {QRNG_ALGO_AUTO: "auto", QRNG_ALGO_DIRECT: "direct", QRNG_ALGO_GEMM
               QRNG_ALGO_GEMM_KARATSUBA: "gemm_karatsuba"}
 
 EXPORTED = ["qrng_create", "qrng_destroy", "qrng_last_error", "qrng_status_string", "qrng_minentropy",
-            "qrng_output_length", "qrng_seed_bits", "qrng_toeplitz_extract", "qrng_postprocess_host",
+            "qrng_output_length", "qrng_seed_bits", "qrng_toeplitz_extract", "qrng_postprocess", "qrng_postprocess_host",
             "qrng_get_stats", "qrng_reset_stats", "qrng_set_timing", "qrng_synchronize",
             "qrng_minentropy_noalloc", "qrng_extract_batch", "qrng_set_autotune", "qrng_inject_fault",
             "qrng_minentropy_sampled", "qrng_minentropy_quantum", "qrng_set_karatsuba", "qrng_karatsuba_plan",
@@ -92,6 +92,8 @@ class Stats(ctypes.Structure):
         ("worst_fft32_round_err", ctypes.c_double),
         ("fft32_recomputed", ctypes.c_uint64),
         ("last_fft32_segment", ctypes.c_uint64),
+        ("kara_presplits", ctypes.c_uint64),
+        ("kara_presplits_used", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:
@@ -137,6 +139,8 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
     lib.qrng_seed_bits.argtypes = [u64, u64, i32]
     lib.qrng_seed_bits.restype = u64
     lib.qrng_toeplitz_extract.argtypes = [vp, vp, u64, u64, vp, i32, i32, u64, vp, vp]
+    lib.qrng_postprocess.argtypes = [vp, vp, u64, i32, dbl, dbl, u64, vp, u64, i32, i32, vp, u64,
+                                     ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(HminReport), vp]
     lib.qrng_postprocess_host.argtypes = [vp, vp, u64, i32, dbl, dbl, u64, vp, u64, i32, i32, vp, u64,
                                           ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(HminReport), vp]
     lib.qrng_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
@@ -266,6 +270,20 @@ def qrng_toeplitz_extract(ctx: Context, raw, n: int, m: int, seed, form: int, al
                                               _ptr(out), _stream(stream))
     ctx.check(st, "qrng_toeplitz_extract")
     return out
+
+
+def qrng_postprocess(ctx: Context, samples, count: int, bits: int, eps: float, eps_lhl: float, n: int, seed,
+                     seed_capacity_bits: int, form: int, algo: int, out, out_capacity_bytes: int, stream=None):
+    """Whole pipeline on device buffers (the samples are also the raw stream); returns
+    (m, num_blocks, report). The hash is left running on `stream`."""
+    m = ctypes.c_uint64()
+    nb = ctypes.c_uint64()
+    rep = HminReport()
+    st = load_library().qrng_postprocess(ctx.handle, _ptr(samples), count, bits, eps, eps_lhl, n, _ptr(seed),
+                                         seed_capacity_bits, form, algo, _ptr(out), out_capacity_bytes,
+                                         ctypes.byref(m), ctypes.byref(nb), ctypes.byref(rep), _stream(stream))
+    ctx.check(st, "qrng_postprocess")
+    return int(m.value), int(nb.value), rep.as_dict()
 
 
 def qrng_postprocess_host(ctx: Context, samples, count: int, bits: int, eps: float, eps_lhl: float, n: int, seed,

@@ -1015,6 +1015,111 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int a
   return QRNG_OK;
 }
 
+// The QRNG_ALGO_AUTO choice already tuned for this shape, or -1.
+int tuned_choice(const qrng_ctx* ctx, uint64_t n, uint64_t m, uint64_t num_blocks, int form) {
+  if (!ctx->autotune) return -1;
+  uint32_t lb = 0;
+  while ((1ull << lb) < num_blocks) ++lb;
+  const qrng_ctx::TuneKey key{n, m, lb, form};
+  for (const auto& e : ctx->tuned)
+    if (e.first == key) return e.second.algo;
+  return -1;
+}
+
+// The block-Karatsuba route's derived operands depend on the raw blocks, n_t and the plan, not on
+// the seed: when the previous pipeline call of this stream shape settled on that route, they are
+// computed on the context's second stream while the min-entropy estimate and its read-back run,
+// for the m that call found (a different m this time only costs the split again). The pipeline
+// makes its stream wait for the second stream before hashing.
+bool pipeline_presplit(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, int form, int algo, uint64_t num_blocks,
+                       uint64_t count, int bits, cudaStream_t s) {
+  ctx->kara.xk_ready = false;
+  const qrng_ctx::PipelineShape shape{n, count, bits, form, num_blocks};
+  if (!ctx->pipeline_seen || !(ctx->pipeline_shape == shape) || num_blocks == 0) return false;
+  const uint64_t m = ctx->pipeline_m;
+  if (m == 0 || m > n || (form == QRNG_FORM_MODIFIED && m >= n)) return false;
+  const int a = algo == QRNG_ALGO_AUTO ? tuned_choice(ctx, n, m, num_blocks, form) : algo;
+  if (a != QRNG_ALGO_GEMM_KARATSUBA) return false;
+  const uint64_t n_t = form == QRNG_FORM_MODIFIED ? n - m : n;
+  if (!algo_applicable(QRNG_ALGO_GEMM_KARATSUBA, n_t, m, num_blocks)) return false;
+  // only when the extraction reads the raw blocks in place (otherwise it repacks them first)
+  if (n % 128 != 0 || (reinterpret_cast<uintptr_t>(raw) & 15) != 0) return false;
+  const KaraPlan plan = karatsuba_plan(n_t, m, num_blocks, ctx->num_sms, ctx->kara_levels, ctx->kara_h,
+                                       ctx->kara_workspace);
+  if (plan.levels == 0) return false;
+  DirectArgs a_args{};
+  a_args.n_t = n_t;
+  a_args.raw = reinterpret_cast<const uint32_t*>(raw);
+  a_args.raw_stride = n / 32;
+  a_args.nw_t = (uint32_t)ceil_div(n_t, 32);
+  a_args.tail_mask = (n_t % 32) ? ((1u << (n_t % 32)) - 1u) : 0xffffffffu;
+  a_args.num_blocks = num_blocks;
+  if (cudaEventRecord(ctx->pre_ready, s) != cudaSuccess) return false;
+  if (cudaStreamWaitEvent(ctx->copy_stream, ctx->pre_ready, 0) != cudaSuccess) return false;
+  uint32_t kernels = 0;
+  if (launch_kara_presplit(a_args, plan, ctx->kara, ctx->num_sms, ctx->copy_stream, &kernels) != cudaSuccess) {
+    ctx->kara.xk_ready = false;
+    cudaGetLastError();
+    return false;
+  }
+  ctx->stats.kernels_launched += kernels;
+  ++ctx->stats.kara_presplits;
+  if (cudaEventRecord(ctx->pre_done, ctx->copy_stream) != cudaSuccess) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    ctx->kara.xk_ready = false;
+  }
+  return true;
+}
+
+// The pipeline's first half on device samples: the pre-split above, the min-entropy estimate
+// (which synchronises `s`) and the output length; `first_blocks` is the block count of the first
+// extraction call that follows. On return `s` is ordered after the pre-split.
+int pipeline_size(qrng_ctx* ctx, const char* who, const void* samples, uint64_t count, int bits, double eps,
+                  double eps_lhl, uint64_t n, uint64_t seed_capacity_bits, int form, int algo,
+                  uint64_t first_blocks, cudaStream_t s, uint64_t* m_out, qrng_hmin_report* rep) {
+  *m_out = 0;
+  const std::string w(who);
+  if (form != QRNG_FORM_STANDARD && form != QRNG_FORM_MODIFIED) return fail(ctx, QRNG_EINVAL, w + ": unknown form");
+  if (n < 2 || n > kMaxBlockBits) return fail(ctx, QRNG_EINVAL, w + ": n must be in [2, 2^26]");
+  if (!(eps_lhl > 0.0 && eps_lhl <= 1.0)) return fail(ctx, QRNG_EINVAL, w + ": eps_lhl in (0, 1]");
+  qrng_hmin_report local{};
+  int st = check_minentropy_args(ctx, samples, count, bits, eps, &local);
+  if (st) return st;
+  const uint64_t bytes = count * (bits <= 8 ? 1 : 2);
+  const uint64_t num_blocks = bytes * 8 / n;
+  const bool pre = pipeline_presplit(ctx, static_cast<const uint8_t*>(samples), n, form, algo, first_blocks, count,
+                                     bits, s);
+  st = minentropy_dev(ctx, samples, count, bits, eps, &local, s);
+  if (pre) {
+    const cudaError_t e = cudaStreamWaitEvent(s, ctx->pre_done, 0);
+    if (e != cudaSuccess) {
+      cudaStreamSynchronize(ctx->copy_stream);
+      ctx->kara.xk_ready = false;
+    }
+  }
+  if (st) {
+    ctx->kara.xk_ready = false;
+    return st;
+  }
+  if (rep) *rep = local;
+  uint64_t m = qrng_output_length(n, local.h_modify, bits, eps_lhl);
+  if (form == QRNG_FORM_MODIFIED && m >= n) m = n - 1;
+  if (m > n) m = n;
+  *m_out = m;
+  ctx->pipeline_seen = true;
+  ctx->pipeline_shape = qrng_ctx::PipelineShape{n, count, bits, form, first_blocks};
+  ctx->pipeline_m = m;
+  const char* bad = m == 0 ? ": the corrected min-entropy gives m = 0"
+                    : num_blocks == 0 ? ": fewer than n raw bits"
+                    : seed_capacity_bits < qrng_seed_bits(n, m, form) ? ": seed shorter than the hash needs"
+                    : nullptr;
+  if (bad) {
+    ctx->kara.xk_ready = false;
+    return fail(ctx, QRNG_EINVAL, w + bad);
+  }
+  return QRNG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1050,14 +1155,15 @@ int qrng_create(qrng_ctx** out, int device) {
   if (cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
       cudaEventCreateWithFlags(&ctx->copy_ready, cudaEventDisableTiming) != cudaSuccess ||
-      cudaEventCreateWithFlags(&ctx->copy_done, cudaEventDisableTiming) != cudaSuccess) {
+      cudaEventCreateWithFlags(&ctx->copy_done, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->pre_ready, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&ctx->pre_done, cudaEventDisableTiming) != cudaSuccess) {
+    if (ctx->pre_done) cudaEventDestroy(ctx->pre_done);
+    if (ctx->pre_ready) cudaEventDestroy(ctx->pre_ready);
     if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
     if (ctx->copy_ready) cudaEventDestroy(ctx->copy_ready);
     if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     if (ctx->capture_stream) cudaStreamDestroy(ctx->capture_stream);
-  if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
-  if (ctx->copy_ready) cudaEventDestroy(ctx->copy_ready);
-  if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
     cudaFreeHost(ctx->result_host);
     ctx->dev_err.release();
     ctx->fft_worst.release();
@@ -1098,6 +1204,8 @@ void qrng_destroy(qrng_ctx* ctx) {
   if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
   if (ctx->copy_ready) cudaEventDestroy(ctx->copy_ready);
   if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
+  if (ctx->pre_ready) cudaEventDestroy(ctx->pre_ready);
+  if (ctx->pre_done) cudaEventDestroy(ctx->pre_done);
   if (ctx->result_host) cudaFreeHost(ctx->result_host);
   for (cudaEvent_t e : ctx->ev_start) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->ev_end) cudaEventDestroy(e);
@@ -1200,54 +1308,72 @@ int qrng_extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, 
   return extract_batch(ctx, reqs, count, algo, static_cast<cudaStream_t>(stream));
 }
 
+int qrng_postprocess(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps, double eps_lhl,
+                     uint64_t n, const uint8_t* seed, uint64_t seed_capacity_bits, int form, int algo, uint8_t* out,
+                     uint64_t out_capacity_bytes, uint64_t* m_out, uint64_t* num_blocks_out, qrng_hmin_report* rep,
+                     qrng_stream_t stream) {
+  if (!ctx) return QRNG_EINVAL;
+  if (!samples || !seed || !out) return fail(ctx, QRNG_EINVAL, "qrng_postprocess: NULL pointer");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+  const uint64_t bytes = count * (bits <= 8 ? 1 : 2);
+  const uint64_t nb = n >= 2 ? bytes * 8 / n : 0;
+  uint64_t m = 0;
+  int st = pipeline_size(ctx, "qrng_postprocess", samples, count, bits, eps, eps_lhl, n, seed_capacity_bits, form,
+                         algo, nb, s, &m, rep);
+  if (m_out) *m_out = m;
+  if (num_blocks_out) *num_blocks_out = nb;
+  if (st) return st;
+  if (out_capacity_bytes < ceil_div(nb * m, 8)) {
+    ctx->kara.xk_ready = false;
+    return fail(ctx, QRNG_EINVAL, "qrng_postprocess: output buffer too small");
+  }
+  st = extract_dispatch(ctx, static_cast<const uint8_t*>(samples), n, m, seed, form, algo, nb, out, s);
+  ctx->kara.xk_ready = false;
+  return st;
+}
+
 int qrng_postprocess_host(qrng_ctx* ctx, const void* samples_host, uint64_t count, int bits, double eps,
                           double eps_lhl, uint64_t n, const uint8_t* seed_host, uint64_t seed_capacity_bits,
                           int form, int algo, uint8_t* out_host, uint64_t out_capacity_bytes, uint64_t* m_out,
                           uint64_t* num_blocks_out, qrng_hmin_report* rep, qrng_stream_t stream) {
   if (!ctx) return QRNG_EINVAL;
   if (!samples_host || !seed_host || !out_host) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: NULL pointer");
-  if (form != QRNG_FORM_STANDARD && form != QRNG_FORM_MODIFIED)
-    return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: unknown form");
-  if (n < 2 || n > kMaxBlockBits) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: n must be in [2, 2^26]");
   qrng_hmin_report local{};
   int st = check_minentropy_args(ctx, samples_host, count, bits, eps, &local);
   if (st) return st;
-  if (!(eps_lhl > 0.0 && eps_lhl <= 1.0)) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: eps_lhl in (0, 1]");
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
 
   const uint64_t bytes = count * (bits <= 8 ? 1 : 2);
   QRNG_CUDA(ctx, ctx->samples_dev.ensure(bytes), "sample workspace");
   QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->samples_dev.p, samples_host, bytes, cudaMemcpyHostToDevice, s), "sample upload");
-  st = minentropy_dev(ctx, ctx->samples_dev.p, count, bits, eps, &local, s);
-  if (st) return st;
-  if (rep) *rep = local;
-
-  uint64_t m = qrng_output_length(n, local.h_modify, bits, eps_lhl);
-  if (form == QRNG_FORM_MODIFIED && m >= n) m = n - 1;
-  if (m > n) m = n;
-  const uint64_t num_blocks = bytes * 8 / n;
-  if (m_out) *m_out = m;
-  if (num_blocks_out) *num_blocks_out = num_blocks;
-  if (m == 0) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: the corrected min-entropy gives m = 0");
-  if (num_blocks == 0) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: fewer than n raw bits");
-  const uint64_t L = qrng_seed_bits(n, m, form);
-  if (seed_capacity_bits < L) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: seed shorter than the hash needs");
-  const uint64_t out_bytes = ceil_div(num_blocks * m, 8);
-  if (out_capacity_bytes < out_bytes) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: output buffer too small");
-
-  QRNG_CUDA(ctx, ctx->seed_dev.ensure(ceil_div(L, 8)), "seed workspace");
-  QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->seed_dev.p, seed_host, ceil_div(L, 8), cudaMemcpyHostToDevice, s), "seed upload");
-  QRNG_CUDA(ctx, ctx->out_dev.ensure(out_bytes), "output workspace");
+  const uint64_t num_blocks = n >= 2 ? bytes * 8 / n : 0;
   // Two parts when the split keeps both raw and output chunks aligned (n a multiple of 128 bits, the
   // first part a multiple of 32 blocks): the first 7/8 of the blocks' output travels to the host on the
   // copy stream while the last 1/8 is hashed, so only 1/8 of the download is left after the last kernel.
   const uint64_t first = ((num_blocks * 7) / 8) & ~31ull;
   const bool split = (n % 128 == 0) && num_blocks >= 64 && first >= 32 && first < num_blocks;
   const uint64_t b0 = split ? first : num_blocks;
+  uint64_t m = 0;
+  st = pipeline_size(ctx, "qrng_postprocess_host", ctx->samples_dev.p, count, bits, eps, eps_lhl, n,
+                     seed_capacity_bits, form, algo, b0, s, &m, rep);
+  if (m_out) *m_out = m;
+  if (num_blocks_out) *num_blocks_out = num_blocks;
+  if (st) return st;
+  const uint64_t out_bytes = ceil_div(num_blocks * m, 8);
+  if (out_capacity_bytes < out_bytes) {
+    ctx->kara.xk_ready = false;
+    return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host: output buffer too small");
+  }
+  const uint64_t L = qrng_seed_bits(n, m, form);
+  QRNG_CUDA(ctx, ctx->seed_dev.ensure(ceil_div(L, 8)), "seed workspace");
+  QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->seed_dev.p, seed_host, ceil_div(L, 8), cudaMemcpyHostToDevice, s), "seed upload");
+  QRNG_CUDA(ctx, ctx->out_dev.ensure(out_bytes), "output workspace");
   uint8_t* out_d = ctx->out_dev.as<uint8_t>();
   st = extract_dispatch(ctx, ctx->samples_dev.as<uint8_t>(), n, m, ctx->seed_dev.as<uint8_t>(), form, algo, b0, out_d,
                         s);
+  ctx->kara.xk_ready = false;
   if (st) return st;
   if (split) {
     const uint64_t bytes0 = b0 * m / 8;  // b0 m is a multiple of 32 bits
@@ -1319,6 +1445,7 @@ int qrng_get_stats(qrng_ctx* ctx, qrng_stats* out) {
   ctx->stats.worst_fft32_round_err = w32;
   ctx->stats.fft32_recomputed = repairs;
   ctx->stats.last_fft32_segment = ctx->last_fft32_log_s ? (1ull << ctx->last_fft32_log_s) : 0;
+  ctx->stats.kara_presplits_used = ctx->kara.presplits_used;
   *out = ctx->stats;
   return QRNG_OK;
 }
@@ -1328,6 +1455,7 @@ int qrng_reset_stats(qrng_ctx* ctx) {
   for (size_t i = 0; i < ctx->ev_used; ++i) cudaEventSynchronize(ctx->ev_end[i]);
   ctx->ev_used = 0;
   ctx->stats = qrng_stats{};
+  ctx->kara.presplits_used = 0;
   QRNG_CUDA(ctx, cudaMemset(ctx->fft_worst.p, 0, 2 * sizeof(unsigned long long)), "FFT error reset");
   QRNG_CUDA(ctx, cudaMemset(ctx->fft32_guard.p, 0, 16), "repair count reset");
   return QRNG_OK;

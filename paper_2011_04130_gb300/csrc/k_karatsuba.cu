@@ -413,6 +413,34 @@ void launch_combine_pack(uint64_t nb, size_t smem, cudaStream_t s, const PairKar
       k.qpar, mwq, log2h, cw, stream, b0, d.num_blocks, d.mw, d.m, d.modified, d.id_off, dc.raw, d.raw_stride);
 }
 
+KaraSplitKey split_key(const DirectArgs& dc, const DirectArgs& d, uint64_t nb, uint64_t xk_words, uint32_t hw,
+                       uint32_t kblocks, uint32_t levels) {
+  KaraSplitKey k;
+  k.raw = dc.raw;
+  k.raw_stride = d.raw_stride;
+  k.blocks = nb;
+  k.xk_words = xk_words;
+  k.nw_t = d.nw_t;
+  k.tail_mask = d.tail_mask;
+  k.hw = hw;
+  k.kblocks = kblocks;
+  k.levels = levels;
+  return k;
+}
+
+cudaError_t launch_split_levels(uint32_t levels, const DirectArgs& dc, const DirectArgs& d, uint64_t nb, uint32_t hw,
+                                uint32_t kblocks, uint64_t xk_words, KaraWorkspace& ws, int num_sms,
+                                cudaStream_t s) {
+  const unsigned gs = grid_for(nb * kblocks * hw, num_sms);
+  switch (levels) {
+    case 1: launch_split<1>(gs, s, dc, d, nb, hw, kblocks, xk_words, ws); break;
+    case 2: launch_split<2>(gs, s, dc, d, nb, hw, kblocks, xk_words, ws); break;
+    case 3: launch_split<3>(gs, s, dc, d, nb, hw, kblocks, xk_words, ws); break;
+    default: launch_split<4>(gs, s, dc, d, nb, hw, kblocks, xk_words, ws); break;
+  }
+  return cudaGetLastError();
+}
+
 template <int L>
 cudaError_t launch_combine_pack_bulk(unsigned grid, size_t smem, cudaStream_t s, const PairKara& k, uint32_t mwq,
                                      uint32_t log2h, uint32_t* stream, uint64_t nb, uint64_t b0, const DirectArgs& d,
@@ -538,15 +566,15 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
     dc.raw = d.raw + b0 * d.raw_stride;
     dc.out = d.out + b0 * d.out_stride;
     dc.num_blocks = nb;
-    const unsigned gs = grid_for(nb * kblocks * hw, num_sms);
-    switch (p.levels) {
-      case 1: launch_split<1>(gs, s, dc, d, nb, hw, kblocks, xk_words, ws); break;
-      case 2: launch_split<2>(gs, s, dc, d, nb, hw, kblocks, xk_words, ws); break;
-      case 3: launch_split<3>(gs, s, dc, d, nb, hw, kblocks, xk_words, ws); break;
-      default: launch_split<4>(gs, s, dc, d, nb, hw, kblocks, xk_words, ws); break;
+    const KaraSplitKey key = split_key(dc, d, nb, xk_words, hw, kblocks, p.levels);
+    const bool presplit = b0 == 0 && ws.xk_ready && ws.xk_key == key;
+    ws.xk_ready = false;
+    if (presplit) ++ws.presplits_used;
+    if (!presplit) {
+      if ((e = launch_split_levels(p.levels, dc, d, nb, hw, kblocks, xk_words, ws, num_sms, s)) != cudaSuccess)
+        return e;
+      ++*kernels;
     }
-    ++*kernels;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
     hook.on_begin(s);
     e = launch_gemm_pair_kara(dc, k, err, fault, num_sms, s, kernels);
     hook.on_end(s);
@@ -594,6 +622,23 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
     ++*kernels;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
+  return cudaSuccess;
+}
+
+cudaError_t launch_kara_presplit(const DirectArgs& d, const KaraPlan& p, KaraWorkspace& ws, int num_sms,
+                                 cudaStream_t s, uint32_t* kernels) {
+  ws.xk_ready = false;
+  if (p.levels < 1 || p.levels > kMaxLevels) return cudaErrorInvalidValue;
+  const uint32_t hw = (uint32_t)(p.h / 32);
+  const uint64_t xk_words = p.kq / 32;
+  const uint64_t chunk = p.chunk_blocks < d.num_blocks ? p.chunk_blocks : d.num_blocks;
+  cudaError_t e = ws.xk.ensure((size_t)p.groups * chunk * xk_words * 4);
+  if (e != cudaSuccess) return e;
+  const uint32_t kblocks = (uint32_t)(p.kq / p.h);
+  if ((e = launch_split_levels(p.levels, d, d, chunk, hw, kblocks, xk_words, ws, num_sms, s)) != cudaSuccess) return e;
+  ++*kernels;
+  ws.xk_key = split_key(d, d, chunk, xk_words, hw, kblocks, p.levels);
+  ws.xk_ready = true;
   return cudaSuccess;
 }
 

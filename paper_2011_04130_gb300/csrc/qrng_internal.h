@@ -259,12 +259,27 @@ struct KaraPlan {
 // derived operands and sub-product parities of one pass. The plan is empty when nothing fits.
 KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_sms, int forced_levels,
                         uint64_t forced_h, uint64_t max_workspace);
+// The arguments of the first pass's derived-operand kernel: a launch whose first pass matches the
+// key of a split already enqueued (launch_kara_presplit) skips that split.
+struct KaraSplitKey {
+  const uint32_t* raw = nullptr;
+  uint64_t raw_stride = 0, blocks = 0, xk_words = 0;
+  uint32_t nw_t = 0, tail_mask = 0, hw = 0, kblocks = 0, levels = 0;
+  bool operator==(const KaraSplitKey& o) const {
+    return raw == o.raw && raw_stride == o.raw_stride && blocks == o.blocks && xk_words == o.xk_words &&
+           nw_t == o.nw_t && tail_mask == o.tail_mask && hw == o.hw && kblocks == o.kblocks && levels == o.levels;
+  }
+};
 struct KaraWorkspace {
   DevBuf seeds, xk, qpar;
+  bool xk_ready = false;  // xk holds the derived operands of xk_key (consumed by the next launch)
+  KaraSplitKey xk_key;
+  uint64_t presplits_used = 0;
   void release() {
     seeds.release();
     xk.release();
     qpar.release();
+    xk_ready = false;
   }
 };
 // The pair kernel on the sub-products: derived seeds (seed_stride words each, front padding
@@ -291,6 +306,12 @@ constexpr uint64_t kKaraPackMaxBits = 1ull << 18;  // 32 KB of output words per 
 cudaError_t launch_gemm_karatsuba(const DirectArgs& a, const KaraPlan& plan, KaraWorkspace& ws, int* err, int fault,
                                   int num_sms, cudaStream_t s, uint32_t* kernels, const TimingHook& hook = TimingHook(),
                                   uint8_t* packed_out = nullptr);
+// Enqueues on `s` the derived operands of the first pass of launch_gemm_karatsuba(a, plan, ...)
+// (a needs n_t, raw, raw_stride, nw_t, tail_mask and num_blocks only) and marks them ready: the
+// next launch whose first pass has the same split arguments skips its split. The caller orders `s`
+// before that launch and clears ws.xk_ready when the operands may go stale.
+cudaError_t launch_kara_presplit(const DirectArgs& a, const KaraPlan& plan, KaraWorkspace& ws, int num_sms,
+                                 cudaStream_t s, uint32_t* kernels);
 
 }  // namespace qrng
 
@@ -310,8 +331,22 @@ struct qrng_ctx {
   qrng::DevBuf batch_meta, batch_raw, batch_rev, batch_out, batch_counter;
   uint64_t batch_generation = 0;  // bumped whenever a batch buffer moves (invalidates cached graphs)
   cudaStream_t capture_stream = nullptr;
-  cudaStream_t copy_stream = nullptr;      // host pipeline: output download beside the extraction
+  cudaStream_t copy_stream = nullptr;      // host pipeline: output download beside the extraction;
+                                           // pipelines: derived operands beside the estimate
   cudaEvent_t copy_ready = nullptr, copy_done = nullptr;
+  cudaEvent_t pre_ready = nullptr, pre_done = nullptr;
+  // the last pipeline call's stream shape and output length (predicts the next call's m)
+  struct PipelineShape {
+    uint64_t n, count;
+    int bits, form;
+    uint64_t blocks;
+    bool operator==(const PipelineShape& o) const {
+      return n == o.n && count == o.count && bits == o.bits && form == o.form && blocks == o.blocks;
+    }
+  };
+  bool pipeline_seen = false;
+  PipelineShape pipeline_shape{};
+  uint64_t pipeline_m = 0;
   struct BatchGraph {
     uint64_t key = 0, generation = 0, stamp = 0;
     cudaGraph_t graph = nullptr;

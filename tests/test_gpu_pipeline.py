@@ -1,0 +1,149 @@
+"""GPU parity of the whole pipeline on device buffers (qrng_postprocess: Sec. II estimate, Sec. III.B
+sizing, Sec. III.B-E hashing of the sample stream's blocks) against the oracle, including the
+block-Karatsuba route's derived operands computed beside the estimate from the previous call's m:
+a hit (same m), a miss (the modified form with a different m, whose operands depend on n - m), new
+sample contents at the same address, a rejected call in between, and the host-buffer pipeline that
+shares the same first half."""
+import numpy as np
+import pytest
+
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+STD, MOD = 0, 1
+
+
+def _run(q, ctx, samples_dev, count, n, seed_dev, seed_bits, form, algo, out, eps_lhl=1.0):
+    m, nb, rep = q.qrng_postprocess(ctx, samples_dev, count, 8, 1e-6, eps_lhl, n, seed_dev, seed_bits, form, algo,
+                                    out, out.numel())
+    q.qrng_synchronize(ctx)
+    return m, nb, rep
+
+
+def _check(oracle_mod, q, samples, n, seed, form, m, nb, rep, out, full=True):
+    ref = oracle_mod.minentropy(samples, 8, 1e-6)
+    assert abs(rep["h_modify"] - ref["h_modify"]) < 1e-12
+    want_m = oracle_mod.output_length(n, ref["h_modify"], 8, 1.0)
+    if form == MOD:
+        want_m = min(want_m, n - 1)
+    assert m == want_m and nb == samples.size * 8 // n
+    raw = samples.view(np.uint8)
+    got = out[:(nb * m + 7) // 8].cpu().numpy()
+    if full:
+        assert np.array_equal(got, oracle_mod.toeplitz_blocks(raw, n, m, seed, form, nb))
+    else:
+        assert not oracle_mod.freivalds(raw, n, m, seed, form, nb, got).any()
+
+
+def _stats(q, ctx):
+    s = q.qrng_get_stats(ctx)
+    return s["kara_presplits"], s["kara_presplits_used"]
+
+
+@pytest.mark.parametrize("algo_name", ["GEMM_KARATSUBA", "AUTO"])
+def test_pipeline_presplit_hit_and_new_contents(qlib, gpu, oracle_mod, algo_name):
+    """Three calls on one stream shape: the first plans alone, the second and third find their
+    derived operands computed beside the estimate; the third call's samples are new contents at the
+    same address (the operands are recomputed from them, not reused)."""
+    import torch
+
+    algo = getattr(qlib, "QRNG_ALGO_" + algo_name)
+    n = 1 << 16
+    count = 1 << 22  # 512 blocks of the laser-stream block length
+    seed = W.random_bits(2 * n - 1, 611)
+    seed_dev = torch.from_numpy(seed).cuda()
+    out = torch.zeros(count, dtype=torch.uint8, device="cuda")
+    samples_dev = torch.empty(count, dtype=torch.uint8, device="cuda")
+    qlib.qrng_reset_stats(gpu)
+    for call, sseed in enumerate((612, 612, 613)):
+        samples = W.adc_samples(count, sseed)
+        samples_dev.copy_(torch.from_numpy(samples))
+        m, nb, rep = _run(qlib, gpu, samples_dev, count, n, seed_dev, 2 * n - 1, STD, algo, out)
+        _check(oracle_mod, qlib, samples, n, seed, STD, m, nb, rep, out, full=False)
+    pre, used = _stats(qlib, gpu)
+    if algo_name == "GEMM_KARATSUBA":
+        assert pre == 2 and used == 2, (pre, used)
+    else:  # AUTO takes the route its tuner picked; the pre-split only follows a Karatsuba choice
+        assert used == pre
+
+
+def test_pipeline_presplit_miss_modified_form(qlib, gpu, oracle_mod):
+    """Modified form: the derived operands depend on n - m, so a call whose m differs from the
+    previous one computes them again (and still matches the oracle)."""
+    import torch
+
+    n = 8192
+    count = 1 << 20
+    seed = W.random_bits(n - 1, 621)
+    seed_dev = torch.from_numpy(seed).cuda()
+    out = torch.zeros(count, dtype=torch.uint8, device="cuda")
+    samples_dev = torch.empty(count, dtype=torch.uint8, device="cuda")
+    qlib.qrng_reset_stats(gpu)
+    ms = []
+    for sseed, sigma in ((622, 16.0), (623, 11.0), (623, 11.0)):
+        samples = W.adc_samples(count, sseed, sigma=sigma)
+        samples_dev.copy_(torch.from_numpy(samples))
+        m, nb, rep = _run(qlib, gpu, samples_dev, count, n, seed_dev, n - 1, MOD, qlib.QRNG_ALGO_GEMM_KARATSUBA, out)
+        _check(oracle_mod, qlib, samples, n, seed, MOD, m, nb, rep, out, full=False)
+        ms.append(m)
+    assert ms[0] != ms[1] and ms[1] == ms[2]
+    pre, used = _stats(qlib, gpu)
+    assert pre == 2 and used == 1, (pre, used)  # the second call's guess was the first call's m
+
+
+def test_pipeline_rejected_call_leaves_nothing_behind(qlib, gpu, oracle_mod):
+    """An output buffer too small is refused after the estimate; the next call is still exact."""
+    import torch
+
+    n = 4096
+    count = 1 << 18
+    samples = W.adc_samples(count, 631)
+    samples_dev = torch.from_numpy(samples).cuda()
+    seed = W.random_bits(2 * n - 1, 632)
+    seed_dev = torch.from_numpy(seed).cuda()
+    out = torch.zeros(count, dtype=torch.uint8, device="cuda")
+    _run(qlib, gpu, samples_dev, count, n, seed_dev, 2 * n - 1, STD, qlib.QRNG_ALGO_GEMM_KARATSUBA, out)
+    small = torch.zeros(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(qlib.QrngError) as e:
+        qlib.qrng_postprocess(gpu, samples_dev, count, 8, 1e-6, 1.0, n, seed_dev, 2 * n - 1, STD,
+                              qlib.QRNG_ALGO_GEMM_KARATSUBA, small, small.numel())
+    assert e.value.status == qlib.QRNG_EINVAL
+    m, nb, rep = _run(qlib, gpu, samples_dev, count, n, seed_dev, 2 * n - 1, STD, qlib.QRNG_ALGO_GEMM_KARATSUBA, out)
+    _check(oracle_mod, qlib, samples, n, seed, STD, m, nb, rep, out)
+
+
+@pytest.mark.parametrize("algo_name", ["DIRECT", "NTT", "GEMM_FP4_PAIR", "AUTO"])
+def test_pipeline_other_routes_match_oracle(qlib, gpu, oracle_mod, algo_name):
+    """Every route through the device pipeline, small shapes compared bit for bit."""
+    import torch
+
+    algo = getattr(qlib, "QRNG_ALGO_" + algo_name)
+    n = 2048
+    count = 200_000
+    samples = W.adc_samples(count, 641)
+    seed = W.random_bits(2 * n - 1, 642)
+    samples_dev = torch.from_numpy(samples).cuda()
+    seed_dev = torch.from_numpy(seed).cuda()
+    out = torch.zeros(count, dtype=torch.uint8, device="cuda")
+    for _ in range(2):
+        m, nb, rep = _run(qlib, gpu, samples_dev, count, n, seed_dev, 2 * n - 1, STD, algo, out)
+        _check(oracle_mod, qlib, samples, n, seed, STD, m, nb, rep, out)
+
+
+def test_host_pipeline_presplit(qlib, gpu, oracle_mod):
+    """The host-buffer pipeline runs the same first half: its second call on a shape finds the
+    derived operands of its first (7/8) part computed beside the estimate."""
+    n = 1 << 16
+    count = 1 << 22
+    samples = W.adc_samples(count, 651)
+    seed = W.random_bits(2 * n - 1, 652)
+    out = np.zeros(count, dtype=np.uint8)
+    qlib.qrng_reset_stats(gpu)
+    for _ in range(2):
+        m, nb, rep = qlib.qrng_postprocess_host(gpu, samples, count, 8, 1e-6, 1.0, n, seed, 2 * n - 1, STD,
+                                               qlib.QRNG_ALGO_GEMM_KARATSUBA, out, out.size)
+        raw = samples.view(np.uint8)
+        assert not oracle_mod.freivalds(raw, n, m, seed, STD, nb, out[:(nb * m + 7) // 8]).any()
+    pre, used = _stats(qlib, gpu)
+    assert pre == 1 and used == 1, (pre, used)

@@ -122,6 +122,7 @@ struct PairArgs {
   uint64_t out_stride;
   uint64_t num_blocks;
   uint32_t mpairs;   // pairs of output tiles
+  uint32_t mtiles;   // output tiles holding needed rows: a pair's second tile at or past it gets no MMAs
   uint32_t ntiles;
   uint32_t ksteps;   // K steps per K block (plain product: all of them, one K block)
   int* err;
@@ -375,6 +376,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       for (uint64_t tile = first_tile; tile < ntile_total && !abort_flag; tile += tile_stride) {
         // both epilogues must have drained the previous tile's accumulators
         if (tile != first_tile && !mbar_wait<true>(&accum_empty_bar, acc_phase ^ 1u, &abort_flag, a.err, 5)) break;
+        // a pair whose second output tile holds no needed row (an odd number of row tiles) issues
+        // the first tile's MMAs only
+        const bool d1_live = 2u * ((uint32_t)tile % a.mpairs) + 1u < a.mtiles;  // tile < 2^32
         bool done = true;
         uint32_t c = 0, el = 0;  // K block and step within it (0: the build-only step)
         for (uint32_t e = 0; e < nsteps; ++e) {
@@ -387,11 +391,17 @@ __global__ void __launch_bounds__(THREADS, 1)
               const uint64_t dA = kDescSw128Hi | (uint64_t)((sA & 0x3FFFFu) >> 4);
               const uint64_t dB = kDescSw128Hi | (uint64_t)(((sA + A_BYTES) & 0x3FFFFu) >> 4);  // X(ks)
               const uint64_t dP = kDescSw128Hi | (uint64_t)(((smem_base + prev * STAGE_BYTES) & 0x3FFFFu) >> 4);
+              if (d1_live) {
 #pragma unroll
-              for (int k = 0; k < ROW_BYTES / 32; ++k) {  // 32 bytes = 2 descriptor units per K chunk
-                const uint32_t acc = (E > 1 || k > 0) ? 1u : 0u;
-                mma_pair(tmem_base, tmem_base, dA + 2 * k, dB + 2 * k, S::IDESC, acc);
-                mma_pair(tmem_base + D1_COL, tmem_base, dP + 2 * k, dB + 2 * k, S::IDESC, acc);  // T(mt+1, ks)
+                for (int k = 0; k < ROW_BYTES / 32; ++k) {  // 32 bytes = 2 descriptor units per K chunk
+                  const uint32_t acc = (E > 1 || k > 0) ? 1u : 0u;
+                  mma_pair(tmem_base, tmem_base, dA + 2 * k, dB + 2 * k, S::IDESC, acc);
+                  mma_pair(tmem_base + D1_COL, tmem_base, dP + 2 * k, dB + 2 * k, S::IDESC, acc);  // T(mt+1, ks)
+                }
+              } else {
+#pragma unroll
+                for (int k = 0; k < ROW_BYTES / 32; ++k)
+                  mma_pair(tmem_base, tmem_base, dA + 2 * k, dB + 2 * k, S::IDESC, (E > 1 || k > 0) ? 1u : 0u);
               }
             }
             commit_both(&empty_bar[prev]);  // the previous stage's T tile is not read again
@@ -443,6 +453,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t nt = tc.nt;
       if (!mbar_wait(&accum_full_bar, acc_phase, &abort_flag, a.err, 8)) break;
       tc_fence_after();
+      if (hs == 1 && tc.mt + 1 >= a.mtiles) {  // this pair's second tile got no MMAs: nothing to drain
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive_cluster_relaxed(accum_empty_leader);
+        __syncwarp();
+        acc_phase ^= 1u;
+        continue;
+      }
       const uint32_t ow = (tc.mt + hs) * (PM / 32) + rank * (HM / 32) + q;  // output word of every block
       const uint32_t rem = (ow < a.mw) ? a.m - 32 * ow : 0u;
       const uint32_t omask = rem >= 32 ? 0xffffffffu : ((1u << rem) - 1u);
@@ -580,6 +598,7 @@ static cudaError_t launch_pair(const PairArgs& a0, const CUtensorMap& map, int n
     if (e != cudaSuccess) return e;
   }
   const uint64_t tiles = (uint64_t)a.mpairs * a.ntiles * (kKara ? a.groups : 1u);
+  if (tiles >= (1ull << 32)) return cudaErrorInvalidValue;  // the issuer takes tile indices as 32-bit
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
@@ -648,7 +667,8 @@ cudaError_t launch_gemm_pair(const DirectArgs& d, int* err, int fault, int num_s
                              uint32_t* kernels) {
   if ((reinterpret_cast<uintptr_t>(d.raw) & 15) != 0 || (d.raw_stride % 4) != 0) return cudaErrorInvalidValue;
   PairArgs a = pair_args_from(d, err, fault);
-  a.mpairs = (uint32_t)ceil_div(ceil_div(d.m, PM), 2);
+  a.mtiles = (uint32_t)ceil_div(d.m, PM);
+  a.mpairs = (uint32_t)ceil_div(a.mtiles, 2);
   a.ksteps = (uint32_t)ceil_div((uint64_t)d.nw_t * 32, BK);
   CUtensorMap map;
   const bool narrow = pair_prefers_192(a.mpairs, d.num_blocks, num_sms);
@@ -668,6 +688,7 @@ cudaError_t launch_gemm_pair_kara(const DirectArgs& d, const PairKara& k, int* e
   a.seed_rev = k.seeds;
   a.seed_front = k.seed_front;
   a.mpairs = (uint32_t)(k.mq / (2 * PM));
+  a.mtiles = (uint32_t)ceil_div(k.mq_live, PM);
   if (k.h == BK) {
     // every tile row block and every K step is a whole h-block: block (R+1, c) = block (R, c-1), so
     // the two output tiles share T tiles along the block diagonal like the plain product, one K

@@ -501,10 +501,14 @@ KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_s
       // block (about half a step; one per tile when h = 256) and its accumulator hand-back (about
       // 2.8 steps); the passes around it (derived operands written and read, parities written and
       // read once, the raw bits and the output) move their bytes at ~6 TB/s, part of them in L2
+      // a pair whose second output tile holds no needed row issues half the MMAs (about 0.6 of a
+      // full pair's time, its fixed per-tile part included)
       const uint64_t passes = ceil_div(num_blocks, chunk);
+      const uint64_t live_tiles = ceil_div(ceil_div(m, span) * h, 256);
+      const double pair_share = ((double)(live_tiles / 2) + 0.6 * (double)(live_tiles % 2)) / (double)(mq / 512);
       const double tiles = (double)G * (double)(mq / 512) * std::ceil((double)chunk / 224.0);
       const double steps = (double)(kq / 256) + 0.5 * (double)(h == 256 ? 1 : kq / h) + 2.8;
-      const double kernel_s = (double)passes * std::ceil(tiles / clusters) * steps * 0.477e-6;
+      const double kernel_s = (double)passes * std::ceil(tiles * pair_share / clusters) * steps * 0.477e-6;
       const double bytes =
           (double)num_blocks * ((double)n_t / 8 + 2.0 * G * (double)kq / 8 + 2.0 * G * (double)mq / 8 + (double)m / 8);
       const double t = kernel_s + bytes / 6e12 + (double)passes * 2e-5;
@@ -557,6 +561,7 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
   k.h = p.h;
   k.span = p.span;
   k.mq = p.mq;
+  k.mq_live = ceil_div(d.m, p.span) * p.h;
   k.kq = p.kq;
   k.groups = G;
   const uint32_t kblocks = (uint32_t)(p.kq / p.h);

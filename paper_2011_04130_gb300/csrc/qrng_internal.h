@@ -294,6 +294,7 @@ struct PairKara {
   uint64_t xk_words;
   uint32_t* qpar;
   uint64_t h, span, mq, kq;
+  uint64_t mq_live;  // sub-product rows that feed an output row below m: ceil(m / span) h
   uint32_t groups;
 };
 cudaError_t launch_gemm_pair_kara(const DirectArgs& a, const PairKara& k, int* err, int fault, int num_sms,

@@ -285,23 +285,34 @@ def run_ours(args, world, rank, local):
     if not args.no_e2e:
         pin_samples = torch.from_numpy(samples_h).pin_memory()
         pin_seed = torch.from_numpy(seed_h).pin_memory()
-        pin_out = torch.empty(num_blocks * n // 8, dtype=torch.uint8).pin_memory()
-        e_ms = []
-        for i in range(args.warmup + args.steps):
-            flush.fill_(i & 0xFF)
-            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            m2, nb2, _ = q.qrng_postprocess_host(ctx, pin_samples, samples_h.size, bits, eps, 1.0, n, pin_seed,
-                                                 2 * n - 1, q.QRNG_FORM_STANDARD, algo, pin_out, pin_out.numel(),
-                                                 stream=stream)
-            b.record(stream)
-            b.synchronize()
-            if i >= args.warmup:
-                e_ms.append(a.elapsed_time(b))
-        et = reduce_max(sum(e_ms), world, dev)
-        e2e = {"value": job_throughput(world, nb2 * m2, len(e_ms), et), "unit": UNIT,
-               "h2d_bytes_per_step": int(samples_h.nbytes + (q.qrng_seed_bits(n, m2, 0) + 7) // 8),
-               "d2h_bytes_per_step": int((nb2 * m2 + 7) // 8 + 112), "ms_per_step": et / len(e_ms)}
+        pin_out = [torch.empty(num_blocks * n // 8, dtype=torch.uint8).pin_memory() for _ in range(2)]
+
+        # the overlapped host pipeline: every step uploads its samples and seed from pinned host
+        # memory and downloads its output; a step's copies run beside its neighbours' hashing
+        def e2e_steps(count):
+            res = None
+            for i in range(count):
+                res = q.qrng_postprocess_host_async(ctx, pin_samples, samples_h.size, bits, eps, 1.0, n, pin_seed,
+                                                    2 * n - 1, q.QRNG_FORM_STANDARD, algo, pin_out[i & 1],
+                                                    pin_out[i & 1].numel(), stream=stream)
+            q.qrng_postprocess_host_wait(ctx, stream=stream)
+            return res
+
+        e2e_steps(args.warmup)
+        torch.cuda.synchronize()
+        if world > 1:
+            torch.distributed.barrier()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        m2, nb2, _ = e2e_steps(args.steps)
+        b.record(stream)
+        b.synchronize()
+        et = reduce_max(a.elapsed_time(b), world, dev)
+        e2e = {"value": job_throughput(world, nb2 * m2, args.steps, et), "unit": UNIT,
+               "h2d_bytes_per_step": int(samples_h.nbytes + pin_seed.numel()),
+               "d2h_bytes_per_step": int((nb2 * m2 + 7) // 8 + 112), "ms_per_step": et / args.steps,
+               "api": "qrng_postprocess_host_async per step, qrng_postprocess_host_wait after the last (consecutive "
+                      "steps overlap: one step's copies beside its neighbours' hashing)"}
 
     result = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

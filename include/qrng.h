@@ -322,6 +322,27 @@ QRNG_API int qrng_postprocess_host(qrng_ctx* ctx, const void* samples_host, uint
                           int form, int algo, uint8_t* out_host, uint64_t out_capacity_bytes, uint64_t* m_out,
                           uint64_t* num_blocks_out, qrng_hmin_report* rep, qrng_stream_t stream);
 
+/*
+ * qrng_postprocess_host_async / qrng_postprocess_host_wait -- the host-buffer pipeline for a stream
+ * of calls that overlap: each call uploads its samples and seed, estimates H_modify, sizes m and
+ * hashes exactly as qrng_postprocess_host does (the whole seed_capacity_bits bits of seed_host are
+ * uploaded), but returns as soon as its hash and the download of its output are enqueued. The
+ * next call's upload then runs on a copy engine while this call hashes, and this call's download
+ * while the next one hashes. Two calls' device buffers are kept (they alternate), so every call
+ * returns once the call before it has finished hashing (its estimate waits for that on `stream`).
+ * The caller keeps samples_host and out_host of a call untouched until a later
+ * qrng_postprocess_host_wait has returned; pinned host memory is needed for the copies to
+ * overlap. m_out, num_blocks_out and rep are written before the call returns.
+ * qrng_postprocess_host_wait waits for every call submitted so far (and reports device-side
+ * failures as qrng_synchronize does).
+ */
+QRNG_API int qrng_postprocess_host_async(qrng_ctx* ctx, const void* samples_host, uint64_t count, int bits,
+                                         double eps, double eps_lhl, uint64_t n, const uint8_t* seed_host,
+                                         uint64_t seed_capacity_bits, int form, int algo, uint8_t* out_host,
+                                         uint64_t out_capacity_bytes, uint64_t* m_out, uint64_t* num_blocks_out,
+                                         qrng_hmin_report* rep, qrng_stream_t stream);
+QRNG_API int qrng_postprocess_host_wait(qrng_ctx* ctx, qrng_stream_t stream);
+
 /* ----------------------------------------------------------------------------------------------
  * Statistics
  * --------------------------------------------------------------------------------------------*/

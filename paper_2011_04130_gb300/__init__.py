@@ -25,6 +25,7 @@ ALGO_NAMES = {QRNG_ALGO_AUTO: "auto", QRNG_ALGO_DIRECT: "direct", QRNG_ALGO_GEMM
 
 EXPORTED = ["qrng_create", "qrng_destroy", "qrng_last_error", "qrng_status_string", "qrng_minentropy",
             "qrng_output_length", "qrng_seed_bits", "qrng_toeplitz_extract", "qrng_postprocess", "qrng_postprocess_host",
+            "qrng_postprocess_host_async", "qrng_postprocess_host_wait",
             "qrng_get_stats", "qrng_reset_stats", "qrng_set_timing", "qrng_synchronize",
             "qrng_minentropy_noalloc", "qrng_extract_batch", "qrng_set_autotune", "qrng_inject_fault",
             "qrng_minentropy_sampled", "qrng_minentropy_quantum", "qrng_set_karatsuba", "qrng_karatsuba_plan",
@@ -143,6 +144,10 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                      ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(HminReport), vp]
     lib.qrng_postprocess_host.argtypes = [vp, vp, u64, i32, dbl, dbl, u64, vp, u64, i32, i32, vp, u64,
                                           ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(HminReport), vp]
+    lib.qrng_postprocess_host_async.argtypes = [vp, vp, u64, i32, dbl, dbl, u64, vp, u64, i32, i32, vp, u64,
+                                                ctypes.POINTER(u64), ctypes.POINTER(u64), ctypes.POINTER(HminReport),
+                                                vp]
+    lib.qrng_postprocess_host_wait.argtypes = [vp, vp]
     lib.qrng_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
     lib.qrng_reset_stats.argtypes = [vp]
     lib.qrng_set_timing.argtypes = [vp, i32]
@@ -284,6 +289,26 @@ def qrng_postprocess(ctx: Context, samples, count: int, bits: int, eps: float, e
                                          ctypes.byref(m), ctypes.byref(nb), ctypes.byref(rep), _stream(stream))
     ctx.check(st, "qrng_postprocess")
     return int(m.value), int(nb.value), rep.as_dict()
+
+
+def qrng_postprocess_host_async(ctx: Context, samples, count: int, bits: int, eps: float, eps_lhl: float, n: int,
+                                seed, seed_capacity_bits: int, form: int, algo: int, out, out_capacity_bytes: int,
+                                stream=None):
+    """Overlapped host pipeline: returns (m, num_blocks, report) once the call's hash and output
+    download are enqueued; `out` is complete after a later qrng_postprocess_host_wait."""
+    m = ctypes.c_uint64()
+    nb = ctypes.c_uint64()
+    rep = HminReport()
+    st = load_library().qrng_postprocess_host_async(ctx.handle, _ptr(samples), count, bits, eps, eps_lhl, n,
+                                                    _ptr(seed), seed_capacity_bits, form, algo, _ptr(out),
+                                                    out_capacity_bytes, ctypes.byref(m), ctypes.byref(nb),
+                                                    ctypes.byref(rep), _stream(stream))
+    ctx.check(st, "qrng_postprocess_host_async")
+    return int(m.value), int(nb.value), rep.as_dict()
+
+
+def qrng_postprocess_host_wait(ctx: Context, stream=None):
+    ctx.check(load_library().qrng_postprocess_host_wait(ctx.handle, _stream(stream)), "qrng_postprocess_host_wait")
 
 
 def qrng_postprocess_host(ctx: Context, samples, count: int, bits: int, eps: float, eps_lhl: float, n: int, seed,

@@ -1206,6 +1206,16 @@ void qrng_destroy(qrng_ctx* ctx) {
   if (ctx->copy_done) cudaEventDestroy(ctx->copy_done);
   if (ctx->pre_ready) cudaEventDestroy(ctx->pre_ready);
   if (ctx->pre_done) cudaEventDestroy(ctx->pre_done);
+  for (auto& sl : ctx->async_slot) {
+    sl.samples.release();
+    sl.seed.release();
+    sl.out.release();
+    if (sl.uploaded) cudaEventDestroy(sl.uploaded);
+    if (sl.computed) cudaEventDestroy(sl.computed);
+    if (sl.downloaded) cudaEventDestroy(sl.downloaded);
+  }
+  if (ctx->up_stream) cudaStreamDestroy(ctx->up_stream);
+  if (ctx->down_stream) cudaStreamDestroy(ctx->down_stream);
   if (ctx->result_host) cudaFreeHost(ctx->result_host);
   for (cudaEvent_t e : ctx->ev_start) cudaEventDestroy(e);
   for (cudaEvent_t e : ctx->ev_end) cudaEventDestroy(e);
@@ -1393,6 +1403,94 @@ int qrng_postprocess_host(qrng_ctx* ctx, const void* samples_host, uint64_t coun
     QRNG_CUDA(ctx, cudaStreamWaitEvent(s, ctx->copy_done, 0), "copy join");
   } else {
     QRNG_CUDA(ctx, cudaMemcpyAsync(out_host, out_d, out_bytes, cudaMemcpyDeviceToHost, s), "output download");
+  }
+  return qrng_synchronize(ctx, stream);
+}
+
+int qrng_postprocess_host_async(qrng_ctx* ctx, const void* samples_host, uint64_t count, int bits, double eps,
+                                double eps_lhl, uint64_t n, const uint8_t* seed_host, uint64_t seed_capacity_bits,
+                                int form, int algo, uint8_t* out_host, uint64_t out_capacity_bytes, uint64_t* m_out,
+                                uint64_t* num_blocks_out, qrng_hmin_report* rep, qrng_stream_t stream) {
+  if (!ctx) return QRNG_EINVAL;
+  if (!samples_host || !seed_host || !out_host)
+    return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host_async: NULL pointer");
+  qrng_hmin_report local{};
+  int st = check_minentropy_args(ctx, samples_host, count, bits, eps, &local);
+  if (st) return st;
+  if (seed_capacity_bits == 0) return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host_async: empty seed");
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (!ctx->up_stream) {
+    QRNG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->up_stream, cudaStreamNonBlocking), "upload stream");
+    QRNG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->down_stream, cudaStreamNonBlocking), "download stream");
+    for (auto& sl : ctx->async_slot) {
+      QRNG_CUDA(ctx, cudaEventCreateWithFlags(&sl.uploaded, cudaEventDisableTiming), "pipeline event");
+      QRNG_CUDA(ctx, cudaEventCreateWithFlags(&sl.computed, cudaEventDisableTiming), "pipeline event");
+      QRNG_CUDA(ctx, cudaEventCreateWithFlags(&sl.downloaded, cudaEventDisableTiming), "pipeline event");
+    }
+  }
+  qrng_ctx::AsyncSlot& sl = ctx->async_slot[ctx->async_calls & 1];
+  const uint64_t bytes = count * (bits <= 8 ? 1 : 2);
+  const uint64_t seed_bytes = ceil_div(seed_capacity_bits, 8);
+  // the slot's earlier call must have finished hashing before its samples and seed are replaced
+  if (sl.used) QRNG_CUDA(ctx, cudaStreamWaitEvent(ctx->up_stream, sl.computed, 0), "pipeline wait");
+  if (sl.used && (sl.samples.cap < bytes || sl.seed.cap < seed_bytes))  // growing frees the old buffer
+    QRNG_CUDA(ctx, cudaEventSynchronize(sl.computed), "pipeline wait");
+  QRNG_CUDA(ctx, sl.samples.ensure(bytes), "pipeline sample workspace");
+  QRNG_CUDA(ctx, sl.seed.ensure(seed_bytes), "pipeline seed workspace");
+  QRNG_CUDA(ctx, cudaMemcpyAsync(sl.samples.p, samples_host, bytes, cudaMemcpyHostToDevice, ctx->up_stream),
+            "sample upload");
+  QRNG_CUDA(ctx, cudaMemcpyAsync(sl.seed.p, seed_host, seed_bytes, cudaMemcpyHostToDevice, ctx->up_stream),
+            "seed upload");
+  QRNG_CUDA(ctx, cudaEventRecord(sl.uploaded, ctx->up_stream), "pipeline event");
+  QRNG_CUDA(ctx, cudaStreamWaitEvent(s, sl.uploaded, 0), "pipeline wait");
+  const uint64_t num_blocks = n >= 2 ? bytes * 8 / n : 0;
+  uint64_t m = 0;
+  st = pipeline_size(ctx, "qrng_postprocess_host_async", sl.samples.p, count, bits, eps, eps_lhl, n,
+                     seed_capacity_bits, form, algo, num_blocks, s, &m, rep);
+  if (m_out) *m_out = m;
+  if (num_blocks_out) *num_blocks_out = num_blocks;
+  if (st) {
+    sl.used = true;  // its upload is in flight: the next use of the slot orders after the compute stream
+    QRNG_CUDA(ctx, cudaEventRecord(sl.computed, s), "pipeline event");
+    ++ctx->async_calls;
+    return st;
+  }
+  const uint64_t out_bytes = ceil_div(num_blocks * m, 8);
+  if (out_capacity_bytes < out_bytes) {
+    ctx->kara.xk_ready = false;
+    sl.used = true;
+    QRNG_CUDA(ctx, cudaEventRecord(sl.computed, s), "pipeline event");
+    ++ctx->async_calls;
+    return fail(ctx, QRNG_EINVAL, "qrng_postprocess_host_async: output buffer too small");
+  }
+  if (sl.used && sl.out.cap < out_bytes) {
+    // growing the buffer frees the old one: its download must be over first
+    QRNG_CUDA(ctx, cudaEventSynchronize(sl.downloaded), "pipeline wait");
+  }
+  QRNG_CUDA(ctx, sl.out.ensure(out_bytes), "pipeline output workspace");
+  // the slot's earlier call must have finished downloading before its output is overwritten
+  if (sl.used) QRNG_CUDA(ctx, cudaStreamWaitEvent(s, sl.downloaded, 0), "pipeline wait");
+  st = extract_dispatch(ctx, sl.samples.as<uint8_t>(), n, m, sl.seed.as<uint8_t>(), form, algo, num_blocks,
+                        sl.out.as<uint8_t>(), s);
+  ctx->kara.xk_ready = false;
+  QRNG_CUDA(ctx, cudaEventRecord(sl.computed, s), "pipeline event");
+  sl.used = true;
+  ++ctx->async_calls;
+  if (st) return st;
+  QRNG_CUDA(ctx, cudaStreamWaitEvent(ctx->down_stream, sl.computed, 0), "pipeline wait");
+  QRNG_CUDA(ctx, cudaMemcpyAsync(out_host, sl.out.p, out_bytes, cudaMemcpyDeviceToHost, ctx->down_stream),
+            "output download");
+  QRNG_CUDA(ctx, cudaEventRecord(sl.downloaded, ctx->down_stream), "pipeline event");
+  return QRNG_OK;
+}
+
+int qrng_postprocess_host_wait(qrng_ctx* ctx, qrng_stream_t stream) {
+  if (!ctx) return QRNG_EINVAL;
+  QRNG_CUDA(ctx, cudaSetDevice(ctx->device), "cudaSetDevice");
+  if (ctx->up_stream) {
+    QRNG_CUDA(ctx, cudaStreamSynchronize(ctx->up_stream), "pipeline wait");
+    QRNG_CUDA(ctx, cudaStreamSynchronize(ctx->down_stream), "pipeline wait");
   }
   return qrng_synchronize(ctx, stream);
 }

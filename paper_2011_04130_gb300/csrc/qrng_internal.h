@@ -348,6 +348,17 @@ struct qrng_ctx {
   bool pipeline_seen = false;
   PipelineShape pipeline_shape{};
   uint64_t pipeline_m = 0;
+  // overlapped host pipeline (qrng_postprocess_host_async): two slots of device buffers, used by
+  // calls in turn; a slot's buffers are reused once its earlier call's hash (samples, seed) and
+  // download (output) are done
+  struct AsyncSlot {
+    qrng::DevBuf samples, seed, out;
+    cudaEvent_t uploaded = nullptr, computed = nullptr, downloaded = nullptr;
+    bool used = false;
+  };
+  AsyncSlot async_slot[2];
+  uint64_t async_calls = 0;
+  cudaStream_t up_stream = nullptr, down_stream = nullptr;
   struct BatchGraph {
     uint64_t key = 0, generation = 0, stamp = 0;
     cudaGraph_t graph = nullptr;

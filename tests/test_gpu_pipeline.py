@@ -2,8 +2,8 @@
 sizing, Sec. III.B-E hashing of the sample stream's blocks) against the oracle, including the
 block-Karatsuba route's derived operands computed beside the estimate from the previous call's m:
 a hit (same m), a miss (the modified form with a different m, whose operands depend on n - m), new
-sample contents at the same address, a rejected call in between, and the host-buffer pipeline that
-shares the same first half."""
+sample contents at the same address, a rejected call in between, the host-buffer pipeline that
+shares the same first half, and its overlapped form (calls submitted back to back)."""
 import numpy as np
 import pytest
 
@@ -147,3 +147,42 @@ def test_host_pipeline_presplit(qlib, gpu, oracle_mod):
         assert not oracle_mod.freivalds(raw, n, m, seed, STD, nb, out[:(nb * m + 7) // 8]).any()
     pre, used = _stats(qlib, gpu)
     assert pre == 1 and used == 1, (pre, used)
+
+
+def test_host_async_pipeline_overlapping_calls(qlib, gpu, oracle_mod):
+    """Calls of the overlapped host pipeline submitted back to back (the device buffers alternate
+    between two slots, each call's upload and download beside another call's hash), with new sample
+    contents every call, a larger shape half-way (the slots' buffers grow) and a rejected call in
+    between: after the wait every output equals the oracle's."""
+    import torch
+
+    calls = [(1 << 20, 1 << 16, 701), (1 << 20, 1 << 16, 702), (1 << 20, 1 << 16, 703),
+             (1 << 21, 1 << 16, 704), (1 << 21, 1 << 16, 705), (3 << 18, 4096, 706)]
+    seed = W.random_bits(2 * (1 << 16) - 1, 707)
+    pin_seed = torch.from_numpy(seed).pin_memory()
+    done = []
+    for i, (count, n, sseed) in enumerate(calls):
+        samples = W.adc_samples(count, sseed)
+        pin_samples = torch.from_numpy(samples).pin_memory()
+        pin_out = torch.zeros(count, dtype=torch.uint8).pin_memory()
+        if i == 2:  # a call whose output buffer is too small is refused; the stream of calls goes on
+            small = torch.zeros(8, dtype=torch.uint8).pin_memory()
+            with pytest.raises(qlib.QrngError) as e:
+                qlib.qrng_postprocess_host_async(gpu, pin_samples, count, 8, 1e-6, 1.0, n, pin_seed, 2 * n - 1,
+                                                 STD, qlib.QRNG_ALGO_AUTO, small, small.numel())
+            assert e.value.status == qlib.QRNG_EINVAL
+        m, nb, rep = qlib.qrng_postprocess_host_async(gpu, pin_samples, count, 8, 1e-6, 1.0, n, pin_seed,
+                                                      2 * n - 1, STD, qlib.QRNG_ALGO_AUTO, pin_out, pin_out.numel())
+        done.append((samples, pin_samples, pin_out, n, m, nb, rep))
+    qlib.qrng_postprocess_host_wait(gpu)
+    for samples, _, pin_out, n, m, nb, rep in done:
+        ref = oracle_mod.minentropy(samples, 8, 1e-6)
+        assert abs(rep["h_modify"] - ref["h_modify"]) < 1e-12
+        assert m == oracle_mod.output_length(n, ref["h_modify"], 8, 1.0) and nb == samples.size * 8 // n
+        got = pin_out.numpy()[:(nb * m + 7) // 8]
+        raw = samples.view(np.uint8)
+        seed_n = seed[:(n + m - 1 + 7) // 8]
+        if n * m * nb <= 1 << 30:
+            assert np.array_equal(got, oracle_mod.toeplitz_blocks(raw, n, m, seed_n, STD, nb))
+        else:
+            assert not oracle_mod.freivalds(raw, n, m, seed_n, STD, nb, got).any()

@@ -416,18 +416,23 @@ def roofline_for(algo, num_blocks, m, n_t, kernel_ms, plan=None, caps=None, n=No
                            else "gemm_tc_kernel<fp4> (tcgen05 kind::mxf4, block scale 2^0)"),
                 "kernel_ms": kernel_ms, "peak_source": "FP4 = 6 x bf16 burst " + pk["source"]}
     if algo == "gemm_karatsuba":
-        # the product kernel's own work: 3^L dense sub-products of mq x kq per block (the plan the
-        # library ran, from qrng_karatsuba_plan)
+        # the product kernel's own work: 3^L dense sub-products per block (the plan the library
+        # ran, from qrng_karatsuba_plan), of kq columns and the rows it issues MMAs for: the
+        # output tiles of 256 rows holding the ceil(m / span) h rows some output needs (mq pads
+        # them to whole pairs of tiles; a pair's second tile past them gets no MMAs)
         pk = measured_peaks()
         peak = 6.0 * pk["bf16_tflops"]
         plan = plan or {}
-        flops = 2.0 * num_blocks * plan["groups"] * plan["mq"] * plan["kq"]
+        span = plan["h"] << plan["levels"]
+        rows = min(plan["mq"], -(-(-(-m // span) * plan["h"]) // 256) * 256)
+        flops = 2.0 * num_blocks * plan["groups"] * rows * plan["kq"]
         achieved = flops / (kernel_ms / 1e3) / 1e12
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": captured_traffic("gemm_pair_kara_kernel", "k_gemm_pair.cu", num_blocks),
                 "kernel": "gemm_pair_kernel<kKara> (tcgen05 cta_group::2 kind::mxf4 on the block-Karatsuba "
                           "sub-products)", "kernel_ms": kernel_ms,
-                "plan": plan, "equivalent_plain_tflops": 2.0 * num_blocks * m * n_t / (kernel_ms / 1e3) / 1e12,
+                "plan": plan, "rows_issued": rows,
+                "equivalent_plain_tflops": 2.0 * num_blocks * m * n_t / (kernel_ms / 1e3) / 1e12,
                 "peak_source": "FP4 = 6 x bf16 burst " + pk["source"]}
     if algo == "fft64":
         # two P-point complex FP64 transforms per pair of blocks (5 P log2 P flops each) and the

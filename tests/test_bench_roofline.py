@@ -14,13 +14,25 @@ def test_karatsuba_roofline_counts_the_sub_products():
     plan = {"levels": 3, "h": 256, "groups": 27, "mq": 4608, "kq": 8192}
     n, m, B, ms = 1 << 16, 36473, 8192, 2.0
     r = bench.roofline_for("gemm_karatsuba", B, m, n, ms, plan)
-    flops = 2.0 * B * 27 * 4608 * 8192
+    flops = 2.0 * B * 27 * 4608 * 8192  # 18 live row blocks of 256: every row tile issued
     assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
     assert abs(r["achieved"] - flops / (ms / 1e3) / 1e12) < 1e-6 * r["achieved"]
     assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
     assert abs(r["peak"] - 6.0 * bench.measured_peaks()["bf16_tflops"]) < 1e-9
     # the plain product the route replaces, reported beside it
     assert abs(r["equivalent_plain_tflops"] - 2.0 * B * m * n / (ms / 1e3) / 1e12) < 1e-6 * r["achieved"]
+
+
+def test_karatsuba_roofline_counts_only_issued_rows():
+    """At four levels the laser stream's sub-products have 9 live row blocks of 256 in a plan of 10
+    (whole pairs of tiles): the tenth gets no MMAs and is not counted."""
+    import bench
+
+    plan = {"levels": 4, "h": 256, "groups": 81, "mq": 2560, "kq": 4096}
+    n, m, B, ms = 1 << 16, 36473, 8192, 1.8
+    r = bench.roofline_for("gemm_karatsuba", B, m, n, ms, plan)
+    assert r["rows_issued"] == 2304
+    assert abs(r["achieved"] - 2.0 * B * 81 * 2304 * 4096 / (ms / 1e3) / 1e12) < 1e-6 * r["achieved"]
 
 
 def test_traffic_record_tracks_the_kernel_source():

@@ -26,7 +26,7 @@ ALGO_NAMES = {QRNG_ALGO_AUTO: "auto", QRNG_ALGO_DIRECT: "direct", QRNG_ALGO_GEMM
 EXPORTED = ["qrng_create", "qrng_destroy", "qrng_last_error", "qrng_status_string", "qrng_minentropy",
             "qrng_output_length", "qrng_seed_bits", "qrng_toeplitz_extract", "qrng_postprocess", "qrng_postprocess_host",
             "qrng_postprocess_host_async", "qrng_postprocess_host_wait",
-            "qrng_get_stats", "qrng_reset_stats", "qrng_set_timing", "qrng_synchronize",
+            "qrng_get_stats", "qrng_extract_stats", "qrng_reset_stats", "qrng_set_timing", "qrng_synchronize",
             "qrng_minentropy_noalloc", "qrng_extract_batch", "qrng_set_autotune", "qrng_inject_fault",
             "qrng_minentropy_sampled", "qrng_minentropy_quantum", "qrng_set_karatsuba", "qrng_karatsuba_plan",
             "qrng_set_fft32", "qrng_fft32_terms_bound"]
@@ -149,6 +149,7 @@ def load_library(path: str = LIB_PATH) -> ctypes.CDLL:
                                                 vp]
     lib.qrng_postprocess_host_wait.argtypes = [vp, vp]
     lib.qrng_get_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+    lib.qrng_extract_stats.argtypes = [vp, ctypes.POINTER(dbl)]
     lib.qrng_reset_stats.argtypes = [vp]
     lib.qrng_set_timing.argtypes = [vp, i32]
     lib.qrng_synchronize.argtypes = [vp, vp]
@@ -328,6 +329,13 @@ def qrng_get_stats(ctx: Context) -> dict:
     s = Stats()
     ctx.check(load_library().qrng_get_stats(ctx.handle, ctypes.byref(s)), "qrng_get_stats")
     return s.as_dict()
+
+
+def qrng_extract_stats(ctx: Context) -> float:
+    """Worst |s - round(s)| of the FFT routes since the last reset."""
+    w = ctypes.c_double()
+    ctx.check(load_library().qrng_extract_stats(ctx.handle, ctypes.byref(w)), "qrng_extract_stats")
+    return w.value
 
 
 def qrng_reset_stats(ctx: Context):

@@ -1548,6 +1548,16 @@ int qrng_get_stats(qrng_ctx* ctx, qrng_stats* out) {
   return QRNG_OK;
 }
 
+int qrng_extract_stats(qrng_ctx* ctx, double* worst_fft_round_err) {
+  if (!ctx) return QRNG_EINVAL;
+  if (!worst_fft_round_err) return fail(ctx, QRNG_EINVAL, "qrng_extract_stats: NULL pointer");
+  qrng_stats st{};
+  const int r = qrng_get_stats(ctx, &st);
+  if (r) return r;
+  *worst_fft_round_err = st.worst_fft_round_err;
+  return QRNG_OK;
+}
+
 int qrng_reset_stats(qrng_ctx* ctx) {
   if (!ctx) return QRNG_EINVAL;
   for (size_t i = 0; i < ctx->ev_used; ++i) cudaEventSynchronize(ctx->ev_end[i]);

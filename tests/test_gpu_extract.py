@@ -138,7 +138,10 @@ def test_fft_rounding_evidence(qlib, gpu, oracle_mod, algo, bound):
     got = extract(qlib, gpu, raw, n, m, seed, STD, ALGOS[algo], B)
     st = qlib.qrng_get_stats(gpu)
     assert 0.0 < st["worst_fft_round_err"] < bound, st
+    assert qlib.qrng_extract_stats(gpu) == st["worst_fft_round_err"]  # the same figure, alone
     assert not oracle_mod.freivalds(raw, n, m, seed, STD, B, got).any()
+    qlib.qrng_reset_stats(gpu)
+    assert qlib.qrng_extract_stats(gpu) == 0.0
 
 
 @pytest.mark.parametrize("log2n", [12, 18, 24])

@@ -101,29 +101,43 @@ def test_gemm_all_ones_largest_sums(qlib, gpu, oracle_mod, gemm, n, m, B):
     spot_check(oracle_mod, raw, n, m, seed, STD, got, blocks=[0, B - 1], per_block=64)
 
 
+_ORACLE_CHECKED = set()  # direct-kernel references already checked against the oracle
+
+
+def _checked_direct(qlib, gpu, oracle_mod, raw, n, m, seed, B, key):
+    """The direct kernel's output, checked once per key against the oracle on every block
+    (Freivalds, 64 random row combinations per block), so that comparisons with it reach the oracle."""
+    ref = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_DIRECT, B)
+    if key not in _ORACLE_CHECKED:
+        assert not oracle_mod.freivalds(raw, n, m, seed, STD, B, ref).any()
+        _ORACLE_CHECKED.add(key)
+    return ref
+
+
 @pytest.mark.parametrize("gemm", list(GEMMS))
-def test_gemm_full_occupancy_repeated(qlib, gpu, gemm):
+def test_gemm_full_occupancy_repeated(qlib, gpu, oracle_mod, gemm):
     """Every SM busy (one or two tiles per CTA), long K (n = 2^16), repeated: the pipelines that
     hand raw tiles and operand stages between warps are exercised at full speed. The output equals
-    the direct kernel's on every repetition."""
+    the direct kernel's (checked against the oracle on every block) on every repetition."""
     n = 1 << 16
     for m, B in ((2048, 224 * 19), (4096, 256 * 19)):
         raw = W.random_bits(n * B, 321 + m)
         seed = W.random_bits(n + m - 1, 654 + m)
-        ref = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_DIRECT, B)
+        ref = _checked_direct(qlib, gpu, oracle_mod, raw, n, m, seed, B, ("occupancy", m, B))
         for _ in range(3):
             assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, STD, GEMMS[gemm], B), ref)
 
 
 @pytest.mark.parametrize("algo", list(ALGOS))
-def test_algorithms_agree_on_laser_stream(qlib, gpu, algo):
-    """Every algorithm gives byte-identical output on the full-size stream."""
+def test_algorithms_agree_on_laser_stream(qlib, gpu, oracle_mod, algo):
+    """Every algorithm gives byte-identical output on the full-size stream, equal to the direct
+    kernel's, which is checked against the oracle on every block."""
     c = W.CFG2
     samples = W.adc_samples(c["samples"], c["sample_seed"])
     n, m = c["n"], 36473
     B = samples.size * 8 // n
     seed = W.random_bits(n + m - 1, c["seed_seed"])
-    ref = extract(qlib, gpu, samples, n, m, seed, STD, qlib.QRNG_ALGO_DIRECT, B)
+    ref = _checked_direct(qlib, gpu, oracle_mod, samples, n, m, seed, B, ("laser",))
     got = extract(qlib, gpu, samples, n, m, seed, STD, ALGOS[algo], B)
     assert np.array_equal(got, ref)
 

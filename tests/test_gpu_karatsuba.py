@@ -66,11 +66,13 @@ def test_chunked_passes(qlib, gpu, oracle_mod, kara, levels, h):
     assert np.array_equal(extract(qlib, gpu, raw, n, m, seed, MOD, KARA, B), want)
 
 
-def test_many_blocks_match_direct(qlib, gpu, kara):
-    """Full occupancy: 76 clusters with several tiles each, repeated; equal to the direct kernel."""
+def test_many_blocks_match_direct(qlib, gpu, oracle_mod, kara):
+    """Full occupancy: 76 clusters with several tiles each, repeated; equal to the direct kernel,
+    whose output is checked against the oracle on every block."""
     n, m, B = 1 << 14, 12000, 224 * 9 + 5
     raw, seed = _case(n, m, STD, B, 13)
     ref = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_DIRECT, B)
+    assert not oracle_mod.freivalds(raw, n, m, seed, STD, B, ref).any()
     for levels, h in ((2, 1024), (3, 512), (3, 256), (4, 256), (0, 0)):
         kara(levels, h)
         for _ in range(2):

@@ -181,9 +181,13 @@ QRNG_API uint64_t qrng_output_length(uint64_t n, double h_per_sample, int bits, 
 enum { QRNG_FORM_STANDARD = 0, QRNG_FORM_MODIFIED = 1 };
 
 enum {
-  QRNG_ALGO_AUTO = 0,     /* the fastest algorithm for the shape: on the first call of a shape the
-                             candidates a cost model keeps are each run once and timed (that call
-                             synchronises the stream), and the winner is cached on the context     */
+  QRNG_ALGO_AUTO = 0,     /* the fastest algorithm for the shape: on the first call of a shape
+                             class (n, form, the block count rounded up to a power of two, m with
+                             its six leading bits kept: calls whose m differs by a few bits share
+                             it) the candidates a cost model keeps are each run once and timed
+                             (that call synchronises the stream), and the winner is cached on the
+                             context; a later call of the class takes it where it applies to its
+                             exact m, else the cost model's choice                                 */
   QRNG_ALGO_DIRECT = 1,   /* bit-packed AND/XOR + parity, each block on its own (Sec. III.B, O(mn)) */
   QRNG_ALGO_GEMM_TC = 2,  /* all blocks as one GF(2) matrix product T X on tcgen05 tensor cores   */
   QRNG_ALGO_FFT64 = 3,    /* circulant embedding + FP64 FFT convolution per block (Sec. III.B-D) */
@@ -371,6 +375,8 @@ typedef struct {
   uint64_t kara_presplits;       /* qrng_postprocess / _host: derived operands of the block-
                                     Karatsuba route computed beside the estimate                 */
   uint64_t kara_presplits_used;  /* ... and taken by the hash (the rest were computed again)     */
+  uint64_t autotune_runs;        /* QRNG_ALGO_AUTO calls that timed the candidates (one per shape
+                                    class)                                                       */
 } qrng_stats;
 
 /* Statistics since creation or the last reset. When timing is on, this call waits for the

@@ -95,6 +95,7 @@ class Stats(ctypes.Structure):
         ("last_fft32_segment", ctypes.c_uint64),
         ("kara_presplits", ctypes.c_uint64),
         ("kara_presplits_used", ctypes.c_uint64),
+        ("autotune_runs", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:

@@ -387,9 +387,26 @@ int extract_one(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uint64_
   return extract_bitwise(ctx, algo, raw, n, m, seed, form, num_blocks, out, s, kernels, fft32_log_s);
 }
 
+// The autotuner's class of an output length: m with its six leading bits kept (the class is 1/64
+// to 1/32 of m wide). The corrected min-entropy of a live stream moves m by a few bits from call
+// to call; the routes' costs do not change over such a step, so those calls share one tuning.
+uint64_t tune_m_class(uint64_t m) {
+  uint32_t lg = 0;
+  while (lg < 63 && (2ull << lg) <= m) ++lg;  // floor(log2 m) for m >= 1
+  const uint32_t sh = lg > 5 ? lg - 5 : 0;
+  return (m >> sh) << sh;
+}
+
+qrng_ctx::TuneKey tune_key(uint64_t n, uint64_t m, uint64_t num_blocks, int form) {
+  uint32_t lb = 0;
+  while ((1ull << lb) < num_blocks) ++lb;
+  return qrng_ctx::TuneKey{n, tune_m_class(m), lb, form};
+}
+
 // QRNG_ALGO_AUTO: the candidates within 4x of the best modelled time are each run once on the
 // call's own data (they give identical bits), timed with CUDA events, and the fastest is kept for
-// this shape; later calls of the shape use it directly. The FP32 route is a candidate once per
+// this shape class; later calls of the class use it directly (or the cost model's choice when the
+// kept route does not apply to their exact m). The FP32 route is a candidate once per
 // segment length (unless the context fixes it), so the segment length is tuned with it.
 int choose_auto(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const uint8_t* seed, int form,
                 uint64_t num_blocks, uint8_t* out, cudaStream_t s, uint32_t* kernels, int* chosen, int* chosen_log_s,
@@ -423,15 +440,15 @@ int choose_auto(qrng_ctx* ctx, const uint8_t* raw, uint64_t n, uint64_t m, const
     *chosen_log_s = best_c.log_s;
     return QRNG_OK;
   }
-  uint32_t lb = 0;
-  while ((1ull << lb) < num_blocks) ++lb;
-  const qrng_ctx::TuneKey key{n, m, lb, form};
+  const qrng_ctx::TuneKey key = tune_key(n, m, num_blocks, form);
   for (const auto& e : ctx->tuned)
     if (e.first == key) {
-      *chosen = e.second.algo;
-      *chosen_log_s = e.second.fft32_log_s;
+      const bool fits = algo_applicable(e.second.algo, n_t, m, num_blocks);
+      *chosen = fits ? e.second.algo : best_c.algo;
+      *chosen_log_s = fits ? e.second.fft32_log_s : best_c.log_s;
       return QRNG_OK;
     }
+  ++ctx->stats.autotune_runs;
   int best = -1, best_ls = 0;
   float best_ms = 0.f;
   bool last_ok = true;
@@ -1018,9 +1035,7 @@ int extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_t count, int a
 // The QRNG_ALGO_AUTO choice already tuned for this shape, or -1.
 int tuned_choice(const qrng_ctx* ctx, uint64_t n, uint64_t m, uint64_t num_blocks, int form) {
   if (!ctx->autotune) return -1;
-  uint32_t lb = 0;
-  while ((1ull << lb) < num_blocks) ++lb;
-  const qrng_ctx::TuneKey key{n, m, lb, form};
+  const qrng_ctx::TuneKey key = tune_key(n, m, num_blocks, form);
   for (const auto& e : ctx->tuned)
     if (e.first == key) return e.second.algo;
   return -1;

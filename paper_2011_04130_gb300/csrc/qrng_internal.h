@@ -384,9 +384,10 @@ struct qrng_ctx {
   size_t tune_host_cap = 0;
   std::vector<BatchGraph> graphs;
   uint64_t graph_clock = 0;
-  // autotuner: fastest measured algorithm per shape (n, m, log2 of the block count, form)
+  // autotuner: fastest measured algorithm per shape class (n, m to its six leading bits, log2 of
+  // the block count rounded up, form)
   struct TuneKey {
-    uint64_t n, m;
+    uint64_t n, m;  // m: the class's lower end
     uint32_t log2_blocks;
     int form;
     bool operator==(const TuneKey& o) const {

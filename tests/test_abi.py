@@ -106,3 +106,47 @@ def test_fft32_terms_bound_is_percivals(qlib):
         assert T * per * (eps + T * u) < F(1, 2)
     assert [q.qrng_fft32_terms_bound(S) for S in (2048, 4096, 8192)] == [16, 8, 3]
     assert q.qrng_fft32_terms_bound(1024) == 0 and q.qrng_fft32_terms_bound(5000) == 0
+
+
+_C_TYPES = {"double": 8, "uint64_t": 8, "int64_t": 8, "uint32_t": 4, "int32_t": 4, "int": 4}
+
+
+def _header_structs():
+    """Field lists (name, byte size, array length) of every typedef'd struct in include/qrng.h."""
+    txt = open(os.path.join(ROOT, "include", "qrng.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    out = {}
+    for body, name in re.findall(r"typedef struct\s*\{(.*?)\}\s*(\w+)\s*;", txt, flags=re.S):
+        fields = []
+        for decl in body.split(";"):
+            decl = decl.strip()
+            if not decl:
+                continue
+            m = re.match(r"((?:const\s+)?\w+\s*\**)\s*(.*)$", decl, flags=re.S)
+            ctype, names = m.group(1), m.group(2)
+            size = 8 if "*" in ctype else _C_TYPES[ctype.strip()]
+            for item in names.split(","):
+                am = re.match(r"(\w+)\s*(?:\[(\d+)\])?$", item.strip())
+                fields.append((am.group(1), size, int(am.group(2) or 1)))
+        out[name] = fields
+    return out
+
+
+def test_binding_structs_mirror_the_header():
+    """Every struct the binding passes through the C ABI has the header's fields, in order, with
+    the same sizes (a field added on one side only would shift every later field)."""
+    import ctypes
+
+    import paper_2011_04130_gb300 as q
+
+    structs = _header_structs()
+    pairs = {"qrng_hmin_report": q.HminReport, "qrng_request": q.Request, "qrng_stats": q.Stats,
+             "qrng_karatsuba_plan_info": q.KaratsubaPlan}
+    assert set(pairs) <= set(structs)
+    for cname, py in pairs.items():
+        got = []
+        for fname, ftype in py._fields_:
+            length = getattr(ftype, "_length_", 1)
+            elem = getattr(ftype, "_type_", ftype) if length > 1 else ftype
+            got.append((fname, ctypes.sizeof(elem), length))
+        assert got == structs[cname], cname

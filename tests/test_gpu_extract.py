@@ -220,6 +220,22 @@ def test_auto_tunes_once_per_shape(qlib, gpu, oracle_mod):
     qlib.qrng_set_autotune(gpu, True)
 
 
+def test_auto_tunes_once_per_m_class(qlib, gpu, oracle_mod):
+    """Calls whose m differs by a few bits (a live stream's corrected min-entropy moves that much
+    from call to call) share one tuning; an m outside the class (its six leading bits differ) is
+    tuned again. Every output equals the oracle's."""
+    n, B = 8192, 256
+    qlib.qrng_set_autotune(gpu, True)  # starts with no tuned shapes
+    qlib.qrng_reset_stats(gpu)
+    runs = []
+    for m, s in ((6144, 81), (6150, 82), (6271, 83), (4100, 84), (6145, 85)):
+        raw, seed = _case(n, m, STD, B, s)
+        got = extract(qlib, gpu, raw, n, m, seed, STD, qlib.QRNG_ALGO_AUTO, B)
+        assert np.array_equal(got, oracle_mod.toeplitz_blocks(raw, n, m, seed, STD, B)), m
+        runs.append(qlib.qrng_get_stats(gpu)["autotune_runs"])
+    assert runs == [1, 1, 1, 2, 2], runs  # 6144..6271 is one class, 4100 another
+
+
 @pytest.mark.parametrize("gemm", list(GEMMS))
 def test_gemm_rejects_too_long_blocks(qlib, gpu, gemm):
     import torch

@@ -291,12 +291,20 @@ QRNG_API int qrng_extract_batch(qrng_ctx* ctx, const qrng_request* reqs, uint64_
  *   m_out, num_blocks_out, rep   host; receive m, the number of blocks and the entropy report
  *                  (any of them may be NULL).
  * Returns QRNG_EINVAL when m comes out 0 or a capacity is too small (m_out / num_blocks_out are
- * still written). The estimate synchronises `stream` (m is needed on the host to plan the hash);
- * the hash is enqueued on `stream` and the call returns without waiting for it. When the previous
- * call on this context had the same n, count, bits and form and its hash ran on the block-Karatsuba
- * route, the derived raw operands of that route (which do not depend on m in the standard form)
- * are computed on a second stream of the context while the estimate runs; a different m only
- * costs computing them again. The buffers belong to the call until `stream` reaches its end.
+ * still written). The call waits for the estimate (m is returned, and plans the hash) but not for
+ * the hash, which is enqueued on `stream`. When the previous call on this context had the same n,
+ * count, bits and form and its hash ran on the block-Karatsuba route, the derived raw operands of
+ * that route (which do not depend on m in the standard form) are computed on a second stream of
+ * the context while the estimate runs; a different m only costs computing them again. In the
+ * standard form such a call (for n a multiple of 128, 16-byte aligned samples, a 4-byte aligned
+ * `out` and a block count that is a multiple of 32) also enqueues the hash right behind the
+ * estimate, before the host has read m: for up to m_cap rows, the previous m rounded up to the
+ * route's row span (at most seed_capacity_bits - n + 1), with m itself computed on the device from
+ * the report in the host's arithmetic. The hash's kernels do nothing unless m <= m_cap (and m >= 64)
+ * and the call is valid; when m is outside, the call hashes again with m as an ordinary call
+ * (qrng_stats counts both). Either way `out` receives exactly the ordinary call's bytes. The
+ * buffers belong to the call until `stream` reaches its end, and calls on one context are made
+ * on one stream (a call's work waits for the work earlier calls left on its stream).
  */
 QRNG_API int qrng_postprocess(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps,
                               double eps_lhl, uint64_t n, const uint8_t* seed, uint64_t seed_capacity_bits, int form,
@@ -377,6 +385,10 @@ typedef struct {
   uint64_t kara_presplits_used;  /* ... and taken by the hash (the rest were computed again)     */
   uint64_t autotune_runs;        /* QRNG_ALGO_AUTO calls that timed the candidates (one per shape
                                     class)                                                       */
+  uint64_t speculative_hashes;   /* qrng_postprocess calls whose hash was enqueued before the
+                                    host read m (see qrng_postprocess)                           */
+  uint64_t speculative_misses;   /* ... of which m fell outside the enqueued rows and the hash
+                                    ran again with m                                             */
 } qrng_stats;
 
 /* Statistics since creation or the last reset. When timing is on, this call waits for the

@@ -96,6 +96,8 @@ class Stats(ctypes.Structure):
         ("kara_presplits", ctypes.c_uint64),
         ("kara_presplits_used", ctypes.c_uint64),
         ("autotune_runs", ctypes.c_uint64),
+        ("speculative_hashes", ctypes.c_uint64),
+        ("speculative_misses", ctypes.c_uint64),
     ]
 
     def as_dict(self) -> dict:

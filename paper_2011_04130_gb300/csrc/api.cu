@@ -261,10 +261,10 @@ int extract_bitwise(qrng_ctx* ctx, int algo, const uint8_t* raw, uint64_t n, uin
   return QRNG_OK;
 }
 
-// Histogram (all samples, or the random subsample when thr < 2^53) + FP64 finaliser, report read back.
-int minentropy_dev(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps, qrng_hmin_report* rep,
-                   cudaStream_t s, uint64_t thr = 1ull << 53, uint64_t sel_seed = 0, double var_sub = 0.0,
-                   double h_ref = 0.0, double* h_subtracted = nullptr) {
+// Histogram (all samples, or the random subsample when thr < 2^53) and FP64 finaliser enqueued on
+// `s`; the report stays on the device (ctx->result).
+int minentropy_enqueue(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps, cudaStream_t s,
+                       uint64_t thr = 1ull << 53, uint64_t sel_seed = 0, double var_sub = 0.0, double h_ref = 0.0) {
   const uint64_t K = 1ull << bits;
   uint32_t kernels = 0;
   QRNG_CUDA(ctx, ctx->hist.ensure((K + 1) * sizeof(unsigned long long)), "histogram workspace");
@@ -285,10 +285,12 @@ int minentropy_dev(qrng_ctx* ctx, const void* samples, uint64_t count, int bits,
   QRNG_CUDA(ctx, launch_hmin_finalize(ctx->hist.as<unsigned long long>(), bits, eps, ctx->result.as<DevHminResult>(),
                                       s, &kernels, var_sub, h_ref),
             "min-entropy finaliser kernel");
-  QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->result_host, ctx->result.p, sizeof(DevHminResult), cudaMemcpyDeviceToHost, s),
-            "report copy");
-  QRNG_CUDA(ctx, cudaStreamSynchronize(s), "min-entropy synchronise");
   ctx->stats.kernels_launched += kernels;
+  return QRNG_OK;
+}
+
+// The report in ctx->result_host (its copy complete), the finaliser's failures as statuses.
+int minentropy_read(qrng_ctx* ctx, qrng_hmin_report* rep, double var_sub = 0.0, double* h_subtracted = nullptr) {
   const DevHminResult& r = *ctx->result_host;
   if (r.out_of_range)
     return fail(ctx, QRNG_EINVAL, "qrng_minentropy: " + std::to_string(r.out_of_range) + " samples are >= 2^bits");
@@ -299,6 +301,18 @@ int minentropy_dev(qrng_ctx* ctx, const void* samples, uint64_t count, int bits,
   *rep = r.rep;
   if (h_subtracted) *h_subtracted = r.h_subtracted;
   return QRNG_OK;
+}
+
+// Histogram (all samples, or the random subsample when thr < 2^53) + FP64 finaliser, report read back.
+int minentropy_dev(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps, qrng_hmin_report* rep,
+                   cudaStream_t s, uint64_t thr = 1ull << 53, uint64_t sel_seed = 0, double var_sub = 0.0,
+                   double h_ref = 0.0, double* h_subtracted = nullptr) {
+  const int st = minentropy_enqueue(ctx, samples, count, bits, eps, s, thr, sel_seed, var_sub, h_ref);
+  if (st) return st;
+  QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->result_host, ctx->result.p, sizeof(DevHminResult), cudaMemcpyDeviceToHost, s),
+            "report copy");
+  QRNG_CUDA(ctx, cudaStreamSynchronize(s), "min-entropy synchronise");
+  return minentropy_read(ctx, rep, var_sub, h_subtracted);
 }
 
 int check_minentropy_args(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, double eps,
@@ -1135,6 +1149,145 @@ int pipeline_size(qrng_ctx* ctx, const char* who, const void* samples, uint64_t 
   return QRNG_OK;
 }
 
+// ---- speculative hash of the pipeline ----
+//
+// After a qrng_postprocess call of a stream shape that hashed on the block-Karatsuba route in the
+// standard form, the next call of that shape does not wait for its estimate before hashing: it
+// enqueues the estimate, the output length computed from it on the device, and the hash for up to
+// m_cap rows (the previous m rounded up to the plan's row span, so the product issues the tiles the
+// previous call did), with the derived operands and seeds on the second stream beside the
+// estimate. The product kernel returns at once and the combination writes nothing unless the
+// device's m is at most m_cap (and at least kSpecMinBits) and the call is valid; the host reads
+// the report while the product runs, finds the same m, and hashes again on the ordinary path when
+// the hash did not stand.
+struct SpecPlan {
+  uint64_t m_cap = 0;
+  KaraPlan plan;
+};
+
+bool spec_plan(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, uint64_t n, int form, int algo,
+               uint64_t nb, uint64_t seed_capacity_bits, const uint8_t* out, SpecPlan* sp) {
+  const qrng_ctx::PipelineShape shape{n, count, bits, form, nb};
+  if (!ctx->pipeline_seen || !(ctx->pipeline_shape == shape) || form != QRNG_FORM_STANDARD || nb == 0) return false;
+  const uint64_t m_prev = ctx->pipeline_m;
+  if (m_prev < kSpecMinBits || m_prev > n || seed_capacity_bits < n + m_prev - 1) return false;
+  const int a = algo == QRNG_ALGO_AUTO ? tuned_choice(ctx, n, m_prev, nb, form) : algo;
+  if (a != QRNG_ALGO_GEMM_KARATSUBA || !algo_applicable(a, n, m_prev, nb)) return false;
+  // raw blocks read in place; the packed output a whole number of aligned words for every m
+  if (n % 128 != 0 || (reinterpret_cast<uintptr_t>(samples) & 15) != 0 ||
+      (reinterpret_cast<uintptr_t>(out) & 3) != 0 || nb % 32 != 0)
+    return false;
+  const KaraPlan p0 = karatsuba_plan(n, m_prev, nb, ctx->num_sms, ctx->kara_levels, ctx->kara_h, ctx->kara_workspace);
+  if (p0.levels == 0) return false;
+  uint64_t m_cap = ceil_div(m_prev, p0.span) * p0.span;
+  if (m_cap > n) m_cap = n;
+  if (m_cap > seed_capacity_bits - n + 1) m_cap = seed_capacity_bits - n + 1;  // >= m_prev
+  const KaraPlan p = karatsuba_plan(n, m_cap, nb, ctx->num_sms, ctx->kara_levels, ctx->kara_h, ctx->kara_workspace);
+  if (!kara_speculation_fits(p, m_cap, nb)) return false;
+  sp->m_cap = m_cap;
+  sp->plan = p;
+  return true;
+}
+
+// Enqueues the speculative call and reads its report. *done: the output is written (or the call
+// refused, st != 0); otherwise the caller hashes with *m_out on the ordinary path.
+int postprocess_speculative(qrng_ctx* ctx, const SpecPlan& sp, const void* samples, uint64_t count, int bits,
+                            double eps, double eps_lhl, uint64_t n, const uint8_t* seed, uint64_t seed_capacity_bits,
+                            uint8_t* out, uint64_t out_capacity_bytes, uint64_t nb, cudaStream_t s, uint64_t* m_out,
+                            qrng_hmin_report* rep, bool* done) {
+  *done = false;
+  *m_out = 0;
+  const std::string w("qrng_postprocess");
+  qrng_hmin_report local{};
+  int st = check_minentropy_args(ctx, samples, count, bits, eps, &local);
+  if (st) return st;
+  ctx->kara.xk_ready = false;
+  QRNG_CUDA(ctx, ctx->spec.ensure(sizeof(DevSpec)), "pipeline size word");
+  if (!ctx->spec_est) QRNG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->spec_est, cudaEventDisableTiming), "event");
+  const uint64_t m_cap = sp.m_cap;
+  const uint64_t rev_words = kSeedFrontWords + ceil_div(n + m_cap - 1, 32) + kSeedBackWords;
+  QRNG_CUDA(ctx, ctx->seed_rev.ensure(rev_words * 4), "seed workspace");
+  DirectArgs a{};
+  a.raw = static_cast<const uint32_t*>(samples);
+  a.raw_stride = n / 32;
+  a.n_t = n;
+  a.nw_t = (uint32_t)ceil_div(n, 32);
+  a.tail_mask = 0xffffffffu;  // n is a multiple of 128
+  a.m = (uint32_t)m_cap;
+  a.mw = (uint32_t)ceil_div(m_cap, 32);
+  a.seed_rev = ctx->seed_rev.as<uint32_t>();
+  a.modified = 0;
+  a.id_off = (uint32_t)(n - m_cap);
+  a.out = nullptr;  // the combination writes the packed stream
+  a.out_stride = a.mw;
+  a.num_blocks = nb;
+
+  // second stream, after the work already on `s`: derived operands, reversed seed, derived seeds
+  uint32_t kernels = 0;
+  QRNG_CUDA(ctx, cudaEventRecord(ctx->pre_ready, s), "pipeline event");
+  QRNG_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->pre_ready, 0), "pipeline event");
+  QRNG_CUDA(ctx, launch_kara_presplit(a, sp.plan, ctx->kara, ctx->num_sms, ctx->copy_stream, &kernels),
+            "derived operands");
+  ++ctx->stats.kara_presplits;
+  QRNG_CUDA(ctx, launch_seed_reverse(seed, n + m_cap - 1, ctx->seed_rev.as<uint32_t>(), rev_words, ctx->copy_stream,
+                                     &kernels),
+            "seed reverse");
+  QRNG_CUDA(ctx, launch_kara_seeds(a, sp.plan, ctx->kara, ctx->copy_stream, &kernels), "derived seeds");
+  QRNG_CUDA(ctx, cudaEventRecord(ctx->pre_done, ctx->copy_stream), "pipeline event");
+  ctx->stats.kernels_launched += kernels;
+  kernels = 0;
+
+  // `s`: estimate, device-side m, the report's copy, then the hash
+  st = minentropy_enqueue(ctx, samples, count, bits, eps, s);
+  if (st) {
+    cudaStreamSynchronize(ctx->copy_stream);
+    ctx->kara.xk_ready = false;
+    return st;
+  }
+  DevSpec* dspec = ctx->spec.as<DevSpec>();
+  const double lhl_term = 2.0 * log2(1.0 / eps_lhl);  // as qrng_output_length forms it
+  QRNG_CUDA(ctx,
+            launch_pipeline_size(ctx->result.as<DevHminResult>(), n, bits, lhl_term, m_cap, seed_capacity_bits,
+                                 out_capacity_bytes, nb, dspec, s, &kernels),
+            "pipeline size kernel");
+  QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->result_host, ctx->result.p, sizeof(DevHminResult), cudaMemcpyDeviceToHost, s),
+            "report copy");
+  QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->spec_host, dspec, sizeof(DevSpec), cudaMemcpyDeviceToHost, s), "size copy");
+  QRNG_CUDA(ctx, cudaEventRecord(ctx->spec_est, s), "pipeline event");
+  QRNG_CUDA(ctx, cudaStreamWaitEvent(s, ctx->pre_done, 0), "pipeline event");
+  QRNG_CUDA(ctx,
+            launch_gemm_karatsuba(a, sp.plan, ctx->kara, ctx->dev_err.as<int>(), 0, ctx->num_sms, s, &kernels,
+                                  extract_hook(ctx), out, dspec, true),
+            "speculative block Karatsuba extraction");
+  ctx->kara.xk_ready = false;
+  ctx->stats.kernels_launched += kernels;
+  ++ctx->stats.speculative_hashes;
+
+  // the host side of the call while the product runs
+  QRNG_CUDA(ctx, cudaEventSynchronize(ctx->spec_est), "min-entropy synchronise");
+  st = minentropy_read(ctx, &local);
+  if (st) return st;  // the device refused the hash too (status 2)
+  if (rep) *rep = local;
+  uint64_t m = qrng_output_length(n, local.h_modify, bits, eps_lhl);
+  if (m > n) m = n;
+  *m_out = m;
+  ctx->pipeline_m = m;
+  const char* bad = m == 0 ? ": the corrected min-entropy gives m = 0"
+                    : seed_capacity_bits < qrng_seed_bits(n, m, QRNG_FORM_STANDARD) ? ": seed shorter than the hash needs"
+                    : out_capacity_bytes < ceil_div(nb * m, 8) ? ": output buffer too small"
+                    : nullptr;
+  if (bad) return fail(ctx, QRNG_EINVAL, w + bad);
+  const DevSpec& d = *ctx->spec_host;
+  if (d.status == 0 && d.m == m) {
+    ctx->stats.last_algo = QRNG_ALGO_GEMM_KARATSUBA;
+    ctx->stats.last_kernels = kernels;
+    *done = true;
+    return QRNG_OK;
+  }
+  ++ctx->stats.speculative_misses;  // m outside the enqueued rows: the ordinary path hashes with m
+  return QRNG_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1152,10 +1305,13 @@ int qrng_create(qrng_ctx** out, int device) {
     delete ctx;
     return QRNG_ECUDA;
   }
-  if (cudaMallocHost(reinterpret_cast<void**>(&ctx->result_host), sizeof(DevHminResult)) != cudaSuccess) {
+  // the report and the pipeline's device-side size word, read back side by side
+  if (cudaMallocHost(reinterpret_cast<void**>(&ctx->result_host), sizeof(DevHminResult) + sizeof(DevSpec)) !=
+      cudaSuccess) {
     delete ctx;
     return QRNG_ENOMEM;
   }
+  ctx->spec_host = reinterpret_cast<DevSpec*>(ctx->result_host + 1);
   if (ctx->dev_err.ensure(sizeof(int)) != cudaSuccess || cudaMemset(ctx->dev_err.p, 0, sizeof(int)) != cudaSuccess ||
       ctx->fft_worst.ensure(2 * sizeof(unsigned long long)) != cudaSuccess ||
       cudaMemset(ctx->fft_worst.p, 0, 2 * sizeof(unsigned long long)) != cudaSuccess ||
@@ -1207,6 +1363,8 @@ void qrng_destroy(qrng_ctx* ctx) {
   ctx->fft32_guard.release();
   ctx->fft.release();
   ctx->kara.release();
+  ctx->spec.release();
+  if (ctx->spec_est) cudaEventDestroy(ctx->spec_est);
   drop_all_graphs(ctx);
   ctx->batch_meta.release();
   ctx->batch_raw.release();
@@ -1344,10 +1502,23 @@ int qrng_postprocess(qrng_ctx* ctx, const void* samples, uint64_t count, int bit
   const uint64_t bytes = count * (bits <= 8 ? 1 : 2);
   const uint64_t nb = n >= 2 ? bytes * 8 / n : 0;
   uint64_t m = 0;
+  if (num_blocks_out) *num_blocks_out = nb;
+  SpecPlan sp;
+  if (eps_lhl > 0.0 && eps_lhl <= 1.0 && n <= kMaxBlockBits &&
+      spec_plan(ctx, samples, count, bits, n, form, algo, nb, seed_capacity_bits, out, &sp)) {
+    bool done = false;
+    int st = postprocess_speculative(ctx, sp, samples, count, bits, eps, eps_lhl, n, seed, seed_capacity_bits, out,
+                                     out_capacity_bytes, nb, s, &m, rep, &done);
+    if (m_out) *m_out = m;
+    if (st || done) return st;
+    // the enqueued hash did not stand (m outside its rows): hash with m, as below
+    st = extract_dispatch(ctx, static_cast<const uint8_t*>(samples), n, m, seed, form, algo, nb, out, s);
+    ctx->kara.xk_ready = false;
+    return st;
+  }
   int st = pipeline_size(ctx, "qrng_postprocess", samples, count, bits, eps, eps_lhl, n, seed_capacity_bits, form,
                          algo, nb, s, &m, rep);
   if (m_out) *m_out = m;
-  if (num_blocks_out) *num_blocks_out = nb;
   if (st) return st;
   if (out_capacity_bytes < ceil_div(nb * m, 8)) {
     ctx->kara.xk_ready = false;

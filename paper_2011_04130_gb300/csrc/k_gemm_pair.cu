@@ -143,6 +143,7 @@ struct PairArgs {
   uint64_t seed_stride;  // words per derived seed
   uint32_t* qpar;        // parities of the sub-products: word (b * groups + z) * mwq + row / 32
   uint32_t mwq;
+  const int* skip;       // non-null: return at once unless *skip == 0 (written by an earlier kernel)
 };
 
 struct TileCoord {
@@ -190,6 +191,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   const uint32_t rank = cluster_ctarank();
   const uint32_t smem_base = (smem_u32(dyn_smem) + 1023u) & ~1023u;
   const uint32_t pk_base = smem_base + STAGES * STAGE_BYTES;
+
+  // a hash enqueued before its output length was known: every thread of both CTAs reads the same
+  // word (an earlier kernel wrote it), so the whole cluster leaves before any barrier or allocation
+  if (a.skip != nullptr && *a.skip != 0) return;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -711,6 +716,7 @@ cudaError_t launch_gemm_pair_kara(const DirectArgs& d, const PairKara& k, int* e
   a.seed_stride = k.seed_stride;
   a.qpar = k.qpar;
   a.mwq = (uint32_t)(k.mq / 32);
+  a.skip = k.skip;
   CUtensorMap map;
   const bool narrow = pair_prefers_192((uint64_t)a.mpairs * k.groups, d.num_blocks, num_sms);
   cudaError_t e = encode_words_map(&map, k.xk, k.xk_words, (uint64_t)k.groups * d.num_blocks, k.xk_words,

@@ -562,6 +562,32 @@ __global__ void __launch_bounds__(kHistThreads) hist_sampled_kernel(const void* 
   }
 }
 
+// Output length of a pipeline call from the finaliser's report (Sec. III.B: m = n H / bits less
+// the leftover-hash term), for a hash enqueued before the host reads the report. One thread; the
+// operations are rounded one by one (no contraction), as in the host's computation of m, so both
+// sides find the same m.
+__global__ void pipeline_size_kernel(const DevHminResult* __restrict__ res, uint64_t n, int bits, double lhl_term,
+                                     uint64_t m_cap, uint64_t seed_cap, uint64_t out_cap, uint64_t nb,
+                                     DevSpec* __restrict__ spec) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  int st = 0;
+  uint64_t m = 0;
+  if (res->out_of_range != 0 || res->status != 0) {
+    st = 2;
+  } else {
+    const double x = __dsub_rn(__ddiv_rn(__dmul_rn((double)n, res->rep.h_modify), (double)bits), lhl_term);
+    if (x > 0.0) m = (uint64_t)floor(x);
+    if (m > n) m = n;
+    if (m == 0 || seed_cap < n + m - 1 || out_cap < (nb * m + 7) / 8)
+      st = 2;
+    else if (m > m_cap || m < kSpecMinBits)
+      st = 1;
+  }
+  spec->m = m;
+  spec->mw = (uint32_t)((m + 31) / 32);
+  spec->status = st;
+}
+
 }  // namespace
 
 cudaError_t launch_histogram(const void* samples, uint64_t count, int bits, unsigned long long* hist, int num_sms,
@@ -627,6 +653,15 @@ cudaError_t launch_hmin_finalize(const unsigned long long* hist, int bits, doubl
   const uint32_t K = 1u << bits;
   hmin_cells_kernel<<<(unsigned)ceil_div(K, (uint64_t)kCellThreads), kCellThreads, 0, s>>>(hist, bits, eps, out,
                                                                                             var_sub, h_ref);
+  ++*kernels;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pipeline_size(const DevHminResult* res, uint64_t n, int bits, double lhl_term, uint64_t m_cap,
+                                 uint64_t seed_capacity_bits, uint64_t out_capacity_bytes, uint64_t num_blocks,
+                                 DevSpec* spec, cudaStream_t s, uint32_t* kernels) {
+  pipeline_size_kernel<<<1, 32, 0, s>>>(res, n, bits, lhl_term, m_cap, seed_capacity_bits, out_capacity_bytes,
+                                        num_blocks, spec);
   ++*kernels;
   return cudaGetLastError();
 }

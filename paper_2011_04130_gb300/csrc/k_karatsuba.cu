@@ -287,9 +287,14 @@ template <int L>
 __global__ void __launch_bounds__(kPackThreads) kara_combine_pack_bulk_kernel(
     const uint32_t* __restrict__ qpar, uint32_t mwq, uint32_t log2h, uint32_t* __restrict__ stream, uint64_t nb,
     uint64_t block0, uint64_t total_blocks, uint32_t mw, uint32_t m, int modified, uint32_t id_off,
-    const uint32_t* __restrict__ raw, uint64_t raw_stride, int* err) {
+    const uint32_t* __restrict__ raw, uint64_t raw_stride, int* err, const DevSpec* __restrict__ spec) {
   using namespace tc;
   constexpr int G = pow3c(L);
+  if (spec != nullptr) {  // a speculative hash: m from the device, nothing written unless it stands
+    if (spec->status != 0) return;
+    m = (uint32_t)spec->m;
+    mw = spec->mw;
+  }
   extern __shared__ __align__(16) uint32_t smem_words[];
   __shared__ __align__(8) uint64_t full[2];
   __shared__ volatile int abort_flag;
@@ -444,7 +449,7 @@ cudaError_t launch_split_levels(uint32_t levels, const DirectArgs& dc, const Dir
 template <int L>
 cudaError_t launch_combine_pack_bulk(unsigned grid, size_t smem, cudaStream_t s, const PairKara& k, uint32_t mwq,
                                      uint32_t log2h, uint32_t* stream, uint64_t nb, uint64_t b0, const DirectArgs& d,
-                                     const DirectArgs& dc, int* err) {
+                                     const DirectArgs& dc, int* err, const DevSpec* spec) {
   // the shared-memory attribute is set once per device and level count
   constexpr int kMaxDev = 64;
   static size_t set_to[kMaxDev] = {};
@@ -459,7 +464,7 @@ cudaError_t launch_combine_pack_bulk(unsigned grid, size_t smem, cudaStream_t s,
   }
   kara_combine_pack_bulk_kernel<L><<<grid, kPackThreads, smem, s>>>(k.qpar, mwq, log2h, stream, nb, b0, d.num_blocks,
                                                                      d.mw, d.m, d.modified, d.id_off, dc.raw,
-                                                                     d.raw_stride, err);
+                                                                     d.raw_stride, err, spec);
   return cudaGetLastError();
 }
 
@@ -529,27 +534,47 @@ KaraPlan karatsuba_plan(uint64_t n_t, uint64_t m, uint64_t num_blocks, int num_s
   return best;
 }
 
+namespace {
+// shared memory of the double-buffered combination: two blocks' parity rows and one output block
+size_t bulk_smem_bytes(const KaraPlan& p, uint64_t mw) {
+  return ((size_t)2 * p.groups * (p.mq / 32) + mw) * sizeof(uint32_t);
+}
+}  // namespace
+
+bool kara_speculation_fits(const KaraPlan& p, uint64_t m_cap, uint64_t num_blocks) {
+  return p.levels >= 1 && p.levels <= kMaxLevels && p.chunk_blocks >= num_blocks && m_cap >= kSpecMinBits &&
+         m_cap <= kKaraPackMaxBits && bulk_smem_bytes(p, ceil_div(m_cap, 32)) <= kPackBulkMaxSmem;
+}
+
+cudaError_t launch_kara_seeds(const DirectArgs& d, const KaraPlan& p, KaraWorkspace& ws, cudaStream_t s,
+                              uint32_t* kernels) {
+  if (p.levels < 1 || p.levels > kMaxLevels) return cudaErrorInvalidValue;
+  cudaError_t e = ws.seeds.ensure((size_t)p.groups * p.seed_stride * 4);
+  if (e != cudaSuccess) return e;
+  const uint64_t L_t = d.n_t + d.m - 1;
+  const uint64_t rev_words = kSeedFrontWords + ceil_div(L_t, 32) + kSeedBackWords;
+  kara_seed_kernel<<<dim3((unsigned)ceil_div(p.seed_stride, kThreads), p.groups), kThreads, 0, s>>>(
+      d.seed_rev, rev_words, p.levels, (uint32_t)(p.h / 32), p.seed_front, p.seed_stride, ws.seeds.as<uint32_t>(),
+      p.seed_stride);
+  ++*kernels;
+  return cudaGetLastError();
+}
+
 cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWorkspace& ws, int* err, int fault,
                                   int num_sms, cudaStream_t s, uint32_t* kernels, const TimingHook& hook,
-                                  uint8_t* packed_out) {
+                                  uint8_t* packed_out, const DevSpec* spec, bool seeds_done) {
   if (p.levels < 1 || p.levels > kMaxLevels) return cudaErrorInvalidValue;
+  if (spec && (!packed_out || !kara_speculation_fits(p, d.m, d.num_blocks))) return cudaErrorInvalidValue;
   const uint32_t G = p.groups;
   const uint32_t hw = (uint32_t)(p.h / 32);
   uint32_t log2h = 0;
   while ((1ull << log2h) < p.h) ++log2h;
   const uint64_t xk_words = p.kq / 32, mwq = p.mq / 32;
   const uint64_t chunk = p.chunk_blocks < d.num_blocks ? p.chunk_blocks : d.num_blocks;
-  cudaError_t e = ws.seeds.ensure((size_t)G * p.seed_stride * 4);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
   if ((e = ws.xk.ensure((size_t)G * chunk * xk_words * 4)) != cudaSuccess) return e;
   if ((e = ws.qpar.ensure((size_t)G * chunk * mwq * 4)) != cudaSuccess) return e;
-
-  const uint64_t L_t = d.n_t + d.m - 1;
-  const uint64_t rev_words = kSeedFrontWords + ceil_div(L_t, 32) + kSeedBackWords;
-  kara_seed_kernel<<<dim3((unsigned)ceil_div(p.seed_stride, kThreads), G), kThreads, 0, s>>>(
-      d.seed_rev, rev_words, p.levels, hw, p.seed_front, p.seed_stride, ws.seeds.as<uint32_t>(), p.seed_stride);
-  ++*kernels;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (!seeds_done && (e = launch_kara_seeds(d, p, ws, s, kernels)) != cudaSuccess) return e;
 
   PairKara k{};
   k.seeds = ws.seeds.as<uint32_t>();
@@ -564,6 +589,7 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
   k.mq_live = ceil_div(d.m, p.span) * p.h;
   k.kq = p.kq;
   k.groups = G;
+  k.skip = spec ? &spec->status : nullptr;
   const uint32_t kblocks = (uint32_t)(p.kq / p.h);
   for (uint64_t b0 = 0; b0 < d.num_blocks; b0 += chunk) {
     const uint64_t nb = d.num_blocks - b0 < chunk ? d.num_blocks - b0 : chunk;
@@ -587,16 +613,16 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
     const uint32_t rblocks = (uint32_t)ceil_div(d.m, p.span);
     if (packed_out) {  // combine and pack in one pass
       uint32_t* stream = reinterpret_cast<uint32_t*>(packed_out);
-      const size_t bulk_smem = ((size_t)2 * G * mwq + d.mw) * sizeof(uint32_t);
+      const size_t bulk_smem = bulk_smem_bytes(p, d.mw);
       if (bulk_smem <= kPackBulkMaxSmem) {  // persistent CTAs, one bulk copy per block, double-buffered
         const uint64_t per_sm = (227 * 1024) / (bulk_smem + 1024);
         const uint64_t ctas = (uint64_t)(num_sms > 0 ? num_sms : 1) * (per_sm < 8 ? per_sm : 8);
         const unsigned grid = (unsigned)(ctas < nb ? ctas : nb);
         switch (p.levels) {
-          case 1: e = launch_combine_pack_bulk<1>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err); break;
-          case 2: e = launch_combine_pack_bulk<2>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err); break;
-          case 3: e = launch_combine_pack_bulk<3>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err); break;
-          default: e = launch_combine_pack_bulk<4>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err); break;
+          case 1: e = launch_combine_pack_bulk<1>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err, spec); break;
+          case 2: e = launch_combine_pack_bulk<2>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err, spec); break;
+          case 3: e = launch_combine_pack_bulk<3>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err, spec); break;
+          default: e = launch_combine_pack_bulk<4>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err, spec); break;
         }
         ++*kernels;
         if (e != cudaSuccess) return e;

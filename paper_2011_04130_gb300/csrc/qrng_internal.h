@@ -68,6 +68,17 @@ struct DevHminResult {
   unsigned int done;
 };
 
+// Output length of a pipeline call found on the device from the finaliser's report, for a hash
+// enqueued before the host has read that report. status 0: the hash enqueued for at most m_cap
+// rows stands; 1: m is above m_cap or below kSpecMinBits (the host hashes again with m); 2: the
+// call is refused (the estimate failed, m = 0, or the seed or the output buffer is too short).
+struct DevSpec {
+  unsigned long long m;
+  uint32_t mw;  // ceil(m / 32)
+  int status;
+};
+constexpr uint64_t kSpecMinBits = 64;
+
 // ---- histogram + finaliser (k_hist.cu) ----
 // hist: (2^bits + 1) uint64 counters, the last one counts samples >= 2^bits. Zeroed by the launcher.
 cudaError_t launch_histogram(const void* samples, uint64_t count, int bits, unsigned long long* hist, int num_sms,
@@ -77,6 +88,12 @@ cudaError_t launch_histogram(const void* samples, uint64_t count, int bits, unsi
 // h_subtracted = (model entropy at the measured variance) - h_ref.
 cudaError_t launch_hmin_finalize(const unsigned long long* hist, int bits, double eps, DevHminResult* out,
                                  cudaStream_t s, uint32_t* kernels, double var_sub = 0.0, double h_ref = 0.0);
+// One thread: m = floor(n h_modify / bits - lhl_term) (clipped to n) from the report, in the
+// operation order and rounding of the host's qrng_output_length (lhl_term = 2 log2(1 / eps_lhl)
+// computed by the host), then the checks of DevSpec.status against m_cap and the capacities.
+cudaError_t launch_pipeline_size(const DevHminResult* res, uint64_t n, int bits, double lhl_term, uint64_t m_cap,
+                                 uint64_t seed_capacity_bits, uint64_t out_capacity_bytes, uint64_t num_blocks,
+                                 DevSpec* spec, cudaStream_t s, uint32_t* kernels);
 // Histogram of the samples kept by the random selection: sample i is kept when output i+1 of
 // splitmix64 started at sel_seed, shifted right by 11, is below thr (thr = 2^53 keeps all).
 cudaError_t launch_histogram_sampled(const void* samples, uint64_t count, int bits, uint64_t thr, uint64_t sel_seed,
@@ -296,6 +313,7 @@ struct PairKara {
   uint64_t h, span, mq, kq;
   uint64_t mq_live;  // sub-product rows that feed an output row below m: ceil(m / span) h
   uint32_t groups;
+  const int* skip;   // non-null: the kernel returns at once unless *skip == 0 (a speculative hash)
 };
 cudaError_t launch_gemm_pair_kara(const DirectArgs& a, const PairKara& k, int* err, int fault, int num_sms,
                                   cudaStream_t s, uint32_t* kernels);
@@ -304,9 +322,22 @@ cudaError_t launch_gemm_pair_kara(const DirectArgs& a, const PairKara& k, int* e
 // straight into that bit-contiguous stream (block b at bit b m; 4-byte aligned, a whole number of
 // 4-byte words long, m >= 64, m <= kKaraPackMaxBits) instead of the word-aligned a.out.
 constexpr uint64_t kKaraPackMaxBits = 1ull << 18;  // 32 KB of output words per CTA
+//
+// A speculative hash (spec non-null) is enqueued before m is known: a.m is the row capacity m_cap,
+// the product kernel returns at once unless spec->status is 0, and the combination writes
+// spec->m bits per block. It needs packed_out, one pass and the double-buffered combination
+// (kara_speculation_fits); seeds_done says the derived seeds are already enqueued
+// (launch_kara_seeds with the same a and plan).
 cudaError_t launch_gemm_karatsuba(const DirectArgs& a, const KaraPlan& plan, KaraWorkspace& ws, int* err, int fault,
                                   int num_sms, cudaStream_t s, uint32_t* kernels, const TimingHook& hook = TimingHook(),
-                                  uint8_t* packed_out = nullptr);
+                                  uint8_t* packed_out = nullptr, const DevSpec* spec = nullptr,
+                                  bool seeds_done = false);
+// The derived seeds of a plan (3^levels windows of a.seed_rev), as launch_gemm_karatsuba enqueues
+// them first.
+cudaError_t launch_kara_seeds(const DirectArgs& a, const KaraPlan& plan, KaraWorkspace& ws, cudaStream_t s,
+                              uint32_t* kernels);
+// Whether a speculative hash of num_blocks blocks with row capacity m_cap runs on this plan.
+bool kara_speculation_fits(const KaraPlan& plan, uint64_t m_cap, uint64_t num_blocks);
 // Enqueues on `s` the derived operands of the first pass of launch_gemm_karatsuba(a, plan, ...)
 // (a needs n_t, raw, raw_stride, nw_t, tail_mask and num_blocks only) and marks them ready: the
 // next launch whose first pass has the same split arguments skips its split. The caller orders `s`
@@ -336,6 +367,11 @@ struct qrng_ctx {
                                            // pipelines: derived operands beside the estimate
   cudaEvent_t copy_ready = nullptr, copy_done = nullptr;
   cudaEvent_t pre_ready = nullptr, pre_done = nullptr;
+  // speculative hash: the device-side output length, its pinned copy (beside result_host) and
+  // the event after the report's copy
+  qrng::DevBuf spec;
+  qrng::DevSpec* spec_host = nullptr;
+  cudaEvent_t spec_est = nullptr;
   // the last pipeline call's stream shape and output length (predicts the next call's m)
   struct PipelineShape {
     uint64_t n, count;

@@ -186,3 +186,112 @@ def test_host_async_pipeline_overlapping_calls(qlib, gpu, oracle_mod):
             assert np.array_equal(got, oracle_mod.toeplitz_blocks(raw, n, m, seed_n, STD, nb))
         else:
             assert not oracle_mod.freivalds(raw, n, m, seed_n, STD, nb, got).any()
+
+
+def _spec_stats(q, ctx):
+    s = q.qrng_get_stats(ctx)
+    return s["speculative_hashes"], s["speculative_misses"]
+
+
+def test_speculative_hash_hits_and_misses(qlib, gpu, oracle_mod):
+    """The hash enqueued before the host reads m: a call whose m is within the previous call's rows
+    (rounded up to the plan's row span) keeps it; a call whose m is above them hashes again with m;
+    a call with a much smaller m keeps the larger launch (its extra rows are not written). Every
+    output equals the oracle's."""
+    import torch
+
+    n = 1 << 16
+    count = 5 << 19  # 320 blocks
+    qlib.qrng_set_karatsuba(gpu, 4, 256, 0)  # row span 256 << 4 = 4096
+    try:
+        seed = W.random_bits(2 * n - 1, 661)
+        seed_dev = torch.from_numpy(seed).cuda()
+        out = torch.zeros(count, dtype=torch.uint8, device="cuda")
+        samples_dev = torch.empty(count, dtype=torch.uint8, device="cuda")
+        qlib.qrng_reset_stats(gpu)
+        ms, expect_miss = [], 0
+        for i, (sseed, sigma) in enumerate(((662, 4.0), (663, 4.0), (664, 32.0), (665, 32.0), (666, 6.0))):
+            samples = W.adc_samples(count, sseed, sigma=sigma)
+            samples_dev.copy_(torch.from_numpy(samples))
+            out.zero_()
+            m, nb, rep = _run(qlib, gpu, samples_dev, count, n, seed_dev, 2 * n - 1, STD,
+                              qlib.QRNG_ALGO_GEMM_KARATSUBA, out)
+            _check(oracle_mod, qlib, samples, n, seed, STD, m, nb, rep, out, full=False)
+            # nothing past the call's bytes is written
+            assert not out[(nb * m + 7) // 8:].any()
+            if i:
+                cap = min(n, -(-ms[-1] // 4096) * 4096)
+                expect_miss += int(m > cap)
+            ms.append(m)
+        hashes, misses = _spec_stats(qlib, gpu)
+        assert hashes == 4 and misses == expect_miss, (ms, hashes, misses)
+        assert expect_miss == 1, ms  # sigma 4 -> 32 raises m by far more than one row span
+    finally:
+        qlib.qrng_set_karatsuba(gpu, 0, 0, 0)
+
+
+@pytest.mark.parametrize("eps_lhl", [1.0, 0.5, 1e-6, 2.0 ** -40, 3e-13])
+def test_speculative_m_matches_host_arithmetic(qlib, gpu, oracle_mod, eps_lhl):
+    """m computed on the device from the report equals the host's qrng_output_length for several
+    leftover-hash terms (a disagreement would count as a miss and hash again)."""
+    import torch
+
+    n = 1 << 15
+    count = 3 << 19  # 384 blocks
+    seed = W.random_bits(2 * n - 1, 671)
+    seed_dev = torch.from_numpy(seed).cuda()
+    out = torch.zeros(count, dtype=torch.uint8, device="cuda")
+    samples = W.adc_samples(count, 672, sigma=12.0)
+    samples_dev = torch.from_numpy(samples).cuda()
+    qlib.qrng_reset_stats(gpu)
+    for _ in range(3):
+        m, nb, rep = _run(qlib, gpu, samples_dev, count, n, seed_dev, 2 * n - 1, STD, qlib.QRNG_ALGO_GEMM_KARATSUBA,
+                          out, eps_lhl=eps_lhl)
+        assert m == qlib.qrng_output_length(n, rep["h_modify"], 8, eps_lhl)
+        raw = samples.view(np.uint8)
+        assert not oracle_mod.freivalds(raw, n, m, seed, STD, nb, out[:(nb * m + 7) // 8].cpu().numpy()).any()
+    hashes, misses = _spec_stats(qlib, gpu)
+    assert hashes >= 2 and misses == 0, (hashes, misses)
+
+
+def test_speculative_hash_tight_seed_and_refusals(qlib, gpu, oracle_mod):
+    """A seed of exactly n + m - 1 bits caps the enqueued rows at m. Refused speculative calls
+    write nothing: one whose output buffer is too small, one whose samples give a larger m than the
+    seed covers. The calls after them are exact again (the first one on the ordinary path, as the
+    refused call's m is beyond the seed)."""
+    import torch
+
+    n = 1 << 14
+    count = 1 << 20  # 512 blocks
+    s1 = W.adc_samples(count, 681, sigma=8.0)
+    m1 = oracle_mod.output_length(n, oracle_mod.minentropy(s1, 8, 1e-6)["h_modify"], 8, 1.0)
+    seed = W.random_bits(n + m1 - 1, 682)
+    seed_dev = torch.from_numpy(seed).cuda()
+    out = torch.zeros(count, dtype=torch.uint8, device="cuda")
+    d1 = torch.from_numpy(s1).cuda()
+    qlib.qrng_reset_stats(gpu)
+    for _ in range(2):
+        m, nb, rep = _run(qlib, gpu, d1, count, n, seed_dev, n + m1 - 1, STD, qlib.QRNG_ALGO_GEMM_KARATSUBA, out)
+        assert m == m1
+        _check(oracle_mod, qlib, s1, n, seed, STD, m, nb, rep, out, full=False)
+    small = torch.full((64,), 0x5A, dtype=torch.uint8, device="cuda")
+    with pytest.raises(qlib.QrngError) as e:
+        qlib.qrng_postprocess(gpu, d1, count, 8, 1e-6, 1.0, n, seed_dev, n + m1 - 1, STD,
+                              qlib.QRNG_ALGO_GEMM_KARATSUBA, small, small.numel())
+    assert e.value.status == qlib.QRNG_EINVAL
+    qlib.qrng_synchronize(gpu)
+    assert bool((small == 0x5A).all())
+    s2 = W.adc_samples(count, 683, sigma=40.0)  # larger m: the seed is too short for it
+    d2 = torch.from_numpy(s2).cuda()
+    out.fill_(0xA5)
+    with pytest.raises(qlib.QrngError) as e:
+        _run(qlib, gpu, d2, count, n, seed_dev, n + m1 - 1, STD, qlib.QRNG_ALGO_GEMM_KARATSUBA, out)
+    assert e.value.status == qlib.QRNG_EINVAL
+    qlib.qrng_synchronize(gpu)
+    assert bool((out == 0xA5).all())
+    for full in (True, False):
+        out.zero_()
+        m, nb, rep = _run(qlib, gpu, d1, count, n, seed_dev, n + m1 - 1, STD, qlib.QRNG_ALGO_GEMM_KARATSUBA, out)
+        _check(oracle_mod, qlib, s1, n, seed, STD, m, nb, rep, out, full=full)
+    hashes, misses = _spec_stats(qlib, gpu)
+    assert hashes == 4 and misses == 0, (hashes, misses)

@@ -342,6 +342,8 @@ QRNG_API int qrng_postprocess_host(qrng_ctx* ctx, const void* samples_host, uint
  * next call's upload then runs on a copy engine while this call hashes, and this call's download
  * while the next one hashes. Two calls' device buffers are kept (they alternate), so every call
  * returns once the call before it has finished hashing (its estimate waits for that on `stream`).
+ * A call after one of the same shape enqueues its hash before reading m, under the conditions and
+ * with the outcome qrng_postprocess states (the device buffers' alignment is the library's).
  * The caller keeps samples_host and out_host of a call untouched until a later
  * qrng_postprocess_host_wait has returned; pinned host memory is needed for the copies to
  * overlap. m_out, num_blocks_out and rep are written before the call returns.

@@ -1203,7 +1203,11 @@ int postprocess_speculative(qrng_ctx* ctx, const SpecPlan& sp, const void* sampl
   if (st) return st;
   ctx->kara.xk_ready = false;
   QRNG_CUDA(ctx, ctx->spec.ensure(sizeof(DevSpec)), "pipeline size word");
-  if (!ctx->spec_est) QRNG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->spec_est, cudaEventDisableTiming), "event");
+  if (!ctx->report_stream) {
+    QRNG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->report_stream, cudaStreamNonBlocking), "report stream");
+    QRNG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->spec_sized, cudaEventDisableTiming), "event");
+    QRNG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->spec_est, cudaEventDisableTiming), "event");
+  }
   const uint64_t m_cap = sp.m_cap;
   const uint64_t rev_words = kSeedFrontWords + ceil_div(n + m_cap - 1, 32) + kSeedBackWords;
   QRNG_CUDA(ctx, ctx->seed_rev.ensure(rev_words * 4), "seed workspace");
@@ -1250,10 +1254,17 @@ int postprocess_speculative(qrng_ctx* ctx, const SpecPlan& sp, const void* sampl
             launch_pipeline_size(ctx->result.as<DevHminResult>(), n, bits, lhl_term, m_cap, seed_capacity_bits,
                                  out_capacity_bytes, nb, dspec, s, &kernels),
             "pipeline size kernel");
-  QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->result_host, ctx->result.p, sizeof(DevHminResult), cudaMemcpyDeviceToHost, s),
+  // the report and m go to the host on a stream of their own, so the hash does not wait for them
+  // (this call waits for the copies before it returns: no later call rewrites them first)
+  QRNG_CUDA(ctx, cudaEventRecord(ctx->spec_sized, s), "pipeline event");
+  QRNG_CUDA(ctx, cudaStreamWaitEvent(ctx->report_stream, ctx->spec_sized, 0), "pipeline event");
+  QRNG_CUDA(ctx,
+            cudaMemcpyAsync(ctx->result_host, ctx->result.p, sizeof(DevHminResult), cudaMemcpyDeviceToHost,
+                            ctx->report_stream),
             "report copy");
-  QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->spec_host, dspec, sizeof(DevSpec), cudaMemcpyDeviceToHost, s), "size copy");
-  QRNG_CUDA(ctx, cudaEventRecord(ctx->spec_est, s), "pipeline event");
+  QRNG_CUDA(ctx, cudaMemcpyAsync(ctx->spec_host, dspec, sizeof(DevSpec), cudaMemcpyDeviceToHost, ctx->report_stream),
+            "size copy");
+  QRNG_CUDA(ctx, cudaEventRecord(ctx->spec_est, ctx->report_stream), "pipeline event");
   QRNG_CUDA(ctx, cudaStreamWaitEvent(s, ctx->pre_done, 0), "pipeline event");
   QRNG_CUDA(ctx,
             launch_gemm_karatsuba(a, sp.plan, ctx->kara, ctx->dev_err.as<int>(), 0, ctx->num_sms, s, &kernels,
@@ -1364,7 +1375,9 @@ void qrng_destroy(qrng_ctx* ctx) {
   ctx->fft.release();
   ctx->kara.release();
   ctx->spec.release();
+  if (ctx->spec_sized) cudaEventDestroy(ctx->spec_sized);
   if (ctx->spec_est) cudaEventDestroy(ctx->spec_est);
+  if (ctx->report_stream) cudaStreamDestroy(ctx->report_stream);
   drop_all_graphs(ctx);
   ctx->batch_meta.release();
   ctx->batch_raw.release();
@@ -1632,10 +1645,44 @@ int qrng_postprocess_host_async(qrng_ctx* ctx, const void* samples_host, uint64_
   QRNG_CUDA(ctx, cudaStreamWaitEvent(s, sl.uploaded, 0), "pipeline wait");
   const uint64_t num_blocks = n >= 2 ? bytes * 8 / n : 0;
   uint64_t m = 0;
+  if (num_blocks_out) *num_blocks_out = num_blocks;
+  SpecPlan sp;
+  if (eps_lhl > 0.0 && eps_lhl <= 1.0 && n <= kMaxBlockBits &&
+      spec_plan(ctx, sl.samples.p, count, bits, n, form, algo, num_blocks, seed_capacity_bits, sl.out.as<uint8_t>(),
+                &sp)) {
+    // the hash is enqueued before m is known (as qrng_postprocess does): the slot's output holds
+    // the enqueued rows, and its earlier download is over before the hash writes it
+    const uint64_t cap_bytes = ceil_div(num_blocks * sp.m_cap, 8);
+    if (sl.used && sl.out.cap < cap_bytes) QRNG_CUDA(ctx, cudaEventSynchronize(sl.downloaded), "pipeline wait");
+    QRNG_CUDA(ctx, sl.out.ensure(cap_bytes), "pipeline output workspace");
+    if (sl.used) QRNG_CUDA(ctx, cudaStreamWaitEvent(s, sl.downloaded, 0), "pipeline wait");
+    bool done = false;
+    st = postprocess_speculative(ctx, sp, sl.samples.p, count, bits, eps, eps_lhl, n, sl.seed.as<uint8_t>(),
+                                 seed_capacity_bits, sl.out.as<uint8_t>(), out_capacity_bytes, num_blocks, s, &m, rep,
+                                 &done);
+    if (m_out) *m_out = m;
+    if (st == QRNG_OK && !done) {  // m outside the enqueued rows: hash again with m
+      const uint64_t out_bytes = ceil_div(num_blocks * m, 8);
+      QRNG_CUDA(ctx, sl.out.ensure(out_bytes), "pipeline output workspace");
+      st = extract_dispatch(ctx, sl.samples.as<uint8_t>(), n, m, sl.seed.as<uint8_t>(), form, algo, num_blocks,
+                            sl.out.as<uint8_t>(), s);
+    }
+    ctx->kara.xk_ready = false;
+    QRNG_CUDA(ctx, cudaEventRecord(sl.computed, s), "pipeline event");
+    sl.used = true;
+    ++ctx->async_calls;
+    if (st) return st;
+    QRNG_CUDA(ctx, cudaStreamWaitEvent(ctx->down_stream, sl.computed, 0), "pipeline wait");
+    QRNG_CUDA(ctx,
+              cudaMemcpyAsync(out_host, sl.out.p, ceil_div(num_blocks * m, 8), cudaMemcpyDeviceToHost,
+                              ctx->down_stream),
+              "output download");
+    QRNG_CUDA(ctx, cudaEventRecord(sl.downloaded, ctx->down_stream), "pipeline event");
+    return QRNG_OK;
+  }
   st = pipeline_size(ctx, "qrng_postprocess_host_async", sl.samples.p, count, bits, eps, eps_lhl, n,
                      seed_capacity_bits, form, algo, num_blocks, s, &m, rep);
   if (m_out) *m_out = m;
-  if (num_blocks_out) *num_blocks_out = num_blocks;
   if (st) {
     sl.used = true;  // its upload is in flight: the next use of the slot orders after the compute stream
     QRNG_CUDA(ctx, cudaEventRecord(sl.computed, s), "pipeline event");

@@ -371,7 +371,8 @@ struct qrng_ctx {
   // the event after the report's copy
   qrng::DevBuf spec;
   qrng::DevSpec* spec_host = nullptr;
-  cudaEvent_t spec_est = nullptr;
+  cudaEvent_t spec_sized = nullptr, spec_est = nullptr;
+  cudaStream_t report_stream = nullptr;  // the report's read-back, beside the hash
   // the last pipeline call's stream shape and output length (predicts the next call's m)
   struct PipelineShape {
     uint64_t n, count;

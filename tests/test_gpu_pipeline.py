@@ -295,3 +295,42 @@ def test_speculative_hash_tight_seed_and_refusals(qlib, gpu, oracle_mod):
         _check(oracle_mod, qlib, s1, n, seed, STD, m, nb, rep, out, full=full)
     hashes, misses = _spec_stats(qlib, gpu)
     assert hashes == 4 and misses == 0, (hashes, misses)
+
+
+def test_host_async_speculative_calls(qlib, gpu, oracle_mod):
+    """The overlapped host pipeline enqueues the hash before reading m as qrng_postprocess does:
+    calls of one shape submitted back to back, new contents every call, one call whose m is above
+    the previous call's rows (hashed again with m), all outputs equal to the oracle's."""
+    import torch
+
+    n = 1 << 16
+    count = 3 << 19  # 192 blocks
+    qlib.qrng_set_karatsuba(gpu, 4, 256, 0)  # row span 4096
+    try:
+        seed = W.random_bits(2 * n - 1, 711)
+        pin_seed = torch.from_numpy(seed).pin_memory()
+        qlib.qrng_reset_stats(gpu)
+        done = []
+        for sseed, sigma in ((712, 6.0), (713, 6.0), (714, 30.0), (715, 30.0)):
+            samples = W.adc_samples(count, sseed, sigma=sigma)
+            pin_samples = torch.from_numpy(samples).pin_memory()
+            pin_out = torch.zeros(count, dtype=torch.uint8).pin_memory()
+            m, nb, rep = qlib.qrng_postprocess_host_async(gpu, pin_samples, count, 8, 1e-6, 1.0, n, pin_seed,
+                                                          2 * n - 1, STD, qlib.QRNG_ALGO_GEMM_KARATSUBA, pin_out,
+                                                          pin_out.numel())
+            done.append((samples, pin_samples, pin_out, m, nb, rep))
+        qlib.qrng_postprocess_host_wait(gpu)
+        ms = []
+        for samples, _, pin_out, m, nb, rep in done:
+            ref = oracle_mod.minentropy(samples, 8, 1e-6)
+            assert abs(rep["h_modify"] - ref["h_modify"]) < 1e-12
+            assert m == oracle_mod.output_length(n, ref["h_modify"], 8, 1.0)
+            got = pin_out.numpy()
+            assert not oracle_mod.freivalds(samples.view(np.uint8), n, m, seed, STD, nb, got[:(nb * m + 7) // 8]).any()
+            assert not got[(nb * m + 7) // 8:].any()
+            ms.append(m)
+        expect_miss = sum(int(ms[i] > min(n, -(-ms[i - 1] // 4096) * 4096)) for i in range(1, len(ms)))
+        s = qlib.qrng_get_stats(gpu)
+        assert s["speculative_hashes"] == 3 and s["speculative_misses"] == expect_miss == 1, (ms, s)
+    finally:
+        qlib.qrng_set_karatsuba(gpu, 0, 0, 0)

@@ -1191,17 +1191,21 @@ bool spec_plan(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, uin
 
 // Enqueues the speculative call and reads its report. *done: the output is written (or the call
 // refused, st != 0); otherwise the caller hashes with *m_out on the ordinary path.
+// ws and seed_rev hold the hash's derived operands, seeds and reversed seed; the second stream's
+// part waits for `inputs_ready` when given (the samples and seed are the library's own upload and
+// nothing on `s` touches ws or seed_rev before it), else for the work already on `s`.
 int postprocess_speculative(qrng_ctx* ctx, const SpecPlan& sp, const void* samples, uint64_t count, int bits,
                             double eps, double eps_lhl, uint64_t n, const uint8_t* seed, uint64_t seed_capacity_bits,
                             uint8_t* out, uint64_t out_capacity_bytes, uint64_t nb, cudaStream_t s, uint64_t* m_out,
-                            qrng_hmin_report* rep, bool* done) {
+                            qrng_hmin_report* rep, bool* done, KaraWorkspace& ws, DevBuf& seed_rev,
+                            cudaEvent_t inputs_ready = nullptr) {
   *done = false;
   *m_out = 0;
   const std::string w("qrng_postprocess");
   qrng_hmin_report local{};
   int st = check_minentropy_args(ctx, samples, count, bits, eps, &local);
   if (st) return st;
-  ctx->kara.xk_ready = false;
+  ws.xk_ready = false;
   QRNG_CUDA(ctx, ctx->spec.ensure(sizeof(DevSpec)), "pipeline size word");
   if (!ctx->report_stream) {
     QRNG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->report_stream, cudaStreamNonBlocking), "report stream");
@@ -1210,7 +1214,7 @@ int postprocess_speculative(qrng_ctx* ctx, const SpecPlan& sp, const void* sampl
   }
   const uint64_t m_cap = sp.m_cap;
   const uint64_t rev_words = kSeedFrontWords + ceil_div(n + m_cap - 1, 32) + kSeedBackWords;
-  QRNG_CUDA(ctx, ctx->seed_rev.ensure(rev_words * 4), "seed workspace");
+  QRNG_CUDA(ctx, seed_rev.ensure(rev_words * 4), "seed workspace");
   DirectArgs a{};
   a.raw = static_cast<const uint32_t*>(samples);
   a.raw_stride = n / 32;
@@ -1219,24 +1223,27 @@ int postprocess_speculative(qrng_ctx* ctx, const SpecPlan& sp, const void* sampl
   a.tail_mask = 0xffffffffu;  // n is a multiple of 128
   a.m = (uint32_t)m_cap;
   a.mw = (uint32_t)ceil_div(m_cap, 32);
-  a.seed_rev = ctx->seed_rev.as<uint32_t>();
+  a.seed_rev = seed_rev.as<uint32_t>();
   a.modified = 0;
   a.id_off = (uint32_t)(n - m_cap);
   a.out = nullptr;  // the combination writes the packed stream
   a.out_stride = a.mw;
   a.num_blocks = nb;
 
-  // second stream, after the work already on `s`: derived operands, reversed seed, derived seeds
+  // second stream: derived operands, reversed seed, derived seeds
   uint32_t kernels = 0;
-  QRNG_CUDA(ctx, cudaEventRecord(ctx->pre_ready, s), "pipeline event");
-  QRNG_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->pre_ready, 0), "pipeline event");
-  QRNG_CUDA(ctx, launch_kara_presplit(a, sp.plan, ctx->kara, ctx->num_sms, ctx->copy_stream, &kernels),
+  if (!inputs_ready) {
+    QRNG_CUDA(ctx, cudaEventRecord(ctx->pre_ready, s), "pipeline event");
+    inputs_ready = ctx->pre_ready;
+  }
+  QRNG_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, inputs_ready, 0), "pipeline event");
+  QRNG_CUDA(ctx, launch_kara_presplit(a, sp.plan, ws, ctx->num_sms, ctx->copy_stream, &kernels),
             "derived operands");
   ++ctx->stats.kara_presplits;
-  QRNG_CUDA(ctx, launch_seed_reverse(seed, n + m_cap - 1, ctx->seed_rev.as<uint32_t>(), rev_words, ctx->copy_stream,
+  QRNG_CUDA(ctx, launch_seed_reverse(seed, n + m_cap - 1, seed_rev.as<uint32_t>(), rev_words, ctx->copy_stream,
                                      &kernels),
             "seed reverse");
-  QRNG_CUDA(ctx, launch_kara_seeds(a, sp.plan, ctx->kara, ctx->copy_stream, &kernels), "derived seeds");
+  QRNG_CUDA(ctx, launch_kara_seeds(a, sp.plan, ws, ctx->copy_stream, &kernels), "derived seeds");
   QRNG_CUDA(ctx, cudaEventRecord(ctx->pre_done, ctx->copy_stream), "pipeline event");
   ctx->stats.kernels_launched += kernels;
   kernels = 0;
@@ -1245,7 +1252,7 @@ int postprocess_speculative(qrng_ctx* ctx, const SpecPlan& sp, const void* sampl
   st = minentropy_enqueue(ctx, samples, count, bits, eps, s);
   if (st) {
     cudaStreamSynchronize(ctx->copy_stream);
-    ctx->kara.xk_ready = false;
+    ws.xk_ready = false;
     return st;
   }
   DevSpec* dspec = ctx->spec.as<DevSpec>();
@@ -1267,10 +1274,10 @@ int postprocess_speculative(qrng_ctx* ctx, const SpecPlan& sp, const void* sampl
   QRNG_CUDA(ctx, cudaEventRecord(ctx->spec_est, ctx->report_stream), "pipeline event");
   QRNG_CUDA(ctx, cudaStreamWaitEvent(s, ctx->pre_done, 0), "pipeline event");
   QRNG_CUDA(ctx,
-            launch_gemm_karatsuba(a, sp.plan, ctx->kara, ctx->dev_err.as<int>(), 0, ctx->num_sms, s, &kernels,
+            launch_gemm_karatsuba(a, sp.plan, ws, ctx->dev_err.as<int>(), 0, ctx->num_sms, s, &kernels,
                                   extract_hook(ctx), out, dspec, true),
             "speculative block Karatsuba extraction");
-  ctx->kara.xk_ready = false;
+  ws.xk_ready = false;
   ctx->stats.kernels_launched += kernels;
   ++ctx->stats.speculative_hashes;
 
@@ -1396,6 +1403,8 @@ void qrng_destroy(qrng_ctx* ctx) {
     sl.samples.release();
     sl.seed.release();
     sl.out.release();
+    sl.kara.release();
+    sl.seed_rev.release();
     if (sl.uploaded) cudaEventDestroy(sl.uploaded);
     if (sl.computed) cudaEventDestroy(sl.computed);
     if (sl.downloaded) cudaEventDestroy(sl.downloaded);
@@ -1521,7 +1530,7 @@ int qrng_postprocess(qrng_ctx* ctx, const void* samples, uint64_t count, int bit
       spec_plan(ctx, samples, count, bits, n, form, algo, nb, seed_capacity_bits, out, &sp)) {
     bool done = false;
     int st = postprocess_speculative(ctx, sp, samples, count, bits, eps, eps_lhl, n, seed, seed_capacity_bits, out,
-                                     out_capacity_bytes, nb, s, &m, rep, &done);
+                                     out_capacity_bytes, nb, s, &m, rep, &done, ctx->kara, ctx->seed_rev);
     if (m_out) *m_out = m;
     if (st || done) return st;
     // the enqueued hash did not stand (m outside its rows): hash with m, as below
@@ -1659,7 +1668,7 @@ int qrng_postprocess_host_async(qrng_ctx* ctx, const void* samples_host, uint64_
     bool done = false;
     st = postprocess_speculative(ctx, sp, sl.samples.p, count, bits, eps, eps_lhl, n, sl.seed.as<uint8_t>(),
                                  seed_capacity_bits, sl.out.as<uint8_t>(), out_capacity_bytes, num_blocks, s, &m, rep,
-                                 &done);
+                                 &done, sl.kara, sl.seed_rev, sl.uploaded);
     if (m_out) *m_out = m;
     if (st == QRNG_OK && !done) {  // m outside the enqueued rows: hash again with m
       const uint64_t out_bytes = ceil_div(num_blocks * m, 8);
@@ -1776,7 +1785,8 @@ int qrng_get_stats(qrng_ctx* ctx, qrng_stats* out) {
   ctx->stats.worst_fft32_round_err = w32;
   ctx->stats.fft32_recomputed = repairs;
   ctx->stats.last_fft32_segment = ctx->last_fft32_log_s ? (1ull << ctx->last_fft32_log_s) : 0;
-  ctx->stats.kara_presplits_used = ctx->kara.presplits_used;
+  ctx->stats.kara_presplits_used =
+      ctx->kara.presplits_used + ctx->async_slot[0].kara.presplits_used + ctx->async_slot[1].kara.presplits_used;
   *out = ctx->stats;
   return QRNG_OK;
 }
@@ -1797,6 +1807,7 @@ int qrng_reset_stats(qrng_ctx* ctx) {
   ctx->ev_used = 0;
   ctx->stats = qrng_stats{};
   ctx->kara.presplits_used = 0;
+  for (auto& sl : ctx->async_slot) sl.kara.presplits_used = 0;
   QRNG_CUDA(ctx, cudaMemset(ctx->fft_worst.p, 0, 2 * sizeof(unsigned long long)), "FFT error reset");
   QRNG_CUDA(ctx, cudaMemset(ctx->fft32_guard.p, 0, 16), "repair count reset");
   return QRNG_OK;

@@ -390,6 +390,10 @@ struct qrng_ctx {
   // download (output) are done
   struct AsyncSlot {
     qrng::DevBuf samples, seed, out;
+    // the speculative hash's workspace of this slot's calls: the next call's derived operands and
+    // seeds are computed right after its upload, while the other slot's call still hashes
+    qrng::KaraWorkspace kara;
+    qrng::DevBuf seed_rev;
     cudaEvent_t uploaded = nullptr, computed = nullptr, downloaded = nullptr;
     bool used = false;
   };

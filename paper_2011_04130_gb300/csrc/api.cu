@@ -1205,6 +1205,12 @@ int postprocess_speculative(qrng_ctx* ctx, const SpecPlan& sp, const void* sampl
   qrng_hmin_report local{};
   int st = check_minentropy_args(ctx, samples, count, bits, eps, &local);
   if (st) return st;
+  // the derived operands enqueued below belong to this call's hash alone: whatever way the call
+  // returns, no later launch may take them for its own
+  struct NotReady {
+    KaraWorkspace& w;
+    ~NotReady() { w.xk_ready = false; }
+  } not_ready{ws};
   ws.xk_ready = false;
   QRNG_CUDA(ctx, ctx->spec.ensure(sizeof(DevSpec)), "pipeline size word");
   if (!ctx->report_stream) {

@@ -1191,14 +1191,16 @@ bool spec_plan(qrng_ctx* ctx, const void* samples, uint64_t count, int bits, uin
 
 // Enqueues the speculative call and reads its report. *done: the output is written (or the call
 // refused, st != 0); otherwise the caller hashes with *m_out on the ordinary path.
-// ws and seed_rev hold the hash's derived operands, seeds and reversed seed; the second stream's
-// part waits for `inputs_ready` when given (the samples and seed are the library's own upload and
-// nothing on `s` touches ws or seed_rev before it), else for the work already on `s`.
+// ws, seed_rev and spec_buf hold the hash's derived operands, seeds, reversed seed and device-side
+// m; the second stream's part waits for `inputs_ready` when given (the samples and seed are the
+// library's own upload and nothing on `s` touches those buffers before it), else for the work
+// already on `s`. With combine_stream the combination runs there, after the product.
 int postprocess_speculative(qrng_ctx* ctx, const SpecPlan& sp, const void* samples, uint64_t count, int bits,
                             double eps, double eps_lhl, uint64_t n, const uint8_t* seed, uint64_t seed_capacity_bits,
                             uint8_t* out, uint64_t out_capacity_bytes, uint64_t nb, cudaStream_t s, uint64_t* m_out,
                             qrng_hmin_report* rep, bool* done, KaraWorkspace& ws, DevBuf& seed_rev,
-                            cudaEvent_t inputs_ready = nullptr) {
+                            DevBuf& spec_buf, cudaEvent_t inputs_ready = nullptr,
+                            cudaStream_t combine_stream = nullptr) {
   *done = false;
   *m_out = 0;
   const std::string w("qrng_postprocess");
@@ -1212,11 +1214,13 @@ int postprocess_speculative(qrng_ctx* ctx, const SpecPlan& sp, const void* sampl
     ~NotReady() { w.xk_ready = false; }
   } not_ready{ws};
   ws.xk_ready = false;
-  QRNG_CUDA(ctx, ctx->spec.ensure(sizeof(DevSpec)), "pipeline size word");
+  QRNG_CUDA(ctx, spec_buf.ensure(sizeof(DevSpec)), "pipeline size word");
   if (!ctx->report_stream) {
     QRNG_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->report_stream, cudaStreamNonBlocking), "report stream");
     QRNG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->spec_sized, cudaEventDisableTiming), "event");
     QRNG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->spec_est, cudaEventDisableTiming), "event");
+    QRNG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->spec_product, cudaEventDisableTiming), "event");
+    QRNG_CUDA(ctx, cudaEventCreateWithFlags(&ctx->spec_hashed, cudaEventDisableTiming), "event");
   }
   const uint64_t m_cap = sp.m_cap;
   const uint64_t rev_words = kSeedFrontWords + ceil_div(n + m_cap - 1, 32) + kSeedBackWords;
@@ -1261,7 +1265,7 @@ int postprocess_speculative(qrng_ctx* ctx, const SpecPlan& sp, const void* sampl
     ws.xk_ready = false;
     return st;
   }
-  DevSpec* dspec = ctx->spec.as<DevSpec>();
+  DevSpec* dspec = spec_buf.as<DevSpec>();
   const double lhl_term = 2.0 * log2(1.0 / eps_lhl);  // as qrng_output_length forms it
   QRNG_CUDA(ctx,
             launch_pipeline_size(ctx->result.as<DevHminResult>(), n, bits, lhl_term, m_cap, seed_capacity_bits,
@@ -1281,7 +1285,8 @@ int postprocess_speculative(qrng_ctx* ctx, const SpecPlan& sp, const void* sampl
   QRNG_CUDA(ctx, cudaStreamWaitEvent(s, ctx->pre_done, 0), "pipeline event");
   QRNG_CUDA(ctx,
             launch_gemm_karatsuba(a, sp.plan, ws, ctx->dev_err.as<int>(), 0, ctx->num_sms, s, &kernels,
-                                  extract_hook(ctx), out, dspec, true),
+                                  extract_hook(ctx), out, dspec, true, combine_stream,
+                                  combine_stream ? ctx->spec_product : nullptr),
             "speculative block Karatsuba extraction");
   ws.xk_ready = false;
   ctx->stats.kernels_launched += kernels;
@@ -1389,6 +1394,8 @@ void qrng_destroy(qrng_ctx* ctx) {
   ctx->kara.release();
   ctx->spec.release();
   if (ctx->spec_sized) cudaEventDestroy(ctx->spec_sized);
+  if (ctx->spec_product) cudaEventDestroy(ctx->spec_product);
+  if (ctx->spec_hashed) cudaEventDestroy(ctx->spec_hashed);
   if (ctx->spec_est) cudaEventDestroy(ctx->spec_est);
   if (ctx->report_stream) cudaStreamDestroy(ctx->report_stream);
   drop_all_graphs(ctx);
@@ -1411,6 +1418,7 @@ void qrng_destroy(qrng_ctx* ctx) {
     sl.out.release();
     sl.kara.release();
     sl.seed_rev.release();
+    sl.spec.release();
     if (sl.uploaded) cudaEventDestroy(sl.uploaded);
     if (sl.computed) cudaEventDestroy(sl.computed);
     if (sl.downloaded) cudaEventDestroy(sl.downloaded);
@@ -1536,7 +1544,7 @@ int qrng_postprocess(qrng_ctx* ctx, const void* samples, uint64_t count, int bit
       spec_plan(ctx, samples, count, bits, n, form, algo, nb, seed_capacity_bits, out, &sp)) {
     bool done = false;
     int st = postprocess_speculative(ctx, sp, samples, count, bits, eps, eps_lhl, n, seed, seed_capacity_bits, out,
-                                     out_capacity_bytes, nb, s, &m, rep, &done, ctx->kara, ctx->seed_rev);
+                                     out_capacity_bytes, nb, s, &m, rep, &done, ctx->kara, ctx->seed_rev, ctx->spec);
     if (m_out) *m_out = m;
     if (st || done) return st;
     // the enqueued hash did not stand (m outside its rows): hash with m, as below
@@ -1671,19 +1679,32 @@ int qrng_postprocess_host_async(qrng_ctx* ctx, const void* samples_host, uint64_
     if (sl.used && sl.out.cap < cap_bytes) QRNG_CUDA(ctx, cudaEventSynchronize(sl.downloaded), "pipeline wait");
     QRNG_CUDA(ctx, sl.out.ensure(cap_bytes), "pipeline output workspace");
     if (sl.used) QRNG_CUDA(ctx, cudaStreamWaitEvent(s, sl.downloaded, 0), "pipeline wait");
+    // the combination runs on the download stream, right before this call's download (the slot's
+    // parities, size word and output are its own), so the caller's stream takes the next call's
+    // estimate as soon as the product has run
     bool done = false;
     st = postprocess_speculative(ctx, sp, sl.samples.p, count, bits, eps, eps_lhl, n, sl.seed.as<uint8_t>(),
                                  seed_capacity_bits, sl.out.as<uint8_t>(), out_capacity_bytes, num_blocks, s, &m, rep,
-                                 &done, sl.kara, sl.seed_rev, sl.uploaded);
+                                 &done, sl.kara, sl.seed_rev, sl.spec, sl.uploaded, ctx->down_stream);
     if (m_out) *m_out = m;
     if (st == QRNG_OK && !done) {  // m outside the enqueued rows: hash again with m
       const uint64_t out_bytes = ceil_div(num_blocks * m, 8);
+      if (sl.out.cap < out_bytes)  // growing frees the old buffer: the enqueued combination must be over
+        QRNG_CUDA(ctx, cudaStreamSynchronize(ctx->down_stream), "pipeline wait");
       QRNG_CUDA(ctx, sl.out.ensure(out_bytes), "pipeline output workspace");
       st = extract_dispatch(ctx, sl.samples.as<uint8_t>(), n, m, sl.seed.as<uint8_t>(), form, algo, num_blocks,
                             sl.out.as<uint8_t>(), s);
     }
     ctx->kara.xk_ready = false;
-    QRNG_CUDA(ctx, cudaEventRecord(sl.computed, s), "pipeline event");
+    // the slot's call is over once the caller's stream (the estimate, the product, a repeated hash)
+    // and the download stream (the combination) have passed it
+    if (ctx->spec_hashed) {
+      QRNG_CUDA(ctx, cudaEventRecord(ctx->spec_hashed, s), "pipeline event");
+      QRNG_CUDA(ctx, cudaStreamWaitEvent(ctx->down_stream, ctx->spec_hashed, 0), "pipeline wait");
+      QRNG_CUDA(ctx, cudaEventRecord(sl.computed, ctx->down_stream), "pipeline event");
+    } else {
+      QRNG_CUDA(ctx, cudaEventRecord(sl.computed, s), "pipeline event");
+    }
     sl.used = true;
     ++ctx->async_calls;
     if (st) return st;

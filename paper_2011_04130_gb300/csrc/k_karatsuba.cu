@@ -562,9 +562,11 @@ cudaError_t launch_kara_seeds(const DirectArgs& d, const KaraPlan& p, KaraWorksp
 
 cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWorkspace& ws, int* err, int fault,
                                   int num_sms, cudaStream_t s, uint32_t* kernels, const TimingHook& hook,
-                                  uint8_t* packed_out, const DevSpec* spec, bool seeds_done) {
+                                  uint8_t* packed_out, const DevSpec* spec, bool seeds_done,
+                                  cudaStream_t combine_stream, cudaEvent_t product_done) {
   if (p.levels < 1 || p.levels > kMaxLevels) return cudaErrorInvalidValue;
   if (spec && (!packed_out || !kara_speculation_fits(p, d.m, d.num_blocks))) return cudaErrorInvalidValue;
+  if (combine_stream && (!product_done || !packed_out || p.chunk_blocks < d.num_blocks)) return cudaErrorInvalidValue;
   const uint32_t G = p.groups;
   const uint32_t hw = (uint32_t)(p.h / 32);
   uint32_t log2h = 0;
@@ -611,6 +613,12 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
     hook.on_end(s);
     if (e != cudaSuccess) return e;
     const uint32_t rblocks = (uint32_t)ceil_div(d.m, p.span);
+    cudaStream_t cs = s;  // the combination's stream
+    if (combine_stream) {
+      if ((e = cudaEventRecord(product_done, s)) != cudaSuccess) return e;
+      if ((e = cudaStreamWaitEvent(combine_stream, product_done, 0)) != cudaSuccess) return e;
+      cs = combine_stream;
+    }
     if (packed_out) {  // combine and pack in one pass
       uint32_t* stream = reinterpret_cast<uint32_t*>(packed_out);
       const size_t bulk_smem = bulk_smem_bytes(p, d.mw);
@@ -619,10 +627,10 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
         const uint64_t ctas = (uint64_t)(num_sms > 0 ? num_sms : 1) * (per_sm < 8 ? per_sm : 8);
         const unsigned grid = (unsigned)(ctas < nb ? ctas : nb);
         switch (p.levels) {
-          case 1: e = launch_combine_pack_bulk<1>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err, spec); break;
-          case 2: e = launch_combine_pack_bulk<2>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err, spec); break;
-          case 3: e = launch_combine_pack_bulk<3>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err, spec); break;
-          default: e = launch_combine_pack_bulk<4>(grid, bulk_smem, s, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err, spec); break;
+          case 1: e = launch_combine_pack_bulk<1>(grid, bulk_smem, cs, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err, spec); break;
+          case 2: e = launch_combine_pack_bulk<2>(grid, bulk_smem, cs, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err, spec); break;
+          case 3: e = launch_combine_pack_bulk<3>(grid, bulk_smem, cs, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err, spec); break;
+          default: e = launch_combine_pack_bulk<4>(grid, bulk_smem, cs, k, (uint32_t)mwq, log2h, stream, nb, b0, d, dc, err, spec); break;
         }
         ++*kernels;
         if (e != cudaSuccess) return e;
@@ -634,10 +642,10 @@ cudaError_t launch_gemm_karatsuba(const DirectArgs& d, const KaraPlan& p, KaraWo
       const uint32_t cw = (uint32_t)(mwq < (uint64_t)room ? mwq : (uint64_t)room) & ~3u;
       const size_t smem = ((size_t)G * cw + d.mw) * sizeof(uint32_t);
       switch (p.levels) {
-        case 1: launch_combine_pack<1>(nb, smem, s, k, mwq, log2h, cw, stream, b0, d, dc); break;
-        case 2: launch_combine_pack<2>(nb, smem, s, k, mwq, log2h, cw, stream, b0, d, dc); break;
-        case 3: launch_combine_pack<3>(nb, smem, s, k, mwq, log2h, cw, stream, b0, d, dc); break;
-        default: launch_combine_pack<4>(nb, smem, s, k, mwq, log2h, cw, stream, b0, d, dc); break;
+        case 1: launch_combine_pack<1>(nb, smem, cs, k, mwq, log2h, cw, stream, b0, d, dc); break;
+        case 2: launch_combine_pack<2>(nb, smem, cs, k, mwq, log2h, cw, stream, b0, d, dc); break;
+        case 3: launch_combine_pack<3>(nb, smem, cs, k, mwq, log2h, cw, stream, b0, d, dc); break;
+        default: launch_combine_pack<4>(nb, smem, cs, k, mwq, log2h, cw, stream, b0, d, dc); break;
       }
       ++*kernels;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;

@@ -328,10 +328,13 @@ constexpr uint64_t kKaraPackMaxBits = 1ull << 18;  // 32 KB of output words per 
 // spec->m bits per block. It needs packed_out, one pass and the double-buffered combination
 // (kara_speculation_fits); seeds_done says the derived seeds are already enqueued
 // (launch_kara_seeds with the same a and plan).
+// With combine_stream (and an event product_done) the combination runs on that stream after the
+// product (recorded on `s`), so `s` is free for other work once the product has run.
 cudaError_t launch_gemm_karatsuba(const DirectArgs& a, const KaraPlan& plan, KaraWorkspace& ws, int* err, int fault,
                                   int num_sms, cudaStream_t s, uint32_t* kernels, const TimingHook& hook = TimingHook(),
                                   uint8_t* packed_out = nullptr, const DevSpec* spec = nullptr,
-                                  bool seeds_done = false);
+                                  bool seeds_done = false, cudaStream_t combine_stream = nullptr,
+                                  cudaEvent_t product_done = nullptr);
 // The derived seeds of a plan (3^levels windows of a.seed_rev), as launch_gemm_karatsuba enqueues
 // them first.
 cudaError_t launch_kara_seeds(const DirectArgs& a, const KaraPlan& plan, KaraWorkspace& ws, cudaStream_t s,
@@ -371,7 +374,7 @@ struct qrng_ctx {
   // the event after the report's copy
   qrng::DevBuf spec;
   qrng::DevSpec* spec_host = nullptr;
-  cudaEvent_t spec_sized = nullptr, spec_est = nullptr;
+  cudaEvent_t spec_sized = nullptr, spec_est = nullptr, spec_product = nullptr, spec_hashed = nullptr;
   cudaStream_t report_stream = nullptr;  // the report's read-back, beside the hash
   // the last pipeline call's stream shape and output length (predicts the next call's m)
   struct PipelineShape {
@@ -394,6 +397,7 @@ struct qrng_ctx {
     // seeds are computed right after its upload, while the other slot's call still hashes
     qrng::KaraWorkspace kara;
     qrng::DevBuf seed_rev;
+    qrng::DevBuf spec;  // the device-side m of the slot's call (its combination runs on the download stream)
     cudaEvent_t uploaded = nullptr, computed = nullptr, downloaded = nullptr;
     bool used = false;
   };

@@ -397,8 +397,8 @@ typedef struct {
  * timed launches to finish (it synchronises their events). */
 QRNG_API int qrng_get_stats(qrng_ctx* ctx, qrng_stats* out);
 
-/* The precision evidence of the transform routes alone (Sec. III.B, the FFT route; the north
- * star's precision pattern): the largest distance |s - round(s)| of a convolution sum from its
+/* The precision evidence of the transform routes alone (Sec. III.B, the FFT route, computed in
+ * floating point): the largest distance |s - round(s)| of a convolution sum from its
  * integer seen by the FP64 and FP32 segmented routes since creation or the last reset (0 when
  * neither ran; the number-theoretic transform is exact). Waits for the work that reports it. */
 QRNG_API int qrng_extract_stats(qrng_ctx* ctx, double* worst_fft_round_err);
